@@ -1,0 +1,125 @@
+"""Seeded synthetic inputs shared by the CUDA path's tests/bench and the CPU oracle.
+
+This module only DRAWS random inputs: candidate sets Gamma, supports I, Fourier
+coefficients, rank-1 lattice generating vectors z (given L and M), additive sample
+noise and the parameters of the sum-of-products test function.  It contains none of
+the reconstruction arithmetic (no hashing, no lattice nodes, no DFT, no parameter
+rule): callers obtain L and M from the method's own plan (GPU library) or from the
+oracle, and pass them in.
+
+Every generator takes an explicit integer seed and a stream tag, so that each input
+is reproducible on any machine (numpy's PCG64 bit generator, seeded through
+``SeedSequence([seed, stream])``).
+
+Workload recipes (shapes/distributions of the paper's experiments, Section 4):
+  * sparse trigonometric polynomial p(x)=sum_{k in I} c_k e^{2 pi i k.x}  (eq. 2.2)
+    with I drawn uniformly from Gamma;
+  * candidate sets: full grids [-N,N]^d (Section 4.2.1) or |Gamma| distinct vectors
+    drawn uniformly from a box (Section 4.1.2);
+  * coefficients: |c| ~ U[a,b] with uniform phase, complex Gaussian CN(0,1), or
+    uniform in [-1,1)+i[-1,1) with |c| >= 1e-6 (Section 4.2.1);
+  * additive complex Gaussian sample noise at a given SNR (dB);
+  * sum-of-products function f_theta = sum_m prod_{t in T_m} g_{theta_m}(x_t)
+    (a smooth periodic variant of eq. 4.3): random triples T_m and theta_m ~ U[0.5,2].
+"""
+from __future__ import annotations
+
+import numpy as np
+
+# stream tags (keep distinct per kind of draw)
+S_GAMMA, S_SUPPORT, S_COEF, S_Z, S_NOISE, S_SOP, S_TAIL, S_MISC = range(1, 9)
+
+
+def rng(seed: int, stream: int) -> np.random.Generator:
+    """Independent numpy Generator for (seed, stream)."""
+    return np.random.Generator(np.random.PCG64(np.random.SeedSequence([int(seed), int(stream)])))
+
+
+# --------------------------------------------------------------------------- candidate sets
+def full_grid(d: int, N: int) -> np.ndarray:
+    """All k in [-N, N]^d, lexicographic, int32 row-major [(2N+1)^d, d]."""
+    axes = [np.arange(-N, N + 1, dtype=np.int32)] * d
+    mesh = np.meshgrid(*axes, indexing="ij")
+    return np.ascontiguousarray(np.stack([m.reshape(-1) for m in mesh], axis=1).astype(np.int32))
+
+
+def uniform_distinct(n: int, d: int, lo: int, hi: int, seed: int, stream: int = S_GAMMA) -> np.ndarray:
+    """n distinct integer vectors drawn uniformly from [lo, hi]^d (int32 [n, d]).
+
+    Rows keep the order in which they were drawn (duplicates are dropped and redrawn).
+    """
+    g = rng(seed, stream)
+    out = np.empty((0, d), dtype=np.int32)
+    need = n
+    while need > 0:
+        draw = g.integers(lo, hi + 1, size=(need + need // 16 + 16, d), dtype=np.int32)
+        allr = np.concatenate([out, draw], axis=0)
+        _, first = np.unique(allr, axis=0, return_index=True)
+        keep = np.sort(first)
+        out = allr[keep][:n]
+        need = n - out.shape[0]
+    return np.ascontiguousarray(out.astype(np.int32))
+
+
+def support_indices(n_cand: int, s: int, seed: int, stream: int = S_SUPPORT) -> np.ndarray:
+    """s distinct indices into Gamma (ascending int64)."""
+    g = rng(seed, stream)
+    return np.sort(g.choice(n_cand, size=s, replace=False)).astype(np.int64)
+
+
+# --------------------------------------------------------------------------- coefficients
+def coef_mag_phase(s: int, lo: float, hi: float, seed: int, stream: int = S_COEF) -> np.ndarray:
+    g = rng(seed, stream)
+    mag = g.uniform(lo, hi, size=s)
+    ph = g.uniform(0.0, 2.0 * np.pi, size=s)
+    return mag * np.exp(1j * ph)
+
+
+def coef_cgauss(s: int, seed: int, stream: int = S_COEF) -> np.ndarray:
+    g = rng(seed, stream)
+    return (g.standard_normal(s) + 1j * g.standard_normal(s)) / np.sqrt(2.0)
+
+
+def coef_box(s: int, seed: int, stream: int = S_COEF, min_abs: float = 1e-6) -> np.ndarray:
+    """Uniform in [-1,1)+i[-1,1) with |c| >= min_abs (redrawn otherwise)."""
+    g = rng(seed, stream)
+    c = g.uniform(-1, 1, s) + 1j * g.uniform(-1, 1, s)
+    bad = np.abs(c) < min_abs
+    while bad.any():
+        c[bad] = g.uniform(-1, 1, bad.sum()) + 1j * g.uniform(-1, 1, bad.sum())
+        bad = np.abs(c) < min_abs
+    return c
+
+
+# --------------------------------------------------------------------------- lattices / noise
+def generators(L: int, d: int, M, seed: int, stream: int = S_Z) -> np.ndarray:
+    """Generating vectors z_l uniform in [0, M_l)^d (int64 [L, d]).  M: int or length-L."""
+    g = rng(seed, stream)
+    Ms = np.broadcast_to(np.asarray(M, dtype=np.int64), (L,))
+    return np.stack([g.integers(0, int(m), size=d, dtype=np.int64) for m in Ms], axis=0)
+
+
+def noise(n: int, sigma: float, seed: int, stream: int = S_NOISE) -> np.ndarray:
+    """Complex Gaussian noise with E|n|^2 = sigma^2 (complex128 [n])."""
+    g = rng(seed, stream)
+    return sigma * (g.standard_normal(n) + 1j * g.standard_normal(n)) / np.sqrt(2.0)
+
+
+def snr_sigma(coef: np.ndarray, snr_db: float) -> float:
+    """Per-sample noise std for a given SNR: signal power P = sum |c|^2 (mean |p(x)|^2)."""
+    P = float(np.sum(np.abs(coef) ** 2))
+    return float(np.sqrt(P / 10.0 ** (snr_db / 10.0)))
+
+
+# --------------------------------------------------------------------------- sum-of-products function
+def sop_params(d: int, n_terms: int, seed: int, stream: int = S_SOP, lo: float = 0.5, hi: float = 2.0):
+    """Random triples T_m (sorted, distinct dims) and theta_m ~ U[lo, hi]."""
+    g = rng(seed, stream)
+    triples = np.stack([np.sort(g.choice(d, size=3, replace=False)) for _ in range(n_terms)]).astype(np.int32)
+    theta = g.uniform(lo, hi, size=n_terms)
+    return triples, theta
+
+
+def uniform_tail(n: int, seed: int, stream: int = S_TAIL) -> np.ndarray:
+    g = rng(seed, stream)
+    return g.random(n)

@@ -1,0 +1,159 @@
+"""Pins of the oracle's Algorithms 1/2/4, the PFP/PFN audit (Section 4.1.1), the
+Remark 2.8 post-processing and the refinement step."""
+import itertools
+
+import numpy as np
+import pytest
+
+import oracle as O
+import sfft_synth as S
+
+
+def _cfg1(seed, s=20):
+    cand = S.full_grid(3, 16)
+    n = cand.shape[0]
+    L = O.L_cor26(n, 0.1)
+    M = O.lattice_size(cand, s)
+    sup = S.support_indices(n, s, seed)
+    c = S.coef_mag_phase(s, 1, 10, seed)
+    z = S.generators(L, 3, M, seed)
+    return cand, sup, c, z, M, L
+
+
+def test_cor26_exact_recovery_config1():
+    """Corollary 2.6 (delta = 0.1): with probability >= 0.9 the output equals (I, c) exactly."""
+    ok = 0
+    for seed in range(30):
+        cand, sup, c, z, M, L = _cfg1(seed)
+        y = O.sample_sparse_poly(cand[sup], c, z, M)
+        r = O.reconstruct(cand, y, z, M, tau_rel=1e-10)
+        if np.array_equal(r.supp, sup):
+            assert np.max(np.abs(r.coef - c)) <= 1e-12 * np.max(np.abs(c))
+            ok += 1
+    assert ok >= 27
+
+
+def test_full_grid_dft_brute_force_tiny():
+    """d = 2, Gamma = [-4,4]^2: a full 9x9 tensor-grid DFT gives every coefficient; a
+    successful Algorithm 2 run must return exactly its non-zero entries."""
+    N, d, s = 4, 2, 5
+    cand = S.full_grid(d, N)
+    n = cand.shape[0]
+    for seed in range(5):
+        sup = S.support_indices(n, s, seed)
+        c = S.coef_cgauss(s, seed)
+        K = 2 * N + 1
+        grid = np.array(list(itertools.product(range(K), repeat=d))) / K
+        vals = O.eval_sparse_poly(cand[sup], c, grid).reshape(K, K)
+        full = np.fft.fft2(vals) / K ** 2
+        ref = {tuple(k): full[k[0] % K, k[1] % K] for k in cand}
+        nz = sorted(i for i, k in enumerate(cand) if abs(ref[tuple(k)]) > 1e-9)
+        L = 31
+        M = O.lattice_size(cand, s)
+        z = S.generators(L, d, M, seed)
+        r = O.reconstruct(cand, O.sample_sparse_poly(cand[sup], c, z, M), z, M, tau_rel=1e-10)
+        assert list(r.supp) == nz
+        assert np.allclose(r.coef, [ref[tuple(cand[i])] for i in nz], atol=1e-12)
+
+
+def test_lemma_2_1_alias_rate():
+    """P(k aliases to another support element on one random lattice) <= |I|/M."""
+    d, s, M = 5, 40, 101
+    cand = S.uniform_distinct(2000, d, -30, 30, 11)
+    sup = S.support_indices(2000, s, 11)
+    hits, tot = 0, 0
+    for seed in range(60):
+        z = S.generators(1, d, M, 100 + seed)
+        H = O.hashes(cand, z, M)[:, 0]
+        hs = np.zeros(M, int)
+        np.add.at(hs, H[sup], 1)
+        inI = np.zeros(2000, bool)
+        inI[sup] = True
+        others = hs[H] - inI  # support elements other than k in k's bucket
+        hits += int((others > 0).sum())
+        tot += 2000
+    assert hits / tot <= s / M
+
+
+def test_alg1_nu_monotone():
+    cand, sup, c, z, M, L = _cfg1(3)
+    y = O.sample_sparse_poly(cand[sup], c, z[:9], M)
+    g = [O.lattice_dft(v, M) for v in O.split_lattices(y, [M] * 9)]
+    tau = O.zero_test_thresholds(g, 0, 1e-10)
+    d_half, _ = O.detect(cand, g, z[:9], [M] * 9, tau, 0.5)
+    d_low, _ = O.detect(cand, g, z[:9], [M] * 9, tau, 0.2)
+    assert set(d_half) <= set(d_low)
+    assert set(sup) <= set(d_low)
+
+
+def test_alg4_filter_and_ties():
+    coef = np.array([3.0, -3.0, 1j * 3.0, 0.5, 2.0, 1e-13])
+    pos = O.select_top(coef, 2, 1e-12)
+    assert list(pos) == [0, 1]  # three-way tie at |3|: lower positions win
+    pos = O.select_top(coef, 10, 1.0)
+    assert list(pos) == [0, 1, 2, 4]
+    assert list(O.select_top(coef, None, 0.0)) == [0, 1, 2, 3, 4, 5]
+
+
+def test_pfp_pfn_audit_brute_force():
+    """Section 4.1.1 / Table 4.1: a candidate is a PFP/PFN iff it aliases to another
+    support element on at least (L+1)/2 of the lattices."""
+    d, M, L = 3, 31, 5
+    cand = S.uniform_distinct(500, d, -12, 12, 9)
+    sup = S.support_indices(500, 12, 9)
+    z = S.generators(L, d, M, 9)
+    out = O.pfp_pfn(cand, sup, z, M)
+    inI = set(int(i) for i in sup)
+    pfp = pfn = 0
+    for i, k in enumerate(cand):
+        al = 0
+        for l in range(L):
+            hk = sum(int(a) * int(b) for a, b in zip(k, z[l])) % M
+            others = sum(1 for j in sup if j != i and sum(int(a) * int(b) for a, b in zip(cand[j], z[l])) % M == hk)
+            al += others > 0
+        if al >= (L + 1) // 2:
+            if i in inI:
+                pfn += 1
+            else:
+                pfp += 1
+    assert (out["n_pfp"], out["n_pfn"]) == (pfp, pfn)
+
+
+def test_refine_exact_fixed_point_and_modes():
+    cand, sup, c, z, M, L = _cfg1(4)
+    y = O.sample_sparse_poly(cand[sup], c, z, M)
+    r = O.reconstruct(cand, y, z, M, tau_rel=1e-10, do_refine=True)
+    assert np.array_equal(r.supp, sup)
+    assert np.max(np.abs(r.coef - c)) < 1e-12 * 10
+    # noisy samples: residual at the nodes (definition) == aliasing identity route
+    sig = S.snr_sigma(c, 30.0)
+    yn = y + S.noise(y.size, sig, 4)
+    sl = O.split_lattices(yn, [M] * L)
+    r0 = O.reconstruct(cand, yn, z, M, tau_abs=6 * sig / np.sqrt(M))
+    a = O.refine(sl, cand, r0.detected, r0.pcheck, z, [M] * L, "direct")
+    b = O.refine(sl, cand, r0.detected, r0.pcheck, z, [M] * L, "bucket")
+    assert np.allclose(a, b, atol=1e-11)
+    # with noise the refined coefficient is the median of (lattice value - other detected
+    # coefficients in the bucket); for a collision-free k it is the plain median again
+    free = np.ones(len(r0.detected), bool)
+    for l in range(L):
+        cnt = np.bincount(r0.H[:, l], minlength=M)
+        free &= cnt[r0.H[:, l]] == 1
+    assert np.allclose(a[free], r0.pcheck[free], atol=1e-12)
+
+
+def test_hybrid_postprocess_brute_force():
+    cand, sup, c, z, M, L = _cfg1(6, s=40)
+    y = O.sample_sparse_poly(cand[sup], c, z[:7], M)
+    r = O.reconstruct(cand, y, z[:7], M, tau_rel=1e-10, postproc="hybrid")
+    g = r.ghat
+    H = r.H
+    for q in range(len(r.detected)):
+        vals = []
+        for l in range(7):
+            if sum(1 for p in range(len(r.detected)) if H[p, l] == H[q, l]) == 1:
+                vals.append(g[l][H[q, l]])
+        expect = np.mean(vals) if vals else r.pcheck[q]
+        i = np.searchsorted(r.supp, r.detected[q])
+        if i < len(r.supp) and r.supp[i] == r.detected[q]:
+            assert abs(r.coef[i] - expect) < 1e-12

@@ -1,0 +1,98 @@
+"""Pins of the oracle's parameter rules (plan step) against numbers the paper prints."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from conftest import read_golden
+
+G41 = {r[0]: float(r[1]) for r in read_golden("section_4_1_numbers.txt")}
+
+
+def test_cor26_failure_bound_values_section_4_1_2():
+    # Section 4.1.2 prints the Corollary 2.6 failure bound for |Gamma| = 10^7, c = 10.33
+    for L in (37, 41, 47):
+        assert round(O.cor26_failure_bound(L, 10 ** 7), 3) == G41[f"cor26_bound_L{L}"]
+    assert round(1.0 - O.cor26_failure_bound(41, 10 ** 7), 2) == G41["cor26_success_L41"]
+    first = min(L for L in range(1, 99, 2) if O.cor26_failure_bound(L, 10 ** 7) < 1.0)
+    assert first == int(G41["cor26_first_nontrivial_L"])
+
+
+def test_cor26_bound_matches_paper_expression():
+    # the paper writes the same bound as 10^7 * 9.331^(-8.331/41.324 L)
+    for L in (29, 33, 37, 41):
+        paper = 1e7 * 9.331 ** (-8.331 / 41.324 * L)
+        assert O.cor26_failure_bound(L, 10 ** 7) == pytest.approx(paper, rel=2e-3)  # paper rounds c-1, 4c
+
+
+def test_lattice_sizes_printed_in_section_4_1():
+    assert O.next_prime_above(10.33 * 1000) == int(G41["lattice_size_s1000"])
+    assert O.next_prime_above(10.33 * 1069) == int(G41["lattice_size_s1069"])
+
+
+def test_distinct_node_counts_section_4_1():
+    # every rank-1 lattice contains the origin, so L lattices of size M have L*M-(L-1) distinct nodes
+    for L, M, key in ((33, 10331, "samples_L33_M10331"), (31, 11047, "samples_L31_M11047")):
+        assert L * M - (L - 1) == int(G41[key])
+        rng = np.random.default_rng(L)
+        z = rng.integers(0, M, size=(L, 3))
+        nodes = np.concatenate([O.lattice_numerators(z[l], M) for l in range(L)])
+        assert np.unique(nodes, axis=0).shape[0] == L * M - (L - 1)
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_theorem_1_1_bounds(seed):
+    # Theorem 1.1 (c = 10.33): M <= 127/11 |I|, L <= 3.183 (ln|Gamma| - ln delta), M L < 37 |I| (...)
+    rng = np.random.default_rng(seed)
+    for _ in range(40):
+        s = int(rng.integers(1, 20000))
+        n = int(rng.integers(8, 10 ** 8))
+        delta = float(rng.uniform(1e-6, 0.999))
+        M = O.next_prime_above(O.C_DEFAULT * s)
+        L = O.L_cor26(n, delta)
+        lg = math.log(n) - math.log(delta)
+        assert M <= 127.0 / 11.0 * s
+        assert L <= 3.183 * lg
+        assert M * L < 37 * s * lg
+
+
+def test_cor26_rule_values():
+    assert O.L_cor26(35937, 0.1) == 29
+    assert O.L_cor26(2 ** 20, 0.1) == 37
+    assert O.L_cor26(2 ** 20, 0.1) % 2 == 1
+    # general-nu Theorem 2.2 count reduces to Corollary 2.6's constant at nu = 1/2
+    c = O.C_DEFAULT
+    assert c * (c - 2) / ((c / 2 - 1) ** 2 * math.log(c - 1)) == pytest.approx(4 * c / ((c - 2) * math.log(c - 1)))
+
+
+def test_fallback_rule():
+    L = O.L_fallback(35937)
+    assert L % 2 == 1 and L >= math.ceil(2 * math.log(35937)) + 1
+    P = O.fallback_primes(L, 20)
+    assert P[0] == 83 and len(P) == L and all(O.is_prime(p) for p in P) and P == sorted(P)
+
+
+def test_lattice_size_admissibility():
+    # |Gamma mod M| = |Gamma| is required; a prime below N_Gamma that folds Gamma is skipped
+    cand = np.array([[0, 0], [11, 0], [5, 3]], dtype=np.int64)  # N_Gamma = 11; 11 folds (0,0) and (11,0)
+    assert O.mod_set_size(cand, 11) == 2
+    M = O.lattice_size(cand, 1, c=10.5)  # smallest prime > 10.5 is 11 -> inadmissible -> 13
+    assert M == 13
+    assert O.expansion(cand) == 11
+
+
+def test_table_4_2_sample_rule(golden):
+    """Table 4.2: M = nextprime(10.33 s) and L by eq. (4.2) with |J_2| = K^2, |J_t| = s K.
+    With |I| = 1000 consecutive rows differ by exactly 5 (L M + K): Step 1 adds K = 65 samples
+    per dimension and Step 2 one Algorithm-4 call of L = 7 lattices of size M = 10331."""
+    tab = {(int(r[0]), int(r[1])): int(r[2]) for r in golden("table_4_2_samples.txt")}
+    M = O.next_prime_above(10.33 * 1000)
+    L = O.L_eq42(1000 * 65, 0.9)
+    assert (M, L, O.L_eq42(65 * 65, 0.9)) == (10331, 7, 5)
+    for d0, d1 in ((10, 15), (25, 30)):
+        assert tab[(d1, 1000)] - tab[(d0, 1000)] == 5 * (L * M + 65)
+    # Steps 1 + 2 of the rule never exceed the table; Step 3 adds the rest (a few % at most)
+    for (d, s), v in tab.items():
+        ours = O.dim_incremental_sample_count(d, 65, s)
+        assert ours <= v <= 1.03 * ours + 25000, (d, s, ours, v)
