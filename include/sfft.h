@@ -1,0 +1,256 @@
+/*
+ * sfft.h -- C ABI of a GB300 (sm_103a) implementation of the sparse FFT for arbitrary
+ * frequency candidate sets by Kaemmerer, Krahmer and Volkmer (arXiv 2006.13053).
+ *
+ * Notation follows the paper: Gamma (the candidate set, "cand") is a finite set of integer
+ * frequency vectors k in Z^d; the unknown function is sampled along L rank-1 lattices
+ * Lambda(z_l, M_l) = { j z_l / M_l mod 1 : j = 0..M_l-1 } (Section 2.1, eq. 2.1); each
+ * lattice's samples are transformed by a length-M_l DFT (Algorithm 2, line 2); a candidate
+ * k is detected when its buckets ghat^(l)_{k.z_l mod M_l} are non-zero for at least nu*L
+ * lattices (Algorithm 1; nu = 1/2 in Algorithm 2) and its coefficient is the component-wise
+ * median of those L bucket values (Algorithm 2, eq. 2.6).  Algorithm 4 then keeps the
+ * s_tilde largest coefficients of modulus >= theta.  Algorithm 3 is the
+ * dimension-incremental driver around Algorithm 4.
+ *
+ * Conventions (every entry point):
+ *   - returns an int status: SFFT_OK (0) or one of the SFFT_E* codes below; nothing throws
+ *     across the ABI.  sfft_last_error() returns a message for the calling thread's last
+ *     failure.
+ *   - "device" pointers are CUDA device memory of the current device (e.g. a torch tensor's
+ *     data_ptr()); "host" pointers are ordinary host memory.  The caller owns every buffer
+ *     it passes; the library never frees them.  A plan owns its own workspace, released by
+ *     sfft_plan_destroy().
+ *   - complex arrays are interleaved (re, im) pairs.  Arrays documented as "complex in the
+ *     plan precision" are float2 for SFFT_FP32 plans and double2 for SFFT_FP64 plans; arrays
+ *     documented as "complex double" are always double2.
+ *   - samples of all lattices are concatenated in lattice order l = 0..L-1; inside lattice l
+ *     the node order is j = 0..M_l-1 (eq. 2.1).  offsets[l] = M_0 + ... + M_{l-1}.
+ *   - stream: a cudaStream_t passed as void* (NULL = legacy default stream).  Work is
+ *     enqueued on it; entry points that return host-side counts synchronise it.
+ */
+#ifndef SFFT_H
+#define SFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define SFFT_OK 0
+#define SFFT_EINVAL 1      /* invalid argument (null pointer, size out of range, even L ...)    */
+#define SFFT_ENOTPRIME 2   /* a lattice size M_l is not prime                                  */
+#define SFFT_EALIAS 3      /* |Gamma mod M_l| < |Gamma| could not be excluded (M_l <= N_Gamma) */
+#define SFFT_EOVERFLOW 4   /* |k.z| bound does not fit the exact 32-bit hash arithmetic        */
+#define SFFT_ENOMEM 5      /* device allocation failed                                         */
+#define SFFT_ECUDA 6       /* a CUDA runtime call failed                                       */
+#define SFFT_ETIMEOUT 7    /* a bounded device-side wait gave up                               */
+#define SFFT_ECAPACITY 8   /* a caller- or plan-sized buffer was too small (count still set)   */
+#define SFFT_ESTATE 9      /* call out of order (e.g. backward before forward)                 */
+
+/* ---------------------------------------------------------------- parameters */
+#define SFFT_FP64 0 /* samples, twiddles and FFT arithmetic in double                         */
+#define SFFT_FP32 1 /* samples, twiddles and FFT arithmetic in float (FP32 accumulation)      */
+
+#define SFFT_L_COR26 0    /* L = min odd n >= 4c/((c-2)ln(c-1)) (ln|Gamma| - ln delta), Cor 2.6 */
+#define SFFT_L_EQ42 1     /* a quarter of the Cor 2.6 bound, rounded up to odd, eq. (4.2)       */
+#define SFFT_L_FALLBACK 2 /* L = ceil(2 ln|Gamma|)+1 rounded up to odd; M_l = L smallest primes >= 4s */
+
+#define SFFT_COMBINE_MEDIAN 0 /* eq. (2.6): component-wise median over the L lattices             */
+#define SFFT_COMBINE_HYBRID 1 /* Remark 2.8: mean over collision-free lattices, median fallback    */
+
+typedef struct sfft_params {
+    double c;         /* Cor 2.6 constant (> 1/nu); default 10.33 (Theorem 1.1)                */
+    double delta;     /* failure probability in the L rule; default 0.1                        */
+    double nu;        /* detection fraction of Algorithm 1, 0 < nu <= 1/2; default 1/2 (Alg 2) */
+    double tau_abs;   /* zero test (Remark 2.3): |ghat| > tau_l counts as non-zero, where      */
+    double tau_rel;   /*   tau_l = max(tau_abs, tau_rel * max_h |ghat^(l)_h|); default 0, 1e-10 */
+    double theta_abs; /* Algorithm 4 threshold theta = max(theta_abs, theta_rel * max|c|)      */
+    double theta_rel; /*   defaults 0, 0                                                       */
+    int64_t s_tilde;  /* Algorithm 4 output limit; 0 = keep every detected frequency (Alg 2)  */
+    int precision;    /* SFFT_FP64 or SFFT_FP32                                                */
+    int refine;       /* number of FP64 refinement steps on the detected support (0 or 1)     */
+    int L_rule;       /* SFFT_L_* (used when the caller does not fix L)                       */
+    int combine;      /* SFFT_COMBINE_*                                                       */
+    uint64_t seed;    /* key of the Philox4x64-10 draws of generating vectors                  */
+    int64_t detect_cap; /* capacity for |Itilde|; 0 = max(4 s + 4096, 16384)                  */
+} sfft_params;
+
+/* Fill *p with the defaults listed above.  Never fails. */
+void sfft_params_default(sfft_params* p);
+
+/* ---------------------------------------------------------------- plans (Algorithm 2 / 4) */
+typedef struct sfft_plan sfft_plan;
+
+/*
+ * Create a plan for candidates Gamma = cand (device int32, row-major [n_cand, d], not copied:
+ * it must stay valid and unchanged until the plan is destroyed) and sparsity s.
+ *   L     > 0: number of lattices (must be odd for the median, Algorithm 2), or 0: take L
+ *              from p->L_rule with |Gamma| = n_cand (Corollary 2.6 / eq. 4.2 / fallback).
+ *   M     host int64 [L] lattice sizes (each prime), or NULL: M_l = the smallest prime
+ *              > c*s (Corollary 2.6), or the fallback primes.  M_l <= N_Gamma (eq. 2.4) is
+ *              rejected with SFFT_EALIAS.
+ *   z     host int64 [L, d] generating vectors with 0 <= z < M_l, or NULL: drawn as
+ *              z_{l,u} = Philox4x64-10(counter=(u, l, 0, 0), key=(seed, 0)).word0 mod M_l.
+ * Needs 1 <= d <= 32, n_cand >= 1, s >= 1, |k_t| small enough that d*max|k|*(M-1) < 2^31
+ * (else SFFT_EOVERFLOW).  Precomputes chirps and Bluestein filters on `stream`.
+ */
+int sfft_plan_create(sfft_plan** out, int d, const int32_t* cand, int64_t n_cand, int64_t s, int L,
+                     const int64_t* M, const int64_t* z, const sfft_params* p, void* stream);
+
+/* L, the lattice sizes M (host int64 [L], optional), z (host int64 [L*d], optional) and the
+ * total number of samples sum_l M_l (optional). */
+int sfft_plan_info(const sfft_plan* plan, int* L, int64_t* M, int64_t* z, int64_t* n_samples);
+
+void sfft_plan_destroy(sfft_plan* plan);
+
+/*
+ * Lattice nodes of eq. (2.1): numer_out (device int32 [sum M, d], optional) receives the exact
+ * integers (j z_l mod M_l); x_out (device double [sum M, d], optional) receives numer / M_l;
+ * offsets (host int64 [L+1], optional) the lattice offsets.
+ */
+int sfft_sample_points(const sfft_plan* plan, int32_t* numer_out, double* x_out, int64_t* offsets);
+
+/* Optional diagnostics of sfft_reconstruct (any member may be NULL / ignored). */
+typedef struct sfft_diag {
+    uint8_t* counts;     /* device [n_cand]: n_k = #{l : |ghat^(l)_{h_kl}| > tau_l}          */
+    int32_t* hashes;     /* device [n_cand, L]: h_kl = k.z_l mod M_l                         */
+    int32_t* collisions; /* device [sum M]: c_l[h] = #{k in Itilde : h_kl = h} (Remark 2.8)  */
+    int64_t* detected;   /* device [detect_cap]: Itilde (indices into Gamma, ascending)       */
+    double* pcheck;      /* device complex double [detect_cap]: medians of Itilde (eq. 2.6)   */
+    double* ghat;        /* device complex double [sum M]: lattice DFTs (Alg 2 line 2)        */
+    double* tau;         /* device double [L]: zero-test thresholds                           */
+    int64_t n_detected;  /* out: |Itilde|                                                     */
+    int64_t n_guard;     /* out: buckets whose zero test was re-done in FP64                  */
+} sfft_diag;
+
+/*
+ * Algorithm 2 (nu = 1/2) or 1 on the plan's Gamma, followed by the optional Remark 2.8
+ * combine, the optional FP64 refinement step(s) and Algorithm 4's theta filter and
+ * top-s_tilde selection.
+ *   samples  device complex in the plan precision [sum M]: f at the lattice nodes.
+ *   supp_out device int64 [cap]: selected indices into Gamma, ascending.
+ *   coef_out device complex double [cap]: their coefficients.
+ *   n_out    host: number of selected frequencies (may exceed cap -> SFFT_ECAPACITY).
+ * Synchronises the plan's stream.
+ */
+int sfft_reconstruct(sfft_plan* plan, const void* samples, int64_t* supp_out, double* coef_out, int64_t cap,
+                     int64_t* n_out, sfft_diag* diag);
+
+/*
+ * Vector-Jacobian product of the last sfft_reconstruct of this plan (refine == 0 only), with
+ * the selected support and the median's selected lattices held fixed: coefficient q is
+ * Re ghat^(l_re)_{h} + i Im ghat^(l_im)_{h}, so the cotangents are scattered into those
+ * buckets and mapped back by the adjoint of the 1/M-normalised DFT (an inverse prime-length
+ * FFT).  dcoef: device complex double [n_out of that call] (dL/dRe + i dL/dIm);
+ * dsamples: device complex in the plan precision [sum M] (overwritten).
+ */
+int sfft_reconstruct_backward(sfft_plan* plan, const double* dcoef, void* dsamples);
+
+/* ---------------------------------------------------------------- synthetic test functions */
+/*
+ * Samples of the sparse trigonometric polynomial p(x) = sum_q coef_q exp(2 pi i kvec_q . x)
+ * (eq. 2.2) at the plan's lattice nodes, plus optional additive noise:
+ *   kvec  device int32 [n_terms, d];  coef device complex double [n_terms];
+ *   noise device complex double [sum M] or NULL;  samples_out device complex (plan precision).
+ * Computed exactly through eq. (2.3): the coefficients are scattered into their buckets
+ * k.z_l mod M_l and each lattice is inverse-transformed.
+ */
+int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const double* coef, int64_t n_terms,
+                            const double* noise, void* samples_out);
+
+/*
+ * Samples of the sum-of-products function f(x) = sum_m prod_{t in T_m} g_{theta_m}(x_t) with
+ * g_theta(x) = sum_{|k| <= K} sinc(pi k / (width theta))^4 exp(2 pi i k x) (real valued).
+ *   triples host int32 [n_terms, 3] (dimensions < d); theta device double [n_terms].
+ * samples_out device complex (plan precision; imaginary parts are 0).
+ */
+int sfft_sample_sop(const sfft_plan* plan, const int32_t* triples, const double* theta, int n_terms, int K,
+                    double width, void* samples_out);
+
+/*
+ * Adjoint of sfft_sample_sop with respect to theta: dtheta[m] = sum_j Re(dsamples_j)
+ * d f(x_j) / d theta_m, recomputing f's factors at the nodes instead of storing them.
+ *   dsamples device complex (plan precision) [sum M]; dtheta device double [n_terms] (overwritten).
+ */
+int sfft_sample_sop_backward(const sfft_plan* plan, const int32_t* triples, const double* theta, int n_terms,
+                             int K, double width, const void* dsamples, double* dtheta);
+
+/* ---------------------------------------------------------------- batched reconstruction */
+typedef struct sfft_batch sfft_batch;
+
+/*
+ * Group n_plans plans (same precision) so that sfft_batch_reconstruct runs every stage of all
+ * of them in shared launches (one launch per stage for the whole batch).  The plans must
+ * outlive the batch.  use_graph != 0 captures the stage sequence once into a CUDA graph on
+ * `stream` and replays it on later calls (samples/outputs must then keep their addresses).
+ */
+int sfft_batch_create(sfft_batch** out, sfft_plan* const* plans, int n_plans, int use_graph, void* stream);
+void sfft_batch_destroy(sfft_batch* b);
+
+/*
+ * Run sfft_reconstruct for every plan of the batch.  samples[i], supp_out[i], coef_out[i]:
+ * device pointers as in sfft_reconstruct; cap[i] host capacities; n_out_dev device int64
+ * [n_plans] receives the counts.  Does not synchronise (counts stay on the device).
+ */
+int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* const* supp_out,
+                           double* const* coef_out, const int64_t* cap, int64_t* n_out_dev);
+
+/* ---------------------------------------------------------------- Algorithm 3 */
+/*
+ * Black-box function for Algorithm 3: evaluate f at n nodes x (device double [n, d],
+ * row-major) into y (device complex double [n]); return 0 on success.
+ */
+typedef int (*sfft_sample_fn)(void* ctx, const double* x, int64_t n, double* y, void* stream);
+
+typedef struct sfft_dimincr_params {
+    int64_t s;         /* sparsity (sets M_l = smallest prime > c s)                        */
+    int64_t s_local;   /* Step 1 / Step 2 (t < d) output size; default 2 s                  */
+    int r;             /* number of detection iterations                                    */
+    double theta_abs;  /* Algorithm 3/4 threshold (absolute) ...                            */
+    double theta_rel;  /* ... or relative to the largest modulus of the current call        */
+    double delta;      /* eq. (4.2) failure parameter                                       */
+    double c;          /* lattice-size constant (10.33)                                      */
+    double tau_abs, tau_rel; /* zero test                                                   */
+    int precision;     /* SFFT_FP64 / SFFT_FP32                                              */
+    int refine;        /* FP64 refinement steps per Algorithm 4 call                          */
+    uint64_t seed;     /* Philox key; draws documented in the implementation                 */
+    int64_t max_samples; /* 0 = unlimited; otherwise stop with SFFT_ECAPACITY                */
+} sfft_dimincr_params;
+
+void sfft_dimincr_params_default(sfft_dimincr_params* p);
+
+/*
+ * Algorithm 3 with Algorithm 4 as Algorithm A on Gamma = the box prod_t [box_lo[t], box_hi[t]]
+ * (host int32 [d] each).  supp_out host int32 [cap, d] (lexicographic order), coef_out host
+ * complex double [cap]; n_out host; n_samples (optional host) = function evaluations used.
+ */
+int sfft_dim_incremental(int d, const int32_t* box_lo, const int32_t* box_hi, const sfft_dimincr_params* p,
+                         sfft_sample_fn f, void* ctx, int32_t* supp_out, double* coef_out, int64_t cap,
+                         int64_t* n_out, int64_t* n_samples, void* stream);
+
+/* Built-in black boxes for Algorithm 3 (ctx = a struct owned by the caller):
+ *   sfft_fn_sparse_poly: ctx = sfft_fn_sparse_poly_ctx (device kvec int32 [n, d], device coef complex double [n]);
+ *   sfft_fn_sop:         ctx = sfft_fn_sop_ctx (host triples int32 [n_terms*3], device theta double [n_terms]). */
+typedef struct sfft_fn_sparse_poly_ctx { const int32_t* kvec; const double* coef; int64_t n_terms; int d; } sfft_fn_sparse_poly_ctx;
+typedef struct sfft_fn_sop_ctx { const int32_t* triples; const double* theta; int n_terms; int K; double width; int d; } sfft_fn_sop_ctx;
+int sfft_fn_sparse_poly(void* ctx, const double* x, int64_t n, double* y, void* stream);
+int sfft_fn_sop(void* ctx, const double* x, int64_t n, double* y, void* stream);
+
+/* ---------------------------------------------------------------- host utilities */
+/* Word 0 of Philox4x64-10 (Salmon et al., SC'11) for counter (c0..c3) and key (key0, 0). */
+uint64_t sfft_philox4x64_word0(uint64_t key0, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3);
+
+/* Smallest prime > x; L of the Cor 2.6 / eq. 4.2 / fallback rules (host, no device work). */
+int64_t sfft_next_prime_above(double x);
+int sfft_L_rule(int rule, int64_t n_cand, double delta, double c);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* sfft_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SFFT_H */

@@ -1,0 +1,9 @@
+"""GB300 (sm_103a) implementation of the rank-1-lattice sparse FFT for arbitrary frequency
+candidate sets (Kaemmerer, Krahmer, Volkmer, arXiv 2006.13053).
+
+The CUDA library libsfft.so (C ABI in include/sfft.h) does all computation; this package
+binds it.  Importing the package fails when the library has not been built.
+"""
+from ._native import (COMBINE_HYBRID, COMBINE_MEDIAN, FP32, FP64, L_COR26, L_EQ42, L_FALLBACK,  # noqa: F401
+                      SfftError, default_dimincr_params, default_params)
+from .api import Plan, SopReconstruct  # noqa: F401

@@ -1,0 +1,194 @@
+"""Python face of the CUDA library: thin wrappers that pass torch device tensors to the C ABI.
+
+    plan = Plan(cand, s, precision=FP32, refine=1, tau_abs=...)   # cand: int32 cuda [n, d]
+    supp, coef = plan.reconstruct(samples)                         # samples: complex cuda [sum M]
+
+All arithmetic runs in libsfft.so; no step falls back to PyTorch or the CPU.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+import torch
+
+from . import _native as N
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def _req(t, dtype, name):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dtype and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA tensor of dtype {dtype}")
+    return t
+
+
+class Plan:
+    """A reconstruction plan (Algorithm 2/4) over the candidate set `cand` (kept referenced)."""
+
+    def __init__(self, cand: torch.Tensor, s: int, L: int = 0, M=None, z=None, stream=None, **params):
+        _req(cand, torch.int32, "cand")
+        if cand.dim() != 2:
+            raise ValueError("cand must be [n, d]")
+        self.cand = cand
+        self.n, self.d = cand.shape
+        self.params = N.default_params(**params)
+        self.stream = stream
+        Mp = zp = None
+        if M is not None:
+            M = np.ascontiguousarray(np.broadcast_to(np.asarray(M, dtype=np.int64), (L,)))
+            Mp = M.ctypes.data_as(C.c_void_p)
+        if z is not None:
+            z = np.ascontiguousarray(np.asarray(z, dtype=np.int64))
+            zp = z.ctypes.data_as(C.c_void_p)
+        h = C.c_void_p()
+        N.check(N.sfft_plan_create(C.byref(h), self.d, C.c_void_p(cand.data_ptr()), self.n, int(s), int(L), Mp, zp,
+                                   C.byref(self.params), _stream(stream)))
+        self.handle = h
+        Lr = C.c_int()
+        ns = C.c_int64()
+        N.check(N.sfft_plan_info(h, C.byref(Lr), None, None, C.byref(ns)))
+        self.L = Lr.value
+        self.n_samples = ns.value
+        Ma = np.zeros(self.L, dtype=np.int64)
+        za = np.zeros(self.L * self.d, dtype=np.int64)
+        N.check(N.sfft_plan_info(h, None, Ma.ctypes.data_as(C.c_void_p), za.ctypes.data_as(C.c_void_p), None))
+        self.M = Ma
+        self.z = za.reshape(self.L, self.d)
+        self.offsets = np.concatenate([[0], np.cumsum(Ma)]).astype(np.int64)
+        self.cdtype = torch.complex64 if self.params.precision == N.FP32 else torch.complex128
+        self.last_nout = 0
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.sfft_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- nodes and samplers
+    def sample_points(self):
+        """(numerators int32 [sum M, d], x float64 [sum M, d]) of eq. (2.1)."""
+        dev = self.cand.device
+        num = torch.empty((self.n_samples, self.d), dtype=torch.int32, device=dev)
+        x = torch.empty((self.n_samples, self.d), dtype=torch.float64, device=dev)
+        N.check(N.sfft_sample_points(self.handle, _ptr(num), _ptr(x), None))
+        return num, x
+
+    def sample_sparse_poly(self, kvec, coef, noise=None, out=None):
+        _req(kvec, torch.int32, "kvec")
+        _req(coef, torch.complex128, "coef")
+        if noise is not None:
+            _req(noise, torch.complex128, "noise")
+        out = out if out is not None else torch.empty(self.n_samples, dtype=self.cdtype, device=self.cand.device)
+        N.check(N.sfft_sample_sparse_poly(self.handle, _ptr(kvec), _ptr(coef), kvec.shape[0], _ptr(noise), _ptr(out)))
+        return out
+
+    def sample_sop(self, triples, theta, K=48, width=32.0, out=None):
+        tri = np.ascontiguousarray(np.asarray(triples, dtype=np.int32))
+        _req(theta, torch.float64, "theta")
+        out = out if out is not None else torch.empty(self.n_samples, dtype=self.cdtype, device=self.cand.device)
+        N.check(N.sfft_sample_sop(self.handle, tri.ctypes.data_as(C.c_void_p), _ptr(theta), tri.shape[0], K,
+                                  float(width), _ptr(out)))
+        return out
+
+    def sample_sop_backward(self, triples, theta, dsamples, K=48, width=32.0):
+        tri = np.ascontiguousarray(np.asarray(triples, dtype=np.int32))
+        _req(theta, torch.float64, "theta")
+        _req(dsamples, self.cdtype, "dsamples")
+        dtheta = torch.empty(tri.shape[0], dtype=torch.float64, device=self.cand.device)
+        N.check(N.sfft_sample_sop_backward(self.handle, tri.ctypes.data_as(C.c_void_p), _ptr(theta), tri.shape[0], K,
+                                           float(width), _ptr(dsamples), _ptr(dtheta)))
+        return dtheta
+
+    # ---------------------------------------------------------------- reconstruction
+    def reconstruct(self, samples, cap=None, diag=False, counts=False, hashes=False, collisions=False):
+        """Returns (supp int64 [k], coef complex128 [k]) and, with diag=True, a dict of diagnostics."""
+        _req(samples, self.cdtype, "samples")
+        dev = self.cand.device
+        cap = int(cap if cap is not None else max(self.params.s_tilde or 0, 1) + 4 * 4096)
+        supp = torch.empty(cap, dtype=torch.int64, device=dev)
+        coef = torch.empty(cap, dtype=torch.complex128, device=dev)
+        nout = C.c_int64()
+        D = None
+        info = {}
+        if diag or counts or hashes or collisions:
+            D = N.Diag()
+            dcap = self.n  # >= the plan's detected-set capacity
+            info["detected_buf"] = torch.empty(dcap, dtype=torch.int64, device=dev)
+            info["pcheck_buf"] = torch.empty(dcap, dtype=torch.complex128, device=dev)
+            info["ghat"] = torch.empty(self.n_samples, dtype=torch.complex128, device=dev)
+            info["tau"] = torch.empty(self.L, dtype=torch.float64, device=dev)
+            D.detected = info["detected_buf"].data_ptr()
+            D.pcheck = info["pcheck_buf"].data_ptr()
+            D.ghat = info["ghat"].data_ptr()
+            D.tau = info["tau"].data_ptr()
+            if counts:
+                info["counts"] = torch.empty(self.n, dtype=torch.uint8, device=dev)
+                D.counts = info["counts"].data_ptr()
+            if hashes:
+                info["hashes"] = torch.empty((self.n, self.L), dtype=torch.int32, device=dev)
+                D.hashes = info["hashes"].data_ptr()
+            if collisions:
+                info["collisions"] = torch.empty(self.n_samples, dtype=torch.int32, device=dev)
+                D.collisions = info["collisions"].data_ptr()
+        rc = N.sfft_reconstruct(self.handle, _ptr(samples), _ptr(supp), _ptr(coef), cap, C.byref(nout),
+                                C.byref(D) if D is not None else None)
+        N.check(rc)
+        k = nout.value
+        self.last_nout = k
+        if D is not None:
+            nd = D.n_detected
+            info["n_detected"] = nd
+            info["n_guard"] = D.n_guard
+            info["detected"] = info.pop("detected_buf")[:nd]
+            info["pcheck"] = info.pop("pcheck_buf")[:nd]
+            return supp[:k], coef[:k], info
+        return supp[:k], coef[:k]
+
+    def backward(self, dcoef):
+        """Sample cotangents for coefficient cotangents of the last reconstruct (support fixed)."""
+        _req(dcoef, torch.complex128, "dcoef")
+        if dcoef.shape[0] != self.last_nout:
+            raise ValueError("dcoef must match the last reconstruct's output size")
+        ds = torch.empty(self.n_samples, dtype=self.cdtype, device=self.cand.device)
+        N.check(N.sfft_reconstruct_backward(self.handle, _ptr(dcoef), _ptr(ds)))
+        return ds
+
+
+class SopReconstruct(torch.autograd.Function):
+    """theta -> samples of the sum-of-products function at the plan's lattice nodes ->
+    reconstructed coefficients on the selected support.  The backward pass runs the adjoint
+    kernels (coefficient cotangents -> buckets -> inverse prime-length FFT -> samples -> theta),
+    recomputing the samples' factors instead of storing them."""
+
+    @staticmethod
+    def forward(ctx, theta, plan, triples, K, width):
+        samples = plan.sample_sop(triples, theta, K=K, width=width)
+        supp, coef = plan.reconstruct(samples)
+        ctx.plan, ctx.triples, ctx.K, ctx.width = plan, triples, K, width
+        ctx.save_for_backward(theta)
+        ctx.mark_non_differentiable(supp)
+        return supp, coef
+
+    @staticmethod
+    def backward(ctx, gsupp, gcoef):
+        (theta,) = ctx.saved_tensors
+        plan = ctx.plan
+        if gcoef is None:
+            return None, None, None, None, None
+        # torch's complex gradient convention for a real loss is dL/dRe + i dL/dIm
+        ds = plan.backward(gcoef.contiguous().to(torch.complex128))
+        dtheta = plan.sample_sop_backward(ctx.triples, theta, ds, K=ctx.K, width=ctx.width)
+        return dtheta, None, None, None, None

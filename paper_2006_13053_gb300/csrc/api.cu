@@ -1,0 +1,627 @@
+// C ABI of the library: plans (Corollary 2.6 / eq. 4.2 parameter rules, lattice generation),
+// workspace layout, and the stage sequence of one reconstruction (Algorithm 2 -> optional
+// Remark 2.8 combine -> optional FP64 refinement -> Algorithm 4 selection), the synthetic
+// samplers and the adjoint.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "plan.cuh"
+
+namespace sfft {
+
+// ================================================================== errors
+static thread_local std::string g_err;
+void set_error(const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+}
+const char* get_error() { return g_err.c_str(); }
+
+// ================================================================== Philox4x64-10 (Salmon et al., SC'11)
+uint64_t philox_word0(uint64_t key0, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3) {
+    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
+    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
+    uint64_t x0 = c0, x1 = c1, x2 = c2, x3 = c3, k0 = key0, k1 = 0;
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) { k0 += W0; k1 += W1; }
+        unsigned __int128 p0 = (unsigned __int128)M0 * x0, p1 = (unsigned __int128)M1 * x2;
+        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0, hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
+        uint64_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ k1;
+        x0 = n0; x1 = lo1; x2 = n2; x3 = lo0;
+    }
+    return x0;
+}
+
+double philox_u01(uint64_t key, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3) {
+    return (double)(philox_word0(key, c0, c1, c2, c3) >> 11) * (1.0 / 9007199254740992.0);
+}
+
+// ================================================================== number theory / rules
+static uint64_t mulmod(uint64_t a, uint64_t b, uint64_t m) { return (uint64_t)((unsigned __int128)a * b % m); }
+static uint64_t powmod(uint64_t a, uint64_t e, uint64_t m) {
+    uint64_t r = 1;
+    a %= m;
+    while (e) {
+        if (e & 1) r = mulmod(r, a, m);
+        a = mulmod(a, a, m);
+        e >>= 1;
+    }
+    return r;
+}
+bool is_prime(int64_t n) {
+    if (n < 2) return false;
+    for (int64_t p : {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37}) {
+        if (n % p == 0) return n == p;
+    }
+    uint64_t d = (uint64_t)n - 1;
+    int s = 0;
+    while ((d & 1) == 0) { d >>= 1; ++s; }
+    for (uint64_t a : {2ull, 3ull, 5ull, 7ull, 11ull, 13ull, 17ull, 19ull, 23ull, 29ull, 31ull, 37ull}) {
+        uint64_t x = powmod(a, d, (uint64_t)n);
+        if (x == 1 || x == (uint64_t)n - 1) continue;
+        bool comp = true;
+        for (int r = 1; r < s; ++r) {
+            x = mulmod(x, x, (uint64_t)n);
+            if (x == (uint64_t)n - 1) { comp = false; break; }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+int64_t next_prime_above(double x) {
+    int64_t p = (int64_t)floor(x) + 1;
+    if (p < 2) p = 2;
+    while (!is_prime(p)) ++p;
+    return p;
+}
+static int odd_ceil(double v) {
+    int n = (int)ceil(v - 1e-12);
+    if (n < 1) n = 1;
+    return (n % 2) ? n : n + 1;
+}
+int L_rule(int rule, int64_t n, double delta, double c) {
+    const double base = 4.0 * c / ((c - 2.0) * log(c - 1.0)) * (log((double)n) - log(delta));
+    switch (rule) {
+        case SFFT_L_COR26: return odd_ceil(base);
+        case SFFT_L_EQ42: return odd_ceil(0.25 * base);
+        default: {
+            int v = (int)ceil(2.0 * log((double)n)) + 1;
+            return (v % 2) ? v : v + 1;
+        }
+    }
+}
+
+// ================================================================== plan lifecycle
+static int dmalloc(void** p, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        set_error("cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        return SFFT_ENOMEM;
+    }
+    return SFFT_OK;
+}
+#define DMALLOC(ptr, bytes) SFFT_TRY(dmalloc((void**)&(ptr), (bytes)))
+
+void Plan::release() {
+    for (void* p : allocs) cudaFree(p);
+    allocs.clear();
+    for (auto* t : tabs) tables_release(t);
+    tabs.clear();
+    if (h_inst) cudaFreeHost(h_inst);
+    if (h_cnt) cudaFreeHost(h_cnt);
+    h_inst = nullptr;
+    h_cnt = nullptr;
+}
+
+int Plan::alloc(void** p, size_t bytes) {
+    SFFT_TRY(dmalloc(p, bytes));
+    allocs.push_back(*p);
+    return SFFT_OK;
+}
+
+size_t Plan::esz() const { return prec ? sizeof(c32) : sizeof(c64); }
+
+static BlueJob make_job(const FftTables* t, int prec, int dir, double scale) {
+    BlueJob J;
+    memset(&J, 0, sizeof J);
+    J.M = (int)t->M;
+    J.N = (int)t->N;
+    J.nstages = t->nstages;
+    for (int s = 0; s < t->nstages; ++s) J.radix[s] = (uint8_t)t->radix[s];
+    J.tw = prec ? (const void*)t->tw32 : (const void*)t->tw64;
+    J.chirp = prec ? (const void*)t->chirp32 : (const void*)t->chirp64;
+    J.filt = prec ? (const void*)t->filt32[dir] : (const void*)t->filt64[dir];
+    J.dft64 = (const double*)t->dft64;
+    J.scale = scale;
+    return J;
+}
+
+bool Plan::fits_smem(int tprec) const {
+    size_t e = tprec ? sizeof(c32) : sizeof(c64);
+    return (size_t)maxN * e <= blue_smem_limit();
+}
+
+int Plan::build_jobs() {
+    const size_t e = esz();
+    char* ghat_b = (char*)ghat;
+    char* resid_b = (char*)resid;
+    char* rhat_b = (char*)rhat;
+    jobs_fwd.clear(); jobs_model.clear(); jobs_rfwd.clear();
+    for (int l = 0; l < L; ++l) {
+        const FftTables* t = tabs[l];
+        const int64_t o = soff[l];
+        // forward analyse: ghat = DFT(samples)/M (plan precision)
+        BlueJob a = make_job(t, prec, 0, 1.0 / (double)M[l]);
+        a.io_flags = 1; a.io_off = o; a.inst = 0;
+        a.out = ghat_b + o * e;
+        a.stat = stats + l;
+        a.scratch = fits_smem(prec) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
+        jobs_fwd.push_back(a);
+        // refinement model: resid = samples - IDFT(C) in FP64
+        BlueJob m = make_job(t, 0, 1, 1.0);
+        m.in = C + o; m.out = resid_b + o * e; m.io_flags = 2; m.io_off = o; m.inst = 0;
+        m.scratch = fits_smem(0) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
+        jobs_model.push_back(m);
+        // refinement forward: rhat = DFT(resid)/M (plan precision)
+        BlueJob r = make_job(t, prec, 0, 1.0 / (double)M[l]);
+        r.in = resid_b + o * e; r.out = rhat_b + o * e;
+        r.scratch = a.scratch;
+        jobs_rfwd.push_back(r);
+    }
+    return SFFT_OK;
+}
+
+// upload a job list into a device array (static lists: once at plan creation)
+int upload_jobs(const std::vector<BlueJob>& v, BlueJob** dst, std::vector<void*>* owner) {
+    SFFT_TRY(dmalloc((void**)dst, sizeof(BlueJob) * std::max<size_t>(1, v.size())));
+    owner->push_back(*dst);
+    SFFT_CU(cudaMemcpy(*dst, v.data(), sizeof(BlueJob) * v.size(), cudaMemcpyHostToDevice));
+    return SFFT_OK;
+}
+
+int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int Lin, const int64_t* Min,
+                const int64_t* zin, const sfft_params* pin, cudaStream_t st) {
+    sfft_params p;
+    if (pin) p = *pin; else sfft_params_default(&p);
+    SFFT_CHECK(d >= 1 && d <= kMaxD, SFFT_EINVAL, "d=%d must be in [1, %d]", d, kMaxD);
+    SFFT_CHECK(cand != nullptr && n >= 1, SFFT_EINVAL, "empty candidate set");
+    SFFT_CHECK(n < ((int64_t)1 << 31), SFFT_EINVAL, "|Gamma| must be < 2^31");
+    SFFT_CHECK(s >= 1, SFFT_EINVAL, "s must be >= 1");
+    SFFT_CHECK(p.nu > 0 && p.nu <= 0.5, SFFT_EINVAL, "nu must be in (0, 1/2]");
+    SFFT_CHECK(p.c > 1.0 / p.nu && p.c > 2.0, SFFT_EINVAL, "c must exceed max(2, 1/nu)");
+    SFFT_CHECK(p.delta > 0 && p.delta < 1, SFFT_EINVAL, "delta must be in (0, 1)");
+    SFFT_CHECK(p.precision == SFFT_FP64 || p.precision == SFFT_FP32, SFFT_EINVAL, "bad precision");
+    SFFT_CHECK(p.refine == 0 || p.refine == 1, SFFT_EINVAL, "refine must be 0 or 1");
+    P->d = d; P->cand = cand; P->n = n; P->s = s; P->p = p; P->prec = p.precision; P->st = st;
+    // ---- L and M (Corollary 2.6 / eq. 4.2 / fallback)
+    int L = Lin > 0 ? Lin : L_rule(p.L_rule, n, p.delta, p.c);
+    SFFT_CHECK(L >= 1 && L <= kMaxL, SFFT_EINVAL, "L=%d must be in [1, %d]", L, kMaxL);
+    SFFT_CHECK(L % 2 == 1, SFFT_EINVAL, "L=%d must be odd (component-wise median, Algorithm 2)", L);
+    P->L = L;
+    P->M.resize(L);
+    if (Min) {
+        for (int l = 0; l < L; ++l) P->M[l] = Min[l];
+    } else if (p.L_rule == SFFT_L_FALLBACK) {
+        int64_t q = next_prime_above((double)(4 * s - 1));
+        for (int l = 0; l < L; ++l) { P->M[l] = q; q = next_prime_above((double)q); }
+    } else {
+        int64_t q = next_prime_above(p.c * (double)s);
+        for (int l = 0; l < L; ++l) P->M[l] = q;
+    }
+    for (int l = 0; l < L; ++l) {
+        SFFT_CHECK(P->M[l] >= 2 && P->M[l] < (1 << 27), SFFT_EINVAL, "M_%d=%lld out of range", l, (long long)P->M[l]);
+        SFFT_CHECK(is_prime(P->M[l]), SFFT_ENOTPRIME, "M_%d=%lld is not prime", l, (long long)P->M[l]);
+    }
+    // ---- candidate bounds: N_Gamma (eq. 2.4) and max |k_t|
+    {
+        int *dmn = nullptr, *dmx = nullptr;
+        SFFT_TRY(P->alloc((void**)&dmn, sizeof(int) * d));
+        SFFT_TRY(P->alloc((void**)&dmx, sizeof(int) * d));
+        std::vector<int> mn(d, INT32_MAX), mx(d, INT32_MIN);
+        SFFT_CU(cudaMemcpyAsync(dmn, mn.data(), sizeof(int) * d, cudaMemcpyHostToDevice, st));
+        SFFT_CU(cudaMemcpyAsync(dmx, mx.data(), sizeof(int) * d, cudaMemcpyHostToDevice, st));
+        SFFT_TRY(launch_cand_stats(cand, n, d, dmn, dmx, st));
+        SFFT_CU(cudaMemcpyAsync(mn.data(), dmn, sizeof(int) * d, cudaMemcpyDeviceToHost, st));
+        SFFT_CU(cudaMemcpyAsync(mx.data(), dmx, sizeof(int) * d, cudaMemcpyDeviceToHost, st));
+        SFFT_CU(cudaStreamSynchronize(st));
+        int64_t NG = 0, kmax = 0;
+        for (int t = 0; t < d; ++t) {
+            NG = std::max<int64_t>(NG, (int64_t)mx[t] - mn[t]);
+            kmax = std::max<int64_t>(kmax, std::max<int64_t>(std::llabs(mn[t]), std::llabs(mx[t])));
+        }
+        P->N_gamma = NG;
+        P->kmax = kmax;
+    }
+    for (int l = 0; l < L; ++l) {
+        SFFT_CHECK(P->M[l] > P->N_gamma, SFFT_EALIAS,
+                   "M_%d=%lld <= N_Gamma=%lld: |Gamma mod M| = |Gamma| is not guaranteed (pass an admissible M)", l,
+                   (long long)P->M[l], (long long)P->N_gamma);
+        const double bound = (double)d * (double)P->kmax * (double)(P->M[l] - 1);
+        SFFT_CHECK(bound + (double)P->M[l] < 2147483647.0, SFFT_EOVERFLOW,
+                   "d*max|k|*(M-1) = %.0f does not fit the exact 32-bit hash", bound);
+    }
+    // ---- generating vectors
+    P->z.resize((size_t)L * d);
+    for (int l = 0; l < L; ++l)
+        for (int t = 0; t < d; ++t) {
+            int64_t v;
+            if (zin) v = zin[(size_t)l * d + t];
+            else v = (int64_t)(philox_word0(p.seed, (uint64_t)t, (uint64_t)l, 0, 0) % (uint64_t)P->M[l]);
+            SFFT_CHECK(v >= 0 && v < P->M[l], SFFT_EINVAL, "z[%d][%d]=%lld outside [0, M)", l, t, (long long)v);
+            P->z[(size_t)l * d + t] = v;
+        }
+    // ---- offsets and tables
+    P->soff.assign(L + 1, 0);
+    P->boff.assign(L, 0);
+    int64_t words = 0;
+    for (int l = 0; l < L; ++l) {
+        P->soff[l + 1] = P->soff[l] + P->M[l];
+        P->boff[l] = (int32_t)words;
+        words += (P->M[l] + 31) / 32;
+    }
+    P->nwords = (int)words;
+    P->sumM = P->soff[L];
+    P->maxN = 0;
+    for (int l = 0; l < L; ++l) {
+        FftTables* t = nullptr;
+        SFFT_TRY(tables_acquire(P->M[l], &t));
+        P->tabs.push_back(t);
+        P->maxN = std::max<int>(P->maxN, (int)t->N);
+    }
+    // ---- workspace
+    const int64_t cap = std::min<int64_t>(n, p.detect_cap > 0 ? p.detect_cap : std::max<int64_t>(4 * s + 4096, 16384));
+    P->cap = cap;
+    const size_t e = P->esz();
+    std::vector<int32_t> z32(P->z.begin(), P->z.end()), M32(P->M.begin(), P->M.end());
+    std::vector<uint32_t> mu(L), offk(L);
+    for (int l = 0; l < L; ++l) {
+        mu[l] = (uint32_t)((1ull << 32) / (uint64_t)P->M[l]);
+        const double bound = (double)d * (double)P->kmax * (double)(P->M[l] - 1);
+        offk[l] = (uint32_t)(P->M[l] * ((int64_t)ceil(bound / (double)P->M[l]) + 1));
+    }
+    int32_t *dz, *dM, *dboff;
+    uint32_t *dmu, *doffk;
+    int64_t* dsoff;
+    SFFT_TRY(P->alloc((void**)&dz, sizeof(int32_t) * z32.size()));
+    SFFT_TRY(P->alloc((void**)&dM, sizeof(int32_t) * L));
+    SFFT_TRY(P->alloc((void**)&dmu, sizeof(uint32_t) * L));
+    SFFT_TRY(P->alloc((void**)&doffk, sizeof(uint32_t) * L));
+    SFFT_TRY(P->alloc((void**)&dsoff, sizeof(int64_t) * (L + 1)));
+    SFFT_TRY(P->alloc((void**)&dboff, sizeof(int32_t) * L));
+    SFFT_CU(cudaMemcpy(dz, z32.data(), sizeof(int32_t) * z32.size(), cudaMemcpyHostToDevice));
+    SFFT_CU(cudaMemcpy(dM, M32.data(), sizeof(int32_t) * L, cudaMemcpyHostToDevice));
+    SFFT_CU(cudaMemcpy(dmu, mu.data(), sizeof(uint32_t) * L, cudaMemcpyHostToDevice));
+    SFFT_CU(cudaMemcpy(doffk, offk.data(), sizeof(uint32_t) * L, cudaMemcpyHostToDevice));
+    SFFT_CU(cudaMemcpy(dsoff, P->soff.data(), sizeof(int64_t) * (L + 1), cudaMemcpyHostToDevice));
+    SFFT_CU(cudaMemcpy(dboff, P->boff.data(), sizeof(int32_t) * L, cudaMemcpyHostToDevice));
+    SFFT_TRY(P->alloc((void**)&P->nzbits, sizeof(uint32_t) * words));
+    SFFT_TRY(P->alloc(&P->ghat, e * P->sumM));
+    SFFT_TRY(P->alloc((void**)&P->stats, sizeof(LatStats) * L));
+    SFFT_TRY(P->alloc((void**)&P->detbits, sizeof(uint32_t) * ((n + 31) / 32)));
+    SFFT_TRY(P->alloc((void**)&P->det, sizeof(int64_t) * cap));
+    SFFT_TRY(P->alloc((void**)&P->cnt, sizeof(int64_t) * 8));
+    SFFT_TRY(P->alloc((void**)&P->coef, sizeof(c64) * cap));
+    SFFT_TRY(P->alloc((void**)&P->H, sizeof(int32_t) * cap * L));
+    SFFT_TRY(P->alloc((void**)&P->sel, 2 * cap));
+    SFFT_TRY(P->alloc((void**)&P->outpos, sizeof(int32_t) * cap));
+    SFFT_TRY(P->alloc((void**)&P->coll, sizeof(int32_t) * P->sumM));
+    SFFT_TRY(P->alloc((void**)&P->C, sizeof(c64) * P->sumM));
+    SFFT_TRY(P->alloc(&P->rhat, e * P->sumM));
+    SFFT_TRY(P->alloc(&P->resid, e * P->sumM));
+    if (!P->fits_smem(0) || !P->fits_smem(P->prec))
+        SFFT_TRY(P->alloc(&P->scratch, sizeof(c64) * (size_t)P->maxN * L));
+    SFFT_TRY(P->alloc((void**)&P->sop_a, sizeof(double) * 2 * 16 * 129));
+    SFFT_TRY(P->alloc((void**)&P->sop_tri, sizeof(int32_t) * 3 * 16));
+    SFFT_TRY(P->alloc((void**)&P->d_jobs_tmp, sizeof(BlueJob) * L));
+    // ---- instance descriptor
+    SFFT_CU(cudaMallocHost((void**)&P->h_inst, sizeof(InstDesc)));
+    SFFT_CU(cudaMallocHost((void**)&P->h_cnt, sizeof(int64_t) * 8));
+    InstDesc& I = *P->h_inst;
+    memset(&I, 0, sizeof I);
+    I.d = d; I.L = L; I.prec = P->prec; I.combine = p.combine; I.nwords = (int)words;
+    I.need = (int)ceil(p.nu * L - 1e-9);
+    I.n = n; I.cap = cap; I.s_tilde = p.s_tilde;
+    I.tau_abs = p.tau_abs; I.tau_rel = p.tau_rel; I.theta_abs = p.theta_abs; I.theta_rel = p.theta_rel;
+    I.cand = cand; I.z = dz; I.Ml = dM; I.mu = dmu; I.offk = doffk; I.soff = dsoff; I.boff = dboff;
+    I.nzbits = P->nzbits; I.ghat = P->ghat; I.stats = P->stats; I.detbits = P->detbits; I.det = P->det;
+    I.cnt = P->cnt; I.coef = P->coef; I.H = P->H; I.sel = P->sel; I.coll = P->coll; I.C = P->C;
+    I.rhat = P->rhat; I.resid = P->resid; I.outpos = P->outpos;
+    SFFT_TRY(P->alloc((void**)&P->d_inst, sizeof(InstDesc)));
+    SFFT_CU(cudaMemcpy(P->d_inst, &I, sizeof(InstDesc), cudaMemcpyHostToDevice));
+    // ---- lattice descriptors and static transform jobs
+    std::vector<LatDesc> lats(L);
+    for (int l = 0; l < L; ++l) {
+        lats[l] = LatDesc{0, l, (int)P->M[l], (int)P->tabs[l]->N, P->soff[l], P->boff[l], 0,
+                          (const double*)P->tabs[l]->dft64};
+    }
+    SFFT_TRY(P->alloc((void**)&P->d_lats, sizeof(LatDesc) * L));
+    SFFT_CU(cudaMemcpy(P->d_lats, lats.data(), sizeof(LatDesc) * L, cudaMemcpyHostToDevice));
+    SFFT_TRY(P->build_jobs());
+    SFFT_TRY(upload_jobs(P->jobs_fwd, &P->d_jobs_fwd, &P->allocs));
+    SFFT_TRY(upload_jobs(P->jobs_model, &P->d_jobs_model, &P->allocs));
+    SFFT_TRY(upload_jobs(P->jobs_rfwd, &P->d_jobs_rfwd, &P->allocs));
+    // hash-count launch shape: one full wave of CTAs
+    P->hash_smem = sizeof(uint32_t) * (size_t)words + sizeof(int32_t) * (size_t)L * (d + 4);
+    SFFT_CHECK(P->hash_smem <= 220 * 1024, SFFT_EINVAL,
+               "non-zero bitmap of %lld words does not fit shared memory", (long long)words);
+    return SFFT_OK;
+}
+
+// ================================================================== the reconstruction stage sequence
+// Runs every stage for `ninst` instances described by d_inst (all of precision prec).
+int run_pipeline(const PipeArgs& a, cudaStream_t st) {
+    const int ni = a.ninst;
+    SFFT_TRY(launch_clear(a.d_inst, ni, 1, a.hybrid, 0, st));
+    // Algorithm 2 line 2: lattice DFTs (normalised by 1/M) + per-lattice statistics
+    SFFT_TRY(launch_bluestein(a.jobs_fwd, a.nlat, a.maxN, a.sm_prec, a.prec, a.prec, a.prec, -1, EPI_ANALYZE, a.d_inst, st));
+    // zero test with FP64 re-tests inside the guard band (Remark 2.3)
+    const double u = a.prec ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+    SFFT_TRY(launch_zero_test(a.d_lats, a.nlat, a.d_inst, a.prec, 32.0 * u, st));
+    // count rule over all candidates, ascending compaction of Itilde
+    SFFT_TRY(launch_hash_count(a.d_inst, ni, a.d, a.hash_gx, a.hash_smem, st));
+    SFFT_TRY(launch_compact(a.d_inst, ni, st));
+    // hashes of Itilde, collision counts, median / hybrid combine
+    SFFT_TRY(launch_det_hashes(a.d_inst, ni, a.maxcap, st));
+    if (a.hybrid) SFFT_TRY(launch_collisions(a.d_inst, ni, st));
+    SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, 0, st));
+    if (a.refine) {
+        SFFT_TRY(launch_clear(a.d_inst, ni, 0, 0, 1, st));
+        SFFT_TRY(launch_scatter_coef(a.d_inst, ni, st));
+        // residual at the nodes in FP64: r = f - IDFT(C)
+        SFFT_TRY(launch_bluestein(a.jobs_model, a.nlat, a.maxN, a.sm64, 0, 0, a.prec, +1, EPI_RESID, a.d_inst, st));
+        SFFT_TRY(launch_bluestein(a.jobs_rfwd, a.nlat, a.maxN, a.sm_prec, a.prec, a.prec, a.prec, -1, EPI_PLAIN, a.d_inst, st));
+        SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, 1, st));
+    }
+    // Algorithm 4: theta filter and top-s_tilde, ascending output
+    SFFT_TRY(launch_select(a.d_inst, ni, st));
+    return SFFT_OK;
+}
+
+int Plan::hash_grid() const {
+    int per_sm = std::max<int>(1, std::min<int>(8, (int)((228 * 1024) / (hash_smem + 1024))));
+    int64_t tiles = (n + 511) / 512;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)152 * per_sm));
+}
+
+PipeArgs Plan::pipe_args() {
+    PipeArgs a;
+    a.ninst = 1; a.d_inst = d_inst; a.d_lats = d_lats; a.nlat = L;
+    a.jobs_fwd = d_jobs_fwd; a.jobs_model = d_jobs_model; a.jobs_rfwd = d_jobs_rfwd;
+    a.maxN = maxN; a.sm_prec = fits_smem(prec); a.sm64 = fits_smem(0);
+    a.prec = prec; a.d = d; a.hash_gx = hash_grid(); a.hash_smem = hash_smem; a.maxcap = cap;
+    a.hybrid = p.combine == SFFT_COMBINE_HYBRID; a.refine = p.refine;
+    return a;
+}
+
+}  // namespace sfft
+
+using namespace sfft;
+
+// ================================================================== C ABI
+extern "C" {
+
+void sfft_params_default(sfft_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->c = 10.33;
+    p->delta = 0.1;
+    p->nu = 0.5;
+    p->tau_abs = 0.0;
+    p->tau_rel = 1e-10;
+    p->theta_abs = 0.0;
+    p->theta_rel = 0.0;
+    p->s_tilde = 0;
+    p->precision = SFFT_FP64;
+    p->refine = 0;
+    p->L_rule = SFFT_L_COR26;
+    p->combine = SFFT_COMBINE_MEDIAN;
+    p->seed = 0;
+    p->detect_cap = 0;
+}
+
+const char* sfft_last_error(void) { return get_error(); }
+
+uint64_t sfft_philox4x64_word0(uint64_t key0, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3) {
+    return philox_word0(key0, c0, c1, c2, c3);
+}
+
+int64_t sfft_next_prime_above(double x) { return next_prime_above(x); }
+
+int sfft_L_rule(int rule, int64_t n_cand, double delta, double c) {
+    if (n_cand < 1 || !(delta > 0 && delta < 1) || !(c > 2)) return -1;
+    return L_rule(rule, n_cand, delta, c);
+}
+
+int sfft_plan_create(sfft_plan** out, int d, const int32_t* cand, int64_t n_cand, int64_t s, int L, const int64_t* M,
+                     const int64_t* z, const sfft_params* p, void* stream) {
+    if (!out) { set_error("out is NULL"); return SFFT_EINVAL; }
+    *out = nullptr;
+    Plan* P = new Plan();
+    int rc = plan_create(P, d, cand, n_cand, s, L, M, z, p, (cudaStream_t)stream);
+    if (rc != SFFT_OK) {
+        P->release();
+        delete P;
+        return rc;
+    }
+    *out = reinterpret_cast<sfft_plan*>(P);
+    return SFFT_OK;
+}
+
+void sfft_plan_destroy(sfft_plan* plan) {
+    if (!plan) return;
+    Plan* P = reinterpret_cast<Plan*>(plan);
+    cudaStreamSynchronize(P->st);
+    P->release();
+    delete P;
+}
+
+int sfft_plan_info(const sfft_plan* plan, int* L, int64_t* M, int64_t* z, int64_t* n_samples) {
+    if (!plan) { set_error("plan is NULL"); return SFFT_EINVAL; }
+    const Plan* P = reinterpret_cast<const Plan*>(plan);
+    if (L) *L = P->L;
+    if (M) for (int l = 0; l < P->L; ++l) M[l] = P->M[l];
+    if (z) for (size_t i = 0; i < P->z.size(); ++i) z[i] = P->z[i];
+    if (n_samples) *n_samples = P->sumM;
+    return SFFT_OK;
+}
+
+int sfft_sample_points(const sfft_plan* plan, int32_t* numer_out, double* x_out, int64_t* offsets) {
+    if (!plan) { set_error("plan is NULL"); return SFFT_EINVAL; }
+    const Plan* P = reinterpret_cast<const Plan*>(plan);
+    if (offsets) for (int l = 0; l <= P->L; ++l) offsets[l] = P->soff[l];
+    if (numer_out || x_out) {
+        SFFT_TRY(launch_points(P->d_inst, numer_out, x_out, P->sumM * P->d, P->st));
+        SFFT_CU(cudaStreamSynchronize(P->st));
+    }
+    return SFFT_OK;
+}
+
+int sfft_reconstruct(sfft_plan* plan, const void* samples, int64_t* supp_out, double* coef_out, int64_t cap,
+                     int64_t* n_out, sfft_diag* diag) {
+    if (!plan || !samples || (cap > 0 && (!supp_out || !coef_out))) {
+        set_error("sfft_reconstruct: null argument");
+        return SFFT_EINVAL;
+    }
+    Plan* P = reinterpret_cast<Plan*>(plan);
+    InstDesc& I = *P->h_inst;
+    I.samples = samples;
+    I.supp_out = supp_out;
+    I.coef_out = reinterpret_cast<c64*>(coef_out);
+    I.out_cap = cap;
+    I.dcounts = diag ? diag->counts : nullptr;
+    I.dhashes = diag ? diag->hashes : nullptr;
+    cudaStream_t st = P->st;
+    SFFT_CU(cudaMemcpyAsync(P->d_inst, &I, sizeof(InstDesc), cudaMemcpyHostToDevice, st));
+    SFFT_TRY(run_pipeline(P->pipe_args(), st));
+    SFFT_CU(cudaMemcpyAsync(P->h_cnt, P->cnt, sizeof(int64_t) * 8, cudaMemcpyDeviceToHost, st));
+    if (diag) {
+        const int64_t nd_cap = P->cap;
+        if (diag->detected) SFFT_CU(cudaMemcpyAsync(diag->detected, P->det, sizeof(int64_t) * nd_cap, cudaMemcpyDeviceToDevice, st));
+        if (diag->pcheck) SFFT_CU(cudaMemcpyAsync(diag->pcheck, P->coef, sizeof(c64) * nd_cap, cudaMemcpyDeviceToDevice, st));
+        if (diag->ghat) SFFT_TRY(launch_to_c64(P->ghat, P->prec, reinterpret_cast<c64*>(diag->ghat), P->sumM, st));
+        if (diag->collisions) {
+            if (I.combine != SFFT_COMBINE_HYBRID) {  // the combine did not need them: count over Itilde now
+                SFFT_CU(cudaMemsetAsync(P->coll, 0, sizeof(int32_t) * P->sumM, st));
+                SFFT_TRY(launch_collisions(P->d_inst, 1, st));
+            }
+            SFFT_CU(cudaMemcpyAsync(diag->collisions, P->coll, sizeof(int32_t) * P->sumM, cudaMemcpyDeviceToDevice, st));
+        }
+        if (diag->tau) {
+            std::vector<LatStats> S(P->L);
+            SFFT_CU(cudaMemcpyAsync(S.data(), P->stats, sizeof(LatStats) * P->L, cudaMemcpyDeviceToHost, st));
+            SFFT_CU(cudaStreamSynchronize(st));
+            std::vector<double> tau(P->L);
+            for (int l = 0; l < P->L; ++l) tau[l] = S[l].tau;
+            SFFT_CU(cudaMemcpy(diag->tau, tau.data(), sizeof(double) * P->L, cudaMemcpyHostToDevice));
+        }
+    }
+    SFFT_CU(cudaStreamSynchronize(st));
+    const int64_t* c = P->h_cnt;
+    if (diag) {
+        diag->n_detected = c[0];
+        diag->n_guard = c[2];
+    }
+    if (n_out) *n_out = c[1];
+    P->have_forward = true;
+    P->last_nout = c[1];
+    if (c[3] & ERR_GUARD_CAP) { set_error("more than 1024 buckets of one lattice inside the FP64 guard band"); return SFFT_ECAPACITY; }
+    if (c[3] & ERR_DET_CAP) { set_error("|Itilde| = %lld exceeds detect_cap = %lld", (long long)c[0], (long long)P->cap); return SFFT_ECAPACITY; }
+    if (c[3] & ERR_OUT_CAP) { set_error("%lld selected frequencies exceed cap = %lld", (long long)c[1], (long long)cap); return SFFT_ECAPACITY; }
+    return SFFT_OK;
+}
+
+int sfft_reconstruct_backward(sfft_plan* plan, const double* dcoef, void* dsamples) {
+    if (!plan || !dsamples) { set_error("null argument"); return SFFT_EINVAL; }
+    Plan* P = reinterpret_cast<Plan*>(plan);
+    SFFT_CHECK(P->have_forward, SFFT_ESTATE, "sfft_reconstruct_backward before sfft_reconstruct");
+    SFFT_CHECK(P->p.refine == 0, SFFT_ESTATE, "the adjoint is defined for refine == 0 plans");
+    SFFT_CHECK(P->p.combine == SFFT_COMBINE_MEDIAN, SFFT_ESTATE, "the adjoint is defined for the median combine");
+    cudaStream_t st = P->st;
+    SFFT_CU(cudaMemsetAsync(P->C, 0, sizeof(c64) * P->sumM, st));
+    if (P->last_nout > 0 && dcoef) SFFT_TRY(launch_adj_scatter(P->d_inst, reinterpret_cast<const c64*>(dcoef), st));
+    // dsamples = A^H gbar with (A^H g)_j = (1/M) sum_h g_h exp(+2 pi i j h / M)
+    std::vector<BlueJob> jobs;
+    const size_t e = P->esz();
+    for (int l = 0; l < P->L; ++l) {
+        BlueJob J = make_job(P->tabs[l], P->prec, 1, 1.0 / (double)P->M[l]);
+        J.in = P->C + P->soff[l];
+        J.out = (char*)dsamples + P->soff[l] * e;
+        J.scratch = P->fits_smem(P->prec) ? nullptr : (char*)P->scratch + (size_t)l * P->maxN * sizeof(c64);
+        jobs.push_back(J);
+    }
+    SFFT_CU(cudaMemcpyAsync(P->d_jobs_tmp, jobs.data(), sizeof(BlueJob) * jobs.size(), cudaMemcpyHostToDevice, st));
+    SFFT_TRY(launch_bluestein(P->d_jobs_tmp, P->L, P->maxN, P->fits_smem(P->prec), P->prec, 0, P->prec, +1, EPI_PLAIN,
+                              P->d_inst, st));
+    SFFT_CU(cudaStreamSynchronize(st));
+    return SFFT_OK;
+}
+
+int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const double* coef, int64_t n_terms,
+                            const double* noise, void* samples_out) {
+    if (!plan || !samples_out || (n_terms > 0 && (!kvec || !coef))) { set_error("null argument"); return SFFT_EINVAL; }
+    Plan* P = const_cast<Plan*>(reinterpret_cast<const Plan*>(plan));
+    cudaStream_t st = P->st;
+    SFFT_CU(cudaMemsetAsync(P->C, 0, sizeof(c64) * P->sumM, st));
+    if (n_terms > 0) SFFT_TRY(launch_scatter_terms(P->d_inst, kvec, reinterpret_cast<const c64*>(coef), n_terms, st));
+    std::vector<BlueJob> jobs;
+    const size_t e = P->esz();
+    for (int l = 0; l < P->L; ++l) {
+        BlueJob J = make_job(P->tabs[l], P->prec, 1, 1.0);
+        J.in = P->C + P->soff[l];
+        J.out = (char*)samples_out + P->soff[l] * e;
+        J.aux = noise ? (const void*)(reinterpret_cast<const c64*>(noise) + P->soff[l]) : nullptr;
+        J.scratch = P->fits_smem(P->prec) ? nullptr : (char*)P->scratch + (size_t)l * P->maxN * sizeof(c64);
+        jobs.push_back(J);
+    }
+    SFFT_CU(cudaMemcpyAsync(P->d_jobs_tmp, jobs.data(), sizeof(BlueJob) * jobs.size(), cudaMemcpyHostToDevice, st));
+    SFFT_TRY(launch_bluestein(P->d_jobs_tmp, P->L, P->maxN, P->fits_smem(P->prec), P->prec, 0, P->prec, +1, EPI_ADDNOISE,
+                              P->d_inst, st));
+    SFFT_CU(cudaStreamSynchronize(st));
+    return SFFT_OK;
+}
+
+static int sop_prepare(Plan* P, const int32_t* triples, const double* theta, int n_terms, int K, double width) {
+    SFFT_CHECK(triples && theta && n_terms >= 1 && n_terms <= 16 && K >= 0 && K <= 128 && width > 0, SFFT_EINVAL,
+               "sum-of-products: need 1 <= n_terms <= 16, 0 <= K <= 128, width > 0");
+    for (int i = 0; i < 3 * n_terms; ++i)
+        SFFT_CHECK(triples[i] >= 0 && triples[i] < P->d, SFFT_EINVAL, "triple entry %d outside [0, d)", triples[i]);
+    SFFT_CU(cudaMemcpyAsync(P->sop_tri, triples, sizeof(int32_t) * 3 * n_terms, cudaMemcpyHostToDevice, P->st));
+    return launch_sop_coefs(theta, n_terms, K, width, P->sop_a, P->sop_a + 16 * 129, P->st);
+}
+
+int sfft_sample_sop(const sfft_plan* plan, const int32_t* triples, const double* theta, int n_terms, int K, double width,
+                    void* samples_out) {
+    if (!plan || !samples_out) { set_error("null argument"); return SFFT_EINVAL; }
+    Plan* P = const_cast<Plan*>(reinterpret_cast<const Plan*>(plan));
+    SFFT_TRY(sop_prepare(P, triples, theta, n_terms, K, width));
+    SFFT_TRY(launch_sop_sample(P->d_inst, P->sop_tri, n_terms, K, P->sop_a, samples_out, P->prec, P->st));
+    SFFT_CU(cudaStreamSynchronize(P->st));
+    return SFFT_OK;
+}
+
+int sfft_sample_sop_backward(const sfft_plan* plan, const int32_t* triples, const double* theta, int n_terms, int K,
+                             double width, const void* dsamples, double* dtheta) {
+    if (!plan || !dsamples || !dtheta) { set_error("null argument"); return SFFT_EINVAL; }
+    Plan* P = const_cast<Plan*>(reinterpret_cast<const Plan*>(plan));
+    SFFT_TRY(sop_prepare(P, triples, theta, n_terms, K, width));
+    SFFT_CU(cudaMemsetAsync(dtheta, 0, sizeof(double) * n_terms, P->st));
+    SFFT_TRY(launch_sop_backward(P->d_inst, P->sop_tri, n_terms, K, P->sop_a, P->sop_a + 16 * 129, dsamples, P->prec,
+                                 dtheta, P->st));
+    SFFT_CU(cudaStreamSynchronize(P->st));
+    return SFFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,210 @@
+// Shared definitions of the sm_103a sparse-FFT library: complex arithmetic, error
+// plumbing and the descriptors that the kernels of every stage consume.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/sfft.h"
+
+namespace sfft {
+
+// ------------------------------------------------------------------ complex numbers
+template <class T>
+struct alignas(2 * sizeof(T)) cplx {
+    T x, y;
+};
+using c32 = cplx<float>;
+using c64 = cplx<double>;
+
+template <class T> __host__ __device__ __forceinline__ cplx<T> mk(T a, T b) { return cplx<T>{a, b}; }
+template <class T> __host__ __device__ __forceinline__ cplx<T> operator+(cplx<T> a, cplx<T> b) { return {a.x + b.x, a.y + b.y}; }
+template <class T> __host__ __device__ __forceinline__ cplx<T> operator-(cplx<T> a, cplx<T> b) { return {a.x - b.x, a.y - b.y}; }
+template <class T> __host__ __device__ __forceinline__ cplx<T> operator*(cplx<T> a, cplx<T> b) {
+    return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <class T> __host__ __device__ __forceinline__ cplx<T> operator*(cplx<T> a, T s) { return {a.x * s, a.y * s}; }
+template <class T> __host__ __device__ __forceinline__ cplx<T> conj(cplx<T> a) { return {a.x, -a.y}; }
+// a * conj(b)
+template <class T> __host__ __device__ __forceinline__ cplx<T> mulc(cplx<T> a, cplx<T> b) {
+    return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <class T> __host__ __device__ __forceinline__ T abs2(cplx<T> a) { return a.x * a.x + a.y * a.y; }
+
+template <class T, class U> __host__ __device__ __forceinline__ cplx<T> cvt(cplx<U> a) { return {(T)a.x, (T)a.y}; }
+
+#ifdef __CUDACC__
+// read-only cached loads of complex values
+__device__ __forceinline__ c32 ldg(const c32* p) {
+    float2 v = __ldg(reinterpret_cast<const float2*>(p));
+    return {v.x, v.y};
+}
+__device__ __forceinline__ c64 ldg(const c64* p) {
+    double2 v = __ldg(reinterpret_cast<const double2*>(p));
+    return {v.x, v.y};
+}
+#endif
+
+// ------------------------------------------------------------------ errors
+void set_error(const char* fmt, ...);
+const char* get_error();
+
+#define SFFT_CU(call)                                                                          \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            ::sfft::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return SFFT_ECUDA;                                                                 \
+        }                                                                                      \
+    } while (0)
+
+#define SFFT_TRY(expr)            \
+    do {                          \
+        int rc_ = (expr);         \
+        if (rc_ != SFFT_OK) return rc_; \
+    } while (0)
+
+#define SFFT_CHECK(cond, code, ...)           \
+    do {                                      \
+        if (!(cond)) {                        \
+            ::sfft::set_error(__VA_ARGS__);   \
+            return (code);                    \
+        }                                     \
+    } while (0)
+
+inline int launch_check(const char* what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("launch of %s failed: %s", what, cudaGetErrorString(e));
+        return SFFT_ECUDA;
+    }
+    return SFFT_OK;
+}
+
+// ------------------------------------------------------------------ constants
+constexpr int kMaxD = 32;      // candidate dimension limit
+constexpr int kMaxL = 64;      // lattices per reconstruction
+constexpr int kMaxStages = 24; // mixed-radix stages of one Bluestein length
+
+// ------------------------------------------------------------------ FFT tables
+// Everything needed to run a length-M DFT by Bluestein's algorithm through a length-N
+// cyclic convolution, N = 2^a 3^b 5^c >= 2M-1, computed once per distinct M.
+struct FftTables {
+    int64_t M = 0, N = 0;
+    int nstages = 0;
+    int radix[kMaxStages];
+    // device tables; the *32 copies are the double tables rounded to float
+    c64* tw64 = nullptr;   // [N] exp(-2 pi i n / N)
+    c32* tw32 = nullptr;
+    c64* chirp64 = nullptr; // [M] exp(-pi i (j^2 mod 2M) / M)
+    c32* chirp32 = nullptr;
+    c64* filt64[2] = {nullptr, nullptr}; // [N] DIF(b)/N, digit-reversed; [0] forward, [1] inverse
+    c32* filt32[2] = {nullptr, nullptr};
+    c64* dft64 = nullptr;  // [M] exp(-2 pi i m / M) for single-bucket FP64 DFTs
+    int refs = 0;
+    int device = -1;
+};
+
+int tables_acquire(int64_t M, FftTables** out);
+void tables_release(FftTables* t);
+int64_t bluestein_size(int64_t M);
+
+// ------------------------------------------------------------------ per-lattice job
+// One Bluestein transform (a length-M DFT of one lattice).
+struct BlueJob {
+    const void* in;      // input complex (element type by launch), M entries
+    void* out;           // output complex, M entries
+    const void* aux;     // epilogue input (noise / samples for the residual), M entries
+    void* scratch;       // global work buffer of N complex (used when the buffer is not in smem)
+    const void* tw;      // twiddles of the transform precision
+    const void* chirp;
+    const void* filt;    // filter of the requested direction
+    const double* dft64; // FP64 single-bucket table (guard re-tests)
+    struct LatStats* stat; // side outputs of EPI_ANALYZE
+    double scale;        // output scale (1/M for the normalised forward DFT)
+    int M, N, nstages;
+    int inst, io_flags;  // io_flags bit 0: in = samples of instance `inst` + io_off; bit 1: aux likewise
+    int64_t io_off;
+    uint8_t radix[kMaxStages];
+};
+
+// epilogue modes of the Bluestein kernel
+enum BlueEpi : int {
+    EPI_PLAIN = 0,    // out = scale * y
+    EPI_ANALYZE = 1,  // out = y / M; per-lattice max|y| and sum |x|^2 recorded
+    EPI_ADDNOISE = 2, // out = y + aux (aux complex double)
+    EPI_RESID = 3,    // out = aux - y (aux in the output precision)
+};
+
+struct LatStats {
+    double max_abs;   // max_h |ghat_h| (FP64 after the guard re-test of the maximum)
+    double rms;       // sqrt(sum_j |x_j|^2 / M)
+    double tau;       // zero-test threshold
+    double band;      // guard half-width around tau
+    float max32;      // max_h |ghat_h| of the working-precision transform
+    int pad;
+};
+
+// One launch of Bluestein transforms over a device job array.  prec/in_prec/out_prec: 0 =
+// double, 1 = float.  sm: work buffer in shared memory (all jobs need N <= maxN fitting).
+struct InstDesc;
+int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, bool sm, int prec, int in_prec, int out_prec, int sign,
+                     int epi, const InstDesc* insts, cudaStream_t st);
+size_t blue_smem_limit();
+
+// ------------------------------------------------------------------ instance / lattice descriptors
+// Everything the per-candidate kernels need about one reconstruction problem.  Lives in
+// device memory; the per-call IO pointers are refreshed before each run.
+struct InstDesc {
+    int d, L, need, prec;      // need = ceil(nu L) (Algorithm 1 count threshold)
+    int combine, nwords, lat0, pad0;
+    int64_t n;                 // |Gamma|
+    int64_t cap;               // capacity of the detected list
+    int64_t s_tilde;
+    double tau_abs, tau_rel, theta_abs, theta_rel;
+    const int32_t* cand;       // [n, d]
+    const int32_t* z;          // [L, d]
+    const int32_t* Ml;         // [L]
+    const uint32_t* mu;        // [L] floor(2^32 / M_l)
+    const uint32_t* offk;      // [L] multiple of M_l added before the Barrett reduction
+    const int64_t* soff;       // [L+1] sample offsets
+    const int32_t* boff;       // [L] bitmap word offsets
+    uint32_t* nzbits;          // [nwords]
+    void* ghat;                // [sum M] complex (prec)
+    LatStats* stats;           // [L]
+    uint32_t* detbits;         // [ceil(n/32)]
+    int64_t* det;              // [cap] detected indices (ascending)
+    int64_t* cnt;              // [8] counters: 0 |Itilde|, 1 n_out, 2 n_guard, 3 error flags
+    c64* coef;                 // [cap]
+    int32_t* H;                // [cap, L]
+    uint8_t* sel;              // [cap, 2] lattice of the Re / Im median
+    int32_t* coll;             // [sum M] collision counts
+    c64* C;                    // [sum M] bucket scatter buffer
+    void* rhat;                // [sum M] complex (prec)
+    void* resid;               // [sum M] complex (prec)
+    int32_t* outpos;           // [cap] detected position of output q
+    // ---- per call
+    const void* samples;       // [sum M] complex (prec)
+    int64_t* supp_out;
+    c64* coef_out;
+    int64_t out_cap;
+    uint8_t* dcounts;          // diag
+    int32_t* dhashes;          // diag
+};
+
+// One lattice of one instance (for per-lattice kernels).
+struct LatDesc {
+    int inst, l, M, N;
+    int64_t soff;
+    int32_t boff;
+    int pad;
+    const double* dft64;       // [M] exp(-2 pi i m / M)
+};
+
+// error flag bits (InstDesc::cnt[3])
+enum : int64_t { ERR_DET_CAP = 1, ERR_GUARD_CAP = 2, ERR_OUT_CAP = 4 };
+
+}  // namespace sfft

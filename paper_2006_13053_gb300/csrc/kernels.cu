@@ -1,0 +1,726 @@
+// Per-lattice and per-candidate kernels of the reconstruction (Algorithms 1, 2 and 4):
+//   zero test of the lattice DFT buckets with FP64 re-tests near the threshold (Remark 2.3),
+//   candidate hashing k.z_l mod M_l and the majority count (Algorithm 1/2, count rule),
+//   ascending compaction of the detected set, the per-candidate gather and component-wise
+//   median (eq. 2.6), bucket collision counts and the Remark 2.8 combine, the refinement
+//   scatter/update, and Algorithm 4's theta filter plus radix top-s_tilde selection.
+#include <limits.h>
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace sfft {
+
+// ================================================================== zero test (per lattice)
+// One CTA per lattice.  The working-precision |ghat| decides every bucket except those within
+// `band` of tau (and the maximum, which sets tau when tau_rel > 0): those are recomputed by a
+// direct FP64 DFT sum of the samples with exact integer phase (j h mod M).
+template <class TS>
+__device__ c64 bucket_dft64(const cplx<TS>* __restrict__ x, int M, int h, const c64* __restrict__ tab, double* red) {
+    double re = 0, im = 0;
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+        int64_t ph = ((int64_t)j * h) % M;
+        c64 w = tab[ph];
+        c64 v = cvt<double>(x[j]);
+        re += v.x * w.x - v.y * w.y;
+        im += v.x * w.y + v.y * w.x;
+    }
+    // block sums of re, im
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) { red[2 * w] = re; red[2 * w + 1] = im; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double a = 0, b = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) { a += red[2 * i]; b += red[2 * i + 1]; }
+        red[64] = a / M;
+        red[65] = b / M;
+    }
+    __syncthreads();
+    c64 r = {red[64], red[65]};
+    __syncthreads();
+    return r;
+}
+
+constexpr int kZtThreads = 512;
+constexpr int kGuardCap = 1024;
+
+template <class TS>
+__global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restrict__ lats, InstDesc* __restrict__ insts,
+                                                          double kappa_u_log) {
+    __shared__ double red[72];
+    __shared__ int glist[kGuardCap];
+    __shared__ int gcount;
+    __shared__ double s_max64;
+    const LatDesc& D = lats[blockIdx.x];
+    InstDesc& I = insts[D.inst];
+    LatStats& S = I.stats[D.l];
+    const int M = D.M;
+    cplx<TS>* g = reinterpret_cast<cplx<TS>*>(I.ghat) + D.soff;
+    const cplx<TS>* x = reinterpret_cast<const cplx<TS>*>(I.samples) + D.soff;
+    const c64* tab = reinterpret_cast<const c64*>(D.dft64);
+    const double band = kappa_u_log * log2((double)D.N) * S.rms;
+    if (threadIdx.x == 0) { gcount = 0; s_max64 = 0; }
+    __syncthreads();
+    // ---- exact maximum: FP64 re-test of every bucket that could be the maximum
+    double tau = I.tau_abs;
+    if (I.tau_rel > 0) {
+        // every bucket that could hold the FP64 maximum (slack for the working precision)
+        const double lo = S.max_abs * (1.0 - 1.0 / 1048576.0) - 2.0 * band;
+        for (int h = threadIdx.x; h < M; h += blockDim.x) {
+            double a = sqrt((double)abs2(cvt<double>(g[h])));
+            if (a >= lo) {
+                int p = atomicAdd(&gcount, 1);
+                if (p < kGuardCap) glist[p] = h;
+            }
+        }
+        __syncthreads();
+        int nc = min(gcount, kGuardCap);
+        if (gcount > kGuardCap && threadIdx.x == 0) atomicOr((unsigned long long*)&I.cnt[3], (unsigned long long)ERR_GUARD_CAP);
+        for (int i = 0; i < nc; ++i) {
+            c64 v = bucket_dft64(x, M, glist[i], tab, red);
+            if (threadIdx.x == 0) {
+                s_max64 = fmax(s_max64, sqrt(abs2(v)));
+                g[glist[i]] = cvt<TS>(v);
+            }
+        }
+        __syncthreads();
+        tau = fmax(tau, I.tau_rel * s_max64);
+        if (threadIdx.x == 0) { S.max_abs = s_max64; gcount = 0; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { S.tau = tau; S.band = band; }
+    // ---- threshold: one warp writes 32 consecutive buckets per ballot
+    uint32_t* words = I.nzbits + D.boff;
+    const int nw = (M + 31) >> 5;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+    for (int wi = warp; wi < nw; wi += nwarp) {
+        int h = wi * 32 + lane;
+        bool nz = false;
+        if (h < M) {
+            double a = sqrt((double)abs2(cvt<double>(g[h])));
+            nz = a > tau;
+            if (fabs(a - tau) <= band) {
+                int p = atomicAdd(&gcount, 1);
+                if (p < kGuardCap) glist[p] = h;
+            }
+        }
+        uint32_t b = __ballot_sync(0xffffffffu, nz);
+        if (lane == 0) words[wi] = b;
+    }
+    __syncthreads();
+    int nc = min(gcount, kGuardCap);
+    if (gcount > kGuardCap && threadIdx.x == 0) atomicOr((unsigned long long*)&I.cnt[3], (unsigned long long)ERR_GUARD_CAP);
+    for (int i = 0; i < nc; ++i) {
+        int h = glist[i];
+        c64 v = bucket_dft64(x, M, h, tab, red);
+        if (threadIdx.x == 0) {
+            double a = sqrt(abs2(v));
+            uint32_t bit = 1u << (h & 31);
+            if (a > tau) atomicOr(&words[h >> 5], bit);
+            else atomicAnd(&words[h >> 5], ~bit);
+            g[h] = cvt<TS>(v);  // the stored bucket is the FP64 value that decided the test
+        }
+    }
+    if (threadIdx.x == 0 && nc) atomicAdd((unsigned long long*)&I.cnt[2], (unsigned long long)nc);
+}
+
+// ================================================================== hash + count (Algorithm 1/2)
+// Candidates are streamed once from HBM; the non-zero bitmap of all lattices of the instance
+// and the generating vectors sit in shared memory.  h = k.z_l mod M_l is exact: the int32
+// inner product is offset by a multiple of M_l to be non-negative and reduced by a Barrett
+// step (q = umulhi(x, floor(2^32/M)), one conditional subtraction).
+constexpr int kHashThreads = 256;
+constexpr int kCPT = 2;  // candidates per thread
+
+template <int D>
+__global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __restrict__ insts) {
+    extern __shared__ __align__(16) uint32_t hsm[];
+    const InstDesc& I = insts[blockIdx.y];
+    const int L = I.L, nwords = I.nwords;
+    uint32_t* bits = hsm;
+    int* sz = reinterpret_cast<int*>(hsm + nwords);     // [L][D]
+    uint32_t* sM = reinterpret_cast<uint32_t*>(sz + L * D);
+    uint32_t* smu = sM + L;
+    uint32_t* soffk = smu + L;
+    uint32_t* sbo = soffk + L;
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = I.nzbits[i];
+    for (int i = threadIdx.x; i < L * D; i += blockDim.x) sz[i] = I.z[i];
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+        sM[i] = (uint32_t)I.Ml[i];
+        smu[i] = I.mu[i];
+        soffk[i] = I.offk[i];
+        sbo[i] = (uint32_t)I.boff[i] * 32u;
+    }
+    __syncthreads();
+    const int64_t n = I.n;
+    const int need = I.need;
+    const int32_t* __restrict__ cand = I.cand;
+    uint8_t* dcounts = I.dcounts;
+    int32_t* dhashes = I.dhashes;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * kCPT;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kCPT; base < n; base += step) {
+        int k[kCPT][D];
+        int64_t idx[kCPT];
+#pragma unroll
+        for (int c = 0; c < kCPT; ++c) {
+            idx[c] = base + threadIdx.x + (int64_t)c * blockDim.x;
+            const int32_t* row = cand + (idx[c] < n ? idx[c] : 0) * D;
+            if constexpr (D % 4 == 0) {
+#pragma unroll
+                for (int t = 0; t < D; t += 4) {
+                    int4 v = __ldg(reinterpret_cast<const int4*>(row + t));
+                    k[c][t] = v.x; k[c][t + 1] = v.y; k[c][t + 2] = v.z; k[c][t + 3] = v.w;
+                }
+            } else if constexpr (D % 2 == 0) {
+#pragma unroll
+                for (int t = 0; t < D; t += 2) {
+                    int2 v = __ldg(reinterpret_cast<const int2*>(row + t));
+                    k[c][t] = v.x; k[c][t + 1] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < D; ++t) k[c][t] = __ldg(row + t);
+            }
+        }
+        int cnt[kCPT];
+#pragma unroll
+        for (int c = 0; c < kCPT; ++c) cnt[c] = 0;
+        for (int l = 0; l < L; ++l) {
+            int zl[D];
+#pragma unroll
+            for (int t = 0; t < D; ++t) zl[t] = sz[l * D + t];
+            const uint32_t M = sM[l], mu = smu[l], off = soffk[l], bo = sbo[l];
+#pragma unroll
+            for (int c = 0; c < kCPT; ++c) {
+                int x = 0;
+#pragma unroll
+                for (int t = 0; t < D; ++t) x += k[c][t] * zl[t];
+                uint32_t xp = (uint32_t)x + off;
+                uint32_t q = __umulhi(xp, mu);
+                uint32_t r = xp - q * M;
+                r = r >= M ? r - M : r;
+                uint32_t bit = bo + r;
+                cnt[c] += (bits[bit >> 5] >> (bit & 31)) & 1u;
+                if (dhashes && idx[c] < n) dhashes[idx[c] * L + l] = (int32_t)r;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kCPT; ++c) {
+            if (idx[c] < n) {
+                if (cnt[c] >= need) atomicOr(&I.detbits[idx[c] >> 5], 1u << (idx[c] & 31));
+                if (dcounts) dcounts[idx[c]] = (uint8_t)cnt[c];
+            }
+        }
+    }
+}
+
+// ================================================================== compaction (ascending Itilde)
+constexpr int kCompactThreads = 1024;
+__global__ void __launch_bounds__(kCompactThreads) k_compact(InstDesc* __restrict__ insts) {
+    __shared__ int64_t wsum[32];
+    InstDesc& I = insts[blockIdx.x];
+    const int64_t W = (I.n + 31) >> 5;
+    const int64_t per = (W + blockDim.x - 1) / blockDim.x;
+    const int64_t w0 = threadIdx.x * per, w1 = min(W, w0 + per);
+    int64_t c = 0;
+    for (int64_t w = w0; w < w1; ++w) c += __popc(I.detbits[w]);
+    // block exclusive scan of c
+    int64_t v = c;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 1; o < 32; o <<= 1) {
+        int64_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int64_t t = lane < (int)(blockDim.x >> 5) ? wsum[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int64_t u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        wsum[lane] = t;
+    }
+    __syncthreads();
+    int64_t pos = v - c + (warp > 0 ? wsum[warp - 1] : 0);
+    const int64_t total = wsum[(blockDim.x >> 5) - 1];
+    for (int64_t w = w0; w < w1; ++w) {
+        uint32_t b = I.detbits[w];
+        while (b) {
+            int t = __ffs(b) - 1;
+            b &= b - 1;
+            if (pos < I.cap) I.det[pos] = w * 32 + t;
+            ++pos;
+        }
+    }
+    if (threadIdx.x == 0) {
+        I.cnt[0] = total;
+        if (total > I.cap) atomicOr((unsigned long long*)&I.cnt[3], (unsigned long long)ERR_DET_CAP);
+    }
+}
+
+// ================================================================== hashes of the detected set
+// One warp per detected candidate; lane l (and l+32) owns lattice l.
+__global__ void k_det_hashes(const InstDesc* __restrict__ insts) {
+    const InstDesc& I = insts[blockIdx.y];
+    const int64_t nd = min(I.cnt[0], I.cap);
+    const int warps = blockDim.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
+    if (q >= nd) return;
+    const int lane = threadIdx.x & 31, L = I.L, d = I.d;
+    const int32_t* k = I.cand + I.det[q] * d;
+    for (int l = lane; l < L; l += 32) {
+        const int32_t* zl = I.z + l * d;
+        int64_t x = 0;
+        for (int t = 0; t < d; ++t) x += (int64_t)__ldg(k + t) * zl[t];
+        int64_t M = I.Ml[l];
+        int64_t r = x % M;
+        if (r < 0) r += M;
+        I.H[q * L + l] = (int32_t)r;
+    }
+}
+
+__global__ void k_collisions(const InstDesc* __restrict__ insts) {
+    const InstDesc& I = insts[blockIdx.y];
+    const int64_t nd = min(I.cnt[0], I.cap);
+    const int L = I.L;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nd * L; e += (int64_t)gridDim.x * blockDim.x) {
+        int l = (int)(e % L);
+        atomicAdd(&I.coll[I.soff[l] + I.H[e]], 1);
+    }
+}
+
+// rank-based selection of the median of the L lane-distributed values (L odd); returns the
+// median value and the lattice it came from (ties: lower lattice index ranks lower)
+template <class T>
+__device__ __forceinline__ void warp_median(T va, T vb, int L, int lane, T& med, int& lsel) {
+    const int mid = (L - 1) >> 1;
+    int ra = 0, rb = 0;  // ranks of lattice lane and lane+32
+    for (int src = 0; src < 32; ++src) {
+        T a = __shfl_sync(0xffffffffu, va, src);
+        T b = __shfl_sync(0xffffffffu, vb, src);
+        int la = src, lb = src + 32;
+        if (la < L) {
+            ra += (a < va) || (a == va && la < lane);
+            rb += (a < vb) || (a == vb && la < lane + 32);
+        }
+        if (lb < L) {
+            ra += (b < va) || (b == va && lb < lane);
+            rb += (b < vb) || (b == vb && lb < lane + 32);
+        }
+    }
+    bool ha = lane < L && ra == mid, hb = lane + 32 < L && rb == mid;
+    uint32_t ba = __ballot_sync(0xffffffffu, ha), bb = __ballot_sync(0xffffffffu, hb);
+    int owner = ba ? __ffs(ba) - 1 : __ffs(bb) - 1;
+    bool first = ba != 0;
+    T v = first ? va : vb;
+    med = __shfl_sync(0xffffffffu, v, owner);
+    lsel = first ? owner : owner + 32;
+}
+
+// Median combine (eq. 2.6) or the Remark 2.8 hybrid combine on the detected set.
+// mode 0: coef = combine(ghat)     mode 1: coef += median(rhat)  (refinement update)
+template <class TS>
+__global__ void k_combine(const InstDesc* __restrict__ insts, int mode) {
+    const InstDesc& I = insts[blockIdx.y];
+    const int64_t nd = min(I.cnt[0], I.cap);
+    const int warps = blockDim.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
+    if (q >= nd) return;
+    const int lane = threadIdx.x & 31, L = I.L;
+    const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(mode == 0 ? I.ghat : I.rhat);
+    cplx<TS> va = {0, 0}, vb = {0, 0};
+    int fa = 0, fb = 0;  // collision-free flags (hybrid)
+    if (lane < L) {
+        int h = I.H[q * L + lane];
+        va = g[I.soff[lane] + h];
+        if (I.combine == SFFT_COMBINE_HYBRID && mode == 0) fa = I.coll[I.soff[lane] + h] == 1;
+    }
+    if (lane + 32 < L) {
+        int h = I.H[q * L + lane + 32];
+        vb = g[I.soff[lane + 32] + h];
+        if (I.combine == SFFT_COMBINE_HYBRID && mode == 0) fb = I.coll[I.soff[lane + 32] + h] == 1;
+    }
+    TS mre, mim;
+    int lre, lim;
+    warp_median<TS>(va.x, vb.x, L, lane, mre, lre);
+    warp_median<TS>(va.y, vb.y, L, lane, mim, lim);
+    c64 out = {(double)mre, (double)mim};
+    if (I.combine == SFFT_COMBINE_HYBRID && mode == 0) {
+        double sr = (fa ? (double)va.x : 0.0) + (fb ? (double)vb.x : 0.0);
+        double si = (fa ? (double)va.y : 0.0) + (fb ? (double)vb.y : 0.0);
+        int nf = fa + fb;
+        for (int o = 16; o > 0; o >>= 1) {
+            sr += __shfl_xor_sync(0xffffffffu, sr, o);
+            si += __shfl_xor_sync(0xffffffffu, si, o);
+            nf += __shfl_xor_sync(0xffffffffu, nf, o);
+        }
+        if (nf > 0) out = c64{sr / nf, si / nf};
+    }
+    if (lane == 0) {
+        if (mode == 0) {
+            I.coef[q] = out;
+            I.sel[2 * q] = (uint8_t)lre;
+            I.sel[2 * q + 1] = (uint8_t)lim;
+        } else {
+            c64 c = I.coef[q];
+            I.coef[q] = c64{c.x + out.x, c.y + out.y};
+        }
+    }
+}
+
+// scatter the detected coefficients into their buckets: C_l[h_kl] += c_k
+__global__ void k_scatter_coef(const InstDesc* __restrict__ insts) {
+    const InstDesc& I = insts[blockIdx.y];
+    const int64_t nd = min(I.cnt[0], I.cap);
+    const int L = I.L;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nd * L; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = e / L;
+        int l = (int)(e - q * L);
+        c64 c = I.coef[q];
+        c64* dst = I.C + I.soff[l] + I.H[e];
+        atomicAdd(&dst->x, c.x);
+        atomicAdd(&dst->y, c.y);
+    }
+}
+
+// ================================================================== Algorithm 4 selection
+constexpr int kSelThreads = 1024;
+
+__device__ __forceinline__ uint64_t mod_key(c64 c) { return (uint64_t)__double_as_longlong(hypot(c.x, c.y)); }
+
+__device__ int64_t block_sum64(int64_t v, int64_t* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int64_t r = 0;
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+        sh[32] = r;
+    }
+    __syncthreads();
+    r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// exclusive block scan of int flags processed in chunks of blockDim (returns prefix, sets total)
+__device__ int block_excl_scan(int f, int* sh, int* total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int v = f;
+    for (int o = 1; o < 32; o <<= 1) {
+        int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    __syncthreads();
+    if (lane == 31) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int t = lane < (int)(blockDim.x >> 5) ? sh[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        sh[lane] = t;
+    }
+    __syncthreads();
+    int pre = v - f + (warp > 0 ? sh[warp - 1] : 0);
+    *total = sh[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return pre;
+}
+
+__global__ void __launch_bounds__(kSelThreads) k_select(InstDesc* __restrict__ insts) {
+    __shared__ int64_t sh64[33];
+    __shared__ int shi[33];
+    __shared__ unsigned int hist[256];
+    __shared__ double smax[32];
+    InstDesc& I = insts[blockIdx.x];
+    const int64_t nd = min(I.cnt[0], I.cap);
+    // theta = max(theta_abs, theta_rel * max |c|)
+    double mx = 0;
+    for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) mx = fmax(mx, hypot(I.coef[q].x, I.coef[q].y));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, smax[i]);
+        smax[0] = m;
+    }
+    __syncthreads();
+    const double theta = fmax(I.theta_abs, I.theta_rel * smax[0]);
+    __syncthreads();
+    // kept set and its size
+    int64_t kept = 0;
+    for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) kept += hypot(I.coef[q].x, I.coef[q].y) >= theta;
+    kept = block_sum64(kept, sh64);
+    int64_t want = (I.s_tilde > 0 && I.s_tilde < kept) ? I.s_tilde : kept;
+    // radix select of the want-th largest key among kept items (only if truncating)
+    uint64_t prefix = 0, mask = 0;
+    int64_t need = want;
+    const bool trunc = want < kept;
+    if (trunc) {
+        for (int p = 7; p >= 0; --p) {
+            for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
+            __syncthreads();
+            for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) {
+                c64 c = I.coef[q];
+                double a = hypot(c.x, c.y);
+                uint64_t key = (uint64_t)__double_as_longlong(a);
+                if (a >= theta && (key & mask) == prefix) atomicAdd(&hist[(key >> (8 * p)) & 255u], 1u);
+            }
+            __syncthreads();
+            if (threadIdx.x == 0) {
+                int64_t acc = 0;
+                int b = 255;
+                for (; b > 0; --b) {
+                    if (acc + hist[b] >= need) break;
+                    acc += hist[b];
+                }
+                sh64[0] = acc;
+                shi[0] = b;
+            }
+            __syncthreads();
+            need -= sh64[0];
+            prefix |= (uint64_t)shi[0] << (8 * p);
+            mask |= (uint64_t)255 << (8 * p);
+            __syncthreads();
+        }
+    }
+    // prefix = key of the want-th largest; 'need' = how many items equal to it are taken
+    // (lowest indices first, i.e. first in detected order)
+    int64_t eq_taken = 0, outn = 0;
+    for (int64_t q0 = 0; q0 < nd; q0 += blockDim.x) {
+        int64_t q = q0 + threadIdx.x;
+        int sel = 0, eq = 0;
+        c64 c = {0, 0};
+        if (q < nd) {
+            c = I.coef[q];
+            double a = hypot(c.x, c.y);
+            uint64_t key = (uint64_t)__double_as_longlong(a);
+            if (a >= theta) {
+                if (!trunc || key > prefix) sel = 1;
+                else if (key == prefix) eq = 1;
+            }
+        }
+        int tot_eq;
+        int pre_eq = block_excl_scan(eq, shi, &tot_eq);
+        if (eq && eq_taken + pre_eq < need) sel = 1;
+        eq_taken += tot_eq;
+        int tot_sel;
+        int pre_sel = block_excl_scan(sel, shi, &tot_sel);
+        if (sel) {
+            int64_t pos = outn + pre_sel;
+            if (pos < I.out_cap) {
+                I.supp_out[pos] = I.det[q];
+                I.coef_out[pos] = c;
+            }
+            if (pos < I.cap) I.outpos[pos] = (int32_t)q;
+        }
+        outn += tot_sel;
+    }
+    if (threadIdx.x == 0) {
+        I.cnt[1] = outn;
+        if (outn > I.out_cap) atomicOr((unsigned long long*)&I.cnt[3], (unsigned long long)ERR_OUT_CAP);
+    }
+}
+
+// ================================================================== samplers and adjoint scatter
+// scatter coefficients of a sparse polynomial into the lattice buckets (eq. 2.3)
+__global__ void k_scatter_terms(const InstDesc* __restrict__ insts, const int32_t* __restrict__ kvec,
+                                const c64* __restrict__ coef, int64_t nterms) {
+    const InstDesc& I = insts[blockIdx.y];
+    const int L = I.L, d = I.d;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nterms * L; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = e / L;
+        int l = (int)(e - q * L);
+        int64_t x = 0;
+        for (int t = 0; t < d; ++t) x += (int64_t)kvec[q * d + t] * I.z[l * d + t];
+        int64_t M = I.Ml[l];
+        int64_t r = x % M;
+        if (r < 0) r += M;
+        c64* dst = I.C + I.soff[l] + r;
+        atomicAdd(&dst->x, coef[q].x);
+        atomicAdd(&dst->y, coef[q].y);
+    }
+}
+
+// adjoint: scatter coefficient cotangents into the buckets that the medians selected
+__global__ void k_adj_scatter(const InstDesc* __restrict__ insts, const c64* __restrict__ dcoef) {
+    const InstDesc& I = insts[blockIdx.y];
+    const int64_t nout = min(I.cnt[1], min(I.out_cap, I.cap));
+    const int L = I.L;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nout; p += (int64_t)gridDim.x * blockDim.x) {
+        int64_t q = I.outpos[p];
+        int lre = I.sel[2 * q], lim = I.sel[2 * q + 1];
+        c64 g = dcoef[p];
+        atomicAdd(&I.C[I.soff[lre] + I.H[q * L + lre]].x, g.x);
+        atomicAdd(&I.C[I.soff[lim] + I.H[q * L + lim]].y, g.y);
+    }
+}
+
+// lattice nodes: numer = j z mod M (exact), x = numer / M
+__global__ void k_points(const InstDesc* __restrict__ insts, int32_t* numer, double* xout) {
+    const InstDesc& I = insts[0];
+    const int L = I.L, d = I.d;
+    const int64_t tot = I.soff[L] * d;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (int64_t)gridDim.x * blockDim.x) {
+        int64_t node = e / d;
+        int t = (int)(e - node * d);
+        int l = 0;
+        while (I.soff[l + 1] <= node) ++l;
+        int64_t j = node - I.soff[l];
+        int64_t M = I.Ml[l];
+        int64_t v = (j * (int64_t)I.z[l * d + t]) % M;
+        if (numer) numer[e] = (int32_t)v;
+        if (xout) xout[e] = (double)v / (double)M;
+    }
+}
+
+// per-dimension min / max of the candidates (plan validation: N_Gamma, |k| bound)
+__global__ void k_cand_stats(const int32_t* __restrict__ cand, int64_t n, int d, int* mn, int* mx) {
+    __shared__ int smn[kMaxD], smx[kMaxD];
+    if (threadIdx.x < d) { smn[threadIdx.x] = INT_MAX; smx[threadIdx.x] = INT_MIN; }
+    __syncthreads();
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * d; e += (int64_t)gridDim.x * blockDim.x) {
+        int t = (int)(e % d);
+        int v = cand[e];
+        atomicMin(&smn[t], v);
+        atomicMax(&smx[t], v);
+    }
+    __syncthreads();
+    if (threadIdx.x < d) {
+        atomicMin(&mn[threadIdx.x], smn[threadIdx.x]);
+        atomicMax(&mx[threadIdx.x], smx[threadIdx.x]);
+    }
+}
+
+__global__ void k_to_c64(const void* src, int prec, c64* dst, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = prec ? cvt<double>(reinterpret_cast<const c32*>(src)[i]) : reinterpret_cast<const c64*>(src)[i];
+}
+
+__global__ void k_clear_inst(InstDesc* __restrict__ insts, int clear_det, int clear_coll, int clear_C) {
+    InstDesc& I = insts[blockIdx.y];
+    const int64_t W = (I.n + 31) >> 5;
+    const int64_t SM = I.soff[I.L];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    if (clear_det)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < W; i += stride) I.detbits[i] = 0;
+    if (clear_coll)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < SM; i += stride) I.coll[i] = 0;
+    if (clear_C)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < SM; i += stride) I.C[i] = c64{0, 0};
+    if (clear_det && blockIdx.x == 0 && threadIdx.x < 8) I.cnt[threadIdx.x] = 0;
+}
+
+// ================================================================== launch wrappers
+int launch_cand_stats(const int32_t* cand, int64_t n, int d, int* mn, int* mx, cudaStream_t st) {
+    int gx = (int)std::min<int64_t>(4 * 152, (n * d + 255) / 256 + 1);
+    k_cand_stats<<<gx, 256, 0, st>>>(cand, n, d, mn, mx);
+    return launch_check("k_cand_stats");
+}
+
+int launch_to_c64(const void* src, int prec, c64* dst, int64_t n, cudaStream_t st) {
+    int gx = (int)std::min<int64_t>(4 * 152, (n + 255) / 256 + 1);
+    k_to_c64<<<gx, 256, 0, st>>>(src, prec, dst, n);
+    return launch_check("k_to_c64");
+}
+
+int launch_clear(InstDesc* di, int ninst, int clear_det, int clear_coll, int clear_C, cudaStream_t st) {
+    k_clear_inst<<<dim3(64, ninst), 256, 0, st>>>(di, clear_det, clear_coll, clear_C);
+    return launch_check("k_clear_inst");
+}
+
+template <int D>
+static int launch_hash_d(const InstDesc* di, int ninst, int gx, size_t smem, cudaStream_t st) {
+    static bool attr = false;
+    if (!attr) {
+        SFFT_CU(cudaFuncSetAttribute(k_hash_count<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+        attr = true;
+    }
+    k_hash_count<D><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di);
+    return launch_check("k_hash_count");
+}
+
+int launch_hash_count(const InstDesc* di, int ninst, int d, int gx, size_t smem, cudaStream_t st) {
+    switch (d) {
+#define SFFT_HD(D) case D: return launch_hash_d<D>(di, ninst, gx, smem, st);
+        SFFT_HD(1) SFFT_HD(2) SFFT_HD(3) SFFT_HD(4) SFFT_HD(5) SFFT_HD(6) SFFT_HD(7) SFFT_HD(8)
+        SFFT_HD(9) SFFT_HD(10) SFFT_HD(11) SFFT_HD(12) SFFT_HD(13) SFFT_HD(14) SFFT_HD(15) SFFT_HD(16)
+        SFFT_HD(17) SFFT_HD(18) SFFT_HD(19) SFFT_HD(20) SFFT_HD(21) SFFT_HD(22) SFFT_HD(23) SFFT_HD(24)
+        SFFT_HD(25) SFFT_HD(26) SFFT_HD(27) SFFT_HD(28) SFFT_HD(29) SFFT_HD(30) SFFT_HD(31) SFFT_HD(32)
+#undef SFFT_HD
+        default: set_error("dimension %d not supported", d); return SFFT_EINVAL;
+    }
+}
+
+int launch_zero_test(const LatDesc* dl, int nlat, InstDesc* di, int prec, double kappa_u, cudaStream_t st) {
+    if (prec) k_zero_test<float><<<nlat, kZtThreads, 0, st>>>(dl, di, kappa_u);
+    else k_zero_test<double><<<nlat, kZtThreads, 0, st>>>(dl, di, kappa_u);
+    return launch_check("k_zero_test");
+}
+
+int launch_compact(InstDesc* di, int ninst, cudaStream_t st) {
+    k_compact<<<ninst, kCompactThreads, 0, st>>>(di);
+    return launch_check("k_compact");
+}
+
+int launch_det_hashes(const InstDesc* di, int ninst, int64_t maxdet, cudaStream_t st) {
+    int gx = (int)((maxdet + 7) / 8);
+    if (gx < 1) gx = 1;
+    k_det_hashes<<<dim3(gx, ninst), 256, 0, st>>>(di);
+    return launch_check("k_det_hashes");
+}
+
+int launch_collisions(const InstDesc* di, int ninst, cudaStream_t st) {
+    k_collisions<<<dim3(152, ninst), 256, 0, st>>>(di);
+    return launch_check("k_collisions");
+}
+
+int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int mode, cudaStream_t st) {
+    int gx = (int)((maxdet + 7) / 8);
+    if (gx < 1) gx = 1;
+    if (prec) k_combine<float><<<dim3(gx, ninst), 256, 0, st>>>(di, mode);
+    else k_combine<double><<<dim3(gx, ninst), 256, 0, st>>>(di, mode);
+    return launch_check("k_combine");
+}
+
+int launch_scatter_coef(const InstDesc* di, int ninst, cudaStream_t st) {
+    k_scatter_coef<<<dim3(152, ninst), 256, 0, st>>>(di);
+    return launch_check("k_scatter_coef");
+}
+
+int launch_select(InstDesc* di, int ninst, cudaStream_t st) {
+    k_select<<<ninst, kSelThreads, 0, st>>>(di);
+    return launch_check("k_select");
+}
+
+int launch_scatter_terms(const InstDesc* di, const int32_t* kvec, const c64* coef, int64_t nterms, cudaStream_t st) {
+    int gx = (int)std::min<int64_t>(1024, (nterms * 64 + 255) / 256 + 1);
+    k_scatter_terms<<<dim3(gx, 1), 256, 0, st>>>(di, kvec, coef, nterms);
+    return launch_check("k_scatter_terms");
+}
+
+int launch_adj_scatter(const InstDesc* di, const c64* dcoef, cudaStream_t st) {
+    k_adj_scatter<<<dim3(64, 1), 256, 0, st>>>(di, dcoef);
+    return launch_check("k_adj_scatter");
+}
+
+int launch_points(const InstDesc* di, int32_t* numer, double* x, int64_t tot, cudaStream_t st) {
+    int gx = (int)std::min<int64_t>(4096, (tot + 255) / 256 + 1);
+    k_points<<<gx, 256, 0, st>>>(di, numer, x);
+    return launch_check("k_points");
+}
+
+}  // namespace sfft

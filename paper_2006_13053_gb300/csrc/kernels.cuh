@@ -1,0 +1,30 @@
+// Launch wrappers of the per-lattice / per-candidate kernels (kernels.cu).
+#pragma once
+#include "common.cuh"
+
+namespace sfft {
+int launch_hash_count(const InstDesc* di, int ninst, int d, int gx, size_t smem, cudaStream_t st);
+int launch_zero_test(const LatDesc* dl, int nlat, InstDesc* di, int prec, double kappa_u, cudaStream_t st);
+int launch_compact(InstDesc* di, int ninst, cudaStream_t st);
+int launch_det_hashes(const InstDesc* di, int ninst, int64_t maxdet, cudaStream_t st);
+int launch_collisions(const InstDesc* di, int ninst, cudaStream_t st);
+int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int mode, cudaStream_t st);
+int launch_scatter_coef(const InstDesc* di, int ninst, cudaStream_t st);
+int launch_select(InstDesc* di, int ninst, cudaStream_t st);
+int launch_scatter_terms(const InstDesc* di, const int32_t* kvec, const c64* coef, int64_t nterms, cudaStream_t st);
+int launch_adj_scatter(const InstDesc* di, const c64* dcoef, cudaStream_t st);
+int launch_points(const InstDesc* di, int32_t* numer, double* x, int64_t tot, cudaStream_t st);
+int launch_cand_stats(const int32_t* cand, int64_t n, int d, int* mn, int* mx, cudaStream_t st);
+int launch_to_c64(const void* src, int prec, c64* dst, int64_t n, cudaStream_t st);
+int launch_clear(InstDesc* di, int ninst, int clear_det, int clear_coll, int clear_C, cudaStream_t st);
+// sum-of-products test function (sop.cu)
+int launch_sop_coefs(const double* theta, int n_terms, int K, double width, double* a, double* da, cudaStream_t st);
+int launch_sop_sample(const InstDesc* di, const int32_t* triples_dev, int n_terms, int K, const double* a, void* out,
+                      int prec, cudaStream_t st);
+int launch_sop_backward(const InstDesc* di, const int32_t* triples_dev, int n_terms, int K, const double* a,
+                        const double* da, const void* dsamples, int prec, double* dtheta, cudaStream_t st);
+int launch_sop_eval_points(const double* x, int64_t n, int d, const int32_t* triples_dev, int n_terms, int K,
+                           const double* a, double* y, cudaStream_t st);
+int launch_sparse_eval_points(const double* x, int64_t n, int d, const int32_t* kvec, const double* coef,
+                              int64_t nterms, double* y, cudaStream_t st);
+}  // namespace sfft

@@ -1,0 +1,79 @@
+// Host-side plan object behind the opaque sfft_plan handle, and the argument block of the
+// reconstruction stage sequence (shared by single plans and batches).
+#pragma once
+#include <vector>
+
+#include "common.cuh"
+
+namespace sfft {
+
+struct PipeArgs {
+    int ninst = 1, nlat = 0, maxN = 0, prec = 0, d = 0, hash_gx = 1;
+    size_t hash_smem = 0;
+    int64_t maxcap = 0;
+    bool sm_prec = true, sm64 = true;
+    int hybrid = 0, refine = 0;
+    InstDesc* d_inst = nullptr;
+    const LatDesc* d_lats = nullptr;
+    const BlueJob* jobs_fwd = nullptr;
+    const BlueJob* jobs_model = nullptr;
+    const BlueJob* jobs_rfwd = nullptr;
+};
+
+struct Plan {
+    int d = 0, L = 0, prec = 0, nwords = 0, maxN = 0;
+    int64_t n = 0, s = 0, sumM = 0, cap = 0, N_gamma = 0, kmax = 0, last_nout = 0;
+    sfft_params p;
+    const int32_t* cand = nullptr;
+    cudaStream_t st = nullptr;
+    std::vector<int64_t> M, z, soff;
+    std::vector<int32_t> boff;
+    std::vector<FftTables*> tabs;
+    std::vector<void*> allocs;
+    // device workspace
+    uint32_t* nzbits = nullptr;
+    void* ghat = nullptr;
+    LatStats* stats = nullptr;
+    uint32_t* detbits = nullptr;
+    int64_t* det = nullptr;
+    int64_t* cnt = nullptr;
+    c64* coef = nullptr;
+    int32_t* H = nullptr;
+    uint8_t* sel = nullptr;
+    int32_t* outpos = nullptr;
+    int32_t* coll = nullptr;
+    c64* C = nullptr;
+    void* rhat = nullptr;
+    void* resid = nullptr;
+    void* scratch = nullptr;
+    double* sop_a = nullptr;
+    int32_t* sop_tri = nullptr;
+    InstDesc* d_inst = nullptr;
+    InstDesc* h_inst = nullptr;  // pinned
+    int64_t* h_cnt = nullptr;    // pinned
+    LatDesc* d_lats = nullptr;
+    std::vector<BlueJob> jobs_fwd, jobs_model, jobs_rfwd;
+    BlueJob *d_jobs_fwd = nullptr, *d_jobs_model = nullptr, *d_jobs_rfwd = nullptr, *d_jobs_tmp = nullptr;
+    size_t hash_smem = 0;
+    bool have_forward = false;
+
+    void release();
+    int alloc(void** p, size_t bytes);
+    size_t esz() const;
+    bool fits_smem(int tprec) const;
+    int build_jobs();
+    int hash_grid() const;
+    PipeArgs pipe_args();
+};
+
+int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L, const int64_t* M, const int64_t* z,
+                const sfft_params* p, cudaStream_t st);
+int run_pipeline(const PipeArgs& a, cudaStream_t st);
+int upload_jobs(const std::vector<BlueJob>& v, BlueJob** dst, std::vector<void*>* owner);
+uint64_t philox_word0(uint64_t key0, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3);
+double philox_u01(uint64_t key, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3);
+bool is_prime(int64_t n);
+int64_t next_prime_above(double x);
+int L_rule(int rule, int64_t n, double delta, double c);
+
+}  // namespace sfft

@@ -120,6 +120,35 @@ def sop_params(d: int, n_terms: int, seed: int, stream: int = S_SOP, lo: float =
     return triples, theta
 
 
+def sop_candidate_set(triples: np.ndarray, d: int, kmax: int, n_total: int, box: int, seed: int,
+                      stream: int = S_GAMMA) -> np.ndarray:
+    """Candidate set for the sum-of-products workload: every k supported on one of the
+    triples with |k_t| <= kmax (deduplicated), then distinct uniform filler from [-box, box]^d
+    up to n_total rows (int32 [n_total, d], structured part first)."""
+    parts = []
+    g3 = full_grid(3, kmax).astype(np.int64)
+    for T in triples:
+        k = np.zeros((g3.shape[0], d), dtype=np.int64)
+        k[:, np.asarray(T)] = g3
+        parts.append(k)
+    core = np.unique(np.concatenate(parts), axis=0)
+    if n_total <= core.shape[0]:
+        return np.ascontiguousarray(core[:n_total].astype(np.int32))
+    g = rng(seed, stream)
+    seen = {tuple(r) for r in core}
+    fill = []
+    while len(fill) < n_total - core.shape[0]:
+        draw = g.integers(-box, box + 1, size=(n_total - core.shape[0] - len(fill) + 64, d))
+        for r in draw:
+            tr = tuple(int(v) for v in r)
+            if tr not in seen:
+                seen.add(tr)
+                fill.append(tr)
+                if len(fill) == n_total - core.shape[0]:
+                    break
+    return np.ascontiguousarray(np.concatenate([core, np.array(fill, dtype=np.int64)]).astype(np.int32))
+
+
 def uniform_tail(n: int, seed: int, stream: int = S_TAIL) -> np.ndarray:
     g = rng(seed, stream)
     return g.random(n)

@@ -1,0 +1,402 @@
+"""CUDA path vs the FP64 oracle on identical seeded inputs (all calls through the C ABI).
+
+Tolerances: hashes, counts, detected sets, supports and collision counts bit-exact; FP64
+coefficients within 1e-10 relative (max-norm over the output, relative to max |c|); FP32
+path (with one FP64 refinement step) within 1e-4 relative; FP32 FFT buckets within the
+guard band 32 u log2(N) rms(x) that the zero test assumes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import sfft_synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def G():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    import paper_2006_13053_gb300 as G
+    return G
+
+
+def dev():
+    import torch
+    return torch.device("cuda:0")
+
+
+def T(a, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(dev())
+
+
+def bluestein_N(M):
+    need, best = 2 * M - 1, None
+    p5 = 1
+    while p5 < 4 * need:
+        p3 = p5
+        while p3 < 4 * need:
+            p2 = p3
+            while p2 < 4 * need:
+                if p2 >= need and (best is None or p2 < best):
+                    best = p2
+                p2 *= 2
+            p3 *= 3
+        p5 *= 5
+    return best
+
+
+def relmax(a, b):
+    b = np.asarray(b)
+    return float(np.max(np.abs(np.asarray(a) - b)) / max(np.max(np.abs(b)), 1e-300)) if b.size else 0.0
+
+
+def cfg1(seed, s=20, N=16):
+    cand = S.full_grid(3, N)
+    n = cand.shape[0]
+    L = O.L_cor26(n, 0.1)
+    M = O.lattice_size(cand, s)
+    sup = S.support_indices(n, s, seed)
+    c = S.coef_mag_phase(s, 1, 10, seed)
+    z = S.generators(L, 3, M, seed)
+    return cand, sup, c, z, M, L
+
+
+def cfg2(seed, n=2 ** 15, d=10, s=200, snr=40.0, box=64):
+    cand = S.uniform_distinct(n, d, -box, box, seed)
+    L = O.L_cor26(n, 0.1)
+    M = O.lattice_size(cand, s)
+    sup = S.support_indices(n, s, seed)
+    c = S.coef_cgauss(s, seed)
+    z = S.generators(L, d, M, seed)
+    sig = S.snr_sigma(c, snr)
+    return cand, sup, c, z, M, L, sig
+
+
+# ------------------------------------------------------------------ FFT stage
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("Ms", [[211] * 5, [10331] * 3, [83, 89, 97, 101, 103]])
+def test_lattice_dft_parity(G, prec, Ms):
+    import torch
+    L = len(Ms)
+    cand = S.uniform_distinct(64, 2, -20, 20, 1)
+    z = np.stack([S.generators(1, 2, m, 10 + i)[0] for i, m in enumerate(Ms)])
+    rng = np.random.default_rng(prec + len(Ms))
+    y = rng.standard_normal(sum(Ms)) + 1j * rng.standard_normal(sum(Ms))
+    if prec == 1:
+        y = y.astype(np.complex64).astype(np.complex128)
+    plan = G.Plan(T(cand), 4, L=L, M=Ms, z=z, precision=prec, tau_abs=1e300)
+    ys = T(y, torch.complex64 if prec else torch.complex128)
+    _, _, info = plan.reconstruct(ys, diag=True)
+    got = info["ghat"].cpu().numpy()
+    for l, (a, b) in enumerate(zip(O.split_lattices(got, Ms), O.split_lattices(y, Ms))):
+        ref = O.lattice_dft(b, Ms[l])
+        rms = np.sqrt(np.mean(np.abs(b) ** 2))
+        N = bluestein_N(Ms[l])
+        if prec == 0:
+            assert np.max(np.abs(a - ref)) <= 1e-13 * rms
+        else:
+            band = 32 * 2.0 ** -24 * math.log2(N) * rms
+            assert np.max(np.abs(a - ref)) <= band
+            assert np.linalg.norm(a - ref) / np.linalg.norm(ref) < 2e-6
+
+
+# ------------------------------------------------------------------ hashes / counts / detection
+@pytest.mark.parametrize("which", ["cfg1", "cfg2"])
+def test_hashes_counts_detected_bit_exact(G, which):
+    import torch
+    if which == "cfg1":
+        cand, sup, c, z, M, L = cfg1(3)
+        y = O.sample_sparse_poly(cand[sup], c, z, M)
+        kw = dict(precision=0, tau_rel=1e-10)
+        okw = dict(tau_rel=1e-10)
+        ys = T(y)
+    else:
+        cand, sup, c, z, M, L, sig = cfg2(4, n=2 ** 13, s=60)
+        y = O.sample_sparse_poly(cand[sup], c, z, M) + S.noise(L * M, sig, 4)
+        y = y.astype(np.complex64).astype(np.complex128)
+        tau = 6 * sig / math.sqrt(M)
+        kw = dict(precision=1, tau_abs=tau, tau_rel=0.0, refine=1)
+        okw = dict(tau_abs=tau, do_refine=True, refine_mode="bucket")
+        ys = T(y, torch.complex64)
+    plan = G.Plan(T(cand), len(sup), L=L, M=[M] * L, z=z, **kw)
+    supp, coef, info = plan.reconstruct(ys, diag=True, counts=True, hashes=True)
+    ref = O.reconstruct(cand, y, z, M, want_counts=True, **okw)
+    assert np.array_equal(info["hashes"].cpu().numpy(), O.hashes(cand, z, M))
+    assert np.array_equal(info["counts"].cpu().numpy(), ref.counts)
+    assert np.array_equal(info["detected"].cpu().numpy(), ref.detected)
+    assert np.array_equal(supp.cpu().numpy(), ref.supp)
+    tol = 1e-10 if which == "cfg1" else 1e-4
+    assert relmax(coef.cpu().numpy(), ref.coef) <= tol
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_config1_fp64_end_to_end(G, seed):
+    cand, sup, c, z, M, L = cfg1(seed)
+    y = O.sample_sparse_poly(cand[sup], c, z, M)
+    ref = O.reconstruct(cand, y, z, M, tau_rel=1e-10)
+    plan = G.Plan(T(cand), 20, L=L, M=[M] * L, z=z, precision=0, tau_rel=1e-10)
+    supp, coef = plan.reconstruct(T(y))
+    assert np.array_equal(supp.cpu().numpy(), ref.supp)
+    assert relmax(coef.cpu().numpy(), ref.coef) <= 1e-10
+    # and the paper's exact recovery (Corollary 2.6) when the oracle recovered I
+    if np.array_equal(ref.supp, sup):
+        assert relmax(coef.cpu().numpy(), c) <= 1e-10
+
+
+def test_config1_plan_rule_defaults(G):
+    """Plan-side parameter rule (Corollary 2.6) and Philox generators vs the oracle's."""
+    cand, sup, c, z, M, L = cfg1(0)
+    plan = G.Plan(T(cand), 20, precision=0, seed=77)
+    assert plan.L == L and np.all(plan.M == M)
+    assert np.array_equal(plan.z, O.plan_generators(77, L, 3, [M] * L))
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_config2_reduced_fp32_refine(G, seed):
+    import torch
+    cand, sup, c, z, M, L, sig = cfg2(seed)
+    y = O.sample_sparse_poly(cand[sup], c, z, M) + S.noise(L * M, sig, seed)
+    y32 = y.astype(np.complex64)
+    tau = 6 * sig / math.sqrt(M)
+    ref = O.reconstruct(cand, y32.astype(np.complex128), z, M, tau_abs=tau, do_refine=True, refine_mode="bucket")
+    plan = G.Plan(T(cand), len(sup), L=L, M=[M] * L, z=z, precision=1, refine=1, tau_abs=tau, tau_rel=0.0)
+    supp, coef, info = plan.reconstruct(T(y32), diag=True)
+    assert np.array_equal(info["detected"].cpu().numpy(), ref.detected)
+    assert np.array_equal(supp.cpu().numpy(), ref.supp)
+    assert relmax(coef.cpu().numpy(), ref.coef) <= 1e-4
+    # the FP64 path on the same samples agrees with the FP64 oracle to 1e-10
+    plan64 = G.Plan(T(cand), len(sup), L=L, M=[M] * L, z=z, precision=0, refine=1, tau_abs=tau, tau_rel=0.0)
+    s64, c64 = plan64.reconstruct(T(y32.astype(np.complex128)))
+    assert np.array_equal(s64.cpu().numpy(), ref.supp)
+    assert relmax(c64.cpu().numpy(), ref.coef) <= 1e-10
+
+
+def test_config2_full_size_one_seed(G):
+    """|Gamma| = 2^20, d = 10, s = 1000, L = 37, M = 10331, 40 dB noise, FP32 + refinement, in the
+    launch configuration of the benchmark."""
+    import torch
+    seed = 0
+    cand, sup, c, z, M, L, sig = cfg2(seed, n=2 ** 20, s=1000)
+    assert (L, M) == (37, 10331)
+    yl = []
+    for l in range(L):  # bucket identity route for the oracle's samples would use the method; evaluate directly
+        yl.append(O.eval_sparse_poly_at_numerators(cand[sup], c, O.lattice_numerators(z[l], M), M))
+    y = (np.concatenate(yl) + S.noise(L * M, sig, seed)).astype(np.complex64)
+    tau = 6 * sig / math.sqrt(M)
+    ref = O.reconstruct(cand, y.astype(np.complex128), z, M, tau_abs=tau, do_refine=True, refine_mode="bucket")
+    plan = G.Plan(T(cand), 1000, L=L, M=[M] * L, z=z, precision=1, refine=1, tau_abs=tau, tau_rel=0.0)
+    supp, coef, info = plan.reconstruct(T(y), diag=True)
+    assert np.array_equal(info["detected"].cpu().numpy(), ref.detected)
+    assert np.array_equal(supp.cpu().numpy(), ref.supp)
+    assert relmax(coef.cpu().numpy(), ref.coef) <= 1e-4
+    # sampled hashes of 4096 candidates, bit-exact
+    idx = np.random.default_rng(0).choice(cand.shape[0], 4096, replace=False)
+    _, _, info2 = plan.reconstruct(T(y), diag=True, hashes=True)
+    assert np.array_equal(info2["hashes"].cpu().numpy()[idx], O.hashes(cand[idx], z, M))
+
+
+# ------------------------------------------------------------------ samplers and nodes
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sampler_and_points(G, prec):
+    import torch
+    cand, sup, c, z, M, L = cfg1(5)
+    plan = G.Plan(T(cand), 20, L=L, M=[M] * L, z=z, precision=prec)
+    num, x = plan.sample_points()
+    ref_num = np.concatenate([O.lattice_numerators(z[l], M) for l in range(L)])
+    assert np.array_equal(num.cpu().numpy(), ref_num)
+    assert np.array_equal(x.cpu().numpy(), ref_num / M)
+    noise = S.noise(L * M, 0.1, 5)
+    y = plan.sample_sparse_poly(T(cand[sup]), T(c), T(noise)).cpu().numpy()
+    ref = O.sample_sparse_poly(cand[sup], c, z, M) + noise
+    tol = 1e-12 if prec == 0 else 3e-6
+    assert np.max(np.abs(y - ref)) <= tol * np.sqrt(np.sum(np.abs(c) ** 2)) * 10
+
+
+# ------------------------------------------------------------------ Algorithm 1, Remark 2.8, Algorithm 4
+def test_alg1_nu_quarter(G):
+    cand, sup, c, z, M, L = cfg1(7)
+    y = O.sample_sparse_poly(cand[sup], c, z, M)
+    ref = O.reconstruct(cand, y, z, M, tau_rel=1e-10, nu=0.25)
+    plan = G.Plan(T(cand), 20, L=L, M=[M] * L, z=z, precision=0, tau_rel=1e-10, nu=0.25, c=10.33)
+    supp, coef, info = plan.reconstruct(T(y), diag=True)
+    assert np.array_equal(info["detected"].cpu().numpy(), ref.detected)
+
+
+def test_hybrid_combine_and_collisions(G):
+    cand, sup, c, z, M, L = cfg1(8, s=40)
+    L = 7
+    z = z[:7]
+    y = O.sample_sparse_poly(cand[sup], c, z, M)
+    ref = O.reconstruct(cand, y, z, M, tau_rel=1e-10, postproc="hybrid")
+    plan = G.Plan(T(cand), 40, L=L, M=[M] * L, z=z, precision=0, tau_rel=1e-10, combine=G.COMBINE_HYBRID)
+    supp, coef, info = plan.reconstruct(T(y), diag=True, collisions=True)
+    assert np.array_equal(supp.cpu().numpy(), ref.supp)
+    assert relmax(coef.cpu().numpy(), ref.coef) <= 1e-10
+    cc = O.collision_counts(ref.H, [M] * L)
+    assert np.array_equal(info["collisions"].cpu().numpy(), cc)
+
+
+def test_top_s_selection_with_ties(G):
+    cand, sup, c, z, M, L = cfg1(9, s=30)
+    c = np.where(np.arange(30) % 3 == 0, 5.0, np.where(np.arange(30) % 3 == 1, -5.0, 2.0 + 1j))  # ties in modulus
+    y = O.sample_sparse_poly(cand[sup], c, z, M)
+    for s_t in (5, 12, 25):
+        ref = O.reconstruct(cand, y, z, M, tau_rel=1e-10, s_tilde=s_t, theta=1.0)
+        plan = G.Plan(T(cand), 30, L=L, M=[M] * L, z=z, precision=0, tau_rel=1e-10, s_tilde=s_t, theta_abs=1.0)
+        supp, coef = plan.reconstruct(T(y))
+        got = supp.cpu().numpy()
+        assert len(got) == len(ref.supp) == s_t
+        # unique part: every item strictly above the cut modulus must be selected; the rest
+        # must have the cut modulus (ties, equal up to FP64 rounding)
+        full = O.reconstruct(cand, y, z, M, tau_rel=1e-10)
+        mod = dict(zip(full.detected.tolist(), np.abs(full.pcheck)))
+        cut = sorted(mod.values(), reverse=True)[s_t - 1]
+        must = {k for k, v in mod.items() if v > cut * (1 + 1e-12)}
+        assert must <= set(got.tolist())
+        assert all(abs(mod[k] - cut) <= 1e-12 * cut for k in set(got.tolist()) - must)
+
+
+# ------------------------------------------------------------------ adjoint
+@pytest.mark.parametrize("prec", [0, 1])
+def test_backward_matches_oracle_vjp(G, prec):
+    import torch
+    d, n, s, M, L = 3, 300, 8, 89, 7
+    cand = S.uniform_distinct(n, d, -10, 10, 2)
+    sup = S.support_indices(n, s, 2)
+    c = S.coef_cgauss(s, 2)
+    z = S.generators(L, d, M, 2)
+    y = O.sample_sparse_poly(cand[sup], c, z, M) + S.noise(L * M, 0.05, 2)
+    if prec:
+        y = y.astype(np.complex64).astype(np.complex128)
+    plan = G.Plan(T(cand), s, L=L, M=[M] * L, z=z, precision=prec, tau_abs=0.02, tau_rel=0.0)
+    ys = T(y, torch.complex64 if prec else torch.complex128)
+    supp, coef = plan.reconstruct(ys)
+    ref = O.reconstruct(cand, y, z, M, tau_abs=0.02)
+    assert np.array_equal(supp.cpu().numpy(), ref.supp)
+    dc = np.random.default_rng(1).standard_normal(len(ref.supp)) + 1j * np.random.default_rng(2).standard_normal(len(ref.supp))
+    H = O.hashes(cand[ref.supp], z, M)
+    gref = O.reconstruct_vjp(y, H, [M] * L, dc)
+    g = plan.backward(T(dc)).cpu().numpy()
+    tol = 1e-12 if prec == 0 else 2e-6
+    assert np.max(np.abs(g - gref)) <= tol * np.max(np.abs(gref))
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sop_sampler_and_theta_adjoint(G, prec):
+    import torch
+    d = 8
+    cand = S.uniform_distinct(500, d, -20, 20, 3)
+    tri, theta = S.sop_params(d, 6, 3)
+    M, L = 211, 5
+    z = S.generators(L, d, M, 3)
+    plan = G.Plan(T(cand), 10, L=L, M=[M] * L, z=z, precision=prec)
+    y = plan.sample_sop(tri, T(theta)).cpu().numpy()
+    nodes = np.concatenate([O.lattice_nodes(z[l], M) for l in range(L)])
+    ref = O.sop_eval(tri, theta, nodes)
+    tol = 1e-12 if prec == 0 else 2e-5
+    assert np.max(np.abs(y.real - ref)) <= tol * np.max(np.abs(ref))
+    assert np.max(np.abs(y.imag)) == 0
+    w = np.random.default_rng(0).standard_normal(L * M)
+    ws = T(w.astype(np.complex128), torch.complex64 if prec else torch.complex128)
+    g = plan.sample_sop_backward(tri, T(theta), ws).cpu().numpy()
+    gref = O.sop_grad_theta(tri, theta, nodes, w)
+    assert np.max(np.abs(g - gref)) <= (1e-9 if prec == 0 else 1e-4) * np.max(np.abs(gref))
+
+
+def test_autograd_theta_gradient_vs_finite_differences(G):
+    """Differentiable reconstruction (support fixed): d loss / d theta via the adjoint kernels
+    vs FP64 central finite differences of the GPU forward, on a sum-of-products function whose
+    candidate set holds the low frequencies of every triple."""
+    import torch
+    d = 8
+    tri, theta0 = S.sop_params(d, 4, 5)
+    cand = S.sop_candidate_set(tri, d, 4, 3000, 8, 5)
+    M, L = 10331, 7
+    z = S.generators(L, d, M, 5)
+    plan = G.Plan(T(cand), 100, L=L, M=[M] * L, z=z, precision=0, tau_abs=1e-3, tau_rel=0.0, s_tilde=100)
+    th = T(theta0).requires_grad_(True)
+    supp, coef = G.SopReconstruct.apply(th, plan, tri, 48, 32.0)
+    target = (coef.detach() * 0.9 + 0.01).contiguous()
+    loss = (coef - target).abs().pow(2).sum()
+    loss.backward()
+    g = th.grad.cpu().numpy()
+    sref = supp.cpu().numpy()
+
+    def f(thv):
+        y = plan.sample_sop(tri, T(thv))
+        s2, c2 = plan.reconstruct(y)
+        assert np.array_equal(s2.cpu().numpy(), sref)
+        return float((c2 - target).abs().pow(2).sum())
+
+    h = 1e-6
+    for m in range(len(theta0)):
+        tp, tm = theta0.copy(), theta0.copy()
+        tp[m] += h
+        tm[m] -= h
+        fd = (f(tp) - f(tm)) / (2 * h)
+        assert g[m] == pytest.approx(fd, rel=1e-5, abs=1e-8)
+
+
+# ------------------------------------------------------------------ errors and edge cases
+def test_error_codes(G):
+    cand, sup, c, z, M, L = cfg1(0)
+    tc = T(cand)
+    with pytest.raises(G.SfftError) as e:
+        G.Plan(tc, 20, L=L, M=[212] * L, z=z % 212)
+    assert e.value.code == 2  # ENOTPRIME
+    with pytest.raises(G.SfftError) as e:
+        G.Plan(tc, 20, L=4, M=[M] * 4, z=z[:4])
+    assert e.value.code == 1  # even L
+    with pytest.raises(G.SfftError) as e:
+        G.Plan(tc, 20, L=3, M=[31] * 3, z=z[:3] % 31)
+    assert e.value.code == 3  # M <= N_Gamma
+    big = np.full((4, 3), 2 ** 28, dtype=np.int32)
+    big[:, 0] = np.arange(4)
+    with pytest.raises(G.SfftError) as e:
+        G.Plan(T(big), 1, L=3, M=[1000003] * 3)
+    assert e.value.code in (3, 4)
+    plan = G.Plan(tc, 20, L=L, M=[M] * L, z=z, precision=0)
+    with pytest.raises(G.SfftError) as e:
+        plan.backward(T(np.zeros(0, dtype=np.complex128)))
+    assert e.value.code == 9  # backward before forward
+    y = O.sample_sparse_poly(cand[sup], c, z, M)
+    import ctypes
+    supp = T(np.zeros(4, dtype=np.int64))
+    coef = T(np.zeros(4, dtype=np.complex128))
+    nout = ctypes.c_int64()
+    rc = G._native.sfft_reconstruct(plan.handle, ctypes.c_void_p(T(y).data_ptr()), ctypes.c_void_p(supp.data_ptr()),
+                                    ctypes.c_void_p(coef.data_ptr()), 4, ctypes.byref(nout), None)
+    assert rc == 8 and nout.value == 20  # ECAPACITY, true count reported
+
+
+def test_edge_cases(G):
+    import torch
+    # one candidate, one lattice, d = 1
+    cand = np.array([[3]], dtype=np.int32)
+    plan = G.Plan(T(cand), 1, L=1, M=[11], z=[[4]], precision=0, tau_rel=1e-10)
+    y = O.sample_sparse_poly(cand, np.array([2.0 - 1j]), np.array([[4]]), 11)
+    supp, coef = plan.reconstruct(T(y))
+    assert supp.cpu().tolist() == [0] and abs(coef.cpu().numpy()[0] - (2 - 1j)) < 1e-13
+    # all-zero samples: nothing is detected
+    cand, sup, c, z, M, L = cfg1(1)
+    plan = G.Plan(T(cand), 20, L=L, M=[M] * L, z=z, precision=0, tau_abs=1e-12, tau_rel=0.0)
+    supp, coef = plan.reconstruct(torch.zeros(L * M, dtype=torch.complex128, device=dev()))
+    assert supp.numel() == 0
+    # ragged lattice sizes (fallback primes), FP32 without refinement
+    Ms = O.fallback_primes(23, 20)
+    z2 = np.stack([S.generators(1, 3, m, 20 + i)[0] for i, m in enumerate(Ms)])
+    y = O.sample_sparse_poly(cand[sup], c, z2, Ms).astype(np.complex64)
+    ref = O.reconstruct(cand, y.astype(np.complex128), z2, Ms, tau_rel=1e-4)
+    plan = G.Plan(T(cand), 20, L=23, M=Ms, z=z2, precision=1, tau_rel=1e-4)
+    supp, coef = plan.reconstruct(T(y))
+    assert np.array_equal(supp.cpu().numpy(), ref.supp)
+    assert relmax(coef.cpu().numpy(), ref.coef) <= 1e-4
