@@ -1,0 +1,398 @@
+#!/usr/bin/env python
+"""Throughput of the rank-1-lattice sparse FFT on GB300.
+
+Workload (one step): 16 independent reconstructions, each with d = 10, |Gamma| = 2^20 distinct
+frequencies drawn uniformly from [-64, 64]^10, a 1000-sparse trigonometric polynomial with
+complex-Gaussian coefficients, 40 dB complex Gaussian sample noise, L = 37 lattices of size
+M = 10331 (Corollary 2.6 with c = 10.33, delta = 0.1), FP32 samples/FFTs with one FP64
+refinement step.  A step samples the function along all lattices (lattice nodes + sampler
+kernels) and runs the whole reconstruction (lattice DFTs, zero test, hash + count, median
+combine, refinement, Algorithm 4 selection) for all 16 instances in one batch.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Prints one JSON line (rank 0).  --impl reference times the FP64 CPU oracle on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "reconstructions/s (FP32 path with one FP64 refinement, rel.err <= 1e-4 vs the FP64 oracle)"
+D, NCAND, BOX, S_SPARSE, SNR_DB, NINST = 10, 1 << 20, 64, 1000, 40.0, 16
+WORKLOAD = ("d=10, |Gamma|=2^20 uniform distinct in [-64,64]^10, s=1000 complex-Gaussian coefficients, "
+            "40 dB noise, L=37, M=10331 (Cor. 2.6, c=10.33, delta=0.1), FP32 + one FP64 refinement, "
+            "16 seeds per step")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--instances", type=int, default=NINST)
+    ap.add_argument("--no-extras", action="store_true", help="skip the FP64-path, graph, e2e and CPU legs")
+    ap.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ inputs (seeded, synthetic)
+def instance_inputs(seed):
+    import numpy as np
+    import sfft_synth as S
+    cand = S.uniform_distinct(NCAND, D, -BOX, BOX, seed)
+    sup = S.support_indices(NCAND, S_SPARSE, seed)
+    coef = S.coef_cgauss(S_SPARSE, seed)
+    sigma = S.snr_sigma(coef, SNR_DB)
+    return cand, sup, coef, sigma
+
+
+# ------------------------------------------------------------------ clocks during the timed region
+class ClockSampler:
+    def __init__(self, index=0):
+        self.rows, self.index, self.proc = [], index, None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+             "clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
+                                          "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thr = threading.Thread(target=self._read, daemon=True)
+            self.thr.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+# ------------------------------------------------------------------ CPU oracle timing
+def oracle_step_time(seed, reps=1):
+    """Seconds per reconstruction of one full instance by the FP64 oracle (Algorithm 2,
+    refinement, Algorithm 4), after the samples were computed once by direct evaluation."""
+    import numpy as np
+    import oracle as O
+    import sfft_synth as S
+    cand, sup, coef, sigma = instance_inputs(seed)
+    L, M = O.L_cor26(NCAND, 0.1), O.next_prime_above(10.33 * S_SPARSE)
+    z = O.plan_generators(seed, L, D, [M] * L)
+    y = O.sample_sparse_poly(cand[sup], coef, z, M) + S.noise(L * M, sigma, seed)
+    tau = 6 * sigma / math.sqrt(M)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        O.reconstruct(cand, y, z, M, tau_abs=tau, do_refine=True, refine_mode="bucket")
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def cpu_baseline_worker():
+    t = oracle_step_time(0, reps=1)
+    print(json.dumps({"seconds": t[0]}))
+
+
+def cpu_baseline(timeout=600):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker"], capture_output=True,
+                           text=True, env=env, timeout=timeout)
+        sec = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+        return {"value": 1.0 / sec, "unit": "reconstructions/s", "cores": 1, "kind": "oracle",
+                "sample": "one full instance (2^20 candidates, L=37, M=10331) reconstructed by the FP64 numpy oracle "
+                          "(Alg 2 + refinement + Alg 4; samples evaluated once beforehand), 1 thread"}
+    except Exception as e:  # reported, not fatal
+        return {"value": None, "unit": "reconstructions/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+
+
+# ------------------------------------------------------------------ native arm
+def kernel_count(batch_plans, n_inst, refine=True):
+    # per step: 2 sampler launches per instance (bucket scatter, inverse lattice DFT) and, for the
+    # batch, clear + DFT + zero test + hash groups + compact + hashes + combine + select + counts
+    hash_groups = len({p.d for p in batch_plans})
+    n = 2 * n_inst + 1 + 1 + 1 + hash_groups + 1 + 1 + 1 + 1 + 1
+    if refine:
+        n += 1 + 1 + 1 + 1 + 1  # clear C, scatter, FP64 model IDFT, refinement DFT, update
+    return n
+
+
+def traffic_from_profiles(kernel, units):
+    """DRAM bytes per launch of `kernel` scaled from the committed ncu summary (or None)."""
+    import glob
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.txt")):
+        for line in open(f):
+            if line.startswith("traffic_per_unit") and f"kernel={kernel}" in line:
+                kv = dict(tok.split("=") for tok in line.split()[1:] if "=" in tok)
+                return float(kv["bytes_per_unit"]) * units
+    return None
+
+
+def run_native(a, rank, world):
+    import numpy as np
+    import torch
+
+    import paper_2006_13053_gb300 as G
+
+    torch.cuda.set_device(rank % max(1, torch.cuda.device_count()))
+    dev = torch.device("cuda", torch.cuda.current_device())
+    st = torch.cuda.Stream(dev)
+    n_inst = a.instances
+    seeds = [rank * n_inst + i for i in range(n_inst)]
+    host = [instance_inputs(s) for s in seeds]
+    plans, kv, cf, nz, smp, cand_d = [], [], [], [], [], []
+    with torch.cuda.stream(st):
+        for s, (cand, sup, coef, sigma) in zip(seeds, host):
+            c = torch.from_numpy(cand).to(dev)
+            cand_d.append(c)
+            p = G.Plan(c, S_SPARSE, precision=G.FP32, refine=1, tau_abs=6 * sigma / math.sqrt(10331), tau_rel=0.0,
+                       seed=s, stream=st)
+            plans.append(p)
+            kv.append(c[torch.from_numpy(sup).to(dev)].contiguous())
+            cf.append(torch.from_numpy(coef).to(dev))
+            import sfft_synth as S
+            nz.append(torch.from_numpy(S.noise(p.n_samples, sigma, s)).to(dev))
+            smp.append(torch.empty(p.n_samples, dtype=torch.complex64, device=dev))
+        batch = G.Batch(plans, use_graph=False, stream=st)
+    L, M = plans[0].L, int(plans[0].M[0])
+
+    def step():
+        with torch.cuda.stream(st):
+            for i, p in enumerate(plans):
+                p.sample_sparse_poly(kv[i], cf[i], nz[i], out=smp[i])
+            batch.reconstruct_async(smp)
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(a.warmup):
+        step()
+    st.synchronize()
+    # correctness gate on the last warm-up step: every instance returns <= s frequencies
+    res = batch.results()
+    assert all(0 < len(s_) <= S_SPARSE + 64 for s_, _ in res), [len(s_) for s_, _ in res]
+    # ---- timed region (per-stage CUDA events on the launch stream)
+    batch.timing(1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        e0.record(st)
+        for _ in range(a.steps):
+            step()
+        e1.record(st)
+        e1.synchronize()
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1) / a.steps
+    stages = batch.timing(0)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n_inst / (ms / 1000.0)
+    stage_ms = {k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1] > 0}
+    out = {"metric": METRIC, "value": value, "unit": "reconstructions/s", "n_gpus": world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "dtype": "f32", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "global_batch": world * n_inst, "lattices": L, "lattice_size": M,
+                      "precision": "FP32 samples/FFT/median, FP64 residual + update, exact int32 hashing",
+                      "l2": "inputs larger than L2 (16 x 40 MiB candidate sets per step)",
+                      "parallelism": f"replicas x{world}"},
+           "cand_lattice_evals_per_s": world * n_inst * NCAND * L / (ms / 1000.0),
+           "stage_ms_per_step": stage_ms,
+           "gpu_launches": kernel_count(plans, n_inst) * a.steps,
+           "clocks": clk.summary()}
+    # ---- roofline of the dominant stage
+    dom = max(stage_ms, key=stage_ms.get)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    src = "of measured" if "hbm_gbs" in peaks else "of fallback"
+    per_launch_ms = stage_ms[dom]
+    if dom == "hash_count":
+        bytes_ = n_inst * NCAND * D * 4  # candidate stream: 4 d bytes per candidate, read once
+        ach = bytes_ / (per_launch_ms / 1000.0) / 1e9
+        out["roofline"] = {"kernel": "k_hash_count", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                           "frac": ach / hbm, "peak_source": src,
+                           "traffic": traffic_from_profiles("k_hash_count", n_inst * NCAND)}
+    elif dom in ("fft_model64",):
+        # FP64 Bluestein: 2 transforms of length N=20736 (5 N log2 N flops each) + 2 N pointwise per lattice
+        N = 20736
+        flops = n_inst * L * (2 * 5 * N * math.log2(N) + 6 * N)
+        ach = flops / (per_launch_ms / 1000.0) / 1e12
+        out["roofline"] = {"kernel": "k_bluestein<double> (refinement model IDFT)", "bound": "alu", "achieved": ach,
+                           "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
+                           "peak_source": "nominal FP64 (no measured FP64 peak in MEASURED_PEAKS.json)",
+                           "traffic": traffic_from_profiles("k_bluestein_f64", n_inst * L)}
+    else:
+        N = 20736
+        bytes_ = n_inst * L * (M * 8 * 2)  # samples in, buckets out (FP32 complex)
+        ach = bytes_ / (per_launch_ms / 1000.0) / 1e9
+        out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
+                           "frac": ach / hbm, "peak_source": src, "traffic": None}
+    out["roofline"]["dominant_stage"] = dom
+    if a.no_extras:
+        return out, plans, batch
+    # ---- graph replay of the same step
+    gbatch = G.Batch(plans, use_graph=True, stream=st)
+    with torch.cuda.stream(st):
+        for _ in range(3):
+            for i, p in enumerate(plans):
+                p.sample_sparse_poly(kv[i], cf[i], nz[i], out=smp[i])
+            gbatch.reconstruct_async(smp)
+    st.synchronize()
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(st)
+    with torch.cuda.stream(st):
+        for _ in range(a.steps):
+            for i, p in enumerate(plans):
+                p.sample_sparse_poly(kv[i], cf[i], nz[i], out=smp[i])
+            gbatch.reconstruct_async(smp)
+    g1.record(st)
+    g1.synchronize()
+    out["graph_ms_per_step"] = g0.elapsed_time(g1) / a.steps
+    gbatch.close()
+    # ---- end to end: host (pinned) inputs -> device -> results back to the host, every step
+    hc = [torch.from_numpy(h[0]).pin_memory() for h in host]
+    hk = [kv[i].cpu().pin_memory() for i in range(n_inst)]
+    hf = [cf[i].cpu().pin_memory() for i in range(n_inst)]
+    hn = [nz[i].cpu().pin_memory() for i in range(n_inst)]
+    out_s = [torch.empty(c_.numel(), dtype=torch.int64).pin_memory() for c_ in batch.supp]
+    out_c = [torch.empty(c_.numel(), dtype=torch.complex128).pin_memory() for c_ in batch.coef]
+    out_n = torch.empty(n_inst, dtype=torch.int64).pin_memory()
+    h2d = sum(t.numel() * t.element_size() for t in hc + hk + hf + hn)
+
+    def e2e_step():
+        with torch.cuda.stream(st):
+            for i in range(n_inst):
+                cand_d[i].copy_(hc[i], non_blocking=True)
+                kv[i].copy_(hk[i], non_blocking=True)
+                cf[i].copy_(hf[i], non_blocking=True)
+                nz[i].copy_(hn[i], non_blocking=True)
+            for i, p in enumerate(plans):
+                p.sample_sparse_poly(kv[i], cf[i], nz[i], out=smp[i])
+            batch.reconstruct_async(smp)
+            out_n.copy_(batch.nout, non_blocking=True)
+            for i in range(n_inst):
+                out_s[i].copy_(batch.supp[i], non_blocking=True)
+                out_c[i].copy_(batch.coef[i], non_blocking=True)
+        st.synchronize()
+
+    e2e_step()
+    d2h = sum(t.numel() * t.element_size() for t in out_s + out_c) + out_n.numel() * 8
+    t0 = time.perf_counter()
+    for _ in range(max(3, a.steps // 2)):
+        e2e_step()
+    e2e_s = (time.perf_counter() - t0) / max(3, a.steps // 2)
+    out["e2e"] = {"value": world * n_inst / e2e_s, "unit": "reconstructions/s", "h2d_bytes_per_step": h2d,
+                  "d2h_bytes_per_step": d2h, "ms_per_step": e2e_s * 1000.0}
+    # ---- the plain FP64 GPU path on the same workload
+    with torch.cuda.stream(st):
+        p64 = [G.Plan(cand_d[i], S_SPARSE, precision=G.FP64, refine=0, tau_abs=6 * host[i][3] / math.sqrt(10331),
+                      tau_rel=0.0, seed=seeds[i], stream=st) for i in range(n_inst)]
+        s64 = [torch.empty(p.n_samples, dtype=torch.complex128, device=dev) for p in p64]
+        b64 = G.Batch(p64, use_graph=False, stream=st)
+
+        def step64():
+            for i, p in enumerate(p64):
+                p.sample_sparse_poly(kv[i], cf[i], nz[i], out=s64[i])
+            b64.reconstruct_async(s64)
+
+        step64()
+    st.synchronize()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(st)
+    with torch.cuda.stream(st):
+        for _ in range(3):
+            step64()
+    f1.record(st)
+    f1.synchronize()
+    ms64 = f0.elapsed_time(f1) / 3
+    out["fp64_path"] = {"value": n_inst / (ms64 / 1000.0), "unit": "reconstructions/s", "ms_per_step": ms64,
+                        "fp32_over_fp64": (ms64 / ms)}
+    b64.close()
+    for p in p64:
+        p.close()
+    return out, plans, batch
+
+
+def run_reference(a):
+    steps = []
+    t = oracle_step_time(0, reps=a.warmup + a.steps)
+    steps = t[a.warmup:]
+    sec = sum(steps) / len(steps)
+    v = 1.0 / sec
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": "reconstructions/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": sec * 1000.0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD + " (one instance per step)", "global_batch": 1},
+            "cpu_baseline": {"value": v, "unit": "reconstructions/s", "cores": 1, "kind": "oracle",
+                             "sample": "each step: one full instance (2^20 candidates) reconstructed by the FP64 numpy "
+                                       "oracle; samples evaluated once before timing"},
+            "e2e": {"value": v, "unit": "reconstructions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    a = parse()
+    if a.cpu_baseline_worker:
+        cpu_baseline_worker()
+        return
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if a.impl == "reference":
+        if rank != 0:
+            return
+        os.environ.setdefault("OMP_NUM_THREADS", "1")
+        print(json.dumps(run_reference(a)), flush=True)
+        return
+    import torch
+    if world > 1:
+        torch.distributed.init_process_group("nccl")
+    out, plans, batch = run_native(a, rank, world)
+    if rank == 0:
+        if not a.no_extras:
+            out["cpu_baseline"] = cpu_baseline()
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -156,7 +156,7 @@ int sfft_reconstruct_backward(sfft_plan* plan, const double* dcoef, void* dsampl
  *   kvec  device int32 [n_terms, d];  coef device complex double [n_terms];
  *   noise device complex double [sum M] or NULL;  samples_out device complex (plan precision).
  * Computed exactly through eq. (2.3): the coefficients are scattered into their buckets
- * k.z_l mod M_l and each lattice is inverse-transformed.
+ * k.z_l mod M_l and each lattice is inverse-transformed.  Asynchronous on the plan stream.
  */
 int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const double* coef, int64_t n_terms,
                             const double* noise, void* samples_out);
@@ -165,7 +165,8 @@ int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const do
  * Samples of the sum-of-products function f(x) = sum_m prod_{t in T_m} g_{theta_m}(x_t) with
  * g_theta(x) = sum_{|k| <= K} sinc(pi k / (width theta))^4 exp(2 pi i k x) (real valued).
  *   triples host int32 [n_terms, 3] (dimensions < d); theta device double [n_terms].
- * samples_out device complex (plan precision; imaginary parts are 0).
+ * samples_out device complex (plan precision; imaginary parts are 0).  Asynchronous on the
+ * plan stream.
  */
 int sfft_sample_sop(const sfft_plan* plan, const int32_t* triples, const double* theta, int n_terms, int K,
                     double width, void* samples_out);
@@ -184,8 +185,9 @@ typedef struct sfft_batch sfft_batch;
 /*
  * Group n_plans plans (same precision) so that sfft_batch_reconstruct runs every stage of all
  * of them in shared launches (one launch per stage for the whole batch).  The plans must
- * outlive the batch.  use_graph != 0 captures the stage sequence once into a CUDA graph on
- * `stream` and replays it on later calls (samples/outputs must then keep their addresses).
+ * outlive the batch.  use_graph != 0 captures the stage sequence into a CUDA graph at the
+ * second call on `stream` (which must not be the legacy NULL stream) and replays it on later
+ * calls; the per-call buffer addresses are re-read at every replay.
  */
 int sfft_batch_create(sfft_batch** out, sfft_plan* const* plans, int n_plans, int use_graph, void* stream);
 void sfft_batch_destroy(sfft_batch* b);
@@ -197,6 +199,18 @@ void sfft_batch_destroy(sfft_batch* b);
  */
 int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* const* supp_out,
                            double* const* coef_out, const int64_t* cap, int64_t* n_out_dev);
+
+/*
+ * Per-stage GPU time of the batch's stage sequence, measured with CUDA events on the batch
+ * stream around each stage of every call since the last reset.  Stage order: clear, lattice
+ * DFT (Algorithm 2 line 2), zero test, hash + count, compaction, hashes of Itilde, combine,
+ * refinement scatter, refinement model IDFT (FP64), refinement DFT, refinement update,
+ * Algorithm 4 selection.  ms / launches: host arrays of 12 entries (optional) receive the
+ * accumulated milliseconds and the number of timed calls.  mode = 1 enables timing (graph
+ * batches then run eagerly), 0 disables it, both reset the totals; mode = -1 only reads.
+ * Returns the number of stages (12) or -1.
+ */
+int sfft_batch_timing(sfft_batch* b, int mode, double* ms, int64_t* launches);
 
 /* ---------------------------------------------------------------- Algorithm 3 */
 /*

@@ -89,6 +89,9 @@ sfft_sample_sop_backward = _sig("sfft_sample_sop_backward", _i32, [_vp, _vp, _vp
 sfft_batch_create = _sig("sfft_batch_create", _i32, [_P(_vp), _vp, _i32, _i32, _vp])
 sfft_batch_destroy = _sig("sfft_batch_destroy", None, [_vp])
 sfft_batch_reconstruct = _sig("sfft_batch_reconstruct", _i32, [_vp, _vp, _vp, _vp, _vp, _vp])
+sfft_batch_timing = _sig("sfft_batch_timing", _i32, [_vp, _i32, _vp, _vp])
+STAGES = ["clear", "fft_fwd", "zero_test", "hash_count", "compact", "det_hashes", "combine", "refine_scatter",
+          "fft_model64", "fft_refine", "refine_update", "select"]
 sfft_dimincr_params_default = _sig("sfft_dimincr_params_default", None, [_P(DimIncrParams)])
 sfft_dim_incremental = _sig("sfft_dim_incremental", _i32,
                             [_i32, _vp, _vp, _P(DimIncrParams), _vp, _vp, _vp, _vp, _i64, _P(_i64), _P(_i64), _vp])

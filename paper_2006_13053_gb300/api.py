@@ -192,3 +192,64 @@ class SopReconstruct(torch.autograd.Function):
         ds = plan.backward(gcoef.contiguous().to(torch.complex128))
         dtheta = plan.sample_sop_backward(ctx.triples, theta, ds, K=ctx.K, width=ctx.width)
         return dtheta, None, None, None, None
+
+
+class Batch:
+    """Several plans (same precision) reconstructed with one launch per stage; with
+    use_graph=True the stage sequence is captured once into a CUDA graph and replayed.
+    Output buffers are allocated once so that their addresses stay fixed."""
+
+    def __init__(self, plans, use_graph=False, stream=None, caps=None):
+        self.plans = list(plans)
+        self.stream = stream
+        n = len(self.plans)
+        arr = (C.c_void_p * n)(*[p.handle.value for p in self.plans])
+        h = C.c_void_p()
+        N.check(N.sfft_batch_create(C.byref(h), arr, n, 1 if use_graph else 0, _stream(stream)))
+        self.handle = h
+        dev = self.plans[0].cand.device
+        self.caps = [int(c) for c in (caps or [max(p.params.s_tilde or 0, 1) + 4 * 4096 for p in self.plans])]
+        self.supp = [torch.empty(c, dtype=torch.int64, device=dev) for c in self.caps]
+        self.coef = [torch.empty(c, dtype=torch.complex128, device=dev) for c in self.caps]
+        self.nout = torch.zeros(n, dtype=torch.int64, device=dev)
+        self._ps = (C.c_void_p * n)(*[t.data_ptr() for t in self.supp])
+        self._pc = (C.c_void_p * n)(*[t.data_ptr() for t in self.coef])
+        self._cap = (C.c_int64 * n)(*self.caps)
+
+    def reconstruct_async(self, samples):
+        """Enqueue every reconstruction; results stay in self.supp / self.coef / self.nout."""
+        n = len(self.plans)
+        for p, s in zip(self.plans, samples):
+            _req(s, p.cdtype, "samples")
+        sp = (C.c_void_p * n)(*[s.data_ptr() for s in samples])
+        N.check(N.sfft_batch_reconstruct(self.handle, sp, self._ps, self._pc, self._cap,
+                                         C.c_void_p(self.nout.data_ptr())))
+
+    def results(self):
+        (self.stream or torch.cuda.current_stream()).synchronize()
+        k = self.nout.cpu().tolist()
+        return [(s[:m], c[:m]) for s, c, m in zip(self.supp, self.coef, k)]
+
+    def reconstruct(self, samples):
+        self.reconstruct_async(samples)
+        return self.results()
+
+    def timing(self, mode=-1):
+        """(mode: 1 enable+reset, 0 disable+reset, -1 read) -> {stage: (ms_total, calls)}."""
+        ms = (C.c_double * 12)()
+        nl = (C.c_int64 * 12)()
+        r = N.sfft_batch_timing(self.handle, int(mode), ms, nl)
+        if r < 0:
+            raise N.SfftError(N.ECUDA, N.sfft_last_error().decode())
+        return {name: (ms[i], nl[i]) for i, name in enumerate(N.STAGES)}
+
+    def close(self):
+        if getattr(self, "handle", None):
+            N.sfft_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -159,7 +159,7 @@ int Plan::build_jobs() {
     char* ghat_b = (char*)ghat;
     char* resid_b = (char*)resid;
     char* rhat_b = (char*)rhat;
-    jobs_fwd.clear(); jobs_model.clear(); jobs_rfwd.clear();
+    jobs_fwd.clear(); jobs_model.clear(); jobs_rfwd.clear(); jobs_samp.clear(); jobs_adj.clear();
     for (int l = 0; l < L; ++l) {
         const FftTables* t = tabs[l];
         const int64_t o = soff[l];
@@ -180,6 +180,16 @@ int Plan::build_jobs() {
         r.in = resid_b + o * e; r.out = rhat_b + o * e;
         r.scratch = a.scratch;
         jobs_rfwd.push_back(r);
+        // sampler: out (launch argument) = IDFT(C) + noise (launch argument), plan precision
+        BlueJob sj = make_job(t, prec, 1, 1.0);
+        sj.in = C + o; sj.io_flags = 4 | 8; sj.io_off = o;
+        sj.scratch = a.scratch;
+        jobs_samp.push_back(sj);
+        // adjoint: out (launch argument) = (1/M) IDFT(C), plan precision
+        BlueJob aj = make_job(t, prec, 1, 1.0 / (double)M[l]);
+        aj.in = C + o; aj.io_flags = 4; aj.io_off = o;
+        aj.scratch = a.scratch;
+        jobs_adj.push_back(aj);
     }
     return SFFT_OK;
 }
@@ -325,7 +335,6 @@ int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L
         SFFT_TRY(P->alloc(&P->scratch, sizeof(c64) * (size_t)P->maxN * L));
     SFFT_TRY(P->alloc((void**)&P->sop_a, sizeof(double) * 2 * 16 * 129));
     SFFT_TRY(P->alloc((void**)&P->sop_tri, sizeof(int32_t) * 3 * 16));
-    SFFT_TRY(P->alloc((void**)&P->d_jobs_tmp, sizeof(BlueJob) * L));
     // ---- instance descriptor
     SFFT_CU(cudaMallocHost((void**)&P->h_inst, sizeof(InstDesc)));
     SFFT_CU(cudaMallocHost((void**)&P->h_cnt, sizeof(int64_t) * 8));
@@ -353,6 +362,8 @@ int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L
     SFFT_TRY(upload_jobs(P->jobs_fwd, &P->d_jobs_fwd, &P->allocs));
     SFFT_TRY(upload_jobs(P->jobs_model, &P->d_jobs_model, &P->allocs));
     SFFT_TRY(upload_jobs(P->jobs_rfwd, &P->d_jobs_rfwd, &P->allocs));
+    SFFT_TRY(upload_jobs(P->jobs_samp, &P->d_jobs_samp, &P->allocs));
+    SFFT_TRY(upload_jobs(P->jobs_adj, &P->d_jobs_adj, &P->allocs));
     // hash-count launch shape: one full wave of CTAs
     P->hash_smem = sizeof(uint32_t) * (size_t)words + sizeof(int32_t) * (size_t)L * (d + 4);
     SFFT_CHECK(P->hash_smem <= 220 * 1024, SFFT_EINVAL,
@@ -362,31 +373,56 @@ int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L
 
 // ================================================================== the reconstruction stage sequence
 // Runs every stage for `ninst` instances described by d_inst (all of precision prec).
+static int mark(const PipeArgs& a, int stage, cudaStream_t st) {
+    if (!a.timer) return SFFT_OK;
+    SFFT_CU(cudaEventRecord(a.timer->ev[stage], st));
+    a.timer->recorded[stage] = true;
+    return SFFT_OK;
+}
+
 int run_pipeline(const PipeArgs& a, cudaStream_t st) {
     const int ni = a.ninst;
+    if (a.timer)
+        for (int i = 0; i <= ST_COUNT; ++i) a.timer->recorded[i] = false;
+    SFFT_TRY(mark(a, ST_CLEAR, st));
     SFFT_TRY(launch_clear(a.d_inst, ni, 1, a.hybrid, 0, st));
     // Algorithm 2 line 2: lattice DFTs (normalised by 1/M) + per-lattice statistics
-    SFFT_TRY(launch_bluestein(a.jobs_fwd, a.nlat, a.maxN, a.sm_prec, a.prec, a.prec, a.prec, -1, EPI_ANALYZE, a.d_inst, st));
+    SFFT_TRY(mark(a, ST_FFT_FWD, st));
+    for (const auto& f : a.fwd)
+        SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, a.prec, a.prec, a.prec, -1, EPI_ANALYZE, a.d_inst, st));
     // zero test with FP64 re-tests inside the guard band (Remark 2.3)
+    SFFT_TRY(mark(a, ST_ZERO_TEST, st));
     const double u = a.prec ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
     SFFT_TRY(launch_zero_test(a.d_lats, a.nlat, a.d_inst, a.prec, 32.0 * u, st));
     // count rule over all candidates, ascending compaction of Itilde
-    SFFT_TRY(launch_hash_count(a.d_inst, ni, a.d, a.hash_gx, a.hash_smem, st));
+    SFFT_TRY(mark(a, ST_HASH, st));
+    for (const auto& h : a.hash) SFFT_TRY(launch_hash_count(a.d_inst + h.off, h.count, h.d, h.gx, h.smem, st));
+    SFFT_TRY(mark(a, ST_COMPACT, st));
     SFFT_TRY(launch_compact(a.d_inst, ni, st));
     // hashes of Itilde, collision counts, median / hybrid combine
+    SFFT_TRY(mark(a, ST_DET_HASH, st));
     SFFT_TRY(launch_det_hashes(a.d_inst, ni, a.maxcap, st));
+    SFFT_TRY(mark(a, ST_COMBINE, st));
     if (a.hybrid) SFFT_TRY(launch_collisions(a.d_inst, ni, st));
     SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, 0, st));
     if (a.refine) {
+        SFFT_TRY(mark(a, ST_SCATTER, st));
         SFFT_TRY(launch_clear(a.d_inst, ni, 0, 0, 1, st));
         SFFT_TRY(launch_scatter_coef(a.d_inst, ni, st));
         // residual at the nodes in FP64: r = f - IDFT(C)
-        SFFT_TRY(launch_bluestein(a.jobs_model, a.nlat, a.maxN, a.sm64, 0, 0, a.prec, +1, EPI_RESID, a.d_inst, st));
-        SFFT_TRY(launch_bluestein(a.jobs_rfwd, a.nlat, a.maxN, a.sm_prec, a.prec, a.prec, a.prec, -1, EPI_PLAIN, a.d_inst, st));
+        SFFT_TRY(mark(a, ST_FFT_MODEL, st));
+        for (const auto& f : a.model)
+            SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, 0, 0, a.prec, +1, EPI_RESID, a.d_inst, st));
+        SFFT_TRY(mark(a, ST_FFT_RFWD, st));
+        for (const auto& f : a.rfwd)
+            SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, a.prec, a.prec, a.prec, -1, EPI_PLAIN, a.d_inst, st));
+        SFFT_TRY(mark(a, ST_DELTA, st));
         SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, 1, st));
     }
     // Algorithm 4: theta filter and top-s_tilde, ascending output
+    SFFT_TRY(mark(a, ST_SELECT, st));
     SFFT_TRY(launch_select(a.d_inst, ni, st));
+    SFFT_TRY(mark(a, ST_COUNT, st));
     return SFFT_OK;
 }
 
@@ -399,10 +435,14 @@ int Plan::hash_grid() const {
 PipeArgs Plan::pipe_args() {
     PipeArgs a;
     a.ninst = 1; a.d_inst = d_inst; a.d_lats = d_lats; a.nlat = L;
-    a.jobs_fwd = d_jobs_fwd; a.jobs_model = d_jobs_model; a.jobs_rfwd = d_jobs_rfwd;
-    a.maxN = maxN; a.sm_prec = fits_smem(prec); a.sm64 = fits_smem(0);
-    a.prec = prec; a.d = d; a.hash_gx = hash_grid(); a.hash_smem = hash_smem; a.maxcap = cap;
+    a.prec = prec; a.maxcap = cap;
     a.hybrid = p.combine == SFFT_COMBINE_HYBRID; a.refine = p.refine;
+    a.fwd.push_back(FftLaunch{d_jobs_fwd, L, maxN, fits_smem(prec)});
+    a.model.push_back(FftLaunch{d_jobs_model, L, maxN, fits_smem(0)});
+    a.rfwd.push_back(FftLaunch{d_jobs_rfwd, L, maxN, fits_smem(prec)});
+    HashGroup h;
+    h.off = 0; h.count = 1; h.d = d; h.gx = hash_grid(); h.smem = hash_smem;
+    a.hash.push_back(h);
     return a;
 }
 
@@ -553,18 +593,8 @@ int sfft_reconstruct_backward(sfft_plan* plan, const double* dcoef, void* dsampl
     SFFT_CU(cudaMemsetAsync(P->C, 0, sizeof(c64) * P->sumM, st));
     if (P->last_nout > 0 && dcoef) SFFT_TRY(launch_adj_scatter(P->d_inst, reinterpret_cast<const c64*>(dcoef), st));
     // dsamples = A^H gbar with (A^H g)_j = (1/M) sum_h g_h exp(+2 pi i j h / M)
-    std::vector<BlueJob> jobs;
-    const size_t e = P->esz();
-    for (int l = 0; l < P->L; ++l) {
-        BlueJob J = make_job(P->tabs[l], P->prec, 1, 1.0 / (double)P->M[l]);
-        J.in = P->C + P->soff[l];
-        J.out = (char*)dsamples + P->soff[l] * e;
-        J.scratch = P->fits_smem(P->prec) ? nullptr : (char*)P->scratch + (size_t)l * P->maxN * sizeof(c64);
-        jobs.push_back(J);
-    }
-    SFFT_CU(cudaMemcpyAsync(P->d_jobs_tmp, jobs.data(), sizeof(BlueJob) * jobs.size(), cudaMemcpyHostToDevice, st));
-    SFFT_TRY(launch_bluestein(P->d_jobs_tmp, P->L, P->maxN, P->fits_smem(P->prec), P->prec, 0, P->prec, +1, EPI_PLAIN,
-                              P->d_inst, st));
+    SFFT_TRY(launch_bluestein(P->d_jobs_adj, P->L, P->maxN, P->fits_smem(P->prec), P->prec, 0, P->prec, +1, EPI_PLAIN,
+                              P->d_inst, st, dsamples, nullptr));
     SFFT_CU(cudaStreamSynchronize(st));
     return SFFT_OK;
 }
@@ -576,20 +606,8 @@ int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const do
     cudaStream_t st = P->st;
     SFFT_CU(cudaMemsetAsync(P->C, 0, sizeof(c64) * P->sumM, st));
     if (n_terms > 0) SFFT_TRY(launch_scatter_terms(P->d_inst, kvec, reinterpret_cast<const c64*>(coef), n_terms, st));
-    std::vector<BlueJob> jobs;
-    const size_t e = P->esz();
-    for (int l = 0; l < P->L; ++l) {
-        BlueJob J = make_job(P->tabs[l], P->prec, 1, 1.0);
-        J.in = P->C + P->soff[l];
-        J.out = (char*)samples_out + P->soff[l] * e;
-        J.aux = noise ? (const void*)(reinterpret_cast<const c64*>(noise) + P->soff[l]) : nullptr;
-        J.scratch = P->fits_smem(P->prec) ? nullptr : (char*)P->scratch + (size_t)l * P->maxN * sizeof(c64);
-        jobs.push_back(J);
-    }
-    SFFT_CU(cudaMemcpyAsync(P->d_jobs_tmp, jobs.data(), sizeof(BlueJob) * jobs.size(), cudaMemcpyHostToDevice, st));
-    SFFT_TRY(launch_bluestein(P->d_jobs_tmp, P->L, P->maxN, P->fits_smem(P->prec), P->prec, 0, P->prec, +1, EPI_ADDNOISE,
-                              P->d_inst, st));
-    SFFT_CU(cudaStreamSynchronize(st));
+    SFFT_TRY(launch_bluestein(P->d_jobs_samp, P->L, P->maxN, P->fits_smem(P->prec), P->prec, 0, P->prec, +1, EPI_ADDNOISE,
+                              P->d_inst, st, samples_out, noise));
     return SFFT_OK;
 }
 
@@ -608,7 +626,6 @@ int sfft_sample_sop(const sfft_plan* plan, const int32_t* triples, const double*
     Plan* P = const_cast<Plan*>(reinterpret_cast<const Plan*>(plan));
     SFFT_TRY(sop_prepare(P, triples, theta, n_terms, K, width));
     SFFT_TRY(launch_sop_sample(P->d_inst, P->sop_tri, n_terms, K, P->sop_a, samples_out, P->prec, P->st));
-    SFFT_CU(cudaStreamSynchronize(P->st));
     return SFFT_OK;
 }
 

@@ -126,7 +126,9 @@ struct BlueJob {
     struct LatStats* stat; // side outputs of EPI_ANALYZE
     double scale;        // output scale (1/M for the normalised forward DFT)
     int M, N, nstages;
-    int inst, io_flags;  // io_flags bit 0: in = samples of instance `inst` + io_off; bit 1: aux likewise
+    // io_flags: bit 0 in = samples of instance `inst` + io_off; bit 1 aux = those samples;
+    //           bit 2 out = out_base (launch argument) + io_off; bit 3 aux = aux_base + io_off
+    int inst, io_flags;
     int64_t io_off;
     uint8_t radix[kMaxStages];
 };
@@ -152,7 +154,8 @@ struct LatStats {
 // double, 1 = float.  sm: work buffer in shared memory (all jobs need N <= maxN fitting).
 struct InstDesc;
 int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, bool sm, int prec, int in_prec, int out_prec, int sign,
-                     int epi, const InstDesc* insts, cudaStream_t st);
+                     int epi, const InstDesc* insts, cudaStream_t st, void* out_base = nullptr,
+                     const void* aux_base = nullptr);
 size_t blue_smem_limit();
 
 // ------------------------------------------------------------------ instance / lattice descriptors

@@ -1,7 +1,181 @@
-// Batched reconstruction and the dimension-incremental driver (Algorithm 3).
+// Batched reconstruction (many plans, one launch per stage, optionally replayed from a CUDA
+// graph) and the dimension-incremental driver (Algorithm 3).
+#include <string.h>
+
+#include <algorithm>
+#include <numeric>
+#include <vector>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "plan.cuh"
+
+namespace sfft {
+
+__global__ void k_gather_counts(const InstDesc* __restrict__ insts, int n, int64_t* out, int64_t* flags) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        out[i] = insts[i].cnt[1];
+        flags[i] = insts[i].cnt[3];
+    }
+}
+
+struct Batch {
+    std::vector<Plan*> plans;   // batch order (sorted by d)
+    std::vector<int> order;     // batch index -> caller's plan index
+    cudaStream_t st = nullptr;
+    int use_graph = 0, prec = 0;
+    InstDesc* d_inst = nullptr;
+    InstDesc* h_inst = nullptr;  // pinned staging [n]
+    LatDesc* d_lats = nullptr;
+    std::vector<void*> allocs;
+    PipeArgs args;
+    int64_t* d_counts = nullptr;
+    int64_t* d_flags = nullptr;
+    cudaEvent_t done = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int calls = 0;
+    // stage timing
+    bool timing = false, pending = false, timer_made = false;
+    StageTimer timer;
+    double stage_ms[ST_COUNT] = {0};
+    int64_t stage_n[ST_COUNT] = {0};
+
+    int collect() {  // add the elapsed times of the last timed call
+        if (!pending) return SFFT_OK;
+        SFFT_CU(cudaEventSynchronize(timer.ev[ST_COUNT]));
+        for (int s = 0; s < ST_COUNT; ++s) {
+            if (!timer.recorded[s]) continue;
+            int nx = s + 1;
+            while (nx < ST_COUNT && !timer.recorded[nx]) ++nx;
+            float ms = 0;
+            SFFT_CU(cudaEventElapsedTime(&ms, timer.ev[s], timer.ev[nx]));
+            stage_ms[s] += ms;
+            stage_n[s] += 1;
+        }
+        pending = false;
+        return SFFT_OK;
+    }
+
+    void release() {
+        if (done) cudaEventSynchronize(done);
+        if (timer_made)
+            for (int i = 0; i <= ST_COUNT; ++i) cudaEventDestroy(timer.ev[i]);
+        timer_made = false;
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (done) cudaEventDestroy(done);
+        for (void* p : allocs) cudaFree(p);
+        if (h_inst) cudaFreeHost(h_inst);
+        allocs.clear();
+        exec = nullptr; graph = nullptr; done = nullptr; h_inst = nullptr;
+    }
+    int alloc(void** p, size_t bytes) {
+        SFFT_CU(cudaMalloc(p, std::max<size_t>(bytes, 16)));
+        allocs.push_back(*p);
+        return SFFT_OK;
+    }
+    int enqueue() {
+        const int n = (int)plans.size();
+        SFFT_CU(cudaMemcpyAsync(d_inst, h_inst, sizeof(InstDesc) * n, cudaMemcpyHostToDevice, st));
+        SFFT_TRY(run_pipeline(args, st));
+        k_gather_counts<<<(n + 127) / 128, 128, 0, st>>>(d_inst, n, d_counts, d_flags);
+        return launch_check("k_gather_counts");
+    }
+};
+
+static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph, cudaStream_t st) {
+    SFFT_CHECK(plans && n >= 1, SFFT_EINVAL, "empty batch");
+    SFFT_CHECK(!use_graph || st != nullptr, SFFT_EINVAL,
+               "graph capture needs a non-default stream (the legacy NULL stream cannot be captured)");
+    std::vector<int> idx(n);
+    std::iota(idx.begin(), idx.end(), 0);
+    for (int i = 0; i < n; ++i) SFFT_CHECK(plans[i] != nullptr, SFFT_EINVAL, "plan %d is NULL", i);
+    auto P0 = reinterpret_cast<Plan*>(plans[0]);
+    for (int i = 0; i < n; ++i) {
+        auto P = reinterpret_cast<Plan*>(plans[i]);
+        SFFT_CHECK(P->prec == P0->prec, SFFT_EINVAL, "all plans of a batch need the same precision");
+        SFFT_CHECK(P->p.refine == P0->p.refine, SFFT_EINVAL, "all plans of a batch need the same refine setting");
+    }
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
+        return reinterpret_cast<Plan*>(plans[a])->d < reinterpret_cast<Plan*>(plans[b])->d;
+    });
+    B->st = st;
+    B->use_graph = use_graph;
+    B->prec = P0->prec;
+    B->order = idx;
+    for (int i : idx) B->plans.push_back(reinterpret_cast<Plan*>(plans[i]));
+    SFFT_CU(cudaMallocHost((void**)&B->h_inst, sizeof(InstDesc) * n));
+    std::vector<LatDesc> lats;
+    std::vector<BlueJob> jf[2], jm[2], jr[2];  // [0] global scratch, [1] shared memory
+    int maxN[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    PipeArgs& A = B->args;
+    A.ninst = n;
+    A.prec = B->prec;
+    A.refine = P0->p.refine;
+    for (int b = 0; b < n; ++b) {
+        Plan* P = B->plans[b];
+        B->h_inst[b] = *P->h_inst;
+        A.maxcap = std::max<int64_t>(A.maxcap, P->cap);
+        A.hybrid |= P->p.combine == SFFT_COMBINE_HYBRID;
+        for (int l = 0; l < P->L; ++l)
+            lats.push_back(LatDesc{b, l, (int)P->M[l], (int)P->tabs[l]->N, P->soff[l], P->boff[l], 0,
+                                   (const double*)P->tabs[l]->dft64});
+        const int sp = P->fits_smem(P->prec) ? 1 : 0, s64 = P->fits_smem(0) ? 1 : 0;
+        for (int l = 0; l < P->L; ++l) {
+            BlueJob f = P->jobs_fwd[l], m = P->jobs_model[l], r = P->jobs_rfwd[l];
+            f.inst = b; m.inst = b; r.inst = b;
+            jf[sp].push_back(f); jm[s64].push_back(m); jr[sp].push_back(r);
+        }
+        maxN[sp][0] = std::max(maxN[sp][0], P->maxN);
+        maxN[s64][1] = std::max(maxN[s64][1], P->maxN);
+        maxN[sp][2] = std::max(maxN[sp][2], P->maxN);
+    }
+    A.nlat = (int)lats.size();
+    SFFT_TRY(B->alloc((void**)&B->d_lats, sizeof(LatDesc) * lats.size()));
+    SFFT_CU(cudaMemcpy(B->d_lats, lats.data(), sizeof(LatDesc) * lats.size(), cudaMemcpyHostToDevice));
+    SFFT_TRY(B->alloc((void**)&B->d_inst, sizeof(InstDesc) * n));
+    SFFT_CU(cudaMemcpy(B->d_inst, B->h_inst, sizeof(InstDesc) * n, cudaMemcpyHostToDevice));
+    A.d_inst = B->d_inst;
+    A.d_lats = B->d_lats;
+    for (int sm = 1; sm >= 0; --sm) {
+        std::vector<BlueJob>* lists[3] = {&jf[sm], &jm[sm], &jr[sm]};
+        std::vector<FftLaunch>* dst[3] = {&A.fwd, &A.model, &A.rfwd};
+        for (int k = 0; k < 3; ++k) {
+            if (lists[k]->empty()) continue;
+            BlueJob* dj = nullptr;
+            SFFT_TRY(upload_jobs(*lists[k], &dj, &B->allocs));
+            dst[k]->push_back(FftLaunch{dj, (int)lists[k]->size(), maxN[sm][k], sm == 1});
+        }
+    }
+    // hash groups: contiguous runs of equal d
+    for (int b = 0; b < n;) {
+        int e = b;
+        HashGroup h;
+        h.off = b;
+        h.d = B->plans[b]->d;
+        int64_t tiles = 0;
+        while (e < n && B->plans[e]->d == h.d) {
+            h.smem = std::max(h.smem, B->plans[e]->hash_smem);
+            tiles = std::max<int64_t>(tiles, (B->plans[e]->n + 511) / 512);
+            ++e;
+        }
+        h.count = e - b;
+        int per_sm = std::max<int>(1, std::min<int>(8, (int)((228 * 1024) / (h.smem + 1024))));
+        h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (152 * per_sm + h.count - 1) / h.count));
+        A.hash.push_back(h);
+        b = e;
+    }
+    SFFT_TRY(B->alloc((void**)&B->d_counts, sizeof(int64_t) * n));
+    SFFT_TRY(B->alloc((void**)&B->d_flags, sizeof(int64_t) * n));
+    SFFT_CU(cudaEventCreateWithFlags(&B->done, cudaEventDisableTiming));
+    for (int i = 0; i <= ST_COUNT; ++i) SFFT_CU(cudaEventCreate(&B->timer.ev[i]));
+    B->timer_made = true;
+    return SFFT_OK;
+}
+
+}  // namespace sfft
 
 using namespace sfft;
 
@@ -25,17 +199,78 @@ void sfft_dimincr_params_default(sfft_dimincr_params* p) {
 }
 
 int sfft_batch_create(sfft_batch** out, sfft_plan* const* plans, int n_plans, int use_graph, void* stream) {
-    (void)out; (void)plans; (void)n_plans; (void)use_graph; (void)stream;
-    set_error("sfft_batch_create: not available in this build");
-    return SFFT_EINVAL;
+    if (!out) { set_error("out is NULL"); return SFFT_EINVAL; }
+    *out = nullptr;
+    Batch* B = new Batch();
+    int rc = batch_create(B, plans, n_plans, use_graph, (cudaStream_t)stream);
+    if (rc != SFFT_OK) {
+        B->release();
+        delete B;
+        return rc;
+    }
+    *out = reinterpret_cast<sfft_batch*>(B);
+    return SFFT_OK;
 }
-void sfft_batch_destroy(sfft_batch* b) { (void)b; }
+
+void sfft_batch_destroy(sfft_batch* b) {
+    if (!b) return;
+    Batch* B = reinterpret_cast<Batch*>(b);
+    B->release();
+    delete B;
+}
+
 int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* const* supp_out, double* const* coef_out,
                            const int64_t* cap, int64_t* n_out_dev) {
-    (void)b; (void)samples; (void)supp_out; (void)coef_out; (void)cap; (void)n_out_dev;
-    set_error("sfft_batch_reconstruct: not available in this build");
-    return SFFT_EINVAL;
+    if (!b || !samples || !supp_out || !coef_out || !cap) { set_error("null argument"); return SFFT_EINVAL; }
+    Batch* B = reinterpret_cast<Batch*>(b);
+    const int n = (int)B->plans.size();
+    // the previous call's copy of the staging descriptors must have completed
+    SFFT_CU(cudaEventSynchronize(B->done));
+    for (int i = 0; i < n; ++i) {
+        const int u = B->order[i];  // caller's index of batch entry i
+        SFFT_CHECK(samples[u] && (cap[u] == 0 || (supp_out[u] && coef_out[u])), SFFT_EINVAL, "null buffer for plan %d", u);
+        InstDesc& I = B->h_inst[i];
+        I.samples = samples[u];
+        I.supp_out = supp_out[u];
+        I.coef_out = reinterpret_cast<c64*>(coef_out[u]);
+        I.out_cap = cap[u];
+        I.dcounts = nullptr;
+        I.dhashes = nullptr;
+        B->plans[i]->have_forward = false;  // batch runs do not keep a backward context
+    }
+    cudaStream_t st = B->st;
+    SFFT_TRY(B->collect());
+    B->args.timer = B->timing ? &B->timer : nullptr;
+    if (B->timing && B->exec == nullptr && B->use_graph && B->calls >= 1) {
+        // the graph is captured without timers; timed runs of a graph batch use the eager path
+        SFFT_TRY(B->enqueue());
+        B->pending = true;
+    } else if (B->use_graph && B->calls >= 1 && !B->timing) {
+        if (!B->exec) {
+            SFFT_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            int rc = B->enqueue();
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamEndCapture(st, &g);
+            if (rc != SFFT_OK) return rc;
+            if (e != cudaSuccess) { set_error("graph capture failed: %s", cudaGetErrorString(e)); return SFFT_ECUDA; }
+            B->graph = g;
+            SFFT_CU(cudaGraphInstantiate(&B->exec, g, 0));
+        }
+        SFFT_CU(cudaGraphLaunch(B->exec, st));
+    } else {
+        SFFT_TRY(B->enqueue());
+        B->pending = B->timing;
+    }
+    if (n_out_dev) {
+        // results in caller order
+        for (int i = 0; i < n; ++i)
+            SFFT_CU(cudaMemcpyAsync(n_out_dev + B->order[i], B->d_counts + i, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
+    }
+    SFFT_CU(cudaEventRecord(B->done, st));
+    B->calls++;
+    return SFFT_OK;
 }
+
 int sfft_dim_incremental(int d, const int32_t* box_lo, const int32_t* box_hi, const sfft_dimincr_params* p,
                          sfft_sample_fn f, void* ctx, int32_t* supp_out, double* coef_out, int64_t cap, int64_t* n_out,
                          int64_t* n_samples, void* stream) {
@@ -53,6 +288,19 @@ int sfft_fn_sop(void* ctx, const double* x, int64_t n, double* y, void* stream) 
     (void)ctx; (void)x; (void)n; (void)y; (void)stream;
     set_error("sfft_fn_sop: not available in this build");
     return SFFT_EINVAL;
+}
+
+int sfft_batch_timing(sfft_batch* b, int mode, double* ms, int64_t* launches) {
+    if (!b) { set_error("batch is NULL"); return -1; }
+    Batch* B = reinterpret_cast<Batch*>(b);
+    if (B->collect() != SFFT_OK) return -1;
+    if (ms) for (int s = 0; s < ST_COUNT; ++s) ms[s] = B->stage_ms[s];
+    if (launches) for (int s = 0; s < ST_COUNT; ++s) launches[s] = B->stage_n[s];
+    if (mode >= 0) {
+        B->timing = mode > 0;
+        for (int s = 0; s < ST_COUNT; ++s) { B->stage_ms[s] = 0; B->stage_n[s] = 0; }
+    }
+    return ST_COUNT;
 }
 
 }  // extern "C"

@@ -290,7 +290,8 @@ constexpr int kBlueThreads = 512;
 // One CTA = one Bluestein transform.  T: arithmetic; TI/TO: element type of input/output.
 template <class T, class TI, class TO, bool SM>
 __global__ void __launch_bounds__(kBlueThreads) k_bluestein(const BlueJob* __restrict__ jobs, int sign, int epi,
-                                                            const InstDesc* __restrict__ insts) {
+                                                            const InstDesc* __restrict__ insts, void* out_base,
+                                                            const void* aux_base) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ T red[32];
     const BlueJob& J = jobs[blockIdx.x];
@@ -301,12 +302,15 @@ __global__ void __launch_bounds__(kBlueThreads) k_bluestein(const BlueJob* __res
     const cplx<T>* __restrict__ filt = reinterpret_cast<const cplx<T>*>(J.filt);
     const void* inp = J.in;
     const void* auxp = J.aux;
-    if (J.io_flags) {
+    void* outp = J.out;
+    if (J.io_flags & 3) {
         const InstDesc& I = insts[J.inst];
         const size_t esz = I.prec ? sizeof(c32) : sizeof(c64);
         if (J.io_flags & 1) inp = (const char*)I.samples + J.io_off * esz;
         if (J.io_flags & 2) auxp = (const char*)I.samples + J.io_off * esz;
     }
+    if (J.io_flags & 4) outp = (char*)out_base + J.io_off * sizeof(cplx<TO>);
+    if (J.io_flags & 8) auxp = aux_base ? (const void*)((const c64*)aux_base + J.io_off) : nullptr;
     const cplx<TI>* __restrict__ in = reinterpret_cast<const cplx<TI>*>(inp);
     const bool inv = sign > 0;
 
@@ -344,7 +348,7 @@ __global__ void __launch_bounds__(kBlueThreads) k_bluestein(const BlueJob* __res
         __syncthreads();
     }
     // ---- epilogue: X_h = w_h conv_h
-    cplx<TO>* __restrict__ out = reinterpret_cast<cplx<TO>*>(J.out);
+    cplx<TO>* __restrict__ out = reinterpret_cast<cplx<TO>*>(outp);
     T mx = 0;
     const T sc = (T)J.scale;
     for (int h = threadIdx.x; h < M; h += blockDim.x) {
@@ -382,7 +386,7 @@ size_t blue_smem_limit() { return 220 * 1024; }
 
 template <class T, class TI, class TO>
 static int launch_t(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign, int epi, const InstDesc* insts,
-                    cudaStream_t st) {
+                    cudaStream_t st, void* ob, const void* ab) {
     if (njobs == 0) return SFFT_OK;
     if (sm) {
         size_t bytes = (size_t)maxN * sizeof(cplx<T>);
@@ -395,26 +399,26 @@ static int launch_t(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign
             SFFT_CU(cudaFuncSetAttribute(k_bluestein<T, TI, TO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blue_smem_limit()));
             attr_done = true;
         }
-        k_bluestein<T, TI, TO, true><<<njobs, kBlueThreads, bytes, st>>>(djobs, sign, epi, insts);
+        k_bluestein<T, TI, TO, true><<<njobs, kBlueThreads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
     } else {
-        k_bluestein<T, TI, TO, false><<<njobs, kBlueThreads, 0, st>>>(djobs, sign, epi, insts);
+        k_bluestein<T, TI, TO, false><<<njobs, kBlueThreads, 0, st>>>(djobs, sign, epi, insts, ob, ab);
     }
     return launch_check("k_bluestein");
 }
 
 int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, bool sm, int prec, int in_prec, int out_prec, int sign,
-                     int epi, const InstDesc* insts, cudaStream_t st) {
+                     int epi, const InstDesc* insts, cudaStream_t st, void* ob, const void* ab) {
     // prec/in/out: 0 = double, 1 = float
     int key = prec * 4 + in_prec * 2 + out_prec;
     switch (key) {
-        case 0: return launch_t<double, double, double>(djobs, njobs, maxN, sm, sign, epi, insts, st);
-        case 1: return launch_t<double, double, float>(djobs, njobs, maxN, sm, sign, epi, insts, st);
-        case 2: return launch_t<double, float, double>(djobs, njobs, maxN, sm, sign, epi, insts, st);
-        case 3: return launch_t<double, float, float>(djobs, njobs, maxN, sm, sign, epi, insts, st);
-        case 4: return launch_t<float, double, double>(djobs, njobs, maxN, sm, sign, epi, insts, st);
-        case 5: return launch_t<float, double, float>(djobs, njobs, maxN, sm, sign, epi, insts, st);
-        case 6: return launch_t<float, float, double>(djobs, njobs, maxN, sm, sign, epi, insts, st);
-        default: return launch_t<float, float, float>(djobs, njobs, maxN, sm, sign, epi, insts, st);
+        case 0: return launch_t<double, double, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
+        case 1: return launch_t<double, double, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
+        case 2: return launch_t<double, float, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
+        case 3: return launch_t<double, float, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
+        case 4: return launch_t<float, double, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
+        case 5: return launch_t<float, double, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
+        case 6: return launch_t<float, float, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
+        default: return launch_t<float, float, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
     }
 }
 

@@ -7,17 +7,37 @@
 
 namespace sfft {
 
+// one launch of Bluestein jobs (all in shared memory or all with global scratch)
+struct FftLaunch {
+    const BlueJob* jobs = nullptr;
+    int njobs = 0, maxN = 0;
+    bool sm = true;
+};
+// one launch of the hash-count kernel over a contiguous range of instances of equal d
+struct HashGroup {
+    int off = 0, count = 0, d = 0, gx = 1;
+    size_t smem = 0;
+};
+
+// optional per-stage CUDA-event timing of the stage sequence
+enum Stage : int {
+    ST_CLEAR = 0, ST_FFT_FWD, ST_ZERO_TEST, ST_HASH, ST_COMPACT, ST_DET_HASH, ST_COMBINE,
+    ST_SCATTER, ST_FFT_MODEL, ST_FFT_RFWD, ST_DELTA, ST_SELECT, ST_COUNT
+};
+struct StageTimer {
+    cudaEvent_t ev[ST_COUNT + 1];
+    bool recorded[ST_COUNT + 1];
+};
+
 struct PipeArgs {
-    int ninst = 1, nlat = 0, maxN = 0, prec = 0, d = 0, hash_gx = 1;
-    size_t hash_smem = 0;
+    StageTimer* timer = nullptr;
+    int ninst = 1, nlat = 0, prec = 0;
     int64_t maxcap = 0;
-    bool sm_prec = true, sm64 = true;
     int hybrid = 0, refine = 0;
     InstDesc* d_inst = nullptr;
     const LatDesc* d_lats = nullptr;
-    const BlueJob* jobs_fwd = nullptr;
-    const BlueJob* jobs_model = nullptr;
-    const BlueJob* jobs_rfwd = nullptr;
+    std::vector<FftLaunch> fwd, model, rfwd;
+    std::vector<HashGroup> hash;
 };
 
 struct Plan {
@@ -52,8 +72,9 @@ struct Plan {
     InstDesc* h_inst = nullptr;  // pinned
     int64_t* h_cnt = nullptr;    // pinned
     LatDesc* d_lats = nullptr;
-    std::vector<BlueJob> jobs_fwd, jobs_model, jobs_rfwd;
-    BlueJob *d_jobs_fwd = nullptr, *d_jobs_model = nullptr, *d_jobs_rfwd = nullptr, *d_jobs_tmp = nullptr;
+    std::vector<BlueJob> jobs_fwd, jobs_model, jobs_rfwd, jobs_samp, jobs_adj;
+    BlueJob *d_jobs_fwd = nullptr, *d_jobs_model = nullptr, *d_jobs_rfwd = nullptr;
+    BlueJob *d_jobs_samp = nullptr, *d_jobs_adj = nullptr;
     size_t hash_smem = 0;
     bool have_forward = false;
 

@@ -46,16 +46,30 @@ def full_grid(d: int, N: int) -> np.ndarray:
 def uniform_distinct(n: int, d: int, lo: int, hi: int, seed: int, stream: int = S_GAMMA) -> np.ndarray:
     """n distinct integer vectors drawn uniformly from [lo, hi]^d (int32 [n, d]).
 
-    Rows keep the order in which they were drawn (duplicates are dropped and redrawn).
+    Rows keep the order in which they were drawn; a row equal to an earlier one is dropped
+    and further rows are drawn.  Distinctness is checked through a 64-bit row key (distinct
+    keys imply distinct rows) and exactly on the rows whose keys collide.
     """
+    if n > (hi - lo + 1) ** d:
+        raise ValueError("more distinct vectors requested than the box holds")
     g = rng(seed, stream)
+    mult = (np.arange(d, dtype=np.uint64) * np.uint64(0x9E3779B97F4A7C15) + np.uint64(0xD1B54A32D192ED03)) | np.uint64(1)
     out = np.empty((0, d), dtype=np.int32)
     need = n
     while need > 0:
         draw = g.integers(lo, hi + 1, size=(need + need // 16 + 16, d), dtype=np.int32)
         allr = np.concatenate([out, draw], axis=0)
-        _, first = np.unique(allr, axis=0, return_index=True)
-        keep = np.sort(first)
+        with np.errstate(over="ignore"):
+            key = (allr.astype(np.int64).astype(np.uint64) * mult[None, :]).sum(axis=1, dtype=np.uint64)
+            key ^= key >> np.uint64(29)
+        _, inv, cnt = np.unique(key, return_inverse=True, return_counts=True)
+        keep = np.ones(allr.shape[0], dtype=bool)
+        shared = np.nonzero(cnt[inv] > 1)[0]
+        if shared.size:
+            # rows whose key is shared: keep the exact first occurrence of each row only
+            _, firstsub = np.unique(allr[shared], axis=0, return_index=True)
+            keep[shared] = False
+            keep[shared[firstsub]] = True
         out = allr[keep][:n]
         need = n - out.shape[0]
     return np.ascontiguousarray(out.astype(np.int32))

@@ -400,3 +400,42 @@ def test_edge_cases(G):
     supp, coef = plan.reconstruct(T(y))
     assert np.array_equal(supp.cpu().numpy(), ref.supp)
     assert relmax(coef.cpu().numpy(), ref.coef) <= 1e-4
+
+
+# ------------------------------------------------------------------ batching
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batch_matches_single_plans(G, use_graph):
+    """Plans of different d / |Gamma| / M in one batch (one launch per stage, optionally a CUDA
+    graph replayed twice) give the single-plan results, which equal the oracle's."""
+    import torch
+    specs = [(3, 4000, 20, 1), (5, 9000, 40, 2), (3, 3000, 25, 3), (8, 6000, 30, 4)]
+    plans, samples, refs = [], [], []
+    for d, n, s, seed in specs:
+        cand = S.uniform_distinct(n, d, -30, 30, seed)
+        L = O.L_cor26(n, 0.1)
+        M = O.lattice_size(cand, s)
+        z = S.generators(L, d, M, seed)
+        sup = S.support_indices(n, s, seed)
+        c = S.coef_cgauss(s, seed)
+        sig = S.snr_sigma(c, 40.0)
+        y = (O.sample_sparse_poly(cand[sup], c, z, M) + S.noise(L * M, sig, seed)).astype(np.complex64)
+        tau = 6 * sig / math.sqrt(M)
+        refs.append(O.reconstruct(cand, y.astype(np.complex128), z, M, tau_abs=tau, do_refine=True, refine_mode="bucket"))
+        plans.append(G.Plan(T(cand), s, L=L, M=[M] * L, z=z, precision=1, refine=1, tau_abs=tau, tau_rel=0.0))
+        samples.append(T(y))
+    st = torch.cuda.Stream() if use_graph else None
+    if use_graph:
+        with pytest.raises(G.SfftError):
+            G.Batch(plans, use_graph=True, stream=torch.cuda.default_stream())
+    B = G.Batch(plans, use_graph=use_graph, stream=st)
+    for rep in range(3):
+        res = B.reconstruct(samples)
+        if st is not None:
+            st.synchronize()
+        for (supp, coef), ref in zip(res, refs):
+            assert np.array_equal(supp.cpu().numpy(), ref.supp)
+            assert relmax(coef.cpu().numpy(), ref.coef) <= 1e-4
+    t = B.timing(1)
+    B.reconstruct(samples)
+    t = B.timing(-1)
+    assert t["hash_count"][1] == 1 and t["hash_count"][0] > 0
