@@ -140,10 +140,10 @@ def cpu_baseline(timeout=600):
 
 # ------------------------------------------------------------------ native arm
 def kernel_count(batch_plans, n_inst, refine=True):
-    # per step: 2 sampler launches per instance (bucket scatter, inverse lattice DFT) and, for the
-    # batch, clear + DFT + zero test + hash groups + compact + hashes + combine + select + counts
+    # per step: batched sampler (clear, bucket scatter, inverse lattice DFT) and the batch's
+    # clear + DFT + zero test + hash groups + compact + hashes + combine + select + counts
     hash_groups = len({p.d for p in batch_plans})
-    n = 2 * n_inst + 1 + 1 + 1 + hash_groups + 1 + 1 + 1 + 1 + 1
+    n = 3 + 1 + 1 + 1 + hash_groups + 1 + 1 + 1 + 1 + 1
     if refine:
         n += 1 + 1 + 1 + 1 + 1  # clear C, scatter, FP64 model IDFT, refinement DFT, update
     return n
@@ -190,8 +190,7 @@ def run_native(a, rank, world):
 
     def step():
         with torch.cuda.stream(st):
-            for i, p in enumerate(plans):
-                p.sample_sparse_poly(kv[i], cf[i], nz[i], out=smp[i])
+            batch.sample_sparse_poly(kv, cf, nz, outs=smp)
             batch.reconstruct_async(smp)
 
     def barrier():
@@ -274,16 +273,14 @@ def run_native(a, rank, world):
     gbatch = G.Batch(plans, use_graph=True, stream=st)
     with torch.cuda.stream(st):
         for _ in range(3):
-            for i, p in enumerate(plans):
-                p.sample_sparse_poly(kv[i], cf[i], nz[i], out=smp[i])
+            gbatch.sample_sparse_poly(kv, cf, nz, outs=smp)
             gbatch.reconstruct_async(smp)
     st.synchronize()
     g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g0.record(st)
     with torch.cuda.stream(st):
         for _ in range(a.steps):
-            for i, p in enumerate(plans):
-                p.sample_sparse_poly(kv[i], cf[i], nz[i], out=smp[i])
+            gbatch.sample_sparse_poly(kv, cf, nz, outs=smp)
             gbatch.reconstruct_async(smp)
     g1.record(st)
     g1.synchronize()
@@ -306,8 +303,7 @@ def run_native(a, rank, world):
                 kv[i].copy_(hk[i], non_blocking=True)
                 cf[i].copy_(hf[i], non_blocking=True)
                 nz[i].copy_(hn[i], non_blocking=True)
-            for i, p in enumerate(plans):
-                p.sample_sparse_poly(kv[i], cf[i], nz[i], out=smp[i])
+            batch.sample_sparse_poly(kv, cf, nz, outs=smp)
             batch.reconstruct_async(smp)
             out_n.copy_(batch.nout, non_blocking=True)
             for i in range(n_inst):
@@ -331,8 +327,7 @@ def run_native(a, rank, world):
         b64 = G.Batch(p64, use_graph=False, stream=st)
 
         def step64():
-            for i, p in enumerate(p64):
-                p.sample_sparse_poly(kv[i], cf[i], nz[i], out=s64[i])
+            b64.sample_sparse_poly(kv, cf, nz, outs=s64)
             b64.reconstruct_async(s64)
 
         step64()

@@ -201,6 +201,16 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
                            double* const* coef_out, const int64_t* cap, int64_t* n_out_dev);
 
 /*
+ * sfft_sample_sparse_poly for every plan of the batch in shared launches (one bucket scatter,
+ * one inverse-transform launch).  Arrays are indexed by the caller's plan order: kvec[i]
+ * device int32 [n_terms[i], d_i]; coef[i] device complex double; noise NULL or noise[i] device
+ * complex double [sum M] (may be NULL); samples_out[i] device complex (plan precision).
+ * Asynchronous on the batch stream.
+ */
+int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, const double* const* coef,
+                                  const int64_t* n_terms, const double* const* noise, void* const* samples_out);
+
+/*
  * Per-stage GPU time of the batch's stage sequence, measured with CUDA events on the batch
  * stream around each stage of every call since the last reset.  Stage order: clear, lattice
  * DFT (Algorithm 2 line 2), zero test, hash + count, compaction, hashes of Itilde, combine,

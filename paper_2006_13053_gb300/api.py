@@ -225,6 +225,25 @@ class Batch:
         N.check(N.sfft_batch_reconstruct(self.handle, sp, self._ps, self._pc, self._cap,
                                          C.c_void_p(self.nout.data_ptr())))
 
+    def sample_sparse_poly(self, kvecs, coefs, noises=None, outs=None):
+        """Samples of every plan's sparse polynomial (+ noise) in shared launches (asynchronous)."""
+        n = len(self.plans)
+        outs = outs if outs is not None else [torch.empty(p.n_samples, dtype=p.cdtype, device=p.cand.device)
+                                              for p in self.plans]
+        for p, k, c, o in zip(self.plans, kvecs, coefs, outs):
+            _req(k, torch.int32, "kvec")
+            _req(c, torch.complex128, "coef")
+            _req(o, p.cdtype, "samples_out")
+        kp = (C.c_void_p * n)(*[k.data_ptr() for k in kvecs])
+        cp = (C.c_void_p * n)(*[c.data_ptr() for c in coefs])
+        nt = (C.c_int64 * n)(*[k.shape[0] for k in kvecs])
+        npp = None
+        if noises is not None:
+            npp = (C.c_void_p * n)(*[(x.data_ptr() if x is not None else 0) for x in noises])
+        op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
+        N.check(N.sfft_batch_sample_sparse_poly(self.handle, kp, cp, nt, npp, op))
+        return outs
+
     def results(self):
         (self.stream or torch.cuda.current_stream()).synchronize()
         k = self.nout.cpu().tolist()

@@ -115,7 +115,18 @@ static int dmalloc(void** p, size_t bytes) {
 }
 #define DMALLOC(ptr, bytes) SFFT_TRY(dmalloc((void**)&(ptr), (bytes)))
 
+int Plan::io_begin() {
+    if (io_ev) SFFT_CU(cudaEventSynchronize(io_ev));
+    return SFFT_OK;
+}
+int Plan::io_upload() {
+    SFFT_CU(cudaMemcpyAsync(d_inst, h_inst, sizeof(InstDesc), cudaMemcpyHostToDevice, st));
+    SFFT_CU(cudaEventRecord(io_ev, st));
+    return SFFT_OK;
+}
+
 void Plan::release() {
+    if (io_ev) { cudaEventSynchronize(io_ev); cudaEventDestroy(io_ev); io_ev = nullptr; }
     for (void* p : allocs) cudaFree(p);
     allocs.clear();
     for (auto* t : tabs) tables_release(t);
@@ -182,7 +193,7 @@ int Plan::build_jobs() {
         jobs_rfwd.push_back(r);
         // sampler: out (launch argument) = IDFT(C) + noise (launch argument), plan precision
         BlueJob sj = make_job(t, prec, 1, 1.0);
-        sj.in = C + o; sj.io_flags = 4 | 8; sj.io_off = o;
+        sj.in = C + o; sj.io_flags = 16 | 32; sj.io_off = o; sj.inst = 0;
         sj.scratch = a.scratch;
         jobs_samp.push_back(sj);
         // adjoint: out (launch argument) = (1/M) IDFT(C), plan precision
@@ -348,6 +359,7 @@ int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L
     I.nzbits = P->nzbits; I.ghat = P->ghat; I.stats = P->stats; I.detbits = P->detbits; I.det = P->det;
     I.cnt = P->cnt; I.coef = P->coef; I.H = P->H; I.sel = P->sel; I.coll = P->coll; I.C = P->C;
     I.rhat = P->rhat; I.resid = P->resid; I.outpos = P->outpos;
+    SFFT_CU(cudaEventCreateWithFlags(&P->io_ev, cudaEventDisableTiming));
     SFFT_TRY(P->alloc((void**)&P->d_inst, sizeof(InstDesc)));
     SFFT_CU(cudaMemcpy(P->d_inst, &I, sizeof(InstDesc), cudaMemcpyHostToDevice));
     // ---- lattice descriptors and static transform jobs
@@ -364,8 +376,10 @@ int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L
     SFFT_TRY(upload_jobs(P->jobs_rfwd, &P->d_jobs_rfwd, &P->allocs));
     SFFT_TRY(upload_jobs(P->jobs_samp, &P->d_jobs_samp, &P->allocs));
     SFFT_TRY(upload_jobs(P->jobs_adj, &P->d_jobs_adj, &P->allocs));
-    // hash-count launch shape: one full wave of CTAs
-    P->hash_smem = sizeof(uint32_t) * (size_t)words + sizeof(int32_t) * (size_t)L * (d + 4);
+    // hash-count kernel choice and launch shape (one full wave of CTAs)
+    int64_t maxM = *std::max_element(P->M.begin(), P->M.end());
+    P->packed = P->kmax <= 127 && maxM <= 32768;
+    P->hash_smem = hash_smem_bytes(d, L, (int)words, P->packed);
     SFFT_CHECK(P->hash_smem <= 220 * 1024, SFFT_EINVAL,
                "non-zero bitmap of %lld words does not fit shared memory", (long long)words);
     return SFFT_OK;
@@ -396,7 +410,8 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
     SFFT_TRY(launch_zero_test(a.d_lats, a.nlat, a.d_inst, a.prec, 32.0 * u, st));
     // count rule over all candidates, ascending compaction of Itilde
     SFFT_TRY(mark(a, ST_HASH, st));
-    for (const auto& h : a.hash) SFFT_TRY(launch_hash_count(a.d_inst + h.off, h.count, h.d, h.gx, h.smem, st));
+    for (const auto& h : a.hash)
+        SFFT_TRY(launch_hash_count(a.d_inst + h.off, h.count, h.d, h.gx, h.smem, h.variant, st));
     SFFT_TRY(mark(a, ST_COMPACT, st));
     SFFT_TRY(launch_compact(a.d_inst, ni, st));
     // hashes of Itilde, collision counts, median / hybrid combine
@@ -442,6 +457,7 @@ PipeArgs Plan::pipe_args() {
     a.rfwd.push_back(FftLaunch{d_jobs_rfwd, L, maxN, fits_smem(prec)});
     HashGroup h;
     h.off = 0; h.count = 1; h.d = d; h.gx = hash_grid(); h.smem = hash_smem;
+    h.variant = packed ? (diag_run ? 2 : 1) : 0;
     a.hash.push_back(h);
     return a;
 }
@@ -536,6 +552,7 @@ int sfft_reconstruct(sfft_plan* plan, const void* samples, int64_t* supp_out, do
         return SFFT_EINVAL;
     }
     Plan* P = reinterpret_cast<Plan*>(plan);
+    SFFT_TRY(P->io_begin());
     InstDesc& I = *P->h_inst;
     I.samples = samples;
     I.supp_out = supp_out;
@@ -544,7 +561,8 @@ int sfft_reconstruct(sfft_plan* plan, const void* samples, int64_t* supp_out, do
     I.dcounts = diag ? diag->counts : nullptr;
     I.dhashes = diag ? diag->hashes : nullptr;
     cudaStream_t st = P->st;
-    SFFT_CU(cudaMemcpyAsync(P->d_inst, &I, sizeof(InstDesc), cudaMemcpyHostToDevice, st));
+    SFFT_TRY(P->io_upload());
+    P->diag_run = diag && (diag->counts || diag->hashes);
     SFFT_TRY(run_pipeline(P->pipe_args(), st));
     SFFT_CU(cudaMemcpyAsync(P->h_cnt, P->cnt, sizeof(int64_t) * 8, cudaMemcpyDeviceToHost, st));
     if (diag) {
@@ -601,13 +619,24 @@ int sfft_reconstruct_backward(sfft_plan* plan, const double* dcoef, void* dsampl
 
 int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const double* coef, int64_t n_terms,
                             const double* noise, void* samples_out) {
-    if (!plan || !samples_out || (n_terms > 0 && (!kvec || !coef))) { set_error("null argument"); return SFFT_EINVAL; }
+    if (!plan || !samples_out || n_terms < 0 || (n_terms > 0 && (!kvec || !coef))) {
+        set_error("null argument");
+        return SFFT_EINVAL;
+    }
     Plan* P = const_cast<Plan*>(reinterpret_cast<const Plan*>(plan));
     cudaStream_t st = P->st;
-    SFFT_CU(cudaMemsetAsync(P->C, 0, sizeof(c64) * P->sumM, st));
-    if (n_terms > 0) SFFT_TRY(launch_scatter_terms(P->d_inst, kvec, reinterpret_cast<const c64*>(coef), n_terms, st));
+    SFFT_TRY(P->io_begin());
+    InstDesc& I = *P->h_inst;
+    I.samp_kvec = kvec;
+    I.samp_coef = reinterpret_cast<const c64*>(coef);
+    I.samp_nterms = n_terms;
+    I.samp_out = samples_out;
+    I.samp_noise = reinterpret_cast<const c64*>(noise);
+    SFFT_TRY(P->io_upload());
+    SFFT_TRY(launch_clear(P->d_inst, 1, 0, 0, 1, st));
+    if (n_terms > 0) SFFT_TRY(launch_scatter_terms(P->d_inst, 1, n_terms * P->L, st));
     SFFT_TRY(launch_bluestein(P->d_jobs_samp, P->L, P->maxN, P->fits_smem(P->prec), P->prec, 0, P->prec, +1, EPI_ADDNOISE,
-                              P->d_inst, st, samples_out, noise));
+                              P->d_inst, st));
     return SFFT_OK;
 }
 

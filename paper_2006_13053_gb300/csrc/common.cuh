@@ -127,7 +127,8 @@ struct BlueJob {
     double scale;        // output scale (1/M for the normalised forward DFT)
     int M, N, nstages;
     // io_flags: bit 0 in = samples of instance `inst` + io_off; bit 1 aux = those samples;
-    //           bit 2 out = out_base (launch argument) + io_off; bit 3 aux = aux_base + io_off
+    //           bit 2 out = out_base (launch argument) + io_off; bit 3 aux = aux_base + io_off;
+    //           bit 4 out = samp_out of instance `inst` + io_off; bit 5 aux = its samp_noise + io_off
     int inst, io_flags;
     int64_t io_off;
     uint8_t radix[kMaxStages];
@@ -196,6 +197,12 @@ struct InstDesc {
     int64_t out_cap;
     uint8_t* dcounts;          // diag
     int32_t* dhashes;          // diag
+    // ---- per call of the sparse-polynomial sampler
+    const int32_t* samp_kvec;  // [samp_nterms, d]
+    const c64* samp_coef;      // [samp_nterms]
+    int64_t samp_nterms;
+    void* samp_out;            // [sum M] complex (prec)
+    const c64* samp_noise;     // [sum M] or NULL
 };
 
 // One lattice of one instance (for per-lattice kernels).

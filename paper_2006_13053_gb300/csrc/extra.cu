@@ -30,6 +30,8 @@ struct Batch {
     LatDesc* d_lats = nullptr;
     std::vector<void*> allocs;
     PipeArgs args;
+    std::vector<FftLaunch> samp;  // sparse-polynomial sampler transforms of every plan
+    int64_t max_samp_terms_L = 0;
     int64_t* d_counts = nullptr;
     int64_t* d_flags = nullptr;
     cudaEvent_t done = nullptr;
@@ -108,7 +110,7 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
     for (int i : idx) B->plans.push_back(reinterpret_cast<Plan*>(plans[i]));
     SFFT_CU(cudaMallocHost((void**)&B->h_inst, sizeof(InstDesc) * n));
     std::vector<LatDesc> lats;
-    std::vector<BlueJob> jf[2], jm[2], jr[2];  // [0] global scratch, [1] shared memory
+    std::vector<BlueJob> jf[2], jm[2], jr[2], js[2];  // [0] global scratch, [1] shared memory
     int maxN[2][3] = {{0, 0, 0}, {0, 0, 0}};
     PipeArgs& A = B->args;
     A.ninst = n;
@@ -124,9 +126,9 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
                                    (const double*)P->tabs[l]->dft64});
         const int sp = P->fits_smem(P->prec) ? 1 : 0, s64 = P->fits_smem(0) ? 1 : 0;
         for (int l = 0; l < P->L; ++l) {
-            BlueJob f = P->jobs_fwd[l], m = P->jobs_model[l], r = P->jobs_rfwd[l];
-            f.inst = b; m.inst = b; r.inst = b;
-            jf[sp].push_back(f); jm[s64].push_back(m); jr[sp].push_back(r);
+            BlueJob f = P->jobs_fwd[l], m = P->jobs_model[l], r = P->jobs_rfwd[l], s = P->jobs_samp[l];
+            f.inst = b; m.inst = b; r.inst = b; s.inst = b;
+            jf[sp].push_back(f); jm[s64].push_back(m); jr[sp].push_back(r); js[sp].push_back(s);
         }
         maxN[sp][0] = std::max(maxN[sp][0], P->maxN);
         maxN[s64][1] = std::max(maxN[s64][1], P->maxN);
@@ -148,6 +150,11 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
             SFFT_TRY(upload_jobs(*lists[k], &dj, &B->allocs));
             dst[k]->push_back(FftLaunch{dj, (int)lists[k]->size(), maxN[sm][k], sm == 1});
         }
+        if (!js[sm].empty()) {
+            BlueJob* dj = nullptr;
+            SFFT_TRY(upload_jobs(js[sm], &dj, &B->allocs));
+            B->samp.push_back(FftLaunch{dj, (int)js[sm].size(), maxN[sm][0], sm == 1});
+        }
     }
     // hash groups: contiguous runs of equal d
     for (int b = 0; b < n;) {
@@ -156,12 +163,13 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
         h.off = b;
         h.d = B->plans[b]->d;
         int64_t tiles = 0;
-        while (e < n && B->plans[e]->d == h.d) {
+        while (e < n && B->plans[e]->d == h.d && B->plans[e]->packed == B->plans[b]->packed) {
             h.smem = std::max(h.smem, B->plans[e]->hash_smem);
             tiles = std::max<int64_t>(tiles, (B->plans[e]->n + 511) / 512);
             ++e;
         }
         h.count = e - b;
+        h.variant = B->plans[b]->packed ? 1 : 0;
         int per_sm = std::max<int>(1, std::min<int>(8, (int)((228 * 1024) / (h.smem + 1024))));
         h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (152 * per_sm + h.count - 1) / h.count));
         A.hash.push_back(h);
@@ -288,6 +296,35 @@ int sfft_fn_sop(void* ctx, const double* x, int64_t n, double* y, void* stream) 
     (void)ctx; (void)x; (void)n; (void)y; (void)stream;
     set_error("sfft_fn_sop: not available in this build");
     return SFFT_EINVAL;
+}
+
+int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, const double* const* coef,
+                                  const int64_t* n_terms, const double* const* noise, void* const* samples_out) {
+    if (!b || !kvec || !coef || !n_terms || !samples_out) { set_error("null argument"); return SFFT_EINVAL; }
+    Batch* B = reinterpret_cast<Batch*>(b);
+    const int n = (int)B->plans.size();
+    SFFT_CU(cudaEventSynchronize(B->done));
+    int64_t mx = 0;
+    for (int i = 0; i < n; ++i) {
+        const int u = B->order[i];
+        SFFT_CHECK(samples_out[u] && n_terms[u] >= 0 && (n_terms[u] == 0 || (kvec[u] && coef[u])), SFFT_EINVAL,
+                   "bad sampler arguments for plan %d", u);
+        InstDesc& I = B->h_inst[i];
+        I.samp_kvec = kvec[u];
+        I.samp_coef = reinterpret_cast<const c64*>(coef[u]);
+        I.samp_nterms = n_terms[u];
+        I.samp_out = samples_out[u];
+        I.samp_noise = noise ? reinterpret_cast<const c64*>(noise[u]) : nullptr;
+        mx = std::max<int64_t>(mx, n_terms[u] * B->plans[i]->L);
+    }
+    cudaStream_t st = B->st;
+    SFFT_CU(cudaMemcpyAsync(B->d_inst, B->h_inst, sizeof(InstDesc) * n, cudaMemcpyHostToDevice, st));
+    SFFT_TRY(launch_clear(B->d_inst, n, 0, 0, 1, st));
+    if (mx > 0) SFFT_TRY(launch_scatter_terms(B->d_inst, n, mx, st));
+    for (const auto& f : B->samp)
+        SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, B->prec, 0, B->prec, +1, EPI_ADDNOISE, B->d_inst, st));
+    SFFT_CU(cudaEventRecord(B->done, st));
+    return SFFT_OK;
 }
 
 int sfft_batch_timing(sfft_batch* b, int mode, double* ms, int64_t* launches) {

@@ -309,6 +309,11 @@ __global__ void __launch_bounds__(kBlueThreads) k_bluestein(const BlueJob* __res
         if (J.io_flags & 1) inp = (const char*)I.samples + J.io_off * esz;
         if (J.io_flags & 2) auxp = (const char*)I.samples + J.io_off * esz;
     }
+    if (J.io_flags & 48) {
+        const InstDesc& I = insts[J.inst];
+        if (J.io_flags & 16) outp = (char*)I.samp_out + J.io_off * sizeof(cplx<TO>);
+        if (J.io_flags & 32) auxp = I.samp_noise ? (const void*)(I.samp_noise + J.io_off) : nullptr;
+    }
     if (J.io_flags & 4) outp = (char*)out_base + J.io_off * sizeof(cplx<TO>);
     if (J.io_flags & 8) auxp = aux_base ? (const void*)((const c64*)aux_base + J.io_off) : nullptr;
     const cplx<TI>* __restrict__ in = reinterpret_cast<const cplx<TI>*>(inp);

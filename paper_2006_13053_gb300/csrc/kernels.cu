@@ -222,6 +222,121 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __r
     }
 }
 
+// Packed variant: |k_t| <= 127 and M_l <= 32768, so k is stored as int8x4 words and z_l as
+// int16x2 words; each dp2a instruction adds two products k_t z_t exactly into the int32 sum.
+// Per lattice a 16-byte aligned record in shared memory holds {M, mu, off, bit offset} and the
+// packed z words (broadcast loads shared by all threads).  DIAG additionally writes the
+// per-candidate hashes and counts.
+constexpr int kCPT2 = 4;
+
+template <int D> struct Pack {
+    static constexpr int KW = (D + 3) / 4;             // int8x4 words of k
+    static constexpr int ZW = (D + 1) / 2;             // int16x2 words of z
+    static constexpr int REC = 4 + ((ZW + 3) / 4) * 4; // words per lattice record (multiple of 4)
+};
+
+template <int D, bool DIAG>
+__global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDesc* __restrict__ insts) {
+    extern __shared__ __align__(16) uint32_t hsm[];
+    using PK = Pack<D>;
+    const InstDesc& I = insts[blockIdx.y];
+    const int L = I.L, nwords = I.nwords;
+    uint32_t* rec = hsm;                       // [L][REC]
+    uint32_t* bits = hsm + L * PK::REC;        // [nwords]
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = I.nzbits[i];
+    for (int l = threadIdx.x; l < L; l += blockDim.x) {
+        uint32_t* r = rec + l * PK::REC;
+        r[0] = (uint32_t)I.Ml[l];
+        r[1] = I.mu[l];
+        r[2] = I.offk[l];
+        r[3] = (uint32_t)I.boff[l] * 32u;
+        for (int w = 0; w < PK::REC - 4; ++w) {
+            uint32_t lo = 0, hi = 0;
+            if (2 * w < D) lo = (uint32_t)I.z[l * D + 2 * w] & 0xffffu;
+            if (2 * w + 1 < D) hi = (uint32_t)I.z[l * D + 2 * w + 1] & 0xffffu;
+            r[4 + w] = lo | (hi << 16);
+        }
+    }
+    __syncthreads();
+    const int64_t n = I.n;
+    const int need = I.need;
+    const int32_t* __restrict__ cand = I.cand;
+    const int64_t step = (int64_t)gridDim.x * blockDim.x * kCPT2;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kCPT2; base < n; base += step) {
+        uint32_t kw[kCPT2][PK::KW];
+        int64_t idx[kCPT2];
+#pragma unroll
+        for (int c = 0; c < kCPT2; ++c) {
+            idx[c] = base + threadIdx.x + (int64_t)c * blockDim.x;
+            const int32_t* row = cand + (idx[c] < n ? idx[c] : 0) * D;
+            int k[PK::KW * 4];
+#pragma unroll
+            for (int t = 0; t < PK::KW * 4; ++t) k[t] = 0;
+            if constexpr (D % 4 == 0) {
+#pragma unroll
+                for (int t = 0; t < D; t += 4) {
+                    int4 v = __ldg(reinterpret_cast<const int4*>(row + t));
+                    k[t] = v.x; k[t + 1] = v.y; k[t + 2] = v.z; k[t + 3] = v.w;
+                }
+            } else if constexpr (D % 2 == 0) {
+#pragma unroll
+                for (int t = 0; t < D; t += 2) {
+                    int2 v = __ldg(reinterpret_cast<const int2*>(row + t));
+                    k[t] = v.x; k[t + 1] = v.y;
+                }
+            } else {
+#pragma unroll
+                for (int t = 0; t < D; ++t) k[t] = __ldg(row + t);
+            }
+#pragma unroll
+            for (int w = 0; w < PK::KW; ++w)
+                kw[c][w] = (uint32_t)(k[4 * w] & 0xff) | ((uint32_t)(k[4 * w + 1] & 0xff) << 8) |
+                           ((uint32_t)(k[4 * w + 2] & 0xff) << 16) | ((uint32_t)(k[4 * w + 3] & 0xff) << 24);
+        }
+        int cnt[kCPT2];
+#pragma unroll
+        for (int c = 0; c < kCPT2; ++c) cnt[c] = 0;
+        for (int l = 0; l < L; ++l) {
+            const uint4* r4 = reinterpret_cast<const uint4*>(rec + l * PK::REC);
+            const uint4 cst = r4[0];
+            uint32_t zw[PK::REC - 4];
+#pragma unroll
+            for (int w = 0; w < (PK::REC - 4) / 4; ++w) {
+                uint4 v = r4[1 + w];
+                zw[4 * w] = v.x; zw[4 * w + 1] = v.y; zw[4 * w + 2] = v.z; zw[4 * w + 3] = v.w;
+            }
+            const uint32_t M = cst.x, mu = cst.y, off = cst.z, bo = cst.w;
+#pragma unroll
+            for (int c = 0; c < kCPT2; ++c) {
+                int x = 0;
+#pragma unroll
+                for (int w = 0; w < PK::ZW; ++w) {
+                    if (w & 1) x = __dp2a_hi((int)zw[w], (int)kw[c][w >> 1], x);
+                    else x = __dp2a_lo((int)zw[w], (int)kw[c][w >> 1], x);
+                }
+                uint32_t xp = (uint32_t)x + off;
+                uint32_t q = __umulhi(xp, mu);
+                uint32_t rr = xp - q * M;
+                rr = rr >= M ? rr - M : rr;
+                uint32_t bit = bo + rr;
+                cnt[c] += __funnelshift_r(bits[bit >> 5], 0u, bit) & 1u;
+                if constexpr (DIAG) {
+                    if (idx[c] < n && I.dhashes) I.dhashes[idx[c] * L + l] = (int32_t)rr;
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kCPT2; ++c) {
+            if (idx[c] < n) {
+                if (cnt[c] >= need) atomicOr(&I.detbits[idx[c] >> 5], 1u << (idx[c] & 31));
+                if constexpr (DIAG) {
+                    if (I.dcounts) I.dcounts[idx[c]] = (uint8_t)cnt[c];
+                }
+            }
+        }
+    }
+}
+
 // ================================================================== compaction (ascending Itilde)
 constexpr int kCompactThreads = 1024;
 __global__ void __launch_bounds__(kCompactThreads) k_compact(InstDesc* __restrict__ insts) {
@@ -537,10 +652,12 @@ __global__ void __launch_bounds__(kSelThreads) k_select(InstDesc* __restrict__ i
 
 // ================================================================== samplers and adjoint scatter
 // scatter coefficients of a sparse polynomial into the lattice buckets (eq. 2.3)
-__global__ void k_scatter_terms(const InstDesc* __restrict__ insts, const int32_t* __restrict__ kvec,
-                                const c64* __restrict__ coef, int64_t nterms) {
+__global__ void k_scatter_terms(const InstDesc* __restrict__ insts) {
     const InstDesc& I = insts[blockIdx.y];
     const int L = I.L, d = I.d;
+    const int32_t* __restrict__ kvec = I.samp_kvec;
+    const c64* __restrict__ coef = I.samp_coef;
+    const int64_t nterms = I.samp_nterms;
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nterms * L; e += (int64_t)gridDim.x * blockDim.x) {
         int64_t q = e / L;
         int l = (int)(e - q * L);
@@ -643,19 +760,40 @@ int launch_clear(InstDesc* di, int ninst, int clear_det, int clear_coll, int cle
 }
 
 template <int D>
-static int launch_hash_d(const InstDesc* di, int ninst, int gx, size_t smem, cudaStream_t st) {
-    static bool attr = false;
-    if (!attr) {
-        SFFT_CU(cudaFuncSetAttribute(k_hash_count<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-        attr = true;
+static int launch_hash_d(const InstDesc* di, int ninst, int gx, size_t smem, int variant, cudaStream_t st) {
+    // variant: 0 int32 kernel, 1 packed kernel, 2 packed kernel with diagnostics
+    static bool attr[3] = {false, false, false};
+    if (variant == 0) {
+        if (!attr[0]) {
+            SFFT_CU(cudaFuncSetAttribute(k_hash_count<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+            attr[0] = true;
+        }
+        k_hash_count<D><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di);
+    } else if (variant == 1) {
+        if (!attr[1]) {
+            SFFT_CU(cudaFuncSetAttribute(k_hash_count_packed<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+            attr[1] = true;
+        }
+        k_hash_count_packed<D, false><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di);
+    } else {
+        if (!attr[2]) {
+            SFFT_CU(cudaFuncSetAttribute(k_hash_count_packed<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
+            attr[2] = true;
+        }
+        k_hash_count_packed<D, true><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di);
     }
-    k_hash_count<D><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di);
     return launch_check("k_hash_count");
 }
 
-int launch_hash_count(const InstDesc* di, int ninst, int d, int gx, size_t smem, cudaStream_t st) {
+size_t hash_smem_bytes(int d, int L, int nwords, bool packed) {
+    if (!packed) return sizeof(uint32_t) * (size_t)nwords + sizeof(int32_t) * (size_t)L * (d + 4);
+    const int ZW = (d + 1) / 2, REC = 4 + ((ZW + 3) / 4) * 4;
+    return sizeof(uint32_t) * ((size_t)nwords + (size_t)L * REC);
+}
+
+int launch_hash_count(const InstDesc* di, int ninst, int d, int gx, size_t smem, int variant, cudaStream_t st) {
     switch (d) {
-#define SFFT_HD(D) case D: return launch_hash_d<D>(di, ninst, gx, smem, st);
+#define SFFT_HD(D) case D: return launch_hash_d<D>(di, ninst, gx, smem, variant, st);
         SFFT_HD(1) SFFT_HD(2) SFFT_HD(3) SFFT_HD(4) SFFT_HD(5) SFFT_HD(6) SFFT_HD(7) SFFT_HD(8)
         SFFT_HD(9) SFFT_HD(10) SFFT_HD(11) SFFT_HD(12) SFFT_HD(13) SFFT_HD(14) SFFT_HD(15) SFFT_HD(16)
         SFFT_HD(17) SFFT_HD(18) SFFT_HD(19) SFFT_HD(20) SFFT_HD(21) SFFT_HD(22) SFFT_HD(23) SFFT_HD(24)
@@ -706,9 +844,9 @@ int launch_select(InstDesc* di, int ninst, cudaStream_t st) {
     return launch_check("k_select");
 }
 
-int launch_scatter_terms(const InstDesc* di, const int32_t* kvec, const c64* coef, int64_t nterms, cudaStream_t st) {
-    int gx = (int)std::min<int64_t>(1024, (nterms * 64 + 255) / 256 + 1);
-    k_scatter_terms<<<dim3(gx, 1), 256, 0, st>>>(di, kvec, coef, nterms);
+int launch_scatter_terms(const InstDesc* di, int ninst, int64_t max_terms_x_L, cudaStream_t st) {
+    int gx = (int)std::min<int64_t>(1024, (max_terms_x_L + 255) / 256 + 1);
+    k_scatter_terms<<<dim3(gx, ninst), 256, 0, st>>>(di);
     return launch_check("k_scatter_terms");
 }
 

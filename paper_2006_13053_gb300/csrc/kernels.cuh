@@ -3,7 +3,9 @@
 #include "common.cuh"
 
 namespace sfft {
-int launch_hash_count(const InstDesc* di, int ninst, int d, int gx, size_t smem, cudaStream_t st);
+// variant: 0 int32 inner products, 1 packed (int8 k, int16 z, dp2a), 2 packed with diagnostics
+int launch_hash_count(const InstDesc* di, int ninst, int d, int gx, size_t smem, int variant, cudaStream_t st);
+size_t hash_smem_bytes(int d, int L, int nwords, bool packed);
 int launch_zero_test(const LatDesc* dl, int nlat, InstDesc* di, int prec, double kappa_u, cudaStream_t st);
 int launch_compact(InstDesc* di, int ninst, cudaStream_t st);
 int launch_det_hashes(const InstDesc* di, int ninst, int64_t maxdet, cudaStream_t st);
@@ -11,7 +13,7 @@ int launch_collisions(const InstDesc* di, int ninst, cudaStream_t st);
 int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int mode, cudaStream_t st);
 int launch_scatter_coef(const InstDesc* di, int ninst, cudaStream_t st);
 int launch_select(InstDesc* di, int ninst, cudaStream_t st);
-int launch_scatter_terms(const InstDesc* di, const int32_t* kvec, const c64* coef, int64_t nterms, cudaStream_t st);
+int launch_scatter_terms(const InstDesc* di, int ninst, int64_t max_terms_x_L, cudaStream_t st);
 int launch_adj_scatter(const InstDesc* di, const c64* dcoef, cudaStream_t st);
 int launch_points(const InstDesc* di, int32_t* numer, double* x, int64_t tot, cudaStream_t st);
 int launch_cand_stats(const int32_t* cand, int64_t n, int d, int* mn, int* mx, cudaStream_t st);

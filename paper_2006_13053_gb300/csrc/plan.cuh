@@ -15,7 +15,7 @@ struct FftLaunch {
 };
 // one launch of the hash-count kernel over a contiguous range of instances of equal d
 struct HashGroup {
-    int off = 0, count = 0, d = 0, gx = 1;
+    int off = 0, count = 0, d = 0, gx = 1, variant = 0;
     size_t smem = 0;
 };
 
@@ -76,7 +76,13 @@ struct Plan {
     BlueJob *d_jobs_fwd = nullptr, *d_jobs_model = nullptr, *d_jobs_rfwd = nullptr;
     BlueJob *d_jobs_samp = nullptr, *d_jobs_adj = nullptr;
     size_t hash_smem = 0;
+    bool packed = false;          // |k| <= 127 and M <= 32768: packed dp2a hash kernel
+    bool diag_run = false;        // the current reconstruct writes per-candidate diagnostics
     bool have_forward = false;
+    cudaEvent_t io_ev = nullptr;  // recorded after each upload of h_inst (staging reuse guard)
+
+    int io_begin();               // wait until the previous upload of h_inst has completed
+    int io_upload();              // enqueue h_inst -> d_inst and record io_ev
 
     void release();
     int alloc(void** p, size_t bytes);

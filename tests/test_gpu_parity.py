@@ -439,3 +439,24 @@ def test_batch_matches_single_plans(G, use_graph):
     B.reconstruct(samples)
     t = B.timing(-1)
     assert t["hash_count"][1] == 1 and t["hash_count"][0] > 0
+
+
+def test_batch_sampler_matches_plan_sampler(G):
+    import torch
+    specs = [(3, 2000, 15, 11), (6, 3000, 25, 12), (3, 1500, 10, 13)]
+    plans, kv, cf, nz = [], [], [], []
+    for d, n, s, seed in specs:
+        cand = S.uniform_distinct(n, d, -25, 25, seed)
+        sup = S.support_indices(n, s, seed)
+        plans.append(G.Plan(T(cand), s, precision=1, seed=seed))
+        kv.append(T(cand[sup]))
+        cf.append(T(S.coef_cgauss(s, seed)))
+        nz.append(T(S.noise(plans[-1].n_samples, 0.01, seed)))
+    st = torch.cuda.Stream()
+    B = G.Batch(plans, stream=st)
+    outs = B.sample_sparse_poly(kv, cf, nz)
+    st.synchronize()
+    for p, k, c, z, o in zip(plans, kv, cf, nz, outs):
+        ref = p.sample_sparse_poly(k, c, z)
+        torch.cuda.synchronize()
+        assert torch.equal(o, ref)
