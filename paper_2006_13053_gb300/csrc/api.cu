@@ -145,6 +145,7 @@ int Plan::alloc(void** p, size_t bytes) {
 
 size_t Plan::esz() const { return prec ? sizeof(c32) : sizeof(c64); }
 
+// prec: 0 double, 1 float, 2 double-float arithmetic
 static BlueJob make_job(const FftTables* t, int prec, int dir, double scale) {
     BlueJob J;
     memset(&J, 0, sizeof J);
@@ -152,9 +153,16 @@ static BlueJob make_job(const FftTables* t, int prec, int dir, double scale) {
     J.N = (int)t->N;
     J.nstages = t->nstages;
     for (int s = 0; s < t->nstages; ++s) J.radix[s] = (uint8_t)t->radix[s];
-    J.tw = prec ? (const void*)t->tw32 : (const void*)t->tw64;
-    J.chirp = prec ? (const void*)t->chirp32 : (const void*)t->chirp64;
-    J.filt = prec ? (const void*)t->filt32[dir] : (const void*)t->filt64[dir];
+    if (prec == 1) {
+        J.tw = t->tw32; J.chirp = t->chirp32; J.filt = t->filt32[dir];
+    } else if (prec == 0) {
+        J.tw = t->tw64; J.chirp = t->chirp64; J.filt = t->filt64[dir];
+    } else {
+        J.tw = t->twdf; J.chirp = t->chirpdf; J.filt = t->filtdf[dir];
+    }
+    J.twa = t->twa32;
+    J.twb = t->twb32;
+    J.tw_na = t->tw_na;
     J.dft64 = (const double*)t->dft64;
     J.scale = scale;
     return J;
@@ -181,8 +189,8 @@ int Plan::build_jobs() {
         a.stat = stats + l;
         a.scratch = fits_smem(prec) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
         jobs_fwd.push_back(a);
-        // refinement model: resid = samples - IDFT(C) in FP64
-        BlueJob m = make_job(t, 0, 1, 1.0);
+        // refinement model: resid = samples - IDFT(C), double-float arithmetic, FP64 in/out
+        BlueJob m = make_job(t, 2, 1, 1.0);
         m.in = C + o; m.out = resid_b + o * e; m.io_flags = 2; m.io_off = o; m.inst = 0;
         m.scratch = fits_smem(0) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
         jobs_model.push_back(m);
@@ -427,7 +435,7 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
         // residual at the nodes in FP64: r = f - IDFT(C)
         SFFT_TRY(mark(a, ST_FFT_MODEL, st));
         for (const auto& f : a.model)
-            SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, 0, 0, a.prec, +1, EPI_RESID, a.d_inst, st));
+            SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, 2, 0, a.prec, +1, EPI_RESID, a.d_inst, st));
         SFFT_TRY(mark(a, ST_FFT_RFWD, st));
         for (const auto& f : a.rfwd)
             SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, a.prec, a.prec, a.prec, -1, EPI_PLAIN, a.d_inst, st));

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "../../include/sfft.h"
+#include "df64.cuh"
 
 namespace sfft {
 
@@ -104,6 +105,14 @@ struct FftTables {
     c64* filt64[2] = {nullptr, nullptr}; // [N] DIF(b)/N, digit-reversed; [0] forward, [1] inverse
     c32* filt32[2] = {nullptr, nullptr};
     c64* dft64 = nullptr;  // [M] exp(-2 pi i m / M) for single-bucket FP64 DFTs
+    // FP32 twiddles as two small tables: exp(-2 pi i k/N) = twa[k >> 8] * twb[k & 255]
+    c32* twa32 = nullptr;  // [tw_na] exp(-2 pi i 256 a / N)
+    c32* twb32 = nullptr;  // [256]   exp(-2 pi i b / N)
+    int tw_na = 0;
+    // double-float copies (hi, lo words of each double entry)
+    void* twdf = nullptr;     // [N]
+    void* chirpdf = nullptr;  // [M]
+    void* filtdf[2] = {nullptr, nullptr};
     int refs = 0;
     int device = -1;
 };
@@ -119,13 +128,15 @@ struct BlueJob {
     void* out;           // output complex, M entries
     const void* aux;     // epilogue input (noise / samples for the residual), M entries
     void* scratch;       // global work buffer of N complex (used when the buffer is not in smem)
-    const void* tw;      // twiddles of the transform precision
+    const void* tw;      // twiddles of the transform precision (full table)
+    const void* twa;     // FP32 two-level twiddle tables
+    const void* twb;
     const void* chirp;
     const void* filt;    // filter of the requested direction
     const double* dft64; // FP64 single-bucket table (guard re-tests)
     struct LatStats* stat; // side outputs of EPI_ANALYZE
     double scale;        // output scale (1/M for the normalised forward DFT)
-    int M, N, nstages;
+    int M, N, nstages, tw_na;
     // io_flags: bit 0 in = samples of instance `inst` + io_off; bit 1 aux = those samples;
     //           bit 2 out = out_base (launch argument) + io_off; bit 3 aux = aux_base + io_off;
     //           bit 4 out = samp_out of instance `inst` + io_off; bit 5 aux = its samp_noise + io_off

@@ -11,6 +11,7 @@
 
 #include <map>
 #include <mutex>
+#include <type_traits>
 
 #include "common.cuh"
 
@@ -81,6 +82,14 @@ static int upload32(c32** dst, const std::vector<c64>& src) {
     return SFFT_OK;
 }
 
+static int upload_df(void** dst, const std::vector<c64>& src) {
+    std::vector<cplx<df64>> tmp(src.size());
+    for (size_t i = 0; i < src.size(); ++i) tmp[i] = cplx<df64>{df_from(src[i].x), df_from(src[i].y)};
+    SFFT_CU(cudaMalloc(dst, sizeof(cplx<df64>) * tmp.size()));
+    SFFT_CU(cudaMemcpy(*dst, tmp.data(), sizeof(cplx<df64>) * tmp.size(), cudaMemcpyHostToDevice));
+    return SFFT_OK;
+}
+
 int tables_acquire(int64_t M, FftTables** out) {
     int dev = 0;
     SFFT_CU(cudaGetDevice(&dev));
@@ -97,7 +106,7 @@ int tables_acquire(int64_t M, FftTables** out) {
     t->N = bluestein_size(M);
     t->device = dev;
     t->nstages = factor_radices(t->N, t->radix);
-    if (t->nstages <= 0 || t->nstages > kMaxStages) {
+    if (t->nstages <= 0 || t->nstages > kMaxStages || t->N > 262144) {
         delete t;
         set_error("no mixed-radix plan for Bluestein length of M=%lld", (long long)M);
         return SFFT_EINVAL;
@@ -116,6 +125,18 @@ int tables_acquire(int64_t M, FftTables** out) {
         dft[j] = c64{cos(a2), sin(a2)};
     }
     int rc = SFFT_OK;
+    t->tw_na = (int)((N + 255) / 256);
+    std::vector<c64> twa(t->tw_na), twb(256);
+    for (int a = 0; a < t->tw_na; ++a) {
+        double ang = -2.0 * M_PI * (double)((int64_t)a * 256) / (double)N;
+        twa[a] = c64{cos(ang), sin(ang)};
+    }
+    for (int b2 = 0; b2 < 256; ++b2) {
+        double ang = -2.0 * M_PI * (double)b2 / (double)N;
+        twb[b2] = c64{cos(ang), sin(ang)};
+    }
+    if (rc == SFFT_OK) rc = upload32(&t->twa32, twa);
+    if (rc == SFFT_OK) rc = upload32(&t->twb32, twb);
     // filters: forward b_n = conj(chirp_|n|), inverse b_n = chirp_|n| (circular), then DIF / N
     for (int dir = 0; dir < 2 && rc == SFFT_OK; ++dir) {
         std::fill(b.begin(), b.end(), c64{0, 0});
@@ -127,12 +148,15 @@ int tables_acquire(int64_t M, FftTables** out) {
         host_dif(b, N, t->radix, t->nstages, tw);
         for (auto& v : b) v = v * (1.0 / (double)N);
         if ((rc = upload64(&t->filt64[dir], b)) == SFFT_OK) rc = upload32(&t->filt32[dir], b);
+        if (rc == SFFT_OK) rc = upload_df(&t->filtdf[dir], b);
     }
     if (rc == SFFT_OK) rc = upload64(&t->tw64, tw);
     if (rc == SFFT_OK) rc = upload32(&t->tw32, tw);
     if (rc == SFFT_OK) rc = upload64(&t->chirp64, chirp);
     if (rc == SFFT_OK) rc = upload32(&t->chirp32, chirp);
     if (rc == SFFT_OK) rc = upload64(&t->dft64, dft);
+    if (rc == SFFT_OK) rc = upload_df(&t->twdf, tw);
+    if (rc == SFFT_OK) rc = upload_df(&t->chirpdf, chirp);
     if (rc != SFFT_OK) {
         t->refs = 1;
         tables_release(t);
@@ -150,19 +174,36 @@ void tables_release(FftTables* t) {
     if (--t->refs > 0) return;
     g_tabs.erase(std::make_pair(t->device, t->M));
     cudaFree(t->tw64); cudaFree(t->tw32); cudaFree(t->chirp64); cudaFree(t->chirp32); cudaFree(t->dft64);
-    for (int d = 0; d < 2; ++d) { cudaFree(t->filt64[d]); cudaFree(t->filt32[d]); }
+    for (int d = 0; d < 2; ++d) { cudaFree(t->filt64[d]); cudaFree(t->filt32[d]); cudaFree(t->filtdf[d]); }
+    cudaFree(t->twa32); cudaFree(t->twb32); cudaFree(t->twdf); cudaFree(t->chirpdf);
     delete t;
+}
+
+// ================================================================== device arithmetic helpers
+// scalar conversion between float, double and df64 (direct for equal types)
+template <class D, class S> __device__ __forceinline__ D scv(S v) {
+    if constexpr (std::is_same<D, S>::value) return v;
+    else if constexpr (std::is_same<D, df64>::value) return from_d<df64>((double)v);
+    else if constexpr (std::is_same<S, df64>::value) {
+        if constexpr (std::is_same<D, float>::value) return v.hi + v.lo;
+        else return (double)v.hi + (double)v.lo;
+    } else return (D)v;
+}
+template <class D, class S> __device__ __forceinline__ cplx<D> ccv(cplx<S> a) { return {scv<D>(a.x), scv<D>(a.y)}; }
+
+// read-only loads of table entries in the transform precision
+__device__ __forceinline__ cplx<df64> ldg(const cplx<df64>* p) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return {df64{v.x, v.y}, df64{v.z, v.w}};
 }
 
 // ================================================================== device butterflies
 // R-point DFT in registers: y_p = sum_q v_q omega^{pq}, omega = exp(S * 2 pi i / R), S = -1 / +1
-template <class T> struct K5 {
-    static constexpr T c1 = (T)0.309016994374947424102293417182819059;   // cos(2 pi/5)
-    static constexpr T c2 = (T)-0.809016994374947424102293417182819059;  // cos(4 pi/5)
-    static constexpr T s1 = (T)0.951056516295153572116439333379382143;   // sin(2 pi/5)
-    static constexpr T s2 = (T)0.587785252292473129168705954639072769;   // sin(4 pi/5)
-    static constexpr T h3 = (T)0.866025403784438646763723170752936183;   // sqrt(3)/2
-};
+constexpr double kC1 = 0.309016994374947424102293417182819059;   // cos(2 pi/5)
+constexpr double kC2 = -0.809016994374947424102293417182819059;  // cos(4 pi/5)
+constexpr double kS1 = 0.951056516295153572116439333379382143;   // sin(2 pi/5)
+constexpr double kS2 = 0.587785252292473129168705954639072769;   // sin(4 pi/5)
+constexpr double kH3 = 0.866025403784438646763723170752936183;   // sqrt(3)/2
 
 // multiply by S*i
 template <int S, class T> __device__ __forceinline__ cplx<T> mul_si(cplx<T> a) {
@@ -182,17 +223,17 @@ template <int R, int S, class T> __device__ __forceinline__ void bfly(cplx<T>* v
         v[3] = t1 - t3;
     } else if constexpr (R == 3) {
         cplx<T> t1 = v[1] + v[2], t2 = v[1] - v[2];
-        cplx<T> a = v[0] - t1 * (T)0.5;
-        cplx<T> b = mul_si<S>(t2 * K5<T>::h3);
+        cplx<T> a = v[0] - t1 * kc<T>(0.5);
+        cplx<T> b = mul_si<S>(t2 * kc<T>(kH3));
         v[0] = v[0] + t1;
         v[1] = a + b;
         v[2] = a - b;
     } else if constexpr (R == 5) {
         cplx<T> t1 = v[1] + v[4], t2 = v[2] + v[3], t3 = v[1] - v[4], t4 = v[2] - v[3];
-        cplx<T> b1 = v[0] + t1 * K5<T>::c1 + t2 * K5<T>::c2;
-        cplx<T> b2 = v[0] + t1 * K5<T>::c2 + t2 * K5<T>::c1;
-        cplx<T> d1 = mul_si<S>(t3 * K5<T>::s1 + t4 * K5<T>::s2);
-        cplx<T> d2 = mul_si<S>(t3 * K5<T>::s2 - t4 * K5<T>::s1);
+        cplx<T> b1 = v[0] + t1 * kc<T>(kC1) + t2 * kc<T>(kC2);
+        cplx<T> b2 = v[0] + t1 * kc<T>(kC2) + t2 * kc<T>(kC1);
+        cplx<T> d1 = mul_si<S>(t3 * kc<T>(kS1) + t4 * kc<T>(kS2));
+        cplx<T> d2 = mul_si<S>(t3 * kc<T>(kS2) - t4 * kc<T>(kS1));
         v[0] = v[0] + t1 + t2;
         v[1] = b1 + d1;
         v[4] = b1 - d1;
@@ -201,12 +242,26 @@ template <int R, int S, class T> __device__ __forceinline__ void bfly(cplx<T>* v
     }
 }
 
-// DIF stage: sub-transform size Ns, radix R, m = Ns / R; twiddle exp(-2 pi i n p / Ns)
-template <int R, class T>
-__device__ __forceinline__ void dif_stage(cplx<T>* __restrict__ buf, int N, int Ns, const cplx<T>* __restrict__ tw) {
+// twiddle exp(-2 pi i k / N) for 0 <= k < N
+template <class T> struct TwFull {  // full table in global memory (L2 / L1 resident)
+    const cplx<T>* tw;
+    __device__ __forceinline__ cplx<T> operator()(int k) const { return ldg(&tw[k]); }
+};
+struct TwTwo {  // FP32: product of two small shared-memory tables, k = 256 a + b
+    const c32* a;
+    const c32* b;
+    __device__ __forceinline__ c32 operator()(int k) const { return a[k >> 8] * b[k & 255]; }
+};
+
+// DIF stage: sub-transform size Ns, radix R, m = Ns / R; twiddle exp(-2 pi i n p / Ns).
+// The block index b = floor(i / m) is formed with a float reciprocal: (i + 1/2) / m is at least
+// 1/(2m) away from an integer, which the float product resolves exactly for i < 2^22.
+template <int R, class T, class TW>
+__device__ __forceinline__ void dif_stage(cplx<T>* __restrict__ buf, int N, int Ns, const TW& tw) {
     const int m = Ns / R, stride = N / Ns, nb = N / R;
+    const float rm = 1.0f / (float)m;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        int b = i / m, n = i - b * m;
+        int b = (int)(((float)i + 0.5f) * rm), n = i - b * m;
         cplx<T>* base = buf + (size_t)b * Ns + n;
         cplx<T> v[R];
 #pragma unroll
@@ -214,28 +269,30 @@ __device__ __forceinline__ void dif_stage(cplx<T>* __restrict__ buf, int N, int 
         bfly<R, -1>(v);
         base[0] = v[0];
 #pragma unroll
-        for (int p = 1; p < R; ++p) base[p * m] = v[p] * ldg(&tw[n * p * stride]);
+        for (int p = 1; p < R; ++p) base[p * m] = v[p] * tw(n * p * stride);
     }
 }
 
 // DIT stage (exact adjoint of dif_stage): conj twiddles, then inverse R-point DFT
-template <int R, class T>
-__device__ __forceinline__ void dit_stage(cplx<T>* __restrict__ buf, int N, int Ns, const cplx<T>* __restrict__ tw) {
+template <int R, class T, class TW>
+__device__ __forceinline__ void dit_stage(cplx<T>* __restrict__ buf, int N, int Ns, const TW& tw) {
     const int m = Ns / R, stride = N / Ns, nb = N / R;
+    const float rm = 1.0f / (float)m;
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-        int b = i / m, n = i - b * m;
+        int b = (int)(((float)i + 0.5f) * rm), n = i - b * m;
         cplx<T>* base = buf + (size_t)b * Ns + n;
         cplx<T> v[R];
         v[0] = base[0];
 #pragma unroll
-        for (int p = 1; p < R; ++p) v[p] = mulc(base[p * m], ldg(&tw[n * p * stride]));
+        for (int p = 1; p < R; ++p) v[p] = mulc(base[p * m], tw(n * p * stride));
         bfly<R, 1>(v);
 #pragma unroll
         for (int q = 0; q < R; ++q) base[q * m] = v[q];
     }
 }
 
-template <class T> __device__ __forceinline__ void run_stage(bool dif, int R, cplx<T>* buf, int N, int Ns, const cplx<T>* tw) {
+template <class T, class TW>
+__device__ __forceinline__ void run_stage(bool dif, int R, cplx<T>* buf, int N, int Ns, const TW& tw) {
     if (dif) {
         switch (R) {
             case 4: dif_stage<4>(buf, N, Ns, tw); break;
@@ -253,53 +310,128 @@ template <class T> __device__ __forceinline__ void run_stage(bool dif, int R, cp
     }
 }
 
-template <class T> __device__ __forceinline__ T block_reduce_max(T v, T* red) {
+__device__ __forceinline__ double block_reduce_max(double v, double* red) {
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
     if (l == 0) red[w] = v;
     __syncthreads();
-    T r = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : (T)0;
+    double r = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
     if (w == 0)
         for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
     if (threadIdx.x == 0) red[0] = r;
     __syncthreads();
-    T out = red[0];
+    double out = red[0];
     __syncthreads();
     return out;
 }
 
-template <class T> __device__ __forceinline__ T block_reduce_sum(T v, T* red) {
+__device__ __forceinline__ double block_reduce_sum(double v, double* red) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     int w = threadIdx.x >> 5, l = threadIdx.x & 31;
     __syncthreads();
     if (l == 0) red[w] = v;
     __syncthreads();
-    T r = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : (T)0;
+    double r = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
     if (w == 0)
         for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
     if (threadIdx.x == 0) red[0] = r;
     __syncthreads();
-    T out = red[0];
+    double out = red[0];
     __syncthreads();
     return out;
 }
 
 constexpr int kBlueThreads = 512;
 
-// One CTA = one Bluestein transform.  T: arithmetic; TI/TO: element type of input/output.
+template <class T, class TI, class TO, class TW>
+__device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, const TW& tw, int sign, int epi,
+                                               const void* inp, const void* auxp, void* outp, double* red) {
+    // max of |x|^2 in the transform precision (double for df64, whose analysis is never requested)
+    using R = typename std::conditional<std::is_same<T, df64>::value, double, T>::type;
+    const int M = J.M, N = J.N, ns = J.nstages;
+    const cplx<T>* __restrict__ chirp = reinterpret_cast<const cplx<T>*>(J.chirp);
+    const cplx<T>* __restrict__ filt = reinterpret_cast<const cplx<T>*>(J.filt);
+    const cplx<TI>* __restrict__ in = reinterpret_cast<const cplx<TI>*>(inp);
+    const bool inv = sign > 0;
+    // ---- load x_j * w_j (w = chirp for the forward DFT, conj(chirp) for the inverse), zero pad
+    R ss = 0;
+    for (int i = threadIdx.x; i < N; i += blockDim.x) {
+        cplx<T> v = {kc<T>(0.0), kc<T>(0.0)};
+        if (i < M) {
+            cplx<T> x = ccv<T>(in[i]);
+            if (epi == EPI_ANALYZE) ss += scv<R>(abs2(x));
+            cplx<T> w = ldg(&chirp[i]);
+            v = inv ? mulc(x, w) : x * w;
+        }
+        buf[i] = v;
+    }
+    double ssd = 0;
+    if (epi == EPI_ANALYZE) ssd = block_reduce_sum((double)ss, red);
+    __syncthreads();
+    // ---- DIF stages
+    int Ns = N;
+    for (int s = 0; s < ns; ++s) {
+        int Rr = J.radix[s];
+        run_stage<T>(true, Rr, buf, N, Ns, tw);
+        Ns /= Rr;
+        __syncthreads();
+    }
+    // ---- pointwise product with the (digit-reversed) filter
+    for (int i = threadIdx.x; i < N; i += blockDim.x) buf[i] = buf[i] * ldg(&filt[i]);
+    __syncthreads();
+    // ---- DIT stages, reverse order
+    Ns = 1;
+    for (int s = ns - 1; s >= 0; --s) {
+        int Rr = J.radix[s];
+        Ns *= Rr;
+        run_stage<T>(false, Rr, buf, N, Ns, tw);
+        __syncthreads();
+    }
+    // ---- epilogue: X_h = w_h conv_h
+    cplx<TO>* __restrict__ out = reinterpret_cast<cplx<TO>*>(outp);
+    R mx2 = 0;
+    const T sc = kc<T>(J.scale);
+    for (int h = threadIdx.x; h < M; h += blockDim.x) {
+        cplx<T> w = ldg(&chirp[h]);
+        cplx<T> X = inv ? mulc(buf[h], w) : buf[h] * w;
+        X = X * sc;
+        if (epi == EPI_PLAIN || epi == EPI_ANALYZE) {
+            out[h] = ccv<TO>(X);
+            if (epi == EPI_ANALYZE) mx2 = fmax(mx2, scv<R>(abs2(X)));
+        } else if (epi == EPI_ADDNOISE) {
+            const c64* aux = reinterpret_cast<const c64*>(auxp);
+            c64 r = ccv<double>(X);
+            if (aux) r = r + aux[h];
+            out[h] = ccv<TO>(r);
+        } else {  // EPI_RESID: out = aux - X, aux in the output precision, difference in double
+            const cplx<TO>* aux = reinterpret_cast<const cplx<TO>*>(auxp);
+            c64 a = ccv<double>(aux[h]);
+            c64 x = ccv<double>(X);
+            out[h] = ccv<TO>(c64{a.x - x.x, a.y - x.y});
+        }
+    }
+    if (epi == EPI_ANALYZE) {
+        double mx = sqrt(block_reduce_max((double)mx2, red));
+        if (threadIdx.x == 0) {
+            LatStats& S = *J.stat;
+            S.max32 = (float)mx;
+            S.max_abs = mx;
+            S.rms = sqrt(ssd / (double)M);
+        }
+    }
+}
+
+// One CTA = one Bluestein transform.  T: arithmetic (float, double or df64); TI/TO: element
+// type of input/output.  SM: work buffer in dynamic shared memory, else in J.scratch.
 template <class T, class TI, class TO, bool SM>
-__global__ void __launch_bounds__(kBlueThreads) k_bluestein(const BlueJob* __restrict__ jobs, int sign, int epi,
+__global__ void __launch_bounds__(kBlueThreads, 1) k_bluestein(const BlueJob* __restrict__ jobs, int sign, int epi,
                                                             const InstDesc* __restrict__ insts, void* out_base,
                                                             const void* aux_base) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ T red[32];
+    __shared__ double red[32];
     const BlueJob& J = jobs[blockIdx.x];
-    const int M = J.M, N = J.N, ns = J.nstages;
     cplx<T>* buf = SM ? reinterpret_cast<cplx<T>*>(smem_raw) : reinterpret_cast<cplx<T>*>(J.scratch);
-    const cplx<T>* __restrict__ chirp = reinterpret_cast<const cplx<T>*>(J.chirp);
-    const cplx<T>* __restrict__ tw = reinterpret_cast<const cplx<T>*>(J.tw);
-    const cplx<T>* __restrict__ filt = reinterpret_cast<const cplx<T>*>(J.filt);
     const void* inp = J.in;
     const void* auxp = J.aux;
     void* outp = J.out;
@@ -316,78 +448,22 @@ __global__ void __launch_bounds__(kBlueThreads) k_bluestein(const BlueJob* __res
     }
     if (J.io_flags & 4) outp = (char*)out_base + J.io_off * sizeof(cplx<TO>);
     if (J.io_flags & 8) auxp = aux_base ? (const void*)((const c64*)aux_base + J.io_off) : nullptr;
-    const cplx<TI>* __restrict__ in = reinterpret_cast<const cplx<TI>*>(inp);
-    const bool inv = sign > 0;
-
-    // ---- load x_j * w_j (w = chirp for the forward DFT, conj(chirp) for the inverse), zero pad
-    T ss = 0;
-    for (int i = threadIdx.x; i < N; i += blockDim.x) {
-        cplx<T> v = {0, 0};
-        if (i < M) {
-            cplx<T> x = cvt<T>(in[i]);
-            if (epi == EPI_ANALYZE) ss += abs2(x);
-            cplx<T> w = ldg(&chirp[i]);
-            v = inv ? mulc(x, w) : x * w;
-        }
-        buf[i] = v;
-    }
-    if (epi == EPI_ANALYZE) ss = block_reduce_sum(ss, red);
-    __syncthreads();
-    // ---- DIF stages
-    int Ns = N;
-    for (int s = 0; s < ns; ++s) {
-        int R = J.radix[s];
-        run_stage<T>(true, R, buf, N, Ns, tw);
-        Ns /= R;
+    if constexpr (std::is_same<T, float>::value) {
+        __shared__ c32 s_twa[1024], s_twb[256];
+        const c32* ga = reinterpret_cast<const c32*>(J.twa);
+        const c32* gb = reinterpret_cast<const c32*>(J.twb);
+        for (int i = threadIdx.x; i < J.tw_na; i += blockDim.x) s_twa[i] = ga[i];
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) s_twb[i] = gb[i];
         __syncthreads();
-    }
-    // ---- pointwise product with the (digit-reversed) filter
-    for (int i = threadIdx.x; i < N; i += blockDim.x) buf[i] = buf[i] * ldg(&filt[i]);
-    __syncthreads();
-    // ---- DIT stages, reverse order
-    Ns = 1;
-    for (int s = ns - 1; s >= 0; --s) {
-        int R = J.radix[s];
-        Ns *= R;
-        run_stage<T>(false, R, buf, N, Ns, tw);
-        __syncthreads();
-    }
-    // ---- epilogue: X_h = w_h conv_h
-    cplx<TO>* __restrict__ out = reinterpret_cast<cplx<TO>*>(outp);
-    T mx = 0;
-    const T sc = (T)J.scale;
-    for (int h = threadIdx.x; h < M; h += blockDim.x) {
-        cplx<T> w = ldg(&chirp[h]);
-        cplx<T> X = inv ? mulc(buf[h], w) : buf[h] * w;
-        X = X * sc;
-        if (epi == EPI_PLAIN || epi == EPI_ANALYZE) {
-            out[h] = cvt<TO>(X);
-            if (epi == EPI_ANALYZE) mx = fmax(mx, sqrt(abs2(X)));
-        } else if (epi == EPI_ADDNOISE) {
-            const c64* aux = reinterpret_cast<const c64*>(auxp);
-            c64 r = {(double)X.x, (double)X.y};
-            if (aux) r = r + aux[h];
-            out[h] = cvt<TO>(r);
-        } else {  // EPI_RESID: out = aux - X, aux in the output precision, difference in double
-            const cplx<TO>* aux = reinterpret_cast<const cplx<TO>*>(auxp);
-            c64 a = cvt<double>(aux[h]);
-            c64 r = {a.x - (double)X.x, a.y - (double)X.y};
-            out[h] = cvt<TO>(r);
-        }
-    }
-    if (epi == EPI_ANALYZE) {
-        mx = block_reduce_max(mx, red);
-        if (threadIdx.x == 0) {
-            LatStats& S = *J.stat;
-            S.max32 = (float)mx;
-            S.max_abs = (double)mx;
-            S.rms = sqrt((double)ss / (double)M);
-        }
+        bluestein_body<T, TI, TO>(J, buf, TwTwo{s_twa, s_twb}, sign, epi, inp, auxp, outp, red);
+    } else {
+        bluestein_body<T, TI, TO>(J, buf, TwFull<T>{reinterpret_cast<const cplx<T>*>(J.tw)}, sign, epi, inp, auxp,
+                                  outp, red);
     }
 }
 
 // ================================================================== host launcher
-size_t blue_smem_limit() { return 220 * 1024; }
+size_t blue_smem_limit() { return 207 * 1024; }
 
 template <class T, class TI, class TO>
 static int launch_t(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign, int epi, const InstDesc* insts,
@@ -401,7 +477,8 @@ static int launch_t(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign
         }
         static bool attr_done = false;  // one attribute call per instantiation
         if (!attr_done) {
-            SFFT_CU(cudaFuncSetAttribute(k_bluestein<T, TI, TO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)blue_smem_limit()));
+            SFFT_CU(cudaFuncSetAttribute(k_bluestein<T, TI, TO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)blue_smem_limit()));
             attr_done = true;
         }
         k_bluestein<T, TI, TO, true><<<njobs, kBlueThreads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
@@ -413,7 +490,12 @@ static int launch_t(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign
 
 int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, bool sm, int prec, int in_prec, int out_prec, int sign,
                      int epi, const InstDesc* insts, cudaStream_t st, void* ob, const void* ab) {
-    // prec/in/out: 0 = double, 1 = float
+    // prec: 0 double, 1 float, 2 double-float; in/out: 0 double, 1 float
+    if (prec == 2) {
+        if (in_prec != 0) { set_error("double-float transforms take double input"); return SFFT_EINVAL; }
+        if (out_prec) return launch_t<df64, double, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
+        return launch_t<df64, double, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
+    }
     int key = prec * 4 + in_prec * 2 + out_prec;
     switch (key) {
         case 0: return launch_t<double, double, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
