@@ -1,8 +1,10 @@
 // Double-float arithmetic: a value is the unevaluated sum hi + lo of two floats with
 // |lo| <= ulp(hi)/2, giving about 48 significant bits on the FP32 pipes.  The operations are
 // built from the error-free transformations two-sum (Knuth) and two-product via a fused
-// multiply-add (Dekker's product with FMA); addition is the "accurate" double-word sum
-// (both words added and renormalised twice), multiplication keeps the cross terms hi*lo.
+// multiply-add (Dekker's product with FMA).  Addition is Dekker's double-word sum (two-sum of
+// the high words, low words added, one renormalisation): its error is bounded relative to
+// |a| + |b| (not |a + b|), which is the normwise bound an FFT's error analysis uses.
+// Multiplication keeps the cross terms hi*lo.
 // Used for the refinement's model evaluation, where FP64 throughput is the bottleneck.
 #pragma once
 #include <cuda_runtime.h>
@@ -37,10 +39,7 @@ __host__ __device__ __forceinline__ df64 df_fast_two_sum(float a, float b) {  //
 }
 __host__ __device__ __forceinline__ df64 operator+(df64 a, df64 b) {
     df64 s = df_two_sum(a.hi, b.hi);
-    df64 t = df_two_sum(a.lo, b.lo);
-    s.lo = DF_ADD(s.lo, t.hi);
-    s = df_fast_two_sum(s.hi, s.lo);
-    s.lo = DF_ADD(s.lo, t.lo);
+    s.lo = DF_ADD(s.lo, DF_ADD(a.lo, b.lo));
     return df_fast_two_sum(s.hi, s.lo);
 }
 __host__ __device__ __forceinline__ df64 operator-(df64 a) { return df64{-a.hi, -a.lo}; }

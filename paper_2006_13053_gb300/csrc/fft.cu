@@ -183,13 +183,28 @@ void tables_release(FftTables* t) {
 // scalar conversion between float, double and df64 (direct for equal types)
 template <class D, class S> __device__ __forceinline__ D scv(S v) {
     if constexpr (std::is_same<D, S>::value) return v;
-    else if constexpr (std::is_same<D, df64>::value) return from_d<df64>((double)v);
+    else if constexpr (std::is_same<D, df64>::value) {
+        if constexpr (std::is_same<S, float>::value) return df64{v, 0.f};
+        else return from_d<df64>((double)v);
+    }
     else if constexpr (std::is_same<S, df64>::value) {
         if constexpr (std::is_same<D, float>::value) return v.hi + v.lo;
         else return (double)v.hi + (double)v.lo;
     } else return (D)v;
 }
 template <class D, class S> __device__ __forceinline__ cplx<D> ccv(cplx<S> a) { return {scv<D>(a.x), scv<D>(a.y)}; }
+
+// load of a transform input: zero entries (most buckets of a scattered sparse vector) skip the
+// double -> double-float conversion, which runs on the FP64 pipe
+template <class T, class TI> __device__ __forceinline__ cplx<T> load_in(const cplx<TI>* p) {
+    if constexpr (std::is_same<T, df64>::value && std::is_same<TI, double>::value) {
+        const longlong2 raw = *reinterpret_cast<const longlong2*>(p);
+        if ((raw.x | raw.y) == 0) return cplx<T>{df64{0.f, 0.f}, df64{0.f, 0.f}};
+        return ccv<T>(cplx<double>{__longlong_as_double(raw.x), __longlong_as_double(raw.y)});
+    } else {
+        return ccv<T>(*p);
+    }
+}
 
 // read-only loads of table entries in the transform precision
 __device__ __forceinline__ cplx<df64> ldg(const cplx<df64>* p) {
@@ -359,7 +374,7 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
     for (int i = threadIdx.x; i < N; i += blockDim.x) {
         cplx<T> v = {kc<T>(0.0), kc<T>(0.0)};
         if (i < M) {
-            cplx<T> x = ccv<T>(in[i]);
+            cplx<T> x = load_in<T, TI>(in + i);
             if (epi == EPI_ANALYZE) ss += scv<R>(abs2(x));
             cplx<T> w = ldg(&chirp[i]);
             v = inv ? mulc(x, w) : x * w;
@@ -404,11 +419,16 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
             c64 r = ccv<double>(X);
             if (aux) r = r + aux[h];
             out[h] = ccv<TO>(r);
-        } else {  // EPI_RESID: out = aux - X, aux in the output precision, difference in double
+        } else {  // EPI_RESID: out = aux - X, aux in the output precision
             const cplx<TO>* aux = reinterpret_cast<const cplx<TO>*>(auxp);
-            c64 a = ccv<double>(aux[h]);
-            c64 x = ccv<double>(X);
-            out[h] = ccv<TO>(c64{a.x - x.x, a.y - x.y});
+            if constexpr (std::is_same<T, df64>::value) {  // difference in double-float
+                cplx<T> a = ccv<T>(aux[h]);
+                out[h] = ccv<TO>(a - X);
+            } else {  // difference in double
+                c64 a = ccv<double>(aux[h]);
+                c64 x = ccv<double>(X);
+                out[h] = ccv<TO>(c64{a.x - x.x, a.y - x.y});
+            }
         }
     }
     if (epi == EPI_ANALYZE) {

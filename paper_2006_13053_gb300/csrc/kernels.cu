@@ -69,14 +69,19 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
     const double band = kappa_u_log * log2((double)D.N) * S.rms;
     if (threadIdx.x == 0) { gcount = 0; s_max64 = 0; }
     __syncthreads();
+    // Squared magnitudes are formed in the working precision and compared with bounds widened
+    // by a relative slack that covers their rounding; only buckets between the bounds need the
+    // FP64 re-test.
+    const double slack = sizeof(TS) == 4 ? 1e-6 : 1e-15;
+    const double big = sizeof(TS) == 4 ? 3.0e38 : 1.0e300;
     // ---- exact maximum: FP64 re-test of every bucket that could be the maximum
     double tau = I.tau_abs;
     if (I.tau_rel > 0) {
-        // every bucket that could hold the FP64 maximum (slack for the working precision)
-        const double lo = S.max_abs * (1.0 - 1.0 / 1048576.0) - 2.0 * band;
+        const double lo = fmax(S.max_abs * (1.0 - 1.0 / 1048576.0) - 2.0 * band, 0.0);
+        const TS lo2 = (TS)fmin(lo * lo * (1.0 - slack), big);
         for (int h = threadIdx.x; h < M; h += blockDim.x) {
-            double a = sqrt((double)abs2(cvt<double>(g[h])));
-            if (a >= lo) {
+            cplx<TS> v = g[h];
+            if (v.x * v.x + v.y * v.y >= lo2) {
                 int p = atomicAdd(&gcount, 1);
                 if (p < kGuardCap) glist[p] = h;
             }
@@ -98,6 +103,9 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
     }
     if (threadIdx.x == 0) { S.tau = tau; S.band = band; }
     // ---- threshold: one warp writes 32 consecutive buckets per ballot
+    const double tlo = fmax(tau - band, 0.0), thi = tau + band;
+    const TS lo2 = (TS)fmin(tlo * tlo * (1.0 - slack), big);  // below: certainly zero
+    const TS hi2 = (TS)fmin(thi * thi * (1.0 + slack), big);  // above: certainly non-zero
     uint32_t* words = I.nzbits + D.boff;
     const int nw = (M + 31) >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
@@ -105,9 +113,10 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
         int h = wi * 32 + lane;
         bool nz = false;
         if (h < M) {
-            double a = sqrt((double)abs2(cvt<double>(g[h])));
-            nz = a > tau;
-            if (fabs(a - tau) <= band) {
+            cplx<TS> v = g[h];
+            TS a2 = v.x * v.x + v.y * v.y;
+            nz = a2 > hi2;
+            if (!nz && a2 >= lo2) {  // uncertain: decided by the FP64 re-test below
                 int p = atomicAdd(&gcount, 1);
                 if (p < kGuardCap) glist[p] = h;
             }
