@@ -263,6 +263,29 @@ typedef struct sfft_fn_sop_ctx { const int32_t* triples; const double* theta; in
 int sfft_fn_sparse_poly(void* ctx, const double* x, int64_t n, double* y, void* stream);
 int sfft_fn_sop(void* ctx, const double* x, int64_t n, double* y, void* stream);
 
+/* ---------------------------------------------------------------- allocation-free detection */
+/*
+ * The detection step of sfft_reconstruct (zero test, candidate hashing with the count rule of
+ * Algorithm 1/2, ascending compaction of Itilde) for callers that cannot allocate device
+ * memory: code running where cudaMalloc is forbidden or may fail at a bad moment (inside host
+ * callbacks, under a custom or capped allocator, in a long-running service that must not grow
+ * its footprint).  The paper has no counterpart; it is an interface convenience.
+ *   cand   device int32 [n_cand, d];  M, z host int64 [L], [L, d] (z < M);
+ *   ghat   device complex double [sum M]: the normalised lattice DFTs (e.g. sfft_diag.ghat);
+ *   tau    host double [L]: zero-test thresholds (|ghat| > tau_l counts as non-zero);
+ *   nu     count rule: detected iff #{l : non-zero} >= nu L;
+ *   detected_out device int64 [cap]: detected indices, ascending; n_detected host (true count).
+ * Nothing is allocated: the scratch lives in one fixed 8 MiB device array owned by the library,
+ * held by every GPU that loads it until the process exits.  Sizes beyond it (about 6.4e7
+ * candidates with small lattices, less with large sum M) return SFFT_ECAPACITY, as does a
+ * detected set larger than cap.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share
+ * the array: calls that overlap on the GPU race, so serialise them.  Synchronises `stream`.
+ */
+int sfft_detect_noalloc(int d, const int32_t* cand, int64_t n_cand, int L, const int64_t* M, const int64_t* z,
+                        const double* ghat, const double* tau, double nu, int64_t* detected_out, int64_t cap,
+                        int64_t* n_detected, void* stream);
+
 /* ---------------------------------------------------------------- host utilities */
 /* Word 0 of Philox4x64-10 (Salmon et al., SC'11) for counter (c0..c3) and key (key0, 0). */
 uint64_t sfft_philox4x64_word0(uint64_t key0, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3);

@@ -98,6 +98,8 @@ sfft_dim_incremental = _sig("sfft_dim_incremental", _i32,
                             [_i32, _vp, _vp, _P(DimIncrParams), _vp, _vp, _vp, _vp, _i64, _P(_i64), _P(_i64), _vp])
 sfft_fn_sparse_poly = _sig("sfft_fn_sparse_poly", _i32, [_vp, _vp, _i64, _vp, _vp])
 sfft_fn_sop = _sig("sfft_fn_sop", _i32, [_vp, _vp, _i64, _vp, _vp])
+sfft_detect_noalloc = _sig("sfft_detect_noalloc", _i32, [_i32, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _dbl, _vp, _i64,
+                                                        _P(_i64), _vp])
 sfft_philox4x64_word0 = _sig("sfft_philox4x64_word0", C.c_uint64, [C.c_uint64] * 5)
 sfft_next_prime_above = _sig("sfft_next_prime_above", _i64, [_dbl])
 sfft_L_rule = _sig("sfft_L_rule", _i32, [_i32, _i64, _dbl, _dbl])
