@@ -256,10 +256,13 @@ int sfft_dim_incremental(int d, const int32_t* box_lo, const int32_t* box_hi, co
                          int64_t* n_out, int64_t* n_samples, void* stream);
 
 /* Built-in black boxes for Algorithm 3 (ctx = a struct owned by the caller):
- *   sfft_fn_sparse_poly: ctx = sfft_fn_sparse_poly_ctx (device kvec int32 [n, d], device coef complex double [n]);
- *   sfft_fn_sop:         ctx = sfft_fn_sop_ctx (host triples int32 [n_terms*3], device theta double [n_terms]). */
+ *   sfft_fn_sparse_poly: direct FP64 evaluation of sum_q coef_q exp(2 pi i kvec_q . x) (eq. 2.2);
+ *       ctx = sfft_fn_sparse_poly_ctx (device kvec int32 [n_terms, d], device coef complex double).
+ *   sfft_fn_sop: the sum-of-products function of sfft_sample_sop at arbitrary nodes;
+ *       ctx = sfft_fn_sop_ctx (host triples int32 [n_terms*3], device theta double [n_terms],
+ *       device work buffer of at least 16 n_terms (K+1) + 12 n_terms bytes). */
 typedef struct sfft_fn_sparse_poly_ctx { const int32_t* kvec; const double* coef; int64_t n_terms; int d; } sfft_fn_sparse_poly_ctx;
-typedef struct sfft_fn_sop_ctx { const int32_t* triples; const double* theta; int n_terms; int K; double width; int d; } sfft_fn_sop_ctx;
+typedef struct sfft_fn_sop_ctx { const int32_t* triples; const double* theta; int n_terms; int K; double width; int d; void* work; } sfft_fn_sop_ctx;
 int sfft_fn_sparse_poly(void* ctx, const double* x, int64_t n, double* y, void* stream);
 int sfft_fn_sop(void* ctx, const double* x, int64_t n, double* y, void* stream);
 

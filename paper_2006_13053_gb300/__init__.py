@@ -6,4 +6,4 @@ binds it.  Importing the package fails when the library has not been built.
 """
 from ._native import (COMBINE_HYBRID, COMBINE_MEDIAN, FP32, FP64, L_COR26, L_EQ42, L_FALLBACK,  # noqa: F401
                       SfftError, default_dimincr_params, default_params)
-from .api import Batch, Plan, SopReconstruct  # noqa: F401
+from .api import Batch, Plan, SopReconstruct, dim_incremental  # noqa: F401

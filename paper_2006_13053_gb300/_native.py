@@ -60,7 +60,7 @@ class SparsePolyCtx(C.Structure):
 
 class SopCtx(C.Structure):
     _fields_ = [("triples", C.c_void_p), ("theta", C.c_void_p), ("n_terms", C.c_int), ("K", C.c_int),
-                ("width", C.c_double), ("d", C.c_int)]
+                ("width", C.c_double), ("d", C.c_int), ("work", C.c_void_p)]
 
 
 SAMPLE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p)

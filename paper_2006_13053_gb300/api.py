@@ -272,3 +272,43 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def dim_incremental(d, lo, hi, s, fn, s_local=0, r=1, stream=None, cap=None, **params):
+    """Algorithm 3 on the box prod_t [lo_t, hi_t] with a built-in black box:
+       fn = ("sparse_poly", kvec int32 cuda [n, d], coef complex128 cuda [n]) or
+       fn = ("sop", triples int [m, 3], theta float64 cuda [m], K, width).
+    Returns (supp int32 numpy [k, d] in lexicographic order, coef complex128 numpy [k], samples)."""
+    p = N.default_dimincr_params(s=int(s), s_local=int(s_local), r=int(r), **params)
+    lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, dtype=np.int32), (d,)))
+    hi = np.ascontiguousarray(np.broadcast_to(np.asarray(hi, dtype=np.int32), (d,)))
+    keep = []
+    if fn[0] == "sparse_poly":
+        _, kvec, coef = fn
+        _req(kvec, torch.int32, "kvec")
+        _req(coef, torch.complex128, "coef")
+        ctx = N.SparsePolyCtx(kvec.data_ptr(), coef.data_ptr(), kvec.shape[0], d)
+        faddr = N.fn_address("sfft_fn_sparse_poly")
+    elif fn[0] == "sop":
+        _, triples, theta, K, width = fn
+        tri = np.ascontiguousarray(np.asarray(triples, dtype=np.int32))
+        _req(theta, torch.float64, "theta")
+        m = tri.shape[0]
+        work = torch.empty(16 * m * (K + 1) + 12 * m + 64, dtype=torch.uint8, device=theta.device)
+        keep += [tri, work]
+        ctx = N.SopCtx(tri.ctypes.data_as(C.c_void_p).value, theta.data_ptr(), m, int(K), float(width), d,
+                       work.data_ptr())
+        faddr = N.fn_address("sfft_fn_sop")
+    else:
+        raise ValueError(fn[0])
+    cap = int(cap if cap is not None else s)
+    supp = np.zeros((cap, d), dtype=np.int32)
+    coefo = np.zeros(cap, dtype=np.complex128)
+    nout = C.c_int64()
+    nsamp = C.c_int64()
+    N.check(N.sfft_dim_incremental(d, lo.ctypes.data_as(C.c_void_p), hi.ctypes.data_as(C.c_void_p), C.byref(p),
+                                   C.c_void_p(faddr), C.byref(ctx), supp.ctypes.data_as(C.c_void_p),
+                                   coefo.ctypes.data_as(C.c_void_p), cap, C.byref(nout), C.byref(nsamp),
+                                   _stream(stream)))
+    k = nout.value
+    return supp[:k], coefo[:k], nsamp.value

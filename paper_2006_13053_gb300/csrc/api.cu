@@ -146,7 +146,7 @@ int Plan::alloc(void** p, size_t bytes) {
 size_t Plan::esz() const { return prec ? sizeof(c32) : sizeof(c64); }
 
 // prec: 0 double, 1 float, 2 double-float arithmetic
-static BlueJob make_job(const FftTables* t, int prec, int dir, double scale) {
+BlueJob make_blue_job(const FftTables* t, int prec, int dir, double scale) {
     BlueJob J;
     memset(&J, 0, sizeof J);
     J.M = (int)t->M;
@@ -183,29 +183,29 @@ int Plan::build_jobs() {
         const FftTables* t = tabs[l];
         const int64_t o = soff[l];
         // forward analyse: ghat = DFT(samples)/M (plan precision)
-        BlueJob a = make_job(t, prec, 0, 1.0 / (double)M[l]);
+        BlueJob a = make_blue_job(t, prec, 0, 1.0 / (double)M[l]);
         a.io_flags = 1; a.io_off = o; a.inst = 0;
         a.out = ghat_b + o * e;
         a.stat = stats + l;
         a.scratch = fits_smem(prec) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
         jobs_fwd.push_back(a);
         // refinement model: resid = samples - IDFT(C), double-float arithmetic, FP64 in/out
-        BlueJob m = make_job(t, 2, 1, 1.0);
+        BlueJob m = make_blue_job(t, 2, 1, 1.0);
         m.in = C + o; m.out = resid_b + o * e; m.io_flags = 2; m.io_off = o; m.inst = 0;
         m.scratch = fits_smem(0) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
         jobs_model.push_back(m);
         // refinement forward: rhat = DFT(resid)/M (plan precision)
-        BlueJob r = make_job(t, prec, 0, 1.0 / (double)M[l]);
+        BlueJob r = make_blue_job(t, prec, 0, 1.0 / (double)M[l]);
         r.in = resid_b + o * e; r.out = rhat_b + o * e;
         r.scratch = a.scratch;
         jobs_rfwd.push_back(r);
         // sampler: out (launch argument) = IDFT(C) + noise (launch argument), plan precision
-        BlueJob sj = make_job(t, prec, 1, 1.0);
+        BlueJob sj = make_blue_job(t, prec, 1, 1.0);
         sj.in = C + o; sj.io_flags = 16 | 32; sj.io_off = o; sj.inst = 0;
         sj.scratch = a.scratch;
         jobs_samp.push_back(sj);
         // adjoint: out (launch argument) = (1/M) IDFT(C), plan precision
-        BlueJob aj = make_job(t, prec, 1, 1.0 / (double)M[l]);
+        BlueJob aj = make_blue_job(t, prec, 1, 1.0 / (double)M[l]);
         aj.in = C + o; aj.io_flags = 4; aj.io_off = o;
         aj.scratch = a.scratch;
         jobs_adj.push_back(aj);

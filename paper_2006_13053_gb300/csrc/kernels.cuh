@@ -29,4 +29,10 @@ int launch_sop_eval_points(const double* x, int64_t n, int d, const int32_t* tri
                            const double* a, double* y, cudaStream_t st);
 int launch_sparse_eval_points(const double* x, int64_t n, int d, const int32_t* kvec, const double* coef,
                               int64_t nterms, double* y, cudaStream_t st);
+// dimension-incremental driver (dimincr_kernels.cu)
+int launch_pairing(const int32_t* prev, int64_t np, int t, const int32_t* cur, int nt, int32_t* out, cudaStream_t st);
+int launch_assemble_nodes(const double* xl, int64_t n, int tc, const double* tail, int d, double* X, cudaStream_t st);
+int launch_step1_nodes(const double* tail, int d, int t, int K, double* X, cudaStream_t st);
+int launch_c64_to_c32(const c64* a, c32* b, int64_t n, cudaStream_t st);
+int launch_gather_rows(const int32_t* J, int w, const int64_t* idx, int64_t n, int32_t* rows, cudaStream_t st);
 }  // namespace sfft

@@ -96,6 +96,8 @@ struct Plan {
 int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L, const int64_t* M, const int64_t* z,
                 const sfft_params* p, cudaStream_t st);
 int run_pipeline(const PipeArgs& a, cudaStream_t st);
+// Bluestein job for the tables of one M; prec: 0 double, 1 float, 2 double-float; dir 0 forward
+BlueJob make_blue_job(const FftTables* t, int prec, int dir, double scale);
 int upload_jobs(const std::vector<BlueJob>& v, BlueJob** dst, std::vector<void*>* owner);
 uint64_t philox_word0(uint64_t key0, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3);
 double philox_u01(uint64_t key, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3);

@@ -126,22 +126,22 @@ __global__ void k_sop_backward(const InstDesc* __restrict__ insts, const int32_t
     }
 }
 
-// f at arbitrary nodes x [n, d] (double), output complex double (imaginary part 0)
+// f at arbitrary nodes x [n, d] (double), output complex double (imaginary part 0); FP64
 __global__ void k_sop_eval_points(const double* __restrict__ x, int64_t n, int d, const int32_t* __restrict__ triples,
                                   int n_terms, int K, const double* __restrict__ a64, double* y) {
-    __shared__ float sa[kMaxTerms * (kMaxK + 1)];
+    __shared__ double sa[kMaxTerms * (kMaxK + 1)];
     __shared__ int str[kMaxTerms * 3];
-    for (int i = threadIdx.x; i < n_terms * (K + 1); i += blockDim.x) sa[i] = (float)a64[i];
+    for (int i = threadIdx.x; i < n_terms * (K + 1); i += blockDim.x) sa[i] = a64[i];
     for (int i = threadIdx.x; i < n_terms * 3; i += blockDim.x) str[i] = triples[i];
     __syncthreads();
     for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
         double f = 0;
         for (int m = 0; m < n_terms; ++m) {
-            float p = 1;
+            double p = 1;
             for (int u = 0; u < 3; ++u) {
                 double xv = x[j * d + str[3 * m + u]];
-                float c = (float)cospi(2.0 * (xv - floor(xv)));
-                p *= clenshaw<float>(sa + m * (K + 1), K, c);
+                double c = cospi(2.0 * (xv - floor(xv)));
+                p *= clenshaw<double>(sa + m * (K + 1), K, c);
             }
             f += p;
         }
