@@ -201,6 +201,14 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
                            double* const* coef_out, const int64_t* cap, int64_t* n_out_dev);
 
 /*
+ * Status of the last sfft_batch_reconstruct (waits for it): flags host int64 [n_plans] in the
+ * caller's plan order, bit 1 = detected set above its capacity, 2 = more uncertain buckets in
+ * the FP64 guard band than one lattice can re-test (tau below the working precision's
+ * resolution), 4 = output above cap.  Returns SFFT_ECAPACITY if any flag is set.
+ */
+int sfft_batch_flags(sfft_batch* b, int64_t* flags);
+
+/*
  * sfft_sample_sparse_poly for every plan of the batch in shared launches (one bucket scatter,
  * one inverse-transform launch).  Arrays are indexed by the caller's plan order: kvec[i]
  * device int32 [n_terms[i], d_i]; coef[i] device complex double; noise NULL or noise[i] device

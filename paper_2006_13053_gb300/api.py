@@ -244,8 +244,16 @@ class Batch:
         N.check(N.sfft_batch_sample_sparse_poly(self.handle, kp, cp, nt, npp, op))
         return outs
 
-    def results(self):
+    def flags(self):
+        fl = (C.c_int64 * len(self.plans))()
+        rc = N.sfft_batch_flags(self.handle, fl)
+        return rc, list(fl)
+
+    def results(self, check=True):
         (self.stream or torch.cuda.current_stream()).synchronize()
+        if check:
+            rc, _ = self.flags()
+            N.check(rc)
         k = self.nout.cpu().tolist()
         return [(s[:m], c[:m]) for s, c, m in zip(self.supp, self.coef, k)]
 

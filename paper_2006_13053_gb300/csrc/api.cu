@@ -384,12 +384,30 @@ int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L
     SFFT_TRY(upload_jobs(P->jobs_rfwd, &P->d_jobs_rfwd, &P->allocs));
     SFFT_TRY(upload_jobs(P->jobs_samp, &P->d_jobs_samp, &P->allocs));
     SFFT_TRY(upload_jobs(P->jobs_adj, &P->d_jobs_adj, &P->allocs));
-    // hash-count kernel choice and launch shape (one full wave of CTAs)
+    // hash-count kernel choice; lattices split into groups whose bitmaps fit shared memory
     int64_t maxM = *std::max_element(P->M.begin(), P->M.end());
     P->packed = P->kmax <= 127 && maxM <= 32768;
-    P->hash_smem = hash_smem_bytes(d, L, (int)words, P->packed);
-    SFFT_CHECK(P->hash_smem <= 220 * 1024, SFFT_EINVAL,
-               "non-zero bitmap of %lld words does not fit shared memory", (long long)words);
+    const size_t kHashSmem = 200 * 1024;
+    for (int l0 = 0; l0 < L;) {
+        int l1 = l0 + 1;
+        while (l1 < L) {
+            int64_t wds = (l1 + 1 < L ? P->boff[l1 + 1] : words) - P->boff[l0];
+            if (hash_smem_bytes(d, l1 + 1 - l0, wds, P->packed) > kHashSmem) break;
+            ++l1;
+        }
+        int64_t wds = (l1 < L ? P->boff[l1] : words) - P->boff[l0];
+        size_t sm = hash_smem_bytes(d, l1 - l0, wds, P->packed);
+        SFFT_CHECK(sm <= 220 * 1024, SFFT_EINVAL, "the bitmap of lattice %d alone does not fit shared memory", l0);
+        P->hgroups.push_back({l0, l1});
+        P->hsmem.push_back(sm);
+        l0 = l1;
+    }
+    P->hash_smem = *std::max_element(P->hsmem.begin(), P->hsmem.end());
+    if (P->hgroups.size() > 1) {
+        SFFT_TRY(P->alloc((void**)&P->cnt8, (size_t)n));
+        P->h_inst->cnt8 = P->cnt8;
+        SFFT_CU(cudaMemcpy(P->d_inst, P->h_inst, sizeof(InstDesc), cudaMemcpyHostToDevice));
+    }
     return SFFT_OK;
 }
 
@@ -419,7 +437,7 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
     // count rule over all candidates, ascending compaction of Itilde
     SFFT_TRY(mark(a, ST_HASH, st));
     for (const auto& h : a.hash)
-        SFFT_TRY(launch_hash_count(a.d_inst + h.off, h.count, h.d, h.gx, h.smem, h.variant, st));
+        SFFT_TRY(launch_hash_count(a.d_inst + h.off, h.count, h.d, h.gx, h.smem, h.variant, h.l0, h.l1, h.mode, st));
     SFFT_TRY(mark(a, ST_COMPACT, st));
     SFFT_TRY(launch_compact(a.d_inst, ni, st));
     // hashes of Itilde, collision counts, median / hybrid combine
@@ -463,10 +481,16 @@ PipeArgs Plan::pipe_args() {
     a.fwd.push_back(FftLaunch{d_jobs_fwd, L, maxN, fits_smem(prec)});
     a.model.push_back(FftLaunch{d_jobs_model, L, maxN, fits_smem(0)});
     a.rfwd.push_back(FftLaunch{d_jobs_rfwd, L, maxN, fits_smem(prec)});
-    HashGroup h;
-    h.off = 0; h.count = 1; h.d = d; h.gx = hash_grid(); h.smem = hash_smem;
-    h.variant = packed ? (diag_run ? 2 : 1) : 0;
-    a.hash.push_back(h);
+    const int ng = (int)hgroups.size();
+    for (int g = 0; g < ng; ++g) {
+        HashGroup h;
+        h.off = 0; h.count = 1; h.d = d; h.gx = hash_grid(); h.smem = hsmem[g];
+        h.variant = packed ? (diag_run ? 2 : 1) : 0;
+        h.l0 = hgroups[g].first;
+        h.l1 = g + 1 < ng ? hgroups[g].second : -1;
+        h.mode = (g == 0 ? 1 : 0) | (g + 1 == ng ? 2 : 0);
+        a.hash.push_back(h);
+    }
     return a;
 }
 
@@ -603,7 +627,11 @@ int sfft_reconstruct(sfft_plan* plan, const void* samples, int64_t* supp_out, do
     if (n_out) *n_out = c[1];
     P->have_forward = true;
     P->last_nout = c[1];
-    if (c[3] & ERR_GUARD_CAP) { set_error("more than 1024 buckets of one lattice inside the FP64 guard band"); return SFFT_ECAPACITY; }
+    if (c[3] & ERR_GUARD_CAP) {
+        set_error("more than 1024 buckets of one lattice lie inside the FP64 guard band around tau: the zero-test "
+                  "threshold is below what the working precision resolves (raise tau or use an FP64 plan)");
+        return SFFT_ECAPACITY;
+    }
     if (c[3] & ERR_DET_CAP) { set_error("|Itilde| = %lld exceeds detect_cap = %lld", (long long)c[0], (long long)P->cap); return SFFT_ECAPACITY; }
     if (c[3] & ERR_OUT_CAP) { set_error("%lld selected frequencies exceed cap = %lld", (long long)c[1], (long long)cap); return SFFT_ECAPACITY; }
     return SFFT_OK;

@@ -191,6 +191,7 @@ struct InstDesc {
     void* ghat;                // [sum M] complex (prec)
     LatStats* stats;           // [L]
     uint32_t* detbits;         // [ceil(n/32)]
+    uint8_t* cnt8;             // [n] partial counts between lattice groups (plans with several groups)
     int64_t* det;              // [cap] detected indices (ascending)
     int64_t* cnt;              // [8] counters: 0 |Itilde|, 1 n_out, 2 n_guard, 3 error flags
     c64* coef;                 // [cap]

@@ -156,20 +156,36 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
             B->samp.push_back(FftLaunch{dj, (int)js[sm].size(), maxN[sm][0], sm == 1});
         }
     }
-    // hash groups: contiguous runs of equal d
+    // hash launches: contiguous runs of single-group plans with equal d and kernel variant share a
+    // launch (grid.y = instances); plans with several lattice groups get one launch per group
     for (int b = 0; b < n;) {
+        Plan* Pb = B->plans[b];
+        if (Pb->hgroups.size() > 1) {
+            const int ng = (int)Pb->hgroups.size();
+            for (int g = 0; g < ng; ++g) {
+                HashGroup h;
+                h.off = b; h.count = 1; h.d = Pb->d; h.gx = Pb->hash_grid(); h.smem = Pb->hsmem[g];
+                h.variant = Pb->packed ? 1 : 0;
+                h.l0 = Pb->hgroups[g].first;
+                h.l1 = g + 1 < ng ? Pb->hgroups[g].second : -1;
+                h.mode = (g == 0 ? 1 : 0) | (g + 1 == ng ? 2 : 0);
+                A.hash.push_back(h);
+            }
+            ++b;
+            continue;
+        }
         int e = b;
         HashGroup h;
         h.off = b;
-        h.d = B->plans[b]->d;
+        h.d = Pb->d;
         int64_t tiles = 0;
-        while (e < n && B->plans[e]->d == h.d && B->plans[e]->packed == B->plans[b]->packed) {
+        while (e < n && B->plans[e]->d == h.d && B->plans[e]->packed == Pb->packed && B->plans[e]->hgroups.size() == 1) {
             h.smem = std::max(h.smem, B->plans[e]->hash_smem);
             tiles = std::max<int64_t>(tiles, (B->plans[e]->n + 511) / 512);
             ++e;
         }
         h.count = e - b;
-        h.variant = B->plans[b]->packed ? 1 : 0;
+        h.variant = Pb->packed ? 1 : 0;
         int per_sm = std::max<int>(1, std::min<int>(8, (int)((228 * 1024) / (h.smem + 1024))));
         h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (152 * per_sm + h.count - 1) / h.count));
         A.hash.push_back(h);
@@ -289,6 +305,23 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
         SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, B->prec, 0, B->prec, +1, EPI_ADDNOISE, B->d_inst, st));
     SFFT_CU(cudaEventRecord(B->done, st));
     return SFFT_OK;
+}
+
+int sfft_batch_flags(sfft_batch* b, int64_t* flags) {
+    if (!b || !flags) { set_error("null argument"); return SFFT_EINVAL; }
+    Batch* B = reinterpret_cast<Batch*>(b);
+    const int n = (int)B->plans.size();
+    std::vector<int64_t> f(n);
+    SFFT_CU(cudaEventSynchronize(B->done));
+    SFFT_CU(cudaMemcpy(f.data(), B->d_flags, sizeof(int64_t) * n, cudaMemcpyDeviceToHost));
+    int rc = SFFT_OK;
+    for (int i = 0; i < n; ++i) {
+        flags[B->order[i]] = f[i];
+        if (f[i]) rc = SFFT_ECAPACITY;
+    }
+    if (rc != SFFT_OK)
+        set_error("a capacity was exceeded in at least one plan (flags: 1 detected set, 2 FP64 guard band, 4 output)");
+    return rc;
 }
 
 int sfft_batch_timing(sfft_batch* b, int mode, double* ms, int64_t* launches) {

@@ -150,23 +150,26 @@ constexpr int kHashThreads = 256;
 constexpr int kCPT = 2;  // candidates per thread
 
 template <int D>
-__global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __restrict__ insts) {
+__global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __restrict__ insts, int l0, int l1in,
+                                                              int mode) {
     extern __shared__ __align__(16) uint32_t hsm[];
     const InstDesc& I = insts[blockIdx.y];
-    const int L = I.L, nwords = I.nwords;
+    // lattice group [l0, l1): its bitmap words [w0, w1) go to shared memory
+    const int L = I.L, l1 = l1in < 0 ? L : l1in, Lg = l1 - l0;
+    const int w0 = I.boff[l0], w1 = l1 < L ? I.boff[l1] : I.nwords, nwords = w1 - w0;
     uint32_t* bits = hsm;
-    int* sz = reinterpret_cast<int*>(hsm + nwords);     // [L][D]
-    uint32_t* sM = reinterpret_cast<uint32_t*>(sz + L * D);
-    uint32_t* smu = sM + L;
-    uint32_t* soffk = smu + L;
-    uint32_t* sbo = soffk + L;
-    for (int i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = I.nzbits[i];
-    for (int i = threadIdx.x; i < L * D; i += blockDim.x) sz[i] = I.z[i];
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-        sM[i] = (uint32_t)I.Ml[i];
-        smu[i] = I.mu[i];
-        soffk[i] = I.offk[i];
-        sbo[i] = (uint32_t)I.boff[i] * 32u;
+    int* sz = reinterpret_cast<int*>(hsm + nwords);     // [Lg][D]
+    uint32_t* sM = reinterpret_cast<uint32_t*>(sz + Lg * D);
+    uint32_t* smu = sM + Lg;
+    uint32_t* soffk = smu + Lg;
+    uint32_t* sbo = soffk + Lg;
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = I.nzbits[w0 + i];
+    for (int i = threadIdx.x; i < Lg * D; i += blockDim.x) sz[i] = I.z[l0 * D + i];
+    for (int i = threadIdx.x; i < Lg; i += blockDim.x) {
+        sM[i] = (uint32_t)I.Ml[l0 + i];
+        smu[i] = I.mu[l0 + i];
+        soffk[i] = I.offk[l0 + i];
+        sbo[i] = (uint32_t)(I.boff[l0 + i] - w0) * 32u;
     }
     __syncthreads();
     const int64_t n = I.n;
@@ -201,8 +204,8 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __r
         }
         int cnt[kCPT];
 #pragma unroll
-        for (int c = 0; c < kCPT; ++c) cnt[c] = 0;
-        for (int l = 0; l < L; ++l) {
+        for (int c = 0; c < kCPT; ++c) cnt[c] = (mode & 1) || idx[c] >= n ? 0 : I.cnt8[idx[c]];
+        for (int l = 0; l < Lg; ++l) {
             int zl[D];
 #pragma unroll
             for (int t = 0; t < D; ++t) zl[t] = sz[l * D + t];
@@ -218,14 +221,18 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __r
                 r = r >= M ? r - M : r;
                 uint32_t bit = bo + r;
                 cnt[c] += (bits[bit >> 5] >> (bit & 31)) & 1u;
-                if (dhashes && idx[c] < n) dhashes[idx[c] * L + l] = (int32_t)r;
+                if (dhashes && idx[c] < n) dhashes[idx[c] * L + l0 + l] = (int32_t)r;
             }
         }
 #pragma unroll
         for (int c = 0; c < kCPT; ++c) {
             if (idx[c] < n) {
-                if (cnt[c] >= need) atomicOr(&I.detbits[idx[c] >> 5], 1u << (idx[c] & 31));
-                if (dcounts) dcounts[idx[c]] = (uint8_t)cnt[c];
+                if (mode & 2) {
+                    if (cnt[c] >= need) atomicOr(&I.detbits[idx[c] >> 5], 1u << (idx[c] & 31));
+                    if (dcounts) dcounts[idx[c]] = (uint8_t)cnt[c];
+                } else {
+                    I.cnt8[idx[c]] = (uint8_t)cnt[c];
+                }
             }
         }
     }
@@ -245,20 +252,24 @@ template <int D> struct Pack {
 };
 
 template <int D, bool DIAG>
-__global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDesc* __restrict__ insts) {
+__global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDesc* __restrict__ insts, int l0,
+                                                                     int l1in, int mode) {
     extern __shared__ __align__(16) uint32_t hsm[];
     using PK = Pack<D>;
     const InstDesc& I = insts[blockIdx.y];
-    const int L = I.L, nwords = I.nwords;
-    uint32_t* rec = hsm;                       // [L][REC]
-    uint32_t* bits = hsm + L * PK::REC;        // [nwords]
-    for (int i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = I.nzbits[i];
-    for (int l = threadIdx.x; l < L; l += blockDim.x) {
-        uint32_t* r = rec + l * PK::REC;
+    // lattice group [l0, l1): its bitmap words [w0, w1) go to shared memory
+    const int L = I.L, l1 = l1in < 0 ? L : l1in, Lg = l1 - l0;
+    const int w0 = I.boff[l0], w1 = l1 < L ? I.boff[l1] : I.nwords, nwords = w1 - w0;
+    uint32_t* rec = hsm;                       // [Lg][REC]
+    uint32_t* bits = hsm + Lg * PK::REC;       // [nwords]
+    for (int i = threadIdx.x; i < nwords; i += blockDim.x) bits[i] = I.nzbits[w0 + i];
+    for (int g = threadIdx.x; g < Lg; g += blockDim.x) {
+        const int l = l0 + g;
+        uint32_t* r = rec + g * PK::REC;
         r[0] = (uint32_t)I.Ml[l];
         r[1] = I.mu[l];
         r[2] = I.offk[l];
-        r[3] = (uint32_t)I.boff[l] * 32u;
+        r[3] = (uint32_t)(I.boff[l] - w0) * 32u;
         for (int w = 0; w < PK::REC - 4; ++w) {
             uint32_t lo = 0, hi = 0;
             if (2 * w < D) lo = (uint32_t)I.z[l * D + 2 * w] & 0xffffu;
@@ -304,8 +315,8 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
         }
         int cnt[kCPT2];
 #pragma unroll
-        for (int c = 0; c < kCPT2; ++c) cnt[c] = 0;
-        for (int l = 0; l < L; ++l) {
+        for (int c = 0; c < kCPT2; ++c) cnt[c] = (mode & 1) || idx[c] >= n ? 0 : I.cnt8[idx[c]];
+        for (int l = 0; l < Lg; ++l) {
             const uint4* r4 = reinterpret_cast<const uint4*>(rec + l * PK::REC);
             const uint4 cst = r4[0];
             uint32_t zw[PK::REC - 4];
@@ -330,16 +341,20 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
                 uint32_t bit = bo + rr;
                 cnt[c] += __funnelshift_r(bits[bit >> 5], 0u, bit) & 1u;
                 if constexpr (DIAG) {
-                    if (idx[c] < n && I.dhashes) I.dhashes[idx[c] * L + l] = (int32_t)rr;
+                    if (idx[c] < n && I.dhashes) I.dhashes[idx[c] * L + l0 + l] = (int32_t)rr;
                 }
             }
         }
 #pragma unroll
         for (int c = 0; c < kCPT2; ++c) {
             if (idx[c] < n) {
-                if (cnt[c] >= need) atomicOr(&I.detbits[idx[c] >> 5], 1u << (idx[c] & 31));
-                if constexpr (DIAG) {
-                    if (I.dcounts) I.dcounts[idx[c]] = (uint8_t)cnt[c];
+                if (mode & 2) {
+                    if (cnt[c] >= need) atomicOr(&I.detbits[idx[c] >> 5], 1u << (idx[c] & 31));
+                    if constexpr (DIAG) {
+                        if (I.dcounts) I.dcounts[idx[c]] = (uint8_t)cnt[c];
+                    }
+                } else {
+                    I.cnt8[idx[c]] = (uint8_t)cnt[c];
                 }
             }
         }
@@ -769,7 +784,8 @@ int launch_clear(InstDesc* di, int ninst, int clear_det, int clear_coll, int cle
 }
 
 template <int D>
-static int launch_hash_d(const InstDesc* di, int ninst, int gx, size_t smem, int variant, cudaStream_t st) {
+static int launch_hash_d(const InstDesc* di, int ninst, int gx, size_t smem, int variant, int l0, int l1, int mode,
+                         cudaStream_t st) {
     // variant: 0 int32 kernel, 1 packed kernel, 2 packed kernel with diagnostics
     static bool attr[3] = {false, false, false};
     if (variant == 0) {
@@ -777,32 +793,33 @@ static int launch_hash_d(const InstDesc* di, int ninst, int gx, size_t smem, int
             SFFT_CU(cudaFuncSetAttribute(k_hash_count<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
             attr[0] = true;
         }
-        k_hash_count<D><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di);
+        k_hash_count<D><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di, l0, l1, mode);
     } else if (variant == 1) {
         if (!attr[1]) {
             SFFT_CU(cudaFuncSetAttribute(k_hash_count_packed<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
             attr[1] = true;
         }
-        k_hash_count_packed<D, false><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di);
+        k_hash_count_packed<D, false><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di, l0, l1, mode);
     } else {
         if (!attr[2]) {
             SFFT_CU(cudaFuncSetAttribute(k_hash_count_packed<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
             attr[2] = true;
         }
-        k_hash_count_packed<D, true><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di);
+        k_hash_count_packed<D, true><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di, l0, l1, mode);
     }
     return launch_check("k_hash_count");
 }
 
-size_t hash_smem_bytes(int d, int L, int nwords, bool packed) {
+size_t hash_smem_bytes(int d, int L, int64_t nwords, bool packed) {
     if (!packed) return sizeof(uint32_t) * (size_t)nwords + sizeof(int32_t) * (size_t)L * (d + 4);
     const int ZW = (d + 1) / 2, REC = 4 + ((ZW + 3) / 4) * 4;
     return sizeof(uint32_t) * ((size_t)nwords + (size_t)L * REC);
 }
 
-int launch_hash_count(const InstDesc* di, int ninst, int d, int gx, size_t smem, int variant, cudaStream_t st) {
+int launch_hash_count(const InstDesc* di, int ninst, int d, int gx, size_t smem, int variant, int l0, int l1, int mode,
+                      cudaStream_t st) {
     switch (d) {
-#define SFFT_HD(D) case D: return launch_hash_d<D>(di, ninst, gx, smem, variant, st);
+#define SFFT_HD(D) case D: return launch_hash_d<D>(di, ninst, gx, smem, variant, l0, l1, mode, st);
         SFFT_HD(1) SFFT_HD(2) SFFT_HD(3) SFFT_HD(4) SFFT_HD(5) SFFT_HD(6) SFFT_HD(7) SFFT_HD(8)
         SFFT_HD(9) SFFT_HD(10) SFFT_HD(11) SFFT_HD(12) SFFT_HD(13) SFFT_HD(14) SFFT_HD(15) SFFT_HD(16)
         SFFT_HD(17) SFFT_HD(18) SFFT_HD(19) SFFT_HD(20) SFFT_HD(21) SFFT_HD(22) SFFT_HD(23) SFFT_HD(24)

@@ -4,8 +4,11 @@
 
 namespace sfft {
 // variant: 0 int32 inner products, 1 packed (int8 k, int16 z, dp2a), 2 packed with diagnostics
-int launch_hash_count(const InstDesc* di, int ninst, int d, int gx, size_t smem, int variant, cudaStream_t st);
-size_t hash_smem_bytes(int d, int L, int nwords, bool packed);
+// lattice group [l0, l1) (l1 < 0: through the last lattice); mode bit 0: first group (counts start
+// at 0, else from cnt8), bit 1: last group (apply the count rule, else store counts in cnt8)
+int launch_hash_count(const InstDesc* di, int ninst, int d, int gx, size_t smem, int variant, int l0, int l1, int mode,
+                      cudaStream_t st);
+size_t hash_smem_bytes(int d, int L, int64_t nwords, bool packed);
 int launch_zero_test(const LatDesc* dl, int nlat, InstDesc* di, int prec, double kappa_u, cudaStream_t st);
 int launch_compact(InstDesc* di, int ninst, cudaStream_t st);
 int launch_det_hashes(const InstDesc* di, int ninst, int64_t maxdet, cudaStream_t st);

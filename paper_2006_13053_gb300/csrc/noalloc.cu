@@ -178,7 +178,7 @@ extern "C" int sfft_detect_noalloc(int d, const int32_t* cand, int64_t n_cand, i
     SFFT_TRY(launch_check("k_nz_from_ghat"));
     int per_sm = std::max<int>(1, std::min<int>(8, (int)((228 * 1024) / (smem + 1024))));
     int gx = (int)std::max<int64_t>(1, std::min<int64_t>((n_cand + 511) / 512, (int64_t)152 * per_sm));
-    SFFT_TRY(launch_hash_count(dI, 1, d, gx, smem, packed ? 1 : 0, st));
+    SFFT_TRY(launch_hash_count(dI, 1, d, gx, smem, packed ? 1 : 0, 0, -1, 3, st));
     SFFT_TRY(launch_compact(dI, 1, st));
     int64_t cnt0 = 0;
     SFFT_CU(cudaMemcpyAsync(&cnt0, S + o_cnt, sizeof(int64_t), cudaMemcpyDeviceToHost, st));

@@ -16,6 +16,7 @@ struct FftLaunch {
 // one launch of the hash-count kernel over a contiguous range of instances of equal d
 struct HashGroup {
     int off = 0, count = 0, d = 0, gx = 1, variant = 0;
+    int l0 = 0, l1 = -1, mode = 3;  // lattice group and first/last flags (see launch_hash_count)
     size_t smem = 0;
 };
 
@@ -77,6 +78,9 @@ struct Plan {
     BlueJob *d_jobs_samp = nullptr, *d_jobs_adj = nullptr;
     size_t hash_smem = 0;
     bool packed = false;          // |k| <= 127 and M <= 32768: packed dp2a hash kernel
+    std::vector<std::pair<int, int>> hgroups;  // lattice groups whose bitmaps fit shared memory
+    std::vector<size_t> hsmem;                 // shared memory of each group
+    uint8_t* cnt8 = nullptr;
     bool diag_run = false;        // the current reconstruct writes per-candidate diagnostics
     bool have_forward = false;
     cudaEvent_t io_ev = nullptr;  // recorded after each upload of h_inst (staging reuse guard)

@@ -460,3 +460,36 @@ def test_batch_sampler_matches_plan_sampler(G):
         ref = p.sample_sparse_poly(k, c, z)
         torch.cuda.synchronize()
         assert torch.equal(o, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_large_lattices_multi_group_hash(G, prec):
+    """M = 100003 (> 32768: int32 hash kernel; bitmap of 25 lattices ~ 320 KB: two lattice groups
+    with partial counts; Bluestein length 202500: global work buffer) vs the oracle."""
+    import torch
+    d, n, s, L = 3, 3000, 20, 25
+    M = O.next_prime_above(100000)
+    cand = S.uniform_distinct(n, d, -30, 30, 21)
+    sup = S.support_indices(n, s, 21)
+    c = S.coef_mag_phase(s, 1, 10, 21)
+    z = S.generators(L, d, M, 21)
+    y = O.sample_sparse_poly(cand[sup], c, z, M)
+    if prec:
+        y = y.astype(np.complex64).astype(np.complex128)
+    tr = 1e-10 if prec == 0 else 1e-3  # FP32: above the guard band 32 u log2(N) rms / max
+    ref = O.reconstruct(cand, y, z, M, tau_rel=tr, want_counts=True)
+    plan = G.Plan(T(cand), s, L=L, M=[M] * L, z=z, precision=prec, tau_rel=tr)
+    ys = T(y, torch.complex64 if prec else torch.complex128)
+    supp, coef, info = plan.reconstruct(ys, diag=True, counts=True)
+    assert np.array_equal(info["counts"].cpu().numpy(), ref.counts)
+    assert np.array_equal(supp.cpu().numpy(), ref.supp)
+    assert relmax(coef.cpu().numpy(), ref.coef) <= (1e-10 if prec == 0 else 1e-4)
+    # the same plan inside a batch with a small single-group plan
+    cand2, sup2, c2, z2, M2, L2 = cfg1(2)
+    y2 = O.sample_sparse_poly(cand2[sup2], c2, z2, M2)
+    ref2 = O.reconstruct(cand2, y2.astype(np.complex64).astype(np.complex128) if prec else y2, z2, M2, tau_rel=tr)
+    p2 = G.Plan(T(cand2), 20, L=L2, M=[M2] * L2, z=z2, precision=prec, tau_rel=tr)
+    B = G.Batch([plan, p2])
+    res = B.reconstruct([ys, T(y2, torch.complex64 if prec else torch.complex128)])
+    assert np.array_equal(res[0][0].cpu().numpy(), ref.supp)
+    assert np.array_equal(res[1][0].cpu().numpy(), ref2.supp)
