@@ -201,6 +201,16 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
                            double* const* coef_out, const int64_t* cap, int64_t* n_out_dev);
 
 /*
+ * Autotuner: runs sfft_batch_reconstruct on the given buffers (reps timed runs per candidate
+ * after one warm-up) for hash-kernel grids of 1/2, 1, 2 and 4 waves of resident CTAs and for
+ * lattice transforms of 256 or 512 threads per CTA, times the affected stage with CUDA events,
+ * keeps the fastest shapes for later calls (a captured graph is re-captured) and reports them
+ * (hash_waves, fft_threads: optional host outputs).  Synchronises the batch stream.
+ */
+int sfft_batch_autotune(sfft_batch* b, const void* const* samples, int64_t* const* supp_out, double* const* coef_out,
+                        const int64_t* cap, int reps, double* hash_waves, int* fft_threads);
+
+/*
  * Status of the last sfft_batch_reconstruct (waits for it): flags host int64 [n_plans] in the
  * caller's plan order, bit 1 = detected set above its capacity, 2 = more uncertain buckets in
  * the FP64 guard band than one lattice can re-test (tau below the working precision's

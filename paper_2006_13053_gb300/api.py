@@ -244,6 +244,16 @@ class Batch:
         N.check(N.sfft_batch_sample_sparse_poly(self.handle, kp, cp, nt, npp, op))
         return outs
 
+    def autotune(self, samples, reps=2):
+        """Pick the fastest hash grid and transform CTA size on these inputs; returns them."""
+        n = len(self.plans)
+        sp = (C.c_void_p * n)(*[s.data_ptr() for s in samples])
+        hw = C.c_double()
+        ft = C.c_int()
+        N.check(N.sfft_batch_autotune(self.handle, sp, self._ps, self._pc, self._cap, int(reps), C.byref(hw),
+                                      C.byref(ft)))
+        return hw.value, ft.value
+
     def flags(self):
         fl = (C.c_int64 * len(self.plans))()
         rc = N.sfft_batch_flags(self.handle, fl)

@@ -429,7 +429,8 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
     // Algorithm 2 line 2: lattice DFTs (normalised by 1/M) + per-lattice statistics
     SFFT_TRY(mark(a, ST_FFT_FWD, st));
     for (const auto& f : a.fwd)
-        SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, a.prec, a.prec, a.prec, -1, EPI_ANALYZE, a.d_inst, st));
+        SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, a.prec, a.prec, a.prec, -1, EPI_ANALYZE, a.d_inst, st,
+                                  nullptr, nullptr, f.threads));
     // zero test with FP64 re-tests inside the guard band (Remark 2.3)
     SFFT_TRY(mark(a, ST_ZERO_TEST, st));
     const double u = a.prec ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
@@ -453,10 +454,12 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
         // residual at the nodes in FP64: r = f - IDFT(C)
         SFFT_TRY(mark(a, ST_FFT_MODEL, st));
         for (const auto& f : a.model)
-            SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, 2, 0, a.prec, +1, EPI_RESID, a.d_inst, st));
+            SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, 2, 0, a.prec, +1, EPI_RESID, a.d_inst, st, nullptr,
+                                      nullptr, f.threads));
         SFFT_TRY(mark(a, ST_FFT_RFWD, st));
         for (const auto& f : a.rfwd)
-            SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, a.prec, a.prec, a.prec, -1, EPI_PLAIN, a.d_inst, st));
+            SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, a.prec, a.prec, a.prec, -1, EPI_PLAIN, a.d_inst, st,
+                                      nullptr, nullptr, f.threads));
         SFFT_TRY(mark(a, ST_DELTA, st));
         SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, 1, st));
     }
@@ -484,7 +487,7 @@ PipeArgs Plan::pipe_args() {
     const int ng = (int)hgroups.size();
     for (int g = 0; g < ng; ++g) {
         HashGroup h;
-        h.off = 0; h.count = 1; h.d = d; h.gx = hash_grid(); h.smem = hsmem[g];
+        h.off = 0; h.count = 1; h.d = d; h.gx = h.gx0 = hash_grid(); h.smem = hsmem[g];
         h.variant = packed ? (diag_run ? 2 : 1) : 0;
         h.l0 = hgroups[g].first;
         h.l1 = g + 1 < ng ? hgroups[g].second : -1;

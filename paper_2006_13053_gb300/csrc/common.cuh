@@ -167,7 +167,7 @@ struct LatStats {
 struct InstDesc;
 int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, bool sm, int prec, int in_prec, int out_prec, int sign,
                      int epi, const InstDesc* insts, cudaStream_t st, void* out_base = nullptr,
-                     const void* aux_base = nullptr);
+                     const void* aux_base = nullptr, int threads = 512);
 size_t blue_smem_limit();
 
 // ------------------------------------------------------------------ instance / lattice descriptors

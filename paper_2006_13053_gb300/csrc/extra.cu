@@ -164,7 +164,7 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
             const int ng = (int)Pb->hgroups.size();
             for (int g = 0; g < ng; ++g) {
                 HashGroup h;
-                h.off = b; h.count = 1; h.d = Pb->d; h.gx = Pb->hash_grid(); h.smem = Pb->hsmem[g];
+                h.off = b; h.count = 1; h.d = Pb->d; h.gx = h.gx0 = Pb->hash_grid(); h.smem = Pb->hsmem[g];
                 h.variant = Pb->packed ? 1 : 0;
                 h.l0 = Pb->hgroups[g].first;
                 h.l1 = g + 1 < ng ? Pb->hgroups[g].second : -1;
@@ -188,6 +188,8 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
         h.variant = Pb->packed ? 1 : 0;
         int per_sm = std::max<int>(1, std::min<int>(8, (int)((228 * 1024) / (h.smem + 1024))));
         h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (152 * per_sm + h.count - 1) / h.count));
+        h.gx0 = h.gx;
+        h.tiles = tiles;
         A.hash.push_back(h);
         b = e;
     }
@@ -304,6 +306,65 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
     for (const auto& f : B->samp)
         SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, B->prec, 0, B->prec, +1, EPI_ADDNOISE, B->d_inst, st));
     SFFT_CU(cudaEventRecord(B->done, st));
+    return SFFT_OK;
+}
+
+int sfft_batch_autotune(sfft_batch* b, const void* const* samples, int64_t* const* supp_out, double* const* coef_out,
+                        const int64_t* cap, int reps, double* hash_waves, int* fft_threads) {
+    if (!b) { set_error("batch is NULL"); return SFFT_EINVAL; }
+    Batch* B = reinterpret_cast<Batch*>(b);
+    if (reps < 1) reps = 1;
+    const bool was_timing = B->timing;
+    // one eager, timed run per candidate; the stage timer isolates the tuned stage
+    auto timed = [&](int stage, double* ms) -> int {
+        B->timing = true;
+        double acc = 0;
+        for (int r = 0; r <= reps; ++r) {  // the first run warms up
+            double m[ST_COUNT] = {0};
+            int64_t nl[ST_COUNT] = {0};
+            SFFT_TRY(B->collect());
+            for (int s = 0; s < ST_COUNT; ++s) { B->stage_ms[s] = 0; B->stage_n[s] = 0; }
+            SFFT_TRY(sfft_batch_reconstruct(b, samples, supp_out, coef_out, cap, nullptr));
+            SFFT_TRY(B->collect());
+            for (int s = 0; s < ST_COUNT; ++s) { m[s] = B->stage_ms[s]; nl[s] = B->stage_n[s]; }
+            if (r > 0) acc += m[stage];
+            (void)nl;
+        }
+        *ms = acc / reps;
+        return SFFT_OK;
+    };
+    // hash kernel: grids of {1/2, 1, 2, 4} waves
+    const double mults[4] = {0.5, 1.0, 2.0, 4.0};
+    double best = 1e30, bestm = 1.0;
+    for (double m : mults) {
+        for (auto& h : B->args.hash)
+            h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(h.tiles, 1), (int64_t)llround(h.gx0 * m)));
+        double ms = 0;
+        SFFT_TRY(timed(ST_HASH, &ms));
+        if (ms < best) { best = ms; bestm = m; }
+    }
+    for (auto& h : B->args.hash)
+        h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(h.tiles, 1), (int64_t)llround(h.gx0 * bestm)));
+    // lattice transforms: 256 or 512 threads per CTA
+    const int ths[2] = {256, 512};
+    best = 1e30;
+    int bestt = 512;
+    for (int th : ths) {
+        for (auto* v : {&B->args.fwd, &B->args.model, &B->args.rfwd})
+            for (auto& f : *v) f.threads = th;
+        double ms = 0;
+        SFFT_TRY(timed(ST_FFT_FWD, &ms));
+        if (ms < best) { best = ms; bestt = th; }
+    }
+    for (auto* v : {&B->args.fwd, &B->args.model, &B->args.rfwd})
+        for (auto& f : *v) f.threads = bestt;
+    B->timing = was_timing;
+    for (int s = 0; s < ST_COUNT; ++s) { B->stage_ms[s] = 0; B->stage_n[s] = 0; }
+    // a captured graph holds the old launch shapes
+    if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+    if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+    if (hash_waves) *hash_waves = bestm;
+    if (fft_threads) *fft_threads = bestt;
     return SFFT_OK;
 }
 

@@ -487,7 +487,8 @@ size_t blue_smem_limit() { return 207 * 1024; }
 
 template <class T, class TI, class TO>
 static int launch_t(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign, int epi, const InstDesc* insts,
-                    cudaStream_t st, void* ob, const void* ab) {
+                    cudaStream_t st, void* ob, const void* ab, int threads) {
+    if (threads < 64 || threads > kBlueThreads || threads % 32) threads = kBlueThreads;
     if (njobs == 0) return SFFT_OK;
     if (sm) {
         size_t bytes = (size_t)maxN * sizeof(cplx<T>);
@@ -501,31 +502,31 @@ static int launch_t(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign
                                          (int)blue_smem_limit()));
             attr_done = true;
         }
-        k_bluestein<T, TI, TO, true><<<njobs, kBlueThreads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
+        k_bluestein<T, TI, TO, true><<<njobs, threads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
     } else {
-        k_bluestein<T, TI, TO, false><<<njobs, kBlueThreads, 0, st>>>(djobs, sign, epi, insts, ob, ab);
+        k_bluestein<T, TI, TO, false><<<njobs, threads, 0, st>>>(djobs, sign, epi, insts, ob, ab);
     }
     return launch_check("k_bluestein");
 }
 
 int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, bool sm, int prec, int in_prec, int out_prec, int sign,
-                     int epi, const InstDesc* insts, cudaStream_t st, void* ob, const void* ab) {
+                     int epi, const InstDesc* insts, cudaStream_t st, void* ob, const void* ab, int threads) {
     // prec: 0 double, 1 float, 2 double-float; in/out: 0 double, 1 float
     if (prec == 2) {
         if (in_prec != 0) { set_error("double-float transforms take double input"); return SFFT_EINVAL; }
-        if (out_prec) return launch_t<df64, double, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
-        return launch_t<df64, double, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
+        if (out_prec) return launch_t<df64, double, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab, threads);
+        return launch_t<df64, double, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab, threads);
     }
     int key = prec * 4 + in_prec * 2 + out_prec;
     switch (key) {
-        case 0: return launch_t<double, double, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
-        case 1: return launch_t<double, double, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
-        case 2: return launch_t<double, float, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
-        case 3: return launch_t<double, float, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
-        case 4: return launch_t<float, double, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
-        case 5: return launch_t<float, double, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
-        case 6: return launch_t<float, float, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
-        default: return launch_t<float, float, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab);
+        case 0: return launch_t<double, double, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab, threads);
+        case 1: return launch_t<double, double, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab, threads);
+        case 2: return launch_t<double, float, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab, threads);
+        case 3: return launch_t<double, float, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab, threads);
+        case 4: return launch_t<float, double, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab, threads);
+        case 5: return launch_t<float, double, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab, threads);
+        case 6: return launch_t<float, float, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab, threads);
+        default: return launch_t<float, float, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab, threads);
     }
 }
 

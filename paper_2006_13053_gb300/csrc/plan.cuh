@@ -12,10 +12,12 @@ struct FftLaunch {
     const BlueJob* jobs = nullptr;
     int njobs = 0, maxN = 0;
     bool sm = true;
+    int threads = 512;  // CTA size (autotuned)
 };
 // one launch of the hash-count kernel over a contiguous range of instances of equal d
 struct HashGroup {
-    int off = 0, count = 0, d = 0, gx = 1, variant = 0;
+    int off = 0, count = 0, d = 0, gx = 1, gx0 = 1, variant = 0;  // gx0: one-wave grid (autotune base)
+    int64_t tiles = 1 << 30;                                       // CTA count beyond which CTAs idle
     int l0 = 0, l1 = -1, mode = 3;  // lattice group and first/last flags (see launch_hash_count)
     size_t smem = 0;
 };

@@ -163,6 +163,21 @@ def sop_candidate_set(triples: np.ndarray, d: int, kmax: int, n_total: int, box:
     return np.ascontiguousarray(np.concatenate([core, np.array(fill, dtype=np.int64)]).astype(np.int32))
 
 
+def uneven_instances(n_inst: int, seed: int, d_range=(5, 20), n_range=(2 ** 14, 2 ** 22), s_range=(100, 10000),
+                     box: int = 32):
+    """Parameters of an uneven batch: per instance d ~ U{d_range}, |Gamma| and s log-uniform in
+    their ranges (s <= |Gamma|), and an instance seed.  Returns a list of dicts (no arrays)."""
+    g = rng(seed, S_MISC)
+    out = []
+    for i in range(n_inst):
+        d = int(g.integers(d_range[0], d_range[1] + 1))
+        n = int(round(np.exp(g.uniform(np.log(n_range[0]), np.log(n_range[1])))))
+        s = int(round(np.exp(g.uniform(np.log(s_range[0]), np.log(s_range[1])))))
+        n = min(n, (2 * box + 1) ** d)
+        out.append({"d": d, "n": n, "s": min(s, n), "box": box, "seed": int(seed) * 100003 + i})
+    return out
+
+
 def uniform_tail(n: int, seed: int, stream: int = S_TAIL) -> np.ndarray:
     g = rng(seed, stream)
     return g.random(n)
