@@ -145,8 +145,25 @@ def kernel_count(batch_plans, n_inst, refine=True):
     hash_groups = len({p.d for p in batch_plans})
     n = 3 + 1 + 1 + 1 + hash_groups + 1 + 1 + 1 + 1 + 1
     if refine:
-        n += 1 + 1 + 1 + 1 + 1  # clear C, scatter, FP64 model IDFT, refinement DFT, update
+        n += 1 + 1 + 1  # clear C, scatter, median update of ghat - C
     return n
+
+
+# double-float roofline: FP32-pipe instructions per df64 operation as implemented (Dekker sum:
+# two-sum 6 + low words 2 + renormalisation 3 = 11; FMA product: 1 + 3 FMA + 3 = 7) and the
+# conventional 5 N log2 N radix-2 flop mix (6 additions : 4 multiplications per butterfly)
+DF64_FP32_INSTR_PER_FLOP = (6 * 11 + 4 * 7) / 10.0
+FP32_LANES = 152 * 128
+
+
+def df64_peak_tflops(sm_mhz):
+    return FP32_LANES * sm_mhz * 1e6 / DF64_FP32_INSTR_PER_FLOP / 1e12
+
+
+def bluestein_flops(N, M):
+    """Algorithmic flops of one Bluestein transform: two length-N FFTs (5 N log2 N each), the
+    chirp product of the input (6 M), the filter product (6 N), output chirp and scale (8 M)."""
+    return 2 * 5 * N * math.log2(N) + 6 * N + 14 * M
 
 
 def traffic_from_profiles(kernel, units):
@@ -226,9 +243,10 @@ def run_native(a, rank, world):
     stage_ms = {k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1] > 0}
     out = {"metric": METRIC, "value": value, "unit": "reconstructions/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "f32", "data": "synthetic",
+           "dtype": "df64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "global_batch": world * n_inst, "lattices": L, "lattice_size": M,
-                      "precision": "FP32 samples/FFT/median, FP64 residual + update, exact int32 hashing",
+                      "precision": "FP32 samples; lattice DFTs in double-float (float pairs on the FP32 pipes); "
+                                   "FP32 zero test + median; FP64 refinement (ghat - C) and update; exact int32 hashing",
                       "l2": "inputs larger than L2 (16 x 40 MiB candidate sets per step)",
                       "parallelism": f"replicas x{world}"},
            "cand_lattice_evals_per_s": world * n_inst * NCAND * L / (ms / 1000.0),
@@ -251,17 +269,19 @@ def run_native(a, rank, world):
         out["roofline"] = {"kernel": "k_hash_count", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
                            "frac": ach / hbm, "peak_source": src,
                            "traffic": traffic_from_profiles("k_hash_count", n_inst * NCAND)}
-    elif dom in ("fft_model64",):
-        # FP64 Bluestein: 2 transforms of length N=20736 (5 N log2 N flops each) + 2 N pointwise per lattice
+    elif dom == "fft_fwd":
+        # double-float forward lattice DFTs (FP32 + refinement): FP32-pipe instruction bound
         N = 20736
-        flops = n_inst * L * (2 * 5 * N * math.log2(N) + 6 * N)
+        flops = n_inst * L * bluestein_flops(N, M)
         ach = flops / (per_launch_ms / 1000.0) / 1e12
-        out["roofline"] = {"kernel": "k_bluestein<double> (refinement model IDFT)", "bound": "alu", "achieved": ach,
-                           "peak": 1.25, "unit": "TFLOP/s", "frac": ach / 1.25,
-                           "peak_source": "nominal FP64 (no measured FP64 peak in MEASURED_PEAKS.json)",
-                           "traffic": traffic_from_profiles("k_bluestein_f64", n_inst * L)}
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        pk = df64_peak_tflops(mhz)
+        out["roofline"] = {"kernel": "k_bluestein<df64> (forward lattice DFTs)", "bound": "alu", "achieved": ach,
+                           "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                           "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {mhz:.0f} MHz / "
+                                          f"{DF64_FP32_INSTR_PER_FLOP:.1f} FP32 instructions per df64 flop",
+                           "traffic": traffic_from_profiles("k_bluestein_df64", n_inst * L)}
     else:
-        N = 20736
         bytes_ = n_inst * L * (M * 8 * 2)  # samples in, buckets out (FP32 complex)
         ach = bytes_ / (per_launch_ms / 1000.0) / 1e9
         out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",

@@ -94,7 +94,7 @@ sfft_batch_autotune = _sig("sfft_batch_autotune", _i32, [_vp, _vp, _vp, _vp, _vp
 sfft_batch_flags = _sig("sfft_batch_flags", _i32, [_vp, _vp])
 sfft_batch_timing = _sig("sfft_batch_timing", _i32, [_vp, _i32, _vp, _vp])
 STAGES = ["clear", "fft_fwd", "zero_test", "hash_count", "compact", "det_hashes", "combine", "refine_scatter",
-          "fft_model64", "fft_refine", "refine_update", "select"]
+          "refine_update", "select"]
 sfft_dimincr_params_default = _sig("sfft_dimincr_params_default", None, [_P(DimIncrParams)])
 sfft_dim_incremental = _sig("sfft_dim_incremental", _i32,
                             [_i32, _vp, _vp, _P(DimIncrParams), _vp, _vp, _vp, _vp, _i64, _P(_i64), _P(_i64), _vp])

@@ -169,45 +169,39 @@ BlueJob make_blue_job(const FftTables* t, int prec, int dir, double scale) {
 }
 
 bool Plan::fits_smem(int tprec) const {
-    size_t e = tprec ? sizeof(c32) : sizeof(c64);
+    size_t e = tprec == 1 ? sizeof(c32) : sizeof(c64);  // double and double-float: 16 bytes
     return (size_t)maxN * e <= blue_smem_limit();
 }
+
+// FP32 plans with refinement run the forward transform in double-float: the refinement's
+// residual spectrum is then r_hat = ghat - C (eq. 2.3), accurate to ~1e-14 without transforms.
+int Plan::fwd_prec() const { return prec == SFFT_FP32 && p.refine ? 2 : prec; }
 
 int Plan::build_jobs() {
     const size_t e = esz();
     char* ghat_b = (char*)ghat;
-    char* resid_b = (char*)resid;
-    char* rhat_b = (char*)rhat;
-    jobs_fwd.clear(); jobs_model.clear(); jobs_rfwd.clear(); jobs_samp.clear(); jobs_adj.clear();
+    const int fp = fwd_prec();
+    jobs_fwd.clear(); jobs_samp.clear(); jobs_adj.clear();
     for (int l = 0; l < L; ++l) {
         const FftTables* t = tabs[l];
         const int64_t o = soff[l];
-        // forward analyse: ghat = DFT(samples)/M (plan precision)
-        BlueJob a = make_blue_job(t, prec, 0, 1.0 / (double)M[l]);
+        // forward analyse: ghat = DFT(samples)/M (double-float: low words to ghat_lo)
+        BlueJob a = make_blue_job(t, fp, 0, 1.0 / (double)M[l]);
         a.io_flags = 1; a.io_off = o; a.inst = 0;
         a.out = ghat_b + o * e;
+        a.aux = ghat_lo ? (const void*)(ghat_lo + o) : nullptr;
         a.stat = stats + l;
-        a.scratch = fits_smem(prec) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
+        a.scratch = fits_smem(fp) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
         jobs_fwd.push_back(a);
-        // refinement model: resid = samples - IDFT(C), double-float arithmetic, FP64 in/out
-        BlueJob m = make_blue_job(t, 2, 1, 1.0);
-        m.in = C + o; m.out = resid_b + o * e; m.io_flags = 2; m.io_off = o; m.inst = 0;
-        m.scratch = fits_smem(0) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
-        jobs_model.push_back(m);
-        // refinement forward: rhat = DFT(resid)/M (plan precision)
-        BlueJob r = make_blue_job(t, prec, 0, 1.0 / (double)M[l]);
-        r.in = resid_b + o * e; r.out = rhat_b + o * e;
-        r.scratch = a.scratch;
-        jobs_rfwd.push_back(r);
         // sampler: out (launch argument) = IDFT(C) + noise (launch argument), plan precision
         BlueJob sj = make_blue_job(t, prec, 1, 1.0);
         sj.in = C + o; sj.io_flags = 16 | 32; sj.io_off = o; sj.inst = 0;
-        sj.scratch = a.scratch;
+        sj.scratch = fits_smem(prec) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
         jobs_samp.push_back(sj);
         // adjoint: out (launch argument) = (1/M) IDFT(C), plan precision
         BlueJob aj = make_blue_job(t, prec, 1, 1.0 / (double)M[l]);
         aj.in = C + o; aj.io_flags = 4; aj.io_off = o;
-        aj.scratch = a.scratch;
+        aj.scratch = sj.scratch;
         jobs_adj.push_back(aj);
     }
     return SFFT_OK;
@@ -348,9 +342,8 @@ int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L
     SFFT_TRY(P->alloc((void**)&P->outpos, sizeof(int32_t) * cap));
     SFFT_TRY(P->alloc((void**)&P->coll, sizeof(int32_t) * P->sumM));
     SFFT_TRY(P->alloc((void**)&P->C, sizeof(c64) * P->sumM));
-    SFFT_TRY(P->alloc(&P->rhat, e * P->sumM));
-    SFFT_TRY(P->alloc(&P->resid, e * P->sumM));
-    if (!P->fits_smem(0) || !P->fits_smem(P->prec))
+    if (P->fwd_prec() == 2) SFFT_TRY(P->alloc((void**)&P->ghat_lo, sizeof(c32) * P->sumM));
+    if (!P->fits_smem(P->fwd_prec()) || !P->fits_smem(P->prec))
         SFFT_TRY(P->alloc(&P->scratch, sizeof(c64) * (size_t)P->maxN * L));
     SFFT_TRY(P->alloc((void**)&P->sop_a, sizeof(double) * 2 * 16 * 129));
     SFFT_TRY(P->alloc((void**)&P->sop_tri, sizeof(int32_t) * 3 * 16));
@@ -366,7 +359,7 @@ int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L
     I.cand = cand; I.z = dz; I.Ml = dM; I.mu = dmu; I.offk = doffk; I.soff = dsoff; I.boff = dboff;
     I.nzbits = P->nzbits; I.ghat = P->ghat; I.stats = P->stats; I.detbits = P->detbits; I.det = P->det;
     I.cnt = P->cnt; I.coef = P->coef; I.H = P->H; I.sel = P->sel; I.coll = P->coll; I.C = P->C;
-    I.rhat = P->rhat; I.resid = P->resid; I.outpos = P->outpos;
+    I.ghat_lo = P->ghat_lo; I.outpos = P->outpos;
     SFFT_CU(cudaEventCreateWithFlags(&P->io_ev, cudaEventDisableTiming));
     SFFT_TRY(P->alloc((void**)&P->d_inst, sizeof(InstDesc)));
     SFFT_CU(cudaMemcpy(P->d_inst, &I, sizeof(InstDesc), cudaMemcpyHostToDevice));
@@ -380,8 +373,6 @@ int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L
     SFFT_CU(cudaMemcpy(P->d_lats, lats.data(), sizeof(LatDesc) * L, cudaMemcpyHostToDevice));
     SFFT_TRY(P->build_jobs());
     SFFT_TRY(upload_jobs(P->jobs_fwd, &P->d_jobs_fwd, &P->allocs));
-    SFFT_TRY(upload_jobs(P->jobs_model, &P->d_jobs_model, &P->allocs));
-    SFFT_TRY(upload_jobs(P->jobs_rfwd, &P->d_jobs_rfwd, &P->allocs));
     SFFT_TRY(upload_jobs(P->jobs_samp, &P->d_jobs_samp, &P->allocs));
     SFFT_TRY(upload_jobs(P->jobs_adj, &P->d_jobs_adj, &P->allocs));
     // hash-count kernel choice; lattices split into groups whose bitmaps fit shared memory
@@ -429,11 +420,13 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
     // Algorithm 2 line 2: lattice DFTs (normalised by 1/M) + per-lattice statistics
     SFFT_TRY(mark(a, ST_FFT_FWD, st));
     for (const auto& f : a.fwd)
-        SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, a.prec, a.prec, a.prec, -1, EPI_ANALYZE, a.d_inst, st,
-                                  nullptr, nullptr, f.threads));
-    // zero test with FP64 re-tests inside the guard band (Remark 2.3)
+        SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, a.fwd_prec, a.prec, a.prec, -1, EPI_ANALYZE, a.d_inst,
+                                  st, nullptr, nullptr, f.threads));
+    // zero test with FP64 re-tests inside the guard band (Remark 2.3); unit roundoff of the
+    // transform arithmetic (double-float: 2^-44, a bound with margin for its ~48-bit operations)
     SFFT_TRY(mark(a, ST_ZERO_TEST, st));
-    const double u = a.prec ? 5.9604644775390625e-08 : 1.1102230246251565e-16;
+    const double u = a.fwd_prec == 1 ? 5.9604644775390625e-08 : a.fwd_prec == 2 ? 5.684341886080802e-14
+                                                                                 : 1.1102230246251565e-16;
     SFFT_TRY(launch_zero_test(a.d_lats, a.nlat, a.d_inst, a.prec, 32.0 * u, st));
     // count rule over all candidates, ascending compaction of Itilde
     SFFT_TRY(mark(a, ST_HASH, st));
@@ -451,15 +444,7 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
         SFFT_TRY(mark(a, ST_SCATTER, st));
         SFFT_TRY(launch_clear(a.d_inst, ni, 0, 0, 1, st));
         SFFT_TRY(launch_scatter_coef(a.d_inst, ni, st));
-        // residual at the nodes in FP64: r = f - IDFT(C)
-        SFFT_TRY(mark(a, ST_FFT_MODEL, st));
-        for (const auto& f : a.model)
-            SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, 2, 0, a.prec, +1, EPI_RESID, a.d_inst, st, nullptr,
-                                      nullptr, f.threads));
-        SFFT_TRY(mark(a, ST_FFT_RFWD, st));
-        for (const auto& f : a.rfwd)
-            SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, a.prec, a.prec, a.prec, -1, EPI_PLAIN, a.d_inst, st,
-                                      nullptr, nullptr, f.threads));
+        // residual spectrum r_hat = ghat - C at the buckets of Itilde (eq. 2.3), median update
         SFFT_TRY(mark(a, ST_DELTA, st));
         SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, 1, st));
     }
@@ -479,11 +464,9 @@ int Plan::hash_grid() const {
 PipeArgs Plan::pipe_args() {
     PipeArgs a;
     a.ninst = 1; a.d_inst = d_inst; a.d_lats = d_lats; a.nlat = L;
-    a.prec = prec; a.maxcap = cap;
+    a.prec = prec; a.fwd_prec = fwd_prec(); a.maxcap = cap;
     a.hybrid = p.combine == SFFT_COMBINE_HYBRID; a.refine = p.refine;
-    a.fwd.push_back(FftLaunch{d_jobs_fwd, L, maxN, fits_smem(prec)});
-    a.model.push_back(FftLaunch{d_jobs_model, L, maxN, fits_smem(0)});
-    a.rfwd.push_back(FftLaunch{d_jobs_rfwd, L, maxN, fits_smem(prec)});
+    a.fwd.push_back(FftLaunch{d_jobs_fwd, L, maxN, fits_smem(fwd_prec())});
     const int ng = (int)hgroups.size();
     for (int g = 0; g < ng; ++g) {
         HashGroup h;

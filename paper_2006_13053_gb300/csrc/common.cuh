@@ -126,7 +126,8 @@ int64_t bluestein_size(int64_t M);
 struct BlueJob {
     const void* in;      // input complex (element type by launch), M entries
     void* out;           // output complex, M entries
-    const void* aux;     // epilogue input (noise / samples for the residual), M entries
+    const void* aux;     // epilogue side buffer: noise input (EPI_ADDNOISE) or low-word output
+                         // (EPI_ANALYZE of a double-float transform with float output), M entries
     void* scratch;       // global work buffer of N complex (used when the buffer is not in smem)
     const void* tw;      // twiddles of the transform precision (full table)
     const void* twa;     // FP32 two-level twiddle tables
@@ -148,9 +149,9 @@ struct BlueJob {
 // epilogue modes of the Bluestein kernel
 enum BlueEpi : int {
     EPI_PLAIN = 0,    // out = scale * y
-    EPI_ANALYZE = 1,  // out = y / M; per-lattice max|y| and sum |x|^2 recorded
+    EPI_ANALYZE = 1,  // out = y / M; per-lattice max|y| and sum |x|^2 recorded; a double-float
+                      // transform with float output also writes the low words of y / M to aux
     EPI_ADDNOISE = 2, // out = y + aux (aux complex double)
-    EPI_RESID = 3,    // out = aux - y (aux in the output precision)
 };
 
 struct LatStats {
@@ -162,8 +163,8 @@ struct LatStats {
     int pad;
 };
 
-// One launch of Bluestein transforms over a device job array.  prec/in_prec/out_prec: 0 =
-// double, 1 = float.  sm: work buffer in shared memory (all jobs need N <= maxN fitting).
+// One launch of Bluestein transforms over a device job array.  prec: 0 double, 1 float,
+// 2 double-float; in_prec/out_prec: 0 double, 1 float.  sm: work buffer in shared memory (all jobs need N <= maxN fitting).
 struct InstDesc;
 int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, bool sm, int prec, int in_prec, int out_prec, int sign,
                      int epi, const InstDesc* insts, cudaStream_t st, void* out_base = nullptr,
@@ -199,8 +200,7 @@ struct InstDesc {
     uint8_t* sel;              // [cap, 2] lattice of the Re / Im median
     int32_t* coll;             // [sum M] collision counts
     c64* C;                    // [sum M] bucket scatter buffer
-    void* rhat;                // [sum M] complex (prec)
-    void* resid;               // [sum M] complex (prec)
+    c32* ghat_lo;              // [sum M] low words of a double-float forward transform, or NULL
     int32_t* outpos;           // [cap] detected position of output q
     // ---- per call
     const void* samples;       // [sum M] complex (prec)

@@ -110,11 +110,12 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
     for (int i : idx) B->plans.push_back(reinterpret_cast<Plan*>(plans[i]));
     SFFT_CU(cudaMallocHost((void**)&B->h_inst, sizeof(InstDesc) * n));
     std::vector<LatDesc> lats;
-    std::vector<BlueJob> jf[2], jm[2], jr[2], js[2];  // [0] global scratch, [1] shared memory
-    int maxN[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    std::vector<BlueJob> jf[2], js[2];  // [0] global scratch, [1] shared memory
+    int maxN[2][2] = {{0, 0}, {0, 0}};
     PipeArgs& A = B->args;
     A.ninst = n;
     A.prec = B->prec;
+    A.fwd_prec = P0->fwd_prec();
     A.refine = P0->p.refine;
     for (int b = 0; b < n; ++b) {
         Plan* P = B->plans[b];
@@ -124,15 +125,14 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
         for (int l = 0; l < P->L; ++l)
             lats.push_back(LatDesc{b, l, (int)P->M[l], (int)P->tabs[l]->N, P->soff[l], P->boff[l], 0,
                                    (const double*)P->tabs[l]->dft64});
-        const int sp = P->fits_smem(P->prec) ? 1 : 0, s64 = P->fits_smem(0) ? 1 : 0;
+        const int sf = P->fits_smem(P->fwd_prec()) ? 1 : 0, sp = P->fits_smem(P->prec) ? 1 : 0;
         for (int l = 0; l < P->L; ++l) {
-            BlueJob f = P->jobs_fwd[l], m = P->jobs_model[l], r = P->jobs_rfwd[l], s = P->jobs_samp[l];
-            f.inst = b; m.inst = b; r.inst = b; s.inst = b;
-            jf[sp].push_back(f); jm[s64].push_back(m); jr[sp].push_back(r); js[sp].push_back(s);
+            BlueJob f = P->jobs_fwd[l], s = P->jobs_samp[l];
+            f.inst = b; s.inst = b;
+            jf[sf].push_back(f); js[sp].push_back(s);
         }
-        maxN[sp][0] = std::max(maxN[sp][0], P->maxN);
-        maxN[s64][1] = std::max(maxN[s64][1], P->maxN);
-        maxN[sp][2] = std::max(maxN[sp][2], P->maxN);
+        maxN[sf][0] = std::max(maxN[sf][0], P->maxN);
+        maxN[sp][1] = std::max(maxN[sp][1], P->maxN);
     }
     A.nlat = (int)lats.size();
     SFFT_TRY(B->alloc((void**)&B->d_lats, sizeof(LatDesc) * lats.size()));
@@ -142,18 +142,15 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
     A.d_inst = B->d_inst;
     A.d_lats = B->d_lats;
     for (int sm = 1; sm >= 0; --sm) {
-        std::vector<BlueJob>* lists[3] = {&jf[sm], &jm[sm], &jr[sm]};
-        std::vector<FftLaunch>* dst[3] = {&A.fwd, &A.model, &A.rfwd};
-        for (int k = 0; k < 3; ++k) {
-            if (lists[k]->empty()) continue;
+        if (!jf[sm].empty()) {
             BlueJob* dj = nullptr;
-            SFFT_TRY(upload_jobs(*lists[k], &dj, &B->allocs));
-            dst[k]->push_back(FftLaunch{dj, (int)lists[k]->size(), maxN[sm][k], sm == 1});
+            SFFT_TRY(upload_jobs(jf[sm], &dj, &B->allocs));
+            A.fwd.push_back(FftLaunch{dj, (int)jf[sm].size(), maxN[sm][0], sm == 1});
         }
         if (!js[sm].empty()) {
             BlueJob* dj = nullptr;
             SFFT_TRY(upload_jobs(js[sm], &dj, &B->allocs));
-            B->samp.push_back(FftLaunch{dj, (int)js[sm].size(), maxN[sm][0], sm == 1});
+            B->samp.push_back(FftLaunch{dj, (int)js[sm].size(), maxN[sm][1], sm == 1});
         }
     }
     // hash launches: contiguous runs of single-group plans with equal d and kernel variant share a
@@ -350,14 +347,12 @@ int sfft_batch_autotune(sfft_batch* b, const void* const* samples, int64_t* cons
     best = 1e30;
     int bestt = 512;
     for (int th : ths) {
-        for (auto* v : {&B->args.fwd, &B->args.model, &B->args.rfwd})
-            for (auto& f : *v) f.threads = th;
+        for (auto& f : B->args.fwd) f.threads = th;
         double ms = 0;
         SFFT_TRY(timed(ST_FFT_FWD, &ms));
         if (ms < best) { best = ms; bestt = th; }
     }
-    for (auto* v : {&B->args.fwd, &B->args.model, &B->args.rfwd})
-        for (auto& f : *v) f.threads = bestt;
+    for (auto& f : B->args.fwd) f.threads = bestt;
     B->timing = was_timing;
     for (int s = 0; s < ST_COUNT; ++s) { B->stage_ms[s] = 0; B->stage_n[s] = 0; }
     // a captured graph holds the old launch shapes

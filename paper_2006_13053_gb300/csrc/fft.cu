@@ -194,17 +194,8 @@ template <class D, class S> __device__ __forceinline__ D scv(S v) {
 }
 template <class D, class S> __device__ __forceinline__ cplx<D> ccv(cplx<S> a) { return {scv<D>(a.x), scv<D>(a.y)}; }
 
-// load of a transform input: zero entries (most buckets of a scattered sparse vector) skip the
-// double -> double-float conversion, which runs on the FP64 pipe
-template <class T, class TI> __device__ __forceinline__ cplx<T> load_in(const cplx<TI>* p) {
-    if constexpr (std::is_same<T, df64>::value && std::is_same<TI, double>::value) {
-        const longlong2 raw = *reinterpret_cast<const longlong2*>(p);
-        if ((raw.x | raw.y) == 0) return cplx<T>{df64{0.f, 0.f}, df64{0.f, 0.f}};
-        return ccv<T>(cplx<double>{__longlong_as_double(raw.x), __longlong_as_double(raw.y)});
-    } else {
-        return ccv<T>(*p);
-    }
-}
+// load of a transform input in the transform precision
+template <class T, class TI> __device__ __forceinline__ cplx<T> load_in(const cplx<TI>* p) { return ccv<T>(*p); }
 
 // read-only loads of table entries in the transform precision
 __device__ __forceinline__ cplx<df64> ldg(const cplx<df64>* p) {
@@ -412,23 +403,19 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
         cplx<T> X = inv ? mulc(buf[h], w) : buf[h] * w;
         X = X * sc;
         if (epi == EPI_PLAIN || epi == EPI_ANALYZE) {
-            out[h] = ccv<TO>(X);
+            if constexpr (std::is_same<T, df64>::value && std::is_same<TO, float>::value) {
+                // float output of a double-float value: high words out, low words to aux
+                out[h] = cplx<TO>{X.x.hi, X.y.hi};
+                if (auxp) reinterpret_cast<c32*>(const_cast<void*>(auxp))[h] = c32{X.x.lo, X.y.lo};
+            } else {
+                out[h] = ccv<TO>(X);
+            }
             if (epi == EPI_ANALYZE) mx2 = fmax(mx2, scv<R>(abs2(X)));
-        } else if (epi == EPI_ADDNOISE) {
+        } else {  // EPI_ADDNOISE
             const c64* aux = reinterpret_cast<const c64*>(auxp);
             c64 r = ccv<double>(X);
             if (aux) r = r + aux[h];
             out[h] = ccv<TO>(r);
-        } else {  // EPI_RESID: out = aux - X, aux in the output precision
-            const cplx<TO>* aux = reinterpret_cast<const cplx<TO>*>(auxp);
-            if constexpr (std::is_same<T, df64>::value) {  // difference in double-float
-                cplx<T> a = ccv<T>(aux[h]);
-                out[h] = ccv<TO>(a - X);
-            } else {  // difference in double
-                c64 a = ccv<double>(aux[h]);
-                c64 x = ccv<double>(X);
-                out[h] = ccv<TO>(c64{a.x - x.x, a.y - x.y});
-            }
         }
     }
     if (epi == EPI_ANALYZE) {
@@ -512,10 +499,9 @@ static int launch_t(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign
 int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, bool sm, int prec, int in_prec, int out_prec, int sign,
                      int epi, const InstDesc* insts, cudaStream_t st, void* ob, const void* ab, int threads) {
     // prec: 0 double, 1 float, 2 double-float; in/out: 0 double, 1 float
-    if (prec == 2) {
-        if (in_prec != 0) { set_error("double-float transforms take double input"); return SFFT_EINVAL; }
-        if (out_prec) return launch_t<df64, double, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab, threads);
-        return launch_t<df64, double, double>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab, threads);
+    if (prec == 2) {  // double-float: float samples in, float high words out (low words to aux)
+        if (in_prec != 1 || out_prec != 1) { set_error("double-float transforms take and give float"); return SFFT_EINVAL; }
+        return launch_t<df64, float, float>(djobs, njobs, maxN, sm, sign, epi, insts, st, ob, ab, threads);
     }
     int key = prec * 4 + in_prec * 2 + out_prec;
     switch (key) {

@@ -49,6 +49,24 @@ __device__ c64 bucket_dft64(const cplx<TS>* __restrict__ x, int M, int h, const 
     return r;
 }
 
+// block-wide maximum of a double (all threads get the result)
+__device__ __forceinline__ double block_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double m = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) m = fmax(m, red[i]);
+        red[64] = m;
+    }
+    __syncthreads();
+    const double r = red[64];
+    __syncthreads();
+    return r;
+}
+
 constexpr int kZtThreads = 512;
 constexpr int kGuardCap = 1024;
 
@@ -64,9 +82,22 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
     LatStats& S = I.stats[D.l];
     const int M = D.M;
     cplx<TS>* g = reinterpret_cast<cplx<TS>*>(I.ghat) + D.soff;
+    // low words of a double-float transform: ghat = g + glo to ~2^-44 relative accuracy
+    c32* glo = I.ghat_lo ? I.ghat_lo + D.soff : nullptr;
     const cplx<TS>* x = reinterpret_cast<const cplx<TS>*>(I.samples) + D.soff;
     const c64* tab = reinterpret_cast<const c64*>(D.dft64);
     const double band = kappa_u_log * log2((double)D.N) * S.rms;
+    auto full = [&](int h) -> c64 {  // the bucket in the transform's full precision
+        cplx<TS> v = g[h];
+        c64 r = {(double)v.x, (double)v.y};
+        if (glo) { c32 w = glo[h]; r.x += (double)w.x; r.y += (double)w.y; }
+        return r;
+    };
+    auto store = [&](int h, c64 v) {  // replace a bucket by its FP64 direct value
+        cplx<TS> hi = cvt<TS>(v);
+        g[h] = hi;
+        if (glo) glo[h] = c32{(float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y)};
+    };
     if (threadIdx.x == 0) { gcount = 0; s_max64 = 0; }
     __syncthreads();
     // Squared magnitudes are formed in the working precision and compared with bounds widened
@@ -89,11 +120,18 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
         __syncthreads();
         int nc = min(gcount, kGuardCap);
         if (gcount > kGuardCap && threadIdx.x == 0) atomicOr((unsigned long long*)&I.cnt[3], (unsigned long long)ERR_GUARD_CAP);
-        for (int i = 0; i < nc; ++i) {
-            c64 v = bucket_dft64(x, M, glist[i], tab, red);
-            if (threadIdx.x == 0) {
-                s_max64 = fmax(s_max64, sqrt(abs2(v)));
-                g[glist[i]] = cvt<TS>(v);
+        if (glo) {  // the double-float value is the maximum's FP64-class value
+            double m = 0;
+            for (int i = threadIdx.x; i < nc; i += blockDim.x) m = fmax(m, sqrt(abs2(full(glist[i]))));
+            m = block_max(m, red);
+            if (threadIdx.x == 0) s_max64 = m;
+        } else {
+            for (int i = 0; i < nc; ++i) {
+                c64 v = bucket_dft64(x, M, glist[i], tab, red);
+                if (threadIdx.x == 0) {
+                    s_max64 = fmax(s_max64, sqrt(abs2(v)));
+                    store(glist[i], v);
+                }
             }
         }
         __syncthreads();
@@ -116,9 +154,19 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
             cplx<TS> v = g[h];
             TS a2 = v.x * v.x + v.y * v.y;
             nz = a2 > hi2;
-            if (!nz && a2 >= lo2) {  // uncertain: decided by the FP64 re-test below
-                int p = atomicAdd(&gcount, 1);
-                if (p < kGuardCap) glist[p] = h;
+            if (!nz && a2 >= lo2) {
+                // uncertain in the working precision: the double-float value decides outside
+                // the transform's error band, the FP64 re-test below inside it
+                bool open = true;
+                if (glo) {
+                    const double a = sqrt(abs2(full(h)));
+                    if (a > thi) { nz = true; open = false; }
+                    else if (a < tlo) open = false;
+                }
+                if (open) {
+                    int p = atomicAdd(&gcount, 1);
+                    if (p < kGuardCap) glist[p] = h;
+                }
             }
         }
         uint32_t b = __ballot_sync(0xffffffffu, nz);
@@ -135,7 +183,7 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
             uint32_t bit = 1u << (h & 31);
             if (a > tau) atomicOr(&words[h >> 5], bit);
             else atomicAnd(&words[h >> 5], ~bit);
-            g[h] = cvt<TS>(v);  // the stored bucket is the FP64 value that decided the test
+            store(h, v);  // the stored bucket is the FP64 value that decided the test
         }
     }
     if (threadIdx.x == 0 && nc) atomicAdd((unsigned long long*)&I.cnt[2], (unsigned long long)nc);
@@ -465,37 +513,61 @@ __device__ __forceinline__ void warp_median(T va, T vb, int L, int lane, T& med,
     lsel = first ? owner : owner + 32;
 }
 
-// Median combine (eq. 2.6) or the Remark 2.8 hybrid combine on the detected set.
-// mode 0: coef = combine(ghat)     mode 1: coef += median(rhat)  (refinement update)
+// Order-preserving integer key of a double (-0 mapped to +0, NaN never occurs): the warp
+// median ranks keys with integer compares instead of the low-rate FP64 pipe.
+__device__ __forceinline__ long long ord_key(double v) {
+    long long b = __double_as_longlong(v);
+    if (b == (long long)0x8000000000000000ull) b = 0;
+    return b ^ ((b >> 63) & 0x7fffffffffffffffll);
+}
+
+// median of doubles across the warp (values and tie rule of warp_median)
+__device__ __forceinline__ void warp_median_f64(double va, double vb, int L, int lane, double& med, int& lsel) {
+    long long km;
+    warp_median<long long>(ord_key(va), ord_key(vb), L, lane, km, lsel);
+    const int owner = lsel & 31;
+    const double a = __shfl_sync(0xffffffffu, va, owner), b = __shfl_sync(0xffffffffu, vb, owner);
+    med = lsel < 32 ? a : b;
+}
+
+// Median combine (eq. 2.6) or the Remark 2.8 hybrid combine on the detected set: coef = combine(ghat)
 template <class TS>
-__global__ void k_combine(const InstDesc* __restrict__ insts, int mode) {
+__global__ void k_combine(const InstDesc* __restrict__ insts) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nd = min(I.cnt[0], I.cap);
     const int warps = blockDim.x >> 5;
     const int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
     if (q >= nd) return;
     const int lane = threadIdx.x & 31, L = I.L;
-    const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(mode == 0 ? I.ghat : I.rhat);
-    cplx<TS> va = {0, 0}, vb = {0, 0};
+    const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
+    const c32* glo = I.ghat_lo;  // low words of a double-float transform (or NULL)
+    auto bucket = [&](int64_t b) -> c64 {
+        const cplx<TS> v = g[b];
+        c64 r = {(double)v.x, (double)v.y};
+        if (glo) { const c32 w = glo[b]; r.x += (double)w.x; r.y += (double)w.y; }
+        return r;
+    };
+    c64 va = {0, 0}, vb = {0, 0};
     int fa = 0, fb = 0;  // collision-free flags (hybrid)
     if (lane < L) {
         int h = I.H[q * L + lane];
-        va = g[I.soff[lane] + h];
-        if (I.combine == SFFT_COMBINE_HYBRID && mode == 0) fa = I.coll[I.soff[lane] + h] == 1;
+        va = bucket(I.soff[lane] + h);
+        if (I.combine == SFFT_COMBINE_HYBRID) fa = I.coll[I.soff[lane] + h] == 1;
     }
     if (lane + 32 < L) {
         int h = I.H[q * L + lane + 32];
-        vb = g[I.soff[lane + 32] + h];
-        if (I.combine == SFFT_COMBINE_HYBRID && mode == 0) fb = I.coll[I.soff[lane + 32] + h] == 1;
+        vb = bucket(I.soff[lane + 32] + h);
+        if (I.combine == SFFT_COMBINE_HYBRID) fb = I.coll[I.soff[lane + 32] + h] == 1;
     }
-    TS mre, mim;
+    // float buckets convert to double exactly, so the ranking equals the working-precision one
+    double mre, mim;
     int lre, lim;
-    warp_median<TS>(va.x, vb.x, L, lane, mre, lre);
-    warp_median<TS>(va.y, vb.y, L, lane, mim, lim);
-    c64 out = {(double)mre, (double)mim};
-    if (I.combine == SFFT_COMBINE_HYBRID && mode == 0) {
-        double sr = (fa ? (double)va.x : 0.0) + (fb ? (double)vb.x : 0.0);
-        double si = (fa ? (double)va.y : 0.0) + (fb ? (double)vb.y : 0.0);
+    warp_median_f64(va.x, vb.x, L, lane, mre, lre);
+    warp_median_f64(va.y, vb.y, L, lane, mim, lim);
+    c64 out = {mre, mim};
+    if (I.combine == SFFT_COMBINE_HYBRID) {
+        double sr = (fa ? va.x : 0.0) + (fb ? vb.x : 0.0);
+        double si = (fa ? va.y : 0.0) + (fb ? vb.y : 0.0);
         int nf = fa + fb;
         for (int o = 16; o > 0; o >>= 1) {
             sr += __shfl_xor_sync(0xffffffffu, sr, o);
@@ -505,14 +577,48 @@ __global__ void k_combine(const InstDesc* __restrict__ insts, int mode) {
         if (nf > 0) out = c64{sr / nf, si / nf};
     }
     if (lane == 0) {
-        if (mode == 0) {
-            I.coef[q] = out;
-            I.sel[2 * q] = (uint8_t)lre;
-            I.sel[2 * q + 1] = (uint8_t)lim;
-        } else {
-            c64 c = I.coef[q];
-            I.coef[q] = c64{c.x + out.x, c.y + out.y};
+        I.coef[q] = out;
+        I.sel[2 * q] = (uint8_t)lre;
+        I.sel[2 * q + 1] = (uint8_t)lim;
+    }
+}
+
+// Refinement update: the residual f - sum_{k in Itilde} c_k e^{2 pi i k.x} has the lattice DFT
+// r_hat_h = ghat_h - C_h (aliasing formula, eq. 2.3), C_h = sum of c_k over the detected k with
+// h_kl = h.  c_k += median_l Re r_hat + i median_l Im r_hat at h_kl, all in FP64; ghat is the
+// forward transform (FP64, or a double-float pair hi + lo for FP32 plans with refinement).
+template <class TS>
+__global__ void k_refine_update(const InstDesc* __restrict__ insts) {
+    const InstDesc& I = insts[blockIdx.y];
+    const int64_t nd = min(I.cnt[0], I.cap);
+    const int warps = blockDim.x >> 5;
+    const int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
+    if (q >= nd) return;
+    const int lane = threadIdx.x & 31, L = I.L;
+    const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
+    const c32* glo = I.ghat_lo;
+    auto rhat = [&](int l) -> c64 {
+        const int64_t b = I.soff[l] + I.H[q * L + l];
+        const cplx<TS> v = g[b];
+        c64 r = {(double)v.x, (double)v.y};
+        if (glo) {
+            const c32 w = glo[b];
+            r.x += (double)w.x;
+            r.y += (double)w.y;
         }
+        const c64 c = I.C[b];
+        return c64{r.x - c.x, r.y - c.y};
+    };
+    c64 va = {0, 0}, vb = {0, 0};
+    if (lane < L) va = rhat(lane);
+    if (lane + 32 < L) vb = rhat(lane + 32);
+    double mre, mim;
+    int lre, lim;
+    warp_median_f64(va.x, vb.x, L, lane, mre, lre);
+    warp_median_f64(va.y, vb.y, L, lane, mim, lim);
+    if (lane == 0) {
+        c64 c = I.coef[q];
+        I.coef[q] = c64{c.x + mre, c.y + mim};
     }
 }
 
@@ -855,8 +961,13 @@ int launch_collisions(const InstDesc* di, int ninst, cudaStream_t st) {
 int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int mode, cudaStream_t st) {
     int gx = (int)((maxdet + 7) / 8);
     if (gx < 1) gx = 1;
-    if (prec) k_combine<float><<<dim3(gx, ninst), 256, 0, st>>>(di, mode);
-    else k_combine<double><<<dim3(gx, ninst), 256, 0, st>>>(di, mode);
+    if (mode == 1) {
+        if (prec) k_refine_update<float><<<dim3(gx, ninst), 256, 0, st>>>(di);
+        else k_refine_update<double><<<dim3(gx, ninst), 256, 0, st>>>(di);
+        return launch_check("k_refine_update");
+    }
+    if (prec) k_combine<float><<<dim3(gx, ninst), 256, 0, st>>>(di);
+    else k_combine<double><<<dim3(gx, ninst), 256, 0, st>>>(di);
     return launch_check("k_combine");
 }
 

@@ -25,7 +25,7 @@ struct HashGroup {
 // optional per-stage CUDA-event timing of the stage sequence
 enum Stage : int {
     ST_CLEAR = 0, ST_FFT_FWD, ST_ZERO_TEST, ST_HASH, ST_COMPACT, ST_DET_HASH, ST_COMBINE,
-    ST_SCATTER, ST_FFT_MODEL, ST_FFT_RFWD, ST_DELTA, ST_SELECT, ST_COUNT
+    ST_SCATTER, ST_DELTA, ST_SELECT, ST_COUNT
 };
 struct StageTimer {
     cudaEvent_t ev[ST_COUNT + 1];
@@ -35,11 +35,12 @@ struct StageTimer {
 struct PipeArgs {
     StageTimer* timer = nullptr;
     int ninst = 1, nlat = 0, prec = 0;
+    int fwd_prec = 0;  // arithmetic of the forward transforms (2 = double-float for FP32 + refinement)
     int64_t maxcap = 0;
     int hybrid = 0, refine = 0;
     InstDesc* d_inst = nullptr;
     const LatDesc* d_lats = nullptr;
-    std::vector<FftLaunch> fwd, model, rfwd;
+    std::vector<FftLaunch> fwd;
     std::vector<HashGroup> hash;
 };
 
@@ -66,8 +67,7 @@ struct Plan {
     int32_t* outpos = nullptr;
     int32_t* coll = nullptr;
     c64* C = nullptr;
-    void* rhat = nullptr;
-    void* resid = nullptr;
+    c32* ghat_lo = nullptr;  // low words of the double-float forward transform (FP32 + refinement)
     void* scratch = nullptr;
     double* sop_a = nullptr;
     int32_t* sop_tri = nullptr;
@@ -75,8 +75,8 @@ struct Plan {
     InstDesc* h_inst = nullptr;  // pinned
     int64_t* h_cnt = nullptr;    // pinned
     LatDesc* d_lats = nullptr;
-    std::vector<BlueJob> jobs_fwd, jobs_model, jobs_rfwd, jobs_samp, jobs_adj;
-    BlueJob *d_jobs_fwd = nullptr, *d_jobs_model = nullptr, *d_jobs_rfwd = nullptr;
+    std::vector<BlueJob> jobs_fwd, jobs_samp, jobs_adj;
+    BlueJob* d_jobs_fwd = nullptr;
     BlueJob *d_jobs_samp = nullptr, *d_jobs_adj = nullptr;
     size_t hash_smem = 0;
     bool packed = false;          // |k| <= 127 and M <= 32768: packed dp2a hash kernel
@@ -93,6 +93,7 @@ struct Plan {
     void release();
     int alloc(void** p, size_t bytes);
     size_t esz() const;
+    int fwd_prec() const;           // arithmetic of the forward transform
     bool fits_smem(int tprec) const;
     int build_jobs();
     int hash_grid() const;

@@ -50,4 +50,4 @@ def test_uneven_batch_graph_autotune_matches_oracle():
             assert np.array_equal(supp.cpu().numpy(), ref.supp)
             b = np.asarray(ref.coef)
             if b.size:
-                assert np.max(np.abs(coef.cpu().numpy() - b)) <= 1e-4 * np.max(np.abs(b))
+                assert np.max(np.abs(coef.cpu().numpy() - b)) <= 1e-9 * np.max(np.abs(b))

@@ -2,8 +2,9 @@
 
 Tolerances: hashes, counts, detected sets, supports and collision counts bit-exact; FP64
 coefficients within 1e-10 relative (max-norm over the output, relative to max |c|); FP32
-path (with one FP64 refinement step) within 1e-4 relative; FP32 FFT buckets within the
-guard band 32 u log2(N) rms(x) that the zero test assumes.
+plans with one refinement step (double-float lattice DFTs, unit roundoff <= 2^-44, FP64
+update) within TOL_FP32_REFINE; FP32 plans without refinement within 1e-4; FP32 FFT buckets
+within the guard band 32 u log2(N) rms(x) that the zero test assumes.
 """
 import math
 
@@ -14,6 +15,10 @@ import oracle as O
 import sfft_synth as S
 
 pytestmark = pytest.mark.gpu
+
+# FP32 samples, double-float transforms: the error of ghat is about 32 * 2^-44 * log2(N) * rms
+# (< 1e-10 of max |ghat|); the median combine and the FP64 update are 1-Lipschitz in ghat
+TOL_FP32_REFINE = 1e-9
 
 
 @pytest.fixture(scope="module")
@@ -134,7 +139,7 @@ def test_hashes_counts_detected_bit_exact(G, which):
     assert np.array_equal(info["counts"].cpu().numpy(), ref.counts)
     assert np.array_equal(info["detected"].cpu().numpy(), ref.detected)
     assert np.array_equal(supp.cpu().numpy(), ref.supp)
-    tol = 1e-10 if which == "cfg1" else 1e-4
+    tol = 1e-10 if which == "cfg1" else TOL_FP32_REFINE
     assert relmax(coef.cpu().numpy(), ref.coef) <= tol
 
 
@@ -172,7 +177,7 @@ def test_config2_reduced_fp32_refine(G, seed):
     supp, coef, info = plan.reconstruct(T(y32), diag=True)
     assert np.array_equal(info["detected"].cpu().numpy(), ref.detected)
     assert np.array_equal(supp.cpu().numpy(), ref.supp)
-    assert relmax(coef.cpu().numpy(), ref.coef) <= 1e-4
+    assert relmax(coef.cpu().numpy(), ref.coef) <= TOL_FP32_REFINE
     # the FP64 path on the same samples agrees with the FP64 oracle to 1e-10
     plan64 = G.Plan(T(cand), len(sup), L=L, M=[M] * L, z=z, precision=0, refine=1, tau_abs=tau, tau_rel=0.0)
     s64, c64 = plan64.reconstruct(T(y32.astype(np.complex128)))
@@ -197,7 +202,7 @@ def test_config2_full_size_one_seed(G):
     supp, coef, info = plan.reconstruct(T(y), diag=True)
     assert np.array_equal(info["detected"].cpu().numpy(), ref.detected)
     assert np.array_equal(supp.cpu().numpy(), ref.supp)
-    assert relmax(coef.cpu().numpy(), ref.coef) <= 1e-4
+    assert relmax(coef.cpu().numpy(), ref.coef) <= TOL_FP32_REFINE
     # sampled hashes of 4096 candidates, bit-exact
     idx = np.random.default_rng(0).choice(cand.shape[0], 4096, replace=False)
     _, _, info2 = plan.reconstruct(T(y), diag=True, hashes=True)
@@ -434,7 +439,7 @@ def test_batch_matches_single_plans(G, use_graph):
             st.synchronize()
         for (supp, coef), ref in zip(res, refs):
             assert np.array_equal(supp.cpu().numpy(), ref.supp)
-            assert relmax(coef.cpu().numpy(), ref.coef) <= 1e-4
+            assert relmax(coef.cpu().numpy(), ref.coef) <= TOL_FP32_REFINE
     t = B.timing(1)
     B.reconstruct(samples)
     t = B.timing(-1)
