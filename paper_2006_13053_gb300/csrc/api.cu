@@ -153,6 +153,8 @@ BlueJob make_blue_job(const FftTables* t, int prec, int dir, double scale) {
     J.N = (int)t->N;
     J.nstages = t->nstages;
     for (int s = 0; s < t->nstages; ++s) J.radix[s] = (uint8_t)t->radix[s];
+    J.npass = (uint8_t)plan_passes(t->radix, t->nstages, prec == 1 ? pass_maxprod<float>() : pass_maxprod<double>(),
+                                   J.pass_r);
     if (prec == 1) {
         J.tw = t->tw32; J.chirp = t->chirp32; J.filt = t->filt32[dir];
     } else if (prec == 0) {

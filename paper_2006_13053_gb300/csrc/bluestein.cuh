@@ -1,0 +1,393 @@
+// Device code of the batched Bluestein transforms (Algorithm 2, line 2): a length-M DFT becomes
+// a cyclic convolution of length N = 2^a 3^b 5^c >= 2M-1, computed by an in-place mixed-radix
+// decimation-in-frequency FFT (natural order in, digit-reversed out), a pointwise product with
+// the precomputed filter (itself stored digit-reversed) and the matching decimation-in-time
+// inverse (digit-reversed in, natural order out), so no reordering pass is needed.  One CTA
+// transforms one lattice; the work buffer lives in shared memory when N complex values fit,
+// otherwise in an L2-resident global scratch buffer.  Included by one translation unit per
+// arithmetic type (fft_f64.cu, fft_f32.cu, fft_df64.cu).
+#pragma once
+#include <math.h>
+
+#include <type_traits>
+
+#include "common.cuh"
+
+namespace sfft {
+
+// ================================================================== device arithmetic helpers
+// scalar conversion between float, double and df64 (direct for equal types)
+template <class D, class S> __device__ __forceinline__ D scv(S v) {
+    if constexpr (std::is_same<D, S>::value) return v;
+    else if constexpr (std::is_same<D, df64>::value) {
+        if constexpr (std::is_same<S, float>::value) return df64{v, 0.f};
+        else return from_d<df64>((double)v);
+    }
+    else if constexpr (std::is_same<S, df64>::value) {
+        if constexpr (std::is_same<D, float>::value) return v.hi + v.lo;
+        else return (double)v.hi + (double)v.lo;
+    } else return (D)v;
+}
+template <class D, class S> __device__ __forceinline__ cplx<D> ccv(cplx<S> a) { return {scv<D>(a.x), scv<D>(a.y)}; }
+
+// load of a transform input in the transform precision
+template <class T, class TI> __device__ __forceinline__ cplx<T> load_in(const cplx<TI>* p) { return ccv<T>(*p); }
+
+// read-only loads of table entries in the transform precision
+__device__ __forceinline__ cplx<df64> ldg(const cplx<df64>* p) {
+    float4 v = __ldg(reinterpret_cast<const float4*>(p));
+    return {df64{v.x, v.y}, df64{v.z, v.w}};
+}
+
+// ================================================================== device butterflies
+// R-point DFT in registers: y_p = sum_q v_q omega^{pq}, omega = exp(S * 2 pi i / R), S = -1 / +1
+constexpr double kC1 = 0.309016994374947424102293417182819059;   // cos(2 pi/5)
+constexpr double kC2 = -0.809016994374947424102293417182819059;  // cos(4 pi/5)
+constexpr double kS1 = 0.951056516295153572116439333379382143;   // sin(2 pi/5)
+constexpr double kS2 = 0.587785252292473129168705954639072769;   // sin(4 pi/5)
+constexpr double kH3 = 0.866025403784438646763723170752936183;   // sqrt(3)/2
+
+// multiply by S*i
+template <int S, class T> __device__ __forceinline__ cplx<T> mul_si(cplx<T> a) {
+    return S < 0 ? cplx<T>{a.y, -a.x} : cplx<T>{-a.y, a.x};
+}
+
+template <int R, int S, class T> __device__ __forceinline__ void bfly(cplx<T>* v) {
+    if constexpr (R == 2) {
+        cplx<T> a = v[0], b = v[1];
+        v[0] = a + b;
+        v[1] = a - b;
+    } else if constexpr (R == 4) {
+        cplx<T> t0 = v[0] + v[2], t1 = v[0] - v[2], t2 = v[1] + v[3], t3 = mul_si<S>(v[1] - v[3]);
+        v[0] = t0 + t2;
+        v[2] = t0 - t2;
+        v[1] = t1 + t3;
+        v[3] = t1 - t3;
+    } else if constexpr (R == 3) {
+        cplx<T> t1 = v[1] + v[2], t2 = v[1] - v[2];
+        cplx<T> a = v[0] - half(t1);
+        cplx<T> b = mul_si<S>(t2 * kc<T>(kH3));
+        v[0] = v[0] + t1;
+        v[1] = a + b;
+        v[2] = a - b;
+    } else if constexpr (R == 5) {
+        cplx<T> t1 = v[1] + v[4], t2 = v[2] + v[3], t3 = v[1] - v[4], t4 = v[2] - v[3];
+        cplx<T> b1 = v[0] + t1 * kc<T>(kC1) + t2 * kc<T>(kC2);
+        cplx<T> b2 = v[0] + t1 * kc<T>(kC2) + t2 * kc<T>(kC1);
+        cplx<T> d1 = mul_si<S>(t3 * kc<T>(kS1) + t4 * kc<T>(kS2));
+        cplx<T> d2 = mul_si<S>(t3 * kc<T>(kS2) - t4 * kc<T>(kS1));
+        v[0] = v[0] + t1 + t2;
+        v[1] = b1 + d1;
+        v[4] = b1 - d1;
+        v[2] = b2 + d2;
+        v[3] = b2 - d2;
+    }
+}
+
+// twiddle exp(-2 pi i k / N) for 0 <= k < N
+template <class T> struct TwFull {  // full table in global memory (L2 / L1 resident)
+    const cplx<T>* tw;
+    __device__ __forceinline__ cplx<T> operator()(int k) const { return ldg(&tw[k]); }
+};
+struct TwTwo {  // FP32: product of two small shared-memory tables, k = 256 a + b
+    const c32* a;
+    const c32* b;
+    __device__ __forceinline__ c32 operator()(int k) const { return a[k >> 8] * b[k & 255]; }
+};
+
+// ------------------------------------------------------------------ radix passes
+// A pass applies one DIF stage (R2 = 1) or two consecutive DIF stages fused in registers:
+// radix R1 on the sub-transforms of size Ns, then radix R2 on those of size Ns / R1.  Each
+// thread transforms the R1*R2 elements b*Ns + n2 + q2*m2 + q1*m1 (m1 = Ns/R1, m2 = m1/R2), so a
+// fused pass reads and writes the work buffer once for two stages.  Twiddles: exp(-2 pi i n p /
+// Ns) = tw(n p s1) with s1 = N/Ns for the first stage and tw(n2 p s2), s2 = s1 R1, for the second.
+// The block index b = floor(i / m2) is formed with a float reciprocal: (i + 1/2) / m2 is at least
+// 1/(2 m2) away from an integer, which the float product resolves exactly for i < 2^22.
+// C supplies the buffer accesses (c.dif_load / c.dif_store / c.dit_load / c.dit_store), which
+// fold the input load, the filter product and the output epilogue into the first and last pass.
+template <int R1, int R2, int S, class T, class TW, class C>
+__device__ __forceinline__ void dif_pass(C& c, int Ns, const TW& tw) {
+    const int N = c.N, m1 = Ns / R1, m2 = m1 / R2, s1 = N / Ns, s2 = s1 * R1, ng = N / (R1 * R2);
+    const float rm = 1.0f / (float)m2;
+    for (int i = threadIdx.x; i < ng; i += blockDim.x) {
+        const int b = (int)(((float)i + 0.5f) * rm), n2 = i - b * m2, base = b * Ns + n2;
+        cplx<T> v[R2][R1];
+#pragma unroll
+        for (int q2 = 0; q2 < R2; ++q2)
+#pragma unroll
+            for (int q1 = 0; q1 < R1; ++q1) v[q2][q1] = c.dif_load(base + q2 * m2 + q1 * m1);
+#pragma unroll
+        for (int q2 = 0; q2 < R2; ++q2) {
+            bfly<R1, S>(v[q2]);
+            const int n = (n2 + q2 * m2) * s1;
+#pragma unroll
+            for (int p1 = 1; p1 < R1; ++p1) v[q2][p1] = v[q2][p1] * tw(n * p1);
+        }
+#pragma unroll
+        for (int p1 = 0; p1 < R1; ++p1) {
+            cplx<T> u[R2];
+#pragma unroll
+            for (int q2 = 0; q2 < R2; ++q2) u[q2] = v[q2][p1];
+            if constexpr (R2 > 1) {
+                bfly<R2, S>(u);
+#pragma unroll
+                for (int p2 = 1; p2 < R2; ++p2) u[p2] = u[p2] * tw(n2 * p2 * s2);
+            }
+#pragma unroll
+            for (int p2 = 0; p2 < R2; ++p2) c.dif_store(base + p1 * m1 + p2 * m2, u[p2]);
+        }
+    }
+}
+
+// exact adjoint of dif_pass: conjugate twiddles and inverse butterflies, second stage first
+template <int R1, int R2, class T, class TW, class C>
+__device__ __forceinline__ void dit_pass(C& c, int Ns, const TW& tw) {
+    const int N = c.N, m1 = Ns / R1, m2 = m1 / R2, s1 = N / Ns, s2 = s1 * R1, ng = N / (R1 * R2);
+    const float rm = 1.0f / (float)m2;
+    for (int i = threadIdx.x; i < ng; i += blockDim.x) {
+        const int b = (int)(((float)i + 0.5f) * rm), n2 = i - b * m2, base = b * Ns + n2;
+        cplx<T> v[R2][R1];
+#pragma unroll
+        for (int p1 = 0; p1 < R1; ++p1) {
+            cplx<T> u[R2];
+#pragma unroll
+            for (int p2 = 0; p2 < R2; ++p2) u[p2] = c.dit_load(base + p1 * m1 + p2 * m2);
+            if constexpr (R2 > 1) {
+#pragma unroll
+                for (int p2 = 1; p2 < R2; ++p2) u[p2] = mulc(u[p2], tw(n2 * p2 * s2));
+                bfly<R2, 1>(u);
+            }
+#pragma unroll
+            for (int q2 = 0; q2 < R2; ++q2) v[q2][p1] = u[q2];
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < R2; ++q2) {
+            const int n = (n2 + q2 * m2) * s1;
+#pragma unroll
+            for (int p1 = 1; p1 < R1; ++p1) v[q2][p1] = mulc(v[q2][p1], tw(n * p1));
+            bfly<R1, 1>(v[q2]);
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < R2; ++q2)
+#pragma unroll
+            for (int q1 = 0; q1 < R1; ++q1) c.dit_store(base + q2 * m2 + q1 * m1, v[q2][q1]);
+    }
+}
+
+template <class T, class TW, class C>
+__device__ __forceinline__ void run_pass(bool dif, int r1, int r2, C& c, int Ns, const TW& tw) {
+    // pairs above the type's register budget are never planned, so they are not compiled
+#define SFFT_PASS(A, B)                                              \
+    if constexpr (A * B <= pass_maxprod<T>()) {                      \
+        if (r1 == A && r2 == B) {                                    \
+            if (dif) dif_pass<A, B, -1, T>(c, Ns, tw);               \
+            else dit_pass<A, B, T>(c, Ns, tw);                       \
+            return;                                                  \
+        }                                                            \
+    }
+    SFFT_PASS(4, 4) SFFT_PASS(3, 3) SFFT_PASS(4, 3) SFFT_PASS(4, 2) SFFT_PASS(2, 3) SFFT_PASS(3, 5)
+    SFFT_PASS(2, 5) SFFT_PASS(4, 1) SFFT_PASS(3, 1) SFFT_PASS(2, 1) SFFT_PASS(5, 1)
+#undef SFFT_PASS
+}
+
+__device__ __forceinline__ double block_reduce_max(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double r = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
+    if (threadIdx.x == 0) red[0] = r;
+    __syncthreads();
+    double out = red[0];
+    __syncthreads();
+    return out;
+}
+
+__device__ __forceinline__ double block_reduce_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    __syncthreads();
+    if (l == 0) red[w] = v;
+    __syncthreads();
+    double r = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
+    if (w == 0)
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+    if (threadIdx.x == 0) red[0] = r;
+    __syncthreads();
+    double out = red[0];
+    __syncthreads();
+    return out;
+}
+
+constexpr int kBlueThreads = 512;
+
+// Buffer access of one Bluestein transform: the first DIF pass reads the chirp-weighted input
+// (zero padded to N), the last DIF pass multiplies by the filter before its store, and the last
+// DIT pass writes the chirp-weighted outputs h < M instead of the buffer.
+template <class T, class TI, class TO>
+struct BlueIo {
+    // statistics precision: the transform's own for float and double, float for double-float
+    // (they only place the zero test's guard band and the maximum's search window)
+    using R = typename std::conditional<std::is_same<T, df64>::value, float, T>::type;
+    cplx<T>* buf;
+    int N, M, epi;
+    bool inv, first = false, last = false;
+    const cplx<TI>* in;
+    const cplx<T>* chirp;
+    const cplx<T>* filt;
+    cplx<TO>* out;
+    const void* auxp;
+    T sc;
+    R ss = 0, mx2 = 0;  // EPI_ANALYZE: sum |x|^2 and max |X|^2 of this thread
+
+    __device__ __forceinline__ cplx<T> dif_load(int e) {
+        if (!first) return buf[e];
+        if (e >= M) return cplx<T>{kc<T>(0.0), kc<T>(0.0)};
+        const cplx<T> x = load_in<T, TI>(in + e);
+        if (epi == EPI_ANALYZE) ss += scv<R>(abs2(x));
+        const cplx<T> w = ldg(&chirp[e]);
+        return inv ? mulc(x, w) : x * w;
+    }
+    __device__ __forceinline__ void dif_store(int e, cplx<T> v) { buf[e] = last ? v * ldg(&filt[e]) : v; }
+    __device__ __forceinline__ cplx<T> dit_load(int e) { return buf[e]; }
+    __device__ __forceinline__ void dit_store(int e, cplx<T> v) {
+        if (!last) { buf[e] = v; return; }
+        if (e >= M) return;
+        const cplx<T> w = ldg(&chirp[e]);
+        cplx<T> X = inv ? mulc(v, w) : v * w;
+        X = X * sc;
+        if (epi == EPI_PLAIN || epi == EPI_ANALYZE) {
+            if constexpr (std::is_same<T, df64>::value && std::is_same<TO, float>::value) {
+                // float output of a double-float value: high words out, low words to aux
+                out[e] = cplx<TO>{X.x.hi, X.y.hi};
+                if (auxp) reinterpret_cast<c32*>(const_cast<void*>(auxp))[e] = c32{X.x.lo, X.y.lo};
+            } else {
+                out[e] = ccv<TO>(X);
+            }
+            if (epi == EPI_ANALYZE) mx2 = fmax(mx2, scv<R>(abs2(X)));
+        } else {  // EPI_ADDNOISE
+            const c64* aux = reinterpret_cast<const c64*>(auxp);
+            c64 r = ccv<double>(X);
+            if (aux) r = r + aux[e];
+            out[e] = ccv<TO>(r);
+        }
+    }
+};
+
+template <class T, class TI, class TO, class TW>
+__device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, const TW& tw, int sign, int epi,
+                                               const void* inp, const void* auxp, void* outp, double* red) {
+    BlueIo<T, TI, TO> c;
+    c.buf = buf;
+    c.N = J.N;
+    c.M = J.M;
+    c.epi = epi;
+    c.inv = sign > 0;
+    c.in = reinterpret_cast<const cplx<TI>*>(inp);
+    c.chirp = reinterpret_cast<const cplx<T>*>(J.chirp);
+    c.filt = reinterpret_cast<const cplx<T>*>(J.filt);
+    c.out = reinterpret_cast<cplx<TO>*>(outp);
+    c.auxp = auxp;
+    c.sc = kc<T>(J.scale);
+    // ---- DIF passes (the first reads the input, the last applies the filter)
+    const int np = J.npass;
+    for (int p = 0, Ns = J.N; p < np; ++p) {
+        const int r1 = J.pass_r[p] & 15, r2 = J.pass_r[p] >> 4;
+        c.first = p == 0;
+        c.last = p == np - 1;
+        run_pass<T>(true, r1, r2, c, Ns, tw);
+        Ns /= r1 * r2;
+        __syncthreads();
+    }
+    // ---- DIT passes in reverse order (the last writes the outputs)
+    c.first = false;
+    for (int p = np - 1, Ns = 1; p >= 0; --p) {
+        const int r1 = J.pass_r[p] & 15, r2 = J.pass_r[p] >> 4;
+        Ns *= r1 * r2;
+        c.last = p == 0;
+        run_pass<T>(false, r1, r2, c, Ns, tw);
+        if (p > 0) __syncthreads();
+    }
+    if (epi == EPI_ANALYZE) {
+        const double ssd = block_reduce_sum((double)c.ss, red);
+        const double mx = sqrt(block_reduce_max((double)c.mx2, red));
+        if (threadIdx.x == 0) {
+            LatStats& S = *J.stat;
+            S.max32 = (float)mx;
+            S.max_abs = mx;
+            S.rms = sqrt(ssd / (double)J.M);
+        }
+    }
+}
+
+// One CTA = one Bluestein transform.  T: arithmetic (float, double or df64); TI/TO: element
+// type of input/output.  SM: work buffer in dynamic shared memory, else in J.scratch.
+template <class T, class TI, class TO, bool SM>
+__global__ void __launch_bounds__(kBlueThreads, 1) k_bluestein(const BlueJob* __restrict__ jobs, int sign, int epi,
+                                                            const InstDesc* __restrict__ insts, void* out_base,
+                                                            const void* aux_base) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    __shared__ double red[32];
+    const BlueJob& J = jobs[blockIdx.x];
+    cplx<T>* buf = SM ? reinterpret_cast<cplx<T>*>(smem_raw) : reinterpret_cast<cplx<T>*>(J.scratch);
+    const void* inp = J.in;
+    const void* auxp = J.aux;
+    void* outp = J.out;
+    if (J.io_flags & 3) {
+        const InstDesc& I = insts[J.inst];
+        const size_t esz = I.prec ? sizeof(c32) : sizeof(c64);
+        if (J.io_flags & 1) inp = (const char*)I.samples + J.io_off * esz;
+        if (J.io_flags & 2) auxp = (const char*)I.samples + J.io_off * esz;
+    }
+    if (J.io_flags & 48) {
+        const InstDesc& I = insts[J.inst];
+        if (J.io_flags & 16) outp = (char*)I.samp_out + J.io_off * sizeof(cplx<TO>);
+        if (J.io_flags & 32) auxp = I.samp_noise ? (const void*)(I.samp_noise + J.io_off) : nullptr;
+    }
+    if (J.io_flags & 4) outp = (char*)out_base + J.io_off * sizeof(cplx<TO>);
+    if (J.io_flags & 8) auxp = aux_base ? (const void*)((const c64*)aux_base + J.io_off) : nullptr;
+    if constexpr (std::is_same<T, float>::value) {
+        __shared__ c32 s_twa[1024], s_twb[256];
+        const c32* ga = reinterpret_cast<const c32*>(J.twa);
+        const c32* gb = reinterpret_cast<const c32*>(J.twb);
+        for (int i = threadIdx.x; i < J.tw_na; i += blockDim.x) s_twa[i] = ga[i];
+        for (int i = threadIdx.x; i < 256; i += blockDim.x) s_twb[i] = gb[i];
+        __syncthreads();
+        bluestein_body<T, TI, TO>(J, buf, TwTwo{s_twa, s_twb}, sign, epi, inp, auxp, outp, red);
+    } else {
+        bluestein_body<T, TI, TO>(J, buf, TwFull<T>{reinterpret_cast<const cplx<T>*>(J.tw)}, sign, epi, inp, auxp,
+                                  outp, red);
+    }
+}
+
+// ================================================================== launch of one instantiation
+
+template <class T, class TI, class TO>
+int launch_t(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign, int epi, const InstDesc* insts,
+                    cudaStream_t st, void* ob, const void* ab, int threads) {
+    if (threads < 64 || threads > kBlueThreads || threads % 32) threads = kBlueThreads;
+    if (njobs == 0) return SFFT_OK;
+    if (sm) {
+        size_t bytes = (size_t)maxN * sizeof(cplx<T>);
+        if (bytes > blue_smem_limit()) {
+            set_error("Bluestein length %d does not fit shared memory", maxN);
+            return SFFT_EINVAL;
+        }
+        static bool attr_done = false;  // one attribute call per instantiation
+        if (!attr_done) {
+            SFFT_CU(cudaFuncSetAttribute(k_bluestein<T, TI, TO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)blue_smem_limit()));
+            attr_done = true;
+        }
+        k_bluestein<T, TI, TO, true><<<njobs, threads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
+    } else {
+        k_bluestein<T, TI, TO, false><<<njobs, threads, 0, st>>>(djobs, sign, epi, insts, ob, ab);
+    }
+    return launch_check("k_bluestein");
+}
+
+
+}  // namespace sfft

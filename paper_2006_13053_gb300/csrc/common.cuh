@@ -35,6 +35,32 @@ template <class T> __host__ __device__ __forceinline__ cplx<T> mulc(cplx<T> a, c
 }
 template <class T> __host__ __device__ __forceinline__ T abs2(cplx<T> a) { return a.x * a.x + a.y * a.y; }
 
+// double-float complex products: each component a*b + c*d with error-free FMA products and one
+// renormalisation (19 FP32 instructions instead of two products and a sum, 25); the error is
+// bounded relative to |a b| + |c d|, the normwise bound an FFT needs
+__host__ __device__ __forceinline__ df64 df_dot2(df64 a, df64 b, df64 c, df64 d) {
+    const float p1 = DF_MUL(a.hi, b.hi), e1 = fmaf(a.hi, b.hi, -p1);
+    const float p2 = DF_MUL(c.hi, d.hi), e2 = fmaf(c.hi, d.hi, -p2);
+    const df64 s = df_two_sum(p1, p2);
+    float t = DF_ADD(e1, e2);
+    t = fmaf(a.hi, b.lo, t);
+    t = fmaf(a.lo, b.hi, t);
+    t = fmaf(c.hi, d.lo, t);
+    t = fmaf(c.lo, d.hi, t);
+    return df_fast_two_sum(s.hi, DF_ADD(s.lo, t));
+}
+__host__ __device__ __forceinline__ cplx<df64> operator*(cplx<df64> a, cplx<df64> b) {
+    return {df_dot2(a.x, b.x, -a.y, b.y), df_dot2(a.x, b.y, a.y, b.x)};
+}
+__host__ __device__ __forceinline__ cplx<df64> mulc(cplx<df64> a, cplx<df64> b) {
+    return {df_dot2(a.x, b.x, a.y, b.y), df_dot2(a.y, b.x, -a.x, b.y)};
+}
+// exact halving
+template <class T> __host__ __device__ __forceinline__ cplx<T> half(cplx<T> a) { return {a.x * (T)0.5, a.y * (T)0.5}; }
+__host__ __device__ __forceinline__ cplx<df64> half(cplx<df64> a) {
+    return {df64{DF_MUL(a.x.hi, 0.5f), DF_MUL(a.x.lo, 0.5f)}, df64{DF_MUL(a.y.hi, 0.5f), DF_MUL(a.y.lo, 0.5f)}};
+}
+
 template <class T, class U> __host__ __device__ __forceinline__ cplx<T> cvt(cplx<U> a) { return {(T)a.x, (T)a.y}; }
 
 #ifdef __CUDACC__
@@ -143,7 +169,11 @@ struct BlueJob {
     //           bit 4 out = samp_out of instance `inst` + io_off; bit 5 aux = its samp_noise + io_off
     int inst, io_flags;
     int64_t io_off;
-    uint8_t radix[kMaxStages];
+    uint8_t radix[kMaxStages];  // stage radices in DIF order
+    // passes over the work buffer: one stage or two consecutive stages fused in registers;
+    // pass_r[p] = r1 | r2 << 4 (r2 = 1 for a single stage)
+    uint8_t npass;
+    uint8_t pass_r[kMaxStages];
 };
 
 // epilogue modes of the Bluestein kernel
@@ -170,6 +200,23 @@ int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, bool sm, int pre
                      int epi, const InstDesc* insts, cudaStream_t st, void* out_base = nullptr,
                      const void* aux_base = nullptr, int threads = 512);
 size_t blue_smem_limit();
+// per-type launchers behind launch_bluestein (one translation unit each)
+int launch_bluestein_f64(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign, int epi, const InstDesc* insts,
+                         cudaStream_t st, void* ob, const void* ab, int threads);
+int launch_bluestein_f32(bool in_double, const BlueJob* djobs, int njobs, int maxN, bool sm, int sign, int epi,
+                         const InstDesc* insts, cudaStream_t st, void* ob, const void* ab, int threads);
+int launch_bluestein_df64(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign, int epi, const InstDesc* insts,
+                          cudaStream_t st, void* ob, const void* ab, int threads);
+// stage pairs that the transform kernels implement as one fused pass (run_pass lists the same)
+constexpr bool pass_fusable(int r1, int r2) {
+    return (r1 == 4 && (r2 == 4 || r2 == 3 || r2 == 2)) || (r1 == 3 && (r2 == 3 || r2 == 5)) ||
+           (r1 == 2 && (r2 == 3 || r2 == 5));
+}
+// register budget of a fused pass: elements per thread (16 complex floats, 12 complex doubles
+// or double-floats, so that 512-thread CTAs stay within 128 registers per thread)
+template <class T> constexpr int pass_maxprod() { return sizeof(T) == 4 ? 16 : 12; }
+// greedy left-to-right fusion of consecutive stages whose radix product is at most maxprod
+int plan_passes(const int* radix, int ns, int maxprod, uint8_t* pass_r);
 
 // ------------------------------------------------------------------ instance / lattice descriptors
 // Everything the per-candidate kernels need about one reconstruction problem.  Lives in
