@@ -271,6 +271,13 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __r
                 cnt[c] += (bits[bit >> 5] >> (bit & 31)) & 1u;
                 if (dhashes && idx[c] < n) dhashes[idx[c] * L + l0 + l] = (int32_t)r;
             }
+            if (!dhashes && !dcounts && (l & 3) == 3) {  // count rule decided for the whole warp
+                const int rem = L - 1 - (l0 + l);
+                bool alive = false;
+#pragma unroll
+                for (int c = 0; c < kCPT; ++c) alive |= cnt[c] + rem >= need;
+                if (!__any_sync(0xffffffffu, alive)) break;
+            }
         }
 #pragma unroll
         for (int c = 0; c < kCPT; ++c) {
@@ -390,6 +397,18 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
                 cnt[c] += __funnelshift_r(bits[bit >> 5], 0u, bit) & 1u;
                 if constexpr (DIAG) {
                     if (idx[c] < n && I.dhashes) I.dhashes[idx[c] * L + l0 + l] = (int32_t)rr;
+                }
+            }
+            if constexpr (!DIAG) {
+                // count rule (Algorithm 1): once no candidate of the warp can still reach `need`
+                // with the lattices left, the rest cannot change a decision (exact counts are only
+                // reported by the DIAG variant)
+                if ((l & 3) == 3) {
+                    const int rem = L - 1 - (l0 + l);
+                    bool alive = false;
+#pragma unroll
+                    for (int c = 0; c < kCPT2; ++c) alive |= cnt[c] + rem >= need;
+                    if (!__any_sync(0xffffffffu, alive)) break;
                 }
             }
         }
