@@ -203,7 +203,7 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
 /*
  * Autotuner: runs sfft_batch_reconstruct on the given buffers (reps timed runs per candidate
  * after one warm-up) for hash-kernel grids of 1/2, 1, 2 and 4 waves of resident CTAs and for
- * lattice transforms of 256 or 512 threads per CTA, times the affected stage with CUDA events,
+ * lattice transforms of 256, 384, 448 or 512 threads per CTA, times the affected stage with CUDA events,
  * keeps the fastest shapes for later calls (a captured graph is re-captured) and reports them
  * (hash_waves, fft_threads: optional host outputs).  Synchronises the batch stream.
  */

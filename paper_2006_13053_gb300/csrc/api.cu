@@ -172,7 +172,15 @@ BlueJob make_blue_job(const FftTables* t, int prec, int dir, double scale) {
 
 bool Plan::fits_smem(int tprec) const {
     size_t e = tprec == 1 ? sizeof(c32) : sizeof(c64);  // double and double-float: 16 bytes
-    return (size_t)maxN * e <= blue_smem_limit();
+    return blue_smem_bytes(maxN, e) <= blue_smem_limit();
+}
+
+int Plan::buf_mode(int tprec) const {
+    if (fits_smem(tprec)) return 1;
+    const size_t e = tprec == 1 ? sizeof(c32) : sizeof(c64);
+    bool even = true;
+    for (const FftTables* t : tabs) even &= t->N % 2 == 0;
+    return even && blue_smem_bytes(maxN / 2, e) <= blue_smem_limit() ? 2 : 0;
 }
 
 // FP32 plans with refinement run the forward transform in double-float: the refinement's
@@ -193,12 +201,12 @@ int Plan::build_jobs() {
         a.out = ghat_b + o * e;
         a.aux = ghat_lo ? (const void*)(ghat_lo + o) : nullptr;
         a.stat = stats + l;
-        a.scratch = fits_smem(fp) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
+        a.scratch = buf_mode(fp) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
         jobs_fwd.push_back(a);
         // sampler: out (launch argument) = IDFT(C) + noise (launch argument), plan precision
         BlueJob sj = make_blue_job(t, prec, 1, 1.0);
         sj.in = C + o; sj.io_flags = 16 | 32; sj.io_off = o; sj.inst = 0;
-        sj.scratch = fits_smem(prec) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
+        sj.scratch = buf_mode(prec) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
         jobs_samp.push_back(sj);
         // adjoint: out (launch argument) = (1/M) IDFT(C), plan precision
         BlueJob aj = make_blue_job(t, prec, 1, 1.0 / (double)M[l]);
@@ -345,7 +353,7 @@ int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L
     SFFT_TRY(P->alloc((void**)&P->coll, sizeof(int32_t) * P->sumM));
     SFFT_TRY(P->alloc((void**)&P->C, sizeof(c64) * P->sumM));
     if (P->fwd_prec() == 2) SFFT_TRY(P->alloc((void**)&P->ghat_lo, sizeof(c32) * P->sumM));
-    if (!P->fits_smem(P->fwd_prec()) || !P->fits_smem(P->prec))
+    if (!P->buf_mode(P->fwd_prec()) || !P->buf_mode(P->prec))
         SFFT_TRY(P->alloc(&P->scratch, sizeof(c64) * (size_t)P->maxN * L));
     SFFT_TRY(P->alloc((void**)&P->sop_a, sizeof(double) * 2 * 16 * 129));
     SFFT_TRY(P->alloc((void**)&P->sop_tri, sizeof(int32_t) * 3 * 16));
@@ -422,7 +430,7 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
     // Algorithm 2 line 2: lattice DFTs (normalised by 1/M) + per-lattice statistics
     SFFT_TRY(mark(a, ST_FFT_FWD, st));
     for (const auto& f : a.fwd)
-        SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, a.fwd_prec, a.prec, a.prec, -1, EPI_ANALYZE, a.d_inst,
+        SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.mode, a.fwd_prec, a.prec, a.prec, -1, EPI_ANALYZE, a.d_inst,
                                   st, nullptr, nullptr, f.threads));
     // zero test with FP64 re-tests inside the guard band (Remark 2.3); unit roundoff of the
     // transform arithmetic (double-float: 2^-44, a bound with margin for its ~48-bit operations)
@@ -468,7 +476,7 @@ PipeArgs Plan::pipe_args() {
     a.ninst = 1; a.d_inst = d_inst; a.d_lats = d_lats; a.nlat = L;
     a.prec = prec; a.fwd_prec = fwd_prec(); a.maxcap = cap;
     a.hybrid = p.combine == SFFT_COMBINE_HYBRID; a.refine = p.refine;
-    a.fwd.push_back(FftLaunch{d_jobs_fwd, L, maxN, fits_smem(fwd_prec())});
+    a.fwd.push_back(FftLaunch{d_jobs_fwd, L, maxN, buf_mode(fwd_prec())});
     const int ng = (int)hgroups.size();
     for (int g = 0; g < ng; ++g) {
         HashGroup h;
@@ -635,7 +643,7 @@ int sfft_reconstruct_backward(sfft_plan* plan, const double* dcoef, void* dsampl
     SFFT_CU(cudaMemsetAsync(P->C, 0, sizeof(c64) * P->sumM, st));
     if (P->last_nout > 0 && dcoef) SFFT_TRY(launch_adj_scatter(P->d_inst, reinterpret_cast<const c64*>(dcoef), st));
     // dsamples = A^H gbar with (A^H g)_j = (1/M) sum_h g_h exp(+2 pi i j h / M)
-    SFFT_TRY(launch_bluestein(P->d_jobs_adj, P->L, P->maxN, P->fits_smem(P->prec), P->prec, 0, P->prec, +1, EPI_PLAIN,
+    SFFT_TRY(launch_bluestein(P->d_jobs_adj, P->L, P->maxN, P->buf_mode(P->prec), P->prec, 0, P->prec, +1, EPI_PLAIN,
                               P->d_inst, st, dsamples, nullptr));
     SFFT_CU(cudaStreamSynchronize(st));
     return SFFT_OK;
@@ -659,7 +667,7 @@ int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const do
     SFFT_TRY(P->io_upload());
     SFFT_TRY(launch_clear(P->d_inst, 1, 0, 0, 1, st));
     if (n_terms > 0) SFFT_TRY(launch_scatter_terms(P->d_inst, 1, n_terms * P->L, st));
-    SFFT_TRY(launch_bluestein(P->d_jobs_samp, P->L, P->maxN, P->fits_smem(P->prec), P->prec, 0, P->prec, +1, EPI_ADDNOISE,
+    SFFT_TRY(launch_bluestein(P->d_jobs_samp, P->L, P->maxN, P->buf_mode(P->prec), P->prec, 0, P->prec, +1, EPI_ADDNOISE,
                               P->d_inst, st));
     return SFFT_OK;
 }

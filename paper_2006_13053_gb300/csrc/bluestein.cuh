@@ -9,6 +9,8 @@
 #pragma once
 #include <math.h>
 
+#include <cooperative_groups.h>
+
 #include <type_traits>
 
 #include "common.cuh"
@@ -52,35 +54,57 @@ template <int S, class T> __device__ __forceinline__ cplx<T> mul_si(cplx<T> a) {
     return S < 0 ? cplx<T>{a.y, -a.x} : cplx<T>{-a.y, a.x};
 }
 
+// Butterfly sums.  Double-float: Knuth two-sum of the high words plus the low words, without the
+// final renormalisation (8 instead of 11 instructions).  The pair still represents the sum to
+// ~2^-47 relative as long as |lo| stays within a few ulps of hi; every product renormalises, and
+// values are renormalised when they are written to the work buffer (qnorm).
+__device__ __forceinline__ df64 df_add_q(df64 a, df64 b) {
+    const df64 s = df_two_sum(a.hi, b.hi);
+    return df64{s.hi, DF_ADD(s.lo, DF_ADD(a.lo, b.lo))};
+}
+template <class T> __device__ __forceinline__ cplx<T> qadd(cplx<T> a, cplx<T> b) { return a + b; }
+template <class T> __device__ __forceinline__ cplx<T> qsub(cplx<T> a, cplx<T> b) { return a - b; }
+template <class T> __device__ __forceinline__ cplx<T> qnorm(cplx<T> a) { return a; }
+template <> __device__ __forceinline__ cplx<df64> qadd(cplx<df64> a, cplx<df64> b) {
+    return {df_add_q(a.x, b.x), df_add_q(a.y, b.y)};
+}
+template <> __device__ __forceinline__ cplx<df64> qsub(cplx<df64> a, cplx<df64> b) {
+    return {df_add_q(a.x, -b.x), df_add_q(a.y, -b.y)};
+}
+template <> __device__ __forceinline__ cplx<df64> qnorm(cplx<df64> a) {
+    return {df_fast_two_sum(a.x.hi, a.x.lo), df_fast_two_sum(a.y.hi, a.y.lo)};
+}
+
 template <int R, int S, class T> __device__ __forceinline__ void bfly(cplx<T>* v) {
     if constexpr (R == 2) {
         cplx<T> a = v[0], b = v[1];
-        v[0] = a + b;
-        v[1] = a - b;
+        v[0] = qadd(a, b);
+        v[1] = qsub(a, b);
     } else if constexpr (R == 4) {
-        cplx<T> t0 = v[0] + v[2], t1 = v[0] - v[2], t2 = v[1] + v[3], t3 = mul_si<S>(v[1] - v[3]);
-        v[0] = t0 + t2;
-        v[2] = t0 - t2;
-        v[1] = t1 + t3;
-        v[3] = t1 - t3;
+        cplx<T> t0 = qadd(v[0], v[2]), t1 = qsub(v[0], v[2]), t2 = qadd(v[1], v[3]);
+        cplx<T> t3 = mul_si<S>(qsub(v[1], v[3]));
+        v[0] = qadd(t0, t2);
+        v[2] = qsub(t0, t2);
+        v[1] = qadd(t1, t3);
+        v[3] = qsub(t1, t3);
     } else if constexpr (R == 3) {
-        cplx<T> t1 = v[1] + v[2], t2 = v[1] - v[2];
-        cplx<T> a = v[0] - half(t1);
+        cplx<T> t1 = qadd(v[1], v[2]), t2 = qsub(v[1], v[2]);
+        cplx<T> a = qsub(v[0], half(t1));
         cplx<T> b = mul_si<S>(t2 * kc<T>(kH3));
-        v[0] = v[0] + t1;
-        v[1] = a + b;
-        v[2] = a - b;
+        v[0] = qadd(v[0], t1);
+        v[1] = qadd(a, b);
+        v[2] = qsub(a, b);
     } else if constexpr (R == 5) {
-        cplx<T> t1 = v[1] + v[4], t2 = v[2] + v[3], t3 = v[1] - v[4], t4 = v[2] - v[3];
+        cplx<T> t1 = qadd(v[1], v[4]), t2 = qadd(v[2], v[3]), t3 = qsub(v[1], v[4]), t4 = qsub(v[2], v[3]);
         cplx<T> b1 = v[0] + t1 * kc<T>(kC1) + t2 * kc<T>(kC2);
         cplx<T> b2 = v[0] + t1 * kc<T>(kC2) + t2 * kc<T>(kC1);
         cplx<T> d1 = mul_si<S>(t3 * kc<T>(kS1) + t4 * kc<T>(kS2));
         cplx<T> d2 = mul_si<S>(t3 * kc<T>(kS2) - t4 * kc<T>(kS1));
-        v[0] = v[0] + t1 + t2;
-        v[1] = b1 + d1;
-        v[4] = b1 - d1;
-        v[2] = b2 + d2;
-        v[3] = b2 - d2;
+        v[0] = qadd(qadd(v[0], t1), t2);
+        v[1] = qadd(b1, d1);
+        v[4] = qsub(b1, d1);
+        v[2] = qadd(b2, d2);
+        v[3] = qsub(b2, d2);
     }
 }
 
@@ -109,7 +133,9 @@ template <int R1, int R2, int S, class T, class TW, class C>
 __device__ __forceinline__ void dif_pass(C& c, int Ns, const TW& tw) {
     const int N = c.N, m1 = Ns / R1, m2 = m1 / R2, s1 = N / Ns, s2 = s1 * R1, ng = N / (R1 * R2);
     const float rm = 1.0f / (float)m2;
-    for (int i = threadIdx.x; i < ng; i += blockDim.x) {
+    // a cluster of two CTAs splits the groups at a block boundary (see BlueIo)
+    const int g0 = c.rank * (ng >> 1), g1 = (c.nrank == 1 || c.rank == 1) ? ng : (ng >> 1);
+    for (int i = g0 + threadIdx.x; i < g1; i += blockDim.x) {
         const int b = (int)(((float)i + 0.5f) * rm), n2 = i - b * m2, base = b * Ns + n2;
         cplx<T> v[R2][R1];
 #pragma unroll
@@ -144,7 +170,9 @@ template <int R1, int R2, class T, class TW, class C>
 __device__ __forceinline__ void dit_pass(C& c, int Ns, const TW& tw) {
     const int N = c.N, m1 = Ns / R1, m2 = m1 / R2, s1 = N / Ns, s2 = s1 * R1, ng = N / (R1 * R2);
     const float rm = 1.0f / (float)m2;
-    for (int i = threadIdx.x; i < ng; i += blockDim.x) {
+    // a cluster of two CTAs splits the groups at a block boundary (see BlueIo)
+    const int g0 = c.rank * (ng >> 1), g1 = (c.nrank == 1 || c.rank == 1) ? ng : (ng >> 1);
+    for (int i = g0 + threadIdx.x; i < g1; i += blockDim.x) {
         const int b = (int)(((float)i + 0.5f) * rm), n2 = i - b * m2, base = b * Ns + n2;
         cplx<T> v[R2][R1];
 #pragma unroll
@@ -227,12 +255,14 @@ constexpr int kBlueThreads = 512;
 // Buffer access of one Bluestein transform: the first DIF pass reads the chirp-weighted input
 // (zero padded to N), the last DIF pass multiplies by the filter before its store, and the last
 // DIT pass writes the chirp-weighted outputs h < M instead of the buffer.
-template <class T, class TI, class TO>
-struct BlueIo {
+template <class T, class TI, class TO, bool SMB, bool CL>
+struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over a two-CTA cluster
     // statistics precision: the transform's own for float and double, float for double-float
     // (they only place the zero test's guard band and the maximum's search window)
     using R = typename std::conditional<std::is_same<T, df64>::value, float, T>::type;
-    cplx<T>* buf;
+    cplx<T>* buf;        // work buffer (CL: this CTA's half, elements [rank N/2, (rank+1) N/2))
+    cplx<T>* rbuf;       // CL: the other CTA's half (distributed shared memory)
+    int hN = 0, rank = 0, nrank = 1;
     int N, M, epi;
     bool inv, first = false, last = false;
     const cplx<TI>* in;
@@ -243,18 +273,30 @@ struct BlueIo {
     T sc;
     R ss = 0, mx2 = 0;  // EPI_ANALYZE: sum |x|^2 and max |X|^2 of this thread
 
+    __device__ __forceinline__ cplx<T>* at(int e) {
+        constexpr int P = blue_pad_shift(sizeof(cplx<T>));
+        if constexpr (CL) {
+            const int o = e >= hN ? 1 : 0;
+            const int le = e - o * hN;
+            return (o == rank ? buf : rbuf) + (P ? le + (le >> P) : le);
+        } else if constexpr (SMB && P > 0) {
+            return buf + e + (e >> P);
+        } else {
+            return buf + e;
+        }
+    }
     __device__ __forceinline__ cplx<T> dif_load(int e) {
-        if (!first) return buf[e];
+        if (!first) return *at(e);
         if (e >= M) return cplx<T>{kc<T>(0.0), kc<T>(0.0)};
         const cplx<T> x = load_in<T, TI>(in + e);
         if (epi == EPI_ANALYZE) ss += scv<R>(abs2(x));
         const cplx<T> w = ldg(&chirp[e]);
         return inv ? mulc(x, w) : x * w;
     }
-    __device__ __forceinline__ void dif_store(int e, cplx<T> v) { buf[e] = last ? v * ldg(&filt[e]) : v; }
-    __device__ __forceinline__ cplx<T> dit_load(int e) { return buf[e]; }
+    __device__ __forceinline__ void dif_store(int e, cplx<T> v) { *at(e) = last ? v * ldg(&filt[e]) : qnorm(v); }
+    __device__ __forceinline__ cplx<T> dit_load(int e) { return *at(e); }
     __device__ __forceinline__ void dit_store(int e, cplx<T> v) {
-        if (!last) { buf[e] = v; return; }
+        if (!last) { *at(e) = qnorm(v); return; }
         if (e >= M) return;
         const cplx<T> w = ldg(&chirp[e]);
         cplx<T> X = inv ? mulc(v, w) : v * w;
@@ -277,11 +319,25 @@ struct BlueIo {
     }
 };
 
-template <class T, class TI, class TO, class TW>
-__device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, const TW& tw, int sign, int epi,
-                                               const void* inp, const void* auxp, void* outp, double* red) {
-    BlueIo<T, TI, TO> c;
+// CL: the transform of one lattice is split over a cluster of two CTAs, each holding half of the
+// work buffer in its shared memory.  Only the first DIF pass and the last DIT pass (sub-transform
+// size N) touch the other half; every later pass works on blocks of size N / (first pass radix
+// product), which lie inside one half when that product is even, so a CTA takes the groups of
+// its own blocks.  Cluster barriers follow the first pass, precede the last one and end the
+// transform (no CTA leaves while the other may still read its half); one more barrier at the
+// start makes sure both CTAs run before the first pass writes into the other half.
+template <class T, class TI, class TO, bool SMB, bool CL, class TW>
+__device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, cplx<T>* rbuf, int rank, const TW& tw,
+                                               int sign, int epi, const void* inp, const void* auxp, void* outp,
+                                               double* red, double* xchg) {
+    BlueIo<T, TI, TO, SMB, CL> c;
     c.buf = buf;
+    c.rbuf = rbuf;
+    if constexpr (CL) {
+        c.hN = J.N >> 1;
+        c.rank = rank;
+        c.nrank = 2;
+    }
     c.N = J.N;
     c.M = J.M;
     c.epi = epi;
@@ -292,6 +348,17 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
     c.out = reinterpret_cast<cplx<TO>*>(outp);
     c.auxp = auxp;
     c.sc = kc<T>(J.scale);
+    auto sync = [&](bool cluster_wide) {
+        if constexpr (CL) {
+            if (cluster_wide) {
+                cooperative_groups::this_cluster().sync();
+                return;
+            }
+        }
+        __syncthreads();
+    };
+    // both CTAs of a cluster must be running before either writes into the other's half
+    if constexpr (CL) cooperative_groups::this_cluster().sync();
     // ---- DIF passes (the first reads the input, the last applies the filter)
     const int np = J.npass;
     for (int p = 0, Ns = J.N; p < np; ++p) {
@@ -300,7 +367,7 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
         c.last = p == np - 1;
         run_pass<T>(true, r1, r2, c, Ns, tw);
         Ns /= r1 * r2;
-        __syncthreads();
+        sync(p == 0);
     }
     // ---- DIT passes in reverse order (the last writes the outputs)
     c.first = false;
@@ -309,30 +376,47 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
         Ns *= r1 * r2;
         c.last = p == 0;
         run_pass<T>(false, r1, r2, c, Ns, tw);
-        if (p > 0) __syncthreads();
+        if (p > 0) sync(p == 1);
     }
     if (epi == EPI_ANALYZE) {
-        const double ssd = block_reduce_sum((double)c.ss, red);
-        const double mx = sqrt(block_reduce_max((double)c.mx2, red));
+        double ssd = block_reduce_sum((double)c.ss, red);
+        double mx2 = block_reduce_max((double)c.mx2, red);
+        if constexpr (CL) {  // partials of both CTAs to rank 0
+            auto cl = cooperative_groups::this_cluster();
+            double* x0 = cl.map_shared_rank(xchg, 0);
+            if (threadIdx.x == 0) { x0[2 * rank] = ssd; x0[2 * rank + 1] = mx2; }
+            cl.sync();
+            if (rank != 0) return;
+            ssd = xchg[0] + xchg[2];
+            mx2 = fmax(xchg[1], xchg[3]);
+        }
         if (threadIdx.x == 0) {
+            const double mx = sqrt(mx2);
             LatStats& S = *J.stat;
             S.max32 = (float)mx;
             S.max_abs = mx;
             S.rms = sqrt(ssd / (double)J.M);
         }
+    } else if constexpr (CL) {
+        cooperative_groups::this_cluster().sync();
     }
 }
 
-// One CTA = one Bluestein transform.  T: arithmetic (float, double or df64); TI/TO: element
-// type of input/output.  SM: work buffer in dynamic shared memory, else in J.scratch.
-template <class T, class TI, class TO, bool SM>
-__global__ void __launch_bounds__(kBlueThreads, 1) k_bluestein(const BlueJob* __restrict__ jobs, int sign, int epi,
-                                                            const InstDesc* __restrict__ insts, void* out_base,
-                                                            const void* aux_base) {
+// One CTA (MODE 0, 1) or a cluster of two CTAs (MODE 2) = one Bluestein transform.  T:
+// arithmetic (float, double or df64); TI/TO: element type of input/output.  MODE 0: work buffer
+// in J.scratch (global, L2-resident); 1: in dynamic shared memory; 2: split over the two CTAs'
+// shared memory.
+template <class T, class TI, class TO, int MODE>
+__device__ __forceinline__ void bluestein_cta(const BlueJob* __restrict__ jobs, int job, int rank, int sign, int epi,
+                                              const InstDesc* __restrict__ insts, void* out_base,
+                                              const void* aux_base) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     __shared__ double red[32];
-    const BlueJob& J = jobs[blockIdx.x];
-    cplx<T>* buf = SM ? reinterpret_cast<cplx<T>*>(smem_raw) : reinterpret_cast<cplx<T>*>(J.scratch);
+    __shared__ double xchg[4];
+    const BlueJob& J = jobs[job];
+    cplx<T>* buf = MODE ? reinterpret_cast<cplx<T>*>(smem_raw) : reinterpret_cast<cplx<T>*>(J.scratch);
+    cplx<T>* rbuf = nullptr;
+    if constexpr (MODE == 2) rbuf = cooperative_groups::this_cluster().map_shared_rank(buf, rank ^ 1);
     const void* inp = J.in;
     const void* auxp = J.aux;
     void* outp = J.out;
@@ -356,38 +440,58 @@ __global__ void __launch_bounds__(kBlueThreads, 1) k_bluestein(const BlueJob* __
         for (int i = threadIdx.x; i < J.tw_na; i += blockDim.x) s_twa[i] = ga[i];
         for (int i = threadIdx.x; i < 256; i += blockDim.x) s_twb[i] = gb[i];
         __syncthreads();
-        bluestein_body<T, TI, TO>(J, buf, TwTwo{s_twa, s_twb}, sign, epi, inp, auxp, outp, red);
+        bluestein_body<T, TI, TO, MODE != 0, MODE == 2>(J, buf, rbuf, rank, TwTwo{s_twa, s_twb}, sign, epi, inp, auxp, outp,
+                                             red, xchg);
     } else {
-        bluestein_body<T, TI, TO>(J, buf, TwFull<T>{reinterpret_cast<const cplx<T>*>(J.tw)}, sign, epi, inp, auxp,
-                                  outp, red);
+        bluestein_body<T, TI, TO, MODE != 0, MODE == 2>(J, buf, rbuf, rank, TwFull<T>{reinterpret_cast<const cplx<T>*>(J.tw)},
+                                             sign, epi, inp, auxp, outp, red, xchg);
     }
+}
+
+template <class T, class TI, class TO, int MODE>
+__global__ void __launch_bounds__(kBlueThreads, 1) k_bluestein(const BlueJob* __restrict__ jobs, int sign, int epi,
+                                                            const InstDesc* __restrict__ insts, void* out_base,
+                                                            const void* aux_base) {
+    bluestein_cta<T, TI, TO, MODE>(jobs, blockIdx.x, 0, sign, epi, insts, out_base, aux_base);
+}
+
+template <class T, class TI, class TO>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBlueThreads, 1)
+    k_bluestein_pair(const BlueJob* __restrict__ jobs, int sign, int epi, const InstDesc* __restrict__ insts,
+                     void* out_base, const void* aux_base) {
+    const int rank = (int)cooperative_groups::this_cluster().block_rank();
+    bluestein_cta<T, TI, TO, 2>(jobs, blockIdx.x >> 1, rank, sign, epi, insts, out_base, aux_base);
 }
 
 // ================================================================== launch of one instantiation
 
 template <class T, class TI, class TO>
-int launch_t(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign, int epi, const InstDesc* insts,
-                    cudaStream_t st, void* ob, const void* ab, int threads) {
+int launch_t(const BlueJob* djobs, int njobs, int maxN, int mode, int sign, int epi, const InstDesc* insts,
+             cudaStream_t st, void* ob, const void* ab, int threads) {
     if (threads < 64 || threads > kBlueThreads || threads % 32) threads = kBlueThreads;
     if (njobs == 0) return SFFT_OK;
-    if (sm) {
-        size_t bytes = (size_t)maxN * sizeof(cplx<T>);
-        if (bytes > blue_smem_limit()) {
-            set_error("Bluestein length %d does not fit shared memory", maxN);
+    if (mode == 1 || mode == 2) {
+        const size_t bytes = blue_smem_bytes(mode == 2 ? maxN / 2 : maxN, sizeof(cplx<T>));
+        if (bytes > blue_smem_limit() || (mode == 2 && maxN % 2)) {
+            set_error("Bluestein length %d does not fit the shared-memory mode %d", maxN, mode);
             return SFFT_EINVAL;
         }
-        static bool attr_done = false;  // one attribute call per instantiation
-        if (!attr_done) {
-            SFFT_CU(cudaFuncSetAttribute(k_bluestein<T, TI, TO, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)blue_smem_limit()));
-            attr_done = true;
+        static bool attr_done[3] = {false, false, false};  // one attribute call per instantiation
+        if (!attr_done[mode]) {
+            if (mode == 1)
+                SFFT_CU(cudaFuncSetAttribute(k_bluestein<T, TI, TO, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)blue_smem_limit()));
+            else
+                SFFT_CU(cudaFuncSetAttribute(k_bluestein_pair<T, TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)blue_smem_limit()));
+            attr_done[mode] = true;
         }
-        k_bluestein<T, TI, TO, true><<<njobs, threads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
+        if (mode == 1) k_bluestein<T, TI, TO, 1><<<njobs, threads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
+        else k_bluestein_pair<T, TI, TO><<<2 * njobs, threads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
     } else {
-        k_bluestein<T, TI, TO, false><<<njobs, threads, 0, st>>>(djobs, sign, epi, insts, ob, ab);
+        k_bluestein<T, TI, TO, 0><<<njobs, threads, 0, st>>>(djobs, sign, epi, insts, ob, ab);
     }
     return launch_check("k_bluestein");
 }
-
 
 }  // namespace sfft

@@ -194,18 +194,28 @@ struct LatStats {
 };
 
 // One launch of Bluestein transforms over a device job array.  prec: 0 double, 1 float,
-// 2 double-float; in_prec/out_prec: 0 double, 1 float.  sm: work buffer in shared memory (all jobs need N <= maxN fitting).
+// 2 double-float; in_prec/out_prec: 0 double, 1 float.  mode: work buffer in global scratch (0),
+// in shared memory (1: N <= maxN complex values fit one CTA), or split over a two-CTA cluster
+// (2: every N even, N/2 values fit one CTA).
 struct InstDesc;
-int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, bool sm, int prec, int in_prec, int out_prec, int sign,
+int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, int mode, int prec, int in_prec, int out_prec, int sign,
                      int epi, const InstDesc* insts, cudaStream_t st, void* out_base = nullptr,
                      const void* aux_base = nullptr, int threads = 512);
 size_t blue_smem_limit();
+// Shared-memory work buffers of 8-byte complex values are padded against bank conflicts of the
+// strided passes: element e lives at e + (e >> 5).  (16-byte values: measured slower padded, the
+// index arithmetic costs more than the conflicts.)
+constexpr int blue_pad_shift(size_t esz) { return esz == 8 ? 5 : 0; }
+inline size_t blue_smem_bytes(int64_t n, size_t esz) {
+    const int p = blue_pad_shift(esz);
+    return (size_t)(n + (p ? (n >> p) + 1 : 0)) * esz;
+}
 // per-type launchers behind launch_bluestein (one translation unit each)
-int launch_bluestein_f64(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign, int epi, const InstDesc* insts,
+int launch_bluestein_f64(const BlueJob* djobs, int njobs, int maxN, int mode, int sign, int epi, const InstDesc* insts,
                          cudaStream_t st, void* ob, const void* ab, int threads);
-int launch_bluestein_f32(bool in_double, const BlueJob* djobs, int njobs, int maxN, bool sm, int sign, int epi,
+int launch_bluestein_f32(bool in_double, const BlueJob* djobs, int njobs, int maxN, int mode, int sign, int epi,
                          const InstDesc* insts, cudaStream_t st, void* ob, const void* ab, int threads);
-int launch_bluestein_df64(const BlueJob* djobs, int njobs, int maxN, bool sm, int sign, int epi, const InstDesc* insts,
+int launch_bluestein_df64(const BlueJob* djobs, int njobs, int maxN, int mode, int sign, int epi, const InstDesc* insts,
                           cudaStream_t st, void* ob, const void* ab, int threads);
 // stage pairs that the transform kernels implement as one fused pass (run_pass lists the same)
 constexpr bool pass_fusable(int r1, int r2) {

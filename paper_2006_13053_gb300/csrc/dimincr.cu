@@ -61,9 +61,9 @@ int small_dft(int K, const c64* in, c64* out, DevBuf& jobbuf, cudaStream_t st) {
         cudaError_t e = cudaMemcpyAsync(jobbuf.p, &J, sizeof J, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) { set_error("job upload: %s", cudaGetErrorString(e)); rc = SFFT_ECUDA; }
     }
-    const bool sm = (size_t)t->N * sizeof(c64) <= blue_smem_limit();
+    const bool sm = blue_smem_bytes(t->N, sizeof(c64)) <= blue_smem_limit();
     if (rc == SFFT_OK && !sm) { set_error("Step 1 length K=%d too large", K); rc = SFFT_EINVAL; }
-    if (rc == SFFT_OK) rc = launch_bluestein(jobbuf.as<BlueJob>(), 1, (int)t->N, true, 0, 0, 0, -1, EPI_PLAIN, nullptr, st);
+    if (rc == SFFT_OK) rc = launch_bluestein(jobbuf.as<BlueJob>(), 1, (int)t->N, 1, 0, 0, 0, -1, EPI_PLAIN, nullptr, st);
     if (rc == SFFT_OK) {
         cudaError_t e = cudaStreamSynchronize(st);  // the tables may be released below
         if (e != cudaSuccess) { set_error("small DFT: %s", cudaGetErrorString(e)); rc = SFFT_ECUDA; }

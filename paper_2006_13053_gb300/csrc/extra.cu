@@ -110,8 +110,8 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
     for (int i : idx) B->plans.push_back(reinterpret_cast<Plan*>(plans[i]));
     SFFT_CU(cudaMallocHost((void**)&B->h_inst, sizeof(InstDesc) * n));
     std::vector<LatDesc> lats;
-    std::vector<BlueJob> jf[2], js[2];  // [0] global scratch, [1] shared memory
-    int maxN[2][2] = {{0, 0}, {0, 0}};
+    std::vector<BlueJob> jf[3], js[3];  // by work-buffer mode: global scratch, shared memory, cluster
+    int maxN[3][2] = {{0, 0}, {0, 0}, {0, 0}};
     PipeArgs& A = B->args;
     A.ninst = n;
     A.prec = B->prec;
@@ -125,7 +125,7 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
         for (int l = 0; l < P->L; ++l)
             lats.push_back(LatDesc{b, l, (int)P->M[l], (int)P->tabs[l]->N, P->soff[l], P->boff[l], 0,
                                    (const double*)P->tabs[l]->dft64});
-        const int sf = P->fits_smem(P->fwd_prec()) ? 1 : 0, sp = P->fits_smem(P->prec) ? 1 : 0;
+        const int sf = P->buf_mode(P->fwd_prec()), sp = P->buf_mode(P->prec);
         for (int l = 0; l < P->L; ++l) {
             BlueJob f = P->jobs_fwd[l], s = P->jobs_samp[l];
             f.inst = b; s.inst = b;
@@ -141,16 +141,16 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
     SFFT_CU(cudaMemcpy(B->d_inst, B->h_inst, sizeof(InstDesc) * n, cudaMemcpyHostToDevice));
     A.d_inst = B->d_inst;
     A.d_lats = B->d_lats;
-    for (int sm = 1; sm >= 0; --sm) {
-        if (!jf[sm].empty()) {
+    for (int md : {1, 2, 0}) {
+        if (!jf[md].empty()) {
             BlueJob* dj = nullptr;
-            SFFT_TRY(upload_jobs(jf[sm], &dj, &B->allocs));
-            A.fwd.push_back(FftLaunch{dj, (int)jf[sm].size(), maxN[sm][0], sm == 1});
+            SFFT_TRY(upload_jobs(jf[md], &dj, &B->allocs));
+            A.fwd.push_back(FftLaunch{dj, (int)jf[md].size(), maxN[md][0], md});
         }
-        if (!js[sm].empty()) {
+        if (!js[md].empty()) {
             BlueJob* dj = nullptr;
-            SFFT_TRY(upload_jobs(js[sm], &dj, &B->allocs));
-            B->samp.push_back(FftLaunch{dj, (int)js[sm].size(), maxN[sm][1], sm == 1});
+            SFFT_TRY(upload_jobs(js[md], &dj, &B->allocs));
+            B->samp.push_back(FftLaunch{dj, (int)js[md].size(), maxN[md][1], md});
         }
     }
     // hash launches: contiguous runs of single-group plans with equal d and kernel variant share a
@@ -301,7 +301,7 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
     SFFT_TRY(launch_clear(B->d_inst, n, 0, 0, 1, st));
     if (mx > 0) SFFT_TRY(launch_scatter_terms(B->d_inst, n, mx, st));
     for (const auto& f : B->samp)
-        SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.sm, B->prec, 0, B->prec, +1, EPI_ADDNOISE, B->d_inst, st));
+        SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.mode, B->prec, 0, B->prec, +1, EPI_ADDNOISE, B->d_inst, st));
     SFFT_CU(cudaEventRecord(B->done, st));
     return SFFT_OK;
 }
@@ -342,8 +342,8 @@ int sfft_batch_autotune(sfft_batch* b, const void* const* samples, int64_t* cons
     }
     for (auto& h : B->args.hash)
         h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(h.tiles, 1), (int64_t)llround(h.gx0 * bestm)));
-    // lattice transforms: 256 or 512 threads per CTA
-    const int ths[2] = {256, 512};
+    // lattice transforms: 256 to 512 threads per CTA
+    const int ths[4] = {256, 384, 448, 512};
     best = 1e30;
     int bestt = 512;
     for (int th : ths) {

@@ -11,7 +11,7 @@ namespace sfft {
 struct FftLaunch {
     const BlueJob* jobs = nullptr;
     int njobs = 0, maxN = 0;
-    bool sm = true;
+    int mode = 1;  // work buffer: 0 global scratch, 1 shared memory, 2 two-CTA cluster
     int threads = 512;  // CTA size (autotuned)
 };
 // one launch of the hash-count kernel over a contiguous range of instances of equal d
@@ -95,6 +95,7 @@ struct Plan {
     size_t esz() const;
     int fwd_prec() const;           // arithmetic of the forward transform
     bool fits_smem(int tprec) const;
+    int buf_mode(int tprec) const;  // work-buffer mode of the transforms in precision tprec
     int build_jobs();
     int hash_grid() const;
     PipeArgs pipe_args();
