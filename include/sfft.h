@@ -52,7 +52,9 @@ extern "C" {
 
 /* ---------------------------------------------------------------- parameters */
 #define SFFT_FP64 0 /* samples, twiddles and FFT arithmetic in double                         */
-#define SFFT_FP32 1 /* samples, twiddles and FFT arithmetic in float (FP32 accumulation)      */
+#define SFFT_FP32 1 /* samples, twiddles and FFT arithmetic in float (FP32 accumulation);
+                       with refine = 1 the forward lattice DFTs run in double-float (float
+                       pairs, ~48 bits) and the refinement works on their high+low words      */
 
 #define SFFT_L_COR26 0    /* L = min odd n >= 4c/((c-2)ln(c-1)) (ln|Gamma| - ln delta), Cor 2.6 */
 #define SFFT_L_EQ42 1     /* a quarter of the Cor 2.6 bound, rounded up to odd, eq. (4.2)       */
@@ -156,7 +158,9 @@ int sfft_reconstruct_backward(sfft_plan* plan, const double* dcoef, void* dsampl
  *   kvec  device int32 [n_terms, d];  coef device complex double [n_terms];
  *   noise device complex double [sum M] or NULL;  samples_out device complex (plan precision).
  * Computed exactly through eq. (2.3): the coefficients are scattered into their buckets
- * k.z_l mod M_l and each lattice is inverse-transformed.  Asynchronous on the plan stream.
+ * k.z_l mod M_l and each lattice is inverse-transformed.  FP32 plans form buckets, transform
+ * and noise sum in FP32 (samples within a few FP32 ulps of the exact value plus noise).
+ * Asynchronous on the plan stream.
  */
 int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const double* coef, int64_t n_terms,
                             const double* noise, void* samples_out);

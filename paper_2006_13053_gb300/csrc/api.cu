@@ -205,7 +205,9 @@ int Plan::build_jobs() {
         jobs_fwd.push_back(a);
         // sampler: out (launch argument) = IDFT(C) + noise (launch argument), plan precision
         BlueJob sj = make_blue_job(t, prec, 1, 1.0);
-        sj.in = C + o; sj.io_flags = 16 | 32; sj.io_off = o; sj.inst = 0;
+        // FP32 plans scatter FP32 buckets into the first half of C (see k_scatter_terms)
+        sj.in = prec ? (const void*)(reinterpret_cast<c32*>(C) + o) : (const void*)(C + o);
+        sj.io_flags = 16 | 32; sj.io_off = o; sj.inst = 0;
         sj.scratch = buf_mode(prec) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
         jobs_samp.push_back(sj);
         // adjoint: out (launch argument) = (1/M) IDFT(C), plan precision
@@ -665,10 +667,11 @@ int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const do
     I.samp_out = samples_out;
     I.samp_noise = reinterpret_cast<const c64*>(noise);
     SFFT_TRY(P->io_upload());
-    SFFT_TRY(launch_clear(P->d_inst, 1, 0, 0, 1, st));
+    // buckets in the plan precision (eq. 2.3), inverse lattice DFTs, noise
+    SFFT_TRY(launch_clear(P->d_inst, 1, 0, 0, P->prec ? 2 : 1, st));
     if (n_terms > 0) SFFT_TRY(launch_scatter_terms(P->d_inst, 1, n_terms * P->L, st));
-    SFFT_TRY(launch_bluestein(P->d_jobs_samp, P->L, P->maxN, P->buf_mode(P->prec), P->prec, 0, P->prec, +1, EPI_ADDNOISE,
-                              P->d_inst, st));
+    SFFT_TRY(launch_bluestein(P->d_jobs_samp, P->L, P->maxN, P->buf_mode(P->prec), P->prec, P->prec, P->prec, +1,
+                              EPI_ADDNOISE, P->d_inst, st));
     return SFFT_OK;
 }
 

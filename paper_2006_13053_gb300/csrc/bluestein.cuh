@@ -310,11 +310,19 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
                 out[e] = ccv<TO>(X);
             }
             if (epi == EPI_ANALYZE) mx2 = fmax(mx2, scv<R>(abs2(X)));
-        } else {  // EPI_ADDNOISE
+        } else {  // EPI_ADDNOISE (noise complex double; added in the transform precision)
             const c64* aux = reinterpret_cast<const c64*>(auxp);
-            c64 r = ccv<double>(X);
-            if (aux) r = r + aux[e];
-            out[e] = ccv<TO>(r);
+            if constexpr (std::is_same<T, float>::value) {
+                if (aux) {
+                    const c64 z = aux[e];
+                    X = X + c32{(float)z.x, (float)z.y};
+                }
+                out[e] = ccv<TO>(X);
+            } else {
+                c64 r = ccv<double>(X);
+                if (aux) r = r + aux[e];
+                out[e] = ccv<TO>(r);
+            }
         }
     }
 };

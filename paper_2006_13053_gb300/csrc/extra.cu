@@ -298,10 +298,11 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
     }
     cudaStream_t st = B->st;
     SFFT_CU(cudaMemcpyAsync(B->d_inst, B->h_inst, sizeof(InstDesc) * n, cudaMemcpyHostToDevice, st));
-    SFFT_TRY(launch_clear(B->d_inst, n, 0, 0, 1, st));
+    SFFT_TRY(launch_clear(B->d_inst, n, 0, 0, B->prec ? 2 : 1, st));
     if (mx > 0) SFFT_TRY(launch_scatter_terms(B->d_inst, n, mx, st));
     for (const auto& f : B->samp)
-        SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.mode, B->prec, 0, B->prec, +1, EPI_ADDNOISE, B->d_inst, st));
+        SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.mode, B->prec, B->prec, B->prec, +1, EPI_ADDNOISE, B->d_inst,
+                                  st));
     SFFT_CU(cudaEventRecord(B->done, st));
     return SFFT_OK;
 }

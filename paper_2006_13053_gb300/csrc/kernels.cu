@@ -429,16 +429,40 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
 }
 
 // ================================================================== compaction (ascending Itilde)
-constexpr int kCompactThreads = 1024;
+// Ascending Itilde from the detection bits.  Each instance's ceil(n/32) bit words are split into
+// kCompactChunks contiguous chunks, one CTA each.  A CTA counts the set bits of all chunks before
+// its own (a block reduction over L2-resident words), scans its own chunk and writes its indices;
+// the last chunk's CTA records |Itilde|.  One launch, no inter-CTA waits.
+constexpr int kCompactThreads = 256;
+constexpr int kCompactChunks = 32;
+
+__device__ int64_t block_sum_i64(int64_t v, int64_t* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int64_t r = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    __syncthreads();
+    return r;
+}
+
 __global__ void __launch_bounds__(kCompactThreads) k_compact(InstDesc* __restrict__ insts) {
     __shared__ int64_t wsum[32];
-    InstDesc& I = insts[blockIdx.x];
+    InstDesc& I = insts[blockIdx.y];
     const int64_t W = (I.n + 31) >> 5;
-    const int64_t per = (W + blockDim.x - 1) / blockDim.x;
-    const int64_t w0 = threadIdx.x * per, w1 = min(W, w0 + per);
+    const int64_t chunk = (W + gridDim.x - 1) / gridDim.x;
+    const int64_t c0 = min(W, (int64_t)blockIdx.x * chunk), c1 = min(W, c0 + chunk);
+    const uint32_t* bits = I.detbits;
+    // set bits before this chunk
+    int64_t pre = 0;
+    for (int64_t w = threadIdx.x; w < c0; w += blockDim.x) pre += __popc(bits[w]);
+    const int64_t base = block_sum_i64(pre, wsum);
+    // this chunk: contiguous words per thread, block exclusive scan of their counts
+    const int64_t per = (c1 - c0 + blockDim.x - 1) / blockDim.x;
+    const int64_t w0 = min(c1, c0 + threadIdx.x * per), w1 = min(c1, w0 + per);
     int64_t c = 0;
-    for (int64_t w = w0; w < w1; ++w) c += __popc(I.detbits[w]);
-    // block exclusive scan of c
+    for (int64_t w = w0; w < w1; ++w) c += __popc(bits[w]);
     int64_t v = c;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int o = 1; o < 32; o <<= 1) {
@@ -456,10 +480,10 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(InstDesc* __restric
         wsum[lane] = t;
     }
     __syncthreads();
-    int64_t pos = v - c + (warp > 0 ? wsum[warp - 1] : 0);
-    const int64_t total = wsum[(blockDim.x >> 5) - 1];
+    int64_t pos = base + v - c + (warp > 0 ? wsum[warp - 1] : 0);
+    const int64_t total = base + wsum[(blockDim.x >> 5) - 1];
     for (int64_t w = w0; w < w1; ++w) {
-        uint32_t b = I.detbits[w];
+        uint32_t b = bits[w];
         while (b) {
             int t = __ffs(b) - 1;
             b &= b - 1;
@@ -467,7 +491,7 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(InstDesc* __restric
             ++pos;
         }
     }
-    if (threadIdx.x == 0) {
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) {
         I.cnt[0] = total;
         if (total > I.cap) atomicOr((unsigned long long*)&I.cnt[3], (unsigned long long)ERR_DET_CAP);
     }
@@ -479,18 +503,18 @@ __global__ void k_det_hashes(const InstDesc* __restrict__ insts) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nd = min(I.cnt[0], I.cap);
     const int warps = blockDim.x >> 5;
-    const int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
-    if (q >= nd) return;
-    const int lane = threadIdx.x & 31, L = I.L, d = I.d;
-    const int32_t* k = I.cand + I.det[q] * d;
-    for (int l = lane; l < L; l += 32) {
-        const int32_t* zl = I.z + l * d;
-        int64_t x = 0;
-        for (int t = 0; t < d; ++t) x += (int64_t)__ldg(k + t) * zl[t];
-        int64_t M = I.Ml[l];
-        int64_t r = x % M;
-        if (r < 0) r += M;
-        I.H[q * L + l] = (int32_t)r;
+    for (int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); q < nd; q += (int64_t)gridDim.x * warps) {
+        const int lane = threadIdx.x & 31, L = I.L, d = I.d;
+        const int32_t* k = I.cand + I.det[q] * d;
+        for (int l = lane; l < L; l += 32) {
+            const int32_t* zl = I.z + l * d;
+            int64_t x = 0;
+            for (int t = 0; t < d; ++t) x += (int64_t)__ldg(k + t) * zl[t];
+            int64_t M = I.Ml[l];
+            int64_t r = x % M;
+            if (r < 0) r += M;
+            I.H[q * L + l] = (int32_t)r;
+        }
     }
 }
 
@@ -555,50 +579,50 @@ __global__ void k_combine(const InstDesc* __restrict__ insts) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nd = min(I.cnt[0], I.cap);
     const int warps = blockDim.x >> 5;
-    const int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
-    if (q >= nd) return;
-    const int lane = threadIdx.x & 31, L = I.L;
-    const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
-    const c32* glo = I.ghat_lo;  // low words of a double-float transform (or NULL)
-    auto bucket = [&](int64_t b) -> c64 {
-        const cplx<TS> v = g[b];
-        c64 r = {(double)v.x, (double)v.y};
-        if (glo) { const c32 w = glo[b]; r.x += (double)w.x; r.y += (double)w.y; }
-        return r;
-    };
-    c64 va = {0, 0}, vb = {0, 0};
-    int fa = 0, fb = 0;  // collision-free flags (hybrid)
-    if (lane < L) {
-        int h = I.H[q * L + lane];
-        va = bucket(I.soff[lane] + h);
-        if (I.combine == SFFT_COMBINE_HYBRID) fa = I.coll[I.soff[lane] + h] == 1;
-    }
-    if (lane + 32 < L) {
-        int h = I.H[q * L + lane + 32];
-        vb = bucket(I.soff[lane + 32] + h);
-        if (I.combine == SFFT_COMBINE_HYBRID) fb = I.coll[I.soff[lane + 32] + h] == 1;
-    }
-    // float buckets convert to double exactly, so the ranking equals the working-precision one
-    double mre, mim;
-    int lre, lim;
-    warp_median_f64(va.x, vb.x, L, lane, mre, lre);
-    warp_median_f64(va.y, vb.y, L, lane, mim, lim);
-    c64 out = {mre, mim};
-    if (I.combine == SFFT_COMBINE_HYBRID) {
-        double sr = (fa ? va.x : 0.0) + (fb ? vb.x : 0.0);
-        double si = (fa ? va.y : 0.0) + (fb ? vb.y : 0.0);
-        int nf = fa + fb;
-        for (int o = 16; o > 0; o >>= 1) {
-            sr += __shfl_xor_sync(0xffffffffu, sr, o);
-            si += __shfl_xor_sync(0xffffffffu, si, o);
-            nf += __shfl_xor_sync(0xffffffffu, nf, o);
+    for (int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); q < nd; q += (int64_t)gridDim.x * warps) {
+        const int lane = threadIdx.x & 31, L = I.L;
+        const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
+        const c32* glo = I.ghat_lo;  // low words of a double-float transform (or NULL)
+        auto bucket = [&](int64_t b) -> c64 {
+            const cplx<TS> v = g[b];
+            c64 r = {(double)v.x, (double)v.y};
+            if (glo) { const c32 w = glo[b]; r.x += (double)w.x; r.y += (double)w.y; }
+            return r;
+        };
+        c64 va = {0, 0}, vb = {0, 0};
+        int fa = 0, fb = 0;  // collision-free flags (hybrid)
+        if (lane < L) {
+            int h = I.H[q * L + lane];
+            va = bucket(I.soff[lane] + h);
+            if (I.combine == SFFT_COMBINE_HYBRID) fa = I.coll[I.soff[lane] + h] == 1;
         }
-        if (nf > 0) out = c64{sr / nf, si / nf};
-    }
-    if (lane == 0) {
-        I.coef[q] = out;
-        I.sel[2 * q] = (uint8_t)lre;
-        I.sel[2 * q + 1] = (uint8_t)lim;
+        if (lane + 32 < L) {
+            int h = I.H[q * L + lane + 32];
+            vb = bucket(I.soff[lane + 32] + h);
+            if (I.combine == SFFT_COMBINE_HYBRID) fb = I.coll[I.soff[lane + 32] + h] == 1;
+        }
+        // float buckets convert to double exactly, so the ranking equals the working-precision one
+        double mre, mim;
+        int lre, lim;
+        warp_median_f64(va.x, vb.x, L, lane, mre, lre);
+        warp_median_f64(va.y, vb.y, L, lane, mim, lim);
+        c64 out = {mre, mim};
+        if (I.combine == SFFT_COMBINE_HYBRID) {
+            double sr = (fa ? va.x : 0.0) + (fb ? vb.x : 0.0);
+            double si = (fa ? va.y : 0.0) + (fb ? vb.y : 0.0);
+            int nf = fa + fb;
+            for (int o = 16; o > 0; o >>= 1) {
+                sr += __shfl_xor_sync(0xffffffffu, sr, o);
+                si += __shfl_xor_sync(0xffffffffu, si, o);
+                nf += __shfl_xor_sync(0xffffffffu, nf, o);
+            }
+            if (nf > 0) out = c64{sr / nf, si / nf};
+        }
+        if (lane == 0) {
+            I.coef[q] = out;
+            I.sel[2 * q] = (uint8_t)lre;
+            I.sel[2 * q + 1] = (uint8_t)lim;
+        }
     }
 }
 
@@ -611,33 +635,33 @@ __global__ void k_refine_update(const InstDesc* __restrict__ insts) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nd = min(I.cnt[0], I.cap);
     const int warps = blockDim.x >> 5;
-    const int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5);
-    if (q >= nd) return;
-    const int lane = threadIdx.x & 31, L = I.L;
-    const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
-    const c32* glo = I.ghat_lo;
-    auto rhat = [&](int l) -> c64 {
-        const int64_t b = I.soff[l] + I.H[q * L + l];
-        const cplx<TS> v = g[b];
-        c64 r = {(double)v.x, (double)v.y};
-        if (glo) {
-            const c32 w = glo[b];
-            r.x += (double)w.x;
-            r.y += (double)w.y;
+    for (int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); q < nd; q += (int64_t)gridDim.x * warps) {
+        const int lane = threadIdx.x & 31, L = I.L;
+        const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
+        const c32* glo = I.ghat_lo;
+        auto rhat = [&](int l) -> c64 {
+            const int64_t b = I.soff[l] + I.H[q * L + l];
+            const cplx<TS> v = g[b];
+            c64 r = {(double)v.x, (double)v.y};
+            if (glo) {
+                const c32 w = glo[b];
+                r.x += (double)w.x;
+                r.y += (double)w.y;
+            }
+            const c64 c = I.C[b];
+            return c64{r.x - c.x, r.y - c.y};
+        };
+        c64 va = {0, 0}, vb = {0, 0};
+        if (lane < L) va = rhat(lane);
+        if (lane + 32 < L) vb = rhat(lane + 32);
+        double mre, mim;
+        int lre, lim;
+        warp_median_f64(va.x, vb.x, L, lane, mre, lre);
+        warp_median_f64(va.y, vb.y, L, lane, mim, lim);
+        if (lane == 0) {
+            c64 c = I.coef[q];
+            I.coef[q] = c64{c.x + mre, c.y + mim};
         }
-        const c64 c = I.C[b];
-        return c64{r.x - c.x, r.y - c.y};
-    };
-    c64 va = {0, 0}, vb = {0, 0};
-    if (lane < L) va = rhat(lane);
-    if (lane + 32 < L) vb = rhat(lane + 32);
-    double mre, mim;
-    int lre, lim;
-    warp_median_f64(va.x, vb.x, L, lane, mre, lre);
-    warp_median_f64(va.y, vb.y, L, lane, mim, lim);
-    if (lane == 0) {
-        c64 c = I.coef[q];
-        I.coef[q] = c64{c.x + mre, c.y + mim};
     }
 }
 
@@ -815,9 +839,15 @@ __global__ void k_scatter_terms(const InstDesc* __restrict__ insts) {
         int64_t M = I.Ml[l];
         int64_t r = x % M;
         if (r < 0) r += M;
-        c64* dst = I.C + I.soff[l] + r;
-        atomicAdd(&dst->x, coef[q].x);
-        atomicAdd(&dst->y, coef[q].y);
+        if (I.prec) {  // FP32 plans: FP32 buckets (the samples are FP32)
+            c32* dst = reinterpret_cast<c32*>(I.C) + I.soff[l] + r;
+            atomicAdd(&dst->x, (float)coef[q].x);
+            atomicAdd(&dst->y, (float)coef[q].y);
+        } else {
+            c64* dst = I.C + I.soff[l] + r;
+            atomicAdd(&dst->x, coef[q].x);
+            atomicAdd(&dst->y, coef[q].y);
+        }
     }
 }
 
@@ -885,8 +915,11 @@ __global__ void k_clear_inst(InstDesc* __restrict__ insts, int clear_det, int cl
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < W; i += stride) I.detbits[i] = 0;
     if (clear_coll)
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < SM; i += stride) I.coll[i] = 0;
-    if (clear_C)
+    if (clear_C == 1)  // FP64 buckets
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < SM; i += stride) I.C[i] = c64{0, 0};
+    if (clear_C == 2)  // FP32 buckets of the sampler of FP32 plans (first half of the buffer)
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < SM; i += stride)
+            reinterpret_cast<c32*>(I.C)[i] = c32{0.f, 0.f};
     if (clear_det && blockIdx.x == 0 && threadIdx.x < 8) I.cnt[threadIdx.x] = 0;
 }
 
@@ -961,13 +994,19 @@ int launch_zero_test(const LatDesc* dl, int nlat, InstDesc* di, int prec, double
 }
 
 int launch_compact(InstDesc* di, int ninst, cudaStream_t st) {
-    k_compact<<<ninst, kCompactThreads, 0, st>>>(di);
+    k_compact<<<dim3(kCompactChunks, ninst), kCompactThreads, 0, st>>>(di);
     return launch_check("k_compact");
 }
 
+// per-detected-candidate kernels: one warp per candidate in a grid-stride loop over a grid of
+// about 8 resident CTAs per SM for the whole batch (|Itilde| is only known on the device)
+static int det_grid(int64_t maxdet, int ninst) {
+    const int64_t need = (maxdet + 7) / 8, cap = (152 * 8 + ninst - 1) / ninst;
+    return (int)std::max<int64_t>(1, std::min(need, cap));
+}
+
 int launch_det_hashes(const InstDesc* di, int ninst, int64_t maxdet, cudaStream_t st) {
-    int gx = (int)((maxdet + 7) / 8);
-    if (gx < 1) gx = 1;
+    const int gx = det_grid(maxdet, ninst);
     k_det_hashes<<<dim3(gx, ninst), 256, 0, st>>>(di);
     return launch_check("k_det_hashes");
 }
@@ -978,8 +1017,7 @@ int launch_collisions(const InstDesc* di, int ninst, cudaStream_t st) {
 }
 
 int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int mode, cudaStream_t st) {
-    int gx = (int)((maxdet + 7) / 8);
-    if (gx < 1) gx = 1;
+    const int gx = det_grid(maxdet, ninst);
     if (mode == 1) {
         if (prec) k_refine_update<float><<<dim3(gx, ninst), 256, 0, st>>>(di);
         else k_refine_update<double><<<dim3(gx, ninst), 256, 0, st>>>(di);
