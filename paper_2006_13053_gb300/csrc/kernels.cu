@@ -86,7 +86,13 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
     c32* glo = I.ghat_lo ? I.ghat_lo + D.soff : nullptr;
     const cplx<TS>* x = reinterpret_cast<const cplx<TS>*>(I.samples) + D.soff;
     const c64* tab = reinterpret_cast<const c64*>(D.dft64);
-    const double band = kappa_u_log * log2((double)D.N) * S.rms;
+    // FP64 scalars are formed by one thread and shared: on this GPU a warp-wide FP64 instruction
+    // costs as much as dozens of FP32 ones
+    __shared__ double s_band, s_tlo, s_thi;
+    __shared__ TS s_lo2, s_hi2;
+    if (threadIdx.x == 0) s_band = kappa_u_log * log2((double)D.N) * S.rms;
+    __syncthreads();
+    const double band = s_band;
     auto full = [&](int h) -> c64 {  // the bucket in the transform's full precision
         cplx<TS> v = g[h];
         c64 r = {(double)v.x, (double)v.y};
@@ -108,8 +114,12 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
     // ---- exact maximum: FP64 re-test of every bucket that could be the maximum
     double tau = I.tau_abs;
     if (I.tau_rel > 0) {
-        const double lo = fmax(S.max_abs * (1.0 - 1.0 / 1048576.0) - 2.0 * band, 0.0);
-        const TS lo2 = (TS)fmin(lo * lo * (1.0 - slack), big);
+        if (threadIdx.x == 0) {
+            const double lo = fmax(S.max_abs * (1.0 - 1.0 / 1048576.0) - 2.0 * band, 0.0);
+            s_lo2 = (TS)fmin(lo * lo * (1.0 - slack), big);
+        }
+        __syncthreads();
+        const TS lo2 = s_lo2;
         for (int h = threadIdx.x; h < M; h += blockDim.x) {
             cplx<TS> v = g[h];
             if (v.x * v.x + v.y * v.y >= lo2) {
@@ -139,11 +149,18 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
         if (threadIdx.x == 0) { S.max_abs = s_max64; gcount = 0; }
         __syncthreads();
     }
-    if (threadIdx.x == 0) { S.tau = tau; S.band = band; }
+    if (threadIdx.x == 0) {
+        S.tau = tau;
+        S.band = band;
+        s_tlo = fmax(tau - band, 0.0);
+        s_thi = tau + band;
+        s_lo2 = (TS)fmin(s_tlo * s_tlo * (1.0 - slack), big);  // below: certainly zero
+        s_hi2 = (TS)fmin(s_thi * s_thi * (1.0 + slack), big);  // above: certainly non-zero
+    }
+    __syncthreads();
     // ---- threshold: one warp writes 32 consecutive buckets per ballot
-    const double tlo = fmax(tau - band, 0.0), thi = tau + band;
-    const TS lo2 = (TS)fmin(tlo * tlo * (1.0 - slack), big);  // below: certainly zero
-    const TS hi2 = (TS)fmin(thi * thi * (1.0 + slack), big);  // above: certainly non-zero
+    const double tlo = s_tlo, thi = s_thi;
+    const TS lo2 = s_lo2, hi2 = s_hi2;
     uint32_t* words = I.nzbits + D.boff;
     const int nw = (M + 31) >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
@@ -564,10 +581,44 @@ __device__ __forceinline__ long long ord_key(double v) {
     return b ^ ((b >> 63) & 0x7fffffffffffffffll);
 }
 
+// Median of L <= 64 int64 keys spread over a warp (lane l holds the keys of lattices l and l+32)
+// by a bitonic sort of the (key, lattice) pairs: element e = 2 lane + j, j = 0 lattice `lane`,
+// j = 1 lattice `lane + 32`, missing lattices padded with +inf.  The result is the (L-1)/2-th
+// smallest pair, i.e. the value and tie rule of warp_median (equal keys: lower lattice first).
+__device__ __forceinline__ void warp_median_sort(long long ka, long long kb, int L, int lane, int& lsel) {
+    long long k0 = lane < L ? ka : LLONG_MAX, k1 = lane + 32 < L ? kb : LLONG_MAX;
+    int i0 = lane, i1 = lane + 32;
+    auto lt = [](long long ka_, int ia, long long kb_, int ib) { return ka_ < kb_ || (ka_ == kb_ && ia < ib); };
+#pragma unroll
+    for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+        for (int d = size >> 1; d > 0; d >>= 1) {
+            if (d == 1) {  // both elements in this lane
+                const bool up = ((2 * lane) & size) == 0;
+                const bool sw = up ? lt(k1, i1, k0, i0) : lt(k0, i0, k1, i1);
+                if (sw) {
+                    const long long tk = k0; k0 = k1; k1 = tk;
+                    const int ti = i0; i0 = i1; i1 = ti;
+                }
+            } else {
+                const int m = d >> 1;  // partner lane = lane ^ m, same j
+                const long long p0 = __shfl_xor_sync(0xffffffffu, k0, m), p1 = __shfl_xor_sync(0xffffffffu, k1, m);
+                const int q0 = __shfl_xor_sync(0xffffffffu, i0, m), q1 = __shfl_xor_sync(0xffffffffu, i1, m);
+                const int e0 = 2 * lane;
+                const bool up = (e0 & size) == 0, low = (e0 & d) == 0;  // same for j = 0 and 1
+                const bool want_min = up == low;
+                if (want_min == lt(p0, q0, k0, i0)) { k0 = p0; i0 = q0; }
+                if (want_min == lt(p1, q1, k1, i1)) { k1 = p1; i1 = q1; }
+            }
+        }
+    }
+    const int mid = (L - 1) >> 1;
+    lsel = __shfl_sync(0xffffffffu, (mid & 1) ? i1 : i0, mid >> 1);
+}
+
 // median of doubles across the warp (values and tie rule of warp_median)
 __device__ __forceinline__ void warp_median_f64(double va, double vb, int L, int lane, double& med, int& lsel) {
-    long long km;
-    warp_median<long long>(ord_key(va), ord_key(vb), L, lane, km, lsel);
+    warp_median_sort(ord_key(va), ord_key(vb), L, lane, lsel);
     const int owner = lsel & 31;
     const double a = __shfl_sync(0xffffffffu, va, owner), b = __shfl_sync(0xffffffffu, vb, owner);
     med = lsel < 32 ? a : b;
