@@ -545,34 +545,6 @@ __global__ void k_collisions(const InstDesc* __restrict__ insts) {
     }
 }
 
-// rank-based selection of the median of the L lane-distributed values (L odd); returns the
-// median value and the lattice it came from (ties: lower lattice index ranks lower)
-template <class T>
-__device__ __forceinline__ void warp_median(T va, T vb, int L, int lane, T& med, int& lsel) {
-    const int mid = (L - 1) >> 1;
-    int ra = 0, rb = 0;  // ranks of lattice lane and lane+32
-    for (int src = 0; src < 32; ++src) {
-        T a = __shfl_sync(0xffffffffu, va, src);
-        T b = __shfl_sync(0xffffffffu, vb, src);
-        int la = src, lb = src + 32;
-        if (la < L) {
-            ra += (a < va) || (a == va && la < lane);
-            rb += (a < vb) || (a == vb && la < lane + 32);
-        }
-        if (lb < L) {
-            ra += (b < va) || (b == va && lb < lane);
-            rb += (b < vb) || (b == vb && lb < lane + 32);
-        }
-    }
-    bool ha = lane < L && ra == mid, hb = lane + 32 < L && rb == mid;
-    uint32_t ba = __ballot_sync(0xffffffffu, ha), bb = __ballot_sync(0xffffffffu, hb);
-    int owner = ba ? __ffs(ba) - 1 : __ffs(bb) - 1;
-    bool first = ba != 0;
-    T v = first ? va : vb;
-    med = __shfl_sync(0xffffffffu, v, owner);
-    lsel = first ? owner : owner + 32;
-}
-
 // Order-preserving integer key of a double (-0 mapped to +0, NaN never occurs): the warp
 // median ranks keys with integer compares instead of the low-rate FP64 pipe.
 __device__ __forceinline__ long long ord_key(double v) {
@@ -581,86 +553,100 @@ __device__ __forceinline__ long long ord_key(double v) {
     return b ^ ((b >> 63) & 0x7fffffffffffffffll);
 }
 
-// Median of L <= 64 int64 keys spread over a warp (lane l holds the keys of lattices l and l+32)
-// by a bitonic sort of the (key, lattice) pairs: element e = 2 lane + j, j = 0 lattice `lane`,
-// j = 1 lattice `lane + 32`, missing lattices padded with +inf.  The result is the (L-1)/2-th
-// smallest pair, i.e. the value and tie rule of warp_median (equal keys: lower lattice first).
-__device__ __forceinline__ void warp_median_sort(long long ka, long long kb, int L, int lane, int& lsel) {
+// Median of L <= 64 packed keys spread over a warp (lane l holds the keys of lattices l and l+32)
+// by a bitonic sort: element e = 2 lane + j (j = 0: lattice `lane`, j = 1: lattice `lane + 32`),
+// missing lattices padded with +inf.  A packed key holds an order-preserving value key in its
+// high 58 bits and the lattice in its low 6, so equal values order by lattice (lower first); the
+// (L-1)/2-th smallest is the median of eq. (2.6) for odd L.  Values that differ only below the
+// key's resolution (2^-46 relative for doubles, 2^-50 for double-float pairs) count as equal.
+__device__ __forceinline__ long long warp_median_packed(long long ka, long long kb, int L, int lane) {
     long long k0 = lane < L ? ka : LLONG_MAX, k1 = lane + 32 < L ? kb : LLONG_MAX;
-    int i0 = lane, i1 = lane + 32;
-    auto lt = [](long long ka_, int ia, long long kb_, int ib) { return ka_ < kb_ || (ka_ == kb_ && ia < ib); };
 #pragma unroll
     for (int size = 2; size <= 64; size <<= 1) {
 #pragma unroll
         for (int d = size >> 1; d > 0; d >>= 1) {
             if (d == 1) {  // both elements in this lane
                 const bool up = ((2 * lane) & size) == 0;
-                const bool sw = up ? lt(k1, i1, k0, i0) : lt(k0, i0, k1, i1);
-                if (sw) {
-                    const long long tk = k0; k0 = k1; k1 = tk;
-                    const int ti = i0; i0 = i1; i1 = ti;
+                if (up == (k1 < k0)) {
+                    const long long t = k0; k0 = k1; k1 = t;
                 }
             } else {
                 const int m = d >> 1;  // partner lane = lane ^ m, same j
                 const long long p0 = __shfl_xor_sync(0xffffffffu, k0, m), p1 = __shfl_xor_sync(0xffffffffu, k1, m);
-                const int q0 = __shfl_xor_sync(0xffffffffu, i0, m), q1 = __shfl_xor_sync(0xffffffffu, i1, m);
-                const int e0 = 2 * lane;
-                const bool up = (e0 & size) == 0, low = (e0 & d) == 0;  // same for j = 0 and 1
+                const bool up = ((2 * lane) & size) == 0, low = ((2 * lane) & d) == 0;
                 const bool want_min = up == low;
-                if (want_min == lt(p0, q0, k0, i0)) { k0 = p0; i0 = q0; }
-                if (want_min == lt(p1, q1, k1, i1)) { k1 = p1; i1 = q1; }
+                if (want_min == (p0 < k0)) k0 = p0;
+                if (want_min == (p1 < k1)) k1 = p1;
             }
         }
     }
     const int mid = (L - 1) >> 1;
-    lsel = __shfl_sync(0xffffffffu, (mid & 1) ? i1 : i0, mid >> 1);
+    return __shfl_sync(0xffffffffu, (mid & 1) ? k1 : k0, mid >> 1);
+}
+__device__ __forceinline__ long long pack_key(long long value_key, int lattice) {
+    return (value_key & ~63ll) | lattice;
 }
 
-// median of doubles across the warp (values and tie rule of warp_median)
-__device__ __forceinline__ void warp_median_f64(double va, double vb, int L, int lane, double& med, int& lsel) {
-    warp_median_sort(ord_key(va), ord_key(vb), L, lane, lsel);
-    const int owner = lsel & 31;
-    const double a = __shfl_sync(0xffffffffu, va, owner), b = __shfl_sync(0xffffffffu, vb, owner);
-    med = lsel < 32 ? a : b;
+// Order-preserving keys.  A normalised double-float pair (hi = fl(hi + lo)) orders like its value
+// lexicographically in (hi, lo), because rounding to nearest is monotone; -0 counts as +0.
+__device__ __forceinline__ int ord32(float f) {
+    int b = __float_as_int(f);
+    if (b == (int)0x80000000) b = 0;
+    return b ^ ((b >> 31) & 0x7fffffff);
+}
+__device__ __forceinline__ long long df_key(float hi, float lo) {
+    return (long long)(((unsigned long long)(long long)ord32(hi) << 32) | (unsigned)(ord32(lo) ^ (int)0x80000000));
+}
+template <class TS> __device__ __forceinline__ long long val_key(TS hi, float lo) {
+    if constexpr (sizeof(TS) == 8) return ord_key((double)hi);
+    else return df_key((float)hi, lo);
+}
+// value of lane (l & 31)'s a (l < 32) or b (l >= 32)
+template <class T> __device__ __forceinline__ T pick(T a, T b, int l) {
+    const T x = __shfl_sync(0xffffffffu, a, l & 31), y = __shfl_sync(0xffffffffu, b, l & 31);
+    return l < 32 ? x : y;
 }
 
-// Median combine (eq. 2.6) or the Remark 2.8 hybrid combine on the detected set: coef = combine(ghat)
+// Median combine (eq. 2.6) or the Remark 2.8 hybrid combine on the detected set: coef = combine(ghat).
+// The ranking uses integer keys of the buckets (float, double-float pair or double); only the
+// selected median is converted to double.
 template <class TS>
 __global__ void k_combine(const InstDesc* __restrict__ insts) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nd = min(I.cnt[0], I.cap);
     const int warps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, L = I.L;
+    const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
+    const c32* glo = I.ghat_lo;  // low words of a double-float transform (or NULL)
+    const bool hybrid = I.combine == SFFT_COMBINE_HYBRID;
     for (int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); q < nd; q += (int64_t)gridDim.x * warps) {
-        const int lane = threadIdx.x & 31, L = I.L;
-        const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
-        const c32* glo = I.ghat_lo;  // low words of a double-float transform (or NULL)
-        auto bucket = [&](int64_t b) -> c64 {
-            const cplx<TS> v = g[b];
-            c64 r = {(double)v.x, (double)v.y};
-            if (glo) { const c32 w = glo[b]; r.x += (double)w.x; r.y += (double)w.y; }
-            return r;
-        };
-        c64 va = {0, 0}, vb = {0, 0};
+        cplx<TS> ha = {0, 0}, hb = {0, 0};
+        c32 la = {0.f, 0.f}, lb = {0.f, 0.f};
         int fa = 0, fb = 0;  // collision-free flags (hybrid)
         if (lane < L) {
-            int h = I.H[q * L + lane];
-            va = bucket(I.soff[lane] + h);
-            if (I.combine == SFFT_COMBINE_HYBRID) fa = I.coll[I.soff[lane] + h] == 1;
+            const int64_t b = I.soff[lane] + I.H[q * L + lane];
+            ha = g[b];
+            if (glo) la = glo[b];
+            if (hybrid) fa = I.coll[b] == 1;
         }
         if (lane + 32 < L) {
-            int h = I.H[q * L + lane + 32];
-            vb = bucket(I.soff[lane + 32] + h);
-            if (I.combine == SFFT_COMBINE_HYBRID) fb = I.coll[I.soff[lane + 32] + h] == 1;
+            const int64_t b = I.soff[lane + 32] + I.H[q * L + lane + 32];
+            hb = g[b];
+            if (glo) lb = glo[b];
+            if (hybrid) fb = I.coll[b] == 1;
         }
-        // float buckets convert to double exactly, so the ranking equals the working-precision one
-        double mre, mim;
-        int lre, lim;
-        warp_median_f64(va.x, vb.x, L, lane, mre, lre);
-        warp_median_f64(va.y, vb.y, L, lane, mim, lim);
-        c64 out = {mre, mim};
-        if (I.combine == SFFT_COMBINE_HYBRID) {
-            double sr = (fa ? va.x : 0.0) + (fb ? vb.x : 0.0);
-            double si = (fa ? va.y : 0.0) + (fb ? vb.y : 0.0);
+        const int lre = (int)(warp_median_packed(pack_key(val_key<TS>(ha.x, la.x), lane),
+                                                 pack_key(val_key<TS>(hb.x, lb.x), lane + 32), L, lane) & 63);
+        const int lim = (int)(warp_median_packed(pack_key(val_key<TS>(ha.y, la.y), lane),
+                                                 pack_key(val_key<TS>(hb.y, lb.y), lane + 32), L, lane) & 63);
+        c64 out = {(double)pick(ha.x, hb.x, lre), (double)pick(ha.y, hb.y, lim)};
+        if (glo) {
+            out.x += (double)pick(la.x, lb.x, lre);
+            out.y += (double)pick(la.y, lb.y, lim);
+        }
+        if (hybrid) {
+            double sr = (fa ? (double)ha.x + (double)la.x : 0.0) + (fb ? (double)hb.x + (double)lb.x : 0.0);
+            double si = (fa ? (double)ha.y + (double)la.y : 0.0) + (fb ? (double)hb.y + (double)lb.y : 0.0);
             int nf = fa + fb;
             for (int o = 16; o > 0; o >>= 1) {
                 sr += __shfl_xor_sync(0xffffffffu, sr, o);
@@ -679,17 +665,17 @@ __global__ void k_combine(const InstDesc* __restrict__ insts) {
 
 // Refinement update: the residual f - sum_{k in Itilde} c_k e^{2 pi i k.x} has the lattice DFT
 // r_hat_h = ghat_h - C_h (aliasing formula, eq. 2.3), C_h = sum of c_k over the detected k with
-// h_kl = h.  c_k += median_l Re r_hat + i median_l Im r_hat at h_kl, all in FP64; ghat is the
-// forward transform (FP64, or a double-float pair hi + lo for FP32 plans with refinement).
+// h_kl = h.  c_k += median_l Re r_hat + i median_l Im r_hat at h_kl, in FP64; ghat is the forward
+// transform (FP64, or a double-float pair hi + lo for FP32 plans with refinement).
 template <class TS>
 __global__ void k_refine_update(const InstDesc* __restrict__ insts) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nd = min(I.cnt[0], I.cap);
     const int warps = blockDim.x >> 5;
+    const int lane = threadIdx.x & 31, L = I.L;
+    const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
+    const c32* glo = I.ghat_lo;
     for (int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); q < nd; q += (int64_t)gridDim.x * warps) {
-        const int lane = threadIdx.x & 31, L = I.L;
-        const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
-        const c32* glo = I.ghat_lo;
         auto rhat = [&](int l) -> c64 {
             const int64_t b = I.soff[l] + I.H[q * L + l];
             const cplx<TS> v = g[b];
@@ -705,18 +691,18 @@ __global__ void k_refine_update(const InstDesc* __restrict__ insts) {
         c64 va = {0, 0}, vb = {0, 0};
         if (lane < L) va = rhat(lane);
         if (lane + 32 < L) vb = rhat(lane + 32);
-        double mre, mim;
-        int lre, lim;
-        warp_median_f64(va.x, vb.x, L, lane, mre, lre);
-        warp_median_f64(va.y, vb.y, L, lane, mim, lim);
+        const int lre = (int)(warp_median_packed(pack_key(ord_key(va.x), lane), pack_key(ord_key(vb.x), lane + 32), L,
+                                                 lane) & 63);
+        const int lim = (int)(warp_median_packed(pack_key(ord_key(va.y), lane), pack_key(ord_key(vb.y), lane + 32), L,
+                                                 lane) & 63);
+        const double dre = pick(va.x, vb.x, lre), dim = pick(va.y, vb.y, lim);
         if (lane == 0) {
-            c64 c = I.coef[q];
-            I.coef[q] = c64{c.x + mre, c.y + mim};
+            const c64 c = I.coef[q];
+            I.coef[q] = c64{c.x + dre, c.y + dim};
         }
     }
 }
 
-// scatter the detected coefficients into their buckets: C_l[h_kl] += c_k
 __global__ void k_scatter_coef(const InstDesc* __restrict__ insts) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nd = min(I.cnt[0], I.cap);
@@ -725,9 +711,9 @@ __global__ void k_scatter_coef(const InstDesc* __restrict__ insts) {
         int64_t q = e / L;
         int l = (int)(e - q * L);
         c64 c = I.coef[q];
-        c64* dst = I.C + I.soff[l] + I.H[e];
-        atomicAdd(&dst->x, c.x);
-        atomicAdd(&dst->y, c.y);
+        const int64_t b = I.soff[l] + I.H[e];
+        atomicAdd(&I.C[b].x, c.x);
+        atomicAdd(&I.C[b].y, c.y);
     }
 }
 
