@@ -108,6 +108,95 @@ template <int R, int S, class T> __device__ __forceinline__ void bfly(cplx<T>* v
     }
 }
 
+// cos and sin of 2 pi j / R (R = 6, 8, 9, 10, 12, 15, 16; 0 < j < R, not a quarter turn) for the
+// inner twiddles of the fused radix pairs, as doubles and as double-float pairs (hi = nearest
+// float, lo = the remainder); values from 50-digit evaluations
+struct RootCS {
+    double c, s;
+    float ch, cl, sh, sl;
+};
+__host__ __device__ constexpr RootCS root_cs(int R, int j) {
+    switch (R * 64 + j) {
+        case 385: return RootCS{0.5, 0.8660254037844386, 0.5f, 0.0f, 0.8660253882408142f, 1.5543625053737742e-08f};  // 1/6
+        case 386: return RootCS{-0.5, 0.8660254037844386, -0.5f, 0.0f, 0.8660253882408142f, 1.5543625053737742e-08f};  // 2/6
+        case 388: return RootCS{-0.5, -0.8660254037844386, -0.5f, -0.0f, -0.8660253882408142f, -1.5543625053737742e-08f};  // 4/6
+        case 389: return RootCS{0.5, -0.8660254037844386, 0.5f, 0.0f, -0.8660253882408142f, -1.5543625053737742e-08f};  // 5/6
+        case 513: return RootCS{0.7071067811865476, 0.7071067811865476, 0.7071067690849304f, 1.2101617485882343e-08f, 0.7071067690849304f, 1.2101617485882343e-08f};  // 1/8
+        case 515: return RootCS{-0.7071067811865476, 0.7071067811865476, -0.7071067690849304f, -1.2101617485882343e-08f, 0.7071067690849304f, 1.2101617485882343e-08f};  // 3/8
+        case 517: return RootCS{-0.7071067811865476, -0.7071067811865476, -0.7071067690849304f, -1.2101617485882343e-08f, -0.7071067690849304f, -1.2101617485882343e-08f};  // 5/8
+        case 519: return RootCS{0.7071067811865476, -0.7071067811865476, 0.7071067690849304f, 1.2101617485882343e-08f, -0.7071067690849304f, -1.2101617485882343e-08f};  // 7/8
+        case 577: return RootCS{0.766044443118978, 0.6427876096865394, 0.7660444378852844f, 5.2336934786012534e-09f, 0.6427876353263855f, -2.5639845802061245e-08f};  // 1/9
+        case 578: return RootCS{0.17364817766693036, 0.984807753012208, 0.1736481785774231f, -9.10492736760915e-10f, 0.9848077297210693f, 2.3291137907222037e-08f};  // 2/9
+        case 579: return RootCS{-0.5, 0.8660254037844386, -0.5f, -0.0f, 0.8660253882408142f, 1.5543625053737742e-08f};  // 3/9
+        case 580: return RootCS{-0.9396926207859084, 0.3420201433256687, -0.9396926164627075f, -4.323200908373792e-09f, 0.3420201539993286f, -1.0673660177928923e-08f};  // 4/9
+        case 581: return RootCS{-0.9396926207859084, -0.3420201433256687, -0.9396926164627075f, -4.323200908373792e-09f, -0.3420201539993286f, 1.0673660177928923e-08f};  // 5/9
+        case 582: return RootCS{-0.5, -0.8660254037844386, -0.5f, 0.0f, -0.8660253882408142f, -1.5543625053737742e-08f};  // 6/9
+        case 583: return RootCS{0.17364817766693036, -0.984807753012208, 0.1736481785774231f, -9.10492736760915e-10f, -0.9848077297210693f, -2.3291137907222037e-08f};  // 7/9
+        case 584: return RootCS{0.766044443118978, -0.6427876096865394, 0.7660444378852844f, 5.2336934786012534e-09f, -0.6427876353263855f, 2.5639845802061245e-08f};  // 8/9
+        case 641: return RootCS{0.8090169943749475, 0.5877852522924731, 0.80901700258255f, -8.207602597565256e-09f, 0.5877852439880371f, 8.304436249773062e-09f};  // 1/10
+        case 642: return RootCS{0.30901699437494745, 0.9510565162951535, 0.30901700258255005f, -8.207602597565256e-09f, 0.9510565400123596f, -2.3717205976936384e-08f};  // 2/10
+        case 643: return RootCS{-0.30901699437494745, 0.9510565162951535, -0.30901700258255005f, 8.207602597565256e-09f, 0.9510565400123596f, -2.3717205976936384e-08f};  // 3/10
+        case 644: return RootCS{-0.8090169943749475, 0.5877852522924731, -0.80901700258255f, 8.207602597565256e-09f, 0.5877852439880371f, 8.304436249773062e-09f};  // 4/10
+        case 646: return RootCS{-0.8090169943749475, -0.5877852522924731, -0.80901700258255f, 8.207602597565256e-09f, -0.5877852439880371f, -8.304436249773062e-09f};  // 6/10
+        case 647: return RootCS{-0.30901699437494745, -0.9510565162951535, -0.30901700258255005f, 8.207602597565256e-09f, -0.9510565400123596f, 2.3717205976936384e-08f};  // 7/10
+        case 648: return RootCS{0.30901699437494745, -0.9510565162951535, 0.30901700258255005f, -8.207602597565256e-09f, -0.9510565400123596f, 2.3717205976936384e-08f};  // 8/10
+        case 649: return RootCS{0.8090169943749475, -0.5877852522924731, 0.80901700258255f, -8.207602597565256e-09f, -0.5877852439880371f, -8.304436249773062e-09f};  // 9/10
+        case 769: return RootCS{0.8660254037844386, 0.5, 0.8660253882408142f, 1.5543625053737742e-08f, 0.5f, 0.0f};  // 1/12
+        case 770: return RootCS{0.5, 0.8660254037844386, 0.5f, 0.0f, 0.8660253882408142f, 1.5543625053737742e-08f};  // 2/12
+        case 772: return RootCS{-0.5, 0.8660254037844386, -0.5f, 0.0f, 0.8660253882408142f, 1.5543625053737742e-08f};  // 4/12
+        case 773: return RootCS{-0.8660254037844386, 0.5, -0.8660253882408142f, -1.5543625053737742e-08f, 0.5f, 0.0f};  // 5/12
+        case 775: return RootCS{-0.8660254037844386, -0.5, -0.8660253882408142f, -1.5543625053737742e-08f, -0.5f, 0.0f};  // 7/12
+        case 776: return RootCS{-0.5, -0.8660254037844386, -0.5f, -0.0f, -0.8660253882408142f, -1.5543625053737742e-08f};  // 8/12
+        case 778: return RootCS{0.5, -0.8660254037844386, 0.5f, 0.0f, -0.8660253882408142f, -1.5543625053737742e-08f};  // 10/12
+        case 779: return RootCS{0.8660254037844386, -0.5, 0.8660253882408142f, 1.5543625053737742e-08f, -0.5f, -0.0f};  // 11/12
+        case 961: return RootCS{0.9135454576426009, 0.4067366430758002, 0.9135454297065735f, 2.7936026825159388e-08f, 0.4067366421222687f, 9.535314760000801e-10f};  // 1/15
+        case 962: return RootCS{0.6691306063588582, 0.7431448254773942, 0.6691306233406067f, -1.698174934006147e-08f, 0.7431448101997375f, 1.527765647324486e-08f};  // 2/15
+        case 963: return RootCS{0.30901699437494745, 0.9510565162951535, 0.30901700258255005f, -8.207602597565256e-09f, 0.9510565400123596f, -2.3717205976936384e-08f};  // 3/15
+        case 964: return RootCS{-0.10452846326765347, 0.9945218953682733, -0.10452846437692642f, 1.1092728957606823e-09f, 0.9945219159126282f, -2.054435555010059e-08f};  // 4/15
+        case 965: return RootCS{-0.5, 0.8660254037844386, -0.5f, 0.0f, 0.8660253882408142f, 1.5543625053737742e-08f};  // 5/15
+        case 966: return RootCS{-0.8090169943749475, 0.5877852522924731, -0.80901700258255f, 8.207602597565256e-09f, 0.5877852439880371f, 8.304436249773062e-09f};  // 6/15
+        case 967: return RootCS{-0.9781476007338057, 0.20791169081775934, -0.9781476259231567f, 2.5189351049448305e-08f, 0.2079116851091385f, 5.708620687272514e-09f};  // 7/15
+        case 968: return RootCS{-0.9781476007338057, -0.20791169081775934, -0.9781476259231567f, 2.5189351049448305e-08f, -0.2079116851091385f, -5.708620687272514e-09f};  // 8/15
+        case 969: return RootCS{-0.8090169943749475, -0.5877852522924731, -0.80901700258255f, 8.207602597565256e-09f, -0.5877852439880371f, -8.304436249773062e-09f};  // 9/15
+        case 970: return RootCS{-0.5, -0.8660254037844386, -0.5f, -0.0f, -0.8660253882408142f, -1.5543625053737742e-08f};  // 10/15
+        case 971: return RootCS{-0.10452846326765347, -0.9945218953682733, -0.10452846437692642f, 1.1092728957606823e-09f, -0.9945219159126282f, 2.054435555010059e-08f};  // 11/15
+        case 972: return RootCS{0.30901699437494745, -0.9510565162951535, 0.30901700258255005f, -8.207602597565256e-09f, -0.9510565400123596f, 2.3717205976936384e-08f};  // 12/15
+        case 973: return RootCS{0.6691306063588582, -0.7431448254773942, 0.6691306233406067f, -1.698174934006147e-08f, -0.7431448101997375f, -1.527765647324486e-08f};  // 13/15
+        case 974: return RootCS{0.9135454576426009, -0.4067366430758002, 0.9135454297065735f, 2.7936026825159388e-08f, -0.4067366421222687f, -9.535314760000801e-10f};  // 14/15
+        case 1025: return RootCS{0.9238795325112867, 0.3826834323650898, 0.9238795042037964f, 2.830748968563057e-08f, 0.3826834261417389f, 6.2233507236442165e-09f};  // 1/16
+        case 1026: return RootCS{0.7071067811865476, 0.7071067811865476, 0.7071067690849304f, 1.2101617485882343e-08f, 0.7071067690849304f, 1.2101617485882343e-08f};  // 2/16
+        case 1027: return RootCS{0.3826834323650898, 0.9238795325112867, 0.3826834261417389f, 6.2233507236442165e-09f, 0.9238795042037964f, 2.830748968563057e-08f};  // 3/16
+        case 1029: return RootCS{-0.3826834323650898, 0.9238795325112867, -0.3826834261417389f, -6.2233507236442165e-09f, 0.9238795042037964f, 2.830748968563057e-08f};  // 5/16
+        case 1030: return RootCS{-0.7071067811865476, 0.7071067811865476, -0.7071067690849304f, -1.2101617485882343e-08f, 0.7071067690849304f, 1.2101617485882343e-08f};  // 6/16
+        case 1031: return RootCS{-0.9238795325112867, 0.3826834323650898, -0.9238795042037964f, -2.830748968563057e-08f, 0.3826834261417389f, 6.2233507236442165e-09f};  // 7/16
+        case 1033: return RootCS{-0.9238795325112867, -0.3826834323650898, -0.9238795042037964f, -2.830748968563057e-08f, -0.3826834261417389f, -6.2233507236442165e-09f};  // 9/16
+        case 1034: return RootCS{-0.7071067811865476, -0.7071067811865476, -0.7071067690849304f, -1.2101617485882343e-08f, -0.7071067690849304f, -1.2101617485882343e-08f};  // 10/16
+        case 1035: return RootCS{-0.3826834323650898, -0.9238795325112867, -0.3826834261417389f, -6.2233507236442165e-09f, -0.9238795042037964f, -2.830748968563057e-08f};  // 11/16
+        case 1037: return RootCS{0.3826834323650898, -0.9238795325112867, 0.3826834261417389f, 6.2233507236442165e-09f, -0.9238795042037964f, -2.830748968563057e-08f};  // 13/16
+        case 1038: return RootCS{0.7071067811865476, -0.7071067811865476, 0.7071067690849304f, 1.2101617485882343e-08f, -0.7071067690849304f, -1.2101617485882343e-08f};  // 14/16
+        case 1039: return RootCS{0.9238795325112867, -0.3826834323650898, 0.9238795042037964f, 2.830748968563057e-08f, -0.3826834261417389f, -6.2233507236442165e-09f};  // 15/16
+        default: return RootCS{1.0, 0.0, 1.0f, 0.0f, 0.0f, 0.0f};
+    }
+}
+
+// v * exp(S 2 pi i j / R); j is a constant once the pass loops are unrolled
+template <int R, int S, class T> __device__ __forceinline__ cplx<T> rot(cplx<T> v, int j) {
+    j %= R;
+    if (j == 0) return v;
+    if (4 * j == R) return mul_si<S>(v);
+    if (2 * j == R) return cplx<T>{-v.x, -v.y};
+    if (4 * j == 3 * R) return mul_si<-S>(v);
+    constexpr float sf = (float)S;
+    const RootCS r = root_cs(R, j);
+    if constexpr (std::is_same<T, df64>::value) {
+        return v * cplx<df64>{df64{r.ch, r.cl}, df64{sf * r.sh, sf * r.sl}};
+    } else if constexpr (std::is_same<T, float>::value) {
+        return v * c32{r.ch, sf * r.sh};
+    } else {
+        return v * cplx<T>{(T)r.c, (T)S * (T)r.s};
+    }
+}
+
 // twiddle exp(-2 pi i k / N) for 0 <= k < N
 template <class T> struct TwFull {  // full table in global memory (L2 / L1 resident)
     const cplx<T>* tw;
@@ -123,15 +212,19 @@ struct TwTwo {  // FP32: product of two small shared-memory tables, k = 256 a + 
 // A pass applies one DIF stage (R2 = 1) or two consecutive DIF stages fused in registers:
 // radix R1 on the sub-transforms of size Ns, then radix R2 on those of size Ns / R1.  Each
 // thread transforms the R1*R2 elements b*Ns + n2 + q2*m2 + q1*m1 (m1 = Ns/R1, m2 = m1/R2), so a
-// fused pass reads and writes the work buffer once for two stages.  Twiddles: exp(-2 pi i n p /
-// Ns) = tw(n p s1) with s1 = N/Ns for the first stage and tw(n2 p s2), s2 = s1 R1, for the second.
+// fused pass reads and writes the work buffer once for two stages.  Twiddles: a single stage
+// multiplies output p by exp(-2 pi i n p / Ns) = tw(n p s1), s1 = N/Ns.  For a pair the first
+// stage's twiddle of block q2 splits into tw(n2 p1 s1) omega_{R1 R2}^{q2 p1}; the first factor
+// is common to the second stage's sum and merges with its twiddle tw(n2 p2 s1 R1), so a fused
+// pass applies the constants omega_{R1 R2}^{q2 p1} between the stages and one table twiddle
+// tw(n2 s1 (p1 + R1 p2)) per output: R1 R2 - 1 table twiddles instead of 2 R1 R2 - R1 - R2.
 // The block index b = floor(i / m2) is formed with a float reciprocal: (i + 1/2) / m2 is at least
 // 1/(2 m2) away from an integer, which the float product resolves exactly for i < 2^22.
 // C supplies the buffer accesses (c.dif_load / c.dif_store / c.dit_load / c.dit_store), which
 // fold the input load, the filter product and the output epilogue into the first and last pass.
 template <int R1, int R2, int S, class T, class TW, class C>
 __device__ __forceinline__ void dif_pass(C& c, int Ns, const TW& tw) {
-    const int N = c.N, m1 = Ns / R1, m2 = m1 / R2, s1 = N / Ns, s2 = s1 * R1, ng = N / (R1 * R2);
+    const int N = c.N, m1 = Ns / R1, m2 = m1 / R2, s1 = N / Ns, ng = N / (R1 * R2);
     const float rm = 1.0f / (float)m2;
     // a cluster of two CTAs splits the groups at a block boundary (see BlueIo)
     const int g0 = c.rank * (ng >> 1), g1 = (c.nrank == 1 || c.rank == 1) ? ng : (ng >> 1);
@@ -143,62 +236,78 @@ __device__ __forceinline__ void dif_pass(C& c, int Ns, const TW& tw) {
 #pragma unroll
             for (int q1 = 0; q1 < R1; ++q1) v[q2][q1] = c.dif_load(base + q2 * m2 + q1 * m1);
 #pragma unroll
-        for (int q2 = 0; q2 < R2; ++q2) {
-            bfly<R1, S>(v[q2]);
-            const int n = (n2 + q2 * m2) * s1;
+        for (int q2 = 0; q2 < R2; ++q2) bfly<R1, S>(v[q2]);
+        if constexpr (R2 == 1) {
+            const int n = n2 * s1;
 #pragma unroll
-            for (int p1 = 1; p1 < R1; ++p1) v[q2][p1] = v[q2][p1] * tw(n * p1);
-        }
+            for (int p1 = 1; p1 < R1; ++p1) v[0][p1] = v[0][p1] * tw(n * p1);
 #pragma unroll
-        for (int p1 = 0; p1 < R1; ++p1) {
-            cplx<T> u[R2];
+            for (int p1 = 0; p1 < R1; ++p1) c.dif_store(base + p1 * m1, v[0][p1]);
+        } else {
+            // the two stages form an R1 R2-point DFT: inner twiddles omega_{R1 R2}^{q2 p1} between
+            // them, then one outer twiddle tw(n2 s1 (p1 + R1 p2)) per output
 #pragma unroll
-            for (int q2 = 0; q2 < R2; ++q2) u[q2] = v[q2][p1];
-            if constexpr (R2 > 1) {
+            for (int q2 = 1; q2 < R2; ++q2)
+#pragma unroll
+                for (int p1 = 1; p1 < R1; ++p1) v[q2][p1] = rot<R1 * R2, S>(v[q2][p1], q2 * p1);
+            const int n = n2 * s1;
+#pragma unroll
+            for (int p1 = 0; p1 < R1; ++p1) {
+                cplx<T> u[R2];
+#pragma unroll
+                for (int q2 = 0; q2 < R2; ++q2) u[q2] = v[q2][p1];
                 bfly<R2, S>(u);
 #pragma unroll
-                for (int p2 = 1; p2 < R2; ++p2) u[p2] = u[p2] * tw(n2 * p2 * s2);
+                for (int p2 = 0; p2 < R2; ++p2) {
+                    const int j = p1 + R1 * p2;
+                    c.dif_store(base + p1 * m1 + p2 * m2, j ? u[p2] * tw(n * j) : u[p2]);
+                }
             }
-#pragma unroll
-            for (int p2 = 0; p2 < R2; ++p2) c.dif_store(base + p1 * m1 + p2 * m2, u[p2]);
         }
     }
 }
 
-// exact adjoint of dif_pass: conjugate twiddles and inverse butterflies, second stage first
+// exact adjoint of dif_pass: conjugate twiddles and inverse butterflies in reverse order
 template <int R1, int R2, class T, class TW, class C>
 __device__ __forceinline__ void dit_pass(C& c, int Ns, const TW& tw) {
-    const int N = c.N, m1 = Ns / R1, m2 = m1 / R2, s1 = N / Ns, s2 = s1 * R1, ng = N / (R1 * R2);
+    const int N = c.N, m1 = Ns / R1, m2 = m1 / R2, s1 = N / Ns, ng = N / (R1 * R2);
     const float rm = 1.0f / (float)m2;
-    // a cluster of two CTAs splits the groups at a block boundary (see BlueIo)
     const int g0 = c.rank * (ng >> 1), g1 = (c.nrank == 1 || c.rank == 1) ? ng : (ng >> 1);
     for (int i = g0 + threadIdx.x; i < g1; i += blockDim.x) {
         const int b = (int)(((float)i + 0.5f) * rm), n2 = i - b * m2, base = b * Ns + n2;
+        const int n = n2 * s1;
         cplx<T> v[R2][R1];
+        if constexpr (R2 == 1) {
 #pragma unroll
-        for (int p1 = 0; p1 < R1; ++p1) {
-            cplx<T> u[R2];
+            for (int p1 = 0; p1 < R1; ++p1) {
+                const cplx<T> x = c.dit_load(base + p1 * m1);
+                v[0][p1] = p1 ? mulc(x, tw(n * p1)) : x;
+            }
+        } else {
 #pragma unroll
-            for (int p2 = 0; p2 < R2; ++p2) u[p2] = c.dit_load(base + p1 * m1 + p2 * m2);
-            if constexpr (R2 > 1) {
+            for (int p1 = 0; p1 < R1; ++p1) {
+                cplx<T> u[R2];
 #pragma unroll
-                for (int p2 = 1; p2 < R2; ++p2) u[p2] = mulc(u[p2], tw(n2 * p2 * s2));
+                for (int p2 = 0; p2 < R2; ++p2) {
+                    const int j = p1 + R1 * p2;
+                    const cplx<T> x = c.dit_load(base + p1 * m1 + p2 * m2);
+                    u[p2] = j ? mulc(x, tw(n * j)) : x;
+                }
                 bfly<R2, 1>(u);
+#pragma unroll
+                for (int q2 = 0; q2 < R2; ++q2) v[q2][p1] = u[q2];
             }
 #pragma unroll
-            for (int q2 = 0; q2 < R2; ++q2) v[q2][p1] = u[q2];
+            for (int q2 = 1; q2 < R2; ++q2)
+#pragma unroll
+                for (int p1 = 1; p1 < R1; ++p1) v[q2][p1] = rot<R1 * R2, 1>(v[q2][p1], q2 * p1);
         }
 #pragma unroll
         for (int q2 = 0; q2 < R2; ++q2) {
-            const int n = (n2 + q2 * m2) * s1;
-#pragma unroll
-            for (int p1 = 1; p1 < R1; ++p1) v[q2][p1] = mulc(v[q2][p1], tw(n * p1));
             bfly<R1, 1>(v[q2]);
-        }
-#pragma unroll
-        for (int q2 = 0; q2 < R2; ++q2)
 #pragma unroll
             for (int q1 = 0; q1 < R1; ++q1) c.dit_store(base + q2 * m2 + q1 * m1, v[q2][q1]);
+        }
     }
 }
 
