@@ -208,6 +208,37 @@ struct TwTwo {  // FP32: product of two small shared-memory tables, k = 256 a + 
     __device__ __forceinline__ c32 operator()(int k) const { return a[k >> 8] * b[k & 255]; }
 };
 
+// The table twiddles of one group, tw(n j) for j = p1 + R1 p2.  FP32 (two-level tables in
+// shared memory): one lookup w = tw(n), then products of powers, w^j = w^p1 w^(R1 p2), with the
+// powers formed by repeated squaring (error a few ulps, well inside the FP32 zero test's band);
+// this replaces R1 R2 - 2 table lookups by products.  Other types: full-table lookups.
+template <int R1, int R2, class T, class TW>
+struct TwRow {
+    const TW& tw;
+    int n;
+    __device__ __forceinline__ TwRow(const TW& t, int n_) : tw(t), n(n_) {}
+    __device__ __forceinline__ cplx<T> operator()(int p1, int p2) const { return tw(n * (p1 + R1 * p2)); }
+};
+template <int R1, int R2>
+struct TwRow<R1, R2, float, TwTwo> {
+    c32 a[R1], b[R2];  // a[p1] = w^p1, b[p2] = w^(R1 p2)
+    __device__ __forceinline__ TwRow(const TwTwo& t, int n) {
+        a[0] = c32{1.f, 0.f};
+        a[1] = t(n);
+#pragma unroll
+        for (int p = 2; p < R1; ++p) a[p] = a[p / 2] * a[p - p / 2];
+        b[0] = a[0];
+        if constexpr (R2 > 1) {
+            b[1] = R1 % 2 ? a[R1 / 2] * a[R1 - R1 / 2] : a[R1 / 2] * a[R1 / 2];
+#pragma unroll
+            for (int p = 2; p < R2; ++p) b[p] = b[p / 2] * b[p - p / 2];
+        }
+    }
+    __device__ __forceinline__ c32 operator()(int p1, int p2) const {
+        return p2 == 0 ? a[p1] : p1 == 0 ? b[p2] : a[p1] * b[p2];
+    }
+};
+
 // ------------------------------------------------------------------ radix passes
 // A pass applies one DIF stage (R2 = 1) or two consecutive DIF stages fused in registers:
 // radix R1 on the sub-transforms of size Ns, then radix R2 on those of size Ns / R1.  Each
@@ -237,10 +268,10 @@ __device__ __forceinline__ void dif_pass(C& c, int Ns, const TW& tw) {
             for (int q1 = 0; q1 < R1; ++q1) v[q2][q1] = c.dif_load(base + q2 * m2 + q1 * m1);
 #pragma unroll
         for (int q2 = 0; q2 < R2; ++q2) bfly<R1, S>(v[q2]);
+        const TwRow<R1, R2, T, TW> w(tw, n2 * s1);
         if constexpr (R2 == 1) {
-            const int n = n2 * s1;
 #pragma unroll
-            for (int p1 = 1; p1 < R1; ++p1) v[0][p1] = v[0][p1] * tw(n * p1);
+            for (int p1 = 1; p1 < R1; ++p1) v[0][p1] = v[0][p1] * w(p1, 0);
 #pragma unroll
             for (int p1 = 0; p1 < R1; ++p1) c.dif_store(base + p1 * m1, v[0][p1]);
         } else {
@@ -250,7 +281,6 @@ __device__ __forceinline__ void dif_pass(C& c, int Ns, const TW& tw) {
             for (int q2 = 1; q2 < R2; ++q2)
 #pragma unroll
                 for (int p1 = 1; p1 < R1; ++p1) v[q2][p1] = rot<R1 * R2, S>(v[q2][p1], q2 * p1);
-            const int n = n2 * s1;
 #pragma unroll
             for (int p1 = 0; p1 < R1; ++p1) {
                 cplx<T> u[R2];
@@ -258,10 +288,8 @@ __device__ __forceinline__ void dif_pass(C& c, int Ns, const TW& tw) {
                 for (int q2 = 0; q2 < R2; ++q2) u[q2] = v[q2][p1];
                 bfly<R2, S>(u);
 #pragma unroll
-                for (int p2 = 0; p2 < R2; ++p2) {
-                    const int j = p1 + R1 * p2;
-                    c.dif_store(base + p1 * m1 + p2 * m2, j ? u[p2] * tw(n * j) : u[p2]);
-                }
+                for (int p2 = 0; p2 < R2; ++p2)
+                    c.dif_store(base + p1 * m1 + p2 * m2, (p1 | p2) ? u[p2] * w(p1, p2) : u[p2]);
             }
         }
     }
@@ -275,13 +303,13 @@ __device__ __forceinline__ void dit_pass(C& c, int Ns, const TW& tw) {
     const int g0 = c.rank * (ng >> 1), g1 = (c.nrank == 1 || c.rank == 1) ? ng : (ng >> 1);
     for (int i = g0 + threadIdx.x; i < g1; i += blockDim.x) {
         const int b = (int)(((float)i + 0.5f) * rm), n2 = i - b * m2, base = b * Ns + n2;
-        const int n = n2 * s1;
+        const TwRow<R1, R2, T, TW> w(tw, n2 * s1);
         cplx<T> v[R2][R1];
         if constexpr (R2 == 1) {
 #pragma unroll
             for (int p1 = 0; p1 < R1; ++p1) {
                 const cplx<T> x = c.dit_load(base + p1 * m1);
-                v[0][p1] = p1 ? mulc(x, tw(n * p1)) : x;
+                v[0][p1] = p1 ? mulc(x, w(p1, 0)) : x;
             }
         } else {
 #pragma unroll
@@ -289,9 +317,8 @@ __device__ __forceinline__ void dit_pass(C& c, int Ns, const TW& tw) {
                 cplx<T> u[R2];
 #pragma unroll
                 for (int p2 = 0; p2 < R2; ++p2) {
-                    const int j = p1 + R1 * p2;
                     const cplx<T> x = c.dit_load(base + p1 * m1 + p2 * m2);
-                    u[p2] = j ? mulc(x, tw(n * j)) : x;
+                    u[p2] = (p1 | p2) ? mulc(x, w(p1, p2)) : x;
                 }
                 bfly<R2, 1>(u);
 #pragma unroll
