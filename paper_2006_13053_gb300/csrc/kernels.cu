@@ -277,13 +277,12 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __r
             const uint32_t M = sM[l], mu = smu[l], off = soffk[l], bo = sbo[l];
 #pragma unroll
             for (int c = 0; c < kCPT; ++c) {
-                int x = 0;
+                uint32_t xp = off;  // unsigned: the offset sum wraps modulo 2^32 by definition
 #pragma unroll
-                for (int t = 0; t < D; ++t) x += k[c][t] * zl[t];
-                uint32_t xp = (uint32_t)x + off;
-                uint32_t q = __umulhi(xp, mu);
+                for (int t = 0; t < D; ++t) xp += (uint32_t)(k[c][t] * zl[t]);
+                const uint32_t q = __umulhi(xp, mu);
                 uint32_t r = xp - q * M;
-                r = r >= M ? r - M : r;
+                r = min(r, r - M);
                 uint32_t bit = bo + r;
                 cnt[c] += (bits[bit >> 5] >> (bit & 31)) & 1u;
                 if (dhashes && idx[c] < n) dhashes[idx[c] * L + l0 + l] = (int32_t)r;
@@ -400,16 +399,17 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
             const uint32_t M = cst.x, mu = cst.y, off = cst.z, bo = cst.w;
 #pragma unroll
             for (int c = 0; c < kCPT2; ++c) {
-                int x = 0;
+                // the offset seeds the dot product (32-bit wrap-around equals the unsigned sum)
+                int x = (int)off;
 #pragma unroll
                 for (int w = 0; w < PK::ZW; ++w) {
                     if (w & 1) x = __dp2a_hi((int)zw[w], (int)kw[c][w >> 1], x);
                     else x = __dp2a_lo((int)zw[w], (int)kw[c][w >> 1], x);
                 }
-                uint32_t xp = (uint32_t)x + off;
-                uint32_t q = __umulhi(xp, mu);
+                const uint32_t xp = (uint32_t)x;
+                const uint32_t q = __umulhi(xp, mu);
                 uint32_t rr = xp - q * M;
-                rr = rr >= M ? rr - M : rr;
+                rr = min(rr, rr - M);  // one conditional subtraction: rr - M wraps above rr when rr < M
                 uint32_t bit = bo + rr;
                 cnt[c] += __funnelshift_r(bits[bit >> 5], 0u, bit) & 1u;
                 if constexpr (DIAG) {
