@@ -34,7 +34,8 @@ struct Batch {
     int64_t max_samp_terms_L = 0;
     int64_t* d_counts = nullptr;
     int64_t* d_flags = nullptr;
-    cudaEvent_t done = nullptr;
+    cudaEvent_t done = nullptr;    // end of the last enqueued call (results and flags ready)
+    cudaEvent_t io_ev = nullptr;   // the last call's descriptor upload has executed (staging reusable)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int calls = 0;
@@ -68,6 +69,8 @@ struct Batch {
         if (exec) cudaGraphExecDestroy(exec);
         if (graph) cudaGraphDestroy(graph);
         if (done) cudaEventDestroy(done);
+        if (io_ev) cudaEventDestroy(io_ev);
+        io_ev = nullptr;
         for (void* p : allocs) cudaFree(p);
         if (h_inst) cudaFreeHost(h_inst);
         allocs.clear();
@@ -78,9 +81,10 @@ struct Batch {
         allocs.push_back(*p);
         return SFFT_OK;
     }
-    int enqueue() {
+    int enqueue(bool record_io) {
         const int n = (int)plans.size();
         SFFT_CU(cudaMemcpyAsync(d_inst, h_inst, sizeof(InstDesc) * n, cudaMemcpyHostToDevice, st));
+        if (record_io) SFFT_CU(cudaEventRecord(io_ev, st));  // not inside a graph capture
         SFFT_TRY(run_pipeline(args, st));
         k_gather_counts<<<(n + 127) / 128, 128, 0, st>>>(d_inst, n, d_counts, d_flags);
         return launch_check("k_gather_counts");
@@ -193,6 +197,7 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
     SFFT_TRY(B->alloc((void**)&B->d_counts, sizeof(int64_t) * n));
     SFFT_TRY(B->alloc((void**)&B->d_flags, sizeof(int64_t) * n));
     SFFT_CU(cudaEventCreateWithFlags(&B->done, cudaEventDisableTiming));
+    SFFT_CU(cudaEventCreateWithFlags(&B->io_ev, cudaEventDisableTiming));
     for (int i = 0; i <= ST_COUNT; ++i) SFFT_CU(cudaEventCreate(&B->timer.ev[i]));
     B->timer_made = true;
     return SFFT_OK;
@@ -230,8 +235,9 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
     if (!b || !samples || !supp_out || !coef_out || !cap) { set_error("null argument"); return SFFT_EINVAL; }
     Batch* B = reinterpret_cast<Batch*>(b);
     const int n = (int)B->plans.size();
-    // the previous call's copy of the staging descriptors must have completed
-    SFFT_CU(cudaEventSynchronize(B->done));
+    // the previous call's upload of the staging descriptors must have executed (the host may run
+    // ahead of the GPU by one call)
+    SFFT_CU(cudaEventSynchronize(B->io_ev));
     for (int i = 0; i < n; ++i) {
         const int u = B->order[i];  // caller's index of batch entry i
         SFFT_CHECK(samples[u] && (cap[u] == 0 || (supp_out[u] && coef_out[u])), SFFT_EINVAL, "null buffer for plan %d", u);
@@ -249,12 +255,12 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
     B->args.timer = B->timing ? &B->timer : nullptr;
     if (B->timing && B->exec == nullptr && B->use_graph && B->calls >= 1) {
         // the graph is captured without timers; timed runs of a graph batch use the eager path
-        SFFT_TRY(B->enqueue());
+        SFFT_TRY(B->enqueue(true));
         B->pending = true;
     } else if (B->use_graph && B->calls >= 1 && !B->timing) {
         if (!B->exec) {
             SFFT_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            int rc = B->enqueue();
+            int rc = B->enqueue(false);
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamEndCapture(st, &g);
             if (rc != SFFT_OK) return rc;
@@ -263,8 +269,9 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
             SFFT_CU(cudaGraphInstantiate(&B->exec, g, 0));
         }
         SFFT_CU(cudaGraphLaunch(B->exec, st));
+        SFFT_CU(cudaEventRecord(B->io_ev, st));  // the graph reads the staging buffer when it runs
     } else {
-        SFFT_TRY(B->enqueue());
+        SFFT_TRY(B->enqueue(true));
         B->pending = B->timing;
     }
     if (n_out_dev) {
@@ -282,7 +289,7 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
     if (!b || !kvec || !coef || !n_terms || !samples_out) { set_error("null argument"); return SFFT_EINVAL; }
     Batch* B = reinterpret_cast<Batch*>(b);
     const int n = (int)B->plans.size();
-    SFFT_CU(cudaEventSynchronize(B->done));
+    SFFT_CU(cudaEventSynchronize(B->io_ev));  // staging buffer free (see sfft_batch_reconstruct)
     int64_t mx = 0;
     for (int i = 0; i < n; ++i) {
         const int u = B->order[i];
@@ -298,6 +305,7 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
     }
     cudaStream_t st = B->st;
     SFFT_CU(cudaMemcpyAsync(B->d_inst, B->h_inst, sizeof(InstDesc) * n, cudaMemcpyHostToDevice, st));
+    SFFT_CU(cudaEventRecord(B->io_ev, st));
     SFFT_TRY(launch_clear(B->d_inst, n, 0, 0, B->prec ? 2 : 1, st));
     if (mx > 0) SFFT_TRY(launch_scatter_terms(B->d_inst, n, mx, st));
     for (const auto& f : B->samp)
