@@ -78,7 +78,13 @@ typedef struct sfft_params {
     int combine;      /* SFFT_COMBINE_*                                                       */
     uint64_t seed;    /* key of the Philox4x64-10 draws of generating vectors                  */
     int64_t detect_cap; /* capacity for |Itilde|; 0 = max(4 s + 4096, 16384)                  */
+    int cand_type;    /* element type of the candidate rows: SFFT_CAND_I32 (default) or _I8     */
+    int cand_ld;      /* row stride in elements: 0 = d (I32); I8 rows: a multiple of 4, >= d   */
 } sfft_params;
+
+#define SFFT_CAND_I32 0 /* int32 rows of d entries                                              */
+#define SFFT_CAND_I8 1  /* int8 rows (|k_t| <= 127), stride cand_ld bytes (multiple of 4), so a  */
+                        /* row is read as whole 32-bit words; bytes past d are ignored          */
 
 /* Fill *p with the defaults listed above.  Never fails. */
 void sfft_params_default(sfft_params* p);
@@ -87,8 +93,10 @@ void sfft_params_default(sfft_params* p);
 typedef struct sfft_plan sfft_plan;
 
 /*
- * Create a plan for candidates Gamma = cand (device int32, row-major [n_cand, d], not copied:
- * it must stay valid and unchanged until the plan is destroyed) and sparsity s.
+ * Create a plan for candidates Gamma = cand (device, row-major [n_cand] rows of d entries of the
+ * type p->cand_type: int32, or int8 rows of stride p->cand_ld bytes with the pointer 4-byte
+ * aligned; not copied: it must stay valid and unchanged until the plan is destroyed) and
+ * sparsity s.
  *   L     > 0: number of lattices (must be odd for the median, Algorithm 2), or 0: take L
  *              from p->L_rule with |Gamma| = n_cand (Corollary 2.6 / eq. 4.2 / fallback).
  *   M     host int64 [L] lattice sizes (each prime), or NULL: M_l = the smallest prime
@@ -99,7 +107,7 @@ typedef struct sfft_plan sfft_plan;
  * Needs 1 <= d <= 32, n_cand >= 1, s >= 1, |k_t| small enough that d*max|k|*(M-1) < 2^31
  * (else SFFT_EOVERFLOW).  Precomputes chirps and Bluestein filters on `stream`.
  */
-int sfft_plan_create(sfft_plan** out, int d, const int32_t* cand, int64_t n_cand, int64_t s, int L,
+int sfft_plan_create(sfft_plan** out, int d, const void* cand, int64_t n_cand, int64_t s, int L,
                      const int64_t* M, const int64_t* z, const sfft_params* p, void* stream);
 
 /* L, the lattice sizes M (host int64 [L], optional), z (host int64 [L*d], optional) and the

@@ -34,11 +34,15 @@ class SfftError(RuntimeError):
         self.code = code
 
 
+CAND_I32, CAND_I8 = 0, 1
+
+
 class Params(C.Structure):
     _fields_ = [("c", C.c_double), ("delta", C.c_double), ("nu", C.c_double), ("tau_abs", C.c_double),
                 ("tau_rel", C.c_double), ("theta_abs", C.c_double), ("theta_rel", C.c_double),
                 ("s_tilde", C.c_int64), ("precision", C.c_int), ("refine", C.c_int), ("L_rule", C.c_int),
-                ("combine", C.c_int), ("seed", C.c_uint64), ("detect_cap", C.c_int64)]
+                ("combine", C.c_int), ("seed", C.c_uint64), ("detect_cap", C.c_int64), ("cand_type", C.c_int),
+                ("cand_ld", C.c_int)]
 
 
 class Diag(C.Structure):

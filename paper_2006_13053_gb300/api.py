@@ -33,12 +33,24 @@ def _req(t, dtype, name):
 class Plan:
     """A reconstruction plan (Algorithm 2/4) over the candidate set `cand` (kept referenced)."""
 
-    def __init__(self, cand: torch.Tensor, s: int, L: int = 0, M=None, z=None, stream=None, **params):
-        _req(cand, torch.int32, "cand")
-        if cand.dim() != 2:
-            raise ValueError("cand must be [n, d]")
+    def __init__(self, cand: torch.Tensor, s: int, L: int = 0, M=None, z=None, stream=None, d=None, **params):
+        """cand: int32 [n, d], or int8 [n, ld] rows (|k_t| <= 127, ld a multiple of 4 >= d, the
+        first d bytes of a row are the frequency; pass d)."""
+        if not (isinstance(cand, torch.Tensor) and cand.dim() == 2):
+            raise ValueError("cand must be a 2-D tensor [n, d] (int32) or [n, ld] (int8)")
+        if cand.dtype == torch.int8:
+            _req(cand, torch.int8, "cand")
+            if d is None:
+                raise ValueError("int8 candidate rows need d")
+            params.setdefault("cand_type", N.CAND_I8)
+            params.setdefault("cand_ld", int(cand.shape[1]))
+            self.n, self.d = int(cand.shape[0]), int(d)
+        else:
+            _req(cand, torch.int32, "cand")
+            self.n, self.d = cand.shape
+            if d is not None and d != self.d:
+                raise ValueError("d does not match the int32 rows")
         self.cand = cand
-        self.n, self.d = cand.shape
         self.params = N.default_params(**params)
         self.stream = stream
         Mp = zp = None

@@ -227,7 +227,7 @@ int upload_jobs(const std::vector<BlueJob>& v, BlueJob** dst, std::vector<void*>
     return SFFT_OK;
 }
 
-int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int Lin, const int64_t* Min,
+int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin, const int64_t* Min,
                 const int64_t* zin, const sfft_params* pin, cudaStream_t st) {
     sfft_params p;
     if (pin) p = *pin; else sfft_params_default(&p);
@@ -240,6 +240,15 @@ int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L
     SFFT_CHECK(p.delta > 0 && p.delta < 1, SFFT_EINVAL, "delta must be in (0, 1)");
     SFFT_CHECK(p.precision == SFFT_FP64 || p.precision == SFFT_FP32, SFFT_EINVAL, "bad precision");
     SFFT_CHECK(p.refine == 0 || p.refine == 1, SFFT_EINVAL, "refine must be 0 or 1");
+    SFFT_CHECK(p.cand_type == SFFT_CAND_I32 || p.cand_type == SFFT_CAND_I8, SFFT_EINVAL, "bad cand_type");
+    if (p.cand_type == SFFT_CAND_I32) {
+        SFFT_CHECK(p.cand_ld == 0 || p.cand_ld == d, SFFT_EINVAL, "int32 candidate rows are dense (cand_ld 0 or d)");
+        p.cand_ld = d;
+    } else {
+        SFFT_CHECK(p.cand_ld >= d && p.cand_ld % 4 == 0, SFFT_EINVAL,
+                   "int8 candidate rows need a stride cand_ld >= d that is a multiple of 4 (got %d)", p.cand_ld);
+        SFFT_CHECK(((uintptr_t)cand & 3) == 0, SFFT_EINVAL, "int8 candidate rows must start 4-byte aligned");
+    }
     P->d = d; P->cand = cand; P->n = n; P->s = s; P->p = p; P->prec = p.precision; P->st = st;
     // ---- L and M (Corollary 2.6 / eq. 4.2 / fallback)
     int L = Lin > 0 ? Lin : L_rule(p.L_rule, n, p.delta, p.c);
@@ -268,7 +277,7 @@ int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L
         std::vector<int> mn(d, INT32_MAX), mx(d, INT32_MIN);
         SFFT_CU(cudaMemcpyAsync(dmn, mn.data(), sizeof(int) * d, cudaMemcpyHostToDevice, st));
         SFFT_CU(cudaMemcpyAsync(dmx, mx.data(), sizeof(int) * d, cudaMemcpyHostToDevice, st));
-        SFFT_TRY(launch_cand_stats(cand, n, d, dmn, dmx, st));
+        SFFT_TRY(launch_cand_stats(cand, p.cand_type == SFFT_CAND_I8, p.cand_ld, n, d, dmn, dmx, st));
         SFFT_CU(cudaMemcpyAsync(mn.data(), dmn, sizeof(int) * d, cudaMemcpyDeviceToHost, st));
         SFFT_CU(cudaMemcpyAsync(mx.data(), dmx, sizeof(int) * d, cudaMemcpyDeviceToHost, st));
         SFFT_CU(cudaStreamSynchronize(st));
@@ -368,7 +377,7 @@ int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L
     I.need = (int)ceil(p.nu * L - 1e-9);
     I.n = n; I.cap = cap; I.s_tilde = p.s_tilde;
     I.tau_abs = p.tau_abs; I.tau_rel = p.tau_rel; I.theta_abs = p.theta_abs; I.theta_rel = p.theta_rel;
-    I.cand = cand; I.z = dz; I.Ml = dM; I.mu = dmu; I.offk = doffk; I.soff = dsoff; I.boff = dboff;
+    I.cand = cand; I.cand_i8 = p.cand_type == SFFT_CAND_I8; I.cand_ld = p.cand_ld; I.z = dz; I.Ml = dM; I.mu = dmu; I.offk = doffk; I.soff = dsoff; I.boff = dboff;
     I.nzbits = P->nzbits; I.ghat = P->ghat; I.stats = P->stats; I.detbits = P->detbits; I.det = P->det;
     I.cnt = P->cnt; I.coef = P->coef; I.H = P->H; I.sel = P->sel; I.coll = P->coll; I.C = P->C;
     I.ghat_lo = P->ghat_lo; I.outpos = P->outpos;
@@ -531,7 +540,7 @@ int sfft_L_rule(int rule, int64_t n_cand, double delta, double c) {
     return L_rule(rule, n_cand, delta, c);
 }
 
-int sfft_plan_create(sfft_plan** out, int d, const int32_t* cand, int64_t n_cand, int64_t s, int L, const int64_t* M,
+int sfft_plan_create(sfft_plan** out, int d, const void* cand, int64_t n_cand, int64_t s, int L, const int64_t* M,
                      const int64_t* z, const sfft_params* p, void* stream) {
     if (!out) { set_error("out is NULL"); return SFFT_EINVAL; }
     *out = nullptr;

@@ -233,12 +233,13 @@ int plan_passes(const int* radix, int ns, int maxprod, uint8_t* pass_r);
 // device memory; the per-call IO pointers are refreshed before each run.
 struct InstDesc {
     int d, L, need, prec;      // need = ceil(nu L) (Algorithm 1 count threshold)
-    int combine, nwords, lat0, pad0;
+    int combine, nwords;
+    int cand_i8, cand_ld;      // candidate rows: int8 (1) or int32 (0); row stride in elements
     int64_t n;                 // |Gamma|
     int64_t cap;               // capacity of the detected list
     int64_t s_tilde;
     double tau_abs, tau_rel, theta_abs, theta_rel;
-    const int32_t* cand;       // [n, d]
+    const void* cand;          // [n, cand_ld] int32 or int8
     const int32_t* z;          // [L, d]
     const int32_t* Ml;         // [L]
     const uint32_t* mu;        // [L] floor(2^32 / M_l)

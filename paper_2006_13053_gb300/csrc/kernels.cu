@@ -239,7 +239,9 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __r
     __syncthreads();
     const int64_t n = I.n;
     const int need = I.need;
-    const int32_t* __restrict__ cand = I.cand;
+    const int32_t* __restrict__ cand = reinterpret_cast<const int32_t*>(I.cand);
+    const int8_t* __restrict__ cand8 = reinterpret_cast<const int8_t*>(I.cand);
+    const int ld = I.cand_ld;
     uint8_t* dcounts = I.dcounts;
     int32_t* dhashes = I.dhashes;
     const int64_t step = (int64_t)gridDim.x * blockDim.x * kCPT;
@@ -249,8 +251,12 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __r
 #pragma unroll
         for (int c = 0; c < kCPT; ++c) {
             idx[c] = base + threadIdx.x + (int64_t)c * blockDim.x;
-            const int32_t* row = cand + (idx[c] < n ? idx[c] : 0) * D;
-            if constexpr (D % 4 == 0) {
+            const int64_t r = idx[c] < n ? idx[c] : 0;
+            const int32_t* row = cand + r * D;
+            if (I.cand_i8) {  // int8 rows of stride ld bytes
+#pragma unroll
+                for (int t = 0; t < D; ++t) k[c][t] = (int)__ldg(cand8 + r * ld + t);
+            } else if constexpr (D % 4 == 0) {
 #pragma unroll
                 for (int t = 0; t < D; t += 4) {
                     int4 v = __ldg(reinterpret_cast<const int4*>(row + t));
@@ -351,7 +357,10 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
     __syncthreads();
     const int64_t n = I.n;
     const int need = I.need;
-    const int32_t* __restrict__ cand = I.cand;
+    const int32_t* __restrict__ cand = reinterpret_cast<const int32_t*>(I.cand);
+    const uint32_t* __restrict__ cand8w = reinterpret_cast<const uint32_t*>(I.cand);  // int8 rows as words
+    const int ldw = I.cand_ld >> 2;
+    const bool i8 = I.cand_i8 != 0;
     const int64_t step = (int64_t)gridDim.x * blockDim.x * kCPT2;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kCPT2; base < n; base += step) {
         uint32_t kw[kCPT2][PK::KW];
@@ -359,7 +368,13 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
 #pragma unroll
         for (int c = 0; c < kCPT2; ++c) {
             idx[c] = base + threadIdx.x + (int64_t)c * blockDim.x;
-            const int32_t* row = cand + (idx[c] < n ? idx[c] : 0) * D;
+            const int64_t r = idx[c] < n ? idx[c] : 0;
+            if (i8) {  // the int8 row already holds the packed words (bytes past d meet zero z entries)
+#pragma unroll
+                for (int w = 0; w < PK::KW; ++w) kw[c][w] = __ldg(cand8w + r * ldw + w);
+                continue;
+            }
+            const int32_t* row = cand + r * D;
             int k[PK::KW * 4];
 #pragma unroll
             for (int t = 0; t < PK::KW * 4; ++t) k[t] = 0;
@@ -522,11 +537,13 @@ __global__ void k_det_hashes(const InstDesc* __restrict__ insts) {
     const int warps = blockDim.x >> 5;
     for (int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); q < nd; q += (int64_t)gridDim.x * warps) {
         const int lane = threadIdx.x & 31, L = I.L, d = I.d;
-        const int32_t* k = I.cand + I.det[q] * d;
+        const int64_t row = I.det[q] * I.cand_ld;
+        const int32_t* k32 = reinterpret_cast<const int32_t*>(I.cand) + row;
+        const int8_t* k8 = reinterpret_cast<const int8_t*>(I.cand) + row;
         for (int l = lane; l < L; l += 32) {
             const int32_t* zl = I.z + l * d;
             int64_t x = 0;
-            for (int t = 0; t < d; ++t) x += (int64_t)__ldg(k + t) * zl[t];
+            for (int t = 0; t < d; ++t) x += (int64_t)(I.cand_i8 ? (int)__ldg(k8 + t) : __ldg(k32 + t)) * zl[t];
             int64_t M = I.Ml[l];
             int64_t r = x % M;
             if (r < 0) r += M;
@@ -921,13 +938,15 @@ __global__ void k_points(const InstDesc* __restrict__ insts, int32_t* numer, dou
 }
 
 // per-dimension min / max of the candidates (plan validation: N_Gamma, |k| bound)
-__global__ void k_cand_stats(const int32_t* __restrict__ cand, int64_t n, int d, int* mn, int* mx) {
+__global__ void k_cand_stats(const void* __restrict__ cand, int i8, int ld, int64_t n, int d, int* mn, int* mx) {
     __shared__ int smn[kMaxD], smx[kMaxD];
     if (threadIdx.x < d) { smn[threadIdx.x] = INT_MAX; smx[threadIdx.x] = INT_MIN; }
     __syncthreads();
     for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n * d; e += (int64_t)gridDim.x * blockDim.x) {
-        int t = (int)(e % d);
-        int v = cand[e];
+        const int64_t r = e / d;
+        const int t = (int)(e - r * d);
+        const int v = i8 ? (int)reinterpret_cast<const int8_t*>(cand)[r * ld + t]
+                         : reinterpret_cast<const int32_t*>(cand)[r * ld + t];
         atomicMin(&smn[t], v);
         atomicMax(&smx[t], v);
     }
@@ -961,9 +980,9 @@ __global__ void k_clear_inst(InstDesc* __restrict__ insts, int clear_det, int cl
 }
 
 // ================================================================== launch wrappers
-int launch_cand_stats(const int32_t* cand, int64_t n, int d, int* mn, int* mx, cudaStream_t st) {
+int launch_cand_stats(const void* cand, int i8, int ld, int64_t n, int d, int* mn, int* mx, cudaStream_t st) {
     int gx = (int)std::min<int64_t>(4 * 152, (n * d + 255) / 256 + 1);
-    k_cand_stats<<<gx, 256, 0, st>>>(cand, n, d, mn, mx);
+    k_cand_stats<<<gx, 256, 0, st>>>(cand, i8, ld, n, d, mn, mx);
     return launch_check("k_cand_stats");
 }
 

@@ -115,7 +115,7 @@ extern "C" int sfft_detect_noalloc(int d, const int32_t* cand, int64_t n_cand, i
     for (int t = 0; t < kMaxD; ++t) { mnx[t] = INT32_MAX; mnx[kMaxD + t] = INT32_MIN; }
     int* dmn = reinterpret_cast<int*>(S + o_mnx);
     SFFT_CU(cudaMemcpyAsync(dmn, mnx, sizeof mnx, cudaMemcpyHostToDevice, st));
-    SFFT_TRY(launch_cand_stats(cand, n_cand, d, dmn, dmn + kMaxD, st));
+    SFFT_TRY(launch_cand_stats(cand, 0, d, n_cand, d, dmn, dmn + kMaxD, st));
     SFFT_CU(cudaMemcpyAsync(mnx, dmn, sizeof mnx, cudaMemcpyDeviceToHost, st));
     SFFT_CU(cudaStreamSynchronize(st));
     int64_t kmax = 0;
@@ -151,6 +151,7 @@ extern "C" int sfft_detect_noalloc(int d, const int32_t* cand, int64_t n_cand, i
     I.d = d; I.L = L; I.need = (int)ceil(nu * L - 1e-9); I.nwords = (int)words;
     I.n = n_cand; I.cap = cap;
     I.cand = cand;
+    I.cand_ld = d;  // dense int32 rows
     I.z = reinterpret_cast<int32_t*>(S + o_z);
     I.Ml = reinterpret_cast<int32_t*>(S + o_M);
     I.mu = reinterpret_cast<uint32_t*>(S + o_mu);

@@ -48,7 +48,7 @@ struct Plan {
     int d = 0, L = 0, prec = 0, nwords = 0, maxN = 0;
     int64_t n = 0, s = 0, sumM = 0, cap = 0, N_gamma = 0, kmax = 0, last_nout = 0;
     sfft_params p;
-    const int32_t* cand = nullptr;
+    const void* cand = nullptr;  // int32 or int8 rows (p.cand_type, p.cand_ld)
     cudaStream_t st = nullptr;
     std::vector<int64_t> M, z, soff;
     std::vector<int32_t> boff;
@@ -101,7 +101,7 @@ struct Plan {
     PipeArgs pipe_args();
 };
 
-int plan_create(Plan* P, int d, const int32_t* cand, int64_t n, int64_t s, int L, const int64_t* M, const int64_t* z,
+int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int L, const int64_t* M, const int64_t* z,
                 const sfft_params* p, cudaStream_t st);
 int run_pipeline(const PipeArgs& a, cudaStream_t st);
 // Bluestein job for the tables of one M; prec: 0 double, 1 float, 2 double-float; dir 0 forward
