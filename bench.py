@@ -49,6 +49,17 @@ def parse():
 
 
 # ------------------------------------------------------------------ inputs (seeded, synthetic)
+ROW8 = 12  # int8 candidate row stride in bytes: d = 10 entries padded to a multiple of 4
+
+
+def rows8(cand):
+    """Compact candidate rows: int8 (|k_t| <= 64 here), stride ROW8 bytes, zero padding."""
+    import numpy as np
+    r = np.zeros((cand.shape[0], ROW8), dtype=np.int8)
+    r[:, :cand.shape[1]] = cand
+    return r
+
+
 def instance_inputs(seed):
     import numpy as np
     import sfft_synth as S
@@ -211,19 +222,23 @@ def run_native(a, rank, world):
     n_inst = a.instances
     seeds = rank_seeds(rank, n_inst)
     host = [instance_inputs(s) for s in seeds]
-    plans, kv, cf, nz, smp, cand_d = [], [], [], [], [], []
+    import sfft_synth as S
+    h8 = [rows8(h[0]) for h in host]                       # compact int8 candidate rows
+    hkv = [h[0][h[1]] for h in host]                        # support frequencies (int32)
+
+    def make_plans(rows, prec=G.FP32, refine=1, d=D):
+        return [G.Plan(r, S_SPARSE, d=d if r.dtype == torch.int8 else None, precision=prec, refine=refine,
+                       tau_abs=6 * h[3] / math.sqrt(10331), tau_rel=0.0, seed=s_, stream=st)
+                for r, h, s_ in zip(rows, host, seeds)]
+
     with torch.cuda.stream(st):
-        for s, (cand, sup, coef, sigma) in zip(seeds, host):
-            c = torch.from_numpy(cand).to(dev)
-            cand_d.append(c)
-            p = G.Plan(c, S_SPARSE, precision=G.FP32, refine=1, tau_abs=6 * sigma / math.sqrt(10331), tau_rel=0.0,
-                       seed=s, stream=st)
-            plans.append(p)
-            kv.append(c[torch.from_numpy(sup).to(dev)].contiguous())
-            cf.append(torch.from_numpy(coef).to(dev))
-            import sfft_synth as S
-            nz.append(torch.from_numpy(S.noise(p.n_samples, sigma, s)).to(dev))
-            smp.append(torch.empty(p.n_samples, dtype=torch.complex64, device=dev))
+        cand8 = [torch.from_numpy(r).to(dev) for r in h8]
+        plans = make_plans(cand8)
+        hnz = [S.noise(p.n_samples, h[3], s_) for p, h, s_ in zip(plans, host, seeds)]
+        kv = [torch.from_numpy(k).to(dev) for k in hkv]
+        cf = [torch.from_numpy(h[2]).to(dev) for h in host]
+        nz = [torch.from_numpy(z_).to(dev) for z_ in hnz]
+        smp = [torch.empty(p.n_samples, dtype=torch.complex64, device=dev) for p in plans]
         batch = G.Batch(plans, use_graph=False, stream=st)
     L, M = plans[0].L, int(plans[0].M[0])
 
@@ -286,7 +301,8 @@ def run_native(a, rank, world):
            "config": {"workload": WORKLOAD, "global_batch": world * n_inst, "lattices": L, "lattice_size": M,
                       "precision": "FP32 samples; lattice DFTs in double-float (float pairs on the FP32 pipes); "
                                    "FP32 zero test + median; FP64 refinement (ghat - C) and update; exact int32 hashing",
-                      "l2": "inputs larger than L2 (16 x 40 MiB candidate sets per step)",
+                      "candidates": f"int8 rows, {ROW8}-byte stride (the library's compact layout)",
+                      "l2": f"inputs larger than L2 (16 x {NCAND * ROW8 / 2**20:.0f} MiB candidate rows per step)",
                       "parallelism": f"replicas x{world}",
                       "autotuned": {"hash_waves": tuned[0], "fft_threads": tuned[1]}},
            "cand_lattice_evals_per_s": world * n_inst * NCAND * L / (ms / 1000.0),
@@ -304,11 +320,11 @@ def run_native(a, rank, world):
     src = "of measured" if "hbm_gbs" in peaks else "of fallback"
     per_launch_ms = stage_ms[dom]
     if dom == "hash_count":
-        bytes_ = n_inst * NCAND * D * 4  # candidate stream: 4 d bytes per candidate, read once
+        bytes_ = n_inst * NCAND * ROW8  # candidate stream: one int8 row per candidate, read once
         ach = bytes_ / (per_launch_ms / 1000.0) / 1e9
-        out["roofline"] = {"kernel": "k_hash_count", "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                           "frac": ach / hbm, "peak_source": src,
-                           "traffic": traffic_from_profiles("k_hash_count", n_inst * NCAND)}
+        out["roofline"] = {"kernel": "k_hash_count_packed", "bound": "hbm", "achieved": ach, "peak": hbm,
+                           "unit": "GB/s", "frac": ach / hbm, "peak_source": src,
+                           "traffic": traffic_from_profiles("k_hash_count_i8", n_inst * NCAND)}
     elif dom == "fft_fwd":
         # double-float forward lattice DFTs (FP32 + refinement): FP32-pipe instruction bound
         N = 20736
@@ -346,43 +362,98 @@ def run_native(a, rank, world):
     g1.synchronize()
     out["graph_ms_per_step"] = g0.elapsed_time(g1) / a.steps
     gbatch.close()
-    # ---- end to end: host (pinned) inputs -> device -> results back to the host, every step
-    hc = [torch.from_numpy(h[0]).pin_memory() for h in host]
-    hk = [kv[i].cpu().pin_memory() for i in range(n_inst)]
-    hf = [cf[i].cpu().pin_memory() for i in range(n_inst)]
-    hn = [nz[i].cpu().pin_memory() for i in range(n_inst)]
-    out_s = [torch.empty(c_.numel(), dtype=torch.int64).pin_memory() for c_ in batch.supp]
-    out_c = [torch.empty(c_.numel(), dtype=torch.complex128).pin_memory() for c_ in batch.coef]
-    out_n = torch.empty(n_inst, dtype=torch.int64).pin_memory()
-    h2d = sum(t.numel() * t.element_size() for t in hc + hk + hf + hn)
-
-    def e2e_step():
+    # ---- end to end through the public API: every step copies its inputs (int8 candidate rows,
+    # support frequencies, coefficients, noise) from pinned host memory and reads the results
+    # back.  Two buffer sets, each with its own plans and batch, alternate so that the copies of
+    # step t+1 run on a copy stream while the kernels of step t run.
+    cs = torch.cuda.Stream(dev)  # host-to-device copies
+    rs = torch.cuda.Stream(dev)  # device-to-host results (its own stream, so that a pending read-back
+    #                               does not hold up the next step's input copies)
+    hp8 = [torch.from_numpy(r).pin_memory() for r in h8]
+    hpk = [torch.from_numpy(k).pin_memory() for k in hkv]
+    hpc = [torch.from_numpy(h[2]).pin_memory() for h in host]
+    hpn = [torch.from_numpy(z_).pin_memory() for z_ in hnz]
+    h2d = sum(t.numel() * t.element_size() for t in hp8 + hpk + hpc + hpn)
+    sets = []
+    for k in range(2):
         with torch.cuda.stream(st):
-            for i in range(n_inst):
-                cand_d[i].copy_(hc[i], non_blocking=True)
-                kv[i].copy_(hk[i], non_blocking=True)
-                cf[i].copy_(hf[i], non_blocking=True)
-                nz[i].copy_(hn[i], non_blocking=True)
-            batch.sample_sparse_poly(kv, cf, nz, outs=smp)
-            batch.reconstruct_async(smp)
-            out_n.copy_(batch.nout, non_blocking=True)
-            for i in range(n_inst):
-                out_s[i].copy_(batch.supp[i], non_blocking=True)
-                out_c[i].copy_(batch.coef[i], non_blocking=True)
-        st.synchronize()
+            c8 = [t.to(dev, non_blocking=True) for t in hp8]
+            ps = make_plans(c8)
+            bset = {"cand": c8, "plans": ps, "batch": G.Batch(ps, use_graph=False, stream=st),
+                    "kv": [t.to(dev, non_blocking=True) for t in hpk],
+                    "cf": [t.to(dev, non_blocking=True) for t in hpc],
+                    "nz": [t.to(dev, non_blocking=True) for t in hpn],
+                    "smp": [torch.empty(p_.n_samples, dtype=torch.complex64, device=dev) for p_ in ps],
+                    "copied": torch.cuda.Event(), "computed": torch.cuda.Event(), "done": torch.cuda.Event()}
+        bb = bset["batch"]
+        bset["out_s"] = [torch.empty(t.numel(), dtype=torch.int64).pin_memory() for t in bb.supp]
+        bset["out_c"] = [torch.empty(t.numel(), dtype=torch.complex128).pin_memory() for t in bb.coef]
+        bset["out_n"] = torch.empty(n_inst, dtype=torch.int64).pin_memory()
+        sets.append(bset)
+    st.synchronize()
+    d2h = sum(t.numel() * t.element_size() for t in sets[0]["out_s"] + sets[0]["out_c"]) + n_inst * 8
 
-    e2e_step()
-    d2h = sum(t.numel() * t.element_size() for t in out_s + out_c) + out_n.numel() * 8
+    def e2e_step(t):
+        b_ = sets[t % 2]
+        with torch.cuda.stream(cs):  # inputs of step t (after step t-2 released this set)
+            cs.wait_event(b_["done"])
+            for i in range(n_inst):
+                b_["cand"][i].copy_(hp8[i], non_blocking=True)
+                b_["kv"][i].copy_(hpk[i], non_blocking=True)
+                b_["cf"][i].copy_(hpc[i], non_blocking=True)
+                b_["nz"][i].copy_(hpn[i], non_blocking=True)
+            b_["copied"].record(cs)
+        with torch.cuda.stream(st):  # kernels of step t
+            st.wait_event(b_["copied"])
+            b_["batch"].sample_sparse_poly(b_["kv"], b_["cf"], b_["nz"], outs=b_["smp"])
+            b_["batch"].reconstruct_async(b_["smp"])
+            b_["computed"].record(st)
+        with torch.cuda.stream(rs):  # results of step t back to the host
+            rs.wait_event(b_["computed"])
+            b_["out_n"].copy_(b_["batch"].nout, non_blocking=True)
+            for i in range(n_inst):
+                b_["out_s"][i].copy_(b_["batch"].supp[i], non_blocking=True)
+                b_["out_c"][i].copy_(b_["batch"].coef[i], non_blocking=True)
+            b_["done"].record(rs)
+
+    for t_ in range(4):
+        e2e_step(t_)
+    torch.cuda.synchronize()
+    ne = max(4, a.steps)
     t0 = time.perf_counter()
-    for _ in range(max(3, a.steps // 2)):
-        e2e_step()
-    e2e_ms = max_over_ranks((time.perf_counter() - t0) / max(3, a.steps // 2) * 1000.0, world, dev)
+    for t_ in range(ne):
+        e2e_step(t_)
+    torch.cuda.synchronize()
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) / ne * 1000.0, world, dev)
     out["e2e"] = {"value": whole_job_value(world, n_inst, e2e_ms), "unit": "reconstructions/s",
-                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms}
+                  "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                  "pipelining": "two buffer sets: step t+1's host-to-device copies overlap step t's kernels"}
+    assert all(int(n_) > 0 for n_ in sets[(ne - 1) % 2]["out_n"].tolist())
+    for b_ in sets:
+        b_["batch"].close()
+    # ---- the same step with int32 candidate rows (4 d bytes per candidate)
+    with torch.cuda.stream(st):
+        c32 = [torch.from_numpy(h[0]).to(dev) for h in host]
+        p32 = make_plans(c32)
+        b32 = G.Batch(p32, use_graph=False, stream=st)
+        for _ in range(2):
+            b32.sample_sparse_poly(kv, cf, nz, outs=smp)
+            b32.reconstruct_async(smp)
+    st.synchronize()
+    i0, i1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    i0.record(st)
+    with torch.cuda.stream(st):
+        for _ in range(a.steps):
+            b32.sample_sparse_poly(kv, cf, nz, outs=smp)
+            b32.reconstruct_async(smp)
+    i1.record(st)
+    i1.synchronize()
+    out["int32_rows"] = {"ms_per_step": i0.elapsed_time(i1) / a.steps,
+                         "value": n_inst / (i0.elapsed_time(i1) / a.steps / 1000.0), "unit": "reconstructions/s"}
+    b32.close()
     # ---- the plain FP64 GPU path on the same workload
     with torch.cuda.stream(st):
-        p64 = [G.Plan(cand_d[i], S_SPARSE, precision=G.FP64, refine=0, tau_abs=6 * host[i][3] / math.sqrt(10331),
-                      tau_rel=0.0, seed=seeds[i], stream=st) for i in range(n_inst)]
+        p64 = make_plans(cand8, prec=G.FP64, refine=0)
         s64 = [torch.empty(p.n_samples, dtype=torch.complex128, device=dev) for p in p64]
         b64 = G.Batch(p64, use_graph=False, stream=st)
 

@@ -120,7 +120,7 @@ int Plan::io_begin() {
     return SFFT_OK;
 }
 int Plan::io_upload() {
-    SFFT_CU(cudaMemcpyAsync(d_inst, h_inst, sizeof(InstDesc), cudaMemcpyHostToDevice, st));
+    SFFT_TRY(launch_upload(d_inst, h_inst, sizeof(InstDesc), st));
     SFFT_CU(cudaEventRecord(io_ev, st));
     return SFFT_OK;
 }

@@ -275,6 +275,8 @@ struct InstDesc {
     const c64* samp_noise;     // [sum M] or NULL
 };
 
+static_assert(sizeof(InstDesc) % 8 == 0, "descriptors are uploaded as 8-byte words");
+
 // One lattice of one instance (for per-lattice kernels).
 struct LatDesc {
     int inst, l, M, N;

@@ -12,11 +12,14 @@
 
 namespace sfft {
 
-__global__ void k_gather_counts(const InstDesc* __restrict__ insts, int n, int64_t* out, int64_t* flags) {
+// output counts and status flags of batch entry i; n_out (optional) in the caller's order
+__global__ void k_gather_counts(const InstDesc* __restrict__ insts, int n, int64_t* out, int64_t* flags,
+                                const int* __restrict__ order, int64_t* n_out) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         out[i] = insts[i].cnt[1];
         flags[i] = insts[i].cnt[3];
+        if (n_out) n_out[order[i]] = insts[i].cnt[1];
     }
 }
 
@@ -33,6 +36,8 @@ struct Batch {
     std::vector<FftLaunch> samp;  // sparse-polynomial sampler transforms of every plan
     int64_t max_samp_terms_L = 0;
     int64_t* d_counts = nullptr;
+    int* d_order = nullptr;     // batch index -> caller's plan index (device copy of order)
+    int64_t* graph_nout = nullptr;  // n_out_dev the captured graph writes
     int64_t* d_flags = nullptr;
     cudaEvent_t done = nullptr;    // end of the last enqueued call (results and flags ready)
     cudaEvent_t io_ev = nullptr;   // the last call's descriptor upload has executed (staging reusable)
@@ -81,12 +86,12 @@ struct Batch {
         allocs.push_back(*p);
         return SFFT_OK;
     }
-    int enqueue(bool record_io) {
+    int enqueue(bool record_io, int64_t* n_out) {
         const int n = (int)plans.size();
-        SFFT_CU(cudaMemcpyAsync(d_inst, h_inst, sizeof(InstDesc) * n, cudaMemcpyHostToDevice, st));
+        SFFT_TRY(launch_upload(d_inst, h_inst, sizeof(InstDesc) * n, st));
         if (record_io) SFFT_CU(cudaEventRecord(io_ev, st));  // not inside a graph capture
         SFFT_TRY(run_pipeline(args, st));
-        k_gather_counts<<<(n + 127) / 128, 128, 0, st>>>(d_inst, n, d_counts, d_flags);
+        k_gather_counts<<<(n + 127) / 128, 128, 0, st>>>(d_inst, n, d_counts, d_flags, d_order, n_out);
         return launch_check("k_gather_counts");
     }
 };
@@ -195,6 +200,8 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
         b = e;
     }
     SFFT_TRY(B->alloc((void**)&B->d_counts, sizeof(int64_t) * n));
+    SFFT_TRY(B->alloc((void**)&B->d_order, sizeof(int) * n));
+    SFFT_CU(cudaMemcpy(B->d_order, B->order.data(), sizeof(int) * n, cudaMemcpyHostToDevice));
     SFFT_TRY(B->alloc((void**)&B->d_flags, sizeof(int64_t) * n));
     SFFT_CU(cudaEventCreateWithFlags(&B->done, cudaEventDisableTiming));
     SFFT_CU(cudaEventCreateWithFlags(&B->io_ev, cudaEventDisableTiming));
@@ -255,12 +262,19 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
     B->args.timer = B->timing ? &B->timer : nullptr;
     if (B->timing && B->exec == nullptr && B->use_graph && B->calls >= 1) {
         // the graph is captured without timers; timed runs of a graph batch use the eager path
-        SFFT_TRY(B->enqueue(true));
+        SFFT_TRY(B->enqueue(true, n_out_dev));
         B->pending = true;
     } else if (B->use_graph && B->calls >= 1 && !B->timing) {
+        if (B->exec && B->graph_nout != n_out_dev) {  // the graph holds the old output pointer
+            cudaGraphExecDestroy(B->exec);
+            cudaGraphDestroy(B->graph);
+            B->exec = nullptr;
+            B->graph = nullptr;
+        }
         if (!B->exec) {
             SFFT_CU(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-            int rc = B->enqueue(false);
+            int rc = B->enqueue(false, n_out_dev);
+            B->graph_nout = n_out_dev;
             cudaGraph_t g = nullptr;
             cudaError_t e = cudaStreamEndCapture(st, &g);
             if (rc != SFFT_OK) return rc;
@@ -271,13 +285,8 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
         SFFT_CU(cudaGraphLaunch(B->exec, st));
         SFFT_CU(cudaEventRecord(B->io_ev, st));  // the graph reads the staging buffer when it runs
     } else {
-        SFFT_TRY(B->enqueue(true));
+        SFFT_TRY(B->enqueue(true, n_out_dev));
         B->pending = B->timing;
-    }
-    if (n_out_dev) {
-        // results in caller order
-        for (int i = 0; i < n; ++i)
-            SFFT_CU(cudaMemcpyAsync(n_out_dev + B->order[i], B->d_counts + i, sizeof(int64_t), cudaMemcpyDeviceToDevice, st));
     }
     SFFT_CU(cudaEventRecord(B->done, st));
     B->calls++;
@@ -304,7 +313,7 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
         mx = std::max<int64_t>(mx, n_terms[u] * B->plans[i]->L);
     }
     cudaStream_t st = B->st;
-    SFFT_CU(cudaMemcpyAsync(B->d_inst, B->h_inst, sizeof(InstDesc) * n, cudaMemcpyHostToDevice, st));
+    SFFT_TRY(launch_upload(B->d_inst, B->h_inst, sizeof(InstDesc) * n, st));
     SFFT_CU(cudaEventRecord(B->io_ev, st));
     SFFT_TRY(launch_clear(B->d_inst, n, 0, 0, B->prec ? 2 : 1, st));
     if (mx > 0) SFFT_TRY(launch_scatter_terms(B->d_inst, n, mx, st));

@@ -979,7 +979,25 @@ __global__ void k_clear_inst(InstDesc* __restrict__ insts, int clear_det, int cl
     if (clear_det && blockIdx.x == 0 && threadIdx.x < 8) I.cnt[threadIdx.x] = 0;
 }
 
+// Copy from pinned host memory (device-accessible through unified addressing) by a kernel on the
+// caller's stream: descriptor uploads do not queue behind bulk transfers on the copy engines.
+__global__ void k_upload(uint64_t* __restrict__ dst, const uint64_t* __restrict__ src, int64_t words) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words; i += (int64_t)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
 // ================================================================== launch wrappers
+int launch_upload(void* dst, const void* pinned_src, size_t bytes, cudaStream_t st) {
+    if (bytes % 8 || ((uintptr_t)dst | (uintptr_t)pinned_src) % 8) {
+        set_error("upload of %zu bytes needs 8-byte sizes and alignment", bytes);
+        return SFFT_EINVAL;
+    }
+    const int64_t words = (int64_t)(bytes / 8);
+    const int gx = (int)std::min<int64_t>(64, (words + 255) / 256 + 1);
+    k_upload<<<gx, 256, 0, st>>>(reinterpret_cast<uint64_t*>(dst), reinterpret_cast<const uint64_t*>(pinned_src), words);
+    return launch_check("k_upload");
+}
+
 int launch_cand_stats(const void* cand, int i8, int ld, int64_t n, int d, int* mn, int* mx, cudaStream_t st) {
     int gx = (int)std::min<int64_t>(4 * 152, (n * d + 255) / 256 + 1);
     k_cand_stats<<<gx, 256, 0, st>>>(cand, i8, ld, n, d, mn, mx);
