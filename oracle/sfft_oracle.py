@@ -22,6 +22,8 @@ Parity status of each function (pins live in tests/test_oracle_*.py):
   refine                                                         pinned (exact case fixed
         point; direct residual == bucket identity)
   hybrid_postprocess, collision_counts                           pinned (brute force)
+  least_squares (Remark 2.8)                                     pinned (exact recovery
+        with collisions, residual orthogonality, explicit lstsq == normal equations)
   dim_incremental                                                pinned (exact recovery,
         Table 4.2 sample-count rule)
   sop_* (sum-of-products test function)                          pinned (FFT on a grid)
@@ -423,6 +425,37 @@ def hybrid_postprocess(ghat, H, pcheck, M_list):
     return np.where(nfree > 0, mean, pcheck), nfree
 
 
+def least_squares(samples_list, cand, det, z, M_list, mode="explicit"):
+    """Remark 2.8: the least-squares fit of the samples at all lattice nodes on the detected
+    frequency set, c = argmin sum_l sum_j |f(x_lj) - sum_{k in Itilde} c_k exp(2 pi i k.x_lj)|^2.
+    mode='explicit' builds the sampling matrix and calls lstsq (the definition); mode='normal'
+    solves the normal equations built with the aliasing identity (eq. 2.3):
+    (A^H A)_{k k'} = sum_l M_l [h_kl = h_k'l] and (A^H f)_k = sum_l M_l ghat^(l)_{h_kl}."""
+    L = len(z)
+    kv = np.asarray(cand, dtype=np.int64)[det]
+    if kv.shape[0] == 0:
+        return np.zeros(0, dtype=np.complex128)
+    if mode == "explicit":
+        rows, rhs = [], []
+        for l in range(L):
+            m = int(M_list[l])
+            x = lattice_numerators(z[l], m)                      # [m, d] exact numerators
+            ph = (x @ kv.T) % m                                   # exact phase numerators
+            rows.append(np.exp(2j * np.pi * ph / m))
+            rhs.append(samples_list[l])
+        A = np.concatenate(rows)
+        return np.linalg.lstsq(A, np.concatenate(rhs), rcond=None)[0]
+    H = hashes(kv, z, M_list)
+    G = np.zeros((kv.shape[0], kv.shape[0]))
+    b = np.zeros(kv.shape[0], dtype=np.complex128)
+    for l in range(L):
+        m = int(M_list[l])
+        same = H[:, l][:, None] == H[:, l][None, :]
+        G += m * same
+        b += m * lattice_dft(samples_list[l], m)[H[:, l]]
+    return np.linalg.lstsq(G, b, rcond=None)[0]
+
+
 def refine(samples_list, cand, det, coef, z, M_list, mode="direct"):
     """One FP64 refinement step on the detected support:
        r_j = f(x_j) - sum_{k in Itilde} c_k exp(2 pi i k.x_j) at every lattice node,
@@ -481,6 +514,8 @@ def reconstruct(cand, samples, z, M, tau_abs=0.0, tau_rel=0.0, nu=0.5, s_tilde=N
     if postproc == "hybrid":
         coef, nfree = hybrid_postprocess(ghat, H, pcheck, M_list)
         extra["nfree"] = nfree
+    elif postproc in ("lsq", "lsq_explicit"):
+        coef = least_squares(sl, cand, det, z, M_list, "explicit" if postproc == "lsq_explicit" else "normal")
     refined = None
     if do_refine and det.size:
         coef = refine(sl, cand, det, coef, z, M_list, refine_mode)
