@@ -62,6 +62,8 @@ extern "C" {
 
 #define SFFT_COMBINE_MEDIAN 0 /* eq. (2.6): component-wise median over the L lattices             */
 #define SFFT_COMBINE_HYBRID 1 /* Remark 2.8: mean over collision-free lattices, median fallback    */
+#define SFFT_COMBINE_LSQ 2    /* Remark 2.8: least-squares fit of all samples on the detected set, */
+                              /* started at the medians (conjugate gradients, FP64)                */
 
 typedef struct sfft_params {
     double c;         /* Cor 2.6 constant (> 1/nu); default 10.33 (Theorem 1.1)                */

@@ -22,7 +22,7 @@ lib = C.CDLL(LIB_PATH)
 OK, EINVAL, ENOTPRIME, EALIAS, EOVERFLOW, ENOMEM, ECUDA, ETIMEOUT, ECAPACITY, ESTATE = range(10)
 FP64, FP32 = 0, 1
 L_COR26, L_EQ42, L_FALLBACK = 0, 1, 2
-COMBINE_MEDIAN, COMBINE_HYBRID = 0, 1
+COMBINE_MEDIAN, COMBINE_HYBRID, COMBINE_LSQ = 0, 1, 2
 
 _NAMES = {0: "SFFT_OK", 1: "SFFT_EINVAL", 2: "SFFT_ENOTPRIME", 3: "SFFT_EALIAS", 4: "SFFT_EOVERFLOW",
           5: "SFFT_ENOMEM", 6: "SFFT_ECUDA", 7: "SFFT_ETIMEOUT", 8: "SFFT_ECAPACITY", 9: "SFFT_ESTATE"}
@@ -97,7 +97,7 @@ sfft_batch_sample_sparse_poly = _sig("sfft_batch_sample_sparse_poly", _i32, [_vp
 sfft_batch_autotune = _sig("sfft_batch_autotune", _i32, [_vp, _vp, _vp, _vp, _vp, _i32, _P(_dbl), _P(_i32)])
 sfft_batch_flags = _sig("sfft_batch_flags", _i32, [_vp, _vp])
 sfft_batch_timing = _sig("sfft_batch_timing", _i32, [_vp, _i32, _vp, _vp])
-STAGES = ["clear", "fft_fwd", "zero_test", "hash_count", "compact", "det_hashes", "combine", "refine_scatter",
+STAGES = ["clear", "fft_fwd", "zero_test", "hash_count", "compact", "det_hashes", "combine", "lsq", "refine_scatter",
           "refine_update", "select"]
 sfft_dimincr_params_default = _sig("sfft_dimincr_params_default", None, [_P(DimIncrParams)])
 sfft_dim_incremental = _sig("sfft_dim_incremental", _i32,

@@ -185,7 +185,9 @@ int Plan::buf_mode(int tprec) const {
 
 // FP32 plans with refinement run the forward transform in double-float: the refinement's
 // residual spectrum is then r_hat = ghat - C (eq. 2.3), accurate to ~1e-14 without transforms.
-int Plan::fwd_prec() const { return prec == SFFT_FP32 && p.refine ? 2 : prec; }
+int Plan::fwd_prec() const {
+    return prec == SFFT_FP32 && (p.refine || p.combine == SFFT_COMBINE_LSQ) ? 2 : prec;
+}
 
 int Plan::build_jobs() {
     const size_t e = esz();
@@ -240,6 +242,8 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     SFFT_CHECK(p.delta > 0 && p.delta < 1, SFFT_EINVAL, "delta must be in (0, 1)");
     SFFT_CHECK(p.precision == SFFT_FP64 || p.precision == SFFT_FP32, SFFT_EINVAL, "bad precision");
     SFFT_CHECK(p.refine == 0 || p.refine == 1, SFFT_EINVAL, "refine must be 0 or 1");
+    SFFT_CHECK(p.combine == SFFT_COMBINE_MEDIAN || p.combine == SFFT_COMBINE_HYBRID || p.combine == SFFT_COMBINE_LSQ,
+               SFFT_EINVAL, "bad combine mode");
     SFFT_CHECK(p.cand_type == SFFT_CAND_I32 || p.cand_type == SFFT_CAND_I8, SFFT_EINVAL, "bad cand_type");
     if (p.cand_type == SFFT_CAND_I32) {
         SFFT_CHECK(p.cand_ld == 0 || p.cand_ld == d, SFFT_EINVAL, "int32 candidate rows are dense (cand_ld 0 or d)");
@@ -364,6 +368,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     SFFT_TRY(P->alloc((void**)&P->coll, sizeof(int32_t) * P->sumM));
     SFFT_TRY(P->alloc((void**)&P->C, sizeof(c64) * P->sumM));
     if (P->fwd_prec() == 2) SFFT_TRY(P->alloc((void**)&P->ghat_lo, sizeof(c32) * P->sumM));
+    if (p.combine == SFFT_COMBINE_LSQ) SFFT_TRY(P->alloc((void**)&P->lsq_work, sizeof(c64) * 3 * cap));
     if (!P->buf_mode(P->fwd_prec()) || !P->buf_mode(P->prec))
         SFFT_TRY(P->alloc(&P->scratch, sizeof(c64) * (size_t)P->maxN * L));
     SFFT_TRY(P->alloc((void**)&P->sop_a, sizeof(double) * 2 * 16 * 129));
@@ -380,7 +385,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     I.cand = cand; I.cand_i8 = p.cand_type == SFFT_CAND_I8; I.cand_ld = p.cand_ld; I.z = dz; I.Ml = dM; I.mu = dmu; I.offk = doffk; I.soff = dsoff; I.boff = dboff;
     I.nzbits = P->nzbits; I.ghat = P->ghat; I.stats = P->stats; I.detbits = P->detbits; I.det = P->det;
     I.cnt = P->cnt; I.coef = P->coef; I.H = P->H; I.sel = P->sel; I.coll = P->coll; I.C = P->C;
-    I.ghat_lo = P->ghat_lo; I.outpos = P->outpos;
+    I.ghat_lo = P->ghat_lo; I.lsq_work = P->lsq_work; I.outpos = P->outpos;
     SFFT_CU(cudaEventCreateWithFlags(&P->io_ev, cudaEventDisableTiming));
     SFFT_TRY(P->alloc((void**)&P->d_inst, sizeof(InstDesc)));
     SFFT_CU(cudaMemcpy(P->d_inst, &I, sizeof(InstDesc), cudaMemcpyHostToDevice));
@@ -461,6 +466,10 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
     SFFT_TRY(mark(a, ST_COMBINE, st));
     if (a.hybrid) SFFT_TRY(launch_collisions(a.d_inst, ni, st));
     SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, 0, st));
+    if (a.lsq) {  // Remark 2.8 least squares on the detected set, from the medians
+        SFFT_TRY(mark(a, ST_LSQ, st));
+        SFFT_TRY(launch_lsq(a.d_inst, ni, a.prec, st));
+    }
     if (a.refine) {
         SFFT_TRY(mark(a, ST_SCATTER, st));
         SFFT_TRY(launch_clear(a.d_inst, ni, 0, 0, 1, st));
@@ -486,7 +495,7 @@ PipeArgs Plan::pipe_args() {
     PipeArgs a;
     a.ninst = 1; a.d_inst = d_inst; a.d_lats = d_lats; a.nlat = L;
     a.prec = prec; a.fwd_prec = fwd_prec(); a.maxcap = cap;
-    a.hybrid = p.combine == SFFT_COMBINE_HYBRID; a.refine = p.refine;
+    a.hybrid = p.combine == SFFT_COMBINE_HYBRID; a.refine = p.refine; a.lsq = p.combine == SFFT_COMBINE_LSQ;
     a.fwd.push_back(FftLaunch{d_jobs_fwd, L, maxN, buf_mode(fwd_prec())});
     const int ng = (int)hgroups.size();
     for (int g = 0; g < ng; ++g) {

@@ -260,6 +260,7 @@ struct InstDesc {
     c64* C;                    // [sum M] bucket scatter buffer
     c32* ghat_lo;              // [sum M] low words of a double-float forward transform, or NULL
     int32_t* outpos;           // [cap] detected position of output q
+    c64* lsq_work;             // [3 cap] conjugate-gradient vectors (least-squares combine) or NULL
     // ---- per call
     const void* samples;       // [sum M] complex (prec)
     int64_t* supp_out;

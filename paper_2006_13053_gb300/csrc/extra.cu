@@ -108,6 +108,8 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
         auto P = reinterpret_cast<Plan*>(plans[i]);
         SFFT_CHECK(P->prec == P0->prec, SFFT_EINVAL, "all plans of a batch need the same precision");
         SFFT_CHECK(P->p.refine == P0->p.refine, SFFT_EINVAL, "all plans of a batch need the same refine setting");
+        SFFT_CHECK(P->fwd_prec() == P0->fwd_prec(), SFFT_EINVAL,
+                   "all plans of a batch need the same forward-transform arithmetic (refine / least-squares)");
     }
     std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) {
         return reinterpret_cast<Plan*>(plans[a])->d < reinterpret_cast<Plan*>(plans[b])->d;
@@ -131,6 +133,7 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
         B->h_inst[b] = *P->h_inst;
         A.maxcap = std::max<int64_t>(A.maxcap, P->cap);
         A.hybrid |= P->p.combine == SFFT_COMBINE_HYBRID;
+        A.lsq |= P->p.combine == SFFT_COMBINE_LSQ;
         for (int l = 0; l < P->L; ++l)
             lats.push_back(LatDesc{b, l, (int)P->M[l], (int)P->tabs[l]->N, P->soff[l], P->boff[l], 0,
                                    (const double*)P->tabs[l]->dft64});

@@ -720,6 +720,111 @@ __global__ void k_refine_update(const InstDesc* __restrict__ insts) {
     }
 }
 
+// Least-squares post-processing (Remark 2.8): with A the sampling matrix of the detected set at
+// all lattice nodes, the aliasing formula (eq. 2.3) gives A^H A = G = sum_l M_l P_l^T P_l (P_l maps
+// k to its bucket h_kl) and A^H f = b, b_k = sum_l M_l ghat^(l)_{h_kl}.  One CTA per instance
+// runs conjugate gradients on G c = b from the median estimates: G v scatters v into the touched
+// buckets of C (FP64 atomics), then gathers sum_l M_l C_l[h_kl].  Stops at |r| <= tol |b| or after
+// max_iter iterations.  G is real symmetric positive semi-definite, so CG on complex vectors works.
+constexpr int kLsqThreads = 1024;
+
+__device__ double block_sum_f64(double v, double* sh) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double r = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    __syncthreads();
+    return r;
+}
+
+template <class TS>
+__global__ void __launch_bounds__(kLsqThreads) k_lsq(InstDesc* __restrict__ insts, int max_iter, double tol) {
+    __shared__ double red[32];
+    InstDesc& I = insts[blockIdx.x];
+    if (I.combine != SFFT_COMBINE_LSQ || I.lsq_work == nullptr) return;
+    const int64_t nd = min(I.cnt[0], I.cap);
+    if (nd == 0) return;
+    const int L = I.L;
+    const int64_t ne = nd * L;
+    c64* x = I.coef;
+    c64* r = I.lsq_work;
+    c64* p = r + I.cap;
+    c64* Ap = p + I.cap;
+    const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
+    const c32* glo = I.ghat_lo;
+    auto bucket = [&](int64_t e) -> int64_t {  // flat bucket index of entry e = q L + l
+        const int l = (int)(e % L);
+        return I.soff[l] + I.H[e];
+    };
+    auto matvec = [&](const c64* v, c64* out) {
+        for (int64_t e = threadIdx.x; e < ne; e += blockDim.x) I.C[bucket(e)] = c64{0, 0};
+        __syncthreads();
+        for (int64_t e = threadIdx.x; e < ne; e += blockDim.x) {
+            const int64_t b = bucket(e);
+            const c64 w = v[e / L];
+            atomicAdd(&I.C[b].x, w.x);
+            atomicAdd(&I.C[b].y, w.y);
+        }
+        __syncthreads();
+        for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) {
+            double sx = 0, sy = 0;
+            for (int l = 0; l < L; ++l) {
+                const c64 c = I.C[I.soff[l] + I.H[q * L + l]];
+                const double m = (double)I.Ml[l];
+                sx += m * c.x;
+                sy += m * c.y;
+            }
+            out[q] = c64{sx, sy};
+        }
+        __syncthreads();
+    };
+    // r = b - G x,  p = r
+    matvec(x, Ap);
+    double rr = 0, bb = 0;
+    for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) {
+        double bx = 0, by = 0;
+        for (int l = 0; l < L; ++l) {
+            const int64_t b = I.soff[l] + I.H[q * L + l];
+            const cplx<TS> v = g[b];
+            double vx = (double)v.x, vy = (double)v.y;
+            if (glo) { vx += (double)glo[b].x; vy += (double)glo[b].y; }
+            const double m = (double)I.Ml[l];
+            bx += m * vx;
+            by += m * vy;
+        }
+        const c64 rq = {bx - Ap[q].x, by - Ap[q].y};
+        r[q] = rq;
+        p[q] = rq;
+        rr += rq.x * rq.x + rq.y * rq.y;
+        bb += bx * bx + by * by;
+    }
+    rr = block_sum_f64(rr, red);
+    bb = block_sum_f64(bb, red);
+    for (int it = 0; it < max_iter && rr > tol * tol * bb; ++it) {
+        matvec(p, Ap);
+        double pAp = 0;
+        for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) pAp += p[q].x * Ap[q].x + p[q].y * Ap[q].y;
+        pAp = block_sum_f64(pAp, red);
+        if (!(pAp > 0)) break;
+        const double alpha = rr / pAp;
+        double rn = 0;
+        for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) {
+            x[q] = c64{x[q].x + alpha * p[q].x, x[q].y + alpha * p[q].y};
+            const c64 rq = {r[q].x - alpha * Ap[q].x, r[q].y - alpha * Ap[q].y};
+            r[q] = rq;
+            rn += rq.x * rq.x + rq.y * rq.y;
+        }
+        rn = block_sum_f64(rn, red);
+        const double beta = rn / rr;
+        for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) p[q] = c64{r[q].x + beta * p[q].x, r[q].y + beta * p[q].y};
+        __syncthreads();
+        rr = rn;
+    }
+}
+
+// scatter the detected coefficients into their buckets: C_l[h_kl] += c_k
 __global__ void k_scatter_coef(const InstDesc* __restrict__ insts) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nd = min(I.cnt[0], I.cap);
@@ -1100,6 +1205,12 @@ int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int 
     if (prec) k_combine<float><<<dim3(gx, ninst), 256, 0, st>>>(di);
     else k_combine<double><<<dim3(gx, ninst), 256, 0, st>>>(di);
     return launch_check("k_combine");
+}
+
+int launch_lsq(InstDesc* di, int ninst, int prec, cudaStream_t st) {
+    if (prec) k_lsq<float><<<ninst, kLsqThreads, 0, st>>>(di, 64, 1e-14);
+    else k_lsq<double><<<ninst, kLsqThreads, 0, st>>>(di, 64, 1e-14);
+    return launch_check("k_lsq");
 }
 
 int launch_scatter_coef(const InstDesc* di, int ninst, cudaStream_t st) {

@@ -14,6 +14,7 @@ int launch_compact(InstDesc* di, int ninst, cudaStream_t st);
 int launch_det_hashes(const InstDesc* di, int ninst, int64_t maxdet, cudaStream_t st);
 int launch_collisions(const InstDesc* di, int ninst, cudaStream_t st);
 int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int mode, cudaStream_t st);
+int launch_lsq(InstDesc* di, int ninst, int prec, cudaStream_t st);
 int launch_scatter_coef(const InstDesc* di, int ninst, cudaStream_t st);
 int launch_select(InstDesc* di, int ninst, cudaStream_t st);
 int launch_scatter_terms(const InstDesc* di, int ninst, int64_t max_terms_x_L, cudaStream_t st);

@@ -25,7 +25,7 @@ struct HashGroup {
 // optional per-stage CUDA-event timing of the stage sequence
 enum Stage : int {
     ST_CLEAR = 0, ST_FFT_FWD, ST_ZERO_TEST, ST_HASH, ST_COMPACT, ST_DET_HASH, ST_COMBINE,
-    ST_SCATTER, ST_DELTA, ST_SELECT, ST_COUNT
+    ST_LSQ, ST_SCATTER, ST_DELTA, ST_SELECT, ST_COUNT
 };
 struct StageTimer {
     cudaEvent_t ev[ST_COUNT + 1];
@@ -37,7 +37,7 @@ struct PipeArgs {
     int ninst = 1, nlat = 0, prec = 0;
     int fwd_prec = 0;  // arithmetic of the forward transforms (2 = double-float for FP32 + refinement)
     int64_t maxcap = 0;
-    int hybrid = 0, refine = 0;
+    int hybrid = 0, refine = 0, lsq = 0;
     InstDesc* d_inst = nullptr;
     const LatDesc* d_lats = nullptr;
     std::vector<FftLaunch> fwd;
@@ -68,6 +68,7 @@ struct Plan {
     int32_t* coll = nullptr;
     c64* C = nullptr;
     c32* ghat_lo = nullptr;  // low words of the double-float forward transform (FP32 + refinement)
+    c64* lsq_work = nullptr; // conjugate-gradient vectors of the least-squares combine
     void* scratch = nullptr;
     double* sop_a = nullptr;
     int32_t* sop_tri = nullptr;
