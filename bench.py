@@ -431,6 +431,35 @@ def run_native(a, rank, world):
     assert all(int(n_) > 0 for n_ in sets[(ne - 1) % 2]["out_n"].tolist())
     for b_ in sets:
         b_["batch"].close()
+    # ---- the same step with the least-squares combine (Remark 2.8) instead of median + refinement
+    with torch.cuda.stream(st):
+        pl = [G.Plan(r, S_SPARSE, d=D, precision=G.FP32, refine=0, combine=G.COMBINE_LSQ,
+                     tau_abs=6 * h[3] / math.sqrt(10331), tau_rel=0.0, seed=s_, stream=st)
+              for r, h, s_ in zip(cand8, host, seeds)]
+        bl = G.Batch(pl, use_graph=False, stream=st)
+        for _ in range(2):
+            bl.sample_sparse_poly(kv, cf, nz, outs=smp)
+            bl.reconstruct_async(smp)
+    st.synchronize()
+    l0, l1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    l0.record(st)
+    with torch.cuda.stream(st):
+        for _ in range(a.steps):
+            bl.sample_sparse_poly(kv, cf, nz, outs=smp)
+            bl.reconstruct_async(smp)
+    l1.record(st)
+    l1.synchronize()
+    bl.timing(1)
+    with torch.cuda.stream(st):
+        for _ in range(3):
+            bl.sample_sparse_poly(kv, cf, nz, outs=smp)
+            bl.reconstruct_async(smp)
+    st.synchronize()
+    lst = bl.timing(0)
+    out["least_squares"] = {"ms_per_step": l0.elapsed_time(l1) / a.steps,
+                            "value": n_inst / (l0.elapsed_time(l1) / a.steps / 1000.0), "unit": "reconstructions/s",
+                            "lsq_stage_ms": lst["lsq"][0] / max(lst["lsq"][1], 1)}
+    bl.close()
     # ---- the same step with int32 candidate rows (4 d bytes per candidate)
     with torch.cuda.stream(st):
         c32 = [torch.from_numpy(h[0]).to(dev) for h in host]

@@ -136,6 +136,7 @@ typedef struct sfft_diag {
     double* tau;         /* device double [L]: zero-test thresholds                           */
     int64_t n_detected;  /* out: |Itilde|                                                     */
     int64_t n_guard;     /* out: buckets whose zero test was re-done in FP64                  */
+    int64_t lsq_iters;   /* out: conjugate-gradient iterations of the least-squares combine   */
 } sfft_diag;
 
 /*

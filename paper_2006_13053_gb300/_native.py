@@ -48,7 +48,7 @@ class Params(C.Structure):
 class Diag(C.Structure):
     _fields_ = [("counts", C.c_void_p), ("hashes", C.c_void_p), ("collisions", C.c_void_p),
                 ("detected", C.c_void_p), ("pcheck", C.c_void_p), ("ghat", C.c_void_p), ("tau", C.c_void_p),
-                ("n_detected", C.c_int64), ("n_guard", C.c_int64)]
+                ("n_detected", C.c_int64), ("n_guard", C.c_int64), ("lsq_iters", C.c_int64)]
 
 
 class DimIncrParams(C.Structure):

@@ -164,6 +164,7 @@ class Plan:
             nd = D.n_detected
             info["n_detected"] = nd
             info["n_guard"] = D.n_guard
+            info["lsq_iters"] = D.lsq_iters
             info["detected"] = info.pop("detected_buf")[:nd]
             info["pcheck"] = info.pop("pcheck_buf")[:nd]
             return supp[:k], coef[:k], info

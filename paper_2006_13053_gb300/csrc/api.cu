@@ -368,7 +368,12 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     SFFT_TRY(P->alloc((void**)&P->coll, sizeof(int32_t) * P->sumM));
     SFFT_TRY(P->alloc((void**)&P->C, sizeof(c64) * P->sumM));
     if (P->fwd_prec() == 2) SFFT_TRY(P->alloc((void**)&P->ghat_lo, sizeof(c32) * P->sumM));
-    if (p.combine == SFFT_COMBINE_LSQ) SFFT_TRY(P->alloc((void**)&P->lsq_work, sizeof(c64) * 3 * cap));
+    if (p.combine == SFFT_COMBINE_LSQ) {
+        SFFT_TRY(P->alloc((void**)&P->lsq_work, sizeof(c64) * 3 * cap));
+        SFFT_TRY(P->alloc((void**)&P->lsq_next, sizeof(int32_t) * cap * L));
+        P->lsq_pair_cap = 16 * cap;  // off-diagonal entries; more (many-way collisions): bucket matvec
+        SFFT_TRY(P->alloc(&P->lsq_pairs, 16 * (size_t)P->lsq_pair_cap));
+    }
     if (!P->buf_mode(P->fwd_prec()) || !P->buf_mode(P->prec))
         SFFT_TRY(P->alloc(&P->scratch, sizeof(c64) * (size_t)P->maxN * L));
     SFFT_TRY(P->alloc((void**)&P->sop_a, sizeof(double) * 2 * 16 * 129));
@@ -386,6 +391,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     I.nzbits = P->nzbits; I.ghat = P->ghat; I.stats = P->stats; I.detbits = P->detbits; I.det = P->det;
     I.cnt = P->cnt; I.coef = P->coef; I.H = P->H; I.sel = P->sel; I.coll = P->coll; I.C = P->C;
     I.ghat_lo = P->ghat_lo; I.lsq_work = P->lsq_work; I.outpos = P->outpos;
+    I.lsq_next = P->lsq_next; I.lsq_pairs = P->lsq_pairs; I.lsq_pair_cap = P->lsq_pair_cap;
     SFFT_CU(cudaEventCreateWithFlags(&P->io_ev, cudaEventDisableTiming));
     SFFT_TRY(P->alloc((void**)&P->d_inst, sizeof(InstDesc)));
     SFFT_CU(cudaMemcpy(P->d_inst, &I, sizeof(InstDesc), cudaMemcpyHostToDevice));
@@ -639,6 +645,7 @@ int sfft_reconstruct(sfft_plan* plan, const void* samples, int64_t* supp_out, do
     if (diag) {
         diag->n_detected = c[0];
         diag->n_guard = c[2];
+        diag->lsq_iters = c[4];
     }
     if (n_out) *n_out = c[1];
     P->have_forward = true;

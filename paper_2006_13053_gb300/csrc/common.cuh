@@ -261,6 +261,9 @@ struct InstDesc {
     c32* ghat_lo;              // [sum M] low words of a double-float forward transform, or NULL
     int32_t* outpos;           // [cap] detected position of output q
     c64* lsq_work;             // [3 cap] conjugate-gradient vectors (least-squares combine) or NULL
+    int32_t* lsq_next;         // [cap, L] bucket lists of the detected entries (least squares)
+    void* lsq_pairs;           // [lsq_pair_cap] colliding pairs (q, q', M_l) of the normal matrix
+    int64_t lsq_pair_cap;
     // ---- per call
     const void* samples;       // [sum M] complex (prec)
     int64_t* supp_out;
@@ -289,5 +292,6 @@ struct LatDesc {
 
 // error flag bits (InstDesc::cnt[3])
 enum : int64_t { ERR_DET_CAP = 1, ERR_GUARD_CAP = 2, ERR_OUT_CAP = 4 };
+// counters InstDesc::cnt[4]: least-squares CG iterations; cnt[5]: colliding pairs found
 
 }  // namespace sfft

@@ -720,13 +720,68 @@ __global__ void k_refine_update(const InstDesc* __restrict__ insts) {
     }
 }
 
-// Least-squares post-processing (Remark 2.8): with A the sampling matrix of the detected set at
+// Least-squares post-processing (Remark 2.8).  With A the sampling matrix of the detected set at
 // all lattice nodes, the aliasing formula (eq. 2.3) gives A^H A = G = sum_l M_l P_l^T P_l (P_l maps
-// k to its bucket h_kl) and A^H f = b, b_k = sum_l M_l ghat^(l)_{h_kl}.  One CTA per instance
-// runs conjugate gradients on G c = b from the median estimates: G v scatters v into the touched
-// buckets of C (FP64 atomics), then gathers sum_l M_l C_l[h_kl].  Stops at |r| <= tol |b| or after
-// max_iter iterations.  G is real symmetric positive semi-definite, so CG on complex vectors works.
+// k to its bucket h_kl) and A^H f = b, b_k = sum_l M_l ghat^(l)_{h_kl}.  G = D + E with the
+// diagonal D_k = sum_l M_l and E_kk' = sum of M_l over the lattices where k and k' collide: with
+// M ~ 10 s, E has a few entries per row.  Three grid-wide kernels build the bucket lists of the
+// detected entries (the collision-count buffer holds the list heads), the right-hand side, and the
+// list of colliding pairs; one CTA per instance then runs conjugate gradients on G c = b from the
+// median estimates with G v = D v + E v over the pairs.  When the pairs exceed their capacity
+// (many-way collisions) G v falls back to a scatter of v into the buckets and a weighted gather.
 constexpr int kLsqThreads = 1024;
+struct LsqPair {
+    int32_t q, q2;
+    double w;
+};
+
+// mode 0: heads of the touched buckets := -1, r := 0, pair count := 0
+// mode 1: push every entry e = q L + l on its bucket's list; r_q += M_l ghat^(l)_{h_ql} (= b)
+template <class TS>
+__global__ void k_lsq_prep(InstDesc* __restrict__ insts, int mode) {
+    InstDesc& I = insts[blockIdx.y];
+    if (I.combine != SFFT_COMBINE_LSQ || I.lsq_work == nullptr) return;
+    const int64_t nd = min(I.cnt[0], I.cap);
+    const int L = I.L;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (mode == 0) {
+        for (int64_t e = t0; e < nd * L; e += stride) I.coll[I.soff[e % L] + I.H[e]] = -1;
+        for (int64_t q = t0; q < nd; q += stride) I.lsq_work[q] = c64{0, 0};
+        if (t0 == 0) I.cnt[5] = 0;
+        return;
+    }
+    const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
+    for (int64_t e = t0; e < nd * L; e += stride) {
+        const int l = (int)(e % L);
+        const int64_t b = I.soff[l] + I.H[e];
+        I.lsq_next[e] = atomicExch(&I.coll[b], (int32_t)e);
+        const cplx<TS> v = g[b];
+        double vx = (double)v.x, vy = (double)v.y;
+        if (I.ghat_lo) { vx += (double)I.ghat_lo[b].x; vy += (double)I.ghat_lo[b].y; }
+        const double m = (double)I.Ml[l];
+        atomicAdd(&I.lsq_work[e / L].x, m * vx);
+        atomicAdd(&I.lsq_work[e / L].y, m * vy);
+    }
+}
+
+// every ordered colliding pair (q, q') of a lattice, with weight M_l
+__global__ void k_lsq_pairs(InstDesc* __restrict__ insts) {
+    InstDesc& I = insts[blockIdx.y];
+    if (I.combine != SFFT_COMBINE_LSQ || I.lsq_work == nullptr) return;
+    const int64_t nd = min(I.cnt[0], I.cap);
+    const int L = I.L;
+    LsqPair* pairs = reinterpret_cast<LsqPair*>(I.lsq_pairs);
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < nd * L; e += (int64_t)gridDim.x * blockDim.x) {
+        const int l = (int)(e % L);
+        const int64_t b = I.soff[l] + I.H[e];
+        for (int32_t f = I.coll[b]; f >= 0; f = I.lsq_next[f]) {
+            if (f == (int32_t)e) continue;
+            const unsigned long long k = atomicAdd((unsigned long long*)&I.cnt[5], 1ull);
+            if ((int64_t)k < I.lsq_pair_cap) pairs[k] = LsqPair{(int32_t)(e / L), (int32_t)(f / L), (double)I.Ml[l]};
+        }
+    }
+}
 
 __device__ double block_sum_f64(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -739,8 +794,7 @@ __device__ double block_sum_f64(double v, double* sh) {
     return r;
 }
 
-template <class TS>
-__global__ void __launch_bounds__(kLsqThreads) k_lsq(InstDesc* __restrict__ insts, int max_iter, double tol) {
+__global__ void __launch_bounds__(kLsqThreads) k_lsq_cg(InstDesc* __restrict__ insts, int max_iter, double tol) {
     __shared__ double red[32];
     InstDesc& I = insts[blockIdx.x];
     if (I.combine != SFFT_COMBINE_LSQ || I.lsq_work == nullptr) return;
@@ -749,32 +803,40 @@ __global__ void __launch_bounds__(kLsqThreads) k_lsq(InstDesc* __restrict__ inst
     const int L = I.L;
     const int64_t ne = nd * L;
     c64* x = I.coef;
-    c64* r = I.lsq_work;
+    c64* r = I.lsq_work;  // holds b on entry
     c64* p = r + I.cap;
     c64* Ap = p + I.cap;
-    const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
-    const c32* glo = I.ghat_lo;
-    auto bucket = [&](int64_t e) -> int64_t {  // flat bucket index of entry e = q L + l
-        const int l = (int)(e % L);
-        return I.soff[l] + I.H[e];
-    };
+    const int64_t npair = I.cnt[5];
+    const bool sparse = npair <= I.lsq_pair_cap;
+    const LsqPair* pairs = reinterpret_cast<const LsqPair*>(I.lsq_pairs);
+    double dg = 0;  // D_k = sum_l M_l
+    for (int l = 0; l < L; ++l) dg += (double)I.Ml[l];
     auto matvec = [&](const c64* v, c64* out) {
-        for (int64_t e = threadIdx.x; e < ne; e += blockDim.x) I.C[bucket(e)] = c64{0, 0};
+        if (sparse) {
+            for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) out[q] = c64{dg * v[q].x, dg * v[q].y};
+            __syncthreads();
+            for (int64_t j = threadIdx.x; j < npair; j += blockDim.x) {
+                const LsqPair pr = pairs[j];
+                atomicAdd(&out[pr.q].x, pr.w * v[pr.q2].x);
+                atomicAdd(&out[pr.q].y, pr.w * v[pr.q2].y);
+            }
+            __syncthreads();
+            return;
+        }
+        for (int64_t e = threadIdx.x; e < ne; e += blockDim.x) I.C[I.soff[e % L] + I.H[e]] = c64{0, 0};
         __syncthreads();
         for (int64_t e = threadIdx.x; e < ne; e += blockDim.x) {
-            const int64_t b = bucket(e);
-            const c64 w = v[e / L];
-            atomicAdd(&I.C[b].x, w.x);
-            atomicAdd(&I.C[b].y, w.y);
+            c64* c = &I.C[I.soff[e % L] + I.H[e]];
+            atomicAdd(&c->x, v[e / L].x);
+            atomicAdd(&c->y, v[e / L].y);
         }
         __syncthreads();
         for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) {
             double sx = 0, sy = 0;
             for (int l = 0; l < L; ++l) {
                 const c64 c = I.C[I.soff[l] + I.H[q * L + l]];
-                const double m = (double)I.Ml[l];
-                sx += m * c.x;
-                sy += m * c.y;
+                sx += (double)I.Ml[l] * c.x;
+                sy += (double)I.Ml[l] * c.y;
             }
             out[q] = c64{sx, sy};
         }
@@ -784,25 +846,17 @@ __global__ void __launch_bounds__(kLsqThreads) k_lsq(InstDesc* __restrict__ inst
     matvec(x, Ap);
     double rr = 0, bb = 0;
     for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) {
-        double bx = 0, by = 0;
-        for (int l = 0; l < L; ++l) {
-            const int64_t b = I.soff[l] + I.H[q * L + l];
-            const cplx<TS> v = g[b];
-            double vx = (double)v.x, vy = (double)v.y;
-            if (glo) { vx += (double)glo[b].x; vy += (double)glo[b].y; }
-            const double m = (double)I.Ml[l];
-            bx += m * vx;
-            by += m * vy;
-        }
-        const c64 rq = {bx - Ap[q].x, by - Ap[q].y};
+        const c64 bq = r[q];
+        const c64 rq = {bq.x - Ap[q].x, bq.y - Ap[q].y};
         r[q] = rq;
         p[q] = rq;
         rr += rq.x * rq.x + rq.y * rq.y;
-        bb += bx * bx + by * by;
+        bb += bq.x * bq.x + bq.y * bq.y;
     }
     rr = block_sum_f64(rr, red);
     bb = block_sum_f64(bb, red);
-    for (int it = 0; it < max_iter && rr > tol * tol * bb; ++it) {
+    int it = 0;
+    for (; it < max_iter && rr > tol * tol * bb; ++it) {
         matvec(p, Ap);
         double pAp = 0;
         for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) pAp += p[q].x * Ap[q].x + p[q].y * Ap[q].y;
@@ -822,6 +876,7 @@ __global__ void __launch_bounds__(kLsqThreads) k_lsq(InstDesc* __restrict__ inst
         __syncthreads();
         rr = rn;
     }
+    if (threadIdx.x == 0) I.cnt[4] = it;  // iterations taken (diagnostics)
 }
 
 // scatter the detected coefficients into their buckets: C_l[h_kl] += c_k
@@ -1208,9 +1263,16 @@ int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int 
 }
 
 int launch_lsq(InstDesc* di, int ninst, int prec, cudaStream_t st) {
-    if (prec) k_lsq<float><<<ninst, kLsqThreads, 0, st>>>(di, 64, 1e-14);
-    else k_lsq<double><<<ninst, kLsqThreads, 0, st>>>(di, 64, 1e-14);
-    return launch_check("k_lsq");
+    const dim3 grid(152, ninst);
+    for (int mode = 0; mode < 2; ++mode) {
+        if (prec) k_lsq_prep<float><<<grid, 256, 0, st>>>(di, mode);
+        else k_lsq_prep<double><<<grid, 256, 0, st>>>(di, mode);
+        SFFT_TRY(launch_check("k_lsq_prep"));
+    }
+    k_lsq_pairs<<<grid, 256, 0, st>>>(di);
+    SFFT_TRY(launch_check("k_lsq_pairs"));
+    k_lsq_cg<<<ninst, kLsqThreads, 0, st>>>(di, 64, 1e-12);
+    return launch_check("k_lsq_cg");
 }
 
 int launch_scatter_coef(const InstDesc* di, int ninst, cudaStream_t st) {

@@ -69,6 +69,9 @@ struct Plan {
     c64* C = nullptr;
     c32* ghat_lo = nullptr;  // low words of the double-float forward transform (FP32 + refinement)
     c64* lsq_work = nullptr; // conjugate-gradient vectors of the least-squares combine
+    int32_t* lsq_next = nullptr;
+    void* lsq_pairs = nullptr;
+    int64_t lsq_pair_cap = 0;
     void* scratch = nullptr;
     double* sop_a = nullptr;
     int32_t* sop_tri = nullptr;

@@ -209,6 +209,22 @@ def test_config2_full_size_one_seed(G):
     assert np.array_equal(info2["hashes"].cpu().numpy()[idx], O.hashes(cand[idx], z, M))
 
 
+def test_config2_full_size_least_squares(G):
+    """The benchmark instance with the least-squares combine (Remark 2.8) instead of the median +
+    refinement: same support as the oracle, coefficients within the FP32-plan tolerance."""
+    seed = 1
+    cand, sup, c, z, M, L, sig = cfg2(seed, n=2 ** 20, s=1000)
+    y = (O.sample_sparse_poly(cand[sup], c, z, M) + S.noise(L * M, sig, seed)).astype(np.complex64)
+    tau = 6 * sig / math.sqrt(M)
+    ref = O.reconstruct(cand, y.astype(np.complex128), z, M, tau_abs=tau, postproc="lsq")
+    plan = G.Plan(T(cand), 1000, L=L, M=[M] * L, z=z, precision=1, combine=G.COMBINE_LSQ, tau_abs=tau, tau_rel=0.0)
+    supp, coef, info = plan.reconstruct(T(y), diag=True)
+    assert np.array_equal(supp.cpu().numpy(), ref.supp)
+    assert relmax(coef.cpu().numpy(), ref.coef) <= TOL_FP32_REFINE
+    print("least-squares CG iterations:", info["lsq_iters"])
+    assert 1 <= info["lsq_iters"] <= 64
+
+
 # ------------------------------------------------------------------ samplers and nodes
 @pytest.mark.parametrize("prec", [0, 1])
 def test_sampler_and_points(G, prec):
