@@ -783,29 +783,47 @@ __global__ void k_lsq_pairs(InstDesc* __restrict__ insts) {
     }
 }
 
+// block sum of a double: warp sums, then warp 0 sums the partials and broadcasts (FP64 work is
+// costly on this GPU, so no thread repeats the final sum)
 __device__ double block_sum_f64(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
     __syncthreads();
     if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
     __syncthreads();
-    double r = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
+    if (threadIdx.x < 32) {
+        double r = threadIdx.x < (blockDim.x >> 5) ? sh[threadIdx.x] : 0.0;
+        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+        if (threadIdx.x == 0) sh[32] = r;
+    }
+    __syncthreads();
+    const double r = sh[32];
     __syncthreads();
     return r;
 }
 
+constexpr int kLsqSmemVec = 2048;  // detected sets up to this size keep the CG vectors in shared memory
+
 __global__ void __launch_bounds__(kLsqThreads) k_lsq_cg(InstDesc* __restrict__ insts, int max_iter, double tol) {
-    __shared__ double red[32];
+    extern __shared__ __align__(16) unsigned char lsq_smem[];
+    __shared__ double red[33];
     InstDesc& I = insts[blockIdx.x];
     if (I.combine != SFFT_COMBINE_LSQ || I.lsq_work == nullptr) return;
     const int64_t nd = min(I.cnt[0], I.cap);
     if (nd == 0) return;
     const int L = I.L;
     const int64_t ne = nd * L;
-    c64* x = I.coef;
-    c64* r = I.lsq_work;  // holds b on entry
-    c64* p = r + I.cap;
-    c64* Ap = p + I.cap;
+    const bool in_smem = nd <= kLsqSmemVec;
+    c64* x = in_smem ? reinterpret_cast<c64*>(lsq_smem) : I.coef;
+    c64* r = in_smem ? x + kLsqSmemVec : I.lsq_work;  // holds b on entry
+    c64* p = in_smem ? r + kLsqSmemVec : I.lsq_work + I.cap;
+    c64* Ap = in_smem ? p + kLsqSmemVec : p + I.cap;
+    if (in_smem) {
+        for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) {
+            x[q] = I.coef[q];
+            r[q] = I.lsq_work[q];
+        }
+        __syncthreads();
+    }
     const int64_t npair = I.cnt[5];
     const bool sparse = npair <= I.lsq_pair_cap;
     const LsqPair* pairs = reinterpret_cast<const LsqPair*>(I.lsq_pairs);
@@ -876,6 +894,8 @@ __global__ void __launch_bounds__(kLsqThreads) k_lsq_cg(InstDesc* __restrict__ i
         __syncthreads();
         rr = rn;
     }
+    if (in_smem)
+        for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) I.coef[q] = x[q];
     if (threadIdx.x == 0) I.cnt[4] = it;  // iterations taken (diagnostics)
 }
 
@@ -1271,7 +1291,13 @@ int launch_lsq(InstDesc* di, int ninst, int prec, cudaStream_t st) {
     }
     k_lsq_pairs<<<grid, 256, 0, st>>>(di);
     SFFT_TRY(launch_check("k_lsq_pairs"));
-    k_lsq_cg<<<ninst, kLsqThreads, 0, st>>>(di, 64, 1e-12);
+    const int smem = 4 * kLsqSmemVec * (int)sizeof(c64);
+    static bool attr_done = false;
+    if (!attr_done) {
+        SFFT_CU(cudaFuncSetAttribute(k_lsq_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_done = true;
+    }
+    k_lsq_cg<<<ninst, kLsqThreads, smem, st>>>(di, 64, 1e-12);
     return launch_check("k_lsq_cg");
 }
 
