@@ -483,6 +483,29 @@ def test_batch_sampler_matches_plan_sampler(G):
         assert torch.equal(o, ref)
 
 
+@pytest.mark.parametrize("prec,refine", [(0, 1), (1, 1)])
+def test_transform_buffer_modes(G, prec, refine):
+    """Work-buffer modes of the transforms: M = 10331 (N = 20736) runs FP64 and double-float
+    transforms on two-CTA clusters; M = 40009 (N = 81000) in the global scratch buffer."""
+    import torch
+    for M, n, s in [(10331, 2 ** 12, 200), (40009, 2 ** 11, 60)]:
+        d, L = 6, 9
+        cand = S.uniform_distinct(n, d, -40, 40, 8)
+        sup = S.support_indices(n, s, 8)
+        c = S.coef_cgauss(s, 8)
+        z = S.generators(L, d, M, 8)
+        sig = S.snr_sigma(c, 40.0)
+        y = O.sample_sparse_poly(cand[sup], c, z, M) + S.noise(L * M, sig, 8)
+        if prec:
+            y = y.astype(np.complex64).astype(np.complex128)
+        tau = 6 * sig / math.sqrt(M)
+        ref = O.reconstruct(cand, y, z, M, tau_abs=tau, do_refine=bool(refine), refine_mode="bucket")
+        plan = G.Plan(T(cand), s, L=L, M=[M] * L, z=z, precision=prec, refine=refine, tau_abs=tau, tau_rel=0.0)
+        supp, coef = plan.reconstruct(T(y, torch.complex64 if prec else torch.complex128))
+        assert np.array_equal(supp.cpu().numpy(), ref.supp), M
+        assert relmax(coef.cpu().numpy(), ref.coef) <= (1e-10 if prec == 0 else TOL_FP32_REFINE), M
+
+
 @pytest.mark.parametrize("prec", [0, 1])
 def test_large_lattices_multi_group_hash(G, prec):
     """M = 100003 (> 32768: int32 hash kernel; bitmap of 25 lattices ~ 320 KB: two lattice groups
