@@ -426,6 +426,13 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
         l0 = l1;
     }
     P->hash_smem = *std::max_element(P->hsmem.begin(), P->hsmem.end());
+    // tensor-core inner products: exact while every |k.z| (and partial sum) is below 2^24, the
+    // bucket bit indices below 2^22, d <= 16 (2d <= 32) and L <= 64 (tensor-memory columns)
+    if (P->packed && d <= 16 && L <= 64 && P->hgroups.size() == 1 &&
+        (double)d * (double)P->kmax * (double)(maxM - 1) < 16777216.0 && words * 32 < (1 << 22)) {
+        P->tc_smem = hash_tc_smem_bytes(L, words);
+        P->hash_tc = P->tc_smem <= 220 * 1024;
+    }
     if (P->hgroups.size() > 1) {
         SFFT_TRY(P->alloc((void**)&P->cnt8, (size_t)n));
         P->h_inst->cnt8 = P->cnt8;
@@ -491,6 +498,12 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
     return SFFT_OK;
 }
 
+// grid of the tensor-core hash kernel: resident CTAs per SM from shared memory, tiles of 128
+int tc_grid(size_t smem, int64_t tiles, int count) {
+    const int per_sm = std::max<int>(1, std::min<int>(4, (int)((228 * 1024) / (smem + 1024))));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, ((int64_t)152 * per_sm + count - 1) / count));
+}
+
 int Plan::hash_grid() const {
     int per_sm = std::max<int>(1, std::min<int>(8, (int)((228 * 1024) / (hash_smem + 1024))));
     int64_t tiles = (n + 511) / 512;
@@ -508,6 +521,12 @@ PipeArgs Plan::pipe_args() {
         HashGroup h;
         h.off = 0; h.count = 1; h.d = d; h.gx = h.gx0 = hash_grid(); h.smem = hsmem[g];
         h.variant = packed ? (diag_run ? 2 : 1) : 0;
+        if (hash_tc && !diag_run) {  // per-candidate diagnostics come from the packed kernel
+            h.variant = 3;
+            h.smem = tc_smem;
+            h.gx = h.gx0 = tc_grid(tc_smem, (n + 127) / 128, 1);
+            h.tiles = (n + 127) / 128;
+        }
         h.l0 = hgroups[g].first;
         h.l1 = g + 1 < ng ? hgroups[g].second : -1;
         h.mode = (g == 0 ? 1 : 0) | (g + 1 == ng ? 2 : 0);

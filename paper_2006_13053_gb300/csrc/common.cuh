@@ -291,7 +291,7 @@ struct LatDesc {
 };
 
 // error flag bits (InstDesc::cnt[3])
-enum : int64_t { ERR_DET_CAP = 1, ERR_GUARD_CAP = 2, ERR_OUT_CAP = 4 };
+enum : int64_t { ERR_DET_CAP = 1, ERR_GUARD_CAP = 2, ERR_OUT_CAP = 4, ERR_TC_TIMEOUT = 8 };
 // counters InstDesc::cnt[4]: least-squares CG iterations; cnt[5]: colliding pairs found
 
 }  // namespace sfft

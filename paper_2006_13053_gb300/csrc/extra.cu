@@ -188,13 +188,22 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
         h.off = b;
         h.d = Pb->d;
         int64_t tiles = 0;
-        while (e < n && B->plans[e]->d == h.d && B->plans[e]->packed == Pb->packed && B->plans[e]->hgroups.size() == 1) {
-            h.smem = std::max(h.smem, B->plans[e]->hash_smem);
-            tiles = std::max<int64_t>(tiles, (B->plans[e]->n + 511) / 512);
+        const bool tc = Pb->hash_tc;
+        while (e < n && B->plans[e]->d == h.d && B->plans[e]->packed == Pb->packed && B->plans[e]->hgroups.size() == 1 &&
+               B->plans[e]->hash_tc == tc) {
+            h.smem = std::max(h.smem, tc ? B->plans[e]->tc_smem : B->plans[e]->hash_smem);
+            tiles = std::max<int64_t>(tiles, (B->plans[e]->n + (tc ? 127 : 511)) / (tc ? 128 : 512));
             ++e;
         }
         h.count = e - b;
-        h.variant = Pb->packed ? 1 : 0;
+        h.variant = tc ? 3 : Pb->packed ? 1 : 0;
+        if (tc) {
+            h.gx = h.gx0 = tc_grid(h.smem, tiles, h.count);
+            h.tiles = tiles;
+            A.hash.push_back(h);
+            b = e;
+            continue;
+        }
         int per_sm = std::max<int>(1, std::min<int>(8, (int)((228 * 1024) / (h.smem + 1024))));
         h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (152 * per_sm + h.count - 1) / h.count));
         h.gx0 = h.gx;

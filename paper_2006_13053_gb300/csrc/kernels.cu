@@ -1198,7 +1198,7 @@ int launch_clear(InstDesc* di, int ninst, int clear_det, int clear_coll, int cle
 template <int D>
 static int launch_hash_d(const InstDesc* di, int ninst, int gx, size_t smem, int variant, int l0, int l1, int mode,
                          cudaStream_t st) {
-    // variant: 0 int32 kernel, 1 packed kernel, 2 packed kernel with diagnostics
+    // variant: 0 int32 kernel, 1 packed kernel, 2 packed kernel with diagnostics (3: hash_tc.cu)
     static bool attr[3] = {false, false, false};
     if (variant == 0) {
         if (!attr[0]) {
@@ -1230,6 +1230,7 @@ size_t hash_smem_bytes(int d, int L, int64_t nwords, bool packed) {
 
 int launch_hash_count(const InstDesc* di, int ninst, int d, int gx, size_t smem, int variant, int l0, int l1, int mode,
                       cudaStream_t st) {
+    if (variant == 3) return launch_hash_count_tc(di, ninst, gx, smem, st);  // tensor-core products
     switch (d) {
 #define SFFT_HD(D) case D: return launch_hash_d<D>(di, ninst, gx, smem, variant, l0, l1, mode, st);
         SFFT_HD(1) SFFT_HD(2) SFFT_HD(3) SFFT_HD(4) SFFT_HD(5) SFFT_HD(6) SFFT_HD(7) SFFT_HD(8)

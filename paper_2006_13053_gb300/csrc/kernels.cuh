@@ -22,6 +22,8 @@ int launch_adj_scatter(const InstDesc* di, const c64* dcoef, cudaStream_t st);
 int launch_points(const InstDesc* di, int32_t* numer, double* x, int64_t tot, cudaStream_t st);
 int launch_cand_stats(const void* cand, int i8, int ld, int64_t n, int d, int* mn, int* mx, cudaStream_t st);
 int launch_to_c64(const void* src, int prec, c64* dst, int64_t n, cudaStream_t st);
+size_t hash_tc_smem_bytes(int L, int64_t nwords);
+int launch_hash_count_tc(const InstDesc* di, int ninst, int gx, size_t smem, cudaStream_t st);
 int launch_upload(void* dst, const void* pinned_src, size_t bytes, cudaStream_t st);
 int launch_clear(InstDesc* di, int ninst, int clear_det, int clear_coll, int clear_C, cudaStream_t st);
 // sum-of-products test function (sop.cu)

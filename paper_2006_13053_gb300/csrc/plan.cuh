@@ -84,6 +84,8 @@ struct Plan {
     BlueJob *d_jobs_samp = nullptr, *d_jobs_adj = nullptr;
     size_t hash_smem = 0;
     bool packed = false;          // |k| <= 127 and M <= 32768: packed dp2a hash kernel
+    bool hash_tc = false;         // tensor-core products (hash_tc.cu): one lattice group, |k.z| < 2^24
+    size_t tc_smem = 0;
     std::vector<std::pair<int, int>> hgroups;  // lattice groups whose bitmaps fit shared memory
     std::vector<size_t> hsmem;                 // shared memory of each group
     uint8_t* cnt8 = nullptr;
@@ -108,6 +110,7 @@ struct Plan {
 int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int L, const int64_t* M, const int64_t* z,
                 const sfft_params* p, cudaStream_t st);
 int run_pipeline(const PipeArgs& a, cudaStream_t st);
+int tc_grid(size_t smem, int64_t tiles, int count);
 // Bluestein job for the tables of one M; prec: 0 double, 1 float, 2 double-float; dir 0 forward
 BlueJob make_blue_job(const FftTables* t, int prec, int dir, double scale);
 int upload_jobs(const std::vector<BlueJob>& v, BlueJob** dst, std::vector<void*>* owner);
