@@ -218,12 +218,23 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
 /*
  * Autotuner: runs sfft_batch_reconstruct on the given buffers (reps timed runs per candidate
  * after one warm-up) for hash-kernel grids of 1/2, 1, 2 and 4 waves of resident CTAs and for
- * lattice transforms of 256, 384, 448 or 512 threads per CTA, times the affected stage with CUDA events,
- * keeps the fastest shapes for later calls (a captured graph is re-captured) and reports them
- * (hash_waves, fft_threads: optional host outputs).  Synchronises the batch stream.
+ * lattice transforms of 256, 384, 448 or 512 threads per CTA, and the tensor-core hash kernel
+ * (1, 2, 4 waves; plans with one lattice group, d <= 16, L <= 64, |k.z| < 2^24) against the
+ * packed one, times the affected stage with CUDA events, keeps the fastest shapes for later
+ * calls (a captured graph is re-captured) and reports them (hash_waves, negative when the
+ * tensor-core kernel won; fft_threads: optional host outputs).  Synchronises the batch stream.
  */
 int sfft_batch_autotune(sfft_batch* b, const void* const* samples, int64_t* const* supp_out, double* const* coef_out,
                         const int64_t* cap, int reps, double* hash_waves, int* fft_threads);
+
+/*
+ * Use the tensor-core hash kernel (tcgen05: the inner products k.z_l of a 128-candidate tile and
+ * all lattices as one bf16 GEMM with exact FP32 accumulation) for every hash launch of the batch
+ * that qualifies (one lattice group, d <= 16, L <= 64, d max|k| (M-1) < 2^24, |k_t| <= 127,
+ * M <= 32768).  tensor = 1 selects it; 0 is accepted only while no launch uses it.  The
+ * default is the packed dp2a kernel; sfft_batch_autotune picks whichever measures faster.
+ */
+int sfft_batch_select_hash(sfft_batch* b, int tensor);
 
 /*
  * Status of the last sfft_batch_reconstruct (waits for it): flags host int64 [n_plans] in the

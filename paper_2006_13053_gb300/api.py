@@ -267,6 +267,10 @@ class Batch:
                                       C.byref(ft)))
         return hw.value, ft.value
 
+    def select_hash(self, tensor=True):
+        """Use the tensor-core hash kernel for the launches that qualify (see the C header)."""
+        N.check(N.sfft_batch_select_hash(self.handle, 1 if tensor else 0))
+
     def flags(self):
         fl = (C.c_int64 * len(self.plans))()
         rc = N.sfft_batch_flags(self.handle, fl)

@@ -522,10 +522,10 @@ PipeArgs Plan::pipe_args() {
         h.off = 0; h.count = 1; h.d = d; h.gx = h.gx0 = hash_grid(); h.smem = hsmem[g];
         h.variant = packed ? (diag_run ? 2 : 1) : 0;
         if (hash_tc && !diag_run) {  // per-candidate diagnostics come from the packed kernel
-            h.variant = 3;
-            h.smem = tc_smem;
-            h.gx = h.gx0 = tc_grid(tc_smem, (n + 127) / 128, 1);
-            h.tiles = (n + 127) / 128;
+            h.tc_ok = true;
+            h.tc_smem = tc_smem;
+            h.tc_tiles = (n + 127) / 128;
+            h.tc_gx0 = tc_grid(tc_smem, h.tc_tiles, 1);
         }
         h.l0 = hgroups[g].first;
         h.l1 = g + 1 < ng ? hgroups[g].second : -1;

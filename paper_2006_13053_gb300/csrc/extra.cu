@@ -188,22 +188,19 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
         h.off = b;
         h.d = Pb->d;
         int64_t tiles = 0;
-        const bool tc = Pb->hash_tc;
-        while (e < n && B->plans[e]->d == h.d && B->plans[e]->packed == Pb->packed && B->plans[e]->hgroups.size() == 1 &&
-               B->plans[e]->hash_tc == tc) {
-            h.smem = std::max(h.smem, tc ? B->plans[e]->tc_smem : B->plans[e]->hash_smem);
-            tiles = std::max<int64_t>(tiles, (B->plans[e]->n + (tc ? 127 : 511)) / (tc ? 128 : 512));
+        h.tc_ok = true;
+        h.tc_tiles = 0;
+        while (e < n && B->plans[e]->d == h.d && B->plans[e]->packed == Pb->packed && B->plans[e]->hgroups.size() == 1) {
+            h.smem = std::max(h.smem, B->plans[e]->hash_smem);
+            tiles = std::max<int64_t>(tiles, (B->plans[e]->n + 511) / 512);
+            h.tc_ok = h.tc_ok && B->plans[e]->hash_tc;
+            h.tc_smem = std::max(h.tc_smem, B->plans[e]->tc_smem);
+            h.tc_tiles = std::max<int64_t>(h.tc_tiles, (B->plans[e]->n + 127) / 128);
             ++e;
         }
         h.count = e - b;
-        h.variant = tc ? 3 : Pb->packed ? 1 : 0;
-        if (tc) {
-            h.gx = h.gx0 = tc_grid(h.smem, tiles, h.count);
-            h.tiles = tiles;
-            A.hash.push_back(h);
-            b = e;
-            continue;
-        }
+        h.variant = Pb->packed ? 1 : 0;
+        if (h.tc_ok) h.tc_gx0 = tc_grid(h.tc_smem, h.tc_tiles, h.count);
         int per_sm = std::max<int>(1, std::min<int>(8, (int)((228 * 1024) / (h.smem + 1024))));
         h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (152 * per_sm + h.count - 1) / h.count));
         h.gx0 = h.gx;
@@ -372,6 +369,32 @@ int sfft_batch_autotune(sfft_batch* b, const void* const* samples, int64_t* cons
     }
     for (auto& h : B->args.hash)
         h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(h.tiles, 1), (int64_t)llround(h.gx0 * bestm)));
+    // the tensor-core hash kernel (groups that qualify), kept only if it measures faster
+    bool any_tc = false;
+    for (const auto& h : B->args.hash) any_tc |= h.tc_ok;
+    if (any_tc) {
+        const std::vector<HashGroup> keep = B->args.hash;
+        const double mtc[3] = {1.0, 2.0, 4.0};
+        double best_tc = 1e30, bmt = 1.0;
+        for (double m : mtc) {
+            for (auto& h : B->args.hash)
+                if (h.tc_ok) {
+                    h.variant = 3;
+                    h.smem = h.tc_smem;
+                    h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(h.tc_tiles, (int64_t)llround(h.tc_gx0 * m)));
+                }
+            double ms = 0;
+            SFFT_TRY(timed(ST_HASH, &ms));
+            if (ms < best_tc) { best_tc = ms; bmt = m; }
+        }
+        if (best_tc < best) {
+            for (auto& h : B->args.hash)
+                if (h.tc_ok) h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(h.tc_tiles, (int64_t)llround(h.tc_gx0 * bmt)));
+            bestm = -bmt;  // reported negative: tensor-core kernel, |value| waves
+        } else {
+            B->args.hash = keep;
+        }
+    }
     // lattice transforms: 256 to 512 threads per CTA
     const int ths[4] = {256, 384, 448, 512};
     best = 1e30;
@@ -390,6 +413,26 @@ int sfft_batch_autotune(sfft_batch* b, const void* const* samples, int64_t* cons
     if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
     if (hash_waves) *hash_waves = bestm;
     if (fft_threads) *fft_threads = bestt;
+    return SFFT_OK;
+}
+
+int sfft_batch_select_hash(sfft_batch* b, int tensor) {
+    if (!b) { set_error("batch is NULL"); return SFFT_EINVAL; }
+    Batch* B = reinterpret_cast<Batch*>(b);
+    int n_tc = 0;
+    for (auto& h : B->args.hash) {
+        if (tensor && h.tc_ok) {
+            h.variant = 3;
+            h.smem = h.tc_smem;
+            h.gx = h.gx0 = h.tc_gx0;
+            ++n_tc;
+        } else if (!tensor && h.variant == 3) {
+            SFFT_CHECK(false, SFFT_EINVAL, "switching back to the packed hash kernel needs a new batch");
+        }
+    }
+    SFFT_CHECK(!tensor || n_tc > 0, SFFT_EINVAL, "no hash launch of this batch qualifies for the tensor-core kernel");
+    if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+    if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
     return SFFT_OK;
 }
 

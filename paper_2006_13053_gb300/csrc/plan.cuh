@@ -20,6 +20,12 @@ struct HashGroup {
     int64_t tiles = 1 << 30;                                       // CTA count beyond which CTAs idle
     int l0 = 0, l1 = -1, mode = 3;  // lattice group and first/last flags (see launch_hash_count)
     size_t smem = 0;
+    // the tensor-core kernel's launch, when every plan of the group qualifies (the autotuner
+    // switches to it if it measures faster)
+    bool tc_ok = false;
+    int tc_gx0 = 1;
+    int64_t tc_tiles = 1;
+    size_t tc_smem = 0;
 };
 
 // optional per-stage CUDA-event timing of the stage sequence

@@ -43,7 +43,8 @@ def test_uneven_batch_graph_autotune_matches_oracle():
     st = torch.cuda.Stream()
     B = G.Batch(plans, use_graph=True, stream=st)
     waves, threads = B.autotune(samples, reps=1)
-    assert waves in (0.5, 1.0, 2.0, 4.0) and threads in (256, 512)
+    # packed kernel: waves in {1/2, 1, 2, 4}; tensor-core kernel: reported negative, {1, 2, 4}
+    assert waves in (0.5, 1.0, 2.0, 4.0, -1.0, -2.0, -4.0) and threads in (256, 384, 448, 512)
     for rep in range(3):  # eager, capture, replay
         res = B.reconstruct(samples)
         for (supp, coef), ref in zip(res, refs):
