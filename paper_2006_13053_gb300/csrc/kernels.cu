@@ -411,7 +411,8 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
                 uint4 v = r4[1 + w];
                 zw[4 * w] = v.x; zw[4 * w + 1] = v.y; zw[4 * w + 2] = v.z; zw[4 * w + 3] = v.w;
             }
-            const uint32_t M = cst.x, mu = cst.y, off = cst.z, bo = cst.w;
+            const uint32_t M = cst.x, mu = cst.y, off = cst.z;
+            const uint32_t* lbits = bits + (cst.w >> 5);  // the lattice's bitmap (segments start on words)
 #pragma unroll
             for (int c = 0; c < kCPT2; ++c) {
                 // the offset seeds the dot product (32-bit wrap-around equals the unsigned sum)
@@ -425,8 +426,7 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
                 const uint32_t q = __umulhi(xp, mu);
                 uint32_t rr = xp - q * M;
                 rr = min(rr, rr - M);  // one conditional subtraction: rr - M wraps above rr when rr < M
-                uint32_t bit = bo + rr;
-                cnt[c] += __funnelshift_r(bits[bit >> 5], 0u, bit) & 1u;
+                cnt[c] += __funnelshift_r(lbits[rr >> 5], 0u, rr) & 1u;  // bit rr & 31 of word rr >> 5
                 if constexpr (DIAG) {
                     if (idx[c] < n && I.dhashes) I.dhashes[idx[c] * L + l0 + l] = (int32_t)rr;
                 }

@@ -37,7 +37,9 @@ def test_dim_incremental_sparse_poly_matches_oracle(G, d, N, s, r, seed, prec):
                                           theta_abs=1e-12, delta=0.9, tau_rel=tau_rel, precision=prec, refine=1)
     assert np.array_equal(supp, ref.supp)
     assert nsamp == ref.samples
-    tol = 1e-10 if prec == 0 else 1e-9  # FP32 plans with refinement: double-float lattice DFTs
+    # FP32 plans: the black box returns FP32 samples (rounding ~6e-8 each) while the oracle samples
+    # in FP64, so the coefficients differ at that level (the transforms themselves are double-float)
+    tol = 1e-10 if prec == 0 else 1e-6
     assert np.max(np.abs(coef - ref.coef)) <= tol * np.max(np.abs(ref.coef))
     # and the recovery itself (Table 4.2 setting: relative l2 error near machine precision in FP64)
     order = np.lexsort(kv.T[::-1])
