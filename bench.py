@@ -5,7 +5,7 @@ Workload (one step): 16 independent reconstructions, each with d = 10, |Gamma| =
 frequencies drawn uniformly from [-64, 64]^10, a 1000-sparse trigonometric polynomial with
 complex-Gaussian coefficients, 40 dB complex Gaussian sample noise, L = 37 lattices of size
 M = 10331 (Corollary 2.6 with c = 10.33, delta = 0.1), FP32 samples/FFTs with one FP64
-refinement step.  A step samples the function along all lattices (lattice nodes + sampler
+refinement step (--dft df64: the forward lattice DFTs in double-float instead).  A step samples the function along all lattices (lattice nodes + sampler
 kernels) and runs the whole reconstruction (lattice DFTs, zero test, hash + count, median
 combine, refinement, Algorithm 4 selection) for all 16 instances in one batch.
 
@@ -44,12 +44,19 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--instances", type=int, default=NINST)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-path, graph, e2e and CPU legs")
-    ap.add_argument("--cpu-baseline-worker", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--dft", default="fp32", choices=["fp32", "df64"],
+                    help="arithmetic of the forward lattice DFTs under the refinement (FP32, or double-float)")
+    ap.add_argument("--cpu-baseline-worker", default=None, metavar="OUT", help=argparse.SUPPRESS)
     return ap.parse_args()
 
 
 # ------------------------------------------------------------------ inputs (seeded, synthetic)
 ROW8 = 12  # int8 candidate row stride in bytes: d = 10 entries padded to a multiple of 4
+PRECISION = {
+    "fp32": "FP32 samples, twiddles, lattice DFTs (FP32 accumulation), zero test and median; FP64 refinement "
+            "(ghat - C) and update; exact int32 hashing",
+    "df64": "FP32 samples; lattice DFTs in double-float (float pairs on the FP32 pipes); FP32 zero test + median; "
+            "FP64 refinement (ghat - C) and update; exact int32 hashing"}
 
 
 def rows8(cand):
@@ -80,13 +87,20 @@ class ClockSampler:
              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
              "clocks_event_reasons.sw_power_cap")
         try:
-            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200",
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "100",
                                           "-i", str(self.index)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thr = threading.Thread(target=self._read, daemon=True)
             self.thr.start()
+            t0 = time.time()
+            while not self.rows and time.time() - t0 < 5.0 and self.proc.poll() is None:
+                time.sleep(0.01)  # the sampler is running before the timed region starts
         except Exception:
             self.proc = None
+        self.first = len(self.rows)
         return self
+
+    def samples_since_start(self):
+        return len(self.rows) - self.first
 
     def _read(self):
         for line in self.proc.stdout:
@@ -100,15 +114,21 @@ class ClockSampler:
             except Exception:
                 self.proc.kill()
 
-    def summary(self):
-        if not self.rows:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    def summary(self, window=""):
+        rows = self.rows[self.first:]
+        if not rows:
+            why = "nvidia-smi unavailable" if self.proc is None else "no sample inside the timed region"
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [why]}
+        self.rows = rows
         sm = [float(r[1]) for r in self.rows if len(r) > 1 and r[1].replace(".", "").isdigit()]
         mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         reasons = sorted({names[i] for r in self.rows for i in range(4) if len(r) > 5 + i and r[5 + i] == "Active"})
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.rows)}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+               "reasons": reasons, "samples": len(self.rows)}
+        if window:
+            out["window"] = window
+        return out
 
 
 # ------------------------------------------------------------------ CPU oracle timing
@@ -123,38 +143,65 @@ def oracle_step_time(seed, reps=1):
     z = O.plan_generators(seed, L, D, [M] * L)
     y = O.sample_sparse_poly(cand[sup], coef, z, M) + S.noise(L * M, sigma, seed)
     tau = 6 * sigma / math.sqrt(M)
-    times = []
+    times, res = [], None
     for _ in range(reps):
         t0 = time.perf_counter()
-        O.reconstruct(cand, y, z, M, tau_abs=tau, do_refine=True, refine_mode="bucket")
+        res = O.reconstruct(cand, y, z, M, tau_abs=tau, do_refine=True, refine_mode="bucket")
         times.append(time.perf_counter() - t0)
-    return times
+    return times, res
 
 
-def cpu_baseline_worker():
-    t = oracle_step_time(0, reps=1)
+def cpu_baseline_worker(out_path):
+    import numpy as np
+    t, res = oracle_step_time(0, reps=1)
+    if out_path:
+        np.savez(out_path, supp=res.supp, coef=res.coef)
     print(json.dumps({"seconds": t[0]}))
 
 
-def cpu_baseline(timeout=600):
+def accuracy(gpu, ref_path):
+    """Instance 0 of the timed batch against the FP64 oracle's reconstruction of the same
+    function from its FP64 samples: support equality and the coefficient error (max-norm,
+    relative to max |c|, and the largest per-coefficient relative error)."""
+    import numpy as np
+    r = np.load(ref_path)
+    supp, coef = gpu
+    same = supp.shape == r["supp"].shape and bool(np.array_equal(supp, r["supp"]))
+    out = {"instance": "seed 0 (instance 0 of rank 0)", "reference": "FP64 numpy oracle on the FP64 samples",
+           "support_equal": same, "n_support": int(supp.shape[0])}
+    if same:
+        d = np.abs(coef - r["coef"])
+        out["coef_rel_err_max_norm"] = float(d.max() / np.abs(r["coef"]).max())
+        out["coef_rel_err_worst"] = float((d / np.abs(r["coef"])).max())
+    return out
+
+
+def cpu_baseline(gpu_result=None, timeout=600):
+    import tempfile
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
-    try:
-        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker"], capture_output=True,
-                           text=True, env=env, timeout=timeout)
-        sec = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
-        return {"value": 1.0 / sec, "unit": "reconstructions/s", "cores": 1, "kind": "oracle",
-                "sample": "one full instance (2^20 candidates, L=37, M=10331) reconstructed by the FP64 numpy oracle "
-                          "(Alg 2 + refinement + Alg 4; samples evaluated once beforehand), 1 thread"}
-    except Exception as e:  # reported, not fatal
-        return {"value": None, "unit": "reconstructions/s", "cores": 1, "kind": "oracle", "sample": f"failed: {e}"}
+    with tempfile.TemporaryDirectory() as td:
+        ref_path = os.path.join(td, "oracle_seed0.npz")
+        try:
+            r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-baseline-worker", ref_path],
+                               capture_output=True, text=True, env=env, timeout=timeout)
+            sec = json.loads(r.stdout.strip().splitlines()[-1])["seconds"]
+            base = {"value": 1.0 / sec, "unit": "reconstructions/s", "cores": 1, "kind": "oracle",
+                    "sample": "one full instance (2^20 candidates, L=37, M=10331) reconstructed by the FP64 numpy "
+                              "oracle (Alg 2 + refinement + Alg 4; samples evaluated once beforehand), 1 thread"}
+        except Exception as e:  # reported, not fatal
+            return {"value": None, "unit": "reconstructions/s", "cores": 1, "kind": "oracle",
+                    "sample": f"failed: {e}"}, None
+        acc = accuracy(gpu_result, ref_path) if gpu_result is not None else None
+    return base, acc
 
 
 # ------------------------------------------------------------------ native arm
 def kernel_count(batch_plans, n_inst, refine=True):
-    # per step: batched sampler (clear, bucket scatter, inverse lattice DFT) and the batch's
-    # clear + DFT + zero test + hash groups + compact + hashes + combine + select + counts
+    # per step: batched sampler (descriptor upload, clear, bucket scatter, inverse lattice DFT)
+    # and the batch's descriptor upload + clear + DFT + zero test + hash groups + compact +
+    # hashes + combine + select + counts
     hash_groups = len({p.d for p in batch_plans})
-    n = 3 + 1 + 1 + 1 + hash_groups + 1 + 1 + 1 + 1 + 1
+    n = 4 + 1 + 1 + 1 + 1 + hash_groups + 1 + 1 + 1 + 1 + 1
     if refine:
         n += 1 + 1 + 1  # clear C, scatter, median update of ghat - C
     return n
@@ -166,6 +213,16 @@ def kernel_count(batch_plans, n_inst, refine=True):
 # renormalisation); a complex sum 2 x 11 (Dekker sum: two-sum 6 + low words 2 + renormalisation 3).
 DF64_FP32_INSTR_PER_FLOP = (2 * 19 + 2 * 2 * 11) / 10.0
 FP32_LANES = 152 * 128
+
+
+# FP32 transforms: per radix-2 butterfly one complex product (2 FMUL + 2 FFMA for 6 flops) and
+# two complex sums (4 FADD for 4 flops): 8 instructions per 10 flops
+FP32_INSTR_PER_FLOP = 8 / 10.0
+# one candidate-lattice hash evaluation, d = 10 int8 rows, at least: 5 dp2a (two int16 z
+# entries x two int8 k entries each, the offset preloaded in the accumulator), Barrett
+# reduction (high product, multiply-subtract, subtract, minimum), and the bitmap test (word
+# index, shared load, bit extract, mask) plus the count add
+HASH_INSTR_PER_EVAL = 5 + 4 + 5
 
 
 def df64_peak_tflops(sm_mhz):
@@ -226,9 +283,11 @@ def run_native(a, rank, world):
     h8 = [rows8(h[0]) for h in host]                       # compact int8 candidate rows
     hkv = [h[0][h[1]] for h in host]                        # support frequencies (int32)
 
-    def make_plans(rows, prec=G.FP32, refine=1, d=D):
+    dft = G.DFT_FP32 if a.dft == "fp32" else G.DFT_DF64
+
+    def make_plans(rows, prec=G.FP32, refine=1, d=D, dft=dft):
         return [G.Plan(r, S_SPARSE, d=d if r.dtype == torch.int8 else None, precision=prec, refine=refine,
-                       tau_abs=6 * h[3] / math.sqrt(10331), tau_rel=0.0, seed=s_, stream=st)
+                       dft=dft, tau_abs=6 * h[3] / math.sqrt(10331), tau_rel=0.0, seed=s_, stream=st)
                 for r, h, s_ in zip(rows, host, seeds)]
 
     with torch.cuda.stream(st):
@@ -274,15 +333,26 @@ def run_native(a, rank, world):
             step()
         e1.record(st)
         e1.synchronize()
+        # a short timed region can end between two 100 ms samples: keep the same steps running
+        # (untimed) until three samples have been taken since the region started
+        extra, t_end = 0, time.time() + 3.0
+        while clk.proc is not None and clk.samples_since_start() < 3 and time.time() < t_end:
+            step()
+            st.synchronize()
+            extra += 1
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1) / a.steps
+    clk_window = "timed region" if extra == 0 else f"timed region + {extra} more identical steps (untimed)"
     # per-stage CUDA-event times, from a second run of the same steps with the stage timer on
     batch.timing(1)
     for _ in range(a.steps):
         step()
     st.synchronize()
     stages = batch.timing(0)
+    # instance 0's result of these steps, for the accuracy check against the oracle
+    s0_, c0_ = batch.results()[0]
+    res0 = (s0_.cpu().numpy(), c0_.cpu().numpy())
     ms = max_over_ranks(ms, world, dev)
     value = whole_job_value(world, n_inst, ms)
     stage_ms = {k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1] > 0}
@@ -297,10 +367,9 @@ def run_native(a, rank, world):
     stage_ms = {"sampler": s0.elapsed_time(s1) / a.steps, **stage_ms}
     out = {"metric": METRIC, "value": value, "unit": "reconstructions/s", "n_gpus": world, "steps": a.steps,
            "warmup": a.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-           "dtype": "df64", "data": "synthetic",
+           "dtype": "f32" if a.dft == "fp32" else "df64", "data": "synthetic",
            "config": {"workload": WORKLOAD, "global_batch": world * n_inst, "lattices": L, "lattice_size": M,
-                      "precision": "FP32 samples; lattice DFTs in double-float (float pairs on the FP32 pipes); "
-                                   "FP32 zero test + median; FP64 refinement (ghat - C) and update; exact int32 hashing",
+                      "precision": PRECISION[a.dft],
                       "candidates": f"int8 rows, {ROW8}-byte stride (the library's compact layout)",
                       "l2": f"inputs larger than L2 (16 x {NCAND * ROW8 / 2**20:.0f} MiB candidate rows per step)",
                       "parallelism": f"replicas x{world}",
@@ -308,7 +377,7 @@ def run_native(a, rank, world):
            "cand_lattice_evals_per_s": world * n_inst * NCAND * L / (ms / 1000.0),
            "stage_ms_per_step": stage_ms,
            "gpu_launches": kernel_count(plans, n_inst) * a.steps,
-           "clocks": clk.summary()}
+           "clocks": clk.summary(clk_window)}
     # ---- roofline of the dominant stage
     dom = max((k for k in stage_ms if k != "sampler"), key=stage_ms.get)
     peaks = {}
@@ -318,33 +387,46 @@ def run_native(a, rank, world):
         pass
     hbm = peaks.get("hbm_gbs", 6800.0)
     src = "of measured" if "hbm_gbs" in peaks else "of fallback"
-    per_launch_ms = stage_ms[dom]
-    if dom == "hash_count":
-        bytes_ = n_inst * NCAND * ROW8  # candidate stream: one int8 row per candidate, read once
-        ach = bytes_ / (per_launch_ms / 1000.0) / 1e9
-        out["roofline"] = {"kernel": "k_hash_count_packed", "bound": "hbm", "achieved": ach, "peak": hbm,
-                           "unit": "GB/s", "frac": ach / hbm, "peak_source": src,
-                           "traffic": traffic_from_profiles("k_hash_count_i8", n_inst * NCAND)}
-    elif dom == "fft_fwd":
-        # double-float forward lattice DFTs (FP32 + refinement): FP32-pipe instruction bound
-        N = 20736
-        flops = n_inst * L * bluestein_flops(N, M)
-        ach = flops / (per_launch_ms / 1000.0) / 1e12
-        mhz = peaks.get("sm_max_mhz", 2070.0)
-        pk = df64_peak_tflops(mhz)
-        out["roofline"] = {"kernel": "k_bluestein<df64> (forward lattice DFTs)", "bound": "alu", "achieved": ach,
-                           "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                           "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {mhz:.0f} MHz / "
-                                          f"{DF64_FP32_INSTR_PER_FLOP:.1f} FP32 instructions per df64 flop",
-                           "traffic": traffic_from_profiles("k_bluestein_df64", n_inst * L)}
-    else:
+    mhz = peaks.get("sm_max_mhz", 2070.0)
+
+    def roofline(stage):
+        t = stage_ms[stage] / 1000.0
+        if stage == "hash_count":
+            # instruction-issue bound: candidate-lattice evaluations (all L lattices of every
+            # candidate, Algorithm 2's count rule) against the issue rate / the minimal
+            # instruction count of one evaluation
+            ev = n_inst * NCAND * L
+            pk = FP32_LANES * mhz * 1e6 / HASH_INSTR_PER_EVAL / 1e12
+            return {"kernel": "k_hash_count_packed", "bound": "alu", "achieved": ev / t / 1e12, "peak": pk,
+                    "unit": "T evaluations/s", "frac": ev / t / 1e12 / pk,
+                    "peak_source": f"derived: 152 SMs x 128 lanes x {mhz:.0f} MHz / {HASH_INSTR_PER_EVAL} "
+                                   "instructions per candidate-lattice evaluation",
+                    "hbm_frac": n_inst * NCAND * ROW8 / t / 1e9 / hbm,
+                    "traffic": traffic_from_profiles("k_hash_count_i8", n_inst * NCAND)}
+        if stage == "fft_fwd":
+            flops = n_inst * L * bluestein_flops(20736, M)
+            if a.dft == "df64":
+                pk, ipf, name, key = df64_peak_tflops(mhz), DF64_FP32_INSTR_PER_FLOP, "k_bluestein<df64>", \
+                    "k_bluestein_df64"
+                what = "FP32 instructions per df64 flop"
+            else:
+                pk, ipf, name, key = FP32_LANES * mhz * 1e6 / FP32_INSTR_PER_FLOP / 1e12, FP32_INSTR_PER_FLOP, \
+                    "k_bluestein<float>", "k_bluestein_f32_fwd"
+                what = "FP32 instructions per FFT flop"
+            return {"kernel": f"{name} (forward lattice DFTs)", "bound": "alu", "achieved": flops / t / 1e12,
+                    "peak": pk, "unit": "TFLOP/s", "frac": flops / t / 1e12 / pk,
+                    "peak_source": f"derived: 152 SMs x 128 FP32 lanes x {mhz:.0f} MHz / {ipf:.1f} {what}",
+                    "traffic": traffic_from_profiles(key, n_inst * L)}
         bytes_ = n_inst * L * (M * 8 * 2)  # samples in, buckets out (FP32 complex)
-        ach = bytes_ / (per_launch_ms / 1000.0) / 1e9
-        out["roofline"] = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s",
-                           "frac": ach / hbm, "peak_source": src, "traffic": None}
+        return {"kernel": stage, "bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm, "unit": "GB/s",
+                "frac": bytes_ / t / 1e9 / hbm, "peak_source": src, "traffic": None}
+
+    out["roofline"] = roofline(dom)
+    out["stage_rooflines"] = {k: {kk: v for kk, v in roofline(k).items() if kk in ("achieved", "peak", "unit", "frac")}
+                              for k in ("fft_fwd", "hash_count") if k != dom}
     out["roofline"]["dominant_stage"] = dom
     if a.no_extras:
-        return out, plans, batch
+        return out, plans, batch, res0
     # ---- graph replay of the same step
     gbatch = G.Batch(plans, use_graph=True, stream=st)
     with torch.cuda.stream(st):
@@ -433,7 +515,7 @@ def run_native(a, rank, world):
         b_["batch"].close()
     # ---- the same step with the least-squares combine (Remark 2.8) instead of median + refinement
     with torch.cuda.stream(st):
-        pl = [G.Plan(r, S_SPARSE, d=D, precision=G.FP32, refine=0, combine=G.COMBINE_LSQ,
+        pl = [G.Plan(r, S_SPARSE, d=D, precision=G.FP32, refine=0, combine=G.COMBINE_LSQ, dft=dft,
                      tau_abs=6 * h[3] / math.sqrt(10331), tau_rel=0.0, seed=s_, stream=st)
               for r, h, s_ in zip(cand8, host, seeds)]
         bl = G.Batch(pl, use_graph=False, stream=st)
@@ -480,6 +562,29 @@ def run_native(a, rank, world):
     out["int32_rows"] = {"ms_per_step": i0.elapsed_time(i1) / a.steps,
                          "value": n_inst / (i0.elapsed_time(i1) / a.steps / 1000.0), "unit": "reconstructions/s"}
     b32.close()
+    # ---- the same step with the other forward-DFT arithmetic under the refinement
+    other = "df64" if a.dft == "fp32" else "fp32"
+    with torch.cuda.stream(st):
+        po = make_plans(cand8, dft=G.DFT_DF64 if other == "df64" else G.DFT_FP32)
+        bo = G.Batch(po, use_graph=False, stream=st)
+        for _ in range(2):
+            bo.sample_sparse_poly(kv, cf, nz, outs=smp)
+            bo.reconstruct_async(smp)
+    st.synchronize()
+    o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    o0.record(st)
+    with torch.cuda.stream(st):
+        for _ in range(a.steps):
+            bo.sample_sparse_poly(kv, cf, nz, outs=smp)
+            bo.reconstruct_async(smp)
+    o1.record(st)
+    o1.synchronize()
+    out[f"{other}_dft"] = {"ms_per_step": o0.elapsed_time(o1) / a.steps,
+                           "value": n_inst / (o0.elapsed_time(o1) / a.steps / 1000.0), "unit": "reconstructions/s",
+                           "precision": PRECISION[other]}
+    bo.close()
+    for p in po:
+        p.close()
     # ---- the plain FP64 GPU path on the same workload
     with torch.cuda.stream(st):
         p64 = make_plans(cand8, prec=G.FP64, refine=0)
@@ -505,12 +610,11 @@ def run_native(a, rank, world):
     b64.close()
     for p in p64:
         p.close()
-    return out, plans, batch
+    return out, plans, batch, res0
 
 
 def run_reference(a):
-    steps = []
-    t = oracle_step_time(0, reps=a.warmup + a.steps)
+    t, _ = oracle_step_time(0, reps=a.warmup + a.steps)
     steps = t[a.warmup:]
     sec = sum(steps) / len(steps)
     v = 1.0 / sec
@@ -526,8 +630,8 @@ def run_reference(a):
 
 def main():
     a = parse()
-    if a.cpu_baseline_worker:
-        cpu_baseline_worker()
+    if a.cpu_baseline_worker is not None:
+        cpu_baseline_worker(a.cpu_baseline_worker)
         return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -540,10 +644,12 @@ def main():
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")
-    out, plans, batch = run_native(a, rank, world)
+    out, plans, batch, res0 = run_native(a, rank, world)
     if rank == 0:
         if not a.no_extras:
-            out["cpu_baseline"] = cpu_baseline()
+            out["cpu_baseline"], acc = cpu_baseline(res0)
+            if acc is not None:
+                out["accuracy"] = acc
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

@@ -53,8 +53,21 @@ extern "C" {
 /* ---------------------------------------------------------------- parameters */
 #define SFFT_FP64 0 /* samples, twiddles and FFT arithmetic in double                         */
 #define SFFT_FP32 1 /* samples, twiddles and FFT arithmetic in float (FP32 accumulation);
-                       with refine = 1 the forward lattice DFTs run in double-float (float
-                       pairs, ~48 bits) and the refinement works on their high+low words      */
+                       with refine = 1 (or the LSQ combine) the forward lattice DFTs run in
+                       the arithmetic that sfft_params.dft selects                            */
+
+/* Arithmetic of the forward lattice DFTs of an FP32 plan with refinement (or the LSQ combine).
+ * The refinement's residual spectrum is ghat - C, C the bucket sums of the detected coefficients
+ * (eq. 2.3), so its accuracy is that of ghat:
+ *   SFFT_DFT_DF64  double-float (float pairs, ~48 bits): coefficients agree with an FP64
+ *                  reconstruction to ~1e-12 relative (the default)
+ *   SFFT_DFT_FP32  float with FP32 accumulation: each bucket carries the transform's rounding,
+ *                  ~1e-7 of the spectrum's rms, so a coefficient of magnitude |c| agrees to
+ *                  ~1e-7 rms/|c| (1e-6 class for complex-Gaussian coefficients); ~3x cheaper
+ * FP64 plans and FP32 plans without refinement ignore it (their transforms run in the plan's
+ * precision).                                                                                 */
+#define SFFT_DFT_DF64 0
+#define SFFT_DFT_FP32 1
 
 #define SFFT_L_COR26 0    /* L = min odd n >= 4c/((c-2)ln(c-1)) (ln|Gamma| - ln delta), Cor 2.6 */
 #define SFFT_L_EQ42 1     /* a quarter of the Cor 2.6 bound, rounded up to odd, eq. (4.2)       */
@@ -82,6 +95,7 @@ typedef struct sfft_params {
     int64_t detect_cap; /* capacity for |Itilde|; 0 = max(4 s + 4096, 16384)                  */
     int cand_type;    /* element type of the candidate rows: SFFT_CAND_I32 (default) or _I8     */
     int cand_ld;      /* row stride in elements: 0 = d (I32); I8 rows: a multiple of 4, >= d   */
+    int dft;          /* SFFT_DFT_*: forward DFT arithmetic of FP32 plans with refinement      */
 } sfft_params;
 
 #define SFFT_CAND_I32 0 /* int32 rows of d entries                                              */

@@ -35,6 +35,7 @@ class SfftError(RuntimeError):
 
 
 CAND_I32, CAND_I8 = 0, 1
+DFT_DF64, DFT_FP32 = 0, 1
 
 
 class Params(C.Structure):
@@ -42,7 +43,7 @@ class Params(C.Structure):
                 ("tau_rel", C.c_double), ("theta_abs", C.c_double), ("theta_rel", C.c_double),
                 ("s_tilde", C.c_int64), ("precision", C.c_int), ("refine", C.c_int), ("L_rule", C.c_int),
                 ("combine", C.c_int), ("seed", C.c_uint64), ("detect_cap", C.c_int64), ("cand_type", C.c_int),
-                ("cand_ld", C.c_int)]
+                ("cand_ld", C.c_int), ("dft", C.c_int)]
 
 
 class Diag(C.Structure):

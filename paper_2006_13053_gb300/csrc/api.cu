@@ -183,10 +183,12 @@ int Plan::buf_mode(int tprec) const {
     return even && blue_smem_bytes(maxN / 2, e) <= blue_smem_limit() ? 2 : 0;
 }
 
-// FP32 plans with refinement run the forward transform in double-float: the refinement's
-// residual spectrum is then r_hat = ghat - C (eq. 2.3), accurate to ~1e-14 without transforms.
+// FP32 plans with refinement run the forward transform in double-float unless the caller asks
+// for FP32: the refinement's residual spectrum is r_hat = ghat - C (eq. 2.3), as accurate as
+// ghat, without further transforms.
 int Plan::fwd_prec() const {
-    return prec == SFFT_FP32 && (p.refine || p.combine == SFFT_COMBINE_LSQ) ? 2 : prec;
+    if (prec == SFFT_FP32 && (p.refine || p.combine == SFFT_COMBINE_LSQ)) return p.dft == SFFT_DFT_FP32 ? 1 : 2;
+    return prec;
 }
 
 int Plan::build_jobs() {
@@ -245,6 +247,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     SFFT_CHECK(p.combine == SFFT_COMBINE_MEDIAN || p.combine == SFFT_COMBINE_HYBRID || p.combine == SFFT_COMBINE_LSQ,
                SFFT_EINVAL, "bad combine mode");
     SFFT_CHECK(p.cand_type == SFFT_CAND_I32 || p.cand_type == SFFT_CAND_I8, SFFT_EINVAL, "bad cand_type");
+    SFFT_CHECK(p.dft == SFFT_DFT_DF64 || p.dft == SFFT_DFT_FP32, SFFT_EINVAL, "bad dft arithmetic %d", p.dft);
     if (p.cand_type == SFFT_CAND_I32) {
         SFFT_CHECK(p.cand_ld == 0 || p.cand_ld == d, SFFT_EINVAL, "int32 candidate rows are dense (cand_ld 0 or d)");
         p.cand_ld = d;

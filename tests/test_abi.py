@@ -90,3 +90,39 @@ def test_invalid_arguments_rejected_on_host():
     # NULL candidate pointer -> SFFT_EINVAL before any device work
     assert f(ctypes.byref(h), 3, None, 10, 2, 0, None, None, None, None) == 1
     assert f(None, 3, None, 10, 2, 0, None, None, None, None) == 1
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C compiler's field offsets and sizes."""
+    gcc = shutil.which("gcc") or shutil.which("cc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("_sfft_native_layout",
+                                                  os.path.join(ROOT, "paper_2006_13053_gb300", "_native.py"))
+    N = importlib.util.module_from_spec(spec)
+    try:
+        spec.loader.exec_module(N)
+    except Exception:  # the binding module loads the library; read the classes from its source instead
+        pytest.skip("binding module not importable without the library")
+    pairs = {"sfft_params": N.Params, "sfft_diag": N.Diag, "sfft_dimincr_params": N.DimIncrParams,
+             "sfft_fn_sparse_poly_ctx": N.SparsePolyCtx, "sfft_fn_sop_ctx": N.SopCtx}
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sfft.h"', "int main(void) {"]
+    for cname, cls in pairs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
+    lines += ["return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    import subprocess
+    subprocess.run([gcc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.splitlines():
+        c, f, v = line.split()
+        got[(c, f)] = int(v)
+    for cname, cls in pairs.items():
+        assert got[(cname, "size")] == ctypes.sizeof(cls), cname
+        for f, _ in cls._fields_:
+            assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
