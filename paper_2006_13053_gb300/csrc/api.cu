@@ -402,7 +402,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     std::vector<LatDesc> lats(L);
     for (int l = 0; l < L; ++l) {
         lats[l] = LatDesc{0, l, (int)P->M[l], (int)P->tabs[l]->N, P->soff[l], P->boff[l], 0,
-                          (const double*)P->tabs[l]->dft64};
+                          (const double*)P->tabs[l]->dft64, P->tabs[l]->dftdf};
     }
     SFFT_TRY(P->alloc((void**)&P->d_lats, sizeof(LatDesc) * L));
     SFFT_CU(cudaMemcpy(P->d_lats, lats.data(), sizeof(LatDesc) * L, cudaMemcpyHostToDevice));
@@ -509,7 +509,7 @@ int tc_grid(size_t smem, int64_t tiles, int count) {
 
 int Plan::hash_grid() const {
     int per_sm = std::max<int>(1, std::min<int>(8, (int)((228 * 1024) / (hash_smem + 1024))));
-    int64_t tiles = (n + 511) / 512;
+    const int64_t tile = hash_tile(packed), tiles = (n + tile - 1) / tile;
     return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)152 * per_sm));
 }
 

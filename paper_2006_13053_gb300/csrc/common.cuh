@@ -138,6 +138,7 @@ struct FftTables {
     // double-float copies (hi, lo words of each double entry)
     void* twdf = nullptr;     // [N]
     void* chirpdf = nullptr;  // [M]
+    void* dftdf = nullptr;    // [M] exp(-2 pi i m / M), single-bucket re-tests of FP32 samples
     void* filtdf[2] = {nullptr, nullptr};
     int refs = 0;
     int device = -1;
@@ -288,6 +289,7 @@ struct LatDesc {
     int32_t boff;
     int pad;
     const double* dft64;       // [M] exp(-2 pi i m / M)
+    const void* dftdf;         // [M] the same roots as double-float pairs (cplx<df64>)
 };
 
 // error flag bits (InstDesc::cnt[3])

@@ -136,7 +136,7 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
         A.lsq |= P->p.combine == SFFT_COMBINE_LSQ;
         for (int l = 0; l < P->L; ++l)
             lats.push_back(LatDesc{b, l, (int)P->M[l], (int)P->tabs[l]->N, P->soff[l], P->boff[l], 0,
-                                   (const double*)P->tabs[l]->dft64});
+                                   (const double*)P->tabs[l]->dft64, P->tabs[l]->dftdf});
         const int sf = P->buf_mode(P->fwd_prec()), sp = P->buf_mode(P->prec);
         for (int l = 0; l < P->L; ++l) {
             BlueJob f = P->jobs_fwd[l], s = P->jobs_samp[l];
@@ -192,7 +192,8 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
         h.tc_tiles = 0;
         while (e < n && B->plans[e]->d == h.d && B->plans[e]->packed == Pb->packed && B->plans[e]->hgroups.size() == 1) {
             h.smem = std::max(h.smem, B->plans[e]->hash_smem);
-            tiles = std::max<int64_t>(tiles, (B->plans[e]->n + 511) / 512);
+            const int64_t tile = hash_tile(Pb->packed);
+            tiles = std::max<int64_t>(tiles, (B->plans[e]->n + tile - 1) / tile);
             h.tc_ok = h.tc_ok && B->plans[e]->hash_tc;
             h.tc_smem = std::max(h.tc_smem, B->plans[e]->tc_smem);
             h.tc_tiles = std::max<int64_t>(h.tc_tiles, (B->plans[e]->n + 127) / 128);

@@ -177,6 +177,7 @@ int tables_acquire(int64_t M, FftTables** out) {
     if (rc == SFFT_OK) rc = upload64(&t->dft64, dft);
     if (rc == SFFT_OK) rc = upload_df(&t->twdf, tw);
     if (rc == SFFT_OK) rc = upload_df(&t->chirpdf, chirp);
+    if (rc == SFFT_OK) rc = upload_df(&t->dftdf, dft);
     if (rc != SFFT_OK) {
         t->refs = 1;
         tables_release(t);
@@ -195,7 +196,7 @@ void tables_release(FftTables* t) {
     g_tabs.erase(std::make_pair(t->device, t->M));
     cudaFree(t->tw64); cudaFree(t->tw32); cudaFree(t->chirp64); cudaFree(t->chirp32); cudaFree(t->dft64);
     for (int d = 0; d < 2; ++d) { cudaFree(t->filt64[d]); cudaFree(t->filt32[d]); cudaFree(t->filtdf[d]); }
-    cudaFree(t->twa32); cudaFree(t->twb32); cudaFree(t->twdf); cudaFree(t->chirpdf);
+    cudaFree(t->twa32); cudaFree(t->twb32); cudaFree(t->twdf); cudaFree(t->chirpdf); cudaFree(t->dftdf);
     delete t;
 }
 

@@ -17,16 +17,52 @@ namespace sfft {
 // ================================================================== zero test (per lattice)
 // One CTA per lattice.  The working-precision |ghat| decides every bucket except those within
 // `band` of tau (and the maximum, which sets tau when tau_rel > 0): those are recomputed by a
-// direct FP64 DFT sum of the samples with exact integer phase (j h mod M).
+// direct DFT sum of the samples with exact integer phase (j h mod M).
+//
+// The phase of thread t's terms j = t, t + B, t + 2B, ... steps by B h mod M.  FP64 samples sum in
+// FP64.  FP32 samples sum in double-float on the FP32 pipes (on this GPU FP64 runs at a small
+// fraction of the FP32 rate): each term x_j w, w = w_hi + w_lo the root as a float pair, enters as
+// float products split exactly (x w_hi = p + e by one FMA) plus x w_lo, accumulated by two-sums
+// into a (hi, lo) pair; relative error ~2^-46 of sum |x_j|, the accuracy class of the FP64 sum.
+__device__ __forceinline__ void df_acc(float& h, float& l, float a, df64 w) {
+    const float p = a * w.hi;
+    float e = fmaf(a, w.hi, -p);
+    e = fmaf(a, w.lo, e);
+    const float s = h + p, bb = s - h;
+    l += ((h - (s - bb)) + (p - bb)) + e;
+    h = s;
+}
+
 template <class TS>
-__device__ c64 bucket_dft64(const cplx<TS>* __restrict__ x, int M, int h, const c64* __restrict__ tab, double* red) {
+__device__ c64 bucket_dft(const cplx<TS>* __restrict__ x, int M, int h, const c64* __restrict__ tab,
+                          const cplx<df64>* __restrict__ tabdf, double* red) {
+    const unsigned B = blockDim.x, uM = (unsigned)M;
+    unsigned ph = (unsigned)(((int64_t)threadIdx.x * h) % M);
+    const unsigned inc = (unsigned)(((int64_t)B * h) % M);
     double re = 0, im = 0;
-    for (int j = threadIdx.x; j < M; j += blockDim.x) {
-        int64_t ph = ((int64_t)j * h) % M;
-        c64 w = tab[ph];
-        c64 v = cvt<double>(x[j]);
-        re += v.x * w.x - v.y * w.y;
-        im += v.x * w.y + v.y * w.x;
+    if constexpr (sizeof(TS) == 4) {
+        float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
+        for (int j = threadIdx.x; j < M; j += B) {
+            const cplx<df64> w = tabdf[ph];
+            const c32 v = x[j];
+            df_acc(rh, rl, v.x, w.x);
+            df_acc(rh, rl, -v.y, w.y);
+            df_acc(ih, il, v.x, w.y);
+            df_acc(ih, il, v.y, w.x);
+            ph += inc;
+            ph = min(ph, ph - uM);  // ph + inc < 2M: one conditional subtraction
+        }
+        re = (double)rh + (double)rl;
+        im = (double)ih + (double)il;
+    } else {
+        for (int j = threadIdx.x; j < M; j += B) {
+            const c64 w = tab[ph];
+            const c64 v = cvt<double>(x[j]);
+            re += v.x * w.x - v.y * w.y;
+            im += v.x * w.y + v.y * w.x;
+            ph += inc;
+            ph = min(ph, ph - uM);
+        }
     }
     // block sums of re, im
     for (int o = 16; o > 0; o >>= 1) {
@@ -86,6 +122,7 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
     c32* glo = I.ghat_lo ? I.ghat_lo + D.soff : nullptr;
     const cplx<TS>* x = reinterpret_cast<const cplx<TS>*>(I.samples) + D.soff;
     const c64* tab = reinterpret_cast<const c64*>(D.dft64);
+    const cplx<df64>* tabdf = reinterpret_cast<const cplx<df64>*>(D.dftdf);
     // FP64 scalars are formed by one thread and shared: on this GPU a warp-wide FP64 instruction
     // costs as much as dozens of FP32 ones
     __shared__ double s_band, s_tlo, s_thi;
@@ -137,7 +174,7 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
             if (threadIdx.x == 0) s_max64 = m;
         } else {
             for (int i = 0; i < nc; ++i) {
-                c64 v = bucket_dft64(x, M, glist[i], tab, red);
+                c64 v = bucket_dft(x, M, glist[i], tab, tabdf, red);
                 if (threadIdx.x == 0) {
                     s_max64 = fmax(s_max64, sqrt(abs2(v)));
                     store(glist[i], v);
@@ -194,7 +231,7 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
     if (gcount > kGuardCap && threadIdx.x == 0) atomicOr((unsigned long long*)&I.cnt[3], (unsigned long long)ERR_GUARD_CAP);
     for (int i = 0; i < nc; ++i) {
         int h = glist[i];
-        c64 v = bucket_dft64(x, M, h, tab, red);
+        c64 v = bucket_dft(x, M, h, tab, tabdf, red);
         if (threadIdx.x == 0) {
             double a = sqrt(abs2(v));
             uint32_t bit = 1u << (h & 31);
@@ -541,12 +578,14 @@ __global__ void k_det_hashes(const InstDesc* __restrict__ insts) {
         const int32_t* k32 = reinterpret_cast<const int32_t*>(I.cand) + row;
         const int8_t* k8 = reinterpret_cast<const int8_t*>(I.cand) + row;
         for (int l = lane; l < L; l += 32) {
+            // the plan bounds |k.z| so that the offset sum fits 32 bits: the hash kernel's exact
+            // Barrett reduction (q = umulhi(x, floor(2^32/M)) is at most one short)
             const int32_t* zl = I.z + l * d;
-            int64_t x = 0;
-            for (int t = 0; t < d; ++t) x += (int64_t)(I.cand_i8 ? (int)__ldg(k8 + t) : __ldg(k32 + t)) * zl[t];
-            int64_t M = I.Ml[l];
-            int64_t r = x % M;
-            if (r < 0) r += M;
+            uint32_t xp = I.offk[l];  // unsigned wrap-around: the sum mod 2^32, in [0, 2^32)
+            for (int t = 0; t < d; ++t) xp += (uint32_t)((I.cand_i8 ? (int)__ldg(k8 + t) : __ldg(k32 + t)) * zl[t]);
+            const uint32_t M = (uint32_t)I.Ml[l];
+            uint32_t r = xp - __umulhi(xp, I.mu[l]) * M;
+            r = min(r, r - M);
             I.H[q * L + l] = (int32_t)r;
         }
     }
@@ -917,7 +956,6 @@ __global__ void k_scatter_coef(const InstDesc* __restrict__ insts) {
 // ================================================================== Algorithm 4 selection
 constexpr int kSelThreads = 1024;
 
-__device__ __forceinline__ uint64_t mod_key(c64 c) { return (uint64_t)__double_as_longlong(hypot(c.x, c.y)); }
 
 __device__ int64_t block_sum64(int64_t v, int64_t* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -961,16 +999,31 @@ __device__ int block_excl_scan(int f, int* sh, int* total) {
     return pre;
 }
 
+// |c| of the first kSelCache coefficients is computed once (FP64 hypot is costly here) and kept
+// in shared memory; beyond that it is recomputed in each pass.
+constexpr int kSelCache = 4096;
+
 __global__ void __launch_bounds__(kSelThreads) k_select(InstDesc* __restrict__ insts) {
     __shared__ int64_t sh64[33];
     __shared__ int shi[33];
     __shared__ unsigned int hist[256];
     __shared__ double smax[32];
+    __shared__ double mag[kSelCache];
     InstDesc& I = insts[blockIdx.x];
     const int64_t nd = min(I.cnt[0], I.cap);
+    auto absc = [&](int64_t q) -> double {
+        if (q < kSelCache) return mag[q];
+        const c64 c = I.coef[q];
+        return hypot(c.x, c.y);
+    };
+    for (int64_t q = threadIdx.x; q < min(nd, (int64_t)kSelCache); q += blockDim.x) {
+        const c64 c = I.coef[q];
+        mag[q] = hypot(c.x, c.y);
+    }
+    __syncthreads();
     // theta = max(theta_abs, theta_rel * max |c|)
     double mx = 0;
-    for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) mx = fmax(mx, hypot(I.coef[q].x, I.coef[q].y));
+    for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) mx = fmax(mx, absc(q));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if ((threadIdx.x & 31) == 0) smax[threadIdx.x >> 5] = mx;
     __syncthreads();
@@ -984,7 +1037,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(InstDesc* __restrict__ i
     __syncthreads();
     // kept set and its size
     int64_t kept = 0;
-    for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) kept += hypot(I.coef[q].x, I.coef[q].y) >= theta;
+    for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) kept += absc(q) >= theta;
     kept = block_sum64(kept, sh64);
     int64_t want = (I.s_tilde > 0 && I.s_tilde < kept) ? I.s_tilde : kept;
     // radix select of the want-th largest key among kept items (only if truncating)
@@ -996,8 +1049,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(InstDesc* __restrict__ i
             for (int i = threadIdx.x; i < 256; i += blockDim.x) hist[i] = 0;
             __syncthreads();
             for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) {
-                c64 c = I.coef[q];
-                double a = hypot(c.x, c.y);
+                const double a = absc(q);
                 uint64_t key = (uint64_t)__double_as_longlong(a);
                 if (a >= theta && (key & mask) == prefix) atomicAdd(&hist[(key >> (8 * p)) & 255u], 1u);
             }
@@ -1028,7 +1080,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(InstDesc* __restrict__ i
         c64 c = {0, 0};
         if (q < nd) {
             c = I.coef[q];
-            double a = hypot(c.x, c.y);
+            const double a = absc(q);
             uint64_t key = (uint64_t)__double_as_longlong(a);
             if (a >= theta) {
                 if (!trunc || key > prefix) sel = 1;
@@ -1221,6 +1273,8 @@ static int launch_hash_d(const InstDesc* di, int ninst, int gx, size_t smem, int
     }
     return launch_check("k_hash_count");
 }
+
+int64_t hash_tile(bool packed) { return (int64_t)kHashThreads * (packed ? kCPT2 : kCPT); }
 
 size_t hash_smem_bytes(int d, int L, int64_t nwords, bool packed) {
     if (!packed) return sizeof(uint32_t) * (size_t)nwords + sizeof(int32_t) * (size_t)L * (d + 4);
