@@ -363,7 +363,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     SFFT_TRY(P->alloc((void**)&P->stats, sizeof(LatStats) * L));
     SFFT_TRY(P->alloc((void**)&P->detbits, sizeof(uint32_t) * ((n + 31) / 32)));
     SFFT_TRY(P->alloc((void**)&P->det, sizeof(int64_t) * cap));
-    SFFT_TRY(P->alloc((void**)&P->cnt, sizeof(int64_t) * 8));
+    SFFT_TRY(P->alloc((void**)&P->cnt, sizeof(int64_t) * kCntWords));
     SFFT_TRY(P->alloc((void**)&P->coef, sizeof(c64) * cap));
     SFFT_TRY(P->alloc((void**)&P->H, sizeof(int32_t) * cap * L));
     SFFT_TRY(P->alloc((void**)&P->sel, 2 * cap));
@@ -487,12 +487,14 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
         SFFT_TRY(launch_lsq(a.d_inst, ni, a.prec, st));
     }
     if (a.refine) {
+        // FP32 transforms: float buckets C (their rounding is far below the transform's error)
+        const bool f32 = a.prec == 1 && a.fwd_prec == 1;
         SFFT_TRY(mark(a, ST_SCATTER, st));
-        SFFT_TRY(launch_clear(a.d_inst, ni, 0, 0, 1, st));
-        SFFT_TRY(launch_scatter_coef(a.d_inst, ni, st));
+        SFFT_TRY(launch_clear(a.d_inst, ni, 0, 0, f32 ? 2 : 1, st));
+        SFFT_TRY(launch_scatter_coef(a.d_inst, ni, f32, st));
         // residual spectrum r_hat = ghat - C at the buckets of Itilde (eq. 2.3), median update
         SFFT_TRY(mark(a, ST_DELTA, st));
-        SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, 1, st));
+        SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, f32 ? 2 : 1, st));
     }
     // Algorithm 4: theta filter and top-s_tilde, ascending output
     SFFT_TRY(mark(a, ST_SELECT, st));

@@ -253,7 +253,7 @@ struct InstDesc {
     uint32_t* detbits;         // [ceil(n/32)]
     uint8_t* cnt8;             // [n] partial counts between lattice groups (plans with several groups)
     int64_t* det;              // [cap] detected indices (ascending)
-    int64_t* cnt;              // [8] counters: 0 |Itilde|, 1 n_out, 2 n_guard, 3 error flags
+    int64_t* cnt;              // [kCntWords] counters: 0 |Itilde|, 1 n_out, 2 n_guard, 3 error flags
     c64* coef;                 // [cap]
     int32_t* H;                // [cap, L]
     uint8_t* sel;              // [cap, 2] lattice of the Re / Im median
@@ -291,6 +291,17 @@ struct LatDesc {
     const double* dft64;       // [M] exp(-2 pi i m / M)
     const void* dftdf;         // [M] the same roots as double-float pairs (cplx<df64>)
 };
+
+// The detection bits of an instance are compacted in kCompactChunks chunks of whole words; the
+// hash kernels count the detections of chunk c in cnt[8 + c] so that each chunk's compaction
+// starts from the sum of the counts before it.
+constexpr int kCompactChunks = 32;
+constexpr int kCntWords = 8 + kCompactChunks;
+__device__ __forceinline__ void mark_detected(const InstDesc& I, int64_t idx) {
+    atomicOr(&I.detbits[idx >> 5], 1u << (idx & 31));
+    const int64_t W = (I.n + 31) >> 5, cw = (W + kCompactChunks - 1) / kCompactChunks;
+    atomicAdd(reinterpret_cast<unsigned long long*>(&I.cnt[8 + (idx >> 5) / cw]), 1ull);
+}
 
 // error flag bits (InstDesc::cnt[3])
 enum : int64_t { ERR_DET_CAP = 1, ERR_GUARD_CAP = 2, ERR_OUT_CAP = 4, ERR_TC_TIMEOUT = 8 };

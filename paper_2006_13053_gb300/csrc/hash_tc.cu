@@ -208,7 +208,7 @@ __global__ void __launch_bounds__(kTcThreads * kTcGroups) k_hash_count_tc(const 
             const int rem = L - min(L, c0 + 16);
             if (!__any_sync(0xffffffffu, idx < n && cnt + rem >= need)) break;
         }
-        if (idx < n && cnt >= need) atomicOr(&I.detbits[idx >> 5], 1u << (idx & 31));
+        if (idx < n && cnt >= need) mark_detected(I, idx);
         asm volatile("tcgen05.fence::before_thread_sync;");
         group_sync(g);  // tensor memory read and A free before this group's next MMA
     }

@@ -201,30 +201,41 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
     uint32_t* words = I.nzbits + D.boff;
     const int nw = (M + 31) >> 5;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
-    for (int wi = warp; wi < nw; wi += nwarp) {
-        int h = wi * 32 + lane;
-        bool nz = false;
-        if (h < M) {
-            cplx<TS> v = g[h];
-            TS a2 = v.x * v.x + v.y * v.y;
-            nz = a2 > hi2;
-            if (!nz && a2 >= lo2) {
-                // uncertain in the working precision: the double-float value decides outside
-                // the transform's error band, the FP64 re-test below inside it
-                bool open = true;
-                if (glo) {
-                    const double a = sqrt(abs2(full(h)));
-                    if (a > thi) { nz = true; open = false; }
-                    else if (a < tlo) open = false;
-                }
-                if (open) {
-                    int p = atomicAdd(&gcount, 1);
-                    if (p < kGuardCap) glist[p] = h;
+    // kZtUnroll words per warp and iteration, their loads issued together
+    constexpr int kZtUnroll = 4;
+    for (int w0 = warp * kZtUnroll; w0 < nw; w0 += nwarp * kZtUnroll) {
+        cplx<TS> v[kZtUnroll];
+#pragma unroll
+        for (int u = 0; u < kZtUnroll; ++u) {
+            const int h = (w0 + u) * 32 + lane;
+            v[u] = h < M ? g[h] : cplx<TS>{(TS)0, (TS)0};
+        }
+#pragma unroll
+        for (int u = 0; u < kZtUnroll; ++u) {
+            const int wi = w0 + u, h = wi * 32 + lane;
+            if (wi >= nw) break;
+            bool nz = false;
+            if (h < M) {
+                TS a2 = v[u].x * v[u].x + v[u].y * v[u].y;
+                nz = a2 > hi2;
+                if (!nz && a2 >= lo2) {
+                    // uncertain in the working precision: the double-float value decides outside
+                    // the transform's error band, the direct re-test below inside it
+                    bool open = true;
+                    if (glo) {
+                        const double a = sqrt(abs2(full(h)));
+                        if (a > thi) { nz = true; open = false; }
+                        else if (a < tlo) open = false;
+                    }
+                    if (open) {
+                        int p = atomicAdd(&gcount, 1);
+                        if (p < kGuardCap) glist[p] = h;
+                    }
                 }
             }
+            uint32_t b = __ballot_sync(0xffffffffu, nz);
+            if (lane == 0) words[wi] = b;
         }
-        uint32_t b = __ballot_sync(0xffffffffu, nz);
-        if (lane == 0) words[wi] = b;
     }
     __syncthreads();
     int nc = min(gcount, kGuardCap);
@@ -342,7 +353,7 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __r
         for (int c = 0; c < kCPT; ++c) {
             if (idx[c] < n) {
                 if (mode & 2) {
-                    if (cnt[c] >= need) atomicOr(&I.detbits[idx[c] >> 5], 1u << (idx[c] & 31));
+                    if (cnt[c] >= need) mark_detected(I, idx[c]);
                     if (dcounts) dcounts[idx[c]] = (uint8_t)cnt[c];
                 } else {
                     I.cnt8[idx[c]] = (uint8_t)cnt[c];
@@ -485,7 +496,7 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
         for (int c = 0; c < kCPT2; ++c) {
             if (idx[c] < n) {
                 if (mode & 2) {
-                    if (cnt[c] >= need) atomicOr(&I.detbits[idx[c] >> 5], 1u << (idx[c] & 31));
+                    if (cnt[c] >= need) mark_detected(I, idx[c]);
                     if constexpr (DIAG) {
                         if (I.dcounts) I.dcounts[idx[c]] = (uint8_t)cnt[c];
                     }
@@ -499,22 +510,10 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
 
 // ================================================================== compaction (ascending Itilde)
 // Ascending Itilde from the detection bits.  Each instance's ceil(n/32) bit words are split into
-// kCompactChunks contiguous chunks, one CTA each.  A CTA counts the set bits of all chunks before
-// its own (a block reduction over L2-resident words), scans its own chunk and writes its indices;
-// the last chunk's CTA records |Itilde|.  One launch, no inter-CTA waits.
+// kCompactChunks contiguous chunks, one CTA each.  A CTA starts at the sum of the detection counts
+// of the chunks before its own (kept by the hash kernels in cnt[8 + c]), scans its own chunk and
+// writes its indices; the last chunk's CTA records |Itilde|.  One launch, no inter-CTA waits.
 constexpr int kCompactThreads = 256;
-constexpr int kCompactChunks = 32;
-
-__device__ int64_t block_sum_i64(int64_t v, int64_t* sh) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
-    __syncthreads();
-    int64_t r = 0;
-    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i];
-    __syncthreads();
-    return r;
-}
 
 __global__ void __launch_bounds__(kCompactThreads) k_compact(InstDesc* __restrict__ insts) {
     __shared__ int64_t wsum[32];
@@ -523,10 +522,9 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(InstDesc* __restric
     const int64_t chunk = (W + gridDim.x - 1) / gridDim.x;
     const int64_t c0 = min(W, (int64_t)blockIdx.x * chunk), c1 = min(W, c0 + chunk);
     const uint32_t* bits = I.detbits;
-    // set bits before this chunk
-    int64_t pre = 0;
-    for (int64_t w = threadIdx.x; w < c0; w += blockDim.x) pre += __popc(bits[w]);
-    const int64_t base = block_sum_i64(pre, wsum);
+    // set bits before this chunk: the hash kernels' per-chunk detection counts
+    int64_t base = 0;
+    for (int b = 0; b < (int)blockIdx.x; ++b) base += I.cnt[8 + b];
     // this chunk: contiguous words per thread, block exclusive scan of their counts
     const int64_t per = (c1 - c0 + blockDim.x - 1) / blockDim.x;
     const int64_t w0 = min(c1, c0 + threadIdx.x * per), w1 = min(c1, w0 + per);
@@ -663,6 +661,46 @@ template <class T> __device__ __forceinline__ T pick(T a, T b, int l) {
     return l < 32 ? x : y;
 }
 
+// The same median for float values: a bitonic sort of 32-bit order keys (half the shuffles and
+// compares of the packed 64-bit keys), then the lattice among the keys equal to the median value
+// at rank mid - #(smaller keys) in lattice order, which is the element the packed (value,
+// lattice) order puts at position mid.
+__device__ __forceinline__ int warp_median32(int ka, int kb, int L, int lane) {
+    const bool va = lane < L, vb = lane + 32 < L;
+    int k0 = va ? ka : INT_MAX, k1 = vb ? kb : INT_MAX;
+#pragma unroll
+    for (int size = 2; size <= 64; size <<= 1) {
+#pragma unroll
+        for (int d = size >> 1; d > 0; d >>= 1) {
+            if (d == 1) {
+                const bool up = ((2 * lane) & size) == 0;
+                if (up == (k1 < k0)) {
+                    const int t = k0; k0 = k1; k1 = t;
+                }
+            } else {
+                const int m = d >> 1;
+                const int p0 = __shfl_xor_sync(0xffffffffu, k0, m), p1 = __shfl_xor_sync(0xffffffffu, k1, m);
+                const bool up = ((2 * lane) & size) == 0, low = ((2 * lane) & d) == 0;
+                const bool want_min = up == low;
+                if (want_min == (p0 < k0)) k0 = p0;
+                if (want_min == (p1 < k1)) k1 = p1;
+            }
+        }
+    }
+    const int mid = (L - 1) >> 1;
+    const int vm = __shfl_sync(0xffffffffu, (mid & 1) ? k1 : k0, mid >> 1);
+    const int less = __popc(__ballot_sync(0xffffffffu, va && ka < vm)) + __popc(__ballot_sync(0xffffffffu, vb && kb < vm));
+    unsigned ea = __ballot_sync(0xffffffffu, va && ka == vm), eb = __ballot_sync(0xffffffffu, vb && kb == vm);
+    int r = mid - less;  // rank among the ties, lattice order
+    const int na = __popc(ea);
+    if (r < na) {
+        for (; r > 0; --r) ea &= ea - 1;
+        return __ffs(ea) - 1;
+    }
+    for (r -= na; r > 0; --r) eb &= eb - 1;
+    return 32 + __ffs(eb) - 1;
+}
+
 // Median combine (eq. 2.6) or the Remark 2.8 hybrid combine on the detected set: coef = combine(ghat).
 // The ranking uses integer keys of the buckets (float, double-float pair or double); only the
 // selected median is converted to double.
@@ -691,10 +729,16 @@ __global__ void k_combine(const InstDesc* __restrict__ insts) {
             if (glo) lb = glo[b];
             if (hybrid) fb = I.coll[b] == 1;
         }
-        const int lre = (int)(warp_median_packed(pack_key(val_key<TS>(ha.x, la.x), lane),
-                                                 pack_key(val_key<TS>(hb.x, lb.x), lane + 32), L, lane) & 63);
-        const int lim = (int)(warp_median_packed(pack_key(val_key<TS>(ha.y, la.y), lane),
-                                                 pack_key(val_key<TS>(hb.y, lb.y), lane + 32), L, lane) & 63);
+        int lre, lim;
+        if (sizeof(TS) == 4 && !glo) {  // plain float buckets: 32-bit keys
+            lre = warp_median32(ord32((float)ha.x), ord32((float)hb.x), L, lane);
+            lim = warp_median32(ord32((float)ha.y), ord32((float)hb.y), L, lane);
+        } else {
+            lre = (int)(warp_median_packed(pack_key(val_key<TS>(ha.x, la.x), lane),
+                                           pack_key(val_key<TS>(hb.x, lb.x), lane + 32), L, lane) & 63);
+            lim = (int)(warp_median_packed(pack_key(val_key<TS>(ha.y, la.y), lane),
+                                           pack_key(val_key<TS>(hb.y, lb.y), lane + 32), L, lane) & 63);
+        }
         c64 out = {(double)pick(ha.x, hb.x, lre), (double)pick(ha.y, hb.y, lim)};
         if (glo) {
             out.x += (double)pick(la.x, lb.x, lre);
@@ -723,7 +767,9 @@ __global__ void k_combine(const InstDesc* __restrict__ insts) {
 // r_hat_h = ghat_h - C_h (aliasing formula, eq. 2.3), C_h = sum of c_k over the detected k with
 // h_kl = h.  c_k += median_l Re r_hat + i median_l Im r_hat at h_kl, in FP64; ghat is the forward
 // transform (FP64, or a double-float pair hi + lo for FP32 plans with refinement).
-template <class TS>
+// FP32 buckets (F32: FP32 transforms, C accumulated in float): r_hat in float, whose rounding is
+// far below the transform's own error, and 32-bit median keys; the update itself stays FP64.
+template <class TS, bool F32>
 __global__ void k_refine_update(const InstDesc* __restrict__ insts) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nd = min(I.cnt[0], I.cap);
@@ -731,6 +777,28 @@ __global__ void k_refine_update(const InstDesc* __restrict__ insts) {
     const int lane = threadIdx.x & 31, L = I.L;
     const cplx<TS>* g = reinterpret_cast<const cplx<TS>*>(I.ghat);
     const c32* glo = I.ghat_lo;
+    if constexpr (F32) {
+        const c32* g32 = reinterpret_cast<const c32*>(I.ghat);
+        const c32* C32 = reinterpret_cast<const c32*>(I.C);
+        for (int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); q < nd; q += (int64_t)gridDim.x * warps) {
+            auto rhat = [&](int l) -> c32 {
+                const int64_t b = I.soff[l] + I.H[q * L + l];
+                const c32 v = g32[b], c = C32[b];
+                return c32{v.x - c.x, v.y - c.y};
+            };
+            c32 va = {0.f, 0.f}, vb = {0.f, 0.f};
+            if (lane < L) va = rhat(lane);
+            if (lane + 32 < L) vb = rhat(lane + 32);
+            const int lre = warp_median32(ord32(va.x), ord32(vb.x), L, lane);
+            const int lim = warp_median32(ord32(va.y), ord32(vb.y), L, lane);
+            const float dre = pick(va.x, vb.x, lre), dim = pick(va.y, vb.y, lim);
+            if (lane == 0) {
+                const c64 c = I.coef[q];
+                I.coef[q] = c64{c.x + (double)dre, c.y + (double)dim};
+            }
+        }
+        return;
+    }
     for (int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); q < nd; q += (int64_t)gridDim.x * warps) {
         auto rhat = [&](int l) -> c64 {
             const int64_t b = I.soff[l] + I.H[q * L + l];
@@ -938,7 +1006,9 @@ __global__ void __launch_bounds__(kLsqThreads) k_lsq_cg(InstDesc* __restrict__ i
     if (threadIdx.x == 0) I.cnt[4] = it;  // iterations taken (diagnostics)
 }
 
-// scatter the detected coefficients into their buckets: C_l[h_kl] += c_k
+// scatter the detected coefficients into their buckets: C_l[h_kl] += c_k (FP64, or float buckets
+// in the first half of the buffer for FP32 transforms)
+template <bool F32>
 __global__ void k_scatter_coef(const InstDesc* __restrict__ insts) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nd = min(I.cnt[0], I.cap);
@@ -948,8 +1018,14 @@ __global__ void k_scatter_coef(const InstDesc* __restrict__ insts) {
         int l = (int)(e - q * L);
         c64 c = I.coef[q];
         const int64_t b = I.soff[l] + I.H[e];
-        atomicAdd(&I.C[b].x, c.x);
-        atomicAdd(&I.C[b].y, c.y);
+        if constexpr (F32) {
+            c32* C32 = reinterpret_cast<c32*>(I.C);
+            atomicAdd(&C32[b].x, (float)c.x);
+            atomicAdd(&C32[b].y, (float)c.y);
+        } else {
+            atomicAdd(&I.C[b].x, c.x);
+            atomicAdd(&I.C[b].y, c.y);
+        }
     }
 }
 
@@ -1208,7 +1284,7 @@ __global__ void k_clear_inst(InstDesc* __restrict__ insts, int clear_det, int cl
     if (clear_C == 2)  // FP32 buckets of the sampler of FP32 plans (first half of the buffer)
         for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < SM; i += stride)
             reinterpret_cast<c32*>(I.C)[i] = c32{0.f, 0.f};
-    if (clear_det && blockIdx.x == 0 && threadIdx.x < 8) I.cnt[threadIdx.x] = 0;
+    if (clear_det && blockIdx.x == 0 && threadIdx.x < kCntWords) I.cnt[threadIdx.x] = 0;
 }
 
 // Copy from pinned host memory (device-accessible through unified addressing) by a kernel on the
@@ -1327,9 +1403,10 @@ int launch_collisions(const InstDesc* di, int ninst, cudaStream_t st) {
 
 int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int mode, cudaStream_t st) {
     const int gx = det_grid(maxdet, ninst);
-    if (mode == 1) {
-        if (prec) k_refine_update<float><<<dim3(gx, ninst), 256, 0, st>>>(di);
-        else k_refine_update<double><<<dim3(gx, ninst), 256, 0, st>>>(di);
+    if (mode == 1 || mode == 2) {  // 2: FP32 buckets
+        if (mode == 2) k_refine_update<float, true><<<dim3(gx, ninst), 256, 0, st>>>(di);
+        else if (prec) k_refine_update<float, false><<<dim3(gx, ninst), 256, 0, st>>>(di);
+        else k_refine_update<double, false><<<dim3(gx, ninst), 256, 0, st>>>(di);
         return launch_check("k_refine_update");
     }
     if (prec) k_combine<float><<<dim3(gx, ninst), 256, 0, st>>>(di);
@@ -1356,8 +1433,9 @@ int launch_lsq(InstDesc* di, int ninst, int prec, cudaStream_t st) {
     return launch_check("k_lsq_cg");
 }
 
-int launch_scatter_coef(const InstDesc* di, int ninst, cudaStream_t st) {
-    k_scatter_coef<<<dim3(152, ninst), 256, 0, st>>>(di);
+int launch_scatter_coef(const InstDesc* di, int ninst, bool f32, cudaStream_t st) {
+    if (f32) k_scatter_coef<true><<<dim3(152, ninst), 256, 0, st>>>(di);
+    else k_scatter_coef<false><<<dim3(152, ninst), 256, 0, st>>>(di);
     return launch_check("k_scatter_coef");
 }
 

@@ -99,7 +99,7 @@ extern "C" int sfft_detect_noalloc(int d, const int32_t* cand, int64_t n_cand, i
     const size_t o_boff = off; off = align256(off + sizeof(int32_t) * L);
     const size_t o_soff = off; off = align256(off + sizeof(int64_t) * (L + 1));
     const size_t o_tau = off;  off = align256(off + sizeof(double) * L);
-    const size_t o_cnt = off;  off = align256(off + sizeof(int64_t) * 8);
+    const size_t o_cnt = off;  off = align256(off + sizeof(int64_t) * kCntWords);
     const size_t o_mnx = off;  off = align256(off + sizeof(int) * 2 * kMaxD);
     const size_t o_nz = off;   off = align256(off + sizeof(uint32_t) * words);
     const size_t o_det = off;  off = align256(off + sizeof(uint32_t) * ((n_cand + 31) / 32));
@@ -172,7 +172,7 @@ extern "C" int sfft_detect_noalloc(int d, const int32_t* cand, int64_t n_cand, i
     SFFT_CU(cudaMemcpyAsync(S + o_soff, so, sizeof(int64_t) * (L + 1), cudaMemcpyHostToDevice, st));
     SFFT_CU(cudaMemcpyAsync(S + o_tau, tau, sizeof(double) * L, cudaMemcpyHostToDevice, st));
     // the array keeps the previous call's contents: clear what must start at zero
-    SFFT_CU(cudaMemsetAsync(S + o_cnt, 0, sizeof(int64_t) * 8, st));
+    SFFT_CU(cudaMemsetAsync(S + o_cnt, 0, sizeof(int64_t) * kCntWords, st));
     SFFT_CU(cudaMemsetAsync(S + o_det, 0, sizeof(uint32_t) * ((n_cand + 31) / 32), st));
     // ---- zero test, count rule, compaction
     k_nz_from_ghat<<<L, 256, 0, st>>>(reinterpret_cast<const c64*>(ghat), dI, reinterpret_cast<const double*>(S + o_tau));
