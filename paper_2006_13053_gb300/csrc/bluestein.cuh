@@ -400,7 +400,7 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
     cplx<T>* rbuf;       // CL: the other CTA's half (distributed shared memory)
     int hN = 0, rank = 0, nrank = 1;
     int N, M, epi;
-    bool inv, first = false, last = false;
+    bool inv, last = false;
     const cplx<TI>* in;
     const cplx<T>* chirp;
     const cplx<T>* filt;
@@ -421,20 +421,67 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
             return buf + e;
         }
     }
-    __device__ __forceinline__ cplx<T> dif_load(int e) {
-        if (!first) return *at(e);
-        if (e >= M) return cplx<T>{kc<T>(0.0), kc<T>(0.0)};
-        const cplx<T> x = load_in<T, TI>(in + e);
-        if (epi == EPI_ANALYZE) ss += scv<R>(abs2(x));
-        const cplx<T> w = ldg(&chirp[e]);
-        return inv ? mulc(x, w) : x * w;
-    }
+    __device__ __forceinline__ cplx<T> dif_load(int e) { return *at(e); }
     __device__ __forceinline__ void dif_store(int e, cplx<T> v) { *at(e) = last ? v * ldg(&filt[e]) : qnorm(v); }
     __device__ __forceinline__ cplx<T> dit_load(int e) { return *at(e); }
-    __device__ __forceinline__ void dit_store(int e, cplx<T> v) {
-        if (!last) { *at(e) = qnorm(v); return; }
-        if (e >= M) return;
-        const cplx<T> w = ldg(&chirp[e]);
+    __device__ __forceinline__ void dit_store(int e, cplx<T> v) { *at(e) = qnorm(v); }
+
+    // Input and output run as phases of their own over elements [e0, e1) of this CTA, in natural
+    // order (coalesced) with kIoUnroll elements per thread whose global loads are issued together:
+    // the passes then only touch shared memory, and the loads' latency is paid once per batch
+    // instead of once per butterfly group.
+    static constexpr int kIoUnroll = 4;
+    // work buffer = x_j chirp_j (conjugate chirp for the inverse) on [0, M), zero on [M, N)
+    __device__ __forceinline__ void load_input(int e0, int e1) {
+        for (int b = e0 + (int)threadIdx.x; b < e1; b += kIoUnroll * (int)blockDim.x) {
+            cplx<TI> xv[kIoUnroll];
+            cplx<T> wv[kIoUnroll];
+#pragma unroll
+            for (int u = 0; u < kIoUnroll; ++u) {
+                const int e = b + u * (int)blockDim.x;
+                if (e < e1 && e < M) {
+                    xv[u] = in[e];
+                    wv[u] = ldg(&chirp[e]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kIoUnroll; ++u) {
+                const int e = b + u * (int)blockDim.x;
+                if (e >= e1) break;
+                cplx<T> v = {kc<T>(0.0), kc<T>(0.0)};
+                if (e < M) {
+                    const cplx<T> x = ccv<T>(xv[u]);
+                    if (epi == EPI_ANALYZE) ss += scv<R>(abs2(x));
+                    v = inv ? mulc(x, wv[u]) : x * wv[u];
+                }
+                *at(e) = v;
+            }
+        }
+    }
+    // outputs j in [e0, e1), e1 <= M: chirp product, scale and the epilogue
+    __device__ __forceinline__ void store_output(int e0, int e1) {
+        const c64* noise = epi == EPI_ADDNOISE ? reinterpret_cast<const c64*>(auxp) : nullptr;
+        for (int b = e0 + (int)threadIdx.x; b < e1; b += kIoUnroll * (int)blockDim.x) {
+            cplx<T> vv[kIoUnroll], wv[kIoUnroll];
+            c64 zv[kIoUnroll];
+#pragma unroll
+            for (int u = 0; u < kIoUnroll; ++u) {
+                const int e = b + u * (int)blockDim.x;
+                if (e < e1) {
+                    vv[u] = *at(e);
+                    wv[u] = ldg(&chirp[e]);
+                    if (noise) zv[u] = noise[e];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kIoUnroll; ++u) {
+                const int e = b + u * (int)blockDim.x;
+                if (e >= e1) break;
+                emit(e, vv[u], wv[u], noise ? &zv[u] : nullptr);
+            }
+        }
+    }
+    __device__ __forceinline__ void emit(int e, cplx<T> v, cplx<T> w, const c64* zp) {
         cplx<T> X = inv ? mulc(v, w) : v * w;
         X = X * sc;
         if (epi == EPI_PLAIN || epi == EPI_ANALYZE) {
@@ -447,16 +494,12 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
             }
             if (epi == EPI_ANALYZE) mx2 = fmax(mx2, scv<R>(abs2(X)));
         } else {  // EPI_ADDNOISE (noise complex double; added in the transform precision)
-            const c64* aux = reinterpret_cast<const c64*>(auxp);
             if constexpr (std::is_same<T, float>::value) {
-                if (aux) {
-                    const c64 z = aux[e];
-                    X = X + c32{(float)z.x, (float)z.y};
-                }
+                if (zp) X = X + c32{(float)zp->x, (float)zp->y};
                 out[e] = ccv<TO>(X);
             } else {
                 c64 r = ccv<double>(X);
-                if (aux) r = r + aux[e];
+                if (zp) r = r + *zp;
                 out[e] = ccv<TO>(r);
             }
         }
@@ -467,9 +510,10 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
 // work buffer in its shared memory.  Only the first DIF pass and the last DIT pass (sub-transform
 // size N) touch the other half; every later pass works on blocks of size N / (first pass radix
 // product), which lie inside one half when that product is even, so a CTA takes the groups of
-// its own blocks.  Cluster barriers follow the first pass, precede the last one and end the
-// transform (no CTA leaves while the other may still read its half); one more barrier at the
-// start makes sure both CTAs run before the first pass writes into the other half.
+// its own blocks.  The input and output phases touch only the CTA's own half.  Cluster barriers
+// follow the input phase (both halves filled, both CTAs running before any remote access), follow
+// the first pass, and come before and after the last one; after that no CTA reads the other's
+// half, so either may leave.
 template <class T, class TI, class TO, bool SMB, bool CL, class TW>
 __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, cplx<T>* rbuf, int rank, const TW& tw,
                                                int sign, int epi, const void* inp, const void* auxp, void* outp,
@@ -501,27 +545,30 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
         }
         __syncthreads();
     };
-    // both CTAs of a cluster must be running before either writes into the other's half
-    if constexpr (CL) cooperative_groups::this_cluster().sync();
-    // ---- DIF passes (the first reads the input, the last applies the filter)
+    // ---- input phase (this CTA's half of the buffer when split over a cluster)
+    const int h0 = CL ? rank * (J.N >> 1) : 0, h1 = CL ? h0 + (J.N >> 1) : J.N;
+    c.load_input(h0, h1);
+    // the first pass reads both halves: both CTAs' inputs must be in place
+    sync(true);
+    // ---- DIF passes (the last applies the filter)
     const int np = J.npass;
     for (int p = 0, Ns = J.N; p < np; ++p) {
         const int r1 = J.pass_r[p] & 15, r2 = J.pass_r[p] >> 4;
-        c.first = p == 0;
         c.last = p == np - 1;
         run_pass<T>(true, r1, r2, c, Ns, tw);
         Ns /= r1 * r2;
         sync(p == 0);
     }
-    // ---- DIT passes in reverse order (the last writes the outputs)
-    c.first = false;
+    // ---- DIT passes in reverse order (the last writes into both halves)
+    c.last = false;
     for (int p = np - 1, Ns = 1; p >= 0; --p) {
         const int r1 = J.pass_r[p] & 15, r2 = J.pass_r[p] >> 4;
         Ns *= r1 * r2;
-        c.last = p == 0;
         run_pass<T>(false, r1, r2, c, Ns, tw);
-        if (p > 0) sync(p == 1);
+        sync(p <= 1);
     }
+    // ---- output phase over this CTA's elements below M
+    c.store_output(h0, min(h1, J.M));
     if (epi == EPI_ANALYZE) {
         double ssd = block_reduce_sum((double)c.ss, red);
         double mx2 = block_reduce_max((double)c.mx2, red);
@@ -541,8 +588,6 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
             S.max_abs = mx;
             S.rms = sqrt(ssd / (double)J.M);
         }
-    } else if constexpr (CL) {
-        cooperative_groups::this_cluster().sync();
     }
 }
 
