@@ -338,14 +338,73 @@ __device__ __forceinline__ void dit_pass(C& c, int Ns, const TW& tw) {
     }
 }
 
+// The last DIF pass, the filter product and the first DIT pass in one: both passes work on the
+// blocks of R1 R2 consecutive elements (sub-transform size Ns = R1 R2, so n2 = 0 and every outer
+// twiddle is 1), so each thread takes a block through the forward R1 R2-point DFT, multiplies by
+// the filter (its loads issued with the block's shared-memory loads) and back through the
+// inverse DFT: one shared-memory round trip and one barrier fewer per transform.
+template <int R1, int R2, class T, class C>
+__device__ __forceinline__ void mid_pass(C& c) {
+    constexpr int m1 = R2;  // m2 = 1
+    const int ng = c.N / (R1 * R2);
+    const int g0 = c.rank * (ng >> 1), g1 = (c.nrank == 1 || c.rank == 1) ? ng : (ng >> 1);
+    for (int i = g0 + threadIdx.x; i < g1; i += blockDim.x) {
+        const int base = i * (R1 * R2);
+        cplx<T> v[R2][R1], f[R1][R2];
+#pragma unroll
+        for (int p1 = 0; p1 < R1; ++p1)
+#pragma unroll
+            for (int p2 = 0; p2 < R2; ++p2) f[p1][p2] = ldg(&c.filt[base + p1 * m1 + p2]);
+#pragma unroll
+        for (int q2 = 0; q2 < R2; ++q2)
+#pragma unroll
+            for (int q1 = 0; q1 < R1; ++q1) v[q2][q1] = c.dif_load(base + q2 + q1 * m1);
+#pragma unroll
+        for (int q2 = 0; q2 < R2; ++q2) bfly<R1, -1>(v[q2]);
+        if constexpr (R2 > 1) {
+#pragma unroll
+            for (int q2 = 1; q2 < R2; ++q2)
+#pragma unroll
+                for (int p1 = 1; p1 < R1; ++p1) v[q2][p1] = rot<R1 * R2, -1>(v[q2][p1], q2 * p1);
+#pragma unroll
+            for (int p1 = 0; p1 < R1; ++p1) {
+                cplx<T> u[R2];
+#pragma unroll
+                for (int q2 = 0; q2 < R2; ++q2) u[q2] = v[q2][p1];
+                bfly<R2, -1>(u);
+#pragma unroll
+                for (int p2 = 0; p2 < R2; ++p2) u[p2] = u[p2] * f[p1][p2];
+                bfly<R2, 1>(u);
+#pragma unroll
+                for (int q2 = 0; q2 < R2; ++q2) v[q2][p1] = u[q2];
+            }
+#pragma unroll
+            for (int q2 = 1; q2 < R2; ++q2)
+#pragma unroll
+                for (int p1 = 1; p1 < R1; ++p1) v[q2][p1] = rot<R1 * R2, 1>(v[q2][p1], q2 * p1);
+        } else {
+#pragma unroll
+            for (int p1 = 0; p1 < R1; ++p1) v[0][p1] = v[0][p1] * f[p1][0];
+        }
+#pragma unroll
+        for (int q2 = 0; q2 < R2; ++q2) {
+            bfly<R1, 1>(v[q2]);
+#pragma unroll
+            for (int q1 = 0; q1 < R1; ++q1) c.dit_store(base + q2 + q1 * m1, v[q2][q1]);
+        }
+    }
+}
+
+// mode 0: DIF pass, 1: DIT pass, 2: the fused middle pass
 template <class T, class TW, class C>
-__device__ __forceinline__ void run_pass(bool dif, int r1, int r2, C& c, int Ns, const TW& tw) {
+__device__ __forceinline__ void run_pass(int mode, int r1, int r2, C& c, int Ns, const TW& tw) {
     // pairs above the type's register budget are never planned, so they are not compiled
 #define SFFT_PASS(A, B)                                              \
     if constexpr (A * B <= pass_maxprod<T>()) {                      \
         if (r1 == A && r2 == B) {                                    \
-            if (dif) dif_pass<A, B, -1, T>(c, Ns, tw);               \
-            else dit_pass<A, B, T>(c, Ns, tw);                       \
+            if (mode == 0) dif_pass<A, B, -1, T>(c, Ns, tw);         \
+            else if (mode == 1) dit_pass<A, B, T>(c, Ns, tw);        \
+            else mid_pass<A, B, T>(c);                               \
             return;                                                  \
         }                                                            \
     }
@@ -400,7 +459,7 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
     cplx<T>* rbuf;       // CL: the other CTA's half (distributed shared memory)
     int hN = 0, rank = 0, nrank = 1;
     int N, M, epi;
-    bool inv, last = false;
+    bool inv;
     const cplx<TI>* in;
     const cplx<T>* chirp;
     const cplx<T>* filt;
@@ -422,7 +481,7 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
         }
     }
     __device__ __forceinline__ cplx<T> dif_load(int e) { return *at(e); }
-    __device__ __forceinline__ void dif_store(int e, cplx<T> v) { *at(e) = last ? v * ldg(&filt[e]) : qnorm(v); }
+    __device__ __forceinline__ void dif_store(int e, cplx<T> v) { *at(e) = qnorm(v); }
     __device__ __forceinline__ cplx<T> dit_load(int e) { return *at(e); }
     __device__ __forceinline__ void dit_store(int e, cplx<T> v) { *at(e) = qnorm(v); }
 
@@ -550,21 +609,23 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
     c.load_input(h0, h1);
     // the first pass reads both halves: both CTAs' inputs must be in place
     sync(true);
-    // ---- DIF passes (the last applies the filter)
+    // ---- DIF passes, the fused middle pass (last DIF pass, filter, first DIT pass), DIT passes
+    // in reverse order (the last writes into both halves)
     const int np = J.npass;
-    for (int p = 0, Ns = J.N; p < np; ++p) {
+    for (int p = 0, Ns = J.N; p < np - 1; ++p) {
         const int r1 = J.pass_r[p] & 15, r2 = J.pass_r[p] >> 4;
-        c.last = p == np - 1;
-        run_pass<T>(true, r1, r2, c, Ns, tw);
+        run_pass<T>(0, r1, r2, c, Ns, tw);
         Ns /= r1 * r2;
         sync(p == 0);
     }
-    // ---- DIT passes in reverse order (the last writes into both halves)
-    c.last = false;
-    for (int p = np - 1, Ns = 1; p >= 0; --p) {
+    int Ns = (J.pass_r[np - 1] & 15) * (J.pass_r[np - 1] >> 4);
+    run_pass<T>(2, J.pass_r[np - 1] & 15, J.pass_r[np - 1] >> 4, c, Ns, tw);
+    // cluster-wide when this pass was also the first (np = 1) or the last DIT pass comes next
+    sync(np <= 2);
+    for (int p = np - 2; p >= 0; --p) {
         const int r1 = J.pass_r[p] & 15, r2 = J.pass_r[p] >> 4;
         Ns *= r1 * r2;
-        run_pass<T>(false, r1, r2, c, Ns, tw);
+        run_pass<T>(1, r1, r2, c, Ns, tw);
         sync(p <= 1);
     }
     // ---- output phase over this CTA's elements below M
