@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--instances", type=int, default=NINST)
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-path, graph, e2e and CPU legs")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default launch shapes instead of autotuning them in setup")
     ap.add_argument("--dft", default="fp32", choices=["fp32", "df64"],
                     help="arithmetic of the forward lattice DFTs under the refinement (FP32, or double-float)")
     ap.add_argument("--cpu-baseline-worker", default=None, metavar="OUT", help=argparse.SUPPRESS)
@@ -316,7 +318,7 @@ def run_native(a, rank, world):
     # launch shapes: hash grid waves and transform CTA size picked by the library's autotuner on
     # the warm-up samples (setup, outside the timed region)
     with torch.cuda.stream(st):
-        tuned = batch.autotune(smp, reps=2)
+        tuned = (None, None) if a.no_autotune else batch.autotune(smp, reps=2)
         step()
     st.synchronize()
     # correctness gate on the last warm-up step: every instance returns <= s frequencies

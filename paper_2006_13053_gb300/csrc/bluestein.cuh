@@ -489,7 +489,7 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
     // order (coalesced) with kIoUnroll elements per thread whose global loads are issued together:
     // the passes then only touch shared memory, and the loads' latency is paid once per batch
     // instead of once per butterfly group.
-    static constexpr int kIoUnroll = 4;
+    static constexpr int kIoUnroll = 8;
     // work buffer = x_j chirp_j (conjugate chirp for the inverse) on [0, M), zero on [M, N)
     __device__ __forceinline__ void load_input(int e0, int e1) {
         for (int b = e0 + (int)threadIdx.x; b < e1; b += kIoUnroll * (int)blockDim.x) {
