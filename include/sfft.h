@@ -94,13 +94,14 @@ typedef struct sfft_params {
     uint64_t seed;    /* key of the Philox4x64-10 draws of generating vectors                  */
     int64_t detect_cap; /* capacity for |Itilde|; 0 = max(4 s + 4096, 16384)                  */
     int cand_type;    /* element type of the candidate rows: SFFT_CAND_I32 (default) or _I8     */
-    int cand_ld;      /* row stride in elements: 0 = d (I32); I8 rows: a multiple of 4, >= d   */
+    int cand_ld;      /* row stride in elements: 0 = d (I32); I8 rows: >= d bytes               */
     int dft;          /* SFFT_DFT_*: forward DFT arithmetic of FP32 plans with refinement      */
 } sfft_params;
 
 #define SFFT_CAND_I32 0 /* int32 rows of d entries                                              */
-#define SFFT_CAND_I8 1  /* int8 rows (|k_t| <= 127), stride cand_ld bytes (multiple of 4), so a  */
-                        /* row is read as whole 32-bit words; bytes past d are ignored          */
+#define SFFT_CAND_I8 1  /* int8 rows (|k_t| <= 127) of stride cand_ld >= d bytes in an array of  */
+                        /* n_cand * cand_ld bytes starting 4-byte aligned (it is read as 32-bit */
+                        /* words); bytes past d are ignored                                     */
 
 /* Fill *p with the defaults listed above.  Never fails. */
 void sfft_params_default(sfft_params* p);
@@ -181,14 +182,15 @@ int sfft_reconstruct_backward(sfft_plan* plan, const double* dcoef, void* dsampl
  * Samples of the sparse trigonometric polynomial p(x) = sum_q coef_q exp(2 pi i kvec_q . x)
  * (eq. 2.2) at the plan's lattice nodes, plus optional additive noise:
  *   kvec  device int32 [n_terms, d];  coef device complex double [n_terms];
- *   noise device complex double [sum M] or NULL;  samples_out device complex (plan precision).
+ *   noise device complex [sum M] in the plan precision, or NULL;  samples_out device complex
+ *   (plan precision).
  * Computed exactly through eq. (2.3): the coefficients are scattered into their buckets
  * k.z_l mod M_l and each lattice is inverse-transformed.  FP32 plans form buckets, transform
  * and noise sum in FP32 (samples within a few FP32 ulps of the exact value plus noise).
  * Asynchronous on the plan stream.
  */
 int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const double* coef, int64_t n_terms,
-                            const double* noise, void* samples_out);
+                            const void* noise, void* samples_out);
 
 /*
  * Samples of the sum-of-products function f(x) = sum_m prod_{t in T_m} g_{theta_m}(x_t) with
@@ -262,11 +264,12 @@ int sfft_batch_flags(sfft_batch* b, int64_t* flags);
  * sfft_sample_sparse_poly for every plan of the batch in shared launches (one bucket scatter,
  * one inverse-transform launch).  Arrays are indexed by the caller's plan order: kvec[i]
  * device int32 [n_terms[i], d_i]; coef[i] device complex double; noise NULL or noise[i] device
- * complex double [sum M] (may be NULL); samples_out[i] device complex (plan precision).
+ * complex [sum M] in the plan precision (may be NULL); samples_out[i] device complex (plan
+ * precision).
  * Asynchronous on the batch stream.
  */
 int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, const double* const* coef,
-                                  const int64_t* n_terms, const double* const* noise, void* const* samples_out);
+                                  const int64_t* n_terms, const void* const* noise, void* const* samples_out);
 
 /*
  * Per-stage GPU time of the batch's stage sequence, measured with CUDA events on the batch

@@ -34,8 +34,8 @@ class Plan:
     """A reconstruction plan (Algorithm 2/4) over the candidate set `cand` (kept referenced)."""
 
     def __init__(self, cand: torch.Tensor, s: int, L: int = 0, M=None, z=None, stream=None, d=None, **params):
-        """cand: int32 [n, d], or int8 [n, ld] rows (|k_t| <= 127, ld a multiple of 4 >= d, the
-        first d bytes of a row are the frequency; pass d)."""
+        """cand: int32 [n, d], or int8 [n, ld] rows (|k_t| <= 127, ld >= d, the first d bytes of a
+        row are the frequency, the tensor 4-byte aligned; pass d)."""
         if not (isinstance(cand, torch.Tensor) and cand.dim() == 2):
             raise ValueError("cand must be a 2-D tensor [n, d] (int32) or [n, ld] (int8)")
         if cand.dtype == torch.int8:
@@ -102,7 +102,7 @@ class Plan:
         _req(kvec, torch.int32, "kvec")
         _req(coef, torch.complex128, "coef")
         if noise is not None:
-            _req(noise, torch.complex128, "noise")
+            _req(noise, self.cdtype, "noise")  # complex in the plan precision
         out = out if out is not None else torch.empty(self.n_samples, dtype=self.cdtype, device=self.cand.device)
         N.check(N.sfft_sample_sparse_poly(self.handle, _ptr(kvec), _ptr(coef), kvec.shape[0], _ptr(noise), _ptr(out)))
         return out
@@ -222,8 +222,13 @@ class Batch:
         self.handle = h
         dev = self.plans[0].cand.device
         self.caps = [int(c) for c in (caps or [max(p.params.s_tilde or 0, 1) + 4 * 4096 for p in self.plans])]
-        self.supp = [torch.empty(c, dtype=torch.int64, device=dev) for c in self.caps]
-        self.coef = [torch.empty(c, dtype=torch.complex128, device=dev) for c in self.caps]
+        # one buffer for all supports and one for all coefficients (a result read-back is one copy
+        # each); self.supp / self.coef hold the per-plan views
+        self.supp_all = torch.empty(sum(self.caps), dtype=torch.int64, device=dev)
+        self.coef_all = torch.empty(sum(self.caps), dtype=torch.complex128, device=dev)
+        offs = np.concatenate([[0], np.cumsum(self.caps)]).astype(np.int64)
+        self.supp = [self.supp_all[offs[i]:offs[i + 1]] for i in range(n)]
+        self.coef = [self.coef_all[offs[i]:offs[i + 1]] for i in range(n)]
         self.nout = torch.zeros(n, dtype=torch.int64, device=dev)
         self._ps = (C.c_void_p * n)(*[t.data_ptr() for t in self.supp])
         self._pc = (C.c_void_p * n)(*[t.data_ptr() for t in self.coef])
@@ -252,6 +257,9 @@ class Batch:
         nt = (C.c_int64 * n)(*[k.shape[0] for k in kvecs])
         npp = None
         if noises is not None:
+            for p, x in zip(self.plans, noises):
+                if x is not None:
+                    _req(x, p.cdtype, "noise")  # complex in the plan precision
             npp = (C.c_void_p * n)(*[(x.data_ptr() if x is not None else 0) for x in noises])
         op = (C.c_void_p * n)(*[o.data_ptr() for o in outs])
         N.check(N.sfft_batch_sample_sparse_poly(self.handle, kp, cp, nt, npp, op))

@@ -252,8 +252,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
         SFFT_CHECK(p.cand_ld == 0 || p.cand_ld == d, SFFT_EINVAL, "int32 candidate rows are dense (cand_ld 0 or d)");
         p.cand_ld = d;
     } else {
-        SFFT_CHECK(p.cand_ld >= d && p.cand_ld % 4 == 0, SFFT_EINVAL,
-                   "int8 candidate rows need a stride cand_ld >= d that is a multiple of 4 (got %d)", p.cand_ld);
+        SFFT_CHECK(p.cand_ld >= d, SFFT_EINVAL, "int8 candidate rows need a stride cand_ld >= d (got %d)", p.cand_ld);
         SFFT_CHECK(((uintptr_t)cand & 3) == 0, SFFT_EINVAL, "int8 candidate rows must start 4-byte aligned");
     }
     P->d = d; P->cand = cand; P->n = n; P->s = s; P->p = p; P->prec = p.precision; P->st = st;
@@ -431,7 +430,8 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     P->hash_smem = *std::max_element(P->hsmem.begin(), P->hsmem.end());
     // tensor-core inner products: exact while every |k.z| (and partial sum) is below 2^24, the
     // bucket bit indices below 2^22, d <= 16 (2d <= 32) and L <= 64 (tensor-memory columns)
-    if (P->packed && d <= 16 && L <= 64 && P->hgroups.size() == 1 &&
+    // (int8 rows are read as whole words there: strides of a multiple of 4 bytes)
+    if (P->packed && d <= 16 && L <= 64 && P->hgroups.size() == 1 && P->p.cand_ld % 4 == 0 &&
         (double)d * (double)P->kmax * (double)(maxM - 1) < 16777216.0 && words * 32 < (1 << 22)) {
         P->tc_smem = hash_tc_smem_bytes(L, words);
         P->hash_tc = P->tc_smem <= 220 * 1024;
@@ -701,7 +701,7 @@ int sfft_reconstruct_backward(sfft_plan* plan, const double* dcoef, void* dsampl
 }
 
 int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const double* coef, int64_t n_terms,
-                            const double* noise, void* samples_out) {
+                            const void* noise, void* samples_out) {
     if (!plan || !samples_out || n_terms < 0 || (n_terms > 0 && (!kvec || !coef))) {
         set_error("null argument");
         return SFFT_EINVAL;
@@ -714,7 +714,7 @@ int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const do
     I.samp_coef = reinterpret_cast<const c64*>(coef);
     I.samp_nterms = n_terms;
     I.samp_out = samples_out;
-    I.samp_noise = reinterpret_cast<const c64*>(noise);
+    I.samp_noise = noise;
     SFFT_TRY(P->io_upload());
     // buckets in the plan precision (eq. 2.3), inverse lattice DFTs, noise
     SFFT_TRY(launch_clear(P->d_inst, 1, 0, 0, P->prec ? 2 : 1, st));

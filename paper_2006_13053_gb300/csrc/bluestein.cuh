@@ -517,12 +517,14 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
             }
         }
     }
-    // outputs j in [e0, e1), e1 <= M: chirp product, scale and the epilogue
+    // outputs j in [e0, e1), e1 <= M: chirp product, scale and the epilogue (the noise of
+    // EPI_ADDNOISE is complex float for float transforms, complex double otherwise)
+    using NZ = typename std::conditional<std::is_same<T, float>::value, c32, c64>::type;
     __device__ __forceinline__ void store_output(int e0, int e1) {
-        const c64* noise = epi == EPI_ADDNOISE ? reinterpret_cast<const c64*>(auxp) : nullptr;
+        const NZ* noise = epi == EPI_ADDNOISE ? reinterpret_cast<const NZ*>(auxp) : nullptr;
         for (int b = e0 + (int)threadIdx.x; b < e1; b += kIoUnroll * (int)blockDim.x) {
             cplx<T> vv[kIoUnroll], wv[kIoUnroll];
-            c64 zv[kIoUnroll];
+            NZ zv[kIoUnroll];
 #pragma unroll
             for (int u = 0; u < kIoUnroll; ++u) {
                 const int e = b + u * (int)blockDim.x;
@@ -540,7 +542,7 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
             }
         }
     }
-    __device__ __forceinline__ void emit(int e, cplx<T> v, cplx<T> w, const c64* zp) {
+    __device__ __forceinline__ void emit(int e, cplx<T> v, cplx<T> w, const NZ* zp) {
         cplx<T> X = inv ? mulc(v, w) : v * w;
         X = X * sc;
         if (epi == EPI_PLAIN || epi == EPI_ANALYZE) {
@@ -552,9 +554,9 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
                 out[e] = ccv<TO>(X);
             }
             if (epi == EPI_ANALYZE) mx2 = fmax(mx2, scv<R>(abs2(X)));
-        } else {  // EPI_ADDNOISE (noise complex double; added in the transform precision)
+        } else {  // EPI_ADDNOISE (noise added in the transform precision)
             if constexpr (std::is_same<T, float>::value) {
-                if (zp) X = X + c32{(float)zp->x, (float)zp->y};
+                if (zp) X = X + *zp;
                 out[e] = ccv<TO>(X);
             } else {
                 c64 r = ccv<double>(X);
@@ -679,7 +681,9 @@ __device__ __forceinline__ void bluestein_cta(const BlueJob* __restrict__ jobs, 
     if (J.io_flags & 48) {
         const InstDesc& I = insts[J.inst];
         if (J.io_flags & 16) outp = (char*)I.samp_out + J.io_off * sizeof(cplx<TO>);
-        if (J.io_flags & 32) auxp = I.samp_noise ? (const void*)(I.samp_noise + J.io_off) : nullptr;
+        if (J.io_flags & 32)
+            auxp = I.samp_noise ? (const void*)((const char*)I.samp_noise + J.io_off * (I.prec ? sizeof(c32) : sizeof(c64)))
+                                : nullptr;
     }
     if (J.io_flags & 4) outp = (char*)out_base + J.io_off * sizeof(cplx<TO>);
     if (J.io_flags & 8) auxp = aux_base ? (const void*)((const c64*)aux_base + J.io_off) : nullptr;

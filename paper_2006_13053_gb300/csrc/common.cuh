@@ -277,7 +277,7 @@ struct InstDesc {
     const c64* samp_coef;      // [samp_nterms]
     int64_t samp_nterms;
     void* samp_out;            // [sum M] complex (prec)
-    const c64* samp_noise;     // [sum M] or NULL
+    const void* samp_noise;    // [sum M] complex in the plan precision, or NULL
 };
 
 static_assert(sizeof(InstDesc) % 8 == 0, "descriptors are uploaded as 8-byte words");

@@ -304,7 +304,7 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
 }
 
 int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, const double* const* coef,
-                                  const int64_t* n_terms, const double* const* noise, void* const* samples_out) {
+                                  const int64_t* n_terms, const void* const* noise, void* const* samples_out) {
     if (!b || !kvec || !coef || !n_terms || !samples_out) { set_error("null argument"); return SFFT_EINVAL; }
     Batch* B = reinterpret_cast<Batch*>(b);
     const int n = (int)B->plans.size();
@@ -319,7 +319,7 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
         I.samp_coef = reinterpret_cast<const c64*>(coef[u]);
         I.samp_nterms = n_terms[u];
         I.samp_out = samples_out[u];
-        I.samp_noise = noise ? reinterpret_cast<const c64*>(noise[u]) : nullptr;
+        I.samp_noise = noise ? noise[u] : nullptr;
         mx = std::max<int64_t>(mx, n_terms[u] * B->plans[i]->L);
     }
     cudaStream_t st = B->st;

@@ -407,8 +407,12 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
     const int need = I.need;
     const int32_t* __restrict__ cand = reinterpret_cast<const int32_t*>(I.cand);
     const uint32_t* __restrict__ cand8w = reinterpret_cast<const uint32_t*>(I.cand);  // int8 rows as words
-    const int ldw = I.cand_ld >> 2;
-    const bool i8 = I.cand_i8 != 0;
+    const int ld = I.cand_ld, ldw = ld >> 2;
+    const bool i8 = I.cand_i8 != 0, ld4 = (ld & 3) == 0;
+    const int64_t nbytes = n * ld;  // int8 rows: bytes of the candidate array
+    // rows below r_safe have their KW + 1 aligned words inside the array (last byte read
+    // r ld + 4 KW + 3 < n ld); the last few rows are read with bounds checks
+    const int64_t r_safe = n - (4 * PK::KW + 3) / (ld > 0 ? ld : 1) - 1;
     const int64_t step = (int64_t)gridDim.x * blockDim.x * kCPT2;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kCPT2; base < n; base += step) {
         uint32_t kw[kCPT2][PK::KW];
@@ -418,8 +422,34 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
             idx[c] = base + threadIdx.x + (int64_t)c * blockDim.x;
             const int64_t r = idx[c] < n ? idx[c] : 0;
             if (i8) {  // the int8 row already holds the packed words (bytes past d meet zero z entries)
+                if (ld4) {
 #pragma unroll
-                for (int w = 0; w < PK::KW; ++w) kw[c][w] = __ldg(cand8w + r * ldw + w);
+                    for (int w = 0; w < PK::KW; ++w) kw[c][w] = __ldg(cand8w + r * ldw + w);
+                } else {  // rows at any byte offset: the aligned words around the row, funnel-shifted
+                    const int64_t b0 = r * ld, w0 = b0 >> 2;
+                    const uint32_t sh = (uint32_t)(b0 & 3) * 8u;
+                    uint32_t wv[PK::KW + 1];
+                    if (r < r_safe) {
+#pragma unroll
+                        for (int j = 0; j <= PK::KW; ++j) wv[j] = __ldg(cand8w + w0 + j);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j <= PK::KW; ++j) {
+                            const int64_t wj = w0 + j;
+                            if ((wj + 1) * 4 <= nbytes) {
+                                wv[j] = __ldg(cand8w + wj);
+                            } else {  // the array's last bytes (no read past its end)
+                                const uint8_t* b8 = reinterpret_cast<const uint8_t*>(I.cand);
+                                uint32_t v = 0;
+                                for (int q = 0; q < 4; ++q)
+                                    if (wj * 4 + q < nbytes) v |= (uint32_t)b8[wj * 4 + q] << (8 * q);
+                                wv[j] = v;
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int w = 0; w < PK::KW; ++w) kw[c][w] = __funnelshift_r(wv[w], wv[w + 1], sh);
+                }
                 continue;
             }
             const int32_t* row = cand + r * D;

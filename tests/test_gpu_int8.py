@@ -1,6 +1,8 @@
-"""Compact int8 candidate rows (|k_t| <= 127, row stride a multiple of 4 bytes) through the C ABI:
-the same detections, hashes, counts, supports and coefficients as the int32 rows, and the FP64
-oracle's, for both hash kernels (packed dp2a for M <= 32768, int32 arithmetic above)."""
+"""Compact int8 candidate rows (|k_t| <= 127, any row stride >= d bytes) through the C ABI: the
+same detections, hashes, counts, supports and coefficients as the int32 rows, and the FP64
+oracle's, for both hash kernels (packed dp2a for M <= 32768, int32 arithmetic above), with rows
+on word boundaries (stride 12) and at any byte offset (strides 10 and 13, the latter with an
+array length that is not a multiple of 4 bytes)."""
 import math
 
 import numpy as np
@@ -37,10 +39,10 @@ def rows8(cand, ld, seed):
     return r
 
 
-@pytest.mark.parametrize("prec,refine", [(1, 1), (0, 0)])
-def test_int8_rows_match_int32_and_oracle(G, prec, refine):
+@pytest.mark.parametrize("prec,refine,ld", [(1, 1, 12), (0, 0, 12), (1, 1, 10), (1, 1, 13)])
+def test_int8_rows_match_int32_and_oracle(G, prec, refine, ld):
     import torch
-    seed, n, d, s = 3, 2 ** 13, 10, 60
+    seed, n, d, s = 3, 2 ** 13 - 1, 10, 60
     cand = S.uniform_distinct(n, d, -64, 64, seed)
     L = O.L_cor26(n, 0.1)
     M = O.lattice_size(cand, s)
@@ -55,7 +57,7 @@ def test_int8_rows_match_int32_and_oracle(G, prec, refine):
     kw = dict(L=L, M=[M] * L, z=z, precision=prec, refine=refine, tau_abs=tau, tau_rel=0.0)
     ys = T(y, torch.complex64 if prec else torch.complex128)
     p32 = G.Plan(T(cand), s, **kw)
-    p8 = G.Plan(T(rows8(cand, 12, seed)), s, d=d, **kw)
+    p8 = G.Plan(T(rows8(cand, ld, seed)), s, d=d, **kw)
     s32, c32, i32 = p32.reconstruct(ys, diag=True, counts=True, hashes=True)
     s8, c8, i8 = p8.reconstruct(ys, diag=True, counts=True, hashes=True)
     for k in ("hashes", "counts", "detected"):
@@ -93,8 +95,6 @@ def test_int8_rows_invalid_layout(G):
     import torch
     cand = S.uniform_distinct(256, 5, -10, 10, 1)
     r = T(rows8(cand, 8, 1))
-    with pytest.raises(G.SfftError):
-        G.Plan(r, 4, d=5, cand_ld=6)            # stride not a multiple of 4
     with pytest.raises(G.SfftError):
         G.Plan(r, 4, d=9)                       # stride below d
     flat = torch.zeros(256 * 8 + 4, dtype=torch.int8, device="cuda:0")

@@ -254,6 +254,8 @@ def test_sampler_and_points(G, prec):
     assert np.array_equal(num.cpu().numpy(), ref_num)
     assert np.array_equal(x.cpu().numpy(), ref_num / M)
     noise = S.noise(L * M, 0.1, 5)
+    if prec == 1:  # noise is passed in the plan precision
+        noise = noise.astype(np.complex64)
     y = plan.sample_sparse_poly(T(cand[sup]), T(c), T(noise)).cpu().numpy()
     ref = O.sample_sparse_poly(cand[sup], c, z, M) + noise
     tol = 1e-12 if prec == 0 else 3e-6
@@ -494,7 +496,7 @@ def test_batch_sampler_matches_plan_sampler(G):
         plans.append(G.Plan(T(cand), s, precision=1, seed=seed))
         kv.append(T(cand[sup]))
         cf.append(T(S.coef_cgauss(s, seed)))
-        nz.append(T(S.noise(plans[-1].n_samples, 0.01, seed)))
+        nz.append(T(S.noise(plans[-1].n_samples, 0.01, seed).astype(np.complex64)))
     st = torch.cuda.Stream()
     B = G.Batch(plans, stream=st)
     outs = B.sample_sparse_poly(kv, cf, nz)
