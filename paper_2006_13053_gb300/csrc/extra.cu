@@ -29,7 +29,17 @@ struct Batch {
     cudaStream_t st = nullptr;
     int use_graph = 0, prec = 0;
     InstDesc* d_inst = nullptr;
-    InstDesc* h_inst = nullptr;  // pinned staging [n]
+    InstDesc* h_inst = nullptr;  // pinned descriptors [n]: the current state (a captured graph uploads it)
+    // eager calls upload a copy of h_inst from a ring of kStage pinned slots, so that the host can
+    // run several calls ahead of the GPU: a slot is rewritten only after its upload kStage calls
+    // ago has executed
+    static constexpr int kStage = 4;
+    InstDesc* h_ring = nullptr;  // pinned [kStage][n]
+    cudaEvent_t ring_ev[kStage] = {};
+    int ring_next = 0;
+    // the descriptors the device holds (kernels never write them): an unchanged call uploads
+    // nothing, so repeated calls on the same buffers read no host memory while bulk copies run
+    std::vector<InstDesc> h_dev;
     LatDesc* d_lats = nullptr;
     std::vector<void*> allocs;
     PipeArgs args;
@@ -40,7 +50,7 @@ struct Batch {
     int64_t* graph_nout = nullptr;  // n_out_dev the captured graph writes
     int64_t* d_flags = nullptr;
     cudaEvent_t done = nullptr;    // end of the last enqueued call (results and flags ready)
-    cudaEvent_t io_ev = nullptr;   // the last call's descriptor upload has executed (staging reusable)
+    cudaEvent_t io_ev = nullptr;   // the last graph launch has read h_inst (h_inst writable)
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int calls = 0;
@@ -76,20 +86,40 @@ struct Batch {
         if (done) cudaEventDestroy(done);
         if (io_ev) cudaEventDestroy(io_ev);
         io_ev = nullptr;
+        for (int k = 0; k < kStage; ++k)
+            if (ring_ev[k]) cudaEventDestroy(ring_ev[k]);
         for (void* p : allocs) cudaFree(p);
         if (h_inst) cudaFreeHost(h_inst);
+        if (h_ring) cudaFreeHost(h_ring);
         allocs.clear();
-        exec = nullptr; graph = nullptr; done = nullptr; h_inst = nullptr;
+        exec = nullptr; graph = nullptr; done = nullptr; h_inst = nullptr; h_ring = nullptr;
+    }
+    // upload the current descriptors through the next ring slot (eager calls)
+    int stage_upload() {
+        const int n = (int)plans.size();
+        if (memcmp(h_dev.data(), h_inst, sizeof(InstDesc) * n) == 0) return SFFT_OK;
+        memcpy(h_dev.data(), h_inst, sizeof(InstDesc) * n);
+        const int k = ring_next;
+        ring_next = (k + 1) % kStage;
+        SFFT_CU(cudaEventSynchronize(ring_ev[k]));
+        InstDesc* slot = h_ring + (size_t)k * n;
+        memcpy(slot, h_inst, sizeof(InstDesc) * n);
+        SFFT_TRY(launch_upload(d_inst, slot, sizeof(InstDesc) * n, st));
+        SFFT_CU(cudaEventRecord(ring_ev[k], st));
+        return SFFT_OK;
     }
     int alloc(void** p, size_t bytes) {
         SFFT_CU(cudaMalloc(p, std::max<size_t>(bytes, 16)));
         allocs.push_back(*p);
         return SFFT_OK;
     }
-    int enqueue(bool record_io, int64_t* n_out) {
+    int enqueue(bool eager, int64_t* n_out) {
         const int n = (int)plans.size();
-        SFFT_TRY(launch_upload(d_inst, h_inst, sizeof(InstDesc) * n, st));
-        if (record_io) SFFT_CU(cudaEventRecord(io_ev, st));  // not inside a graph capture
+        if (eager) {
+            SFFT_TRY(stage_upload());
+        } else {  // graph capture: every launch uploads h_inst as it is then
+            SFFT_TRY(launch_upload(d_inst, h_inst, sizeof(InstDesc) * n, st));
+        }
         SFFT_TRY(run_pipeline(args, st));
         k_gather_counts<<<(n + 127) / 128, 128, 0, st>>>(d_inst, n, d_counts, d_flags, d_order, n_out);
         return launch_check("k_gather_counts");
@@ -120,6 +150,7 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
     B->order = idx;
     for (int i : idx) B->plans.push_back(reinterpret_cast<Plan*>(plans[i]));
     SFFT_CU(cudaMallocHost((void**)&B->h_inst, sizeof(InstDesc) * n));
+    SFFT_CU(cudaMallocHost((void**)&B->h_ring, sizeof(InstDesc) * n * Batch::kStage));
     std::vector<LatDesc> lats;
     std::vector<BlueJob> jf[3], js[3];  // by work-buffer mode: global scratch, shared memory, cluster
     int maxN[3][2] = {{0, 0}, {0, 0}, {0, 0}};
@@ -151,6 +182,7 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
     SFFT_CU(cudaMemcpy(B->d_lats, lats.data(), sizeof(LatDesc) * lats.size(), cudaMemcpyHostToDevice));
     SFFT_TRY(B->alloc((void**)&B->d_inst, sizeof(InstDesc) * n));
     SFFT_CU(cudaMemcpy(B->d_inst, B->h_inst, sizeof(InstDesc) * n, cudaMemcpyHostToDevice));
+    B->h_dev.assign(B->h_inst, B->h_inst + n);
     A.d_inst = B->d_inst;
     A.d_lats = B->d_lats;
     for (int md : {1, 2, 0}) {
@@ -215,6 +247,7 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
     SFFT_TRY(B->alloc((void**)&B->d_flags, sizeof(int64_t) * n));
     SFFT_CU(cudaEventCreateWithFlags(&B->done, cudaEventDisableTiming));
     SFFT_CU(cudaEventCreateWithFlags(&B->io_ev, cudaEventDisableTiming));
+    for (int k = 0; k < Batch::kStage; ++k) SFFT_CU(cudaEventCreateWithFlags(&B->ring_ev[k], cudaEventDisableTiming));
     for (int i = 0; i <= ST_COUNT; ++i) SFFT_CU(cudaEventCreate(&B->timer.ev[i]));
     B->timer_made = true;
     return SFFT_OK;
@@ -252,8 +285,7 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
     if (!b || !samples || !supp_out || !coef_out || !cap) { set_error("null argument"); return SFFT_EINVAL; }
     Batch* B = reinterpret_cast<Batch*>(b);
     const int n = (int)B->plans.size();
-    // the previous call's upload of the staging descriptors must have executed (the host may run
-    // ahead of the GPU by one call)
+    // a pending graph launch reads h_inst when it runs (eager uploads use the ring)
     SFFT_CU(cudaEventSynchronize(B->io_ev));
     for (int i = 0; i < n; ++i) {
         const int u = B->order[i];  // caller's index of batch entry i
@@ -293,6 +325,7 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
             SFFT_CU(cudaGraphInstantiate(&B->exec, g, 0));
         }
         SFFT_CU(cudaGraphLaunch(B->exec, st));
+        memcpy(B->h_dev.data(), B->h_inst, sizeof(InstDesc) * n);  // what the launch uploads
         SFFT_CU(cudaEventRecord(B->io_ev, st));  // the graph reads the staging buffer when it runs
     } else {
         SFFT_TRY(B->enqueue(true, n_out_dev));
@@ -308,7 +341,7 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
     if (!b || !kvec || !coef || !n_terms || !samples_out) { set_error("null argument"); return SFFT_EINVAL; }
     Batch* B = reinterpret_cast<Batch*>(b);
     const int n = (int)B->plans.size();
-    SFFT_CU(cudaEventSynchronize(B->io_ev));  // staging buffer free (see sfft_batch_reconstruct)
+    SFFT_CU(cudaEventSynchronize(B->io_ev));  // h_inst writable (see sfft_batch_reconstruct)
     int64_t mx = 0;
     for (int i = 0; i < n; ++i) {
         const int u = B->order[i];
@@ -323,8 +356,7 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
         mx = std::max<int64_t>(mx, n_terms[u] * B->plans[i]->L);
     }
     cudaStream_t st = B->st;
-    SFFT_TRY(launch_upload(B->d_inst, B->h_inst, sizeof(InstDesc) * n, st));
-    SFFT_CU(cudaEventRecord(B->io_ev, st));
+    SFFT_TRY(B->stage_upload());
     SFFT_TRY(launch_clear(B->d_inst, n, 0, 0, B->prec ? 2 : 1, st));
     if (mx > 0) SFFT_TRY(launch_scatter_terms(B->d_inst, n, mx, st));
     for (const auto& f : B->samp)
