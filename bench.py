@@ -497,10 +497,14 @@ def run_native(a, rank, world):
     st.synchronize()
     d2h = sum(t.numel() * t.element_size() for t in (sets[0]["out_s"], sets[0]["out_c"], sets[0]["out_n"]))
 
-    def e2e_step(t):
+    span0, span1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def e2e_step(t, first=False, last=False):
         b_ = sets[t % E2E_SETS]
         with torch.cuda.stream(cs):  # inputs of step t (after step t - E2E_SETS released this set)
             cs.wait_event(b_["done"])
+            if first:
+                span0.record(cs)
             b_["dbuf"].copy_(hbuf, non_blocking=True)
             b_["copied"].record(cs)
         with torch.cuda.stream(st):  # kernels of step t
@@ -514,15 +518,22 @@ def run_native(a, rank, world):
             b_["out_s"].copy_(b_["batch"].supp_all, non_blocking=True)
             b_["out_c"].copy_(b_["batch"].coef_all, non_blocking=True)
             b_["done"].record(rs)
+            if last:
+                span1.record(rs)
 
     for t_ in range(4):
         e2e_step(t_)
     torch.cuda.synchronize()
-    ne = max(4, a.steps)
+    ne = max(20, a.steps)
     t0 = time.perf_counter()
     for t_ in range(ne):
-        e2e_step(t_)
+        e2e_step(t_, first=t_ == 0, last=t_ == ne - 1)
     host_ms = (time.perf_counter() - t0) / ne * 1000.0  # enqueue time (the host runs ahead until it blocks)
+    span1.synchronize()
+    wall_ms = (time.perf_counter() - t0) / ne * 1000.0
+    # device span from the start of the first step's host-to-device copy to the end of the last
+    # step's read-back: every copy, kernel and read-back of the ne steps
+    dev_ms = span0.elapsed_time(span1) / ne
     torch.cuda.synchronize()
     # host cost of enqueueing one step on an idle GPU (nothing to wait for)
     hc = []
@@ -532,17 +543,20 @@ def run_native(a, rank, world):
         hc.append((time.perf_counter() - t1) * 1000.0)
         torch.cuda.synchronize()
     host_idle_ms = statistics.median(hc)
-    e2e_ms = max_over_ranks((time.perf_counter() - t0) / ne * 1000.0, world, dev)
+    e2e_ms = max_over_ranks(dev_ms, world, dev)
     # the host-to-device transfer alone (the step's lower bound when it exceeds the kernels)
     torch.cuda.synchronize()
-    t1 = time.perf_counter()
     with torch.cuda.stream(cs):
+        span0.record(cs)
         for t_ in range(ne):
             sets[t_ % E2E_SETS]["dbuf"].copy_(hbuf, non_blocking=True)
-    torch.cuda.synchronize()
-    h2d_ms = (time.perf_counter() - t1) / ne * 1000.0
+        span1.record(cs)
+    span1.synchronize()
+    h2d_ms = span0.elapsed_time(span1) / ne
     out["e2e"] = {"value": whole_job_value(world, n_inst, e2e_ms), "unit": "reconstructions/s",
                   "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e2e_ms,
+                  "timing": f"CUDA events: first step's host-to-device copy to the last step's read-back, "
+                            f"{ne} steps", "wall_ms_per_step_at_last_event": wall_ms,
                   "h2d_alone_ms_per_step": h2d_ms, "h2d_alone_gbs": h2d / (h2d_ms / 1000.0) / 1e9,
                   "host_enqueue_ms_per_step": host_ms, "host_idle_enqueue_ms_per_step": host_idle_ms,
                   "pipelining": f"{E2E_SETS} buffer sets: step t+1's host-to-device copy (one transfer of all "
