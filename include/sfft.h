@@ -5,7 +5,7 @@
  * Notation follows the paper: Gamma (the candidate set, "cand") is a finite set of integer
  * frequency vectors k in Z^d; the unknown function is sampled along L rank-1 lattices
  * Lambda(z_l, M_l) = { j z_l / M_l mod 1 : j = 0..M_l-1 } (Section 2.1, eq. 2.1); each
- * lattice's samples are transformed by a length-M_l DFT (Algorithm 2, line 2); a candidate
+ * lattice's samples are transformed by a length-M_l DFT (Algorithm 2); a candidate
  * k is detected when its buckets ghat^(l)_{k.z_l mod M_l} are non-zero for at least nu*L
  * lattices (Algorithm 1; nu = 1/2 in Algorithm 2) and its coefficient is the component-wise
  * median of those L bucket values (Algorithm 2, eq. 2.6).  Algorithm 4 then keeps the
@@ -147,7 +147,7 @@ typedef struct sfft_diag {
     int32_t* collisions; /* device [sum M]: c_l[h] = #{k in Itilde : h_kl = h} (Remark 2.8)  */
     int64_t* detected;   /* device [detect_cap]: Itilde (indices into Gamma, ascending)       */
     double* pcheck;      /* device complex double [detect_cap]: medians of Itilde (eq. 2.6)   */
-    double* ghat;        /* device complex double [sum M]: lattice DFTs (Alg 2 line 2)        */
+    double* ghat;        /* device complex double [sum M]: lattice DFTs (Algorithm 2)        */
     double* tau;         /* device double [L]: zero-test thresholds                           */
     int64_t n_detected;  /* out: |Itilde|                                                     */
     int64_t n_guard;     /* out: buckets whose zero test was re-done in FP64                  */
@@ -274,7 +274,7 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
 /*
  * Per-stage GPU time of the batch's stage sequence, measured with CUDA events on the batch
  * stream around each stage of every call since the last reset.  Stage order: clear, lattice
- * DFT (Algorithm 2 line 2), zero test, hash + count, compaction, hashes of Itilde, combine,
+ * DFT (Algorithm 2), zero test, hash + count, compaction, hashes of Itilde, combine,
  * refinement scatter, refinement model IDFT (FP64), refinement DFT, refinement update,
  * Algorithm 4 selection.  ms / launches: host arrays of 12 entries (optional) receive the
  * accumulated milliseconds and the number of timed calls.  mode = 1 enables timing (graph

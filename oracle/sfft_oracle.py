@@ -322,7 +322,7 @@ def sop_norm2(triples, theta, K=48, width=32.0):
     return tot
 
 
-# =========================================================================== lattice DFT (Alg 2 line 2)
+# =========================================================================== lattice DFT (Algorithm 2)
 def lattice_dft(samples: np.ndarray, M: int) -> np.ndarray:
     """ghat_h = (1/M) sum_j p_j exp(-2 pi i j h / M), h = 0..M-1 (library FFT)."""
     return np.fft.fft(np.asarray(samples, dtype=np.complex128)) / M
@@ -483,7 +483,7 @@ def refine(samples_list, cand, det, coef, z, M_list, mode="direct"):
 
 
 def select_top(coef, s_tilde, theta):
-    """Algorithm 4 lines 2-3: keep |c| >= theta, sort by modulus descending (ties: lower
+    """Algorithm 4, filter and selection: keep |c| >= theta, sort by modulus descending (ties: lower
     index first) and keep the first s_tilde.  Returns positions into coef, ascending."""
     a = np.abs(coef)
     keep = np.nonzero(a >= theta)[0]

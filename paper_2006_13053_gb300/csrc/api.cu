@@ -459,7 +459,7 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
         for (int i = 0; i <= ST_COUNT; ++i) a.timer->recorded[i] = false;
     SFFT_TRY(mark(a, ST_CLEAR, st));
     SFFT_TRY(launch_clear(a.d_inst, ni, 1, a.hybrid, 0, st));
-    // Algorithm 2 line 2: lattice DFTs (normalised by 1/M) + per-lattice statistics
+    // Algorithm 2: lattice DFTs (normalised by 1/M) + per-lattice statistics
     SFFT_TRY(mark(a, ST_FFT_FWD, st));
     for (const auto& f : a.fwd)
         SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.mode, a.fwd_prec, a.prec, a.prec, -1, EPI_ANALYZE, a.d_inst,

@@ -1,4 +1,4 @@
-// Device code of the batched Bluestein transforms (Algorithm 2, line 2): a length-M DFT becomes
+// Device code of the batched Bluestein transforms (Algorithm 2): a length-M DFT becomes
 // a cyclic convolution of length N = 2^a 3^b 5^c >= 2M-1, computed by an in-place mixed-radix
 // decimation-in-frequency FFT (natural order in, digit-reversed out), a pointwise product with
 // the precomputed filter (itself stored digit-reversed) and the matching decimation-in-time

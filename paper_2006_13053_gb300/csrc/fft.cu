@@ -1,4 +1,4 @@
-// Host side of the batched prime-length DFTs (Algorithm 2, line 2) by Bluestein's algorithm:
+// Host side of the batched prime-length DFTs (Algorithm 2) by Bluestein's algorithm:
 // per distinct M the Bluestein length N = 2^a 3^b 5^c >= 2M-1, its radix order and pass plan,
 // and the chirp, filter and twiddle tables (computed once in double: chirp phases j^2 mod 2M
 // and all twiddle indices are exact integers), plus the launch dispatcher over the arithmetic

@@ -1,4 +1,4 @@
-// Hash + count (Algorithm 2, lines 4-6) with the inner products k.z_l on the tensor cores.
+// Hash + count (Algorithm 2) with the inner products k.z_l on the tensor cores.
 //
 // For a tile of 128 candidates the products k.z_l of all L lattices form one small GEMM
 // D = A B^T: A [128 x 2H] holds each candidate's k at K offsets 0 and H (H = 8 for d <= 8, else
