@@ -202,11 +202,11 @@ def cpu_baseline(gpu_result=None, timeout=600):
 # ------------------------------------------------------------------ native arm
 def kernel_count(batch_plans, n_inst, refine=True):
     # per step: batched sampler (clear, bucket scatter, inverse lattice DFT) and the batch's
-    # clear + DFT + zero test + hash groups + compact + hashes + combine + select + counts (the
-    # descriptor uploads run only when a call's buffers differ from the last call's: not in the
-    # timed loop, which reuses its buffers)
+    # clear + DFT + zero test + hash groups + compact + combine (which forms the hashes of the
+    # detected set) + select + counts (the descriptor uploads run only when a call's buffers
+    # differ from the last call's: not in the timed loop, which reuses its buffers)
     hash_groups = len({p.d for p in batch_plans})
-    n = 3 + 1 + 1 + 1 + hash_groups + 1 + 1 + 1 + 1 + 1
+    n = 3 + 1 + 1 + 1 + hash_groups + 1 + 1 + 1 + 1
     if refine:
         n += 1 + 1 + 1  # clear C, scatter, median update of ghat - C
     return n

@@ -477,11 +477,12 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
     SFFT_TRY(mark(a, ST_COMPACT, st));
     SFFT_TRY(launch_compact(a.d_inst, ni, st));
     // hashes of Itilde, collision counts, median / hybrid combine
+    // (the median combine forms the hashes itself; the hybrid one needs all collision counts first)
     SFFT_TRY(mark(a, ST_DET_HASH, st));
-    SFFT_TRY(launch_det_hashes(a.d_inst, ni, a.maxcap, st));
+    if (a.hybrid) SFFT_TRY(launch_det_hashes(a.d_inst, ni, a.maxcap, st));
     SFFT_TRY(mark(a, ST_COMBINE, st));
     if (a.hybrid) SFFT_TRY(launch_collisions(a.d_inst, ni, st));
-    SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, 0, st));
+    SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, a.hybrid ? 0 : 3, st));
     if (a.lsq) {  // Remark 2.8 least squares on the detected set, from the medians
         SFFT_TRY(mark(a, ST_LSQ, st));
         SFFT_TRY(launch_lsq(a.d_inst, ni, a.prec, st));

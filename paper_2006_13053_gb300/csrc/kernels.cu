@@ -512,8 +512,9 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
             if constexpr (!DIAG) {
                 // count rule (Algorithm 1): once no candidate of the warp can still reach `need`
                 // with the lattices left, the rest cannot change a decision (exact counts are only
-                // reported by the DIAG variant)
-                if ((l & 3) == 3) {
+                // reported by the DIAG variant); tested every second lattice (every fourth or
+                // eighth measured slower: later exits; every one: more checks)
+                if ((l & 1) == 1) {
                     const int rem = L - 1 - (l0 + l);
                     bool alive = false;
 #pragma unroll
@@ -596,26 +597,29 @@ __global__ void __launch_bounds__(kCompactThreads) k_compact(InstDesc* __restric
 
 // ================================================================== hashes of the detected set
 // One warp per detected candidate; lane l (and l+32) owns lattice l.
+// h = k.z_l mod M_l of detected candidate q.  The plan bounds |k.z| so that the offset sum fits
+// 32 bits: the hash kernel's exact Barrett reduction (q = umulhi(x, floor(2^32/M)) is at most one
+// short, so one conditional subtraction).
+__device__ __forceinline__ int32_t det_hash(const InstDesc& I, int64_t q, int l) {
+    const int d = I.d;
+    const int64_t row = I.det[q] * I.cand_ld;
+    const int32_t* k32 = reinterpret_cast<const int32_t*>(I.cand) + row;
+    const int8_t* k8 = reinterpret_cast<const int8_t*>(I.cand) + row;
+    const int32_t* zl = I.z + l * d;
+    uint32_t xp = I.offk[l];  // unsigned wrap-around: the sum mod 2^32, in [0, 2^32)
+    for (int t = 0; t < d; ++t) xp += (uint32_t)((I.cand_i8 ? (int)__ldg(k8 + t) : __ldg(k32 + t)) * zl[t]);
+    const uint32_t M = (uint32_t)I.Ml[l];
+    uint32_t r = xp - __umulhi(xp, I.mu[l]) * M;
+    return (int32_t)min(r, r - M);
+}
+
 __global__ void k_det_hashes(const InstDesc* __restrict__ insts) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nd = min(I.cnt[0], I.cap);
     const int warps = blockDim.x >> 5;
     for (int64_t q = (int64_t)blockIdx.x * warps + (threadIdx.x >> 5); q < nd; q += (int64_t)gridDim.x * warps) {
-        const int lane = threadIdx.x & 31, L = I.L, d = I.d;
-        const int64_t row = I.det[q] * I.cand_ld;
-        const int32_t* k32 = reinterpret_cast<const int32_t*>(I.cand) + row;
-        const int8_t* k8 = reinterpret_cast<const int8_t*>(I.cand) + row;
-        for (int l = lane; l < L; l += 32) {
-            // the plan bounds |k.z| so that the offset sum fits 32 bits: the hash kernel's exact
-            // Barrett reduction (q = umulhi(x, floor(2^32/M)) is at most one short)
-            const int32_t* zl = I.z + l * d;
-            uint32_t xp = I.offk[l];  // unsigned wrap-around: the sum mod 2^32, in [0, 2^32)
-            for (int t = 0; t < d; ++t) xp += (uint32_t)((I.cand_i8 ? (int)__ldg(k8 + t) : __ldg(k32 + t)) * zl[t]);
-            const uint32_t M = (uint32_t)I.Ml[l];
-            uint32_t r = xp - __umulhi(xp, I.mu[l]) * M;
-            r = min(r, r - M);
-            I.H[q * L + l] = (int32_t)r;
-        }
+        const int lane = threadIdx.x & 31, L = I.L;
+        for (int l = lane; l < L; l += 32) I.H[q * L + l] = det_hash(I, q, l);
     }
 }
 
@@ -734,7 +738,10 @@ __device__ __forceinline__ int warp_median32(int ka, int kb, int L, int lane) {
 // Median combine (eq. 2.6) or the Remark 2.8 hybrid combine on the detected set: coef = combine(ghat).
 // The ranking uses integer keys of the buckets (float, double-float pair or double); only the
 // selected median is converted to double.
-template <class TS>
+// HASH: the hashes of Itilde are formed here (and stored for the later stages) instead of by a
+// separate k_det_hashes launch (every combine but the hybrid one, which needs the collision counts
+// of all hashes first).
+template <class TS, bool HASH>
 __global__ void k_combine(const InstDesc* __restrict__ insts) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nd = min(I.cnt[0], I.cap);
@@ -748,13 +755,27 @@ __global__ void k_combine(const InstDesc* __restrict__ insts) {
         c32 la = {0.f, 0.f}, lb = {0.f, 0.f};
         int fa = 0, fb = 0;  // collision-free flags (hybrid)
         if (lane < L) {
-            const int64_t b = I.soff[lane] + I.H[q * L + lane];
+            int32_t h;
+            if constexpr (HASH) {
+                h = det_hash(I, q, lane);
+                I.H[q * L + lane] = h;
+            } else {
+                h = I.H[q * L + lane];
+            }
+            const int64_t b = I.soff[lane] + h;
             ha = g[b];
             if (glo) la = glo[b];
             if (hybrid) fa = I.coll[b] == 1;
         }
         if (lane + 32 < L) {
-            const int64_t b = I.soff[lane + 32] + I.H[q * L + lane + 32];
+            int32_t h;
+            if constexpr (HASH) {
+                h = det_hash(I, q, lane + 32);
+                I.H[q * L + lane + 32] = h;
+            } else {
+                h = I.H[q * L + lane + 32];
+            }
+            const int64_t b = I.soff[lane + 32] + h;
             hb = g[b];
             if (glo) lb = glo[b];
             if (hybrid) fb = I.coll[b] == 1;
@@ -1439,8 +1460,13 @@ int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int 
         else k_refine_update<double, false><<<dim3(gx, ninst), 256, 0, st>>>(di);
         return launch_check("k_refine_update");
     }
-    if (prec) k_combine<float><<<dim3(gx, ninst), 256, 0, st>>>(di);
-    else k_combine<double><<<dim3(gx, ninst), 256, 0, st>>>(di);
+    if (mode == 3) {  // combine that forms the hashes of Itilde itself
+        if (prec) k_combine<float, true><<<dim3(gx, ninst), 256, 0, st>>>(di);
+        else k_combine<double, true><<<dim3(gx, ninst), 256, 0, st>>>(di);
+    } else {
+        if (prec) k_combine<float, false><<<dim3(gx, ninst), 256, 0, st>>>(di);
+        else k_combine<double, false><<<dim3(gx, ninst), 256, 0, st>>>(di);
+    }
     return launch_check("k_combine");
 }
 
