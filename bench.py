@@ -251,6 +251,35 @@ def traffic_from_profiles(kernel, units):
     return None
 
 
+# ------------------------------------------------------------------ one-transfer input packing
+def pack_layout(pieces, align=256):
+    """Byte offsets of numpy arrays packed back to back at `align`-byte boundaries, and the total."""
+    offs, o = [], 0
+    for p_ in pieces:
+        offs.append(o)
+        o += (p_.nbytes + align - 1) // align * align
+    return offs, o
+
+
+def pack_into(buf, pieces, offs):
+    """Copy the arrays' bytes into the uint8 tensor `buf` at `offs`."""
+    import numpy as np
+    import torch
+    for p_, o_ in zip(pieces, offs):
+        buf[o_:o_ + p_.nbytes].copy_(torch.from_numpy(np.ascontiguousarray(p_).view(np.uint8).reshape(-1)))
+
+
+def unpack_views(buf, pieces, offs):
+    """Typed, shaped views of a uint8 tensor laid out by pack_layout (no copies)."""
+    import numpy as np
+    import torch
+    out = []
+    for p_, o_ in zip(pieces, offs):
+        t = buf[o_:o_ + p_.nbytes].view(torch.from_numpy(np.empty(0, dtype=p_.dtype)).dtype)
+        out.append(t.view(p_.shape))
+    return out
+
+
 # ------------------------------------------------------------------ multi-rank helpers (replicas)
 def rank_seeds(rank, n_inst):
     """Seeds of this rank's instances: every rank reconstructs its own n_inst instances."""
@@ -462,20 +491,12 @@ def run_native(a, rank, world):
     pieces = []
     for i in range(n_inst):
         pieces += [h8[i], hkv[i], host[i][2], hnz[i]]
-    offs, o = [], 0
-    for p_ in pieces:
-        offs.append(o)
-        o += (p_.nbytes + 255) // 256 * 256
-    h2d = o
+    offs, h2d = pack_layout(pieces)
     hbuf = torch.empty(h2d, dtype=torch.uint8).pin_memory()
-    for p_, o_ in zip(pieces, offs):
-        hbuf[o_:o_ + p_.nbytes].copy_(torch.from_numpy(np.ascontiguousarray(p_).view(np.uint8).reshape(-1)))
+    pack_into(hbuf, pieces, offs)
 
     def views(dbuf):
-        v = []
-        for p_, o_ in zip(pieces, offs):
-            t = dbuf[o_:o_ + p_.nbytes].view(torch.from_numpy(np.empty(0, dtype=p_.dtype)).dtype)
-            v.append(t.view(p_.shape))
+        v = unpack_views(dbuf, pieces, offs)
         return v[0::4], v[1::4], v[2::4], v[3::4]
 
     sets = []

@@ -274,12 +274,12 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
 /*
  * Per-stage GPU time of the batch's stage sequence, measured with CUDA events on the batch
  * stream around each stage of every call since the last reset.  Stage order: clear, lattice
- * DFT (Algorithm 2), zero test, hash + count, compaction, hashes of Itilde, combine,
- * refinement scatter, refinement model IDFT (FP64), refinement DFT, refinement update,
- * Algorithm 4 selection.  ms / launches: host arrays of 12 entries (optional) receive the
- * accumulated milliseconds and the number of timed calls.  mode = 1 enables timing (graph
- * batches then run eagerly), 0 disables it, both reset the totals; mode = -1 only reads.
- * Returns the number of stages (12) or -1.
+ * DFT (Algorithm 2), zero test, hash + count, compaction, hashes of Itilde (a separate launch
+ * only for the hybrid combine; else formed by the combine), combine, least squares (Remark
+ * 2.8), refinement scatter, refinement update, Algorithm 4 selection.  ms / launches: host
+ * arrays of 11 entries (optional) receive the accumulated milliseconds and the number of timed
+ * calls.  mode = 1 enables timing (graph batches then run eagerly), 0 disables it, both reset
+ * the totals; mode = -1 only reads.  Returns the number of stages (11) or -1.
  */
 int sfft_batch_timing(sfft_batch* b, int mode, double* ms, int64_t* launches);
 

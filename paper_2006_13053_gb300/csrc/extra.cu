@@ -97,6 +97,7 @@ struct Batch {
     // upload the current descriptors through the next ring slot (eager calls)
     int stage_upload() {
         const int n = (int)plans.size();
+        // a byte comparison: h_dev is a byte copy of h_inst, so padding bytes compare equal too
         if (memcmp(h_dev.data(), h_inst, sizeof(InstDesc) * n) == 0) return SFFT_OK;
         memcpy(h_dev.data(), h_inst, sizeof(InstDesc) * n);
         const int k = ring_next;
