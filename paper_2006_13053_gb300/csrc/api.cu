@@ -464,7 +464,7 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
     for (const auto& f : a.fwd)
         SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.mode, a.fwd_prec, a.prec, a.prec, -1, EPI_ANALYZE, a.d_inst,
                                   st, nullptr, nullptr, f.threads));
-    // zero test with FP64 re-tests inside the guard band (Remark 2.3); unit roundoff of the
+    // zero test with direct re-tests inside the guard band (Remark 2.3); unit roundoff of the
     // transform arithmetic (double-float: 2^-44, a bound with margin for its ~48-bit operations)
     SFFT_TRY(mark(a, ST_ZERO_TEST, st));
     const double u = a.fwd_prec == 1 ? 5.9604644775390625e-08 : a.fwd_prec == 2 ? 5.684341886080802e-14

@@ -3,9 +3,10 @@
 // decimation-in-frequency FFT (natural order in, digit-reversed out), a pointwise product with
 // the precomputed filter (itself stored digit-reversed) and the matching decimation-in-time
 // inverse (digit-reversed in, natural order out), so no reordering pass is needed.  One CTA
-// transforms one lattice; the work buffer lives in shared memory when N complex values fit,
-// otherwise in an L2-resident global scratch buffer.  Included by one translation unit per
-// arithmetic type (fft_f64.cu, fft_f32.cu, fft_df64.cu).
+// transforms one lattice; the work buffer lives in shared memory when N complex values fit, in
+// the shared memory of a two-CTA cluster when half of them fit, otherwise in an L2-resident
+// global scratch buffer.  Included by one translation unit per arithmetic type (fft_f64.cu,
+// fft_f32.cu, fft_df64.cu).
 #pragma once
 #include <math.h>
 
@@ -251,8 +252,9 @@ struct TwRow<R1, R2, float, TwTwo> {
 // tw(n2 s1 (p1 + R1 p2)) per output: R1 R2 - 1 table twiddles instead of 2 R1 R2 - R1 - R2.
 // The block index b = floor(i / m2) is formed with a float reciprocal: (i + 1/2) / m2 is at least
 // 1/(2 m2) away from an integer, which the float product resolves exactly for i < 2^22.
-// C supplies the buffer accesses (c.dif_load / c.dif_store / c.dit_load / c.dit_store), which
-// fold the input load, the filter product and the output epilogue into the first and last pass.
+// C supplies the buffer accesses (c.dif_load / c.dif_store / c.dit_load / c.dit_store: the work
+// buffer's layout); the input, the filter product and the output are handled outside the generic
+// passes (BlueIo's phases and mid_pass).
 template <int R1, int R2, int S, class T, class TW, class C>
 __device__ __forceinline__ void dif_pass(C& c, int Ns, const TW& tw) {
     const int N = c.N, m1 = Ns / R1, m2 = m1 / R2, s1 = N / Ns, ng = N / (R1 * R2);

@@ -161,7 +161,7 @@ struct BlueJob {
     const void* twb;
     const void* chirp;
     const void* filt;    // filter of the requested direction
-    const double* dft64; // FP64 single-bucket table (guard re-tests)
+    const double* dft64; // single-bucket root table (guard re-tests of FP64 samples)
     struct LatStats* stat; // side outputs of EPI_ANALYZE
     double scale;        // output scale (1/M for the normalised forward DFT)
     int M, N, nstages, tw_na;

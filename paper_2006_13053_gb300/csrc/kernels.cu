@@ -1,5 +1,5 @@
 // Per-lattice and per-candidate kernels of the reconstruction (Algorithms 1, 2 and 4):
-//   zero test of the lattice DFT buckets with FP64 re-tests near the threshold (Remark 2.3),
+//   zero test of the lattice DFT buckets with direct re-tests near the threshold (Remark 2.3),
 //   candidate hashing k.z_l mod M_l and the majority count (Algorithm 1/2, count rule),
 //   ascending compaction of the detected set, the per-candidate gather and component-wise
 //   median (eq. 2.6), bucket collision counts and the Remark 2.8 combine, the refinement
@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
         if (glo) { c32 w = glo[h]; r.x += (double)w.x; r.y += (double)w.y; }
         return r;
     };
-    auto store = [&](int h, c64 v) {  // replace a bucket by its FP64 direct value
+    auto store = [&](int h, c64 v) {  // replace a bucket by its directly summed value
         cplx<TS> hi = cvt<TS>(v);
         g[h] = hi;
         if (glo) glo[h] = c32{(float)(v.x - (double)hi.x), (float)(v.y - (double)hi.y)};
@@ -145,10 +145,10 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
     __syncthreads();
     // Squared magnitudes are formed in the working precision and compared with bounds widened
     // by a relative slack that covers their rounding; only buckets between the bounds need the
-    // FP64 re-test.
+    // direct re-test.
     const double slack = sizeof(TS) == 4 ? 1e-6 : 1e-15;
     const double big = sizeof(TS) == 4 ? 3.0e38 : 1.0e300;
-    // ---- exact maximum: FP64 re-test of every bucket that could be the maximum
+    // ---- exact maximum: direct re-test of every bucket that could be the maximum
     double tau = I.tau_abs;
     if (I.tau_rel > 0) {
         if (threadIdx.x == 0) {
