@@ -27,6 +27,9 @@ Parity status of each function (pins live in tests/test_oracle_*.py):
   dim_incremental                                                pinned (exact recovery,
         Table 4.2 sample-count rule)
   sop_* (sum-of-products test function)                          pinned (FFT on a grid)
+  bspline_* (Section 4.3 test function), relative_l2_error,      pinned (FFT of the closed
+        hyperbolic_cross                                         form, unit norm, m = 2 hat,
+                                                                 quadrature, brute-force set)
   reconstruct_vjp (adjoint)                                      pinned (FP64 finite
         differences)
   philox4x64                                                     pinned (numpy Philox)
@@ -320,6 +323,113 @@ def sop_norm2(triples, theta, K=48, width=32.0):
                     prod *= float(a[q][K])
             tot += prod
     return tot
+
+
+# --------------------------------------------------------------------------- B-spline test function
+# Section 4.3's approximately sparse test function (eq. 4.3): a sum over terms of products of
+# periodic B-splines N_m(x_t), N_m(x) = C_m sum_k sinc(pi k / m)^m (-1)^k e^{2 pi i k x} with C_m
+# such that ||N_m||_{L2(T)} = 1.  In the time domain N_m is one scaled cardinal B-spline per
+# period: N_m(x) = C_m m phi_m(m (x - 1/2)) on [0, 1), phi_m the centred cardinal B-spline of
+# order m (support [-m/2, m/2], Fourier transform sinc(w/2)^m); then sum_k sinc(pi k/m)^(2m)
+# = m * integral phi_m^2 = m phi_2m(0), so C_m = (m phi_2m(0))^(-1/2).
+def bspline_centered(m: int, t):
+    """phi_m(t) by the truncated-power sum (1/(m-1)!) sum_j (-1)^j binom(m, j) (t + m/2 - j)_+^(m-1),
+    evaluated at -|t| (phi_m is even; on the left half fewer terms are non-zero, so the sum
+    cancels less)."""
+    t = -np.abs(np.asarray(t, dtype=np.float64))
+    out = np.zeros_like(t)
+    for j in range(m + 1):
+        u = t + m / 2.0 - j
+        out += (-1) ** j * math.comb(m, j) * np.where(u > 0, u, 0.0) ** (m - 1)
+    out /= math.factorial(m - 1)
+    return np.where(np.abs(t) < m / 2.0, out, 0.0)
+
+
+def bspline_norm_const(m: int) -> float:
+    """C_m with ||N_m||_{L2(T)} = 1."""
+    return 1.0 / math.sqrt(m * float(bspline_centered(2 * m, 0.0)))
+
+
+def bspline_periodic(m: int, x):
+    """N_m(x) for x in T (any real x, reduced mod 1)."""
+    x = np.mod(np.asarray(x, dtype=np.float64), 1.0)
+    return bspline_norm_const(m) * m * bspline_centered(m, m * (x - 0.5))
+
+
+def bspline_coef(m: int, k):
+    """Fourier coefficients of N_m: C_m sinc(pi k/m)^m (-1)^k (sinc(0) = 1)."""
+    k = np.asarray(k, dtype=np.float64)
+    return bspline_norm_const(m) * np.sinc(k / m) ** m * np.where(np.mod(k, 2) == 0, 1.0, -1.0)
+
+
+def bspline_sop_eval(terms, x):
+    """f(x) = sum over terms (dims, m) of prod_{t in dims} N_m(x_t); x: [n, d]."""
+    x = np.asarray(x, dtype=np.float64)
+    out = np.zeros(x.shape[0])
+    for dims, m in terms:
+        prod = np.ones(x.shape[0])
+        for t in dims:
+            prod *= bspline_periodic(m, x[:, t])
+        out += prod
+    return out
+
+
+def bspline_sop_fourier(terms, kvec):
+    """fhat(k): a term contributes prod_{t in dims} coef_m(k_t) when k vanishes off its dims."""
+    kvec = np.asarray(kvec, dtype=np.int64)
+    out = np.zeros(kvec.shape[0])
+    for dims, m in terms:
+        off = np.ones(kvec.shape[1], dtype=bool)
+        off[list(dims)] = False
+        prod = np.where(np.all(kvec[:, off] == 0, axis=1), 1.0, 0.0)
+        for t in dims:
+            prod = prod * bspline_coef(m, kvec[:, t])
+        out += prod
+    return out
+
+
+def bspline_sop_norm2(terms, K=1 << 16):
+    """||f||_{L2}^2 = sum over pairs of terms of <A, B>: per dimension <N_a, N_b> where both act
+    (1 for equal orders, else Parseval over |k| <= K), the mean C_m of the one that acts alone,
+    1 elsewhere."""
+    tot = 0.0
+    ks = np.arange(-K, K + 1)
+    for dims_a, ma in terms:
+        for dims_b, mb in terms:
+            prod = 1.0
+            for t in set(dims_a) | set(dims_b):
+                if t in dims_a and t in dims_b:
+                    prod *= 1.0 if ma == mb else float(np.sum(bspline_coef(ma, ks) * bspline_coef(mb, ks)))
+                elif t in dims_a:
+                    prod *= bspline_norm_const(ma)
+                else:
+                    prod *= bspline_norm_const(mb)
+            tot += prod
+    return tot
+
+
+def relative_l2_error(terms, kvec, coef):
+    """||f - p|| / ||f|| for p = sum_{k in I} coef_k e^{2 pi i k.x} (Section 4.3's formula):
+    sqrt(||f||^2 - sum_I |fhat_k|^2 + sum_I |coef_k - fhat_k|^2) / ||f||."""
+    fh = bspline_sop_fourier(terms, kvec)
+    n2 = bspline_sop_norm2(terms)
+    e2 = n2 - float(np.sum(np.abs(fh) ** 2)) + float(np.sum(np.abs(np.asarray(coef) - fh) ** 2))
+    return math.sqrt(max(e2, 0.0) / n2)
+
+
+def hyperbolic_cross(t: int, N: int) -> np.ndarray:
+    """Symmetric hyperbolic cross {k in Z^t : prod_i max(1, |k_i|) <= N}, lexicographic."""
+    pts = [()]
+    for _ in range(t):
+        nxt = []
+        for p in pts:
+            bound = N
+            for v in p:
+                bound //= max(1, abs(v))
+            for v in range(-bound, bound + 1):
+                nxt.append(p + (v,))
+        pts = nxt
+    return np.array(sorted(pts), dtype=np.int64)
 
 
 # =========================================================================== lattice DFT (Algorithm 2)
