@@ -210,6 +210,20 @@ int sfft_sample_sop(const sfft_plan* plan, const int32_t* triples, const double*
 int sfft_sample_sop_backward(const sfft_plan* plan, const int32_t* triples, const double* theta, int n_terms,
                              int K, double width, const void* dsamples, double* dtheta);
 
+/*
+ * Samples of Section 4.3's test function (eq. 4.3), a sum of products of periodic B-splines,
+ *   f(x) = sum_{q < n_terms} prod_{t in dims_q} N_{m_q}(x_t),
+ *   N_m(x) = C_m sum_k sinc(pi k/m)^m (-1)^k exp(2 pi i k x),  ||N_m||_{L2(T)} = 1,
+ * at the plan's lattice nodes.  dims: host int32 [n_terms, 4], the term's distinct dimensions
+ * (< d; a -1 ends a term with fewer than 4); orders: host int32 [n_terms], 1 <= m <= 12;
+ * 1 <= n_terms <= 8.  N_m is evaluated in closed form (one scaled cardinal B-spline per period,
+ * Cox-de Boor recurrence in FP64), so the samples carry rounding only.  samples_out: device
+ * complex in the plan precision (imaginary parts 0).  Asynchronous on the plan stream.
+ * Errors: SFFT_EINVAL for a bad term.
+ */
+int sfft_sample_bspline(const sfft_plan* plan, const int32_t* dims, const int32_t* orders, int n_terms,
+                        void* samples_out);
+
 /* ---------------------------------------------------------------- batched reconstruction */
 typedef struct sfft_batch sfft_batch;
 

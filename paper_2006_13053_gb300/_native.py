@@ -90,6 +90,7 @@ sfft_reconstruct = _sig("sfft_reconstruct", _i32, [_vp, _vp, _vp, _vp, _i64, _P(
 sfft_reconstruct_backward = _sig("sfft_reconstruct_backward", _i32, [_vp, _vp, _vp])
 sfft_sample_sparse_poly = _sig("sfft_sample_sparse_poly", _i32, [_vp, _vp, _vp, _i64, _vp, _vp])
 sfft_sample_sop = _sig("sfft_sample_sop", _i32, [_vp, _vp, _vp, _i32, _i32, _dbl, _vp])
+sfft_sample_bspline = _sig("sfft_sample_bspline", _i32, [_vp, _vp, _vp, _i32, _vp])
 sfft_sample_sop_backward = _sig("sfft_sample_sop_backward", _i32, [_vp, _vp, _vp, _i32, _i32, _dbl, _vp, _vp])
 sfft_batch_create = _sig("sfft_batch_create", _i32, [_P(_vp), _vp, _i32, _i32, _vp])
 sfft_batch_destroy = _sig("sfft_batch_destroy", None, [_vp])

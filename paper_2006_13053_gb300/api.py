@@ -115,6 +115,21 @@ class Plan:
                                   float(width), _ptr(out)))
         return out
 
+    def sample_bspline(self, terms, out=None):
+        """Section 4.3's test function (eq. 4.3) at the lattice nodes: terms = [(dims, m), ...],
+        f(x) = sum over terms of prod_{t in dims} N_m(x_t) (periodic B-splines, unit L2 norm)."""
+        dims = np.full((len(terms), 4), -1, dtype=np.int32)
+        orders = np.zeros(len(terms), dtype=np.int32)
+        for q, (dq, m) in enumerate(terms):
+            if len(dq) > 4:
+                raise ValueError("a B-spline term acts on at most 4 dimensions")
+            dims[q, :len(dq)] = dq
+            orders[q] = m
+        out = out if out is not None else torch.empty(self.n_samples, dtype=self.cdtype, device=self.cand.device)
+        N.check(N.sfft_sample_bspline(self.handle, dims.ctypes.data_as(C.c_void_p), orders.ctypes.data_as(C.c_void_p),
+                                      len(terms), _ptr(out)))
+        return out
+
     def sample_sop_backward(self, triples, theta, dsamples, K=48, width=32.0):
         tri = np.ascontiguousarray(np.asarray(triples, dtype=np.int32))
         _req(theta, torch.float64, "theta")
