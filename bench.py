@@ -284,6 +284,62 @@ def traffic_from_profiles(kernel, units):
     return None
 
 
+def inst_from_profiles(kernel):
+    """Warp instructions per unit of `kernel` from the committed ncu summary (or None)."""
+    import glob
+    for f in glob.glob(os.path.join(ROOT, "profiles", "*.txt")):
+        for line in open(f):
+            if line.startswith("inst_per_unit") and f"kernel={kernel}" in line:
+                kv = dict(tok.split("=") for tok in line.split()[1:] if "=" in tok)
+                return float(kv["warp_inst_per_unit"])
+    return None
+
+
+# the packed hash kernel's candidate-to-warp mapping (csrc/kernels.cu: kHashThreads threads per CTA,
+# kCPT2 candidates per thread at tile offsets thread + c * kHashThreads; the count-rule exit is
+# tested after every second lattice)
+HASH_THREADS, HASH_CPT = 256, 4
+
+
+def executed_hash_evals(plan, samples):
+    """Candidate-lattice evaluations that the packed hash kernel executes for one reconstruction:
+    a warp evaluates its 4 x 32 candidates on lattice after lattice and stops after lattice l
+    (l odd) once no candidate can still reach the count threshold ceil(nu L) with the L - 1 - l
+    lattices left.  Replayed from the per-lattice non-zero indicators of the reconstruction's
+    diagnostics (hashes, lattice DFTs, thresholds), with the kernel's candidate-to-warp mapping."""
+    import torch
+    _, _, info = plan.reconstruct(samples, diag=True, hashes=True)
+    H = info["hashes"].long()
+    n, L = H.shape
+    need = math.ceil(plan.params.nu * L - 1e-9)
+    g, tau, offs = info["ghat"], info["tau"], plan.offsets
+    nz = torch.zeros((n, L), dtype=torch.int16, device=H.device)
+    for l in range(L):
+        nz[:, l] = (g[int(offs[l]):int(offs[l + 1])].abs() > tau[l])[H[:, l]].to(torch.int16)
+    return executed_from_indicators(nz, need)
+
+
+def executed_from_indicators(nz, need):
+    """Executed evaluations for per-candidate, per-lattice non-zero indicators nz [n, L] (0/1) and
+    the count threshold `need` (see executed_hash_evals)."""
+    import torch
+    n, L = nz.shape
+    tile = HASH_THREADS * HASH_CPT
+    T = (n + tile - 1) // tile
+    cnt = torch.zeros((T * tile, L), dtype=torch.int16, device=nz.device)
+    cnt[:n] = torch.cumsum(nz.to(torch.int16), dim=1).to(torch.int16)
+    rem = torch.arange(L - 1, -1, -1, device=nz.device, dtype=torch.int16)
+    alive = (cnt + rem[None, :]) >= need                                   # [T*tile, L]
+    # tile-local index i = c * HASH_THREADS + thread, warp = thread // 32
+    alive = alive.view(T, HASH_CPT, HASH_THREADS // 32, 32, L).any(dim=3).any(dim=1)  # [T, warps, L]
+    check = torch.zeros(L, dtype=torch.bool, device=nz.device)
+    check[1::2] = True
+    dead = (~alive) & check[None, None, :]
+    first = torch.where(dead.any(dim=2), dead.to(torch.int8).argmax(dim=2) + 1,
+                        torch.full(dead.shape[:2], L, dtype=torch.long, device=nz.device))
+    return int(first.sum().item()) * 32 * HASH_CPT
+
+
 # ------------------------------------------------------------------ one-transfer input packing
 def pack_layout(pieces, align=256):
     """Byte offsets of numpy arrays packed back to back at `align`-byte boundaries, and the total."""
@@ -421,6 +477,9 @@ def run_native(a, rank, world):
     # instance 0's result of these steps, for the accuracy check against the oracle
     s0_, c0_ = batch.results()[0]
     res0 = (s0_.cpu().numpy(), c0_.cpu().numpy())
+    # candidate-lattice evaluations the hash kernel executes (early exit), replayed for instance 0
+    # and scaled to the batch (all instances have the same shape and statistics)
+    executed_evals = executed_hash_evals(plans[0], smp[0]) * n_inst
     ms = max_over_ranks(ms, world, dev)
     value = whole_job_value(world, n_inst, ms)
     stage_ms = {k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1] > 0}
@@ -457,20 +516,38 @@ def run_native(a, rank, world):
     src = "of measured" if "hbm_gbs" in peaks else "of fallback"
     mhz = peaks.get("sm_max_mhz", 2070.0)
 
+    clk_mhz = out["clocks"].get("sm_mhz") or mhz
+
     def roofline(stage):
         t = stage_ms[stage] / 1000.0
         if stage == "hash_count":
-            # instruction-issue bound: candidate-lattice evaluations (all L lattices of every
-            # candidate, Algorithm 2's count rule) against the issue rate / the minimal
-            # instruction count of one evaluation
-            ev = n_inst * NCAND * L
-            pk = FP32_LANES * mhz * 1e6 / HASH_INSTR_PER_EVAL / 1e12
-            return {"kernel": "k_hash_count_packed", "bound": "alu", "achieved": ev / t / 1e12, "peak": pk,
-                    "unit": "T evaluations/s", "frac": ev / t / 1e12 / pk,
-                    "peak_source": f"derived: 152 SMs x 128 lanes x {mhz:.0f} MHz / {HASH_INSTR_PER_EVAL} "
-                                   "instructions per candidate-lattice evaluation",
-                    "hbm_frac": n_inst * NCAND * ROW8 / t / 1e9 / hbm,
-                    "traffic": traffic_from_profiles(f"k_hash_count_i8_ld{ROW8}", n_inst * NCAND)}
+            # HBM roofline of the hash + count kernel: the candidate rows are its algorithmic bytes
+            # (ROW8 bytes per candidate in the compact int8 layout, read once per reconstruction)
+            units = n_inst * NCAND
+            bytes_ = units * ROW8
+            ex = executed_evals
+            wi = inst_from_profiles(f"k_hash_count_i8_ld{ROW8}")
+            alu = {"evaluations_nominal": units * L, "evaluations_executed": ex,
+                   "executed_per_candidate": ex / units,
+                   "executed_evals_per_s": ex / t,
+                   "why": "warps stop once none of their 128 candidates can reach the count threshold; "
+                          "executed = sum over warps of 128 x lattices visited, replayed from instance 0's "
+                          "per-lattice non-zero indicators with the kernel's candidate-to-warp mapping"}
+            if wi is not None:
+                ipeak = 152 * 4 * clk_mhz * 1e6  # warp instructions per second: 4 schedulers per SM
+                alu.update({"warp_inst_per_candidate": wi, "issue_achieved": wi * units / t, "issue_peak": ipeak,
+                            "issue_frac": wi * units / t / ipeak,
+                            "issue_peak_source": f"152 SMs x 4 schedulers x 1 warp instruction/cycle x "
+                                                 f"{clk_mhz:.0f} MHz (median SM clock of the timed region); "
+                                                 "warp instructions per candidate from the committed ncu summary"})
+                if ex:
+                    alu["thread_inst_per_executed_eval"] = wi * units * 32 / ex
+            return {"kernel": "k_hash_count_packed", "bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm,
+                    "unit": "GB/s", "frac": bytes_ / t / 1e9 / hbm, "peak_source": src,
+                    "algorithmic_bytes_per_candidate": ROW8, "candidates_per_launch": units,
+                    "traffic": traffic_from_profiles(f"k_hash_count_i8_ld{ROW8}", units),
+                    "int32_layout_bytes_per_candidate": 4 * D,
+                    "alu": alu}
         if stage == "fft_fwd":
             flops = n_inst * L * bluestein_flops(20736, M)
             if a.dft == "df64":
@@ -664,8 +741,22 @@ def run_native(a, rank, world):
             b32.reconstruct_async(smp)
     i1.record(st)
     i1.synchronize()
+    b32.timing(1)
+    with torch.cuda.stream(st):
+        for _ in range(3):
+            b32.sample_sparse_poly(kv, cf, nz, outs=smp)
+            b32.reconstruct_async(smp)
+    st.synchronize()
+    t32 = b32.timing(0)["hash_count"]
+    h32 = t32[0] / max(t32[1], 1)
     out["int32_rows"] = {"ms_per_step": i0.elapsed_time(i1) / a.steps,
-                         "value": n_inst / (i0.elapsed_time(i1) / a.steps / 1000.0), "unit": "reconstructions/s"}
+                         "value": n_inst / (i0.elapsed_time(i1) / a.steps / 1000.0), "unit": "reconstructions/s",
+                         "hash_count_ms": h32}
+    if out["roofline"].get("kernel") == "k_hash_count_packed":
+        by = n_inst * NCAND * 4 * D  # int32 rows: 4 d bytes per candidate (the layout of the C ABI's default)
+        out["roofline"]["int32_layout"] = {"bytes_per_candidate": 4 * D, "hash_count_ms": h32,
+                                           "achieved": by / (h32 / 1000.0) / 1e9,
+                                           "frac": by / (h32 / 1000.0) / 1e9 / out["roofline"]["peak"]}
     b32.close()
     # ---- the same step with the other forward-DFT arithmetic under the refinement
     other = "df64" if a.dft == "fp32" else "fp32"
@@ -766,12 +857,37 @@ def run_reference(a):
             "e2e": {"value": v, "unit": "reconstructions/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def rank_plan(gpus, env):
+    """How this invocation runs on `gpus` GPUs: ("run", world) when the ranks already exist
+    (torchrun set WORLD_SIZE = gpus, or a single GPU), ("spawn", gpus) when bench.py must start
+    the gpus ranks itself, ("refuse", message) when WORLD_SIZE disagrees with --gpus."""
+    world = env.get("WORLD_SIZE")
+    if world is None:
+        return ("run", 1) if gpus <= 1 else ("spawn", gpus)
+    if int(world) != gpus:
+        return ("refuse", f"WORLD_SIZE={world} but --gpus {gpus}: launch one rank per GPU (torchrun "
+                          f"--nproc-per-node {gpus}) or omit WORLD_SIZE and let bench.py start them")
+    return ("run", int(world))
+
+
+def spawn_ranks(gpus):
+    """Start `gpus` ranks of this script through torch.distributed.run (one process per GPU,
+    rendezvous on 127.0.0.1) and return their exit status."""
+    import socket
+    sk = socket.socket()
+    sk.bind(("127.0.0.1", 0))
+    port = sk.getsockname()[1]
+    sk.close()
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={gpus}",
+           "--master-addr", "127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd)
+
+
 def main():
     a = parse()
     if a.cpu_baseline_worker is not None:
         cpu_baseline_worker(a.cpu_baseline_worker)
         return
-    world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if a.impl == "reference":
         if rank != 0:
@@ -780,6 +896,13 @@ def main():
             os.environ.setdefault(var, "1")  # one thread per oracle process
         print(json.dumps(run_reference(a)), flush=True)
         return
+    how, arg = rank_plan(a.gpus, os.environ)
+    if how == "refuse":
+        print(json.dumps({"error": arg}), flush=True)
+        sys.exit(2)
+    if how == "spawn":
+        sys.exit(spawn_ranks(arg))
+    world = arg
     import torch
     if world > 1:
         torch.distributed.init_process_group("nccl")

@@ -111,8 +111,10 @@ typedef struct sfft_plan sfft_plan;
 
 /*
  * Create a plan for candidates Gamma = cand (device, row-major [n_cand] rows of d entries of the
- * type p->cand_type: int32, or int8 rows of stride p->cand_ld bytes with the pointer 4-byte
- * aligned; not copied: it must stay valid and unchanged until the plan is destroyed) and
+ * type p->cand_type: int32 rows with the pointer 16-byte aligned when d % 4 == 0 and 8-byte
+ * aligned when d % 2 == 0 (they are read as vector words), or int8 rows of stride p->cand_ld
+ * bytes with the pointer 4-byte aligned; a misaligned pointer returns SFFT_EINVAL before any
+ * device work.  Not copied: it must stay valid and unchanged until the plan is destroyed) and
  * sparsity s.
  *   L     > 0: number of lattices (must be odd for the median, Algorithm 2), or 0: take L
  *              from p->L_rule with |Gamma| = n_cand (Corollary 2.6 / eq. 4.2 / fallback).
@@ -343,12 +345,15 @@ int sfft_fn_sop(void* ctx, const double* x, int64_t n, double* y, void* stream);
 
 /* ---------------------------------------------------------------- allocation-free detection */
 /*
- * The detection step of sfft_reconstruct (zero test, candidate hashing with the count rule of
- * Algorithm 1/2, ascending compaction of Itilde) for callers that cannot allocate device
- * memory: code running where cudaMalloc is forbidden or may fail at a bad moment (inside host
- * callbacks, under a custom or capped allocator, in a long-running service that must not grow
- * its footprint).  The paper has no counterpart; it is an interface convenience.
- *   cand   device int32 [n_cand, d];  M, z host int64 [L], [L, d] (z < M);
+ * The detection step of sfft_reconstruct (zero test, candidate hashing with the count rule
+ * "detected iff #{l : |ghat^(l)_{k.z_l mod M_l}| > tau_l} >= nu L", ascending compaction of
+ * Itilde) for callers that cannot allocate device memory: code running where cudaMalloc is
+ * forbidden or may fail at a bad moment (inside host callbacks, under a custom or capped
+ * allocator, in a long-running service that must not grow its footprint).  The paper has no
+ * counterpart; it is an interface convenience.
+ *   cand   device int32 [n_cand, d], starting 16-byte aligned when d % 4 == 0, 8-byte aligned
+ *          when d % 2 == 0 (the rows are read as vector words; else SFFT_EINVAL);
+ *   M, z   host int64 [L], [L, d] (z < M);
  *   ghat   device complex double [sum M]: the normalised lattice DFTs (e.g. sfft_diag.ghat);
  *   tau    host double [L]: zero-test thresholds (|ghat| > tau_l counts as non-zero);
  *   nu     count rule: detected iff #{l : non-zero} >= nu L;
@@ -356,9 +361,11 @@ int sfft_fn_sop(void* ctx, const double* x, int64_t n, double* y, void* stream);
  * Nothing is allocated: the scratch lives in one fixed 8 MiB device array owned by the library,
  * held by every GPU that loads it until the process exits.  Sizes beyond it (about 6.4e7
  * candidates with small lattices, less with large sum M) return SFFT_ECAPACITY, as does a
- * detected set larger than cap.  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress); make that first call before any stream capture.  All calls share
- * the array: calls that overlap on the GPU race, so serialise them.  Synchronises `stream`.
+ * detected set larger than cap.  Every call looks the array's address up on the current device
+ * (cudaGetSymbolAddress), so a device reset between calls is harmless; the first call on a device
+ * also loads the library's device code there, so make that first call before any stream capture.
+ * All calls share the array and it keeps the last call's contents (each call clears what must
+ * start at zero): calls that overlap on the GPU race, so serialise them.  Synchronises `stream`.
  */
 int sfft_detect_noalloc(int d, const int32_t* cand, int64_t n_cand, int L, const int64_t* M, const int64_t* z,
                         const double* ghat, const double* tau, double nu, int64_t* detected_out, int64_t cap,

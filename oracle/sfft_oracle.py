@@ -771,7 +771,9 @@ def dim_incremental_sample_count(d, K, s, delta=0.9, c=C_DEFAULT, r=1, J2=None, 
 
 # =========================================================================== adjoint (oracle gradient)
 def median_selection(vals: np.ndarray):
-    """Index l* of the median element of Re and of Im per row (ties: lowest l)."""
+    """Index l* of the median element of Re and of Im per row.  Equal values keep lattice order (a
+    stable sort), so within a run of tied values the selected lattice is the one at the middle
+    rank (L-1)/2 of that order, not necessarily the lowest l of the run."""
     L = vals.shape[1]
     mid = (L - 1) // 2
     lre = np.argsort(vals.real, axis=1, kind="stable")[:, mid]

@@ -8,7 +8,10 @@
 #include <string.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "common.cuh"
@@ -28,6 +31,20 @@ void set_error(const char* fmt, ...) {
     g_err = buf;
 }
 const char* get_error() { return g_err.c_str(); }
+
+int allow_smem(const void* kernel, int bytes) {
+    int dev = 0;
+    SFFT_CU(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static std::map<std::pair<const void*, int>, int> done;  // (kernel, device) -> limit set
+    std::lock_guard<std::mutex> lk(mu);
+    const auto key = std::make_pair(kernel, dev);
+    const auto it = done.find(key);
+    if (it != done.end() && it->second >= bytes) return SFFT_OK;
+    SFFT_CU(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    done[key] = bytes;
+    return SFFT_OK;
+}
 
 // ================================================================== Philox4x64-10 (Salmon et al., SC'11)
 uint64_t philox_word0(uint64_t key0, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3) {
@@ -250,6 +267,10 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     SFFT_CHECK(p.dft == SFFT_DFT_DF64 || p.dft == SFFT_DFT_FP32, SFFT_EINVAL, "bad dft arithmetic %d", p.dft);
     if (p.cand_type == SFFT_CAND_I32) {
         SFFT_CHECK(p.cand_ld == 0 || p.cand_ld == d, SFFT_EINVAL, "int32 candidate rows are dense (cand_ld 0 or d)");
+        // the hash kernels read a row as int4 words (d % 4 == 0) or int2 words (d % 2 == 0)
+        const uintptr_t al = d % 4 == 0 ? 16 : d % 2 == 0 ? 8 : 4;
+        SFFT_CHECK((uintptr_t)cand % al == 0, SFFT_EINVAL,
+                   "int32 candidate rows of d = %d must start %d-byte aligned", d, (int)al);
         p.cand_ld = d;
     } else {
         SFFT_CHECK(p.cand_ld >= d, SFFT_EINVAL, "int8 candidate rows need a stride cand_ld >= d (got %d)", p.cand_ld);

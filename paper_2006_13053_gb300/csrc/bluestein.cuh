@@ -732,16 +732,8 @@ int launch_t(const BlueJob* djobs, int njobs, int maxN, int mode, int sign, int 
             set_error("Bluestein length %d does not fit the shared-memory mode %d", maxN, mode);
             return SFFT_EINVAL;
         }
-        static bool attr_done[3] = {false, false, false};  // one attribute call per instantiation
-        if (!attr_done[mode]) {
-            if (mode == 1)
-                SFFT_CU(cudaFuncSetAttribute(k_bluestein<T, TI, TO, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)blue_smem_limit()));
-            else
-                SFFT_CU(cudaFuncSetAttribute(k_bluestein_pair<T, TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)blue_smem_limit()));
-            attr_done[mode] = true;
-        }
+        if (mode == 1) SFFT_TRY(allow_smem((const void*)k_bluestein<T, TI, TO, 1>, (int)blue_smem_limit()));
+        else SFFT_TRY(allow_smem((const void*)k_bluestein_pair<T, TI, TO>, (int)blue_smem_limit()));
         if (mode == 1) k_bluestein<T, TI, TO, 1><<<njobs, threads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
         else k_bluestein_pair<T, TI, TO><<<2 * njobs, threads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
     } else {

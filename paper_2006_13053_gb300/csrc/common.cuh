@@ -102,6 +102,10 @@ const char* get_error();
         }                                     \
     } while (0)
 
+// Raise a kernel's dynamic shared-memory limit to `bytes` on the current device; the attribute is
+// set once per (kernel, device) and the record is guarded by a mutex (thread-safe, multi-GPU).
+int allow_smem(const void* kernel, int bytes);
+
 inline int launch_check(const char* what) {
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {

@@ -219,11 +219,7 @@ __global__ void __launch_bounds__(kTcThreads * kTcGroups) k_hash_count_tc(const 
 }
 
 int launch_hash_count_tc(const InstDesc* di, int ninst, int gx, size_t smem, cudaStream_t st) {
-    static bool attr_done = false;
-    if (!attr_done) {
-        SFFT_CU(cudaFuncSetAttribute(k_hash_count_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-        attr_done = true;
-    }
+    SFFT_TRY(allow_smem((const void*)k_hash_count_tc, 220 * 1024));
     k_hash_count_tc<<<dim3(gx, ninst), kTcThreads * kTcGroups, smem, st>>>(di);
     return launch_check("k_hash_count_tc");
 }

@@ -1378,24 +1378,14 @@ template <int D>
 static int launch_hash_d(const InstDesc* di, int ninst, int gx, size_t smem, int variant, int l0, int l1, int mode,
                          cudaStream_t st) {
     // variant: 0 int32 kernel, 1 packed kernel, 2 packed kernel with diagnostics (3: hash_tc.cu)
-    static bool attr[3] = {false, false, false};
     if (variant == 0) {
-        if (!attr[0]) {
-            SFFT_CU(cudaFuncSetAttribute(k_hash_count<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-            attr[0] = true;
-        }
+        SFFT_TRY(allow_smem((const void*)k_hash_count<D>, 220 * 1024));
         k_hash_count<D><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di, l0, l1, mode);
     } else if (variant == 1) {
-        if (!attr[1]) {
-            SFFT_CU(cudaFuncSetAttribute(k_hash_count_packed<D, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-            attr[1] = true;
-        }
+        SFFT_TRY(allow_smem((const void*)k_hash_count_packed<D, false>, 220 * 1024));
         k_hash_count_packed<D, false><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di, l0, l1, mode);
     } else {
-        if (!attr[2]) {
-            SFFT_CU(cudaFuncSetAttribute(k_hash_count_packed<D, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 220 * 1024));
-            attr[2] = true;
-        }
+        SFFT_TRY(allow_smem((const void*)k_hash_count_packed<D, true>, 220 * 1024));
         k_hash_count_packed<D, true><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di, l0, l1, mode);
     }
     return launch_check("k_hash_count");
@@ -1480,11 +1470,7 @@ int launch_lsq(InstDesc* di, int ninst, int prec, cudaStream_t st) {
     k_lsq_pairs<<<grid, 256, 0, st>>>(di);
     SFFT_TRY(launch_check("k_lsq_pairs"));
     const int smem = 4 * kLsqSmemVec * (int)sizeof(c64);
-    static bool attr_done = false;
-    if (!attr_done) {
-        SFFT_CU(cudaFuncSetAttribute(k_lsq_cg, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr_done = true;
-    }
+    SFFT_TRY(allow_smem((const void*)k_lsq_cg, smem));
     k_lsq_cg<<<ninst, kLsqThreads, smem, st>>>(di, 64, 1e-12);
     return launch_check("k_lsq_cg");
 }

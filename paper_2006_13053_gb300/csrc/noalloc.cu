@@ -12,7 +12,6 @@
 #include <string.h>
 
 #include <algorithm>
-#include <mutex>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -23,26 +22,16 @@ namespace {
 constexpr size_t kScratchBytes = size_t(8) << 20;  // 8 MiB per device
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {nullptr};
-
-// device address of the scratch array on the current device (looked up once per device)
+// device address of the scratch array on the current device.  Looked up at every call (cheap), so
+// that a device reset or a re-created primary context between calls cannot leave a stale address.
 int scratch_address(void** out) {
-    int dev = 0;
-    SFFT_CU(cudaGetDevice(&dev));
-    SFFT_CHECK(dev >= 0 && dev < kMaxDevices, SFFT_EINVAL, "device %d out of range", dev);
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-        if (e != cudaSuccess) {
-            set_error("cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
-            return SFFT_ECUDA;
-        }
-        g_addr[dev] = p;
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+    if (e != cudaSuccess) {
+        set_error("cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+        return SFFT_ECUDA;
     }
-    *out = g_addr[dev];
+    *out = p;
     return SFFT_OK;
 }
 
@@ -82,6 +71,10 @@ extern "C" int sfft_detect_noalloc(int d, const int32_t* cand, int64_t n_cand, i
     SFFT_CHECK(cand && n_cand >= 1 && M && z && ghat && tau && n_detected && (cap == 0 || detected_out), SFFT_EINVAL,
                "null argument");
     SFFT_CHECK(nu > 0 && nu <= 0.5, SFFT_EINVAL, "nu must be in (0, 1/2]");
+    // the hash kernels read an int32 row as int4 words (d % 4 == 0) or int2 words (d % 2 == 0)
+    const uintptr_t al = d % 4 == 0 ? 16 : d % 2 == 0 ? 8 : 4;
+    SFFT_CHECK((uintptr_t)cand % al == 0, SFFT_EINVAL, "candidate rows of d = %d must start %d-byte aligned", d,
+               (int)al);
     // ---- scratch layout (bytes, 256-aligned pieces)
     int64_t words = 0, sumM = 0, maxM = 0;
     for (int l = 0; l < L; ++l) {

@@ -92,6 +92,35 @@ def test_invalid_arguments_rejected_on_host():
     assert f(None, 3, None, 10, 2, 0, None, None, None, None) == 1
 
 
+def test_misaligned_candidate_rows_rejected_on_host():
+    """int32 rows are read as int4 (d % 4 == 0) or int2 (d % 2 == 0) words: a pointer that is only
+    4-byte aligned (a tensor view with an offset) returns SFFT_EINVAL before any device work, from
+    the plan and from the allocation-free detection alike (the fake addresses are never touched)."""
+    lib = _lib()
+    f = lib.sfft_plan_create
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    err = lib.sfft_last_error
+    err.restype = ctypes.c_char_p
+    h = ctypes.c_void_p()
+    for d, addr in ((4, 0x10004), (8, 0x10008), (6, 0x10004), (10, 0x1000C)):
+        assert f(ctypes.byref(h), d, addr, 100, 2, 0, None, None, None, None) == 1, d
+        assert b"aligned" in err()
+    det = lib.sfft_detect_noalloc
+    det.restype = ctypes.c_int
+    det.argtypes = [ctypes.c_int, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_double, ctypes.c_void_p, ctypes.c_int64,
+                    ctypes.c_void_p, ctypes.c_void_p]
+    Ms = np.full(1, 101, dtype=np.int64)
+    zz = np.zeros(4, dtype=np.int64)
+    taus = np.zeros(1)
+    nd = ctypes.c_int64()
+    rc = det(4, 0x10004, 100, 1, Ms.ctypes.data, zz.ctypes.data, 0x20000, taus.ctypes.data, 0.5, 0x30000, 100,
+             ctypes.byref(nd), None)
+    assert rc == 1 and b"aligned" in err()
+
+
 def test_struct_layouts_match_the_header(tmp_path):
     """The ctypes mirrors of the header's structs have the C compiler's field offsets and sizes."""
     gcc = shutil.which("gcc") or shutil.which("cc")

@@ -40,3 +40,30 @@ def test_launch_count_of_a_step():
     assert bench.kernel_count([P(10)] * 16, 16) == 14
     assert bench.kernel_count([P(10)] * 8 + [P(12)] * 8, 16) == 15  # two hash launches
     assert bench.kernel_count([P(10)] * 16, 16, refine=False) == 11
+
+
+def test_executed_hash_evals_replay_matches_kernel_loop():
+    """The replay of the hash kernel's early exit equals a plain loop over its warps: each warp of a
+    1024-candidate tile holds candidates base + 32 w + lane + 256 c (c < 4) and stops after lattice
+    l (l odd) once no candidate's count plus the lattices left reaches the threshold."""
+    import numpy as np
+    import torch
+    import bench
+    rng = np.random.default_rng(5)
+    for n, L, p, need in ((3000, 37, 0.1, 19), (2048, 9, 0.45, 5), (1500, 13, 0.3, 7)):
+        nz = (rng.random((n, L)) < p).astype(np.int64)
+        nz[rng.choice(n, 5)] = 1  # a few candidates with every lattice non-zero (true support)
+        tile = 1024
+        expect = 0
+        for base in range(0, n, tile):
+            for w in range(8):
+                idx = [base + 32 * w + lane + 256 * c for c in range(4) for lane in range(32)]
+                cnt = np.zeros(len(idx), dtype=np.int64)
+                visited = L
+                for l in range(L):
+                    cnt += np.array([nz[i, l] if i < n else 0 for i in idx])
+                    if l % 2 == 1 and not np.any(cnt + (L - 1 - l) >= need):
+                        visited = l + 1
+                        break
+                expect += 128 * visited
+        assert bench.executed_from_indicators(torch.from_numpy(nz), need) == expect

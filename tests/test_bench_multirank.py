@@ -72,3 +72,20 @@ def test_reference_arm_rank_nonzero_exits_quietly():
                         "--steps", "1", "--warmup", "0"], env=env, capture_output=True, text=True, timeout=120)
     assert r.returncode == 0
     assert r.stdout.strip() == ""
+
+
+def test_gpus_flag_starts_or_refuses_ranks():
+    """bench.py --gpus N never silently runs fewer ranks: without WORLD_SIZE it starts N ranks
+    itself, with a WORLD_SIZE that differs from N it refuses (exit status 2, no measurement)."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert bench.rank_plan(1, {}) == ("run", 1)
+    assert bench.rank_plan(4, {}) == ("spawn", 4)
+    assert bench.rank_plan(2, {"WORLD_SIZE": "2"}) == ("run", 2)
+    how, msg = bench.rank_plan(8, {"WORLD_SIZE": "1"})
+    assert how == "refuse" and "--gpus 8" in msg
+    env = dict(os.environ, WORLD_SIZE="3", RANK="0", LOCAL_RANK="0", MASTER_ADDR="127.0.0.1")
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--gpus", "2", "--steps", "1"], env=env,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 2
+    assert "WORLD_SIZE=3" in json.loads(r.stdout.strip().splitlines()[-1])["error"]

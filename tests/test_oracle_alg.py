@@ -157,3 +157,72 @@ def test_hybrid_postprocess_brute_force():
         i = np.searchsorted(r.supp, r.detected[q])
         if i < len(r.supp) and r.supp[i] == r.detected[q]:
             assert abs(r.coef[i] - expect) < 1e-12
+
+
+def _aliasing_false_positive_case(seed=0):
+    """k, j in I and k' not in I with (k' - k).z_l = 0 mod M on lattices A = {0, 1} and
+    (k' - j).z_l = 0 mod M on B = {2, 3} (L = 7): k' holds a true coefficient on 4 = (L+1)/2
+    lattices and is detected; k and j never alias with each other and k' aliases with nothing
+    else.  Generating vectors: component 0 solves the congruence, the others are random."""
+    d, M, L = 3, 101, 7
+    k, j, kp = np.array([3, -5, 7]), np.array([-8, 2, 4]), np.array([1, 6, -2])
+    rng = np.random.default_rng(seed)
+    while True:
+        z = rng.integers(0, M, size=(L, d))
+        for l, v in [(0, kp - k), (1, kp - k), (2, kp - j), (3, kp - j)]:
+            rest = int(v[1] * z[l, 1] + v[2] * z[l, 2])
+            z[l, 0] = (-rest * pow(int(v[0]) % M, -1, M)) % M
+        h = O.hashes(np.stack([k, j, kp]), z, M)
+        ok = all(h[0, l] != h[1, l] for l in range(L))
+        ok &= all((h[2, l] == h[0, l]) == (l in (0, 1)) for l in range(L))
+        ok &= all((h[2, l] == h[1, l]) == (l in (2, 3)) for l in range(L))
+        if ok:
+            return np.stack([k, j, kp]).astype(np.int64), z, M, L
+
+
+def test_refine_removes_aliasing_false_positive():
+    """One refinement step with Delta != 0.  The false positive k' has the median pcheck_k' != 0;
+    the residual spectrum ghat - C at its buckets is -pcheck_k' on every lattice, so the step sets
+    c_k' to 0, while k and j (sharing a bucket with k' on a minority of lattices) keep their exact
+    values.  A sign error in the update (c - Delta) would leave 2 pcheck_k'."""
+    cand, z, M, L = _aliasing_false_positive_case()
+    c = np.array([2.0 + 1.0j, 3.0 - 2.0j])  # coefficients of k, j
+    y = O.sample_sparse_poly(cand[:2], c, z, M)
+    r0 = O.reconstruct(cand, y, z, M, tau_rel=1e-10)
+    assert list(r0.detected) == [0, 1, 2]
+    assert abs(r0.pcheck[2]) > 1.0            # the false positive's median is spoiled (= 2 here)
+    assert np.allclose(r0.pcheck[:2], c, atol=1e-12)
+    sl = O.split_lattices(y, [M] * L)
+    for mode in ("direct", "bucket"):
+        ref = O.refine(sl, cand, r0.detected, r0.pcheck, z, [M] * L, mode)
+        assert np.allclose(ref, [c[0], c[1], 0.0], atol=1e-12), mode
+    r = O.reconstruct(cand, y, z, M, tau_rel=1e-10, do_refine=True, theta=1e-9)
+    assert list(r.supp) == [0, 1] and np.allclose(r.coef, c, atol=1e-12)
+
+
+def test_hybrid_combine_exact_on_collision_free_lattices():
+    """Remark 2.8, exact case: when every true frequency is detected (I in Itilde), a bucket that no
+    other detected frequency shares holds only k's own coefficient.  So every detected k with at
+    least one collision-free lattice gets exactly its true coefficient (0 for a false positive),
+    including frequencies whose median is spoiled by aliasing."""
+    d, N, s, M, L = 3, 8, 40, 101, 7
+    cand = S.full_grid(d, N)
+    spoiled_seen = 0
+    for seed in range(40):
+        sup = S.support_indices(cand.shape[0], s, seed)
+        c = S.coef_mag_phase(s, 1, 10, seed)
+        z = S.generators(L, d, M, seed)
+        y = O.sample_sparse_poly(cand[sup], c, z, M)
+        r = O.reconstruct(cand, y, z, M, tau_rel=1e-10, postproc="hybrid")
+        if not set(sup) <= set(r.detected):
+            continue
+        truth = np.zeros(cand.shape[0], dtype=np.complex128)
+        truth[sup] = c
+        det = r.detected
+        coef = np.empty(len(det), dtype=np.complex128)  # hybrid coefficients of every detected k
+        pos = np.searchsorted(det, r.supp)
+        coef[pos] = r.coef
+        free = r.extra["nfree"] > 0
+        assert np.allclose(coef[free], truth[det][free], atol=1e-12), seed
+        spoiled_seen += int(np.sum(free & (np.abs(r.pcheck - truth[det]) > 1e-6)))
+    assert spoiled_seen > 0  # the property was exercised where the median is wrong

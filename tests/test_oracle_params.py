@@ -19,6 +19,14 @@ def test_cor26_failure_bound_values_section_4_1_2():
     assert first == int(G41["cor26_first_nontrivial_L"])
 
 
+def test_cor26_rule_at_section_4_1_2_scale():
+    """Section 4.1.2 / Figure 4.1: with |Gamma| = 10^7 the bound is 0.237 at L = 39 and 0.096 at
+    L = 41, so delta = 0.1 needs L = 41: the rule's value there is fixed by the paper."""
+    assert round(O.cor26_failure_bound(39, 10 ** 7), 3) == G41["cor26_bound_L39"]
+    assert O.cor26_failure_bound(39, 10 ** 7) > 0.1 > O.cor26_failure_bound(41, 10 ** 7)
+    assert O.L_cor26(10 ** 7, 0.1) == 41
+
+
 def test_cor26_bound_matches_paper_expression():
     # the paper writes the same bound as 10^7 * 9.331^(-8.331/41.324 L)
     for L in (29, 33, 37, 41):

@@ -1,9 +1,15 @@
-"""The allocation-free detection entry point (sfft_detect_noalloc) against the detection that
-sfft_reconstruct reports (sfft_diag.detected), through the C ABI, on two calls in a row.
+"""The allocation-free detection entry point (sfft_detect_noalloc) against the oracle's detection
+(Algorithm 1/2 count rule), through the C ABI, on two calls in a row per case.
 
-Callers that cannot allocate device memory (host callbacks, capped allocators, services that
-must keep a fixed footprint) use this entry point; its scratch is a fixed device array inside
-the library, so these tests also check that a second call does not see stale contents."""
+Callers that cannot allocate device memory (host callbacks where cudaMalloc is forbidden, capped or
+custom allocators, services that must keep a fixed footprint) use this entry point; its scratch is
+a fixed device array inside the library that every call reuses, so each case runs twice and the
+cases alternate between large and small problems: stale contents of an earlier call would show.
+
+The lattice DFTs and the thresholds are the oracle's (FP64, and the same values rounded to FP32 as
+an FP32 transform would deliver them); both sides decide on identical inputs, so the detected sets
+must be identical.  The entry point takes int32 rows: small boxes (|k| <= 127, M <= 32768) run the
+packed dp2a hash kernel, the box of 200 the int32 kernel (int4 row loads at d = 4 and d = 8)."""
 import ctypes
 import math
 
@@ -16,7 +22,7 @@ import sfft_synth as S
 pytestmark = pytest.mark.gpu
 
 
-def _case(seed, n, d, s, box):
+def _case(seed, n, d, s, box, fp32, nu):
     cand = S.uniform_distinct(n, d, -box, box, seed)
     L = O.L_cor26(n, 0.1)
     M = O.lattice_size(cand, s)
@@ -25,39 +31,48 @@ def _case(seed, n, d, s, box):
     c = S.coef_cgauss(s, seed)
     sig = S.snr_sigma(c, 40.0)
     y = O.sample_sparse_poly(cand[sup], c, z, M) + S.noise(L * M, sig, seed)
-    return cand, z, M, L, y, 6 * sig / math.sqrt(M)
+    ghat = [O.lattice_dft(v, M) for v in O.split_lattices(y, [M] * L)]
+    if fp32:  # an FP32 transform's output, widened back to complex double for the entry point
+        ghat = [g.astype(np.complex64).astype(np.complex128) for g in ghat]
+    tau = np.full(L, 6 * sig / math.sqrt(M))
+    det, _ = O.detect(cand, ghat, z, [M] * L, tau, nu)
+    return cand, z, M, L, np.concatenate(ghat), tau, det, sup
 
 
-def test_noalloc_detection_matches_reconstruct_twice():
+CASES = [  # (seed, n, d, s, box, fp32, nu): packed kernel, int32 kernel with int4 rows, FP32 buckets,
+    #           d = 3, and Algorithm 1 with nu = 0.2 (many false positives: a larger detected set)
+    (1, 20000, 6, 60, 30, False, 0.5),
+    (2, 6000, 8, 40, 200, False, 0.5),
+    (3, 12000, 4, 50, 200, True, 0.5),
+    (4, 5000, 3, 25, 20, True, 0.5),
+    (5, 30000, 5, 80, 40, False, 0.2),
+]
+
+
+def test_noalloc_detection_matches_oracle_twice():
     import torch
     if not torch.cuda.is_available():
         pytest.fail("CUDA device required")
-    import paper_2006_13053_gb300 as G
     from paper_2006_13053_gb300 import _native as N
     dev = torch.device("cuda:0")
-    # two different problems in a row (the second is smaller, so stale scratch would show)
-    for seed, n, d, s, box in ((1, 20000, 6, 60, 30), (2, 5000, 3, 25, 20)):
-        cand, z, M, L, y, tau = _case(seed, n, d, s, box)
+    for seed, n, d, s, box, fp32, nu in CASES:
+        cand, z, M, L, ghat, tau, ref, sup = _case(seed, n, d, s, box, fp32, nu)
+        assert set(sup) <= set(ref)  # a meaningful detection: the true support is found
         tc = torch.from_numpy(cand).to(dev)
-        plan = G.Plan(tc, s, L=L, M=[M] * L, z=z, precision=0, tau_abs=tau, tau_rel=0.0)
-        _, _, info = plan.reconstruct(torch.from_numpy(y).to(dev), diag=True)
-        ref = info["detected"].cpu().numpy()
-        ghat = info["ghat"].contiguous()
-        taus = info["tau"].cpu().numpy().astype(np.float64)
+        g = torch.from_numpy(ghat).to(dev)
         Ms = np.full(L, M, dtype=np.int64)
         zz = np.ascontiguousarray(z.astype(np.int64))
         for rep in range(2):
             out = torch.full((n,), -1, dtype=torch.int64, device=dev)
             nd = ctypes.c_int64()
             rc = N.sfft_detect_noalloc(d, ctypes.c_void_p(tc.data_ptr()), n, L, Ms.ctypes.data_as(ctypes.c_void_p),
-                                       zz.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(ghat.data_ptr()),
-                                       taus.ctypes.data_as(ctypes.c_void_p), 0.5, ctypes.c_void_p(out.data_ptr()), n,
+                                       zz.ctypes.data_as(ctypes.c_void_p), ctypes.c_void_p(g.data_ptr()),
+                                       tau.ctypes.data_as(ctypes.c_void_p), nu, ctypes.c_void_p(out.data_ptr()), n,
                                        ctypes.byref(nd), None)
             N.check(rc)
             got = out[:nd.value].cpu().numpy()
+            assert nd.value == len(ref), (seed, rep)
             assert np.array_equal(got, ref), (seed, rep)
-            assert nd.value == len(ref)
-        plan.close()
 
 
 def test_noalloc_rejects_oversize():
