@@ -96,6 +96,10 @@ typedef struct sfft_params {
     int cand_type;    /* element type of the candidate rows: SFFT_CAND_I32 (default) or _I8     */
     int cand_ld;      /* row stride in elements: 0 = d (I32); I8 rows: >= d bytes               */
     int dft;          /* SFFT_DFT_*: forward DFT arithmetic of FP32 plans with refinement      */
+    int rank_bits;    /* Algorithm 4 sort by modulus: 0 = exact FP64 order; 1..51 = moduli that  */
+                      /* agree when rounded to rank_bits significant bits rank as equal, and    */
+                      /* equal ranks keep the lower candidate index (a deterministic rule for   */
+                      /* near-ties, e.g. the +-k symmetric coefficients of real functions)      */
 } sfft_params;
 
 #define SFFT_CAND_I32 0 /* int32 rows of d entries                                              */
@@ -309,7 +313,8 @@ typedef int (*sfft_sample_fn)(void* ctx, const double* x, int64_t n, double* y, 
 typedef struct sfft_dimincr_params {
     int64_t s;         /* sparsity (sets M_l = smallest prime > c s)                        */
     int64_t s_local;   /* Step 1 / Step 2 (t < d) output size; default 2 s                  */
-    int r;             /* number of detection iterations                                    */
+    int r;             /* number of detection iterations; 0 = the theory's choice
+                          r = ceil(2 s ln(3 d s / delta)) (Section 3.3)                      */
     double theta_abs;  /* Algorithm 3/4 threshold (absolute) ...                            */
     double theta_rel;  /* ... or relative to the largest modulus of the current call        */
     double delta;      /* eq. (4.2) failure parameter                                       */
@@ -319,6 +324,10 @@ typedef struct sfft_dimincr_params {
     int refine;        /* FP64 refinement steps per Algorithm 4 call                          */
     uint64_t seed;     /* Philox key; draws documented in the implementation                 */
     int64_t max_samples; /* 0 = unlimited; otherwise stop with SFFT_ECAPACITY                */
+    int rank_bits;     /* near-tie rule of every Algorithm 4 selection (see sfft_params)     */
+    int L_rule;        /* lattices per Step-2 call: SFFT_L_EQ42 (default, Section 4.2: eq. 4.2
+                          with delta) or SFFT_L_COR26 with the theory's failure probability
+                          gamma_A = delta / (3 d r) of Section 3.3                            */
 } sfft_dimincr_params;
 
 void sfft_dimincr_params_default(sfft_dimincr_params* p);
@@ -339,9 +348,14 @@ int sfft_dim_incremental(int d, const int32_t* box_lo, const int32_t* box_hi, co
  *       ctx = sfft_fn_sop_ctx (host triples int32 [n_terms*3], device theta double [n_terms],
  *       device work buffer of at least 16 n_terms (K+1) + 12 n_terms bytes). */
 typedef struct sfft_fn_sparse_poly_ctx { const int32_t* kvec; const double* coef; int64_t n_terms; int d; } sfft_fn_sparse_poly_ctx;
+/*   sfft_fn_bspline: Section 4.3's B-spline sum (eq. 4.3, as in sfft_sample_bspline) at arbitrary
+ *       nodes, FP64 closed form; ctx = sfft_fn_bspline_ctx (host dims int32 [n_terms, 4] with -1
+ *       ending a term, host orders int32 [n_terms], 1 <= n_terms <= 8, d the node dimension). */
+typedef struct sfft_fn_bspline_ctx { const int32_t* dims; const int32_t* orders; int n_terms; int d; } sfft_fn_bspline_ctx;
 typedef struct sfft_fn_sop_ctx { const int32_t* triples; const double* theta; int n_terms; int K; double width; int d; void* work; } sfft_fn_sop_ctx;
 int sfft_fn_sparse_poly(void* ctx, const double* x, int64_t n, double* y, void* stream);
 int sfft_fn_sop(void* ctx, const double* x, int64_t n, double* y, void* stream);
+int sfft_fn_bspline(void* ctx, const double* x, int64_t n, double* y, void* stream);
 
 /* ---------------------------------------------------------------- allocation-free detection */
 /*

@@ -250,16 +250,23 @@ def sop_kernel_dcoef(theta: float, K: int = 48, width: float = 32.0) -> np.ndarr
     return 4.0 * sn ** 3 * dsn * (-u / theta)
 
 
+def _kernel_at(a, xcol, K):
+    """g(x) = sum_{|k|<=K} a_k e^{2 pi i k x} (real part) at every entry of the column xcol, evaluated
+    once per distinct value of the column (lattice coordinates take at most M values)."""
+    kk = np.arange(-K, K + 1, dtype=np.float64)
+    u, inv = np.unique(xcol, return_inverse=True)
+    return (np.exp(2j * np.pi * np.outer(u, kk)) @ a).real[inv]
+
+
 def sop_eval(triples, theta, x, K=48, width=32.0):
     """f_theta(x) for x [n, d] (real valued), by direct summation of each 1-D kernel."""
     x = np.atleast_2d(np.asarray(x, dtype=np.float64))
-    kk = np.arange(-K, K + 1, dtype=np.float64)
     out = np.zeros(x.shape[0], dtype=np.float64)
     for m, T in enumerate(triples):
         a = sop_kernel_coef(theta[m], K, width)
         prod = np.ones(x.shape[0])
         for t in T:
-            prod *= (np.exp(2j * np.pi * np.outer(x[:, t], kk)) @ a).real
+            prod *= _kernel_at(a, x[:, t], K)
         out += prod
     return out
 
@@ -267,14 +274,12 @@ def sop_eval(triples, theta, x, K=48, width=32.0):
 def sop_grad_theta(triples, theta, x, w, K=48, width=32.0):
     """sum_j w_j d f_theta(x_j) / d theta_m  for real weights w (vector-Jacobian product)."""
     x = np.atleast_2d(np.asarray(x, dtype=np.float64))
-    kk = np.arange(-K, K + 1, dtype=np.float64)
     g = np.zeros(len(theta))
     for m, T in enumerate(triples):
         a = sop_kernel_coef(theta[m], K, width)
         da = sop_kernel_dcoef(theta[m], K, width)
-        E = [np.exp(2j * np.pi * np.outer(x[:, t], kk)) for t in T]
-        vals = [(e @ a).real for e in E]
-        dvals = [(e @ da).real for e in E]
+        vals = [_kernel_at(a, x[:, t], K) for t in T]
+        dvals = [_kernel_at(da, x[:, t], K) for t in T]
         tot = np.zeros(x.shape[0])
         for i in range(3):
             term = dvals[i].copy()
@@ -592,20 +597,33 @@ def refine(samples_list, cand, det, coef, z, M_list, mode="direct"):
     return coef + delta
 
 
-def select_top(coef, s_tilde, theta):
+def rank_key(mag, bits=0):
+    """Algorithm 4's sort key of moduli |c| >= 0: the FP64 bit pattern (which orders like the value),
+    rounded half up to `bits` significant bits when 0 < bits < 52.  Moduli with equal keys rank by
+    position (the near-tie rule of the rank_bits parameter; bits = 0 is the exact FP64 order)."""
+    b = np.ascontiguousarray(np.asarray(mag, dtype=np.float64)).view(np.uint64)
+    if 0 < bits < 52:
+        drop = np.uint64(52 - bits)
+        b = ((b + (np.uint64(1) << (drop - np.uint64(1)))) >> drop) << drop
+    return b
+
+
+def select_top(coef, s_tilde, theta, rank_bits=0):
     """Algorithm 4, filter and selection: keep |c| >= theta, sort by modulus descending (ties: lower
-    index first) and keep the first s_tilde.  Returns positions into coef, ascending."""
+    index first; moduli are compared through rank_key) and keep the first s_tilde.  Returns
+    positions into coef, ascending."""
     a = np.abs(coef)
     keep = np.nonzero(a >= theta)[0]
     if s_tilde is None or s_tilde >= keep.size:
         return keep
-    order = np.lexsort((keep, -a[keep]))  # primary: -|c|, secondary: position (index)
+    key = rank_key(a[keep], rank_bits)
+    order = np.lexsort((keep, ~key))  # primary: key descending, secondary: position
     return np.sort(keep[order[:s_tilde]])
 
 
 def reconstruct(cand, samples, z, M, tau_abs=0.0, tau_rel=0.0, nu=0.5, s_tilde=None, theta=0.0,
                 theta_rel=0.0, do_refine=False, refine_mode="direct", postproc="median",
-                want_counts=False):
+                want_counts=False, rank_bits=0):
     """Algorithm 2 (nu=1/2) [or 1] -> optional Remark 2.8 post-processing -> optional one FP64
     refinement step -> Algorithm 4 theta filter and top-s_tilde.  samples are concatenated
     by lattice (lattice l has M_l samples in node order j = 0..M_l-1)."""
@@ -631,7 +649,7 @@ def reconstruct(cand, samples, z, M, tau_abs=0.0, tau_rel=0.0, nu=0.5, s_tilde=N
         coef = refine(sl, cand, det, coef, z, M_list, refine_mode)
         refined = coef
     th = max(theta, theta_rel * (np.abs(coef).max() if coef.size else 0.0))
-    pos = select_top(coef, s_tilde, th)
+    pos = select_top(coef, s_tilde, th, rank_bits)
     return Result(supp=det[pos], coef=coef[pos], detected=det, pcheck=pcheck, counts=counts,
                   ghat=ghat, tau=tau, H=H, refined=refined, extra=extra)
 
@@ -680,22 +698,46 @@ class DimIncrResult:
     I1: list = field(default_factory=list)     # Step 1 index sets I^(t)
 
 
-def _topk_abs(vals, s_local, theta):
-    a = np.abs(vals)
-    keep = np.nonzero(a >= theta)[0]
-    order = np.lexsort((keep, -a[keep]))
-    return np.sort(keep[order[:s_local]])
+def _topk_abs(vals, s_local, theta, rank_bits=0):
+    return select_top(np.asarray(vals), s_local, theta, rank_bits)
+
+
+def theory_r(s, d, delta):
+    """Detection iterations of Algorithm 3 in the theory (Section 3.3): r = ceil(2 s ln(3 d s / delta))."""
+    return int(math.ceil(2.0 * s * math.log(3.0 * d * s / delta)))
+
+
+def theory_gamma_A(delta, d, r):
+    """Failure probability allowed to one Algorithm 4 call of Step 2 (Section 3.3): delta / (3 d r)."""
+    return delta / (3.0 * d * r)
+
+
+def theory_gamma(delta, d):
+    """Failure probability of Step 3 (Section 3.3): delta / (3 d)."""
+    return delta / (3.0 * d)
+
+
+def theory_failure_union(delta, d, r):
+    """Union bound of Section 3.3 over the parts of Algorithm 3 with these parameters: delta/3 for
+    Step 1, (d-2) delta/(3d) + ((d-2) r + 1) gamma_A for Step 2 and gamma for Step 3."""
+    return (delta / 3.0 + (d - 2) * delta / (3.0 * d) + ((d - 2) * r + 1) * theory_gamma_A(delta, d, r)
+            + theory_gamma(delta, d))
 
 
 def dim_incremental(f, d, lo, hi, s, s_local, r, seed, theta=1e-12, theta_rel=0.0, delta=0.9,
-                    c=C_DEFAULT, tau_abs=0.0, tau_rel=1e-10, do_refine=False):
-    """Algorithm 3 with Algorithm 4 in the role of Algorithm A on Gamma = box [lo, hi]^d.
+                    c=C_DEFAULT, tau_abs=0.0, tau_rel=1e-10, do_refine=False, rank_bits=0, L_rule="eq42"):
+    """Algorithm 3 with Algorithm 4 in the role of Algorithm A on Gamma = box [lo, hi]^d (d >= 2).
 
     f(x) evaluates the function at nodes x [n, d] (complex or real).  Readings: M on s
-    (not s_local); L by eq. 4.2 with |J_t|; theta absolute or relative to the call's
-    largest modulus; Step 3 takes the coefficients of the t = d call of Algorithm 4."""
+    (not s_local); L by eq. 4.2 with |J_t| (L_rule="eq42") or by Corollary 2.6 with the theory's
+    gamma_A = delta/(3 d r) (L_rule="cor26"); r = 0 takes the theory's r; theta absolute or
+    relative to the call's largest modulus; Step 3 takes the coefficients of the t = d call of
+    Algorithm 4."""
+    assert d >= 2
     lo = np.broadcast_to(np.asarray(lo, dtype=np.int64), (d,))
     hi = np.broadcast_to(np.asarray(hi, dtype=np.int64), (d,))
+    if not r:
+        r = theory_r(s, d, delta)
     nsamp = 0
     res = DimIncrResult(supp=None, coef=None, samples=0)
     # ---- Step 1: single component identification
@@ -713,7 +755,7 @@ def dim_incremental(f, d, lo, hi, s, s_local, r, seed, theta=1e-12, theta_rel=0.
             ks = np.arange(lo[t], hi[t] + 1)
             vals = ph[np.mod(ks, K)]
             th = max(theta, theta_rel * np.abs(vals).max())
-            for pos in _topk_abs(vals, s_local, th):
+            for pos in _topk_abs(vals, s_local, th, rank_bits):
                 sel.add(int(ks[pos]))
         I1.append(np.array(sorted(sel), dtype=np.int64))
     res.I1 = I1
@@ -730,7 +772,7 @@ def dim_incremental(f, d, lo, hi, s, s_local, r, seed, theta=1e-12, theta_rel=0.
             J = np.concatenate([np.repeat(Icur, len(I1[t]), axis=0),
                                 np.tile(I1[t], len(Icur))[:, None]], axis=1)
             M = lattice_size(J, s, c)
-            L = L_eq42(J.shape[0], delta, c)
+            L = L_eq42(J.shape[0], delta, c) if L_rule == "eq42" else L_cor26(J.shape[0], theory_gamma_A(delta, d, r), c)
             u = np.arange(t + 1, dtype=np.uint64)
             z = np.stack([rand_below(seed, M, u, np.uint64(l), np.uint64(t * (1 << 20) + i), np.uint64(3))
                           for l in range(L)], axis=0)
@@ -740,7 +782,7 @@ def dim_incremental(f, d, lo, hi, s, s_local, r, seed, theta=1e-12, theta_rel=0.
             y = np.asarray(f(X), dtype=np.complex128)
             nsamp += X.shape[0]
             rr = reconstruct(J, y, z, M, tau_abs=tau_abs, tau_rel=tau_rel, s_tilde=st, theta=theta,
-                             theta_rel=theta_rel, do_refine=do_refine, refine_mode="bucket")
+                             theta_rel=theta_rel, do_refine=do_refine, refine_mode="bucket", rank_bits=rank_bits)
             res.steps.append((t, i, J.shape[0], L, M, len(rr.supp)))
             for row, cv in zip(J[rr.supp], rr.coef):
                 acc[tuple(int(v) for v in row)] = cv
@@ -748,7 +790,7 @@ def dim_incremental(f, d, lo, hi, s, s_local, r, seed, theta=1e-12, theta_rel=0.
         Icur = np.array(keys, dtype=np.int64).reshape(-1, t + 1)
         coef = np.array([acc[k] for k in keys], dtype=np.complex128)
     # ---- Step 3 (reading): coefficients of the final t = d call, top-s by modulus
-    pos = select_top(coef, s, 0.0)
+    pos = select_top(coef, s, 0.0, rank_bits)
     res.supp = Icur[pos]
     res.coef = coef[pos]
     res.samples = nsamp

@@ -43,7 +43,7 @@ class Params(C.Structure):
                 ("tau_rel", C.c_double), ("theta_abs", C.c_double), ("theta_rel", C.c_double),
                 ("s_tilde", C.c_int64), ("precision", C.c_int), ("refine", C.c_int), ("L_rule", C.c_int),
                 ("combine", C.c_int), ("seed", C.c_uint64), ("detect_cap", C.c_int64), ("cand_type", C.c_int),
-                ("cand_ld", C.c_int), ("dft", C.c_int)]
+                ("cand_ld", C.c_int), ("dft", C.c_int), ("rank_bits", C.c_int)]
 
 
 class Diag(C.Structure):
@@ -56,11 +56,15 @@ class DimIncrParams(C.Structure):
     _fields_ = [("s", C.c_int64), ("s_local", C.c_int64), ("r", C.c_int), ("theta_abs", C.c_double),
                 ("theta_rel", C.c_double), ("delta", C.c_double), ("c", C.c_double), ("tau_abs", C.c_double),
                 ("tau_rel", C.c_double), ("precision", C.c_int), ("refine", C.c_int), ("seed", C.c_uint64),
-                ("max_samples", C.c_int64)]
+                ("max_samples", C.c_int64), ("rank_bits", C.c_int), ("L_rule", C.c_int)]
 
 
 class SparsePolyCtx(C.Structure):
     _fields_ = [("kvec", C.c_void_p), ("coef", C.c_void_p), ("n_terms", C.c_int64), ("d", C.c_int)]
+
+
+class BsplineCtx(C.Structure):
+    _fields_ = [("dims", C.c_void_p), ("orders", C.c_void_p), ("n_terms", C.c_int), ("d", C.c_int)]
 
 
 class SopCtx(C.Structure):
@@ -107,6 +111,7 @@ sfft_dim_incremental = _sig("sfft_dim_incremental", _i32,
                             [_i32, _vp, _vp, _P(DimIncrParams), _vp, _vp, _vp, _vp, _i64, _P(_i64), _P(_i64), _vp])
 sfft_fn_sparse_poly = _sig("sfft_fn_sparse_poly", _i32, [_vp, _vp, _i64, _vp, _vp])
 sfft_fn_sop = _sig("sfft_fn_sop", _i32, [_vp, _vp, _i64, _vp, _vp])
+sfft_fn_bspline = _sig("sfft_fn_bspline", _i32, [_vp, _vp, _i64, _vp, _vp])
 sfft_detect_noalloc = _sig("sfft_detect_noalloc", _i32, [_i32, _vp, _i64, _i32, _vp, _vp, _vp, _vp, _dbl, _vp, _i64,
                                                         _P(_i64), _vp])
 sfft_philox4x64_word0 = _sig("sfft_philox4x64_word0", C.c_uint64, [C.c_uint64] * 5)

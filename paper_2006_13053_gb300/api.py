@@ -335,7 +335,8 @@ class Batch:
 def dim_incremental(d, lo, hi, s, fn, s_local=0, r=1, stream=None, cap=None, **params):
     """Algorithm 3 on the box prod_t [lo_t, hi_t] with a built-in black box:
        fn = ("sparse_poly", kvec int32 cuda [n, d], coef complex128 cuda [n]) or
-       fn = ("sop", triples int [m, 3], theta float64 cuda [m], K, width).
+       fn = ("sop", triples int [m, 3], theta float64 cuda [m], K, width) or
+       fn = ("bspline", terms): Section 4.3's B-spline sum, terms = [(dims, order), ...].
     Returns (supp int32 numpy [k, d] in lexicographic order, coef complex128 numpy [k], samples)."""
     p = N.default_dimincr_params(s=int(s), s_local=int(s_local), r=int(r), **params)
     lo = np.ascontiguousarray(np.broadcast_to(np.asarray(lo, dtype=np.int32), (d,)))
@@ -357,6 +358,17 @@ def dim_incremental(d, lo, hi, s, fn, s_local=0, r=1, stream=None, cap=None, **p
         ctx = N.SopCtx(tri.ctypes.data_as(C.c_void_p).value, theta.data_ptr(), m, int(K), float(width), d,
                        work.data_ptr())
         faddr = N.fn_address("sfft_fn_sop")
+    elif fn[0] == "bspline":
+        terms = fn[1]
+        dims = np.full((len(terms), 4), -1, dtype=np.int32)
+        orders = np.zeros(len(terms), dtype=np.int32)
+        for q, (dq, m) in enumerate(terms):
+            dims[q, :len(dq)] = dq
+            orders[q] = m
+        keep += [dims, orders]
+        ctx = N.BsplineCtx(dims.ctypes.data_as(C.c_void_p).value, orders.ctypes.data_as(C.c_void_p).value,
+                           len(terms), d)
+        faddr = N.fn_address("sfft_fn_bspline")
     else:
         raise ValueError(fn[0])
     cap = int(cap if cap is not None else s)

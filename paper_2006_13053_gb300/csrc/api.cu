@@ -16,6 +16,7 @@
 
 #include "common.cuh"
 #include "kernels.cuh"
+#include "philox.cuh"
 #include "plan.cuh"
 
 namespace sfft {
@@ -46,23 +47,13 @@ int allow_smem(const void* kernel, int bytes) {
     return SFFT_OK;
 }
 
-// ================================================================== Philox4x64-10 (Salmon et al., SC'11)
+// ================================================================== Philox4x64-10 (philox.cuh)
 uint64_t philox_word0(uint64_t key0, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3) {
-    const uint64_t M0 = 0xD2E7470EE14C6C93ull, M1 = 0xCA5A826395121157ull;
-    const uint64_t W0 = 0x9E3779B97F4A7C15ull, W1 = 0xBB67AE8584CAA73Bull;
-    uint64_t x0 = c0, x1 = c1, x2 = c2, x3 = c3, k0 = key0, k1 = 0;
-    for (int r = 0; r < 10; ++r) {
-        if (r > 0) { k0 += W0; k1 += W1; }
-        unsigned __int128 p0 = (unsigned __int128)M0 * x0, p1 = (unsigned __int128)M1 * x2;
-        uint64_t hi0 = (uint64_t)(p0 >> 64), lo0 = (uint64_t)p0, hi1 = (uint64_t)(p1 >> 64), lo1 = (uint64_t)p1;
-        uint64_t n0 = hi1 ^ x1 ^ k0, n2 = hi0 ^ x3 ^ k1;
-        x0 = n0; x1 = lo1; x2 = n2; x3 = lo0;
-    }
-    return x0;
+    return philox4x64_w0(key0, c0, c1, c2, c3);
 }
 
 double philox_u01(uint64_t key, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3) {
-    return (double)(philox_word0(key, c0, c1, c2, c3) >> 11) * (1.0 / 9007199254740992.0);
+    return philox4x64_u01(key, c0, c1, c2, c3);
 }
 
 // ================================================================== number theory / rules
@@ -265,6 +256,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
                SFFT_EINVAL, "bad combine mode");
     SFFT_CHECK(p.cand_type == SFFT_CAND_I32 || p.cand_type == SFFT_CAND_I8, SFFT_EINVAL, "bad cand_type");
     SFFT_CHECK(p.dft == SFFT_DFT_DF64 || p.dft == SFFT_DFT_FP32, SFFT_EINVAL, "bad dft arithmetic %d", p.dft);
+    SFFT_CHECK(p.rank_bits >= 0 && p.rank_bits <= 52, SFFT_EINVAL, "rank_bits must be in [0, 52]");
     if (p.cand_type == SFFT_CAND_I32) {
         SFFT_CHECK(p.cand_ld == 0 || p.cand_ld == d, SFFT_EINVAL, "int32 candidate rows are dense (cand_ld 0 or d)");
         // the hash kernels read a row as int4 words (d % 4 == 0) or int2 words (d % 2 == 0)
@@ -410,6 +402,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     I.need = (int)ceil(p.nu * L - 1e-9);
     I.n = n; I.cap = cap; I.s_tilde = p.s_tilde;
     I.tau_abs = p.tau_abs; I.tau_rel = p.tau_rel; I.theta_abs = p.theta_abs; I.theta_rel = p.theta_rel;
+    I.rank_bits = p.rank_bits;
     I.cand = cand; I.cand_i8 = p.cand_type == SFFT_CAND_I8; I.cand_ld = p.cand_ld; I.z = dz; I.Ml = dM; I.mu = dmu; I.offk = doffk; I.soff = dsoff; I.boff = dboff;
     I.nzbits = P->nzbits; I.ghat = P->ghat; I.stats = P->stats; I.detbits = P->detbits; I.det = P->det;
     I.cnt = P->cnt; I.coef = P->coef; I.H = P->H; I.sel = P->sel; I.coll = P->coll; I.C = P->C;

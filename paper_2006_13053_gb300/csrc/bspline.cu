@@ -11,6 +11,8 @@
 // period is m times the autocorrelation of M_m at 0, which is M_2m at its centre.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "plan.cuh"
@@ -75,35 +77,73 @@ __global__ void k_bspline_sample(const InstDesc* __restrict__ insts, BsTerms ter
     }
 }
 
+// f at arbitrary nodes x [n, d] (FP64), output complex double (imaginary part 0): the black box of
+// Algorithm 3 for this test function
+__global__ void k_bspline_eval_points(const double* __restrict__ x, int64_t n, int d, BsTerms terms, double* y) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        double f = 0.0;
+        for (int q = 0; q < terms.n; ++q) {
+            const int m = terms.m[q];
+            double p = 1.0;
+            for (int u = 0; u < terms.ndim[q]; ++u) {
+                const double xv = x[j * d + terms.dims[q][u]];
+                p *= terms.scale[q] * cardinal_bspline<kBsMaxOrder>(m, (double)m * (xv - floor(xv)));
+            }
+            f += p;
+        }
+        y[2 * j] = f;
+        y[2 * j + 1] = 0.0;
+    }
+}
+
+// the terms from the host arrays of the C ABI (dims [n_terms, 4], -1 ends a term; orders [n_terms])
+static int make_terms(const int32_t* dims, const int32_t* orders, int n_terms, int d, BsTerms* T) {
+    SFFT_CHECK(dims && orders, SFFT_EINVAL, "null argument");
+    SFFT_CHECK(n_terms >= 1 && n_terms <= kBsMaxTerms, SFFT_EINVAL, "B-spline sums take 1 to %d terms", kBsMaxTerms);
+    *T = BsTerms{};
+    T->n = n_terms;
+    for (int q = 0; q < n_terms; ++q) {
+        const int m = orders[q];
+        SFFT_CHECK(m >= 1 && m <= kBsMaxOrder, SFFT_EINVAL, "B-spline order %d must be in [1, %d]", m, kBsMaxOrder);
+        T->m[q] = m;
+        int nd = 0;
+        for (int u = 0; u < kBsMaxDims; ++u) {
+            const int t = dims[q * kBsMaxDims + u];
+            if (t < 0) break;
+            SFFT_CHECK(t < d, SFFT_EINVAL, "term %d: dimension %d is not below d = %d", q, t, d);
+            for (int w = 0; w < nd; ++w)
+                SFFT_CHECK(T->dims[q][w] != t, SFFT_EINVAL, "term %d repeats dimension %d", q, t);
+            T->dims[q][nd++] = t;
+        }
+        SFFT_CHECK(nd >= 1, SFFT_EINVAL, "term %d has no dimension", q);
+        T->ndim[q] = nd;
+        // C_m = (m M_2m(m))^(-1/2)
+        T->scale[q] = (double)m / sqrt((double)m * cardinal_bspline<2 * kBsMaxOrder>(2 * m, (double)m));
+    }
+    return SFFT_OK;
+}
+
 }  // namespace sfft
 
 using namespace sfft;
+
+extern "C" int sfft_fn_bspline(void* ctx, const double* x, int64_t n, double* y, void* stream) {
+    auto* c = reinterpret_cast<sfft_fn_bspline_ctx*>(ctx);
+    if (!c || !x || !y) return SFFT_EINVAL;
+    BsTerms T;
+    SFFT_TRY(make_terms(c->dims, c->orders, c->n_terms, c->d, &T));
+    if (n <= 0) return SFFT_OK;
+    const int gx = (int)std::min<int64_t>(4 * 152, (n + 255) / 256 + 1);
+    k_bspline_eval_points<<<gx, 256, 0, (cudaStream_t)stream>>>(x, n, c->d, T, y);
+    return launch_check("k_bspline_eval_points");
+}
 
 extern "C" int sfft_sample_bspline(const sfft_plan* plan, const int32_t* dims, const int32_t* orders, int n_terms,
                                    void* samples_out) {
     if (!plan || !dims || !orders || !samples_out) { set_error("null argument"); return SFFT_EINVAL; }
     const Plan* P = reinterpret_cast<const Plan*>(plan);
-    SFFT_CHECK(n_terms >= 1 && n_terms <= kBsMaxTerms, SFFT_EINVAL, "B-spline sums take 1 to %d terms", kBsMaxTerms);
-    BsTerms T{};
-    T.n = n_terms;
-    for (int q = 0; q < n_terms; ++q) {
-        const int m = orders[q];
-        SFFT_CHECK(m >= 1 && m <= kBsMaxOrder, SFFT_EINVAL, "B-spline order %d must be in [1, %d]", m, kBsMaxOrder);
-        T.m[q] = m;
-        int nd = 0;
-        for (int u = 0; u < kBsMaxDims; ++u) {
-            const int t = dims[q * kBsMaxDims + u];
-            if (t < 0) break;
-            SFFT_CHECK(t < P->d, SFFT_EINVAL, "term %d: dimension %d is not below d = %d", q, t, P->d);
-            for (int w = 0; w < nd; ++w)
-                SFFT_CHECK(T.dims[q][w] != t, SFFT_EINVAL, "term %d repeats dimension %d", q, t);
-            T.dims[q][nd++] = t;
-        }
-        SFFT_CHECK(nd >= 1, SFFT_EINVAL, "term %d has no dimension", q);
-        T.ndim[q] = nd;
-        // C_m = (m M_2m(m))^(-1/2)
-        T.scale[q] = (double)m / sqrt((double)m * cardinal_bspline<2 * kBsMaxOrder>(2 * m, (double)m));
-    }
+    BsTerms T;
+    SFFT_TRY(make_terms(dims, orders, n_terms, P->d, &T));
     if (P->prec) k_bspline_sample<float><<<4 * 152, 256, 0, P->st>>>(P->d_inst, T, samples_out);
     else k_bspline_sample<double><<<4 * 152, 256, 0, P->st>>>(P->d_inst, T, samples_out);
     return launch_check("k_bspline_sample");

@@ -240,6 +240,7 @@ struct InstDesc {
     int d, L, need, prec;      // need = ceil(nu L) (Algorithm 1 count threshold)
     int combine, nwords;
     int cand_i8, cand_ld;      // candidate rows: int8 (1) or int32 (0); row stride in elements
+    int rank_bits, spare;      // Algorithm 4 rank-key precision (sfft_params.rank_bits)
     int64_t n;                 // |Gamma|
     int64_t cap;               // capacity of the detected list
     int64_t s_tilde;
@@ -306,6 +307,21 @@ __device__ __forceinline__ void mark_detected(const InstDesc& I, int64_t idx) {
     const int64_t W = (I.n + 31) >> 5, cw = (W + kCompactChunks - 1) / kCompactChunks;
     atomicAdd(reinterpret_cast<unsigned long long*>(&I.cnt[8 + (idx >> 5) / cw]), 1ull);
 }
+
+#ifdef __CUDACC__
+// Order-preserving key of a non-negative double rounded to `bits` significant bits (0: all 52):
+// the bit pattern of a non-negative double orders like its value, and rounding the pattern to a
+// multiple of 2^(52 - bits) (half up; a carry moves into the exponent) keeps that order.  Moduli
+// whose keys agree rank by position (Algorithm 4's near-tie rule, sfft_params.rank_bits).
+__device__ __forceinline__ unsigned long long rank_key(double v, int bits) {
+    unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    if (bits > 0 && bits < 52) {
+        const int drop = 52 - bits;
+        b = ((b + (1ull << (drop - 1))) >> drop) << drop;
+    }
+    return b;
+}
+#endif
 
 // error flag bits (InstDesc::cnt[3])
 enum : int64_t { ERR_DET_CAP = 1, ERR_GUARD_CAP = 2, ERR_OUT_CAP = 4, ERR_TC_TIMEOUT = 8 };

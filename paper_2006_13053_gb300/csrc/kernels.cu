@@ -1177,7 +1177,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(InstDesc* __restrict__ i
             __syncthreads();
             for (int64_t q = threadIdx.x; q < nd; q += blockDim.x) {
                 const double a = absc(q);
-                uint64_t key = (uint64_t)__double_as_longlong(a);
+                const uint64_t key = rank_key(a, I.rank_bits);
                 if (a >= theta && (key & mask) == prefix) atomicAdd(&hist[(key >> (8 * p)) & 255u], 1u);
             }
             __syncthreads();
@@ -1208,7 +1208,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(InstDesc* __restrict__ i
         if (q < nd) {
             c = I.coef[q];
             const double a = absc(q);
-            uint64_t key = (uint64_t)__double_as_longlong(a);
+            const uint64_t key = rank_key(a, I.rank_bits);
             if (a >= theta) {
                 if (!trunc || key > prefix) sel = 1;
                 else if (key == prefix) eq = 1;

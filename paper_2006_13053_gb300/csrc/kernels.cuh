@@ -45,4 +45,12 @@ int launch_assemble_nodes(const double* xl, int64_t n, int tc, const double* tai
 int launch_step1_nodes(const double* tail, int d, int t, int K, double* X, cudaStream_t st);
 int launch_c64_to_c32(const c64* a, c32* b, int64_t n, cudaStream_t st);
 int launch_gather_rows(const int32_t* J, int w, const int64_t* idx, int64_t n, int32_t* rows, cudaStream_t st);
+int launch_philox_tail(uint64_t key, uint64_t c1, uint64_t c2, uint64_t c3, int d, double* out, cudaStream_t st);
+int launch_step1_select(const c64* ph, int K, int lo, int64_t s_keep, double theta_abs, double theta_rel, int rank_bits,
+                        double* mag, uint8_t* mask, cudaStream_t st);
+int launch_union_scatter(const int64_t* supp, const c64* coef, int64_t n, uint8_t* flag, c64* acc, cudaStream_t st);
+int64_t flag_compact_blocks(int64_t n);  // entries of the counts scratch of launch_flag_compact
+int launch_flag_compact(const uint8_t* flag, int64_t n, int64_t* counts, int64_t* out, int64_t* total, cudaStream_t st);
+int launch_gather_c64(const c64* v, const int64_t* idx, int64_t n, c64* out, cudaStream_t st);
+int launch_positions_to_values(const int64_t* pos, int64_t n, int lo, int32_t* out, cudaStream_t st);
 }  // namespace sfft

@@ -45,13 +45,16 @@ template <class T> __device__ __forceinline__ T cos2pi_frac(int64_t num, int64_t
     else return cospi(2.0 * ((double)num / (double)M));
 }
 
+// f at the plan's lattice nodes.  The kernels are evaluated in FP64 for either plan precision and
+// only the stored sample is rounded to T: an FP32 plan receives the correctly rounded FP32 value of
+// f at each node (not an FP32 Clenshaw sum, whose error grows with K).
 template <class T>
 __global__ void k_sop_sample(const InstDesc* __restrict__ insts, const int32_t* __restrict__ triples, int n_terms, int K,
                              const double* __restrict__ a64, void* out) {
-    __shared__ T sa[kMaxTerms * (kMaxK + 1)];
+    __shared__ double sa[kMaxTerms * (kMaxK + 1)];
     __shared__ int str[kMaxTerms * 3];
     const InstDesc& I = insts[0];
-    for (int i = threadIdx.x; i < n_terms * (K + 1); i += blockDim.x) sa[i] = (T)a64[i];
+    for (int i = threadIdx.x; i < n_terms * (K + 1); i += blockDim.x) sa[i] = a64[i];
     for (int i = threadIdx.x; i < n_terms * 3; i += blockDim.x) str[i] = triples[i];
     __syncthreads();
     const int L = I.L, d = I.d;
@@ -61,32 +64,34 @@ __global__ void k_sop_sample(const InstDesc* __restrict__ insts, const int32_t* 
         int l = 0;
         while (I.soff[l + 1] <= node) ++l;
         const int64_t j = node - I.soff[l], M = I.Ml[l];
-        T f = 0;
+        double f = 0;
         for (int m = 0; m < n_terms; ++m) {
-            T p = 1;
+            double p = 1;
             for (int u = 0; u < 3; ++u) {
                 int t = str[3 * m + u];
                 int64_t num = (j * (int64_t)I.z[l * d + t]) % M;
-                p *= clenshaw<T>(sa + m * (K + 1), K, cos2pi_frac<T>(num, M));
+                p *= clenshaw<double>(sa + m * (K + 1), K, cos2pi_frac<double>(num, M));
             }
             f += p;
         }
-        y[node] = cplx<T>{f, (T)0};
+        y[node] = cplx<T>{(T)f, (T)0};
     }
 }
 
+// theta-adjoint of k_sop_sample: the factors and their theta-derivatives are recomputed at every
+// node in FP64 (nothing is stored), the sample cotangent is read in the plan precision
 template <class T>
 __global__ void k_sop_backward(const InstDesc* __restrict__ insts, const int32_t* __restrict__ triples, int n_terms, int K,
                                const double* __restrict__ a64, const double* __restrict__ da64, const void* dsamples,
                                double* dtheta) {
-    __shared__ T sa[kMaxTerms * (kMaxK + 1)];
-    __shared__ T sda[kMaxTerms * (kMaxK + 1)];
+    __shared__ double sa[kMaxTerms * (kMaxK + 1)];
+    __shared__ double sda[kMaxTerms * (kMaxK + 1)];
     __shared__ int str[kMaxTerms * 3];
     __shared__ double red[32];
     const InstDesc& I = insts[0];
     for (int i = threadIdx.x; i < n_terms * (K + 1); i += blockDim.x) {
-        sa[i] = (T)a64[i];
-        sda[i] = (T)da64[i];
+        sa[i] = a64[i];
+        sda[i] = da64[i];
     }
     for (int i = threadIdx.x; i < n_terms * 3; i += blockDim.x) str[i] = triples[i];
     __syncthreads();
@@ -99,17 +104,17 @@ __global__ void k_sop_backward(const InstDesc* __restrict__ insts, const int32_t
         int l = 0;
         while (I.soff[l + 1] <= node) ++l;
         const int64_t j = node - I.soff[l], M = I.Ml[l];
-        const T wr = w[node].x;
+        const double wr = (double)w[node].x;
         for (int m = 0; m < n_terms; ++m) {
-            T g[3], dg[3];
+            double g[3], dg[3];
             for (int u = 0; u < 3; ++u) {
                 int t = str[3 * m + u];
                 int64_t num = (j * (int64_t)I.z[l * d + t]) % M;
-                T c = cos2pi_frac<T>(num, M);
-                g[u] = clenshaw<T>(sa + m * (K + 1), K, c);
-                dg[u] = clenshaw<T>(sda + m * (K + 1), K, c);
+                double c = cos2pi_frac<double>(num, M);
+                g[u] = clenshaw<double>(sa + m * (K + 1), K, c);
+                dg[u] = clenshaw<double>(sda + m * (K + 1), K, c);
             }
-            acc[m] += (double)(wr * (dg[0] * g[1] * g[2] + g[0] * dg[1] * g[2] + g[0] * g[1] * dg[2]));
+            acc[m] += wr * (dg[0] * g[1] * g[2] + g[0] * dg[1] * g[2] + g[0] * g[1] * dg[2]);
         }
     }
     for (int m = 0; m < n_terms; ++m) {

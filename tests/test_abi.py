@@ -135,7 +135,8 @@ def test_struct_layouts_match_the_header(tmp_path):
     except Exception:  # the binding module loads the library; read the classes from its source instead
         pytest.skip("binding module not importable without the library")
     pairs = {"sfft_params": N.Params, "sfft_diag": N.Diag, "sfft_dimincr_params": N.DimIncrParams,
-             "sfft_fn_sparse_poly_ctx": N.SparsePolyCtx, "sfft_fn_sop_ctx": N.SopCtx}
+             "sfft_fn_sparse_poly_ctx": N.SparsePolyCtx, "sfft_fn_sop_ctx": N.SopCtx,
+             "sfft_fn_bspline_ctx": N.BsplineCtx}
     lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "sfft.h"', "int main(void) {"]
     for cname, cls in pairs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')

@@ -306,6 +306,31 @@ def test_top_s_selection_with_ties(G):
         assert all(abs(mod[k] - cut) <= 1e-12 * cut for k in set(got.tolist()) - must)
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_top_s_rank_bits_near_ties_bit_exact(G, prec):
+    """Algorithm 4 with the rank_bits near-tie rule: moduli 5 (1 + eps_q) with |eps_q| <= 1e-6 agree
+    to 12 significant bits, so they rank by candidate index and the selection is unique: it must
+    equal the oracle's bit for bit (FP64 plans, and FP32 plans with refinement whose moduli carry
+    their own rounding)."""
+    cand, sup, c, z, M, L = cfg1(9, s=30)
+    rng = np.random.default_rng(4)
+    eps = rng.uniform(-1e-6, 1e-6, 30)
+    ph = np.exp(2j * np.pi * rng.random(30))
+    c = np.where(np.arange(30) % 3 == 2, 2.0, 5.0 * (1 + eps)) * ph
+    y = O.sample_sparse_poly(cand[sup], c, z, M)
+    if prec:
+        y = y.astype(np.complex64).astype(np.complex128)
+    import torch
+    for s_t in (4, 11, 19):
+        ref = O.reconstruct(cand, y, z, M, tau_rel=1e-5, s_tilde=s_t, theta=1.0, rank_bits=12,
+                            do_refine=bool(prec), refine_mode="bucket")
+        plan = G.Plan(T(cand), 30, L=L, M=[M] * L, z=z, precision=prec, tau_rel=1e-5, s_tilde=s_t, theta_abs=1.0,
+                      rank_bits=12, refine=prec)
+        supp, coef = plan.reconstruct(T(y, torch.complex64 if prec else torch.complex128))
+        assert np.array_equal(supp.cpu().numpy(), ref.supp), s_t
+        plan.close()
+
+
 # ------------------------------------------------------------------ adjoint
 @pytest.mark.parametrize("prec", [0, 1])
 def test_backward_matches_oracle_vjp(G, prec):
