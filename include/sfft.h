@@ -174,12 +174,19 @@ int sfft_reconstruct(sfft_plan* plan, const void* samples, int64_t* supp_out, do
                      int64_t* n_out, sfft_diag* diag);
 
 /*
- * Vector-Jacobian product of the last sfft_reconstruct of this plan (refine == 0 only), with
- * the selected support and the median's selected lattices held fixed: coefficient q is
- * Re ghat^(l_re)_{h} + i Im ghat^(l_im)_{h}, so the cotangents are scattered into those
- * buckets and mapped back by the adjoint of the 1/M-normalised DFT (an inverse prime-length
- * FFT).  dcoef: device complex double [n_out of that call] (dL/dRe + i dL/dIm);
+ * Vector-Jacobian product of the last sfft_reconstruct of this plan (median combine, with or
+ * without the refinement step), with the selected support and the lattices every median selected
+ * held fixed.  The median coefficient is Re ghat^(l_re)_h + i Im ghat^(l_im)_h (eq. 2.6); the
+ * refinement adds Re rhat^(m_re)_h + i Im rhat^(m_im)_h with rhat = ghat - C and C the median
+ * coefficients summed into their buckets (eq. 2.3), so the map samples -> coefficients is linear
+ * and its adjoint is: the cotangents into the refinement's selected buckets, minus their gather
+ * over all lattices into the median coefficients of the whole detected set, those into the
+ * median's selected buckets, then the adjoint of the 1/M-normalised DFT (an inverse prime-length
+ * transform, run in FP64 for every plan precision).
+ * dcoef: device complex double [n_out of that call] (dL/dRe + i dL/dIm);
  * dsamples: device complex in the plan precision [sum M] (overwritten).
+ * The first call on a plan allocates the adjoint's job list (and, for FP32 plans, an FP64 buffer
+ * of sum M complex values); later calls allocate nothing.  Synchronises the plan's stream.
  */
 int sfft_reconstruct_backward(sfft_plan* plan, const double* dcoef, void* dsamples);
 

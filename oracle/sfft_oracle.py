@@ -843,3 +843,73 @@ def reconstruct_vjp(samples, det_H, M_list, dcoef):
         m = int(M_list[l])
         out.append(np.fft.ifft(gb[l]))  # (1/M) sum_h g_h e^{+2 pi i jh/M}
     return np.concatenate(out)
+
+
+def _bucket_sum(h, v, M):
+    """C[b] = sum of v over the entries with h == b (complex), b < M."""
+    return np.bincount(h, weights=v.real, minlength=M) + 1j * np.bincount(h, weights=v.imag, minlength=M)
+
+
+def refine_selection(samples, H, M_list):
+    """The lattices both medians of a median + one-refinement reconstruction pick, per detected
+    frequency (rows of H, the hashes of the detected set): (lre, lim) of the median combine (eq. 2.6)
+    and (mre, mim) of the refinement's median of rhat = ghat - C (C: the median coefficients summed
+    into their buckets, eq. 2.3).  Returns (lre, lim, mre, mim, pcheck, refined)."""
+    L = H.shape[1]
+    sl = split_lattices(np.asarray(samples, dtype=np.complex128), M_list)
+    ghat = [lattice_dft(sl[l], int(M_list[l])) for l in range(L)]
+    vals = gather(ghat, H)
+    lre, lim = median_selection(vals)
+    pcheck = median_pair(vals)
+    rh = [ghat[l] - _bucket_sum(H[:, l], pcheck, int(M_list[l])) for l in range(L)]
+    rvals = gather(rh, H)
+    mre, mim = median_selection(rvals)
+    return lre, lim, mre, mim, pcheck, pcheck + median_pair(rvals)
+
+
+def refined_map(samples, H, M_list, sel, out_pos):
+    """The linear map samples -> refined coefficients of the detected frequencies at out_pos with the
+    selections sel = (lre, lim, mre, mim) held fixed: c = pcheck + Delta, pcheck_q = Re ghat^(lre_q)
+    + i Im ghat^(lim_q) at h_q, Delta_q = Re rhat^(mre_q) + i Im rhat^(mim_q), rhat = ghat - C, C the
+    pcheck of every detected frequency summed into its buckets.  Only the selected bucket values are
+    gathered (one per frequency and component)."""
+    lre, lim, mre, mim = sel
+    L = H.shape[1]
+    nd = H.shape[0]
+    q = np.arange(nd)
+    offs = np.concatenate([[0], np.cumsum(M_list)]).astype(np.int64)
+    sl = split_lattices(np.asarray(samples, dtype=np.complex128), M_list)
+    ghat = np.concatenate([lattice_dft(sl[l], int(M_list[l])) for l in range(L)])
+    pcheck = ghat[offs[lre] + H[q, lre]].real + 1j * ghat[offs[lim] + H[q, lim]].imag
+    C = np.concatenate([_bucket_sum(H[:, l], pcheck, int(M_list[l])) for l in range(L)])
+    rhat = ghat - C
+    p = np.asarray(out_pos)
+    return pcheck[p] + rhat[offs[mre[p]] + H[p, mre[p]]].real + 1j * rhat[offs[mim[p]] + H[p, mim[p]]].imag
+
+
+def reconstruct_vjp_refined(samples, H, M_list, out_pos, dcoef):
+    """Vector-Jacobian product of refined_map at these samples with the selections of the samples
+    themselves held fixed.  Cotangents W (dcoef at out_pos, 0 elsewhere on the detected set) enter
+    the refinement's buckets (G1: Re W at (mre, h), Im W at (mim, h)); the median coefficients get
+    V = W - sum_l G1_l[h_ql] (the path through C); V enters the median's buckets (G2); the sample
+    cotangent is A^H (G1 + G2), (A^H g)_j = (1/M) sum_h g_h exp(+2 pi i j h / M)."""
+    L = H.shape[1]
+    nd = H.shape[0]
+    lre, lim, mre, mim, _, _ = refine_selection(samples, H, M_list)
+    q = np.arange(nd)
+    W = np.zeros(nd, dtype=np.complex128)
+    W[np.asarray(out_pos)] = dcoef
+    G1 = []
+    for l in range(L):
+        a, b = q[mre == l], q[mim == l]
+        M = int(M_list[l])
+        G1.append(np.bincount(H[a, l], weights=W[a].real, minlength=M)
+                  + 1j * np.bincount(H[b, l], weights=W[b].imag, minlength=M))
+    V = W - sum(G1[l][H[:, l]] for l in range(L))
+    G = []
+    for l in range(L):
+        a, b = q[lre == l], q[lim == l]
+        M = int(M_list[l])
+        G.append(G1[l] + np.bincount(H[a, l], weights=V[a].real, minlength=M)
+                 + 1j * np.bincount(H[b, l], weights=V[b].imag, minlength=M))
+    return np.concatenate([np.fft.ifft(G[l]) for l in range(L)])

@@ -203,7 +203,7 @@ int Plan::build_jobs() {
     const size_t e = esz();
     char* ghat_b = (char*)ghat;
     const int fp = fwd_prec();
-    jobs_fwd.clear(); jobs_samp.clear(); jobs_adj.clear();
+    jobs_fwd.clear(); jobs_samp.clear();
     for (int l = 0; l < L; ++l) {
         const FftTables* t = tabs[l];
         const int64_t o = soff[l];
@@ -222,13 +222,29 @@ int Plan::build_jobs() {
         sj.io_flags = 16 | 32; sj.io_off = o; sj.inst = 0;
         sj.scratch = buf_mode(prec) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
         jobs_samp.push_back(sj);
-        // adjoint: out (launch argument) = (1/M) IDFT(C), plan precision
-        BlueJob aj = make_blue_job(t, prec, 1, 1.0 / (double)M[l]);
-        aj.in = C + o; aj.io_flags = 4; aj.io_off = o;
-        aj.scratch = sj.scratch;
-        jobs_adj.push_back(aj);
     }
     return SFFT_OK;
+}
+
+// The adjoint's inverse lattice transforms run in FP64 for every plan precision (their output, the
+// sample cotangent, is rounded to the plan precision only at the end).  Built on the first backward
+// call: the job list, a global work buffer when a length fits neither one CTA nor a two-CTA cluster
+// in FP64, and for FP32 plans an FP64 output buffer.
+int Plan::prepare_adjoint() {
+    if (d_jobs_adj) return SFFT_OK;
+    const int mode = buf_mode(0);
+    void* scr = nullptr;
+    if (mode == 0) SFFT_TRY(alloc(&scr, sizeof(c64) * (size_t)maxN * L));
+    if (prec != SFFT_FP64) SFFT_TRY(alloc((void**)&adj_out, sizeof(c64) * (size_t)sumM));
+    jobs_adj.clear();
+    for (int l = 0; l < L; ++l) {
+        // out (launch argument) = (1/M) IDFT(C) in FP64
+        BlueJob aj = make_blue_job(tabs[l], 0, 1, 1.0 / (double)M[l]);
+        aj.in = C + soff[l]; aj.io_flags = 4; aj.io_off = soff[l];
+        aj.scratch = mode ? nullptr : (char*)scr + (size_t)l * maxN * sizeof(c64);
+        jobs_adj.push_back(aj);
+    }
+    return upload_jobs(jobs_adj, &d_jobs_adj, &allocs);
 }
 
 // upload a job list into a device array (static lists: once at plan creation)
@@ -379,6 +395,8 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     SFFT_TRY(P->alloc((void**)&P->coef, sizeof(c64) * cap));
     SFFT_TRY(P->alloc((void**)&P->H, sizeof(int32_t) * cap * L));
     SFFT_TRY(P->alloc((void**)&P->sel, 2 * cap));
+    if (p.refine) SFFT_TRY(P->alloc((void**)&P->rsel, 2 * cap));
+    SFFT_TRY(P->alloc((void**)&P->adj_w, sizeof(c64) * cap));
     SFFT_TRY(P->alloc((void**)&P->outpos, sizeof(int32_t) * cap));
     SFFT_TRY(P->alloc((void**)&P->coll, sizeof(int32_t) * P->sumM));
     SFFT_TRY(P->alloc((void**)&P->C, sizeof(c64) * P->sumM));
@@ -406,6 +424,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     I.cand = cand; I.cand_i8 = p.cand_type == SFFT_CAND_I8; I.cand_ld = p.cand_ld; I.z = dz; I.Ml = dM; I.mu = dmu; I.offk = doffk; I.soff = dsoff; I.boff = dboff;
     I.nzbits = P->nzbits; I.ghat = P->ghat; I.stats = P->stats; I.detbits = P->detbits; I.det = P->det;
     I.cnt = P->cnt; I.coef = P->coef; I.H = P->H; I.sel = P->sel; I.coll = P->coll; I.C = P->C;
+    I.rsel = P->rsel; I.adj_w = P->adj_w;
     I.ghat_lo = P->ghat_lo; I.lsq_work = P->lsq_work; I.outpos = P->outpos;
     I.lsq_next = P->lsq_next; I.lsq_pairs = P->lsq_pairs; I.lsq_pair_cap = P->lsq_pair_cap;
     SFFT_CU(cudaEventCreateWithFlags(&P->io_ev, cudaEventDisableTiming));
@@ -422,7 +441,6 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     SFFT_TRY(P->build_jobs());
     SFFT_TRY(upload_jobs(P->jobs_fwd, &P->d_jobs_fwd, &P->allocs));
     SFFT_TRY(upload_jobs(P->jobs_samp, &P->d_jobs_samp, &P->allocs));
-    SFFT_TRY(upload_jobs(P->jobs_adj, &P->d_jobs_adj, &P->allocs));
     // hash-count kernel choice; lattices split into groups whose bitmaps fit shared memory
     int64_t maxM = *std::max_element(P->M.begin(), P->M.end());
     P->packed = P->kmax <= 127 && maxM <= 32768;
@@ -703,14 +721,19 @@ int sfft_reconstruct_backward(sfft_plan* plan, const double* dcoef, void* dsampl
     if (!plan || !dsamples) { set_error("null argument"); return SFFT_EINVAL; }
     Plan* P = reinterpret_cast<Plan*>(plan);
     SFFT_CHECK(P->have_forward, SFFT_ESTATE, "sfft_reconstruct_backward before sfft_reconstruct");
-    SFFT_CHECK(P->p.refine == 0, SFFT_ESTATE, "the adjoint is defined for refine == 0 plans");
     SFFT_CHECK(P->p.combine == SFFT_COMBINE_MEDIAN, SFFT_ESTATE, "the adjoint is defined for the median combine");
+    SFFT_TRY(P->prepare_adjoint());
     cudaStream_t st = P->st;
     SFFT_CU(cudaMemsetAsync(P->C, 0, sizeof(c64) * P->sumM, st));
-    if (P->last_nout > 0 && dcoef) SFFT_TRY(launch_adj_scatter(P->d_inst, reinterpret_cast<const c64*>(dcoef), st));
-    // dsamples = A^H gbar with (A^H g)_j = (1/M) sum_h g_h exp(+2 pi i j h / M)
-    SFFT_TRY(launch_bluestein(P->d_jobs_adj, P->L, P->maxN, P->buf_mode(P->prec), P->prec, 0, P->prec, +1, EPI_PLAIN,
-                              P->d_inst, st, dsamples, nullptr));
+    SFFT_CU(cudaMemsetAsync(P->adj_w, 0, sizeof(c64) * P->cap, st));
+    SFFT_TRY(launch_adjoint_buckets(P->d_inst, P->last_nout > 0 ? reinterpret_cast<const c64*>(dcoef) : nullptr,
+                                    P->p.refine != 0, P->cap, st));
+    // dsamples = A^H gbar with (A^H g)_j = (1/M) sum_h g_h exp(+2 pi i j h / M), in FP64
+    void* out = P->prec == SFFT_FP64 ? dsamples : (void*)P->adj_out;
+    SFFT_TRY(launch_bluestein(P->d_jobs_adj, P->L, P->maxN, P->buf_mode(0), 0, 0, 0, +1, EPI_PLAIN, P->d_inst, st, out,
+                              nullptr));
+    if (P->prec != SFFT_FP64)
+        SFFT_TRY(launch_c64_to_c32(P->adj_out, reinterpret_cast<c32*>(dsamples), P->sumM, st));
     SFFT_CU(cudaStreamSynchronize(st));
     return SFFT_OK;
 }

@@ -262,6 +262,8 @@ struct InstDesc {
     c64* coef;                 // [cap]
     int32_t* H;                // [cap, L]
     uint8_t* sel;              // [cap, 2] lattice of the Re / Im median
+    uint8_t* rsel;             // [cap, 2] lattice of the refinement's Re / Im median (refine plans)
+    c64* adj_w;                // [cap] adjoint: cotangents of the detected set
     int32_t* coll;             // [sum M] collision counts
     c64* C;                    // [sum M] bucket scatter buffer
     c32* ghat_lo;              // [sum M] low words of a double-float forward transform, or NULL

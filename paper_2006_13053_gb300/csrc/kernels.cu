@@ -846,6 +846,10 @@ __global__ void k_refine_update(const InstDesc* __restrict__ insts) {
             if (lane == 0) {
                 const c64 c = I.coef[q];
                 I.coef[q] = c64{c.x + (double)dre, c.y + (double)dim};
+                if (I.rsel) {
+                    I.rsel[2 * q] = (uint8_t)lre;
+                    I.rsel[2 * q + 1] = (uint8_t)lim;
+                }
             }
         }
         return;
@@ -874,6 +878,10 @@ __global__ void k_refine_update(const InstDesc* __restrict__ insts) {
         if (lane == 0) {
             const c64 c = I.coef[q];
             I.coef[q] = c64{c.x + dre, c.y + dim};
+            if (I.rsel) {
+                I.rsel[2 * q] = (uint8_t)lre;
+                I.rsel[2 * q + 1] = (uint8_t)lim;
+            }
         }
     }
 }
@@ -1264,17 +1272,63 @@ __global__ void k_scatter_terms(const InstDesc* __restrict__ insts) {
     }
 }
 
-// adjoint: scatter coefficient cotangents into the buckets that the medians selected
-__global__ void k_adj_scatter(const InstDesc* __restrict__ insts, const c64* __restrict__ dcoef) {
+// ---- adjoint (vector-Jacobian product) with the support and every median's selected lattices held
+// fixed.  The median coefficient is p_q = Re ghat^(lre)_h + i Im ghat^(lim)_h; with one refinement
+// step c_q = p_q + Re rhat^(mre)_h + i Im rhat^(mim)_h, rhat = ghat - C, C_l[h] = sum of p over the
+// detected frequencies in bucket h.  Both are linear in ghat, so the cotangent of ghat is G1 + G2:
+// G1 puts the output cotangents W into the refinement's selected buckets, the median coefficients
+// receive V = W - sum_l G1_l[h_ql] (their path through C), and G2 puts V into the median's buckets.
+// Without refinement G1 = 0 and V = W.  The sample cotangent is the adjoint of the 1/M-normalised
+// DFT applied to G (an inverse transform).
+
+// W: dense cotangents of the detected set (adj_w cleared before; 0 for frequencies not selected)
+__global__ void k_adj_dense(const InstDesc* __restrict__ insts, const c64* __restrict__ dcoef) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nout = min(I.cnt[1], min(I.out_cap, I.cap));
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nout; p += (int64_t)gridDim.x * blockDim.x)
+        I.adj_w[I.outpos[p]] = dcoef[p];
+}
+
+// G1: W into the buckets the refinement's median selected (C holds the cotangent of ghat)
+__global__ void k_adj_refine_scatter(const InstDesc* __restrict__ insts) {
+    const InstDesc& I = insts[blockIdx.y];
+    const int64_t nd = min(I.cnt[0], I.cap);
     const int L = I.L;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < nout; p += (int64_t)gridDim.x * blockDim.x) {
-        int64_t q = I.outpos[p];
-        int lre = I.sel[2 * q], lim = I.sel[2 * q + 1];
-        c64 g = dcoef[p];
-        atomicAdd(&I.C[I.soff[lre] + I.H[q * L + lre]].x, g.x);
-        atomicAdd(&I.C[I.soff[lim] + I.H[q * L + lim]].y, g.y);
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nd; q += (int64_t)gridDim.x * blockDim.x) {
+        const c64 w = I.adj_w[q];
+        const int mre = I.rsel[2 * q], mim = I.rsel[2 * q + 1];
+        if (w.x != 0.0) atomicAdd(&I.C[I.soff[mre] + I.H[q * L + mre]].x, w.x);
+        if (w.y != 0.0) atomicAdd(&I.C[I.soff[mim] + I.H[q * L + mim]].y, w.y);
+    }
+}
+
+// V = W - sum_l G1_l[h_ql], in place (G1 is only read here)
+__global__ void k_adj_refine_gather(const InstDesc* __restrict__ insts) {
+    const InstDesc& I = insts[blockIdx.y];
+    const int64_t nd = min(I.cnt[0], I.cap);
+    const int L = I.L;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nd; q += (int64_t)gridDim.x * blockDim.x) {
+        double sx = 0.0, sy = 0.0;
+        for (int l = 0; l < L; ++l) {
+            const c64 g = I.C[I.soff[l] + I.H[q * L + l]];
+            sx += g.x;
+            sy += g.y;
+        }
+        const c64 w = I.adj_w[q];
+        I.adj_w[q] = c64{w.x - sx, w.y - sy};
+    }
+}
+
+// G2: V into the buckets the combine's median selected (added to G1)
+__global__ void k_adj_median_scatter(const InstDesc* __restrict__ insts) {
+    const InstDesc& I = insts[blockIdx.y];
+    const int64_t nd = min(I.cnt[0], I.cap);
+    const int L = I.L;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < nd; q += (int64_t)gridDim.x * blockDim.x) {
+        const c64 v = I.adj_w[q];
+        const int lre = I.sel[2 * q], lim = I.sel[2 * q + 1];
+        if (v.x != 0.0) atomicAdd(&I.C[I.soff[lre] + I.H[q * L + lre]].x, v.x);
+        if (v.y != 0.0) atomicAdd(&I.C[I.soff[lim] + I.H[q * L + lim]].y, v.y);
     }
 }
 
@@ -1492,9 +1546,20 @@ int launch_scatter_terms(const InstDesc* di, int ninst, int64_t max_terms_x_L, c
     return launch_check("k_scatter_terms");
 }
 
-int launch_adj_scatter(const InstDesc* di, const c64* dcoef, cudaStream_t st) {
-    k_adj_scatter<<<dim3(64, 1), 256, 0, st>>>(di, dcoef);
-    return launch_check("k_adj_scatter");
+int launch_adjoint_buckets(const InstDesc* di, const c64* dcoef, bool refine, int64_t maxdet, cudaStream_t st) {
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(4 * 152, (maxdet + 255) / 256));
+    if (dcoef) {
+        k_adj_dense<<<dim3(gx, 1), 256, 0, st>>>(di, dcoef);
+        SFFT_TRY(launch_check("k_adj_dense"));
+    }
+    if (refine) {
+        k_adj_refine_scatter<<<dim3(gx, 1), 256, 0, st>>>(di);
+        SFFT_TRY(launch_check("k_adj_refine_scatter"));
+        k_adj_refine_gather<<<dim3(gx, 1), 256, 0, st>>>(di);
+        SFFT_TRY(launch_check("k_adj_refine_gather"));
+    }
+    k_adj_median_scatter<<<dim3(gx, 1), 256, 0, st>>>(di);
+    return launch_check("k_adj_median_scatter");
 }
 
 int launch_points(const InstDesc* di, int32_t* numer, double* x, int64_t tot, cudaStream_t st) {

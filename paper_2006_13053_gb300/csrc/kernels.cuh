@@ -21,7 +21,9 @@ int launch_lsq(InstDesc* di, int ninst, int prec, cudaStream_t st);
 int launch_scatter_coef(const InstDesc* di, int ninst, bool f32, cudaStream_t st);
 int launch_select(InstDesc* di, int ninst, cudaStream_t st);
 int launch_scatter_terms(const InstDesc* di, int ninst, int64_t max_terms_x_L, cudaStream_t st);
-int launch_adj_scatter(const InstDesc* di, const c64* dcoef, cudaStream_t st);
+// adjoint cotangent of the lattice DFTs into I.C (cleared before), from the output cotangents dcoef
+// (NULL: zero) through the optional refinement step and the median (see kernels.cu)
+int launch_adjoint_buckets(const InstDesc* di, const c64* dcoef, bool refine, int64_t maxdet, cudaStream_t st);
 int launch_points(const InstDesc* di, int32_t* numer, double* x, int64_t tot, cudaStream_t st);
 int launch_cand_stats(const void* cand, int i8, int ld, int64_t n, int d, int* mn, int* mx, cudaStream_t st);
 int launch_to_c64(const void* src, int prec, c64* dst, int64_t n, cudaStream_t st);

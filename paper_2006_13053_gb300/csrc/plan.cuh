@@ -70,6 +70,9 @@ struct Plan {
     c64* coef = nullptr;
     int32_t* H = nullptr;
     uint8_t* sel = nullptr;
+    uint8_t* rsel = nullptr;      // refinement's selected lattices (refine plans)
+    c64* adj_w = nullptr;         // adjoint cotangents of the detected set
+    c64* adj_out = nullptr;       // FP64 sample cotangents of FP32 plans (first backward call)
     int32_t* outpos = nullptr;
     int32_t* coll = nullptr;
     c64* C = nullptr;
@@ -109,6 +112,7 @@ struct Plan {
     bool fits_smem(int tprec) const;
     int buf_mode(int tprec) const;  // work-buffer mode of the transforms in precision tprec
     int build_jobs();
+    int prepare_adjoint();
     int hash_grid() const;
     PipeArgs pipe_args();
 };

@@ -134,6 +134,11 @@ def sop_params(d: int, n_terms: int, seed: int, stream: int = S_SOP, lo: float =
     return triples, theta
 
 
+def sop_theta(n_terms: int, seed: int, stream: int = S_MISC, lo: float = 0.5, hi: float = 2.0) -> np.ndarray:
+    """Another draw of theta_m ~ U[lo, hi] for the same triples (e.g. the target parameters)."""
+    return rng(seed, stream).uniform(lo, hi, size=n_terms)
+
+
 def sop_candidate_set(triples: np.ndarray, d: int, kmax: int, n_total: int, box: int, seed: int,
                       stream: int = S_GAMMA) -> np.ndarray:
     """Candidate set for the sum-of-products workload: every k supported on one of the

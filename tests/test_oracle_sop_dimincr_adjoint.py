@@ -100,3 +100,44 @@ def test_adjoint_matches_finite_differences():
             fd = (0.5 * np.sum(np.abs(coefs(yp) - target) ** 2) - 0.5 * np.sum(np.abs(coefs(ym) - target) ** 2)) / (2 * h)
             an = gy[j].real if unit == 1.0 else gy[j].imag
             assert an == pytest.approx(fd, abs=1e-7)
+
+
+def test_refined_adjoint_matches_finite_differences():
+    """The adjoint through one refinement step: the gradient of 0.5 |c - t|^2 with c the refined
+    coefficients of the selected frequencies, w.r.t. the samples, vs central finite differences of
+    the oracle's own reconstruction (selections recomputed at every perturbed point: a small step
+    changes none).  Aliasing with L = 7 and M = 89 makes the C path (other detected frequencies in
+    the same bucket) contribute."""
+    d, n, s, M, L = 3, 300, 10, 89, 7
+    cand = S.uniform_distinct(n, d, -10, 10, 4)
+    sup = S.support_indices(n, s, 4)
+    c = S.coef_cgauss(s, 4)
+    z = S.generators(L, d, M, 4)
+    y = O.sample_sparse_poly(cand[sup], c, z, M) + S.noise(L * M, 0.05, 4)
+    kw = dict(tau_abs=0.02, do_refine=True, refine_mode="bucket", s_tilde=8)
+    r = O.reconstruct(cand, y, z, M, **kw)
+    H = O.hashes(cand[r.detected], z, M)
+    pos = np.searchsorted(r.detected, r.supp)
+    sel = O.refine_selection(y, H, [M] * L)
+    assert np.allclose(O.refined_map(y, H, [M] * L, sel[:4], pos), r.coef, atol=1e-13)
+    assert np.allclose(sel[5][pos], r.coef, atol=1e-13)
+    target = r.coef + 0.1 - 0.05j
+    gy = O.reconstruct_vjp_refined(y, H, [M] * L, pos, r.coef - target)
+    # the refinement's C path is exercised: some detected frequencies share buckets
+    assert any(np.bincount(H[:, l], minlength=M).max() > 1 for l in range(L))
+
+    def loss(yy):
+        rr = O.reconstruct(cand, yy, z, M, **kw)
+        assert np.array_equal(rr.supp, r.supp)
+        return 0.5 * np.sum(np.abs(rr.coef - target) ** 2)
+
+    rng = np.random.default_rng(0)
+    h = 1e-7
+    for j in rng.choice(L * M, 10, replace=False):
+        for unit in (1.0, 1j):
+            yp, ym = y.copy(), y.copy()
+            yp[j] += h * unit
+            ym[j] -= h * unit
+            fd = (loss(yp) - loss(ym)) / (2 * h)
+            an = gy[j].real if unit == 1.0 else gy[j].imag
+            assert an == pytest.approx(fd, abs=1e-7)
