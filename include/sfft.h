@@ -133,6 +133,26 @@ typedef struct sfft_plan sfft_plan;
 int sfft_plan_create(sfft_plan** out, int d, const void* cand, int64_t n_cand, int64_t s, int L,
                      const int64_t* M, const int64_t* z, const sfft_params* p, void* stream);
 
+/*
+ * Rebind the plan to another candidate set Gamma' (same row layout, n_cand <= the n_cand the plan was
+ * created with, every |k_t| within the plan's creation bound, N_Gamma' < every M_l: then the
+ * lattices, tables, hash offsets and kernel choice stay valid).  Nothing is allocated; the rows
+ * are scanned for their bounds (synchronises the plan's stream).  Returns SFFT_EINVAL or
+ * SFFT_EALIAS when the set does not fit the plan.  Batches created earlier keep the old set.
+ * (Repeated experiments on fixed lattices, e.g. the PFP/PFN audit of Section 4.1, use it to
+ * reconstruct on a fresh random candidate set per repetition.)
+ */
+int sfft_plan_set_candidates(sfft_plan* plan, const void* cand, int64_t n_cand);
+
+/*
+ * Replace the generating vectors (host int64 [L, d], 0 <= z < M_l; the lattice sizes stay): a new
+ * random lattice configuration on the same plan, nothing allocated.  Synchronises the plan's
+ * stream first.  Batches containing the plan read the same device array, so their later calls
+ * use the new vectors too.  (Section 4.1.3's experiment draws a fresh configuration per
+ * repetition on fixed Gamma and I.)
+ */
+int sfft_plan_set_generators(sfft_plan* plan, const int64_t* z);
+
 /* L, the lattice sizes M (host int64 [L], optional), z (host int64 [L*d], optional) and the
  * total number of samples sum_l M_l (optional). */
 int sfft_plan_info(const sfft_plan* plan, int* L, int64_t* M, int64_t* z, int64_t* n_samples);

@@ -87,6 +87,8 @@ def _sig(name, res, args):
 
 sfft_params_default = _sig("sfft_params_default", None, [_P(Params)])
 sfft_plan_create = _sig("sfft_plan_create", _i32, [_P(_vp), _i32, _vp, _i64, _i64, _i32, _vp, _vp, _P(Params), _vp])
+sfft_plan_set_candidates = _sig("sfft_plan_set_candidates", _i32, [_vp, _vp, _i64])
+sfft_plan_set_generators = _sig("sfft_plan_set_generators", _i32, [_vp, _vp])
 sfft_plan_info = _sig("sfft_plan_info", _i32, [_vp, _P(_i32), _vp, _vp, _P(_i64)])
 sfft_plan_destroy = _sig("sfft_plan_destroy", None, [_vp])
 sfft_sample_points = _sig("sfft_sample_points", _i32, [_vp, _vp, _vp, _vp])

@@ -89,6 +89,22 @@ class Plan:
         except Exception:
             pass
 
+    def set_candidates(self, cand):
+        """Rebind to another candidate set of the same layout (at most the creation size, |k_t|
+        within the creation bound); kept referenced like the first one."""
+        if cand.dtype != self.cand.dtype or cand.dim() != 2 or cand.shape[1] != self.cand.shape[1]:
+            raise ValueError("the new candidate rows need the plan's dtype and row width")
+        _req(cand, cand.dtype, "cand")
+        N.check(N.sfft_plan_set_candidates(self.handle, C.c_void_p(cand.data_ptr()), int(cand.shape[0])))
+        self.cand = cand
+        self.n = int(cand.shape[0])
+
+    def set_generators(self, z):
+        """New generating vectors (int [L, d], 0 <= z < M_l) on the same lattice sizes."""
+        z = np.ascontiguousarray(np.asarray(z, dtype=np.int64).reshape(self.L, self.d))
+        N.check(N.sfft_plan_set_generators(self.handle, z.ctypes.data_as(C.c_void_p)))
+        self.z = z.copy()
+
     # ---------------------------------------------------------------- nodes and samplers
     def sample_points(self):
         """(numerators int32 [sum M, d], x float64 [sum M, d]) of eq. (2.1)."""

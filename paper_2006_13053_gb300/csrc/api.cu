@@ -255,6 +255,30 @@ int upload_jobs(const std::vector<BlueJob>& v, BlueJob** dst, std::vector<void*>
     return SFFT_OK;
 }
 
+// N_Gamma = max_t (max k_t - min k_t) (eq. 2.4) and max |k_t| of n candidate rows in the plan's layout
+static int candidate_bounds(Plan* P, const void* cand, int64_t n, int64_t* NG_out, int64_t* kmax_out) {
+    const int d = P->d;
+    cudaStream_t st = P->st;
+    if (!P->d_minmax) SFFT_TRY(P->alloc((void**)&P->d_minmax, sizeof(int) * 2 * kMaxD));
+    int* dmn = P->d_minmax;
+    int* dmx = P->d_minmax + kMaxD;
+    std::vector<int> mn(d, INT32_MAX), mx(d, INT32_MIN);
+    SFFT_CU(cudaMemcpyAsync(dmn, mn.data(), sizeof(int) * d, cudaMemcpyHostToDevice, st));
+    SFFT_CU(cudaMemcpyAsync(dmx, mx.data(), sizeof(int) * d, cudaMemcpyHostToDevice, st));
+    SFFT_TRY(launch_cand_stats(cand, P->p.cand_type == SFFT_CAND_I8, P->p.cand_ld, n, d, dmn, dmx, st));
+    SFFT_CU(cudaMemcpyAsync(mn.data(), dmn, sizeof(int) * d, cudaMemcpyDeviceToHost, st));
+    SFFT_CU(cudaMemcpyAsync(mx.data(), dmx, sizeof(int) * d, cudaMemcpyDeviceToHost, st));
+    SFFT_CU(cudaStreamSynchronize(st));
+    int64_t NG = 0, kmax = 0;
+    for (int t = 0; t < d; ++t) {
+        NG = std::max<int64_t>(NG, (int64_t)mx[t] - mn[t]);
+        kmax = std::max<int64_t>(kmax, std::max<int64_t>(std::llabs(mn[t]), std::llabs(mx[t])));
+    }
+    *NG_out = NG;
+    *kmax_out = kmax;
+    return SFFT_OK;
+}
+
 int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin, const int64_t* Min,
                 const int64_t* zin, const sfft_params* pin, cudaStream_t st) {
     sfft_params p;
@@ -305,25 +329,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
         SFFT_CHECK(is_prime(P->M[l]), SFFT_ENOTPRIME, "M_%d=%lld is not prime", l, (long long)P->M[l]);
     }
     // ---- candidate bounds: N_Gamma (eq. 2.4) and max |k_t|
-    {
-        int *dmn = nullptr, *dmx = nullptr;
-        SFFT_TRY(P->alloc((void**)&dmn, sizeof(int) * d));
-        SFFT_TRY(P->alloc((void**)&dmx, sizeof(int) * d));
-        std::vector<int> mn(d, INT32_MAX), mx(d, INT32_MIN);
-        SFFT_CU(cudaMemcpyAsync(dmn, mn.data(), sizeof(int) * d, cudaMemcpyHostToDevice, st));
-        SFFT_CU(cudaMemcpyAsync(dmx, mx.data(), sizeof(int) * d, cudaMemcpyHostToDevice, st));
-        SFFT_TRY(launch_cand_stats(cand, p.cand_type == SFFT_CAND_I8, p.cand_ld, n, d, dmn, dmx, st));
-        SFFT_CU(cudaMemcpyAsync(mn.data(), dmn, sizeof(int) * d, cudaMemcpyDeviceToHost, st));
-        SFFT_CU(cudaMemcpyAsync(mx.data(), dmx, sizeof(int) * d, cudaMemcpyDeviceToHost, st));
-        SFFT_CU(cudaStreamSynchronize(st));
-        int64_t NG = 0, kmax = 0;
-        for (int t = 0; t < d; ++t) {
-            NG = std::max<int64_t>(NG, (int64_t)mx[t] - mn[t]);
-            kmax = std::max<int64_t>(kmax, std::max<int64_t>(std::llabs(mn[t]), std::llabs(mx[t])));
-        }
-        P->N_gamma = NG;
-        P->kmax = kmax;
-    }
+    SFFT_TRY(candidate_bounds(P, cand, n, &P->N_gamma, &P->kmax));
     for (int l = 0; l < L; ++l) {
         SFFT_CHECK(P->M[l] > P->N_gamma, SFFT_EALIAS,
                    "M_%d=%lld <= N_Gamma=%lld: |Gamma mod M| = |Gamma| is not guaranteed (pass an admissible M)", l,
@@ -363,6 +369,8 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     // ---- workspace
     const int64_t cap = std::min<int64_t>(n, p.detect_cap > 0 ? p.detect_cap : std::max<int64_t>(4 * s + 4096, 16384));
     P->cap = cap;
+    P->cap_alloc = cap;
+    P->n_alloc = n;
     const size_t e = P->esz();
     std::vector<int32_t> z32(P->z.begin(), P->z.end()), M32(P->M.begin(), P->M.end());
     std::vector<uint32_t> mu(L), offk(L);
@@ -375,6 +383,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     uint32_t *dmu, *doffk;
     int64_t* dsoff;
     SFFT_TRY(P->alloc((void**)&dz, sizeof(int32_t) * z32.size()));
+    P->d_z = dz;
     SFFT_TRY(P->alloc((void**)&dM, sizeof(int32_t) * L));
     SFFT_TRY(P->alloc((void**)&dmu, sizeof(uint32_t) * L));
     SFFT_TRY(P->alloc((void**)&doffk, sizeof(uint32_t) * L));
@@ -633,6 +642,63 @@ void sfft_plan_destroy(sfft_plan* plan) {
     cudaStreamSynchronize(P->st);
     P->release();
     delete P;
+}
+
+int sfft_plan_set_candidates(sfft_plan* plan, const void* cand, int64_t n_cand) {
+    if (!plan || !cand) { set_error("null argument"); return SFFT_EINVAL; }
+    Plan* P = reinterpret_cast<Plan*>(plan);
+    SFFT_CHECK(n_cand >= 1 && n_cand <= P->n_alloc, SFFT_EINVAL,
+               "n_cand = %lld must be in [1, %lld] (the plan's workspace size)", (long long)n_cand,
+               (long long)P->n_alloc);
+    const int d = P->d;
+    if (P->p.cand_type == SFFT_CAND_I32) {
+        const uintptr_t al = d % 4 == 0 ? 16 : d % 2 == 0 ? 8 : 4;
+        SFFT_CHECK((uintptr_t)cand % al == 0, SFFT_EINVAL,
+                   "int32 candidate rows of d = %d must start %d-byte aligned", d, (int)al);
+    } else {
+        SFFT_CHECK(((uintptr_t)cand & 3) == 0, SFFT_EINVAL, "int8 candidate rows must start 4-byte aligned");
+    }
+    SFFT_TRY(P->io_begin());
+    int64_t NG = 0, kmax = 0;
+    SFFT_TRY(candidate_bounds(P, cand, n_cand, &NG, &kmax));
+    // the hash offsets, the kernel choice and the overflow check were derived from the plan's bound
+    // on |k_t|: a set within that bound keeps them valid
+    SFFT_CHECK(kmax <= P->kmax, SFFT_EINVAL,
+               "max |k_t| = %lld exceeds the plan's %lld (create a new plan for this candidate set)",
+               (long long)kmax, (long long)P->kmax);
+    for (int l = 0; l < P->L; ++l)
+        SFFT_CHECK(P->M[l] > NG, SFFT_EALIAS, "M_%d=%lld <= N_Gamma=%lld of the new candidate set", l,
+                   (long long)P->M[l], (long long)NG);
+    P->cand = cand;
+    P->n = n_cand;
+    P->N_gamma = NG;
+    P->cap = std::min<int64_t>(n_cand, P->cap_alloc);
+    InstDesc& I = *P->h_inst;
+    I.cand = cand;
+    I.n = n_cand;
+    I.cap = P->cap;
+    SFFT_TRY(P->io_upload());
+    P->have_forward = false;
+    return SFFT_OK;
+}
+
+int sfft_plan_set_generators(sfft_plan* plan, const int64_t* z) {
+    if (!plan || !z) { set_error("null argument"); return SFFT_EINVAL; }
+    Plan* P = reinterpret_cast<Plan*>(plan);
+    const int L = P->L, d = P->d;
+    std::vector<int32_t> z32((size_t)L * d);
+    for (int l = 0; l < L; ++l)
+        for (int t = 0; t < d; ++t) {
+            const int64_t v = z[(size_t)l * d + t];
+            SFFT_CHECK(v >= 0 && v < P->M[l], SFFT_EINVAL, "z[%d][%d]=%lld outside [0, M)", l, t, (long long)v);
+            z32[(size_t)l * d + t] = (int32_t)v;
+        }
+    // the hash offsets depend on M and the bound on |k_t| only, the FFT tables on M only
+    SFFT_CU(cudaStreamSynchronize(P->st));  // no launch of this plan may still read the old vectors
+    SFFT_CU(cudaMemcpy(P->d_z, z32.data(), sizeof(int32_t) * z32.size(), cudaMemcpyHostToDevice));
+    for (size_t i = 0; i < z32.size(); ++i) P->z[i] = z[i];
+    P->have_forward = false;
+    return SFFT_OK;
 }
 
 int sfft_plan_info(const sfft_plan* plan, int* L, int64_t* M, int64_t* z, int64_t* n_samples) {

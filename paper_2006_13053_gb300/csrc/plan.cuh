@@ -53,6 +53,7 @@ struct PipeArgs {
 struct Plan {
     int d = 0, L = 0, prec = 0, nwords = 0, maxN = 0;
     int64_t n = 0, s = 0, sumM = 0, cap = 0, N_gamma = 0, kmax = 0, last_nout = 0;
+    int64_t n_alloc = 0, cap_alloc = 0;  // candidate count and detected capacity the workspace was sized for
     sfft_params p;
     const void* cand = nullptr;  // int32 or int8 rows (p.cand_type, p.cand_ld)
     cudaStream_t st = nullptr;
@@ -98,6 +99,8 @@ struct Plan {
     std::vector<std::pair<int, int>> hgroups;  // lattice groups whose bitmaps fit shared memory
     std::vector<size_t> hsmem;                 // shared memory of each group
     uint8_t* cnt8 = nullptr;
+    int* d_minmax = nullptr;      // [2 kMaxD] candidate bounds scratch
+    int32_t* d_z = nullptr;       // [L, d] generating vectors on the device
     bool diag_run = false;        // the current reconstruct writes per-candidate diagnostics
     bool have_forward = false;
     cudaEvent_t io_ev = nullptr;  // recorded after each upload of h_inst (staging reuse guard)
