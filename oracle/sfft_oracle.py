@@ -672,7 +672,7 @@ def pfp_pfn(cand, supp_idx, z, M):
     inI[supp_idx] = True
     pfn = inI & (med >= 2)
     pfp = (~inI) & (med >= 1)
-    return {"n_pfn": int(pfn.sum()), "n_pfp": int(pfp.sum()), "median": med, "ghat": ghat}
+    return {"n_pfn": int(pfn.sum()), "n_pfp": int(pfp.sum()), "median": med, "ghat": ghat, "samples": samples}
 
 
 # =========================================================================== Algorithm 3 (dimension-incremental)

@@ -186,3 +186,62 @@ def uneven_instances(n_inst: int, seed: int, d_range=(5, 20), n_range=(2 ** 14, 
 def uniform_tail(n: int, seed: int, stream: int = S_TAIL) -> np.ndarray:
     g = rng(seed, stream)
     return g.random(n)
+
+
+# --------------------------------------------------------------------------- audit inputs (Section 4.1)
+def uniform_distinct_device(n: int, d: int, lo: int, hi: int, seed: int, device, stream: int = S_GAMMA):
+    """n distinct integer vectors uniform in [lo, hi]^d drawn on a CUDA device (int32 tensor [n, d]).
+
+    Vectors are drawn with replacement (torch's device generator seeded from (seed, stream)), the
+    distinct ones kept, and a uniformly random n-subset of them taken: by exchangeability that is a
+    uniform n-subset of the box.  Rows come in random order.  For the PFP/PFN audit at |Gamma| = 10^7
+    (one fresh set per repetition), where a host generator would dominate the run time."""
+    import torch
+    W = hi - lo + 1
+    if W ** d >= 2 ** 62:
+        raise ValueError("the box is too large for 64-bit keys")
+    if n > W ** d:
+        raise ValueError("more distinct vectors requested than the box holds")
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) * 1000003 + int(stream))
+    mult = torch.tensor([W ** t for t in range(d)], dtype=torch.int64, device=device)
+    keys = torch.empty(0, dtype=torch.int64, device=device)
+    m = n + n // 64 + 1024
+    while True:
+        draw = torch.randint(0, W, (m, d), generator=g, device=device, dtype=torch.int64)
+        keys = torch.unique(torch.cat([keys, (draw * mult).sum(dim=1)]))
+        if keys.numel() >= n:
+            break
+        m = n - keys.numel() + n // 64 + 1024
+    keys = keys[torch.randperm(keys.numel(), generator=g, device=device)[:n]]
+    rows = torch.stack([(keys // (W ** t)) % W for t in range(d)], dim=1) + lo
+    return rows.to(torch.int32).contiguous()
+
+
+def subset_device(n: int, s: int, seed: int, device, stream: int = S_SUPPORT):
+    """s distinct indices into [0, n) drawn uniformly on a CUDA device (int64 tensor, ascending)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) * 1000003 + int(stream))
+    return torch.sort(torch.randperm(n, generator=g, device=device)[:s]).values
+
+
+def hyperbolic_cross_weighted(d: int, N: float, weights=None) -> np.ndarray:
+    """{k in Z^d : prod_t max(1, w_t |k_t|) <= N} (w_t = 1: the symmetric hyperbolic cross), int32
+    [n, d] in lexicographic order, enumerated dimension by dimension with the partial products
+    (vectorised).  Section 4.1.3 takes w_t = 1 (Gamma, N = 32) and w_t = t^1.08 (I, N = 32)."""
+    w = np.ones(d) if weights is None else np.asarray(weights, dtype=np.float64)
+    K = int(np.floor(N / np.min(w))) if np.min(w) > 0 else int(N)
+    rows = np.zeros((1, 0), dtype=np.int64)
+    prod = np.ones(1)
+    eps = 1e-9 * N
+    for t in range(d):
+        v = np.arange(-K, K + 1)
+        f = np.maximum(1.0, w[t] * np.abs(v))
+        newp = prod[:, None] * f[None, :]
+        keep = newp <= N + eps
+        ri, vi = np.nonzero(keep)
+        rows = np.concatenate([rows[ri], v[vi][:, None]], axis=1)
+        prod = newp[ri, vi]
+    order = np.lexsort(rows.T[::-1])
+    return np.ascontiguousarray(rows[order].astype(np.int32))

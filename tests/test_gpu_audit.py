@@ -1,0 +1,108 @@
+"""The PFP/PFN audit (Section 4.1.1) through the library against the oracle's audit, and the
+hyperbolic-cross setting of Section 4.1.3 on a few lattice draws.
+
+Every audit's counts of potential false positives and false negatives must equal the oracle's
+(bit-exact integers), and so must the median + R1L outcome (the Remark 2.8 hybrid combine keeps
+exactly I) whenever there is no PFN."""
+import numpy as np
+import pytest
+
+import oracle as O
+import sfft_synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def A():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA device required")
+    from paper_2006_13053_gb300 import audit
+    return audit
+
+
+def _oracle_audit(cand, sup, z, M):
+    out = O.pfp_pfn(cand, sup, z, M)
+    ok_r1l = False
+    if out["n_pfn"] == 0:
+        r = O.reconstruct(cand, out["samples"], z, M, tau_abs=0.5, postproc="hybrid", theta=0.5)
+        ok_r1l = np.array_equal(r.supp, np.sort(sup))
+    return out["n_pfp"], out["n_pfn"], ok_r1l
+
+
+def test_random_sets_audit_matches_oracle(A):
+    """Section 4.1.2's experiment at |Gamma| = 10^6 (10^7 in the paper) from [-1000, 1000]^3,
+    |I| = 1000, M = 10331, two draws of (Gamma, I) for L = 9 and 25."""
+    import torch
+    dev = torch.device("cuda:0")
+    n, s, M, box = 10 ** 6, 1000, 10331, 1000
+    seen_pfp = 0
+    for rep in range(2):
+        cand = S.uniform_distinct_device(n, 3, -box, box, 40 + rep, dev)
+        sup = S.subset_device(n, s, 40 + rep, dev)
+        hc, hs = cand.cpu().numpy(), sup.cpu().numpy()
+        for L in (9, 25):
+            z = A._generators(1000 + L, L, 3, M)
+            med, hyb = A.audit_plans(cand, s, L, M, z)
+            n_pfp, n_pfn, ok_med, ok_r1l = A.audit_once(med, hyb, cand, sup)
+            med.close()
+            hyb.close()
+            ref = _oracle_audit(hc, hs, z, M)
+            assert (n_pfp, n_pfn) == ref[:2], (rep, L)
+            assert ok_med == (ref[0] == 0 and ref[1] == 0)
+            assert ok_r1l == ref[2], (rep, L)
+            seen_pfp += n_pfp
+    assert seen_pfp > 0  # the small-L runs do produce false positives
+
+
+def test_rebinding_candidates_and_generators_matches_fresh_plans(A):
+    """A plan rebound to a new candidate set (sfft_plan_set_candidates) or to new generating
+    vectors (sfft_plan_set_generators) gives the audit of a plan created for them."""
+    import torch
+    dev = torch.device("cuda:0")
+    n, s, M, L = 200000, 300, 3119, 15
+    c1 = S.uniform_distinct_device(n, 3, -500, 500, 1, dev)
+    c2 = S.uniform_distinct_device(n - 1000, 3, -400, 400, 2, dev)
+    s2 = S.subset_device(n - 1000, s, 2, dev)
+    z1, z2 = A._generators(5, L, 3, M), A._generators(6, L, 3, M)
+    med, hyb = A.audit_plans(c1, s, L, M, z1)
+    med.set_candidates(c2)
+    hyb.set_candidates(c2)
+    med.set_generators(z2)
+    hyb.set_generators(z2)
+    got = A.audit_once(med, hyb, c2, s2)
+    f_med, f_hyb = A.audit_plans(c2, s, L, M, z2)
+    assert got == A.audit_once(f_med, f_hyb, c2, s2)
+    ref = _oracle_audit(c2.cpu().numpy(), s2.cpu().numpy(), z2, M)
+    assert got[:2] == ref[:2] and got[3] == ref[2]
+    # a set beyond the plan's |k| bound is refused
+    big = S.uniform_distinct_device(1000, 3, -600, 600, 3, dev)
+    with pytest.raises(Exception):
+        med.set_candidates(big)
+    for p in (med, hyb, f_med, f_hyb):
+        p.close()
+
+
+def test_hyperbolic_cross_audit_matches_oracle(A):
+    """Section 4.1.3: Gamma the 8-D hyperbolic cross of expansion 32 (10,665,297 frequencies),
+    I the weighted cross (1069), M = 11047: the audit of a lattice draw at L = 15 equals the
+    oracle's; then the experiment driver runs 3 repetitions for L = 15 and 31."""
+    import torch
+    res, perf = A.hyperbolic_cross_experiment([15, 31], 3)
+    assert [r["L"] for r in res] == [15, 31] and all(r["reps"] == 3 for r in res)
+    assert perf["candidates_per_audit"] == 10665297
+    G = S.hyperbolic_cross_weighted(8, 32)
+    I = S.hyperbolic_cross_weighted(8, 32, [t ** 1.08 for t in range(1, 9)])
+    key = lambda a: np.ravel_multi_index((a.astype(np.int64) + 32).T, (65,) * 8)
+    pos = np.searchsorted(key(G), key(I))
+    dev = torch.device("cuda:0")
+    cand, sup = torch.from_numpy(G).to(dev), torch.from_numpy(pos.astype(np.int64)).to(dev)
+    for rep in range(1):
+        z = A._generators(77 + rep, 15, 8, 11047)
+        med, hyb = A.audit_plans(cand, len(I), 15, 11047, z)
+        got = A.audit_once(med, hyb, cand, sup)
+        med.close()
+        hyb.close()
+        ref = _oracle_audit(G, pos, z, 11047)
+        assert got[:2] == ref[:2] and got[3] == ref[2], rep
