@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-path, graph, e2e and CPU legs")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch shapes instead of autotuning them in setup")
+    ap.add_argument("--legs", default="config1,config5,config3",
+                    help="the configuration legs run after the headline (comma list of config1, config5, config3)")
     ap.add_argument("--dft", default="fp32", choices=["fp32", "df64"],
                     help="arithmetic of the forward lattice DFTs under the refinement (FP32, or double-float)")
     ap.add_argument("--cpu-baseline-worker", default=None, metavar="OUT", help=argparse.SUPPRESS)
@@ -209,6 +211,60 @@ def accuracy(gpu, ref_path):
     return out
 
 
+def oracle_checks(out, checks):
+    """The oracle's side of the legs' accuracy checks (part of the CPU-baseline leg): config 1's
+    instance 0, config 3's 16-instance subsample (spawned single-threaded processes, one per
+    instance), the relative L2 errors of the Algorithm 3 runs (Section 4.3's formula with the
+    closed-form coefficients)."""
+    import multiprocessing as mp
+    import numpy as np
+    import oracle as O
+    c1 = checks.get("config1")
+    if c1:
+        ref = O.reconstruct(c1["cand"], O.sample_sparse_poly(c1["cand"][c1["sup"]], c1["coef"], c1["z"], c1["M"]),
+                            c1["z"], c1["M"], tau_rel=1e-10)
+        ok = bool(np.array_equal(c1["supp"], ref.supp))
+        out["config1"]["oracle_instance0"] = {
+            "support_equal": ok,
+            "coef_rel_err": float(np.max(np.abs(c1["got"] - ref.coef)) / np.max(np.abs(ref.coef))) if ok else None}
+    c5 = checks.get("config5")
+    if c5:
+        fh = O.sop_fourier(c5["triples"], c5["theta"], c5["supp"])
+        n2 = O.sop_norm2(c5["triples"], c5["theta"])
+        e2 = n2 - float(np.sum(fh ** 2)) + float(np.sum(np.abs(c5["coef"] - fh) ** 2))
+        out["config5"]["rel_l2_error"] = math.sqrt(max(e2, 0.0) / n2)
+        out["config5"]["note"] = ("the function keeps under 1 % of its energy in its 1000 largest coefficients: "
+                                  "a 1000-term approximation cannot be accurate (parity with the oracle is tested)")
+    for key in [k for k in checks if k.startswith("table_4_4")]:
+        c = checks[key]
+        out[key]["rel_l2_error"] = O.relative_l2_error(c["terms"], c["supp"], c["coef"])
+    c3 = checks.get("config3")
+    if c3:
+        ctx = mp.get_context("spawn")
+        env_threads = {v: os.environ.get(v) for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+        for v in env_threads:
+            os.environ[v] = "1"
+        try:
+            with ctx.Pool(max(1, min(16, os.cpu_count() or 1))) as pool:
+                refs = pool.map(_c3_oracle_worker, c3["args"], chunksize=1)
+        finally:
+            for v, val in env_threads.items():
+                if val is None:
+                    os.environ.pop(v, None)
+                else:
+                    os.environ[v] = val
+        same, errs = 0, []
+        for (gs, gc), (rs, rc) in zip(c3["got"], refs):
+            if gs.shape == rs.shape and np.array_equal(gs, rs):
+                same += 1
+                if rc.size:
+                    errs.append(float(np.max(np.abs(gc - rc)) / np.max(np.abs(rc))))
+        out["config3"]["oracle_subsample"] = {
+            "instances": c3["instances"], "support_equal": same, "of": len(refs),
+            "coef_rel_err_max_norm": max(errs) if errs else None,
+            "reference": "FP64 oracle on FP64 samples (aliasing formula) plus the same noise; the GPU samples in FP32"}
+
+
 def cpu_baseline(gpu_result=None, timeout=600):
     import tempfile
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
@@ -233,18 +289,6 @@ def cpu_baseline(gpu_result=None, timeout=600):
 
 
 # ------------------------------------------------------------------ native arm
-def kernel_count(batch_plans, n_inst, refine=True):
-    # per step: batched sampler (clear, bucket scatter, inverse lattice DFT) and the batch's
-    # clear + DFT + zero test + hash groups + compact + combine (which forms the hashes of the
-    # detected set) + select + counts (the descriptor uploads run only when a call's buffers
-    # differ from the last call's: not in the timed loop, which reuses its buffers)
-    hash_groups = len({p.d for p in batch_plans})
-    n = 3 + 1 + 1 + 1 + hash_groups + 1 + 1 + 1 + 1
-    if refine:
-        n += 1 + 1 + 1  # clear C, scatter, median update of ghat - C
-    return n
-
-
 # double-float roofline: FP32-pipe instructions per df64 flop as implemented, on the conventional
 # 5 N log2 N radix-2 count (per butterfly: one complex product = 6 flops, two complex sums = 4).
 # A complex product costs 2 x 19 instructions (df_dot2: error-free FMA products, one two-sum, one
@@ -503,7 +547,7 @@ def run_native(a, rank, world):
                       "autotuned": {"hash_waves": tuned[0], "fft_threads": tuned[1]}},
            "cand_lattice_evals_per_s": world * n_inst * NCAND * L / (ms / 1000.0),
            "stage_ms_per_step": stage_ms,
-           "gpu_launches": kernel_count(plans, n_inst) * a.steps,
+           "gpu_launches": sum(batch.launch_count()) * a.steps,
            "clocks": clk.summary(clk_window)}
     # ---- roofline of the dominant stage
     dom = max((k for k in stage_ms if k != "sampler"), key=stage_ms.get)
@@ -810,6 +854,243 @@ def run_native(a, rank, world):
     return out, plans, batch, res0
 
 
+# ------------------------------------------------------------------ config 1: many small FP64 instances
+C1_INST = 1024
+
+
+def leg_config1(a, dev, st):
+    """d = 3, Gamma = the full grid [-16, 16]^3 (35,937), s = 20 with |c| uniform in [1, 10] and
+    uniform phase, no noise, FP64; L = 29, M = 211 by Corollary 2.6 (delta = 0.1).  1024 seeds
+    (each its own lattices and polynomial) in one graph-captured batch; a step samples and
+    reconstructs all of them.  Returns the leg and instance 0's inputs and result for the oracle
+    check of the CPU-baseline leg."""
+    import numpy as np
+    import torch
+    import paper_2006_13053_gb300 as G
+    import sfft_synth as S
+    cand = S.full_grid(3, 16)
+    n, s_ = cand.shape[0], 20
+    with torch.cuda.stream(st):
+        tc = torch.from_numpy(cand).to(dev)
+        plans = [G.Plan(tc, s_, precision=G.FP64, tau_rel=1e-10, seed=1000 + i, stream=st) for i in range(C1_INST)]
+        sups = [S.support_indices(n, s_, 1000 + i) for i in range(C1_INST)]
+        kv = [tc[torch.from_numpy(sp).to(dev)].contiguous() for sp in sups]
+        cf = [torch.from_numpy(S.coef_mag_phase(s_, 1, 10, 1000 + i)).to(dev) for i in range(C1_INST)]
+        smp = [torch.empty(p.n_samples, dtype=torch.complex128, device=dev) for p in plans]
+    batch = G.Batch(plans, use_graph=True, stream=st)
+
+    def step():
+        with torch.cuda.stream(st):
+            batch.sample_sparse_poly(kv, cf, None, outs=smp)
+            batch.reconstruct_async(smp)
+
+    for _ in range(max(3, a.warmup)):
+        step()
+    st.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(a.steps):
+        step()
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    res = batch.results()
+    z0 = plans[0].z
+    L, M = plans[0].L, int(plans[0].M[0])
+    exact = sum(bool(np.array_equal(r[0].cpu().numpy(), np.sort(sp))) for r, sp in zip(res, sups))
+    out = {"value": C1_INST / (ms / 1000.0), "unit": "reconstructions/s", "ms_per_step": ms, "instances": C1_INST,
+           "lattices": L, "lattice_size": M, "cand_lattice_evals_per_s": C1_INST * n * L / (ms / 1000.0),
+           "workload": "d=3, Gamma=[-16,16]^3 (35,937), s=20, |c| U[1,10], FP64, no noise, L=29, M=211; 1024 seeds "
+                       "per step (sampler + reconstruction) in one graph-captured batch",
+           "gpu_launches_per_step": sum(batch.launch_count()),
+           "exact_recoveries": exact}
+    check = {"cand": cand, "sup": sups[0], "coef": cf[0].cpu().numpy(), "z": z0.copy(), "M": M,
+             "supp": res[0][0].cpu().numpy(), "got": res[0][1].cpu().numpy()}
+    batch.close()
+    for p in plans:
+        p.close()
+    return out, check
+
+
+# ------------------------------------------------------------------ config 5: Algorithm 3 at size
+def leg_config5(a, dev, st):
+    """Algorithm 3 on d = 25, Gamma = [-32, 32]^25, the sum-of-products function with 10 random
+    triples (theta in [0.5, 2]), s = 1000, s_local = 2000, r = 1, theta = 1e-12 relative, delta =
+    0.999, FP32 samples, one refinement per Algorithm 4 call (zero test 1e-6 relative), moduli
+    ranked to 16 significant bits; and the Section 4.3 B-spline function of Table 4.4 (d = 10,
+    N = 16 and 64, s = 1000, r = 5, FP64).  Each run is timed whole (host driver included)."""
+    import torch
+    import paper_2006_13053_gb300 as G
+    import sfft_synth as S
+    out = {}
+    triples, theta = S.sop_params(25, 10, 0)
+    th = torch.from_numpy(theta).to(dev)
+    kw = dict(s_local=2000, seed=0, theta_abs=0.0, theta_rel=1e-12, delta=0.999, refine=1, rank_bits=16, stream=st)
+    G.dim_incremental(25, -32, 32, 1000, ("sop", triples, th, 48, 32.0), r=1, tau_rel=1e-6, precision=G.FP32,
+                      **kw)  # warm-up (tables, modules)
+    runs = []
+    for _ in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        supp, coef, ns = G.dim_incremental(25, -32, 32, 1000, ("sop", triples, th, 48, 32.0), r=1, tau_rel=1e-6,
+                                           precision=G.FP32, **kw)
+        torch.cuda.synchronize()
+        runs.append(time.perf_counter() - t0)
+    t = min(runs)
+    out["config5"] = {"value": 1.0 / t, "unit": "reconstructions/s", "seconds": t, "samples": ns,
+                      "samples_per_s": ns / t, "frequencies": int(len(supp)),
+                      "workload": "Algorithm 3, d=25, [-32,32]^25, sum of products (10 triples), s=1000, "
+                                  "s_local=2000, r=1, theta=1e-12 rel, delta=0.999, FP32 + refinement"}
+    checks = {"config5": {"triples": triples, "theta": theta, "supp": supp, "coef": coef}}
+    terms = [((0, 2, 7), 2), ((1, 4, 5, 9), 4), ((3, 6, 8), 6)]
+    for N in (16, 64):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        supp, coef, ns = G.dim_incremental(10, -N, N, 1000, ("bspline", terms), r=5, tau_rel=1e-10,
+                                           precision=G.FP64, **kw)
+        torch.cuda.synchronize()
+        t = time.perf_counter() - t0
+        key = f"table_4_4_N{N}_s1000"
+        out[key] = {"seconds": t, "samples": ns, "frequencies": int(len(supp)),
+                    "paper_samples": {16: 2903576, 64: 3540792}[N], "paper_rel_l2_max_of_10": 1.2e-2,
+                    "workload": f"Section 4.3 B-spline sum, d=10, Gamma=[-{N},{N}]^10, s=1000, s_local=2000, r=5, "
+                                "delta=0.999, FP64, one refinement per call"}
+        checks[key] = {"terms": terms, "supp": supp, "coef": coef}
+    return out, checks
+
+
+# ------------------------------------------------------------------ config 3: uneven batch at size
+C3_INST, C3_SEED, C3_SUB = 512, 3, 16
+
+
+def c3_inputs(spec, dev):
+    """One instance of the uneven workload, drawn on the device: distinct candidates from
+    [-32, 32]^d as int8 rows of stride d bytes, the support, complex-Gaussian coefficients."""
+    import torch
+    import sfft_synth as S
+    d, n, s, seed = spec["d"], spec["n"], spec["s"], spec["seed"]
+    cand = S.uniform_distinct_device(n, d, -spec["box"], spec["box"], seed, dev)
+    sup = S.subset_device(n, s, seed, dev)
+    coef = torch.from_numpy(S.coef_cgauss(s, seed)).to(dev)
+    return cand.to(torch.int8).contiguous(), sup, coef
+
+
+def _c3_oracle_worker(args):
+    """The oracle's reconstruction of one config-3 instance (samples by the aliasing formula plus
+    the instance's noise, Algorithm 2, refinement, Algorithm 4)."""
+    cand, sup, coef, noise, z, M, tau = args
+    import numpy as np
+    import oracle as O
+    y = O.sample_sparse_poly_aliasing(cand[sup], coef, z, M) + noise
+    r = O.reconstruct(cand.astype(np.int64), y, z, M, tau_abs=tau, do_refine=True, refine_mode="bucket")
+    return r.supp, r.coef
+
+
+def leg_config3(a, dev, st):
+    """512 independent reconstructions of uneven sizes in one batch, replayed from a CUDA graph
+    after autotuning: d uniform in {5..20}, |Gamma| log-uniform in [2^14, 2^22] from [-32, 32]^d,
+    s log-uniform in [100, 10^4], M = nextprime(10.33 s), L by Corollary 2.6 (delta = 0.1), FP32
+    samples with 40 dB noise, one refinement step on FP32 lattice DFTs.  A step samples every
+    instance and reconstructs all of them.  Returns the leg and the inputs and results of 16
+    instances (every 32nd) for the oracle check of the CPU-baseline leg."""
+    import numpy as np
+    import torch
+    import paper_2006_13053_gb300 as G
+    import sfft_synth as S
+    t_setup = time.perf_counter()
+    specs = S.uneven_instances(C3_INST, C3_SEED)
+    plans, kv, cf, nz, smp, keep = [], [], [], [], [], []
+    sub_idx = list(range(0, C3_INST, C3_INST // C3_SUB))
+    sub_args = []
+    with torch.cuda.stream(st):
+        for i, sp in enumerate(specs):
+            cand8, sup, coef = c3_inputs(sp, dev)
+            s_ = sp["s"]
+            M = int(G._native.sfft_next_prime_above(10.33 * s_))
+            sigma = math.sqrt(float((coef.abs() ** 2).sum()) / 10 ** (SNR_DB / 10))
+            tau = 6 * sigma / math.sqrt(M)
+            p = G.Plan(cand8, s_, d=sp["d"], precision=G.FP32, refine=1, dft=G.DFT_FP32, tau_abs=tau, tau_rel=0.0,
+                       seed=sp["seed"], stream=st)
+            noise = S.noise_device(p.n_samples, sigma, sp["seed"], dev)
+            plans.append(p)
+            kv.append(cand8[sup].to(torch.int32).contiguous())
+            cf.append(coef)
+            nz.append(noise)
+            smp.append(torch.empty(p.n_samples, dtype=torch.complex64, device=dev))
+            keep.append(cand8)
+            if i in sub_idx:
+                sub_args.append((cand8.cpu().numpy(), sup.cpu().numpy(), coef.cpu().numpy(),
+                                 noise.cpu().numpy().astype(np.complex128), p.z.copy(), M, tau))
+    st.synchronize()
+    batch = G.Batch(plans, use_graph=True, stream=st)
+
+    def step():
+        with torch.cuda.stream(st):
+            batch.sample_sparse_poly(kv, cf, nz, outs=smp)
+            batch.reconstruct_async(smp)
+
+    for _ in range(a.warmup):
+        step()
+    st.synchronize()
+    with torch.cuda.stream(st):
+        tuned = batch.autotune(smp, reps=1)
+    for _ in range(2):  # capture, then replay
+        step()
+    st.synchronize()
+    setup_s = time.perf_counter() - t_setup
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(a.steps):
+        step()
+    e1.record(st)
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / a.steps
+    res = batch.results()
+    batch.timing(1)
+    for _ in range(3):
+        step()
+    st.synchronize()
+    stages = {k: v[0] / max(v[1], 1) for k, v in batch.timing(0).items() if v[1] > 0}
+    # eager (no graph) step for the launch-overhead comparison
+    eb = G.Batch(plans, use_graph=False, stream=st)
+    for _ in range(2):
+        with torch.cuda.stream(st):
+            eb.sample_sparse_poly(kv, cf, nz, outs=smp)
+            eb.reconstruct_async(smp)
+    st.synchronize()
+    q0, q1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    q0.record(st)
+    for _ in range(3):
+        with torch.cuda.stream(st):
+            eb.sample_sparse_poly(kv, cf, nz, outs=smp)
+            eb.reconstruct_async(smp)
+    q1.record(st)
+    q1.synchronize()
+    eager_ms = q0.elapsed_time(q1) / 3
+    n_rec, n_samp = batch.launch_count()
+    eb.close()
+    evals = sum(p.n * p.L for p in plans)
+    Ms = [int(p.M[0]) for p in plans]
+    out = {"value": C3_INST / (ms / 1000.0), "unit": "reconstructions/s", "ms_per_step": ms, "steps": a.steps,
+           "cand_lattice_evals_per_s": evals / (ms / 1000.0), "candidates": sum(p.n for p in plans),
+           "candidate_bytes": sum(p.n * p.d for p in plans), "instances": C3_INST,
+           "M_range": [min(Ms), max(Ms)], "M_above_32768": sum(m > 32768 for m in Ms),
+           "L_range": [min(p.L for p in plans), max(p.L for p in plans)],
+           "workload": "512 instances: d U{5..20}, |Gamma| log-U[2^14, 2^22] from [-32,32]^d (int8 rows, stride d), "
+                       "s log-U[100, 10^4], M = nextprime(10.33 s), L Cor. 2.6 (delta 0.1), FP32 + 40 dB noise, one "
+                       "refinement on FP32 DFTs; one step = sampler + reconstruction of all 512",
+           "graph": True, "autotuned": {"hash_waves": tuned[0], "fft_threads": tuned[1]},
+           "gpu_launches_per_step": n_rec + n_samp, "eager_ms_per_step": eager_ms,
+           "stage_ms_per_step": stages, "setup_s": setup_s}
+    check = {"args": sub_args, "instances": sub_idx,
+             "got": [(res[j][0].cpu().numpy(), res[j][1].cpu().numpy()) for j in sub_idx]}
+    batch.close()
+    for p in plans:
+        p.close()
+    return out, check
+
+
 def _reference_worker(args):
     """One oracle process of the reference arm: its instance's inputs and samples once, then one
     timed reconstruction per step, started together with the other processes (barrier)."""
@@ -907,11 +1188,28 @@ def main():
     if world > 1:
         torch.distributed.init_process_group("nccl")
     out, plans, batch, res0 = run_native(a, rank, world)
+    checks = {}
+    if not a.no_extras:
+        dev = torch.device("cuda", torch.cuda.current_device())
+        st = torch.cuda.Stream(dev)
+        for p in plans:
+            p.close()
+        batch.close()
+        legs = set(a.legs.split(",")) if a.legs else set()
+        if "config1" in legs:
+            out["config1"], checks["config1"] = leg_config1(a, dev, st)
+        if "config5" in legs:
+            o5, c5 = leg_config5(a, dev, st)
+            out.update(o5)
+            checks.update(c5)
+        if "config3" in legs:
+            out["config3"], checks["config3"] = leg_config3(a, dev, st)
     if rank == 0:
         if not a.no_extras:
             out["cpu_baseline"], acc = cpu_baseline(res0)
             if acc is not None:
                 out["accuracy"] = acc
+            oracle_checks(out, checks)
         print(json.dumps(out), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

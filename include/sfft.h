@@ -300,6 +300,13 @@ int sfft_batch_autotune(sfft_batch* b, const void* const* samples, int64_t* cons
 int sfft_batch_select_hash(sfft_batch* b, int tensor);
 
 /*
+ * Kernel launches that one sfft_batch_reconstruct (reconstruct) and one
+ * sfft_batch_sample_sparse_poly with terms (sampler) enqueue in the steady state (descriptor
+ * uploads happen only when a call's buffers differ from the previous call's).  Host only.
+ */
+int sfft_batch_launch_count(sfft_batch* b, int* reconstruct, int* sampler);
+
+/*
  * Status of the last sfft_batch_reconstruct (waits for it): flags host int64 [n_plans] in the
  * caller's plan order, bit 1 = detected set above its capacity, 2 = more uncertain buckets in
  * the FP64 guard band than one lattice can re-test (tau below the working precision's

@@ -231,6 +231,24 @@ def sample_sparse_poly(kvec, coef, z, M):
                            for l in range(len(z))])
 
 
+def sample_sparse_poly_aliasing(kvec, coef, z, M):
+    """The same samples as sample_sparse_poly through the aliasing formula (eq. 2.3): on lattice l
+    the normalised DFT of the samples is the bucket sum ghat_h = sum of c_k over h_kl = h, so the
+    samples are M times the inverse DFT of those bucket sums (library FFT).  O(L (s + M log M))
+    instead of O(L M s): for large s and M (the batched workload), pinned against the direct sum."""
+    kvec = np.asarray(kvec, dtype=np.int64)
+    coef = np.asarray(coef, dtype=np.complex128)
+    z = np.asarray(z, dtype=np.int64)
+    Ms = np.broadcast_to(np.asarray(M, dtype=np.int64), (z.shape[0],))
+    out = []
+    for l in range(z.shape[0]):
+        m = int(Ms[l])
+        h = np.mod(kvec @ z[l], m)
+        g = np.bincount(h, weights=coef.real, minlength=m) + 1j * np.bincount(h, weights=coef.imag, minlength=m)
+        out.append(np.fft.ifft(g) * m)
+    return np.concatenate(out)
+
+
 # ---- sum-of-products test function f_theta = sum_m prod_{t in T_m} g_{theta_m}(x_t)
 def sop_kernel_coef(theta: float, K: int = 48, width: float = 32.0) -> np.ndarray:
     """a_k(theta) = sinc(pi k / (width theta))^4 for k = -K..K (sinc(x)=sin(x)/x, sinc(0)=1)."""

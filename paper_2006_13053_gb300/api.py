@@ -310,6 +310,12 @@ class Batch:
         """Use the tensor-core hash kernel for the launches that qualify (see the C header)."""
         N.check(N.sfft_batch_select_hash(self.handle, 1 if tensor else 0))
 
+    def launch_count(self):
+        """(kernel launches of one reconstruct call, of one sampler call) in the steady state."""
+        r, sm = C.c_int(), C.c_int()
+        N.check(N.sfft_batch_launch_count(self.handle, C.byref(r), C.byref(sm)))
+        return r.value, sm.value
+
     def flags(self):
         fl = (C.c_int64 * len(self.plans))()
         rc = N.sfft_batch_flags(self.handle, fl)

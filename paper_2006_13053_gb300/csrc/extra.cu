@@ -470,6 +470,22 @@ int sfft_batch_select_hash(sfft_batch* b, int tensor) {
     return SFFT_OK;
 }
 
+int sfft_batch_launch_count(sfft_batch* b, int* reconstruct, int* sampler) {
+    if (!b) { set_error("batch is NULL"); return SFFT_EINVAL; }
+    Batch* B = reinterpret_cast<Batch*>(b);
+    const PipeArgs& A = B->args;
+    // run_pipeline: clear, forward transforms, zero test, hash groups, compaction, combine, select;
+    // the hybrid combine adds the hashes of Itilde and the collision counts, least squares four
+    // launches, the refinement a clear, the scatter and the update; the batch adds the counts
+    int n = 1 + (int)A.fwd.size() + 1 + (int)A.hash.size() + 1 + 1 + 1 + 1;
+    if (A.hybrid) n += 2;
+    if (A.lsq) n += 4;
+    if (A.refine) n += 3;
+    if (reconstruct) *reconstruct = n;
+    if (sampler) *sampler = 2 + (int)B->samp.size();  // clear, bucket scatter, inverse transforms
+    return SFFT_OK;
+}
+
 int sfft_batch_flags(sfft_batch* b, int64_t* flags) {
     if (!b || !flags) { set_error("null argument"); return SFFT_EINVAL; }
     Batch* B = reinterpret_cast<Batch*>(b);

@@ -190,32 +190,55 @@ def uniform_tail(n: int, seed: int, stream: int = S_TAIL) -> np.ndarray:
 
 # --------------------------------------------------------------------------- audit inputs (Section 4.1)
 def uniform_distinct_device(n: int, d: int, lo: int, hi: int, seed: int, device, stream: int = S_GAMMA):
-    """n distinct integer vectors uniform in [lo, hi]^d drawn on a CUDA device (int32 tensor [n, d]).
+    """n distinct integer vectors uniform in [lo, hi]^d drawn on a device (int32 tensor [n, d]).
 
-    Vectors are drawn with replacement (torch's device generator seeded from (seed, stream)), the
-    distinct ones kept, and a uniformly random n-subset of them taken: by exchangeability that is a
-    uniform n-subset of the box.  Rows come in random order.  For the PFP/PFN audit at |Gamma| = 10^7
-    (one fresh set per repetition), where a host generator would dominate the run time."""
+    Vectors are drawn with replacement (torch's generator on that device, seeded from (seed,
+    stream)), the distinct ones kept (rows packed into 64-bit words of up to 62 bits, compared
+    whole), and a uniformly random n-subset of them taken: by exchangeability that is a uniform
+    n-subset of the box.  Rows come in random order.  For the large candidate sets of the audit
+    (|Gamma| = 10^7 per repetition) and of the batched workload, where a host generator would
+    dominate the run time."""
     import torch
     W = hi - lo + 1
-    if W ** d >= 2 ** 62:
-        raise ValueError("the box is too large for 64-bit keys")
     if n > W ** d:
         raise ValueError("more distinct vectors requested than the box holds")
+    per = 1
+    while W ** (per + 1) < 2 ** 62 and per < d:
+        per += 1
+    groups = [list(range(a, min(d, a + per))) for a in range(0, d, per)]
     g = torch.Generator(device=device)
     g.manual_seed(int(seed) * 1000003 + int(stream))
-    mult = torch.tensor([W ** t for t in range(d)], dtype=torch.int64, device=device)
-    keys = torch.empty(0, dtype=torch.int64, device=device)
+
+    def pack(rows):  # [m, d] offsets in [0, W) -> [m, words] int64
+        return torch.stack([sum(rows[:, t] * (W ** i) for i, t in enumerate(gr)) for gr in groups], dim=1)
+
+    words = torch.empty((0, len(groups)), dtype=torch.int64, device=device)
     m = n + n // 64 + 1024
     while True:
         draw = torch.randint(0, W, (m, d), generator=g, device=device, dtype=torch.int64)
-        keys = torch.unique(torch.cat([keys, (draw * mult).sum(dim=1)]))
-        if keys.numel() >= n:
+        allw = torch.cat([words, pack(draw)])
+        words = torch.unique(allw, dim=0) if len(groups) > 1 else torch.unique(allw[:, 0]).unsqueeze(1)
+        if words.shape[0] >= n:
             break
-        m = n - keys.numel() + n // 64 + 1024
-    keys = keys[torch.randperm(keys.numel(), generator=g, device=device)[:n]]
-    rows = torch.stack([(keys // (W ** t)) % W for t in range(d)], dim=1) + lo
-    return rows.to(torch.int32).contiguous()
+        m = n - words.shape[0] + n // 64 + 1024
+    words = words[torch.randperm(words.shape[0], generator=g, device=device)[:n]]
+    cols = [None] * d
+    for j, gr in enumerate(groups):
+        for i, t in enumerate(gr):
+            cols[t] = (words[:, j] // (W ** i)) % W
+    return (torch.stack(cols, dim=1) + lo).to(torch.int32).contiguous()
+
+
+def noise_device(n: int, sigma: float, seed: int, device, stream: int = S_NOISE, dtype=None):
+    """Complex Gaussian noise with E|n|^2 = sigma^2 drawn on a device (complex64 by default)."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed) * 1000003 + int(stream))
+    dt = dtype or torch.complex64
+    rt = torch.float32 if dt == torch.complex64 else torch.float64
+    re = torch.randn(n, generator=g, device=device, dtype=rt)
+    im = torch.randn(n, generator=g, device=device, dtype=rt)
+    return (torch.complex(re, im) * (sigma / 2 ** 0.5)).to(dt)
 
 
 def subset_device(n: int, s: int, seed: int, device, stream: int = S_SUPPORT):

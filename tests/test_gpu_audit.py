@@ -4,6 +4,8 @@ hyperbolic-cross setting of Section 4.1.3 on a few lattice draws.
 Every audit's counts of potential false positives and false negatives must equal the oracle's
 (bit-exact integers), and so must the median + R1L outcome (the Remark 2.8 hybrid combine keeps
 exactly I) whenever there is no PFN."""
+import math
+
 import numpy as np
 import pytest
 
@@ -106,3 +108,24 @@ def test_hyperbolic_cross_audit_matches_oracle(A):
         hyb.close()
         ref = _oracle_audit(G, pos, z, 11047)
         assert got[:2] == ref[:2] and got[3] == ref[2], rep
+
+
+def test_figure_4_1_success_rates_match_paper(A, golden):
+    """The success rates of the random-set experiment at the paper's scale (|Gamma| = 10^7) with 300
+    repetitions per L, against the rates Figure 4.1 plots for 1000 repetitions: within four
+    standard deviations of the two binomial estimates (plus 0.01), for the median curve at
+    L = 23..31 and the median + R1L curve at L = 11..17 (the steep parts of both curves)."""
+    paper = {(r[0], int(r[1])): float(r[2]) for r in golden("figure_4_1_success.txt")}
+    Ls = [11, 13, 15, 17, 23, 25, 27, 29, 31]
+    reps = 300
+    res, perf = A.random_sets_experiment(Ls, reps, seed=5)
+    by_L = {r["L"]: r for r in res}
+    for curve, key, Lc in (("median", "success_median", (23, 25, 27, 29, 31)),
+                           ("r1l", "success_median_r1l", (11, 13, 15, 17))):
+        for L in Lc:
+            p = paper[(curve, L)]
+            q = by_L[L][key]
+            sd = math.sqrt(max(p * (1 - p), 1e-3) / reps + max(p * (1 - p), 1e-3) / 1000)
+            assert abs(q - p) <= 4 * sd + 0.01, (curve, L, q, p)
+    print(f"Figure 4.1 at |Gamma| = 10^7: {perf['audits']} audits, {perf['audits_per_s']:.0f} audits/s; "
+          + ", ".join(f"L={r['L']}: {r['success_median']:.3f}/{r['success_median_r1l']:.3f}" for r in res))

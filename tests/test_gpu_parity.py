@@ -511,6 +511,26 @@ def test_batch_matches_single_plans(G, use_graph, dft):
     assert t["hash_count"][1] == 1 and t["hash_count"][0] > 0
 
 
+def test_batch_launch_count(G):
+    """The launches one batch call enqueues: sampler 3 (clear, bucket scatter, inverse transforms);
+    reconstruction clear, forward transforms, zero test, one hash launch per run of equal d,
+    compaction, combine, select, counts, plus 3 for the refinement (as in the benchmark's launch
+    list: 14 per step)."""
+    import torch
+    plans = []
+    for i, d in enumerate((10, 10, 12)):
+        cand = S.uniform_distinct(4000, d, -20, 20, i)
+        plans.append(G.Plan(T(cand), 40, precision=1, refine=1, tau_rel=1e-5, seed=i))
+    B = G.Batch(plans[:2])
+    assert B.launch_count() == (11, 3)
+    B.close()
+    B = G.Batch(plans)
+    assert B.launch_count() == (12, 3)  # d = 10 and d = 12: two hash launches
+    B.close()
+    for p in plans:
+        p.close()
+
+
 def test_batch_sampler_matches_plan_sampler(G):
     import torch
     specs = [(3, 2000, 15, 11), (6, 3000, 25, 12), (3, 1500, 10, 13)]

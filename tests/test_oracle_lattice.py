@@ -110,3 +110,17 @@ def test_integer_phase_evaluation_matches_float_nodes():
     assert np.allclose(a, b, atol=1e-11)
     # node j = 1 is z / M and the nodes are j z / M mod 1
     assert np.array_equal(num[1], z % M) and np.array_equal(num[5], (5 * z) % M)
+
+
+def test_aliasing_sampler_equals_direct_sum():
+    """eq. 2.3: samples via the inverse DFT of the bucket sums equal the direct evaluation of the
+    sparse polynomial at the lattice nodes (several lattices of different prime sizes)."""
+    rng = np.random.default_rng(12)
+    for d, n, s, Ms in ((3, 400, 30, [101, 103, 107]), (6, 2000, 200, [211] * 5), (12, 500, 64, [97, 89])):
+        cand = S.uniform_distinct(n, d, -20, 20, d)
+        kv = cand[S.support_indices(n, s, d)]
+        c = S.coef_cgauss(s, d)
+        z = np.stack([rng.integers(0, m, size=d) for m in Ms])
+        a = O.sample_sparse_poly(kv, c, z, Ms)
+        b = O.sample_sparse_poly_aliasing(kv, c, z, Ms)
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.sqrt(s) * np.max(np.abs(c))

@@ -17,6 +17,12 @@ def test_uniform_distinct_device_generator_on_cpu():
         assert np.unique(a, axis=0).shape[0] == n
         b = S.uniform_distinct_device(n, d, lo, hi, 3, dev).numpy()
         assert np.array_equal(a, b)  # seeded
+    # rows of d = 14 in [-32, 32]: packed into two key words
+    c = S.uniform_distinct_device(3000, 14, -32, 32, 5, dev).numpy()
+    assert c.shape == (3000, 14) and np.unique(c, axis=0).shape[0] == 3000 and c.min() >= -32 and c.max() <= 32
+    assert len(np.unique(c[:, 13])) > 40  # every column drawn
+    nz = S.noise_device(200000, 0.3, 1, dev)
+    assert abs(float((nz.abs() ** 2).mean()) - 0.09) < 0.002
     # the whole box when n equals its size
     full = S.uniform_distinct_device(900, 2, -15, 14, 1, dev).numpy()
     assert np.unique(full, axis=0).shape[0] == 900
