@@ -210,6 +210,28 @@ int sfft_reconstruct(sfft_plan* plan, const void* samples, int64_t* supp_out, do
  */
 int sfft_reconstruct_backward(sfft_plan* plan, const double* dcoef, void* dsamples);
 
+/*
+ * Sharded reconstruction of one instance whose candidate set is split into slices, one plan per
+ * slice (one per GPU / process), every plan with the instance's lattices (the same M and z) and
+ * the same parameters (median combine, absolute theta: theta_rel = 0).  Every shard transforms
+ * the same samples (the lattice DFTs are repeated per shard: sum M is small next to |Gamma|).
+ *   begin: Algorithm 2 on the slice (lattice DFTs, zero test, hash + count, median combine),
+ *          then C_out (device complex double [sum M]) = the slice's median coefficients summed
+ *          into their buckets (eq. 2.3); n_detected (optional host) = the slice's |Itilde|.
+ *   The caller sums C over the shards (an all-reduce: the refinement's residual spectrum
+ *   ghat - C needs every shard's detected coefficients).
+ *   end:   the refinement update with the summed C_sum (plans with refine = 1; others ignore it),
+ *          then Algorithm 4's theta filter and top-s_tilde on the slice: supp_out (indices into
+ *          the slice, ascending), coef_out (complex double), keys_out (optional device uint64
+ *          [cap]: the rank key of each output, see sfft_params.rank_bits).  Merging the shards'
+ *          outputs by (key descending, global index ascending) and keeping s_tilde gives the
+ *          unsharded selection.
+ * Both synchronise the plan's stream; end must follow begin on the same plan.
+ */
+int sfft_reconstruct_shard_begin(sfft_plan* plan, const void* samples, double* C_out, int64_t* n_detected);
+int sfft_reconstruct_shard_end(sfft_plan* plan, const double* C_sum, int64_t* supp_out, double* coef_out,
+                               uint64_t* keys_out, int64_t cap, int64_t* n_out);
+
 /* ---------------------------------------------------------------- synthetic test functions */
 /*
  * Samples of the sparse trigonometric polynomial p(x) = sum_q coef_q exp(2 pi i kvec_q . x)

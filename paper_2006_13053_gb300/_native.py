@@ -93,6 +93,8 @@ sfft_plan_info = _sig("sfft_plan_info", _i32, [_vp, _P(_i32), _vp, _vp, _P(_i64)
 sfft_plan_destroy = _sig("sfft_plan_destroy", None, [_vp])
 sfft_sample_points = _sig("sfft_sample_points", _i32, [_vp, _vp, _vp, _vp])
 sfft_reconstruct = _sig("sfft_reconstruct", _i32, [_vp, _vp, _vp, _vp, _i64, _P(_i64), _P(Diag)])
+sfft_reconstruct_shard_begin = _sig("sfft_reconstruct_shard_begin", _i32, [_vp, _vp, _vp, _P(_i64)])
+sfft_reconstruct_shard_end = _sig("sfft_reconstruct_shard_end", _i32, [_vp, _vp, _vp, _vp, _vp, _i64, _P(_i64)])
 sfft_reconstruct_backward = _sig("sfft_reconstruct_backward", _i32, [_vp, _vp, _vp])
 sfft_sample_sparse_poly = _sig("sfft_sample_sparse_poly", _i32, [_vp, _vp, _vp, _i64, _vp, _vp])
 sfft_sample_sop = _sig("sfft_sample_sop", _i32, [_vp, _vp, _vp, _i32, _i32, _dbl, _vp])

@@ -201,6 +201,31 @@ class Plan:
             return supp[:k], coef[:k], info
         return supp[:k], coef[:k]
 
+    def shard_begin(self, samples):
+        """First half of a sharded reconstruction: this plan's slice through the median combine;
+        returns C (complex128 cuda [sum M]), the slice's median coefficients in their buckets."""
+        _req(samples, self.cdtype, "samples")
+        C_ = torch.empty(self.n_samples, dtype=torch.complex128, device=self.cand.device)
+        nd = C.c_int64()
+        N.check(N.sfft_reconstruct_shard_begin(self.handle, _ptr(samples), _ptr(C_), C.byref(nd)))
+        self.shard_detected = nd.value
+        return C_
+
+    def shard_end(self, C_sum, cap=None):
+        """Second half: refinement with the summed C, Algorithm 4 on the slice.  Returns (supp into
+        the slice, coef, rank keys as int64 tensors of the key bits)."""
+        _req(C_sum, torch.complex128, "C_sum")
+        dev = self.cand.device
+        cap = int(cap if cap is not None else max(self.params.s_tilde or 0, 1) + 4 * 4096)
+        supp = torch.empty(cap, dtype=torch.int64, device=dev)
+        coef = torch.empty(cap, dtype=torch.complex128, device=dev)
+        keys = torch.empty(cap, dtype=torch.int64, device=dev)  # uint64 bits (keys of moduli < 2^63)
+        nout = C.c_int64()
+        N.check(N.sfft_reconstruct_shard_end(self.handle, _ptr(C_sum), _ptr(supp), _ptr(coef), _ptr(keys), cap,
+                                             C.byref(nout)))
+        k = nout.value
+        return supp[:k], coef[:k], keys[:k]
+
     def backward(self, dcoef):
         """Sample cotangents for coefficient cotangents of the last reconstruct (support fixed)."""
         _req(dcoef, torch.complex128, "dcoef")

@@ -498,42 +498,53 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
     const int ni = a.ninst;
     if (a.timer)
         for (int i = 0; i <= ST_COUNT; ++i) a.timer->recorded[i] = false;
-    SFFT_TRY(mark(a, ST_CLEAR, st));
-    SFFT_TRY(launch_clear(a.d_inst, ni, 1, a.hybrid, 0, st));
-    // Algorithm 2: lattice DFTs (normalised by 1/M) + per-lattice statistics
-    SFFT_TRY(mark(a, ST_FFT_FWD, st));
-    for (const auto& f : a.fwd)
-        SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.mode, a.fwd_prec, a.prec, a.prec, -1, EPI_ANALYZE, a.d_inst,
-                                  st, nullptr, nullptr, f.threads));
-    // zero test with direct re-tests inside the guard band (Remark 2.3); unit roundoff of the
-    // transform arithmetic (double-float: 2^-44, a bound with margin for its ~48-bit operations)
-    SFFT_TRY(mark(a, ST_ZERO_TEST, st));
-    const double u = a.fwd_prec == 1 ? 5.9604644775390625e-08 : a.fwd_prec == 2 ? 5.684341886080802e-14
-                                                                                 : 1.1102230246251565e-16;
-    SFFT_TRY(launch_zero_test(a.d_lats, a.nlat, a.d_inst, a.prec, 32.0 * u, st));
-    // count rule over all candidates, ascending compaction of Itilde
-    SFFT_TRY(mark(a, ST_HASH, st));
-    for (const auto& h : a.hash)
-        SFFT_TRY(launch_hash_count(a.d_inst + h.off, h.count, h.d, h.gx, h.smem, h.variant, h.l0, h.l1, h.mode, st));
-    SFFT_TRY(mark(a, ST_COMPACT, st));
-    SFFT_TRY(launch_compact(a.d_inst, ni, st));
-    // hashes of Itilde, collision counts, median / hybrid combine
-    // (the median combine forms the hashes itself; the hybrid one needs all collision counts first)
-    SFFT_TRY(mark(a, ST_DET_HASH, st));
-    if (a.hybrid) SFFT_TRY(launch_det_hashes(a.d_inst, ni, a.maxcap, st));
-    SFFT_TRY(mark(a, ST_COMBINE, st));
-    if (a.hybrid) SFFT_TRY(launch_collisions(a.d_inst, ni, st));
-    SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, a.hybrid ? 0 : 3, st));
-    if (a.lsq) {  // Remark 2.8 least squares on the detected set, from the medians
-        SFFT_TRY(mark(a, ST_LSQ, st));
-        SFFT_TRY(launch_lsq(a.d_inst, ni, a.prec, st));
+    if (a.phase != 2) {
+        SFFT_TRY(mark(a, ST_CLEAR, st));
+        SFFT_TRY(launch_clear(a.d_inst, ni, 1, a.hybrid, 0, st));
+        // Algorithm 2: lattice DFTs (normalised by 1/M) + per-lattice statistics
+        SFFT_TRY(mark(a, ST_FFT_FWD, st));
+        for (const auto& f : a.fwd)
+            SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.mode, a.fwd_prec, a.prec, a.prec, -1, EPI_ANALYZE,
+                                      a.d_inst, st, nullptr, nullptr, f.threads));
+        // zero test with direct re-tests inside the guard band (Remark 2.3); unit roundoff of the
+        // transform arithmetic (double-float: 2^-44, a bound with margin for its ~48-bit operations)
+        SFFT_TRY(mark(a, ST_ZERO_TEST, st));
+        const double u = a.fwd_prec == 1 ? 5.9604644775390625e-08 : a.fwd_prec == 2 ? 5.684341886080802e-14
+                                                                                     : 1.1102230246251565e-16;
+        SFFT_TRY(launch_zero_test(a.d_lats, a.nlat, a.d_inst, a.prec, 32.0 * u, st));
+        // count rule over all candidates, ascending compaction of Itilde
+        SFFT_TRY(mark(a, ST_HASH, st));
+        for (const auto& h : a.hash)
+            SFFT_TRY(launch_hash_count(a.d_inst + h.off, h.count, h.d, h.gx, h.smem, h.variant, h.l0, h.l1, h.mode, st));
+        SFFT_TRY(mark(a, ST_COMPACT, st));
+        SFFT_TRY(launch_compact(a.d_inst, ni, st));
+        // hashes of Itilde, collision counts, median / hybrid combine
+        // (the median combine forms the hashes itself; the hybrid one needs all collision counts first)
+        SFFT_TRY(mark(a, ST_DET_HASH, st));
+        if (a.hybrid) SFFT_TRY(launch_det_hashes(a.d_inst, ni, a.maxcap, st));
+        SFFT_TRY(mark(a, ST_COMBINE, st));
+        if (a.hybrid) SFFT_TRY(launch_collisions(a.d_inst, ni, st));
+        SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, a.hybrid ? 0 : 3, st));
+        if (a.lsq) {  // Remark 2.8 least squares on the detected set, from the medians
+            SFFT_TRY(mark(a, ST_LSQ, st));
+            SFFT_TRY(launch_lsq(a.d_inst, ni, a.prec, st));
+        }
+        if (a.phase == 1) {  // a shard's part of C (FP64 buckets), summed over the shards by the caller
+            SFFT_TRY(launch_clear(a.d_inst, ni, 0, 0, 1, st));
+            SFFT_TRY(launch_scatter_coef(a.d_inst, ni, false, st));
+            SFFT_TRY(mark(a, ST_COUNT, st));
+            return SFFT_OK;
+        }
     }
     if (a.refine) {
-        // FP32 transforms: float buckets C (their rounding is far below the transform's error)
-        const bool f32 = a.prec == 1 && a.fwd_prec == 1;
-        SFFT_TRY(mark(a, ST_SCATTER, st));
-        SFFT_TRY(launch_clear(a.d_inst, ni, 0, 0, f32 ? 2 : 1, st));
-        SFFT_TRY(launch_scatter_coef(a.d_inst, ni, f32, st));
+        // FP32 transforms: float buckets C (their rounding is far below the transform's error);
+        // the second half of a sharded reconstruction gets FP64 buckets
+        const bool f32 = a.prec == 1 && a.fwd_prec == 1 && a.phase == 0;
+        if (a.phase == 0) {
+            SFFT_TRY(mark(a, ST_SCATTER, st));
+            SFFT_TRY(launch_clear(a.d_inst, ni, 0, 0, f32 ? 2 : 1, st));
+            SFFT_TRY(launch_scatter_coef(a.d_inst, ni, f32, st));
+        }
         // residual spectrum r_hat = ghat - C at the buckets of Itilde (eq. 2.3), median update
         SFFT_TRY(mark(a, ST_DELTA, st));
         SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, f32 ? 2 : 1, st));
@@ -737,8 +748,10 @@ int sfft_reconstruct(sfft_plan* plan, const void* samples, int64_t* supp_out, do
     I.out_cap = cap;
     I.dcounts = diag ? diag->counts : nullptr;
     I.dhashes = diag ? diag->hashes : nullptr;
+    I.key_out = nullptr;
     cudaStream_t st = P->st;
     SFFT_TRY(P->io_upload());
+    P->shard_open = false;
     P->diag_run = diag && (diag->counts || diag->hashes);
     SFFT_TRY(run_pipeline(P->pipe_args(), st));
     SFFT_CU(cudaMemcpyAsync(P->h_cnt, P->cnt, sizeof(int64_t) * 8, cudaMemcpyDeviceToHost, st));
@@ -780,6 +793,72 @@ int sfft_reconstruct(sfft_plan* plan, const void* samples, int64_t* supp_out, do
     }
     if (c[3] & ERR_DET_CAP) { set_error("|Itilde| = %lld exceeds detect_cap = %lld", (long long)c[0], (long long)P->cap); return SFFT_ECAPACITY; }
     if (c[3] & ERR_OUT_CAP) { set_error("%lld selected frequencies exceed cap = %lld", (long long)c[1], (long long)cap); return SFFT_ECAPACITY; }
+    return SFFT_OK;
+}
+
+static int read_counts(Plan* P) {
+    SFFT_CU(cudaMemcpyAsync(P->h_cnt, P->cnt, sizeof(int64_t) * 8, cudaMemcpyDeviceToHost, P->st));
+    SFFT_CU(cudaStreamSynchronize(P->st));
+    const int64_t* c = P->h_cnt;
+    if (c[3] & ERR_GUARD_CAP) {
+        set_error("more than 1024 buckets of one lattice lie inside the FP64 guard band around tau");
+        return SFFT_ECAPACITY;
+    }
+    if (c[3] & ERR_DET_CAP) { set_error("|Itilde| = %lld exceeds detect_cap = %lld", (long long)c[0], (long long)P->cap); return SFFT_ECAPACITY; }
+    return SFFT_OK;
+}
+
+int sfft_reconstruct_shard_begin(sfft_plan* plan, const void* samples, double* C_out, int64_t* n_detected) {
+    if (!plan || !samples || !C_out) { set_error("null argument"); return SFFT_EINVAL; }
+    Plan* P = reinterpret_cast<Plan*>(plan);
+    SFFT_CHECK(P->p.combine == SFFT_COMBINE_MEDIAN, SFFT_EINVAL, "sharded reconstructions use the median combine");
+    SFFT_CHECK(P->p.theta_rel == 0.0, SFFT_EINVAL,
+               "sharded reconstructions need an absolute theta (theta_rel = 0: the largest modulus is global)");
+    SFFT_TRY(P->io_begin());
+    InstDesc& I = *P->h_inst;
+    I.samples = samples;
+    I.supp_out = nullptr;
+    I.coef_out = nullptr;
+    I.key_out = nullptr;
+    I.out_cap = 0;
+    I.dcounts = nullptr;
+    I.dhashes = nullptr;
+    SFFT_TRY(P->io_upload());
+    P->diag_run = false;
+    PipeArgs a = P->pipe_args();
+    a.phase = 1;
+    SFFT_TRY(run_pipeline(a, P->st));
+    SFFT_CU(cudaMemcpyAsync(C_out, P->C, sizeof(c64) * P->sumM, cudaMemcpyDeviceToDevice, P->st));
+    SFFT_TRY(read_counts(P));
+    if (n_detected) *n_detected = P->h_cnt[0];
+    P->have_forward = false;
+    P->shard_open = true;
+    return SFFT_OK;
+}
+
+int sfft_reconstruct_shard_end(sfft_plan* plan, const double* C_sum, int64_t* supp_out, double* coef_out,
+                               uint64_t* keys_out, int64_t cap, int64_t* n_out) {
+    if (!plan || !C_sum || (cap > 0 && (!supp_out || !coef_out))) { set_error("null argument"); return SFFT_EINVAL; }
+    Plan* P = reinterpret_cast<Plan*>(plan);
+    SFFT_CHECK(P->shard_open, SFFT_ESTATE, "sfft_reconstruct_shard_end without sfft_reconstruct_shard_begin");
+    P->shard_open = false;
+    SFFT_TRY(P->io_begin());
+    InstDesc& I = *P->h_inst;
+    I.supp_out = supp_out;
+    I.coef_out = reinterpret_cast<c64*>(coef_out);
+    I.key_out = keys_out;
+    I.out_cap = cap;
+    SFFT_TRY(P->io_upload());
+    SFFT_CU(cudaMemcpyAsync(P->C, C_sum, sizeof(c64) * P->sumM, cudaMemcpyDeviceToDevice, P->st));
+    PipeArgs a = P->pipe_args();
+    a.phase = 2;
+    SFFT_TRY(run_pipeline(a, P->st));
+    SFFT_TRY(read_counts(P));
+    if (n_out) *n_out = P->h_cnt[1];
+    if (P->h_cnt[3] & ERR_OUT_CAP) {
+        set_error("%lld selected frequencies exceed cap = %lld", (long long)P->h_cnt[1], (long long)cap);
+        return SFFT_ECAPACITY;
+    }
     return SFFT_OK;
 }
 

@@ -275,6 +275,7 @@ struct InstDesc {
     // ---- per call
     const void* samples;       // [sum M] complex (prec)
     int64_t* supp_out;
+    uint64_t* key_out;         // optional: the rank key of each output (sharded merges)
     c64* coef_out;
     int64_t out_cap;
     uint8_t* dcounts;          // diag

@@ -298,6 +298,7 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
         I.out_cap = cap[u];
         I.dcounts = nullptr;
         I.dhashes = nullptr;
+        I.key_out = nullptr;
         B->plans[i]->have_forward = false;  // batch runs do not keep a backward context
     }
     cudaStream_t st = B->st;

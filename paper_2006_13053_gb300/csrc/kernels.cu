@@ -1213,10 +1213,11 @@ __global__ void __launch_bounds__(kSelThreads) k_select(InstDesc* __restrict__ i
         int64_t q = q0 + threadIdx.x;
         int sel = 0, eq = 0;
         c64 c = {0, 0};
+        uint64_t key = 0;
         if (q < nd) {
             c = I.coef[q];
             const double a = absc(q);
-            const uint64_t key = rank_key(a, I.rank_bits);
+            key = rank_key(a, I.rank_bits);
             if (a >= theta) {
                 if (!trunc || key > prefix) sel = 1;
                 else if (key == prefix) eq = 1;
@@ -1233,6 +1234,7 @@ __global__ void __launch_bounds__(kSelThreads) k_select(InstDesc* __restrict__ i
             if (pos < I.out_cap) {
                 I.supp_out[pos] = I.det[q];
                 I.coef_out[pos] = c;
+                if (I.key_out) I.key_out[pos] = key;
             }
             if (pos < I.cap) I.outpos[pos] = (int32_t)q;
         }

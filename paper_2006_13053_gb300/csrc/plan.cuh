@@ -44,6 +44,10 @@ struct PipeArgs {
     int fwd_prec = 0;  // arithmetic of the forward transforms (2 = double-float for FP32 + refinement)
     int64_t maxcap = 0;
     int hybrid = 0, refine = 0, lsq = 0;
+    // 0: the whole stage sequence; 1: through the combine, then the detected coefficients summed
+    // into FP64 buckets C (a shard's part of the refinement's C); 2: the refinement update on a C
+    // given in the buckets, then Algorithm 4 (the second half of a sharded reconstruction)
+    int phase = 0;
     InstDesc* d_inst = nullptr;
     const LatDesc* d_lats = nullptr;
     std::vector<FftLaunch> fwd;
@@ -103,6 +107,7 @@ struct Plan {
     int32_t* d_z = nullptr;       // [L, d] generating vectors on the device
     bool diag_run = false;        // the current reconstruct writes per-candidate diagnostics
     bool have_forward = false;
+    bool shard_open = false;      // sfft_reconstruct_shard_begin ran; _end is due
     cudaEvent_t io_ev = nullptr;  // recorded after each upload of h_inst (staging reuse guard)
 
     int io_begin();               // wait until the previous upload of h_inst has completed
