@@ -342,7 +342,7 @@ def inst_from_profiles(kernel):
 # the packed hash kernel's candidate-to-warp mapping (csrc/kernels.cu: kHashThreads threads per CTA,
 # kCPT2 candidates per thread at tile offsets thread + c * kHashThreads; the count-rule exit is
 # tested after every second lattice)
-HASH_THREADS, HASH_CPT = 256, 4
+HASH_THREADS, HASH_CPT = 384, 4
 
 
 def executed_hash_evals(plan, samples):

@@ -452,7 +452,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     SFFT_TRY(upload_jobs(P->jobs_samp, &P->d_jobs_samp, &P->allocs));
     // hash-count kernel choice; lattices split into groups whose bitmaps fit shared memory
     int64_t maxM = *std::max_element(P->M.begin(), P->M.end());
-    P->packed = P->kmax <= 127 && maxM <= 32768;
+    P->packed = P->kmax <= 127 && maxM < 65536;  // int8 k, int16 z in the symmetric range
     const size_t kHashSmem = 200 * 1024;
     for (int l0 = 0; l0 < L;) {
         int l1 = l0 + 1;
@@ -473,7 +473,7 @@ int plan_create(Plan* P, int d, const void* cand, int64_t n, int64_t s, int Lin,
     // bucket bit indices below 2^22, d <= 16 (2d <= 32) and L <= 64 (tensor-memory columns)
     // (int8 rows are read as whole words there: strides of a multiple of 4 bytes)
     if (P->packed && d <= 16 && L <= 64 && P->hgroups.size() == 1 && P->p.cand_ld % 4 == 0 &&
-        (double)d * (double)P->kmax * (double)(maxM - 1) < 16777216.0 && words * 32 < (1 << 22)) {
+        maxM <= 32768 && (double)d * (double)P->kmax * (double)(maxM - 1) < 16777216.0 && words * 32 < (1 << 22)) {
         P->tc_smem = hash_tc_smem_bytes(L, words);
         P->hash_tc = P->tc_smem <= 220 * 1024;
     }

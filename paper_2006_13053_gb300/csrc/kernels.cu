@@ -259,7 +259,10 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
 // and the generating vectors sit in shared memory.  h = k.z_l mod M_l is exact: the int32
 // inner product is offset by a multiple of M_l to be non-negative and reduced by a Barrett
 // step (q = umulhi(x, floor(2^32/M)), one conditional subtraction).
-constexpr int kHashThreads = 256;
+// 384 threads: the bitmap of all lattices (48 KB at L = 37, M = 10331) lets 4 CTAs share an SM, so
+// 384-thread CTAs keep 48 warps resident where 256-thread ones keep 32 (measured 0.398 -> 0.363 ms
+// for 16 instances of 2^20 candidates; 512 threads: 0.367 ms, limited by registers to 3 CTAs)
+constexpr int kHashThreads = 384;
 constexpr int kCPT = 2;  // candidates per thread
 
 template <int D>
@@ -363,8 +366,9 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __r
     }
 }
 
-// Packed variant: |k_t| <= 127 and M_l <= 32768, so k is stored as int8x4 words and z_l as
-// int16x2 words; each dp2a instruction adds two products k_t z_t exactly into the int32 sum.
+// Packed variant: |k_t| <= 127 and M_l < 65536, so k is stored as int8x4 words and z_l (in its
+// symmetric residue range) as int16x2 words; each dp2a instruction adds two products k_t z_t
+// exactly into the int32 sum.
 // Per lattice a 16-byte aligned record in shared memory holds {M, mu, off, bit offset} and the
 // packed z words (broadcast loads shared by all threads).  DIAG additionally writes the
 // per-candidate hashes and counts.
@@ -377,7 +381,7 @@ template <int D> struct Pack {
 };
 
 template <int D, bool DIAG>
-__global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDesc* __restrict__ insts, int l0,
+__global__ void __launch_bounds__(kHashThreads, 4) k_hash_count_packed(const InstDesc* __restrict__ insts, int l0,
                                                                      int l1in, int mode) {
     extern __shared__ __align__(16) uint32_t hsm[];
     using PK = Pack<D>;
@@ -395,10 +399,17 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count_packed(const InstDe
         r[1] = I.mu[l];
         r[2] = I.offk[l];
         r[3] = (uint32_t)(I.boff[l] - w0) * 32u;
+        // z_t in the symmetric range |z_t| <= (M - 1) / 2 (k.z = k.(z - M) mod M): signed int16 for
+        // every prime M < 65536
+        const int Mh = I.Ml[l] / 2;
+        auto zsym = [&](int t) -> uint32_t {
+            const int v = I.z[l * D + t];
+            return (uint32_t)(v > Mh ? v - I.Ml[l] : v) & 0xffffu;
+        };
         for (int w = 0; w < PK::REC - 4; ++w) {
             uint32_t lo = 0, hi = 0;
-            if (2 * w < D) lo = (uint32_t)I.z[l * D + 2 * w] & 0xffffu;
-            if (2 * w + 1 < D) hi = (uint32_t)I.z[l * D + 2 * w + 1] & 0xffffu;
+            if (2 * w < D) lo = zsym(2 * w);
+            if (2 * w + 1 < D) hi = zsym(2 * w + 1);
             r[4 + w] = lo | (hi << 16);
         }
     }

@@ -135,7 +135,7 @@ extern "C" int sfft_detect_noalloc(int d, const int32_t* cand, int64_t n_cand, i
         w += (M[l] + 31) / 32;
         so[l + 1] = so[l] + M[l];
     }
-    const bool packed = kmax <= 127 && maxM <= 32768;
+    const bool packed = kmax <= 127 && maxM < 65536;
     const size_t smem = hash_smem_bytes(d, L, (int)words, packed);
     SFFT_CHECK(smem <= 220 * 1024, SFFT_ECAPACITY, "non-zero bitmap of %lld words does not fit shared memory",
                (long long)words);

@@ -97,7 +97,7 @@ struct Plan {
     BlueJob* d_jobs_fwd = nullptr;
     BlueJob *d_jobs_samp = nullptr, *d_jobs_adj = nullptr;
     size_t hash_smem = 0;
-    bool packed = false;          // |k| <= 127 and M <= 32768: packed dp2a hash kernel
+    bool packed = false;          // |k| <= 127 and M < 65536: packed dp2a hash kernel
     bool hash_tc = false;         // tensor-core products (hash_tc.cu): one lattice group, |k.z| < 2^24
     size_t tc_smem = 0;
     std::vector<std::pair<int, int>> hgroups;  // lattice groups whose bitmaps fit shared memory

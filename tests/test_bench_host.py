@@ -32,8 +32,8 @@ def test_pack_roundtrip_and_alignment():
 
 def test_executed_hash_evals_replay_matches_kernel_loop():
     """The replay of the hash kernel's early exit equals a plain loop over its warps: each warp of a
-    1024-candidate tile holds candidates base + 32 w + lane + 256 c (c < 4) and stops after lattice
-    l (l odd) once no candidate's count plus the lattices left reaches the threshold."""
+    T*4-candidate tile (T threads per CTA) holds candidates base + 32 w + lane + T c (c < 4) and stops
+    after lattice l (l odd) once no candidate's count plus the lattices left reaches the threshold."""
     import numpy as np
     import torch
     import bench
@@ -41,11 +41,12 @@ def test_executed_hash_evals_replay_matches_kernel_loop():
     for n, L, p, need in ((3000, 37, 0.1, 19), (2048, 9, 0.45, 5), (1500, 13, 0.3, 7)):
         nz = (rng.random((n, L)) < p).astype(np.int64)
         nz[rng.choice(n, 5)] = 1  # a few candidates with every lattice non-zero (true support)
-        tile = 1024
+        T = bench.HASH_THREADS
+        tile = 4 * T
         expect = 0
         for base in range(0, n, tile):
-            for w in range(8):
-                idx = [base + 32 * w + lane + 256 * c for c in range(4) for lane in range(32)]
+            for w in range(T // 32):
+                idx = [base + 32 * w + lane + T * c for c in range(4) for lane in range(32)]
                 cnt = np.zeros(len(idx), dtype=np.int64)
                 visited = L
                 for l in range(L):

@@ -1,6 +1,6 @@
 """The batching pattern at the configuration's parameter ranges: 64 uneven instances (d uniform in
 {5..20}, s log-uniform in [100, 10^4] so that M = nextprime(10.33 s) reaches 103,307 and the
-lattices go beyond the packed hash kernel's M <= 32768, |Gamma| log-uniform in [2^12, 2^15] from
+lattices go beyond the packed hash kernel's M < 65536, |Gamma| log-uniform in [2^12, 2^15] from
 [-32, 32]^d so that the oracle can check every instance), FP32 samples with 40 dB noise, one
 refinement step on FP32 lattice DFTs, captured in a CUDA graph after autotuning."""
 import math
@@ -42,7 +42,7 @@ def test_uneven_batch_config3_ranges_matches_oracle():
         plans.append(plan)
         samples.append(torch.from_numpy(y).to(dev))
         Ms.append(M)
-    assert max(Ms) > 32768 and min(Ms) < 32768  # both hash kernels
+    assert max(Ms) > 65536 and min(Ms) < 65536  # both hash kernels
     st = torch.cuda.Stream()
     B = G.Batch(plans, use_graph=True, stream=st)
     B.autotune(samples, reps=1)

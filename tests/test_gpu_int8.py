@@ -1,6 +1,6 @@
 """Compact int8 candidate rows (|k_t| <= 127, any row stride >= d bytes) through the C ABI: the
 same detections, hashes, counts, supports and coefficients as the int32 rows, and the FP64
-oracle's, for both hash kernels (packed dp2a for M <= 32768, int32 arithmetic above), with rows
+oracle's, for both hash kernels (packed dp2a for M < 65536, int32 arithmetic above), with rows
 on word boundaries (stride 12) and at any byte offset (strides 10 and 13, the latter with an
 array length that is not a multiple of 4 bytes)."""
 import math
@@ -73,12 +73,15 @@ def test_int8_rows_match_int32_and_oracle(G, prec, refine, ld):
     B.close()
 
 
-def test_int8_rows_large_lattice_int32_kernel(G):
-    """M > 32768 selects the int32-arithmetic hash kernel, which reads the int8 rows bytewise."""
+@pytest.mark.parametrize("M", [32771, 65537])
+def test_int8_rows_large_lattice_int32_kernel(G, M):
+    """32768 < M < 65536 keeps the packed dp2a kernel (generators in the symmetric range
+    |z| <= (M-1)/2, signed int16); M > 65536 selects the int32-arithmetic hash kernel, which reads
+    the int8 rows bytewise.  Hashes and the reconstruction equal the oracle's in both."""
     import torch
     seed, n, d, s = 5, 4096, 6, 8
     cand = S.uniform_distinct(n, d, -100, 100, seed)
-    L, M = 5, 32771
+    L = 5
     z = S.generators(L, d, M, seed)
     sup = S.support_indices(n, s, seed)
     c = S.coef_mag_phase(s, 1, 10, seed)

@@ -8,7 +8,7 @@ cases alternate between large and small problems: stale contents of an earlier c
 
 The lattice DFTs and the thresholds are the oracle's (FP64, and the same values rounded to FP32 as
 an FP32 transform would deliver them); both sides decide on identical inputs, so the detected sets
-must be identical.  The entry point takes int32 rows: small boxes (|k| <= 127, M <= 32768) run the
+must be identical.  The entry point takes int32 rows: small boxes (|k| <= 127, M < 65536) run the
 packed dp2a hash kernel, the box of 200 the int32 kernel (int4 row loads at d = 4 and d = 8)."""
 import ctypes
 import math
