@@ -265,6 +265,43 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
 constexpr int kHashThreads = 384;
 constexpr int kCPT = 2;  // candidates per thread
 
+// Row r of int8 candidate rows of stride ld bytes as KW int8x4 words: directly when ld is a multiple
+// of 4, else from the aligned words around the row by funnel shifts.  Rows below r_safe have those
+// KW + 1 words inside the array; the last rows are read with bounds checks (no read past nbytes).
+// Bytes past d belong to the next row (or are zero at the array's end).
+template <int KW>
+__device__ __forceinline__ void load_row8(const uint32_t* __restrict__ w8, const uint8_t* __restrict__ b8, int64_t r,
+                                          int ld, int64_t nbytes, int64_t r_safe, uint32_t* kw) {
+    if ((ld & 3) == 0) {
+        const int ldw = ld >> 2;
+#pragma unroll
+        for (int w = 0; w < KW; ++w) kw[w] = __ldg(w8 + r * ldw + w);
+        return;
+    }
+    const int64_t b0 = r * ld, w0 = b0 >> 2;
+    const uint32_t sh = (uint32_t)(b0 & 3) * 8u;
+    uint32_t wv[KW + 1];
+    if (r < r_safe) {
+#pragma unroll
+        for (int j = 0; j <= KW; ++j) wv[j] = __ldg(w8 + w0 + j);
+    } else {
+#pragma unroll
+        for (int j = 0; j <= KW; ++j) {
+            const int64_t wj = w0 + j;
+            if ((wj + 1) * 4 <= nbytes) {
+                wv[j] = __ldg(w8 + wj);
+            } else {  // the array's last bytes
+                uint32_t v = 0;
+                for (int q = 0; q < 4; ++q)
+                    if (wj * 4 + q < nbytes) v |= (uint32_t)b8[wj * 4 + q] << (8 * q);
+                wv[j] = v;
+            }
+        }
+    }
+#pragma unroll
+    for (int w = 0; w < KW; ++w) kw[w] = __funnelshift_r(wv[w], wv[w + 1], sh);
+}
+
 template <int D>
 __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __restrict__ insts, int l0, int l1in,
                                                               int mode) {
@@ -295,18 +332,37 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __r
     const int ld = I.cand_ld;
     uint8_t* dcounts = I.dcounts;
     int32_t* dhashes = I.dhashes;
+    const uint32_t* __restrict__ cand8w = reinterpret_cast<const uint32_t*>(I.cand);
+    const int64_t nbytes = n * ld;
+    constexpr int KW = (D + 3) / 4;
+    const int64_t r_safe = n - (4 * KW + 3) / (ld > 0 ? ld : 1) - 1;
     const int64_t step = (int64_t)gridDim.x * blockDim.x * kCPT;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kCPT; base < n; base += step) {
         int k[kCPT][D];
         int64_t idx[kCPT];
+        int cnt[kCPT];
 #pragma unroll
         for (int c = 0; c < kCPT; ++c) {
             idx[c] = base + threadIdx.x + (int64_t)c * blockDim.x;
+            cnt[c] = (mode & 1) || idx[c] >= n ? 0 : I.cnt8[idx[c]];
+        }
+        if (!(mode & 1) && !dhashes && !dcounts) {
+            // a later lattice group: a warp none of whose candidates can still reach the count
+            // threshold with this and the following groups' lattices is decided (counts unchanged)
+            bool alive = false;
+#pragma unroll
+            for (int c = 0; c < kCPT; ++c) alive |= idx[c] < n && cnt[c] + (L - l0) >= need;
+            if (!__any_sync(0xffffffffu, alive)) continue;
+        }
+#pragma unroll
+        for (int c = 0; c < kCPT; ++c) {
             const int64_t r = idx[c] < n ? idx[c] : 0;
             const int32_t* row = cand + r * D;
-            if (I.cand_i8) {  // int8 rows of stride ld bytes
+            if (I.cand_i8) {  // int8 rows of stride ld bytes, read as words, sign-extended per byte
+                uint32_t kw[KW];
+                load_row8<KW>(cand8w, reinterpret_cast<const uint8_t*>(cand8), r, ld, nbytes, r_safe, kw);
 #pragma unroll
-                for (int t = 0; t < D; ++t) k[c][t] = (int)__ldg(cand8 + r * ld + t);
+                for (int t = 0; t < D; ++t) k[c][t] = (int)(int32_t)(kw[t >> 2] << (24 - 8 * (t & 3))) >> 24;
             } else if constexpr (D % 4 == 0) {
 #pragma unroll
                 for (int t = 0; t < D; t += 4) {
@@ -324,9 +380,6 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __r
                 for (int t = 0; t < D; ++t) k[c][t] = __ldg(row + t);
             }
         }
-        int cnt[kCPT];
-#pragma unroll
-        for (int c = 0; c < kCPT; ++c) cnt[c] = (mode & 1) || idx[c] >= n ? 0 : I.cnt8[idx[c]];
         for (int l = 0; l < Lg; ++l) {
             int zl[D];
 #pragma unroll
@@ -428,9 +481,24 @@ __global__ void __launch_bounds__(kHashThreads, 4) k_hash_count_packed(const Ins
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x * kCPT2; base < n; base += step) {
         uint32_t kw[kCPT2][PK::KW];
         int64_t idx[kCPT2];
+        int cnt[kCPT2];
 #pragma unroll
         for (int c = 0; c < kCPT2; ++c) {
             idx[c] = base + threadIdx.x + (int64_t)c * blockDim.x;
+            cnt[c] = (mode & 1) || idx[c] >= n ? 0 : I.cnt8[idx[c]];
+        }
+        if constexpr (!DIAG) {
+            if (!(mode & 1)) {
+                // a later lattice group: a warp none of whose candidates can still reach the count
+                // threshold with this and the following groups' lattices is decided (counts unchanged)
+                bool alive = false;
+#pragma unroll
+                for (int c = 0; c < kCPT2; ++c) alive |= idx[c] < n && cnt[c] + (L - l0) >= need;
+                if (!__any_sync(0xffffffffu, alive)) continue;
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < kCPT2; ++c) {
             const int64_t r = idx[c] < n ? idx[c] : 0;
             if (i8) {  // the int8 row already holds the packed words (bytes past d meet zero z entries)
                 if (ld4) {
@@ -488,9 +556,6 @@ __global__ void __launch_bounds__(kHashThreads, 4) k_hash_count_packed(const Ins
                 kw[c][w] = (uint32_t)(k[4 * w] & 0xff) | ((uint32_t)(k[4 * w + 1] & 0xff) << 8) |
                            ((uint32_t)(k[4 * w + 2] & 0xff) << 16) | ((uint32_t)(k[4 * w + 3] & 0xff) << 24);
         }
-        int cnt[kCPT2];
-#pragma unroll
-        for (int c = 0; c < kCPT2; ++c) cnt[c] = (mode & 1) || idx[c] >= n ? 0 : I.cnt8[idx[c]];
         for (int l = 0; l < Lg; ++l) {
             const uint4* r4 = reinterpret_cast<const uint4*>(rec + l * PK::REC);
             const uint4 cst = r4[0];
