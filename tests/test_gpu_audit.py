@@ -24,18 +24,23 @@ def A():
     return audit
 
 
-def _oracle_audit(cand, sup, z, M):
+def _oracle_audit(cand, sup, z, M, lsq=False):
     out = O.pfp_pfn(cand, sup, z, M)
     ok_r1l = False
+    ok_lsq = None if not lsq else False
     if out["n_pfn"] == 0:
         r = O.reconstruct(cand, out["samples"], z, M, tau_abs=0.5, postproc="hybrid", theta=0.5)
         ok_r1l = np.array_equal(r.supp, np.sort(sup))
-    return out["n_pfp"], out["n_pfn"], ok_r1l
+        if lsq:
+            r = O.reconstruct(cand, out["samples"], z, M, tau_abs=0.5, postproc="lsq", theta=0.5)
+            ok_lsq = np.array_equal(r.supp, np.sort(sup))
+    return out["n_pfp"], out["n_pfn"], ok_r1l, ok_lsq
 
 
 def test_random_sets_audit_matches_oracle(A):
     """Section 4.1.2's experiment at |Gamma| = 10^6 (10^7 in the paper) from [-1000, 1000]^3,
-    |I| = 1000, M = 10331, two draws of (Gamma, I) for L = 9 and 25."""
+    |I| = 1000, M = 10331, two draws of (Gamma, I) for L = 9 and 25, with the least-squares
+    post-processing as a third outcome."""
     import torch
     dev = torch.device("cuda:0")
     n, s, M, box = 10 ** 6, 1000, 10331, 1000
@@ -46,14 +51,14 @@ def test_random_sets_audit_matches_oracle(A):
         hc, hs = cand.cpu().numpy(), sup.cpu().numpy()
         for L in (9, 25):
             z = A._generators(1000 + L, L, 3, M)
-            med, hyb = A.audit_plans(cand, s, L, M, z)
-            n_pfp, n_pfn, ok_med, ok_r1l = A.audit_once(med, hyb, cand, sup)
-            med.close()
-            hyb.close()
-            ref = _oracle_audit(hc, hs, z, M)
+            pl = A.audit_plans(cand, s, L, M, z, lsq=True)
+            n_pfp, n_pfn, ok_med, ok_r1l, ok_lsq = A.audit_once(pl, cand, sup)
+            pl.close()
+            ref = _oracle_audit(hc, hs, z, M, lsq=True)
             assert (n_pfp, n_pfn) == ref[:2], (rep, L)
             assert ok_med == (ref[0] == 0 and ref[1] == 0)
             assert ok_r1l == ref[2], (rep, L)
+            assert ok_lsq == ref[3], (rep, L)
             seen_pfp += n_pfp
     assert seen_pfp > 0  # the small-L runs do produce false positives
 
@@ -68,22 +73,20 @@ def test_rebinding_candidates_and_generators_matches_fresh_plans(A):
     c2 = S.uniform_distinct_device(n - 1000, 3, -400, 400, 2, dev)
     s2 = S.subset_device(n - 1000, s, 2, dev)
     z1, z2 = A._generators(5, L, 3, M), A._generators(6, L, 3, M)
-    med, hyb = A.audit_plans(c1, s, L, M, z1)
-    med.set_candidates(c2)
-    hyb.set_candidates(c2)
-    med.set_generators(z2)
-    hyb.set_generators(z2)
-    got = A.audit_once(med, hyb, c2, s2)
-    f_med, f_hyb = A.audit_plans(c2, s, L, M, z2)
-    assert got == A.audit_once(f_med, f_hyb, c2, s2)
+    pl = A.audit_plans(c1, s, L, M, z1)
+    pl.set_candidates(c2)
+    pl.set_generators(z2)
+    got = A.audit_once(pl, c2, s2)
+    fresh = A.audit_plans(c2, s, L, M, z2)
+    assert got == A.audit_once(fresh, c2, s2)
     ref = _oracle_audit(c2.cpu().numpy(), s2.cpu().numpy(), z2, M)
     assert got[:2] == ref[:2] and got[3] == ref[2]
     # a set beyond the plan's |k| bound is refused
     big = S.uniform_distinct_device(1000, 3, -600, 600, 3, dev)
     with pytest.raises(Exception):
-        med.set_candidates(big)
-    for p in (med, hyb, f_med, f_hyb):
-        p.close()
+        pl.med.set_candidates(big)
+    pl.close()
+    fresh.close()
 
 
 def test_hyperbolic_cross_audit_matches_oracle(A):
@@ -102,10 +105,9 @@ def test_hyperbolic_cross_audit_matches_oracle(A):
     cand, sup = torch.from_numpy(G).to(dev), torch.from_numpy(pos.astype(np.int64)).to(dev)
     for rep in range(1):
         z = A._generators(77 + rep, 15, 8, 11047)
-        med, hyb = A.audit_plans(cand, len(I), 15, 11047, z)
-        got = A.audit_once(med, hyb, cand, sup)
-        med.close()
-        hyb.close()
+        pl = A.audit_plans(cand, len(I), 15, 11047, z)
+        got = A.audit_once(pl, cand, sup)
+        pl.close()
         ref = _oracle_audit(G, pos, z, 11047)
         assert got[:2] == ref[:2] and got[3] == ref[2], rep
 
