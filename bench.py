@@ -341,15 +341,16 @@ def inst_from_profiles(kernel):
 
 # the packed hash kernel's candidate-to-warp mapping (csrc/kernels.cu: kHashThreads threads per CTA,
 # kCPT2 candidates per thread at tile offsets thread + c * kHashThreads; the count-rule exit is
-# tested after every second lattice)
-HASH_THREADS, HASH_CPT = 384, 4
+# tested after lattice l when the lattices left, rem = L - 1 - l, are fewer than the threshold and
+# rem is a multiple of kHashCheckEvery)
+HASH_THREADS, HASH_CPT, HASH_CHECK_EVERY = 384, 4, 1
 
 
 def executed_hash_evals(plan, samples):
     """Candidate-lattice evaluations that the packed hash kernel executes for one reconstruction:
-    a warp evaluates its 4 x 32 candidates on lattice after lattice and stops after lattice l
-    (l odd) once no candidate can still reach the count threshold ceil(nu L) with the L - 1 - l
-    lattices left.  Replayed from the per-lattice non-zero indicators of the reconstruction's
+    a warp evaluates its 4 x 32 candidates on lattice after lattice and stops after a tested lattice
+    l (rem = L - 1 - l below the threshold and a multiple of HASH_CHECK_EVERY) once no candidate can
+    still reach the count threshold ceil(nu L) with the rem lattices left.  Replayed from the per-lattice non-zero indicators of the reconstruction's
     diagnostics (hashes, lattice DFTs, thresholds), with the kernel's candidate-to-warp mapping."""
     import torch
     _, _, info = plan.reconstruct(samples, diag=True, hashes=True)
@@ -376,8 +377,7 @@ def executed_from_indicators(nz, need):
     alive = (cnt + rem[None, :]) >= need                                   # [T*tile, L]
     # tile-local index i = c * HASH_THREADS + thread, warp = thread // 32
     alive = alive.view(T, HASH_CPT, HASH_THREADS // 32, 32, L).any(dim=3).any(dim=1)  # [T, warps, L]
-    check = torch.zeros(L, dtype=torch.bool, device=nz.device)
-    check[1::2] = True
+    check = (rem < need) & (rem % HASH_CHECK_EVERY == 0)
     dead = (~alive) & check[None, None, :]
     first = torch.where(dead.any(dim=2), dead.to(torch.int8).argmax(dim=2) + 1,
                         torch.full(dead.shape[:2], L, dtype=torch.long, device=nz.device))

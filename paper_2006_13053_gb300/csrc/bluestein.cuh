@@ -447,7 +447,17 @@ __device__ __forceinline__ double block_reduce_sum(double v, double* red) {
     return out;
 }
 
-constexpr int kBlueThreads = 512;
+// Largest CTA of a transform (the register budget follows from it): FP32 transforms run up to
+// 864 threads (27 warps, 72 registers), so that the 1728 groups of a radix-12 pass of N = 20736
+// take two rounds of every thread; double and double-float transforms need more registers per
+// thread and stop at 512.
+#ifndef SFFT_BLUE_F32_THREADS
+#define SFFT_BLUE_F32_THREADS 864
+#endif
+template <class T> constexpr int blue_max_threads() { return std::is_same<T, float>::value ? SFFT_BLUE_F32_THREADS : 512; }
+// the same for a buffer mode: the global-scratch (0) and cluster (2) modes have longer address
+// arithmetic and stay at 512 threads so that they do not spill
+template <class T> constexpr int blue_max_threads(int mode) { return mode == 1 ? blue_max_threads<T>() : 512; }
 
 // Buffer access of one Bluestein transform: the first DIF pass reads the chirp-weighted input
 // (zero padded to N), the last DIF pass multiplies by the filter before its store, and the last
@@ -705,14 +715,14 @@ __device__ __forceinline__ void bluestein_cta(const BlueJob* __restrict__ jobs, 
 }
 
 template <class T, class TI, class TO, int MODE>
-__global__ void __launch_bounds__(kBlueThreads, 1) k_bluestein(const BlueJob* __restrict__ jobs, int sign, int epi,
+__global__ void __launch_bounds__(blue_max_threads<T>(MODE), 1) k_bluestein(const BlueJob* __restrict__ jobs, int sign, int epi,
                                                             const InstDesc* __restrict__ insts, void* out_base,
                                                             const void* aux_base) {
     bluestein_cta<T, TI, TO, MODE>(jobs, blockIdx.x, 0, sign, epi, insts, out_base, aux_base);
 }
 
 template <class T, class TI, class TO>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBlueThreads, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(blue_max_threads<T>(2), 1)
     k_bluestein_pair(const BlueJob* __restrict__ jobs, int sign, int epi, const InstDesc* __restrict__ insts,
                      void* out_base, const void* aux_base) {
     const int rank = (int)cooperative_groups::this_cluster().block_rank();
@@ -724,7 +734,9 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kBlueThreads, 1)
 template <class T, class TI, class TO>
 int launch_t(const BlueJob* djobs, int njobs, int maxN, int mode, int sign, int epi, const InstDesc* insts,
              cudaStream_t st, void* ob, const void* ab, int threads) {
-    if (threads < 64 || threads > kBlueThreads || threads % 32) threads = kBlueThreads;
+    // 0 (or any size the kernel cannot take): the largest CTA
+    const int tmax = blue_max_threads<T>(mode);
+    if (threads < 64 || threads > tmax || threads % 32) threads = tmax;
     if (njobs == 0) return SFFT_OK;
     if (mode == 1 || mode == 2) {
         const size_t bytes = blue_smem_bytes(mode == 2 ? maxN / 2 : maxN, sizeof(cplx<T>));

@@ -205,7 +205,7 @@ struct LatStats {
 struct InstDesc;
 int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, int mode, int prec, int in_prec, int out_prec, int sign,
                      int epi, const InstDesc* insts, cudaStream_t st, void* out_base = nullptr,
-                     const void* aux_base = nullptr, int threads = 512);
+                     const void* aux_base = nullptr, int threads = 0);
 size_t blue_smem_limit();
 // Shared-memory work buffers of 8-byte complex values are padded against bank conflicts of the
 // strided passes: element e lives at e + (e >> 5).  (16-byte values: measured slower padded, the
@@ -323,6 +323,46 @@ __device__ __forceinline__ unsigned long long rank_key(double v, int bits) {
         b = ((b + (1ull << (drop - 1))) >> drop) << drop;
     }
     return b;
+}
+
+// Copy of n 32-bit words from global to shared memory by the whole CTA with kCopyBatch loads of
+// every thread in flight (16-byte loads when both addresses are 16-byte aligned), so that a
+// CTA's prologue pays the global-memory latency a few times instead of once per word.
+template <int kCopyBatch = 4>
+__device__ __forceinline__ void copy_words_to_smem(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, int n) {
+    int done = 0;
+    if (((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(dst)) & 15) == 0) {
+        const int n4 = n >> 2;
+        const uint4* s4 = reinterpret_cast<const uint4*>(src);
+        uint4* d4 = reinterpret_cast<uint4*>(dst);
+        for (int i0 = threadIdx.x; i0 < n4; i0 += kCopyBatch * blockDim.x) {
+            uint4 v[kCopyBatch];
+#pragma unroll
+            for (int u = 0; u < kCopyBatch; ++u) {
+                const int i = i0 + u * blockDim.x;
+                if (i < n4) v[u] = __ldg(s4 + i);
+            }
+#pragma unroll
+            for (int u = 0; u < kCopyBatch; ++u) {
+                const int i = i0 + u * blockDim.x;
+                if (i < n4) d4[i] = v[u];
+            }
+        }
+        done = n4 << 2;
+    }
+    for (int i0 = done + threadIdx.x; i0 < n; i0 += kCopyBatch * blockDim.x) {
+        uint32_t v[kCopyBatch];
+#pragma unroll
+        for (int u = 0; u < kCopyBatch; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < n) v[u] = __ldg(src + i);
+        }
+#pragma unroll
+        for (int u = 0; u < kCopyBatch; ++u) {
+            const int i = i0 + u * blockDim.x;
+            if (i < n) dst[i] = v[u];
+        }
+    }
 }
 #endif
 

@@ -430,10 +430,11 @@ int sfft_batch_autotune(sfft_batch* b, const void* const* samples, int64_t* cons
             B->args.hash = keep;
         }
     }
-    // lattice transforms: 256 to 512 threads per CTA
-    const int ths[4] = {256, 384, 448, 512};
+    // lattice transforms: 256 to 864 threads per CTA (sizes above a transform type's largest CTA
+    // run at that largest)
+    const int ths[5] = {256, 384, 512, 576, 864};
     best = 1e30;
-    int bestt = 512;
+    int bestt = 0;
     for (int th : ths) {
         for (auto& f : B->args.fwd) f.threads = th;
         double ms = 0;

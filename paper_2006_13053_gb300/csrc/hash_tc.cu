@@ -60,7 +60,7 @@ __global__ void __launch_bounds__(kTcThreads * kTcGroups) k_hash_count_tc(const 
     unsigned char* sa = sb + kTcCols * kTcK * 2 + g * 128 * kTcK * 2;  // this group's A [128 x 32]
     float4* cst = reinterpret_cast<float4*>(tsm + kTcCols * kTcK * 2 + kTcGroups * 128 * kTcK * 2);
     uint32_t* bits = reinterpret_cast<uint32_t*>(cst + L);
-    for (int i = tid; i < nwords; i += blockDim.x) bits[i] = I.nzbits[i];
+    copy_words_to_smem(bits, I.nzbits, nwords);
     for (int e = tid; e < kTcGroups * 128 * kTcK / 2; e += blockDim.x)
         reinterpret_cast<uint32_t*>(tsm + kTcCols * kTcK * 2)[e] = 0u;
     for (int e = tid; e < kTcCols * kTcK; e += blockDim.x) {

@@ -12,7 +12,7 @@ struct FftLaunch {
     const BlueJob* jobs = nullptr;
     int njobs = 0, maxN = 0;
     int mode = 1;  // work buffer: 0 global scratch, 1 shared memory, 2 two-CTA cluster
-    int threads = 512;  // CTA size (autotuned)
+    int threads = 0;  // CTA size (0: the transform's largest; autotuned)
 };
 // one launch of the hash-count kernel over a contiguous range of instances of equal d
 struct HashGroup {

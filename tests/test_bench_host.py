@@ -33,7 +33,8 @@ def test_pack_roundtrip_and_alignment():
 def test_executed_hash_evals_replay_matches_kernel_loop():
     """The replay of the hash kernel's early exit equals a plain loop over its warps: each warp of a
     T*4-candidate tile (T threads per CTA) holds candidates base + 32 w + lane + T c (c < 4) and stops
-    after lattice l (l odd) once no candidate's count plus the lattices left reaches the threshold."""
+    after a tested lattice l (rem = L - 1 - l below the threshold and a multiple of the test
+    interval) once no candidate's count plus the rem lattices left reaches the threshold."""
     import numpy as np
     import torch
     import bench
@@ -51,7 +52,9 @@ def test_executed_hash_evals_replay_matches_kernel_loop():
                 visited = L
                 for l in range(L):
                     cnt += np.array([nz[i, l] if i < n else 0 for i in idx])
-                    if l % 2 == 1 and not np.any(cnt + (L - 1 - l) >= need):
+                    rem = L - 1 - l
+                    tested = rem < need and rem % bench.HASH_CHECK_EVERY == 0
+                    if tested and not np.any(cnt + rem >= need):
                         visited = l + 1
                         break
                 expect += 128 * visited
