@@ -349,8 +349,9 @@ HASH_THREADS, HASH_CPT, HASH_CHECK_EVERY = 384, 4, 1
 def executed_hash_evals(plan, samples):
     """Candidate-lattice evaluations that the packed hash kernel executes for one reconstruction:
     a warp evaluates its 4 x 32 candidates on lattice after lattice and stops after a tested lattice
-    l (rem = L - 1 - l below the threshold and a multiple of HASH_CHECK_EVERY) once no candidate can
-    still reach the count threshold ceil(nu L) with the rem lattices left.  Replayed from the per-lattice non-zero indicators of the reconstruction's
+    l (rem = L - 1 - l below the threshold and a multiple of HASH_CHECK_EVERY) once every candidate
+    is decided: its count has reached the threshold ceil(nu L), or cannot reach it with the rem
+    lattices left.  Replayed from the per-lattice non-zero indicators of the reconstruction's
     diagnostics (hashes, lattice DFTs, thresholds), with the kernel's candidate-to-warp mapping."""
     import torch
     _, _, info = plan.reconstruct(samples, diag=True, hashes=True)
@@ -374,9 +375,9 @@ def executed_from_indicators(nz, need):
     cnt = torch.zeros((T * tile, L), dtype=torch.int16, device=nz.device)
     cnt[:n] = torch.cumsum(nz.to(torch.int16), dim=1).to(torch.int16)
     rem = torch.arange(L - 1, -1, -1, device=nz.device, dtype=torch.int16)
-    alive = (cnt + rem[None, :]) >= need                                   # [T*tile, L]
+    undecided = (cnt < need) & ((cnt + rem[None, :]) >= need)              # [T*tile, L]
     # tile-local index i = c * HASH_THREADS + thread, warp = thread // 32
-    alive = alive.view(T, HASH_CPT, HASH_THREADS // 32, 32, L).any(dim=3).any(dim=1)  # [T, warps, L]
+    alive = undecided.view(T, HASH_CPT, HASH_THREADS // 32, 32, L).any(dim=3).any(dim=1)  # [T, warps, L]
     check = (rem < need) & (rem % HASH_CHECK_EVERY == 0)
     dead = (~alive) & check[None, None, :]
     first = torch.where(dead.any(dim=2), dead.to(torch.int8).argmax(dim=2) + 1,
@@ -570,11 +571,12 @@ def run_native(a, rank, world):
             units = n_inst * NCAND
             bytes_ = units * ROW8
             ex = executed_evals
-            wi = inst_from_profiles(f"k_hash_count_i8_ld{ROW8}")
+            wi = inst_from_profiles(f"k_hash_count_packed_ld{ROW8}")
             alu = {"evaluations_nominal": units * L, "evaluations_executed": ex,
                    "executed_per_candidate": ex / units,
                    "executed_evals_per_s": ex / t,
-                   "why": "warps stop once none of their 128 candidates can reach the count threshold; "
+                   "why": "warps stop once every one of their 128 candidates is decided (reached the count "
+                          "threshold or cannot reach it); "
                           "executed = sum over warps of 128 x lattices visited, replayed from instance 0's "
                           "per-lattice non-zero indicators with the kernel's candidate-to-warp mapping"}
             if wi is not None:
@@ -589,7 +591,7 @@ def run_native(a, rank, world):
             return {"kernel": "k_hash_count_packed", "bound": "hbm", "achieved": bytes_ / t / 1e9, "peak": hbm,
                     "unit": "GB/s", "frac": bytes_ / t / 1e9 / hbm, "peak_source": src,
                     "algorithmic_bytes_per_candidate": ROW8, "candidates_per_launch": units,
-                    "traffic": traffic_from_profiles(f"k_hash_count_i8_ld{ROW8}", units),
+                    "traffic": traffic_from_profiles(f"k_hash_count_packed_ld{ROW8}", units),
                     "int32_layout_bytes_per_candidate": 4 * D,
                     "alu": alu}
         if stage == "fft_fwd":

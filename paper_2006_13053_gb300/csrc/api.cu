@@ -505,7 +505,7 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
         SFFT_TRY(mark(a, ST_FFT_FWD, st));
         for (const auto& f : a.fwd)
             SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.mode, a.fwd_prec, a.prec, a.prec, -1, EPI_ANALYZE,
-                                      a.d_inst, st, nullptr, nullptr, f.threads));
+                                      a.d_inst, st, nullptr, nullptr, f.threads, f.upair));
         // zero test with direct re-tests inside the guard band (Remark 2.3); unit roundoff of the
         // transform arithmetic (double-float: 2^-44, a bound with margin for its ~48-bit operations)
         SFFT_TRY(mark(a, ST_ZERO_TEST, st));
@@ -574,6 +574,7 @@ PipeArgs Plan::pipe_args() {
     a.prec = prec; a.fwd_prec = fwd_prec(); a.maxcap = cap;
     a.hybrid = p.combine == SFFT_COMBINE_HYBRID; a.refine = p.refine; a.lsq = p.combine == SFFT_COMBINE_LSQ;
     a.fwd.push_back(FftLaunch{d_jobs_fwd, L, maxN, buf_mode(fwd_prec())});
+    a.fwd.back().upair = uniform_pair(jobs_fwd.data(), jobs_fwd.size());
     const int ng = (int)hgroups.size();
     for (int g = 0; g < ng; ++g) {
         HashGroup h;
@@ -903,7 +904,8 @@ int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const do
     SFFT_TRY(launch_clear(P->d_inst, 1, 0, 0, P->prec ? 2 : 1, st));
     if (n_terms > 0) SFFT_TRY(launch_scatter_terms(P->d_inst, 1, n_terms * P->L, st));
     SFFT_TRY(launch_bluestein(P->d_jobs_samp, P->L, P->maxN, P->buf_mode(P->prec), P->prec, P->prec, P->prec, +1,
-                              EPI_ADDNOISE, P->d_inst, st));
+                              EPI_ADDNOISE, P->d_inst, st, nullptr, nullptr, 0,
+                              uniform_pair(P->jobs_samp.data(), P->jobs_samp.size())));
     return SFFT_OK;
 }
 

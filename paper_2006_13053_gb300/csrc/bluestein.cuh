@@ -415,44 +415,55 @@ __device__ __forceinline__ void run_pass(int mode, int r1, int r2, C& c, int Ns,
 #undef SFFT_PASS
 }
 
-__device__ __forceinline__ double block_reduce_max(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    __syncthreads();
-    if (l == 0) red[w] = v;
-    __syncthreads();
-    double r = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-    if (w == 0)
-        for (int o = 16; o > 0; o >>= 1) r = fmax(r, __shfl_xor_sync(0xffffffffu, r, o));
-    if (threadIdx.x == 0) red[0] = r;
-    __syncthreads();
-    double out = red[0];
-    __syncthreads();
-    return out;
+// A transform whose passes are all the same fused pair (UP = r1 | r2 << 4, e.g. N = 20736 =
+// 12^4 for M = 10331) runs a kernel compiled with that pair only: no run-time dispatch and a
+// fraction of the generic kernel's code (fewer instruction-fetch stalls).  UP = 0: generic.
+template <int UP, class T, class TW, class C>
+__device__ __forceinline__ void run_pass_u(int mode, int r1, int r2, C& c, int Ns, const TW& tw) {
+    if constexpr (UP != 0) {
+        constexpr int A = UP & 15, B = UP >> 4;
+        if (mode == 0) dif_pass<A, B, -1, T>(c, Ns, tw);
+        else if (mode == 1) dit_pass<A, B, T>(c, Ns, tw);
+        else mid_pass<A, B, T>(c);
+    } else {
+        run_pass<T>(mode, r1, r2, c, Ns, tw);
+    }
 }
 
-__device__ __forceinline__ double block_reduce_sum(double v, double* red) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+// CTA-wide sum of a and maximum of b in one pass (three barriers), in the statistics precision R:
+// float for float and double-float transforms (FP64 instructions are scarce on this GPU and the
+// statistics only place the zero test's guard band), double for double transforms.  red holds at
+// least 2 x 32 values of R.
+template <class R>
+__device__ __forceinline__ void block_reduce_sum_max(R& a, R& b, R* red) {
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
     __syncthreads();
-    if (l == 0) red[w] = v;
+    if (l == 0) { red[w] = a; red[32 + w] = b; }
     __syncthreads();
-    double r = (threadIdx.x < (blockDim.x >> 5)) ? red[threadIdx.x] : 0.0;
-    if (w == 0)
-        for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
-    if (threadIdx.x == 0) red[0] = r;
+    if (w == 0) {
+        R x = l < nw ? red[l] : R(0), y = l < nw ? red[32 + l] : R(0);
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_xor_sync(0xffffffffu, x, o);
+            y = fmax(y, __shfl_xor_sync(0xffffffffu, y, o));
+        }
+        if (l == 0) { red[0] = x; red[32] = y; }
+    }
     __syncthreads();
-    double out = red[0];
-    __syncthreads();
-    return out;
+    a = red[0];
+    b = red[32];
 }
 
 // Largest CTA of a transform (the register budget follows from it): FP32 transforms run up to
-// 864 threads (27 warps, 72 registers), so that the 1728 groups of a radix-12 pass of N = 20736
-// take two rounds of every thread; double and double-float transforms need more registers per
-// thread and stop at 512.
+// 576 threads (18 warps, 113 registers), so that the 1728 groups of a radix-12 pass of N = 20736
+// take three rounds of every thread (measured against 512 threads at 128 registers and 864 at 72:
+// the step's transforms 0.332 ms at 576, 0.346 at 864, 0.375 at 512); double and double-float
+// transforms need more registers per thread and stop at 512.
 #ifndef SFFT_BLUE_F32_THREADS
-#define SFFT_BLUE_F32_THREADS 864
+#define SFFT_BLUE_F32_THREADS 576
 #endif
 template <class T> constexpr int blue_max_threads() { return std::is_same<T, float>::value ? SFFT_BLUE_F32_THREADS : 512; }
 // the same for a buffer mode: the global-scratch (0) and cluster (2) modes have longer address
@@ -587,7 +598,7 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
 // follow the input phase (both halves filled, both CTAs running before any remote access), follow
 // the first pass, and come before and after the last one; after that no CTA reads the other's
 // half, so either may leave.
-template <class T, class TI, class TO, bool SMB, bool CL, class TW>
+template <class T, class TI, class TO, bool SMB, bool CL, int UP, class TW>
 __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, cplx<T>* rbuf, int rank, const TW& tw,
                                                int sign, int epi, const void* inp, const void* auxp, void* outp,
                                                double* red, double* xchg) {
@@ -628,25 +639,27 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
     const int np = J.npass;
     for (int p = 0, Ns = J.N; p < np - 1; ++p) {
         const int r1 = J.pass_r[p] & 15, r2 = J.pass_r[p] >> 4;
-        run_pass<T>(0, r1, r2, c, Ns, tw);
+        run_pass_u<UP, T>(0, r1, r2, c, Ns, tw);
         Ns /= r1 * r2;
         sync(p == 0);
     }
     int Ns = (J.pass_r[np - 1] & 15) * (J.pass_r[np - 1] >> 4);
-    run_pass<T>(2, J.pass_r[np - 1] & 15, J.pass_r[np - 1] >> 4, c, Ns, tw);
+    run_pass_u<UP, T>(2, J.pass_r[np - 1] & 15, J.pass_r[np - 1] >> 4, c, Ns, tw);
     // cluster-wide when this pass was also the first (np = 1) or the last DIT pass comes next
     sync(np <= 2);
     for (int p = np - 2; p >= 0; --p) {
         const int r1 = J.pass_r[p] & 15, r2 = J.pass_r[p] >> 4;
         Ns *= r1 * r2;
-        run_pass<T>(1, r1, r2, c, Ns, tw);
+        run_pass_u<UP, T>(1, r1, r2, c, Ns, tw);
         sync(p <= 1);
     }
     // ---- output phase over this CTA's elements below M
     c.store_output(h0, min(h1, J.M));
     if (epi == EPI_ANALYZE) {
-        double ssd = block_reduce_sum((double)c.ss, red);
-        double mx2 = block_reduce_max((double)c.mx2, red);
+        using R = typename BlueIo<T, TI, TO, SMB, CL>::R;
+        R ssr = c.ss, mxr = c.mx2;
+        block_reduce_sum_max(ssr, mxr, reinterpret_cast<R*>(red));
+        double ssd = (double)ssr, mx2 = (double)mxr;
         if constexpr (CL) {  // partials of both CTAs to rank 0
             auto cl = cooperative_groups::this_cluster();
             double* x0 = cl.map_shared_rank(xchg, 0);
@@ -670,12 +683,12 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
 // arithmetic (float, double or df64); TI/TO: element type of input/output.  MODE 0: work buffer
 // in J.scratch (global, L2-resident); 1: in dynamic shared memory; 2: split over the two CTAs'
 // shared memory.
-template <class T, class TI, class TO, int MODE>
+template <class T, class TI, class TO, int MODE, int UP>
 __device__ __forceinline__ void bluestein_cta(const BlueJob* __restrict__ jobs, int job, int rank, int sign, int epi,
                                               const InstDesc* __restrict__ insts, void* out_base,
                                               const void* aux_base) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    __shared__ double red[32];
+    __shared__ double red[64];
     __shared__ double xchg[4];
     const BlueJob& J = jobs[job];
     cplx<T>* buf = MODE ? reinterpret_cast<cplx<T>*>(smem_raw) : reinterpret_cast<cplx<T>*>(J.scratch);
@@ -706,19 +719,19 @@ __device__ __forceinline__ void bluestein_cta(const BlueJob* __restrict__ jobs, 
         for (int i = threadIdx.x; i < J.tw_na; i += blockDim.x) s_twa[i] = ga[i];
         for (int i = threadIdx.x; i < 256; i += blockDim.x) s_twb[i] = gb[i];
         __syncthreads();
-        bluestein_body<T, TI, TO, MODE != 0, MODE == 2>(J, buf, rbuf, rank, TwTwo{s_twa, s_twb}, sign, epi, inp, auxp, outp,
+        bluestein_body<T, TI, TO, MODE != 0, MODE == 2, UP>(J, buf, rbuf, rank, TwTwo{s_twa, s_twb}, sign, epi, inp, auxp, outp,
                                              red, xchg);
     } else {
-        bluestein_body<T, TI, TO, MODE != 0, MODE == 2>(J, buf, rbuf, rank, TwFull<T>{reinterpret_cast<const cplx<T>*>(J.tw)},
+        bluestein_body<T, TI, TO, MODE != 0, MODE == 2, UP>(J, buf, rbuf, rank, TwFull<T>{reinterpret_cast<const cplx<T>*>(J.tw)},
                                              sign, epi, inp, auxp, outp, red, xchg);
     }
 }
 
-template <class T, class TI, class TO, int MODE>
+template <class T, class TI, class TO, int MODE, int UP = 0>
 __global__ void __launch_bounds__(blue_max_threads<T>(MODE), 1) k_bluestein(const BlueJob* __restrict__ jobs, int sign, int epi,
                                                             const InstDesc* __restrict__ insts, void* out_base,
                                                             const void* aux_base) {
-    bluestein_cta<T, TI, TO, MODE>(jobs, blockIdx.x, 0, sign, epi, insts, out_base, aux_base);
+    bluestein_cta<T, TI, TO, MODE, UP>(jobs, blockIdx.x, 0, sign, epi, insts, out_base, aux_base);
 }
 
 template <class T, class TI, class TO>
@@ -726,14 +739,17 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(blue_max_threads<T>(
     k_bluestein_pair(const BlueJob* __restrict__ jobs, int sign, int epi, const InstDesc* __restrict__ insts,
                      void* out_base, const void* aux_base) {
     const int rank = (int)cooperative_groups::this_cluster().block_rank();
-    bluestein_cta<T, TI, TO, 2>(jobs, blockIdx.x >> 1, rank, sign, epi, insts, out_base, aux_base);
+    bluestein_cta<T, TI, TO, 2, 0>(jobs, blockIdx.x >> 1, rank, sign, epi, insts, out_base, aux_base);
 }
 
 // ================================================================== launch of one instantiation
 
+// upair: the pass pair shared by every pass of every job (r1 | r2 << 4), or 0; FP32 transforms in
+// shared memory whose passes are all (4, 3) run the kernel specialised for that pair
+constexpr int kUniformPair43 = 4 | (3 << 4);
 template <class T, class TI, class TO>
 int launch_t(const BlueJob* djobs, int njobs, int maxN, int mode, int sign, int epi, const InstDesc* insts,
-             cudaStream_t st, void* ob, const void* ab, int threads) {
+             cudaStream_t st, void* ob, const void* ab, int threads, int upair) {
     // 0 (or any size the kernel cannot take): the largest CTA
     const int tmax = blue_max_threads<T>(mode);
     if (threads < 64 || threads > tmax || threads % 32) threads = tmax;
@@ -743,6 +759,13 @@ int launch_t(const BlueJob* djobs, int njobs, int maxN, int mode, int sign, int 
         if (bytes > blue_smem_limit() || (mode == 2 && maxN % 2)) {
             set_error("Bluestein length %d does not fit the shared-memory mode %d", maxN, mode);
             return SFFT_EINVAL;
+        }
+        if constexpr (std::is_same<T, float>::value) {
+            if (mode == 1 && upair == kUniformPair43) {
+                SFFT_TRY(allow_smem((const void*)k_bluestein<T, TI, TO, 1, kUniformPair43>, (int)blue_smem_limit()));
+                k_bluestein<T, TI, TO, 1, kUniformPair43><<<njobs, threads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
+                return launch_check("k_bluestein");
+            }
         }
         if (mode == 1) SFFT_TRY(allow_smem((const void*)k_bluestein<T, TI, TO, 1>, (int)blue_smem_limit()));
         else SFFT_TRY(allow_smem((const void*)k_bluestein_pair<T, TI, TO>, (int)blue_smem_limit()));

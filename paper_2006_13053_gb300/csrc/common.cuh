@@ -203,9 +203,12 @@ struct LatStats {
 // in shared memory (1: N <= maxN complex values fit one CTA), or split over a two-CTA cluster
 // (2: every N even, N/2 values fit one CTA).
 struct InstDesc;
+// upair: r1 | r2 << 4 when every pass of every job is the fused pair (r1, r2) (uniform_pair), else 0.
 int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, int mode, int prec, int in_prec, int out_prec, int sign,
                      int epi, const InstDesc* insts, cudaStream_t st, void* out_base = nullptr,
-                     const void* aux_base = nullptr, int threads = 0);
+                     const void* aux_base = nullptr, int threads = 0, int upair = 0);
+// the pass pair shared by every pass of the jobs (r1 | r2 << 4), or 0
+int uniform_pair(const BlueJob* jobs, size_t n);
 size_t blue_smem_limit();
 // Shared-memory work buffers of 8-byte complex values are padded against bank conflicts of the
 // strided passes: element e lives at e + (e >> 5).  (16-byte values: measured slower padded, the
@@ -217,11 +220,11 @@ inline size_t blue_smem_bytes(int64_t n, size_t esz) {
 }
 // per-type launchers behind launch_bluestein (one translation unit each)
 int launch_bluestein_f64(const BlueJob* djobs, int njobs, int maxN, int mode, int sign, int epi, const InstDesc* insts,
-                         cudaStream_t st, void* ob, const void* ab, int threads);
+                         cudaStream_t st, void* ob, const void* ab, int threads, int upair);
 int launch_bluestein_f32(bool in_double, const BlueJob* djobs, int njobs, int maxN, int mode, int sign, int epi,
-                         const InstDesc* insts, cudaStream_t st, void* ob, const void* ab, int threads);
+                         const InstDesc* insts, cudaStream_t st, void* ob, const void* ab, int threads, int upair);
 int launch_bluestein_df64(const BlueJob* djobs, int njobs, int maxN, int mode, int sign, int epi, const InstDesc* insts,
-                          cudaStream_t st, void* ob, const void* ab, int threads);
+                          cudaStream_t st, void* ob, const void* ab, int threads, int upair);
 // stage pairs that the transform kernels implement as one fused pass (run_pass lists the same)
 constexpr bool pass_fusable(int r1, int r2) {
     return (r1 == 4 && (r2 == 4 || r2 == 3 || r2 == 2)) || (r1 == 3 && (r2 == 3 || r2 == 5)) ||

@@ -191,11 +191,13 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
             BlueJob* dj = nullptr;
             SFFT_TRY(upload_jobs(jf[md], &dj, &B->allocs));
             A.fwd.push_back(FftLaunch{dj, (int)jf[md].size(), maxN[md][0], md});
+            A.fwd.back().upair = uniform_pair(jf[md].data(), jf[md].size());
         }
         if (!js[md].empty()) {
             BlueJob* dj = nullptr;
             SFFT_TRY(upload_jobs(js[md], &dj, &B->allocs));
             B->samp.push_back(FftLaunch{dj, (int)js[md].size(), maxN[md][1], md});
+            B->samp.back().upair = uniform_pair(js[md].data(), js[md].size());
         }
     }
     // hash launches: contiguous runs of single-group plans with equal d and kernel variant share a
@@ -363,7 +365,7 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
     if (mx > 0) SFFT_TRY(launch_scatter_terms(B->d_inst, n, mx, st));
     for (const auto& f : B->samp)
         SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.mode, B->prec, B->prec, B->prec, +1, EPI_ADDNOISE, B->d_inst,
-                                  st));
+                                  st, nullptr, nullptr, f.threads, f.upair));
     SFFT_CU(cudaEventRecord(B->done, st));
     return SFFT_OK;
 }
@@ -430,9 +432,9 @@ int sfft_batch_autotune(sfft_batch* b, const void* const* samples, int64_t* cons
             B->args.hash = keep;
         }
     }
-    // lattice transforms: 256 to 864 threads per CTA (sizes above a transform type's largest CTA
+    // lattice transforms: 256 to 576 threads per CTA (sizes above a transform type's largest CTA
     // run at that largest)
-    const int ths[5] = {256, 384, 512, 576, 864};
+    const int ths[4] = {256, 384, 512, 576};
     best = 1e30;
     int bestt = 0;
     for (int th : ths) {

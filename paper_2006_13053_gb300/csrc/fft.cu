@@ -202,18 +202,28 @@ void tables_release(FftTables* t) {
 
 size_t blue_smem_limit() { return 207 * 1024; }
 
+int uniform_pair(const BlueJob* jobs, size_t n) {
+    int up = -1;
+    for (size_t j = 0; j < n; ++j)
+        for (int p = 0; p < jobs[j].npass; ++p) {
+            if (up < 0) up = jobs[j].pass_r[p];
+            else if (up != jobs[j].pass_r[p]) return 0;
+        }
+    return up < 0 ? 0 : up;
+}
+
 int launch_bluestein(const BlueJob* djobs, int njobs, int maxN, int mode, int prec, int in_prec, int out_prec, int sign,
-                     int epi, const InstDesc* insts, cudaStream_t st, void* ob, const void* ab, int threads) {
+                     int epi, const InstDesc* insts, cudaStream_t st, void* ob, const void* ab, int threads, int upair) {
     // prec: 0 double, 1 float, 2 double-float; in/out: 0 double, 1 float
     if (prec == 2) {  // double-float: float samples in, float high words out (low words to aux)
         if (in_prec != 1 || out_prec != 1) { set_error("double-float transforms take and give float"); return SFFT_EINVAL; }
-        return launch_bluestein_df64(djobs, njobs, maxN, mode, sign, epi, insts, st, ob, ab, threads);
+        return launch_bluestein_df64(djobs, njobs, maxN, mode, sign, epi, insts, st, ob, ab, threads, upair);
     }
     // the element-type combinations the library uses: FP64 everything; FP32 with FP32 or FP64 input
     if (prec == 0 && in_prec == 0 && out_prec == 0)
-        return launch_bluestein_f64(djobs, njobs, maxN, mode, sign, epi, insts, st, ob, ab, threads);
+        return launch_bluestein_f64(djobs, njobs, maxN, mode, sign, epi, insts, st, ob, ab, threads, upair);
     if (prec == 1 && out_prec == 1)
-        return launch_bluestein_f32(in_prec == 0, djobs, njobs, maxN, mode, sign, epi, insts, st, ob, ab, threads);
+        return launch_bluestein_f32(in_prec == 0, djobs, njobs, maxN, mode, sign, epi, insts, st, ob, ab, threads, upair);
     set_error("unsupported transform precision combination (%d, %d, %d)", prec, in_prec, out_prec);
     return SFFT_EINVAL;
 }

@@ -397,13 +397,14 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __r
                 cnt[c] += (bits[bit >> 5] >> (bit & 31)) & 1u;
                 if (dhashes && idx[c] < n) dhashes[idx[c] * L + l0 + l] = (int32_t)r;
             }
-            // count rule decided for the whole warp (tested every fourth lattice once fewer than
-            // `need` remain: before that nobody can have missed more than L - need)
+            // count rule decided for the whole warp: every candidate has reached `need` or cannot
+            // reach it (tested every fourth lattice once fewer than `need` remain: before that
+            // nobody can have missed more than L - need)
             const int rem = L - 1 - (l0 + l);
             if (!dhashes && !dcounts && rem < need && (rem & 3) == 0) {
                 bool alive = false;
 #pragma unroll
-                for (int c = 0; c < kCPT; ++c) alive |= cnt[c] + rem >= need;
+                for (int c = 0; c < kCPT; ++c) alive |= cnt[c] < need && cnt[c] + rem >= need;
                 if (!__any_sync(0xffffffffu, alive)) break;
             }
         }
@@ -439,21 +440,16 @@ template <int D> struct Pack {
     static constexpr int REC = 4 + ((ZW + 3) / 4) * 4; // words per lattice record (multiple of 4)
 };
 
-template <int D, bool DIAG>
-__global__ void __launch_bounds__(kHashThreads, 4) k_hash_count_packed(const InstDesc* __restrict__ insts, int l0,
-                                                                     int l1in, int mode) {
-    extern __shared__ __align__(16) uint32_t hsm[];
+// Shared-memory prologue of the packed kernels for the lattice group [l0, l1): the group's bitmap
+// words and one record per lattice.  Record words: {M, mu, off, bit offset}, then the packed z
+// words, z_t in the symmetric range |z_t| <= (M - 1) / 2 (k.z = k.(z - M) mod M: signed int16 for
+// every prime M < 65536), one record word per thread.
+template <int D>
+__device__ __forceinline__ void packed_prologue(const InstDesc& I, int l0, int l1, uint32_t* rec, uint32_t* bits) {
     using PK = Pack<D>;
-    const InstDesc& I = insts[blockIdx.y];
-    // lattice group [l0, l1): its bitmap words [w0, w1) go to shared memory
-    const int L = I.L, l1 = l1in < 0 ? L : l1in, Lg = l1 - l0;
-    const int w0 = I.boff[l0], w1 = l1 < L ? I.boff[l1] : I.nwords, nwords = w1 - w0;
-    uint32_t* rec = hsm;                       // [Lg][REC]
-    uint32_t* bits = hsm + Lg * PK::REC;       // [nwords]
-    copy_words_to_smem(bits, I.nzbits + w0, nwords);
-    // one record word per thread: {M, mu, off, bit offset} and the packed z words, z_t in the
-    // symmetric range |z_t| <= (M - 1) / 2 (k.z = k.(z - M) mod M): signed int16 for every prime
-    // M < 65536
+    const int L = I.L, Lg = l1 - l0;
+    const int w0 = I.boff[l0], w1 = l1 < L ? I.boff[l1] : I.nwords;
+    copy_words_to_smem(bits, I.nzbits + w0, w1 - w0);
     for (int j = threadIdx.x; j < Lg * PK::REC; j += blockDim.x) {
         const int g = j / PK::REC, w = j - g * PK::REC, l = l0 + g;
         const int Ml = I.Ml[l];
@@ -476,6 +472,38 @@ __global__ void __launch_bounds__(kHashThreads, 4) k_hash_count_packed(const Ins
         }
         rec[j] = v;
     }
+}
+
+// One lattice's contribution to a candidate's count: bit (off + k.z mod M) of the lattice's bitmap.
+// The offset seeds the dot product (32-bit wrap-around equals the unsigned sum); bytes of k at
+// positions >= d meet zero z halves.
+template <int D>
+__device__ __forceinline__ uint32_t packed_hash(const uint32_t* kw, const uint32_t* zw, uint32_t M, uint32_t mu,
+                                                uint32_t off) {
+    using PK = Pack<D>;
+    int x = (int)off;
+#pragma unroll
+    for (int w = 0; w < PK::ZW; ++w) {
+        if (w & 1) x = __dp2a_hi((int)zw[w], (int)kw[w >> 1], x);
+        else x = __dp2a_lo((int)zw[w], (int)kw[w >> 1], x);
+    }
+    const uint32_t xp = (uint32_t)x;
+    const uint32_t q = __umulhi(xp, mu);
+    uint32_t rr = xp - q * M;
+    return min(rr, rr - M);  // one conditional subtraction: rr - M wraps above rr when rr < M
+}
+
+template <int D, bool DIAG>
+__global__ void __launch_bounds__(kHashThreads, 4) k_hash_count_packed(const InstDesc* __restrict__ insts, int l0,
+                                                                     int l1in, int mode) {
+    extern __shared__ __align__(16) uint32_t hsm[];
+    using PK = Pack<D>;
+    const InstDesc& I = insts[blockIdx.y];
+    // lattice group [l0, l1): its bitmap words go to shared memory
+    const int L = I.L, l1 = l1in < 0 ? L : l1in, Lg = l1 - l0;
+    uint32_t* rec = hsm;                       // [Lg][REC]
+    uint32_t* bits = hsm + Lg * PK::REC;       // [nwords]
+    packed_prologue<D>(I, l0, l1, rec, bits);
     __syncthreads();
     const int64_t n = I.n;
     const int need = I.need;
@@ -579,28 +607,19 @@ __global__ void __launch_bounds__(kHashThreads, 4) k_hash_count_packed(const Ins
             const uint32_t* lbits = bits + (cst.w >> 5);  // the lattice's bitmap (segments start on words)
 #pragma unroll
             for (int c = 0; c < kCPT2; ++c) {
-                // the offset seeds the dot product (32-bit wrap-around equals the unsigned sum)
-                int x = (int)off;
-#pragma unroll
-                for (int w = 0; w < PK::ZW; ++w) {
-                    if (w & 1) x = __dp2a_hi((int)zw[w], (int)kw[c][w >> 1], x);
-                    else x = __dp2a_lo((int)zw[w], (int)kw[c][w >> 1], x);
-                }
-                const uint32_t xp = (uint32_t)x;
-                const uint32_t q = __umulhi(xp, mu);
-                uint32_t rr = xp - q * M;
-                rr = min(rr, rr - M);  // one conditional subtraction: rr - M wraps above rr when rr < M
+                const uint32_t rr = packed_hash<D>(kw[c], zw, M, mu, off);
                 cnt[c] += __funnelshift_r(lbits[rr >> 5], 0u, rr) & 1u;  // bit rr & 31 of word rr >> 5
                 if constexpr (DIAG) {
                     if (idx[c] < n && I.dhashes) I.dhashes[idx[c] * L + l0 + l] = (int32_t)rr;
                 }
             }
         };
-        // count rule (Algorithm 1): once no candidate of the warp can still reach `need` with the
-        // lattices left, the rest cannot change a decision (exact counts are only reported by the
-        // DIAG variant).  While rem >= need lattices remain, no candidate can have missed more than
-        // L - need of them, so the warp test starts below that and then runs every kHashCheckEvery
-        // lattices (every lattice measured 1.7 % faster than every second, every third 0.2 % slower).
+        // count rule (Algorithm 1): once every candidate of the warp is decided -- it has reached
+        // `need`, or cannot reach it with the lattices left -- the rest cannot change a decision
+        // (exact counts are only reported by the DIAG variant).  While rem >= need lattices
+        // remain, no candidate can have missed more than L - need of them, so the warp test starts
+        // below that and then runs every kHashCheckEvery lattices (every lattice measured 1.7 %
+        // faster than every second, every third 0.2 % slower).
         for (int l = 0; l < Lg; ++l) {
             lattice(l);
             if constexpr (!DIAG) {
@@ -608,7 +627,7 @@ __global__ void __launch_bounds__(kHashThreads, 4) k_hash_count_packed(const Ins
                 if (rem < need && rem % kHashCheckEvery == 0) {
                     bool alive = false;
 #pragma unroll
-                    for (int c = 0; c < kCPT2; ++c) alive |= cnt[c] + rem >= need;
+                    for (int c = 0; c < kCPT2; ++c) alive |= cnt[c] < need && cnt[c] + rem >= need;
                     if (!__any_sync(0xffffffffu, alive)) break;
                 }
             }

@@ -13,6 +13,7 @@ struct FftLaunch {
     int njobs = 0, maxN = 0;
     int mode = 1;  // work buffer: 0 global scratch, 1 shared memory, 2 two-CTA cluster
     int threads = 0;  // CTA size (0: the transform's largest; autotuned)
+    int upair = 0;    // the pass pair of every pass of every job, or 0 (uniform_pair)
 };
 // one launch of the hash-count kernel over a contiguous range of instances of equal d
 struct HashGroup {

@@ -34,7 +34,8 @@ def test_executed_hash_evals_replay_matches_kernel_loop():
     """The replay of the hash kernel's early exit equals a plain loop over its warps: each warp of a
     T*4-candidate tile (T threads per CTA) holds candidates base + 32 w + lane + T c (c < 4) and stops
     after a tested lattice l (rem = L - 1 - l below the threshold and a multiple of the test
-    interval) once no candidate's count plus the rem lattices left reaches the threshold."""
+    interval) once every candidate is decided: its count has reached the threshold, or its count
+    plus the rem lattices left falls short of it."""
     import numpy as np
     import torch
     import bench
@@ -54,7 +55,7 @@ def test_executed_hash_evals_replay_matches_kernel_loop():
                     cnt += np.array([nz[i, l] if i < n else 0 for i in idx])
                     rem = L - 1 - l
                     tested = rem < need and rem % bench.HASH_CHECK_EVERY == 0
-                    if tested and not np.any(cnt + rem >= need):
+                    if tested and not np.any((cnt < need) & (cnt + rem >= need)):
                         visited = l + 1
                         break
                 expect += 128 * visited

@@ -121,6 +121,29 @@ def test_lattice_dft_parity(G, prec, Ms):
             assert np.linalg.norm(a - ref) / np.linalg.norm(ref) < 2e-6
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_lattice_dft_tiny_lattices(G, prec):
+    """Bluestein lengths with one pass (M = 5: N = 9 = 3 x 3; M = 7: N = 15 = 3 x 5: the fused middle
+    pass alone) and two passes (M = 11: N = 24; M = 13: N = 25; M = 17: N = 36), in one plan."""
+    import torch
+    Ms = [5, 7, 11, 13, 17]
+    L = len(Ms)
+    cand = S.uniform_distinct(9, 2, -1, 1, 1)
+    z = np.stack([S.generators(1, 2, m, 20 + i)[0] for i, m in enumerate(Ms)])
+    rng = np.random.default_rng(7 + prec)
+    y = rng.standard_normal(sum(Ms)) + 1j * rng.standard_normal(sum(Ms))
+    if prec == 1:
+        y = y.astype(np.complex64).astype(np.complex128)
+    plan = G.Plan(T(cand), 2, L=L, M=Ms, z=z, precision=prec, tau_abs=1e300)
+    _, _, info = plan.reconstruct(T(y, torch.complex64 if prec else torch.complex128), diag=True)
+    got = info["ghat"].cpu().numpy()
+    for l, (a, b) in enumerate(zip(O.split_lattices(got, Ms), O.split_lattices(y, Ms))):
+        ref = O.lattice_dft(b, Ms[l])
+        rms = np.sqrt(np.mean(np.abs(b) ** 2))
+        tol = 1e-13 * rms if prec == 0 else 32 * 2.0 ** -24 * math.log2(bluestein_N(Ms[l])) * rms
+        assert np.max(np.abs(a - ref)) <= tol, Ms[l]
+
+
 # ------------------------------------------------------------------ hashes / counts / detection
 @pytest.mark.parametrize("which", ["cfg1", "cfg2"])
 def test_hashes_counts_detected_bit_exact(G, which):
