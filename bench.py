@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--instances", type=int, default=NINST)
+    ap.add_argument("--streams", type=int, default=2,
+                    help="batch objects (own plans and buffers, same instances) alternating on their own "
+                         "streams, so that one step's tail kernels overlap the next step's sampler")
     ap.add_argument("--no-extras", action="store_true", help="skip the FP64-path, graph, e2e and CPU legs")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the library's default launch shapes instead of autotuning them in setup")
@@ -453,9 +456,9 @@ def run_native(a, rank, world):
 
     dft = G.DFT_FP32 if a.dft == "fp32" else G.DFT_DF64
 
-    def make_plans(rows, prec=G.FP32, refine=1, d=D, dft=dft):
+    def make_plans(rows, prec=G.FP32, refine=1, d=D, dft=dft, stream=st):
         return [G.Plan(r, S_SPARSE, d=d if r.dtype == torch.int8 else None, precision=prec, refine=refine,
-                       dft=dft, tau_abs=6 * h[3] / math.sqrt(10331), tau_rel=0.0, seed=s_, stream=st)
+                       dft=dft, tau_abs=6 * h[3] / math.sqrt(10331), tau_rel=0.0, seed=s_, stream=stream)
                 for r, h, s_ in zip(rows, host, seeds)]
 
     with torch.cuda.stream(st):
@@ -469,49 +472,88 @@ def run_native(a, rank, world):
         smp = [torch.empty(p.n_samples, dtype=torch.complex64, device=dev) for p in plans]
         batch = G.Batch(plans, use_graph=False, stream=st)
     L, M = plans[0].L, int(plans[0].M[0])
+    # further batch objects for the pipelined timed region: the same instances (the candidate rows
+    # and sampler inputs are shared, read only), their own plans, buffers and stream
+    nsets = max(1, a.streams)
+    sets = [(st, batch, smp, plans)]
+    for _ in range(1, nsets):
+        st_k = torch.cuda.Stream(dev)
+        with torch.cuda.stream(st_k):
+            plans_k = make_plans(cand8, stream=st_k)
+            smp_k = [torch.empty(p.n_samples, dtype=torch.complex64, device=dev) for p in plans_k]
+            batch_k = G.Batch(plans_k, use_graph=False, stream=st_k)
+        sets.append((st_k, batch_k, smp_k, plans_k))
 
-    def step():
-        with torch.cuda.stream(st):
-            batch.sample_sparse_poly(kv, cf, nz, outs=smp)
-            batch.reconstruct_async(smp)
+    def step(k=0):
+        st_k, batch_k, smp_k, _ = sets[k % nsets]
+        with torch.cuda.stream(st_k):
+            batch_k.sample_sparse_poly(kv, cf, nz, outs=smp_k)
+            batch_k.reconstruct_async(smp_k)
 
     def barrier():
         if world > 1:
             torch.distributed.barrier()
 
-    for _ in range(a.warmup):
-        step()
-    st.synchronize()
+    for k in range(nsets):
+        for _ in range(a.warmup):
+            step(k)
+        sets[k][0].synchronize()
     # launch shapes: hash grid waves and transform CTA size picked by the library's autotuner on
-    # the warm-up samples (setup, outside the timed region)
-    with torch.cuda.stream(st):
-        tuned = (None, None) if a.no_autotune else batch.autotune(smp, reps=2)
-        step()
-    st.synchronize()
+    # the warm-up samples (setup, outside the timed region), for every batch object
+    for k in range(nsets - 1, -1, -1):
+        st_k, batch_k, smp_k, _ = sets[k]
+        with torch.cuda.stream(st_k):
+            tuned = (None, None) if a.no_autotune else batch_k.autotune(smp_k, reps=2)
+            step(k)
+        st_k.synchronize()
     # correctness gate on the last warm-up step: every instance returns <= s frequencies
     res = batch.results()
     assert all(0 < len(s_) <= S_SPARSE + 64 for s_, _ in res), [len(s_) for s_, _ in res]
     # ---- timed region (no per-stage events: their collection synchronises the host)
     batch.timing(0)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
+    def timed(nk, k_steps):
+        """Device time of k_steps steps alternating over the first nk batch objects (CUDA events on
+        stream 0, which first releases and finally joins the other streams)."""
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0.record(st)
+        for k in range(1, nk):
+            sets[k][0].wait_event(t0)
+        for k in range(k_steps):
+            step(k % nk)
+        for k in range(1, nk):
+            ev = torch.cuda.Event()
+            ev.record(sets[k][0])
+            st.wait_event(ev)
+        t1.record(st)
+        return t0, t1
+
     with ClockSampler(dev.index) as clk:
-        e0.record(st)
-        for _ in range(a.steps):
-            step()
-        e1.record(st)
+        e0, e1 = timed(nsets, a.steps)
         e1.synchronize()
         # a short timed region can end between two 100 ms samples: keep the same steps running
         # (untimed) until three samples have been taken since the region started
         extra, t_end = 0, time.time() + 3.0
         while clk.proc is not None and clk.samples_since_start() < 3 and time.time() < t_end:
-            step()
-            st.synchronize()
+            step(extra)
+            sets[extra % nsets][0].synchronize()
             extra += 1
     torch.cuda.synchronize()
     barrier()
     ms = e0.elapsed_time(e1) / a.steps
+    # the same steps on one stream (no overlap between consecutive steps), for comparison
+    torch.cuda.synchronize()
+    f0, f1 = timed(1, a.steps)
+    f1.synchronize()
+    ms_single = f0.elapsed_time(f1) / a.steps
+    for st_k, batch_k, _, plans_k in sets[1:]:  # only the timed region uses the further batch objects
+        st_k.synchronize()
+        batch_k.close()
+        for p_ in plans_k:
+            p_.close()
+    del sets[1:]
+    n_streams, nsets = nsets, 1
     clk_window = "timed region" if extra == 0 else f"timed region + {extra} more identical steps (untimed)"
     # per-stage CUDA-event times, from a second run of the same steps with the stage timer on
     batch.timing(1)
@@ -547,6 +589,12 @@ def run_native(a, rank, world):
                       "parallelism": f"replicas x{world}",
                       "autotuned": {"hash_waves": tuned[0], "fft_threads": tuned[1]}},
            "cand_lattice_evals_per_s": world * n_inst * NCAND * L / (ms / 1000.0),
+           "streams": n_streams,
+           "pipelining": (f"{n_streams} batch objects (their own plans and buffers, the same instances and "
+                          "read-only inputs) alternate over their own streams, so that a step's tail "
+                          "kernels (combine, refinement, select) overlap the next step's sampler"
+                          if n_streams > 1 else "one stream"),
+           "single_stream_ms_per_step": ms_single,
            "stage_ms_per_step": stage_ms,
            "gpu_launches": sum(batch.launch_count()) * a.steps,
            "clocks": clk.summary(clk_window)}
