@@ -144,6 +144,35 @@ def test_lattice_dft_tiny_lattices(G, prec):
         assert np.max(np.abs(a - ref)) <= tol, Ms[l]
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_zero_test_guard_band_retest(G, prec):
+    """Remark 2.3's guard band with an absolute threshold: tau is set a hair above the exact modulus
+    of a non-zero bucket, so that the working-precision value cannot decide it.  The bucket must be
+    re-tested by the direct sum (n_guard >= 1), stored as that sum (FP64-class value), and judged
+    zero; the detected set and coefficients must be the oracle's with the same threshold."""
+    import torch
+    cand, sup, c, z, M, L = cfg1(3)
+    y = O.sample_sparse_poly(cand[sup], c, z, M)
+    if prec:
+        y = y.astype(np.complex64).astype(np.complex128)
+    g0 = O.lattice_dft(y[:M], M)
+    order = np.argsort(-np.abs(g0))
+    h0 = int(order[len(sup) // 2])  # a mid-size non-zero bucket of lattice 0
+    assert np.abs(g0[h0]) > 1e-3
+    # inside the band kappa u log2(N) rms (FP32 ~4e-4, FP64 ~8e-13 here), far outside the direct
+    # sum's error
+    tau = float(np.abs(g0[h0])) * (1 + (1e-9 if prec else 1e-13))
+    ref = O.reconstruct(cand, y, z, M, tau_abs=tau)
+    plan = G.Plan(T(cand), 20, L=L, M=[M] * L, z=z, precision=prec, tau_abs=tau, tau_rel=0.0)
+    supp, coef, info = plan.reconstruct(T(y, torch.complex64 if prec else torch.complex128), diag=True)
+    assert info["n_guard"] >= 1
+    got = info["ghat"].cpu().numpy()[h0]
+    assert abs(got - g0[h0]) <= (2.0 ** -23 if prec else 1e-14) * abs(g0[h0])
+    assert np.array_equal(supp.cpu().numpy(), ref.supp)
+    assert relmax(coef.cpu().numpy(), ref.coef) <= (1e-5 if prec else 1e-10)
+    plan.close()
+
+
 # ------------------------------------------------------------------ hashes / counts / detection
 @pytest.mark.parametrize("which", ["cfg1", "cfg2"])
 def test_hashes_counts_detected_bit_exact(G, which):
