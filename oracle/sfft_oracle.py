@@ -20,7 +20,14 @@ Parity status of each function (pins live in tests/test_oracle_*.py):
   detect / alg2 / alg4                                           pinned (Cor 2.6 exact
         recovery, brute-force full-grid DFT, PFP/PFN audit)
   refine                                                         pinned (exact case fixed
-        point; direct residual == bucket identity)
+        point; direct residual == bucket identity; an aliasing false positive driven to 0
+        and its partner to the true value by one step)
+  sample_sparse_poly_aliasing                                    pinned (direct sum at
+        the lattice nodes, eq. 2.3)
+  rank_key, select_top (Algorithm 4, near-tie rule)             pinned (FP64 order kept,
+        rounding to b bits, ties by index)
+  theory_r, theory_gamma_A, theory_gamma, theory_failure_union  pinned (Section 3.3
+        formulas evaluated by hand, union bound)
   hybrid_postprocess, collision_counts                           pinned (brute force)
   least_squares (Remark 2.8)                                     pinned (exact recovery
         with collisions, residual orthogonality, explicit lstsq == normal equations)
@@ -30,8 +37,8 @@ Parity status of each function (pins live in tests/test_oracle_*.py):
   bspline_* (Section 4.3 test function), relative_l2_error,      pinned (FFT of the closed
         hyperbolic_cross                                         form, unit norm, m = 2 hat,
                                                                  quadrature, brute-force set)
-  reconstruct_vjp (adjoint)                                      pinned (FP64 finite
-        differences)
+  reconstruct_vjp, reconstruct_vjp_refined (adjoints)           pinned (FP64 finite
+        differences, with and without the refinement step)
   philox4x64                                                     pinned (numpy Philox)
 """
 from __future__ import annotations
