@@ -428,7 +428,10 @@ __global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __r
 // Per lattice a 16-byte aligned record in shared memory holds {M, mu, off, bit offset} and the
 // packed z words (broadcast loads shared by all threads).  DIAG additionally writes the
 // per-candidate hashes and counts.
-constexpr int kCPT2 = 4;
+#ifndef SFFT_HASH_CPT
+#define SFFT_HASH_CPT 4
+#endif
+constexpr int kCPT2 = SFFT_HASH_CPT;  // candidates per thread of the packed kernel
 #ifndef SFFT_HASH_CHECK_EVERY
 #define SFFT_HASH_CHECK_EVERY 1
 #endif
