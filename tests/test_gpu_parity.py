@@ -563,6 +563,57 @@ def test_batch_matches_single_plans(G, use_graph, dft):
     assert t["hash_count"][1] == 1 and t["hash_count"][0] > 0
 
 
+def test_two_batches_interleaved_on_two_streams(G):
+    """Two batch objects over the same candidate tensors and sampler inputs (the benchmark's timed
+    region), their sampler + reconstruction calls interleaved on two streams without host
+    synchronisation: every call's result equals the oracle's (no shared mutable state between the
+    batch objects)."""
+    import torch
+    specs = [(4, 5000, 25, 21), (6, 7000, 30, 22), (4, 4000, 20, 23)]
+    sts = [torch.cuda.Stream(), torch.cuda.Stream()]
+    mk = []
+    for d, n, s, seed in specs:
+        cand = S.uniform_distinct(n, d, -30, 30, seed)
+        sup = S.support_indices(n, s, seed)
+        c = S.coef_cgauss(s, seed)
+        sig = S.snr_sigma(c, 40.0)
+        mk.append(dict(np_cand=cand, cand=T(cand), s=s, seed=seed, sup=sup, c=c, sig=sig))
+    batches, outs = [], []
+    for st in sts:
+        with torch.cuda.stream(st):
+            plans = [G.Plan(m["cand"], m["s"], precision=1, refine=1, dft=G.DFT_FP32, seed=m["seed"],
+                            tau_abs=6 * m["sig"] / math.sqrt(O.lattice_size(m["np_cand"], m["s"])),
+                            tau_rel=0.0, stream=st) for m in mk]
+            outs.append([torch.empty(p.n_samples, dtype=torch.complex64, device=dev()) for p in plans])
+            batches.append((G.Batch(plans, use_graph=False, stream=st), plans))
+    torch.cuda.synchronize()
+    kvs, cfs, nzs, refs = [], [], [], []
+    for m, p in zip(mk, batches[0][1]):
+        L, M = p.L, int(p.M[0])
+        assert M == O.lattice_size(m["np_cand"], m["s"])  # the plan's tau above used this M
+        z = np.asarray(p.z)
+        nz = S.noise(L * M, m["sig"], m["seed"]).astype(np.complex64)
+        y = O.sample_sparse_poly_aliasing(m["np_cand"][m["sup"]], m["c"], z, M).astype(np.complex64) + nz
+        refs.append(O.reconstruct(m["np_cand"], y.astype(np.complex128), z, M, tau_abs=6 * m["sig"] / math.sqrt(M),
+                                  do_refine=True, refine_mode="bucket"))
+        kvs.append(T(m["np_cand"][m["sup"]]))
+        cfs.append(T(m["c"]))
+        nzs.append(T(nz))
+    for k in range(6):
+        B, _ = batches[k % 2]
+        with torch.cuda.stream(sts[k % 2]):
+            B.sample_sparse_poly(kvs, cfs, nzs, outs=outs[k % 2])
+            B.reconstruct_async(outs[k % 2])
+        if k >= 4:  # the last call of each batch object
+            for (supp, coef), ref in zip(B.results(), refs):
+                assert np.array_equal(supp.cpu().numpy(), ref.supp)
+                assert relmax(coef.cpu().numpy(), ref.coef) <= TOL_FP32_DFT
+    for B, plans in batches:
+        B.close()
+        for p in plans:
+            p.close()
+
+
 def test_batch_launch_count(G):
     """The launches one batch call enqueues: sampler 3 (clear, bucket scatter, inverse transforms);
     reconstruction clear, forward transforms, zero test, one hash launch per run of equal d,
