@@ -39,7 +39,7 @@ WORKLOAD = ("d=10, |Gamma|=2^20 uniform distinct in [-64,64]^10, s=1000 complex-
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--instances", type=int, default=NINST)

@@ -563,8 +563,8 @@ int tc_grid(size_t smem, int64_t tiles, int count) {
 }
 
 int Plan::hash_grid() const {
-    int per_sm = std::max<int>(1, std::min<int>(8, (int)((228 * 1024) / (hash_smem + 1024))));
-    const int64_t tile = hash_tile(packed), tiles = (n + tile - 1) / tile;
+    const int per_sm = hash_ctas_per_sm(hash_smem);
+    const int64_t tile = hash_tile(packed, hash_smem), tiles = (n + tile - 1) / tile;
     return (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)152 * per_sm));
 }
 

@@ -222,13 +222,12 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
         HashGroup h;
         h.off = b;
         h.d = Pb->d;
-        int64_t tiles = 0;
+        int64_t maxn = 0;
         h.tc_ok = true;
         h.tc_tiles = 0;
         while (e < n && B->plans[e]->d == h.d && B->plans[e]->packed == Pb->packed && B->plans[e]->hgroups.size() == 1) {
             h.smem = std::max(h.smem, B->plans[e]->hash_smem);
-            const int64_t tile = hash_tile(Pb->packed);
-            tiles = std::max<int64_t>(tiles, (B->plans[e]->n + tile - 1) / tile);
+            maxn = std::max<int64_t>(maxn, B->plans[e]->n);
             h.tc_ok = h.tc_ok && B->plans[e]->hash_tc;
             h.tc_smem = std::max(h.tc_smem, B->plans[e]->tc_smem);
             h.tc_tiles = std::max<int64_t>(h.tc_tiles, (B->plans[e]->n + 127) / 128);
@@ -237,7 +236,8 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
         h.count = e - b;
         h.variant = Pb->packed ? 1 : 0;
         if (h.tc_ok) h.tc_gx0 = tc_grid(h.tc_smem, h.tc_tiles, h.count);
-        int per_sm = std::max<int>(1, std::min<int>(8, (int)((228 * 1024) / (h.smem + 1024))));
+        const int64_t tile = hash_tile(Pb->packed, h.smem), tiles = (maxn + tile - 1) / tile;
+        const int per_sm = hash_ctas_per_sm(h.smem);
         h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (152 * per_sm + h.count - 1) / h.count));
         h.gx0 = h.gx;
         h.tiles = tiles;

@@ -263,6 +263,7 @@ __global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restr
 // 384-thread CTAs keep 48 warps resident where 256-thread ones keep 32 (measured 0.398 -> 0.363 ms
 // for 16 instances of 2^20 candidates; 512 threads: 0.367 ms, limited by registers to 3 CTAs)
 constexpr int kHashThreads = 384;
+constexpr int kHashThreadsBig = 768;  // CTAs whose bitmap leaves room for at most two per SM
 constexpr int kCPT = 2;  // candidates per thread
 
 // Row r of int8 candidate rows of stride ld bytes as KW int8x4 words: directly when ld is a multiple
@@ -302,8 +303,8 @@ __device__ __forceinline__ void load_row8(const uint32_t* __restrict__ w8, const
     for (int w = 0; w < KW; ++w) kw[w] = __funnelshift_r(wv[w], wv[w + 1], sh);
 }
 
-template <int D>
-__global__ void __launch_bounds__(kHashThreads) k_hash_count(const InstDesc* __restrict__ insts, int l0, int l1in,
+template <int D, int NT = kHashThreads>
+__global__ void __launch_bounds__(NT) k_hash_count(const InstDesc* __restrict__ insts, int l0, int l1in,
                                                               int mode) {
     extern __shared__ __align__(16) uint32_t hsm[];
     const InstDesc& I = insts[blockIdx.y];
@@ -496,9 +497,9 @@ __device__ __forceinline__ uint32_t packed_hash(const uint32_t* kw, const uint32
     return min(rr, rr - M);  // one conditional subtraction: rr - M wraps above rr when rr < M
 }
 
-template <int D, bool DIAG>
-__global__ void __launch_bounds__(kHashThreads, 4) k_hash_count_packed(const InstDesc* __restrict__ insts, int l0,
-                                                                     int l1in, int mode) {
+template <int D, bool DIAG, int NT = kHashThreads>
+__global__ void __launch_bounds__(NT, NT == kHashThreads ? 4 : 2) k_hash_count_packed(const InstDesc* __restrict__ insts,
+                                                                                      int l0, int l1in, int mode) {
     extern __shared__ __align__(16) uint32_t hsm[];
     using PK = Pack<D>;
     const InstDesc& I = insts[blockIdx.y];
@@ -1545,13 +1546,25 @@ int launch_clear(InstDesc* di, int ninst, int clear_det, int clear_coll, int cle
 template <int D>
 static int launch_hash_d(const InstDesc* di, int ninst, int gx, size_t smem, int variant, int l0, int l1, int mode,
                          cudaStream_t st) {
-    // variant: 0 int32 kernel, 1 packed kernel, 2 packed kernel with diagnostics (3: hash_tc.cu)
+    // variant: 0 int32 kernel, 1 packed kernel, 2 packed kernel with diagnostics (3: hash_tc.cu);
+    // the CTA size follows the bitmap's shared memory (hash_threads)
+    const int nt = variant == 2 ? kHashThreads : hash_threads(variant == 1, smem);
     if (variant == 0) {
-        SFFT_TRY(allow_smem((const void*)k_hash_count<D>, 220 * 1024));
-        k_hash_count<D><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di, l0, l1, mode);
+        if (nt == kHashThreadsBig) {
+            SFFT_TRY(allow_smem((const void*)k_hash_count<D, kHashThreadsBig>, 220 * 1024));
+            k_hash_count<D, kHashThreadsBig><<<dim3(gx, ninst), nt, smem, st>>>(di, l0, l1, mode);
+        } else {
+            SFFT_TRY(allow_smem((const void*)k_hash_count<D>, 220 * 1024));
+            k_hash_count<D><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di, l0, l1, mode);
+        }
     } else if (variant == 1) {
-        SFFT_TRY(allow_smem((const void*)k_hash_count_packed<D, false>, 220 * 1024));
-        k_hash_count_packed<D, false><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di, l0, l1, mode);
+        if (nt == kHashThreadsBig) {
+            SFFT_TRY(allow_smem((const void*)k_hash_count_packed<D, false, kHashThreadsBig>, 220 * 1024));
+            k_hash_count_packed<D, false, kHashThreadsBig><<<dim3(gx, ninst), nt, smem, st>>>(di, l0, l1, mode);
+        } else {
+            SFFT_TRY(allow_smem((const void*)k_hash_count_packed<D, false>, 220 * 1024));
+            k_hash_count_packed<D, false><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di, l0, l1, mode);
+        }
     } else {
         SFFT_TRY(allow_smem((const void*)k_hash_count_packed<D, true>, 220 * 1024));
         k_hash_count_packed<D, true><<<dim3(gx, ninst), kHashThreads, smem, st>>>(di, l0, l1, mode);
@@ -1559,7 +1572,17 @@ static int launch_hash_d(const InstDesc* di, int ninst, int gx, size_t smem, int
     return launch_check("k_hash_count");
 }
 
-int64_t hash_tile(bool packed) { return (int64_t)kHashThreads * (packed ? kCPT2 : kCPT); }
+int hash_ctas_per_sm(size_t smem) { return std::max<int>(1, std::min<int>(8, (int)((228 * 1024) / (smem + 1024)))); }
+
+// CTA size of the hash kernels for a bitmap segment of smem bytes: 384 threads while 3 or more CTAs
+// share an SM; 768 when the bitmap leaves room for one CTA (both kernels) or two (the packed
+// kernel, 40 registers), so that an SM keeps 24 or 48 warps instead of 12 or 24
+int hash_threads(bool packed, size_t smem) {
+    const int per_sm = hash_ctas_per_sm(smem);
+    return per_sm == 1 || (packed && per_sm == 2) ? kHashThreadsBig : kHashThreads;
+}
+
+int64_t hash_tile(bool packed, size_t smem) { return (int64_t)hash_threads(packed, smem) * (packed ? kCPT2 : kCPT); }
 
 size_t hash_smem_bytes(int d, int L, int64_t nwords, bool packed) {
     if (!packed) return sizeof(uint32_t) * (size_t)nwords + sizeof(int32_t) * (size_t)L * (d + 4);

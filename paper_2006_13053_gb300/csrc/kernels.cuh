@@ -9,7 +9,11 @@ namespace sfft {
 int launch_hash_count(const InstDesc* di, int ninst, int d, int gx, size_t smem, int variant, int l0, int l1, int mode,
                       cudaStream_t st);
 size_t hash_smem_bytes(int d, int L, int64_t nwords, bool packed);
-int64_t hash_tile(bool packed);  // candidates one CTA covers per pass of its grid-stride loop
+// candidates one CTA covers per pass of its grid-stride loop, CTA size and CTAs per SM of the hash
+// kernels for a bitmap segment of smem bytes
+int64_t hash_tile(bool packed, size_t smem);
+int hash_threads(bool packed, size_t smem);
+int hash_ctas_per_sm(size_t smem);
 int launch_zero_test(const LatDesc* dl, int nlat, InstDesc* di, int prec, double kappa_u, cudaStream_t st);
 int launch_compact(InstDesc* di, int ninst, cudaStream_t st);
 int launch_det_hashes(const InstDesc* di, int ninst, int64_t maxdet, cudaStream_t st);
