@@ -499,12 +499,17 @@ def run_native(a, rank, world):
             step(k)
         sets[k][0].synchronize()
     # launch shapes: hash grid waves and transform CTA size picked by the library's autotuner on
-    # the warm-up samples (setup, outside the timed region), for every batch object
-    for k in range(nsets - 1, -1, -1):
-        st_k, batch_k, smp_k, _ = sets[k]
-        with torch.cuda.stream(st_k):
-            tuned = (None, None) if a.no_autotune else batch_k.autotune(smp_k, reps=2)
-            step(k)
+    # the warm-up samples (setup, outside the timed region) for the first batch object; the others
+    # take the same shapes, so that every step runs the same launches (tuned separately, they could
+    # land on different shapes)
+    with torch.cuda.stream(st):
+        tuned = (None, None) if a.no_autotune else batch.autotune(smp, reps=2)
+    st.synchronize()
+    for k in range(nsets):
+        st_k, batch_k, _, _ = sets[k]
+        if k > 0 and not a.no_autotune:
+            batch_k.set_shapes(*tuned)
+        step(k)
         st_k.synchronize()
     # correctness gate on the last warm-up step: every instance returns <= s frequencies
     res = batch.results()

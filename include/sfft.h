@@ -303,7 +303,7 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
 /*
  * Autotuner: runs sfft_batch_reconstruct on the given buffers (reps timed runs per candidate
  * after one warm-up) for hash-kernel grids of 1/2, 1, 2 and 4 waves of resident CTAs and for
- * lattice transforms of 256, 384, 448 or 512 threads per CTA, and the tensor-core hash kernel
+ * lattice transforms of 256, 384, 512 or 576 threads per CTA, and the tensor-core hash kernel
  * (1, 2, 4 waves; plans with one lattice group, d <= 16, L <= 64, |k.z| < 2^24) against the
  * packed one, times the affected stage with CUDA events, keeps the fastest shapes for later
  * calls (a captured graph is re-captured) and reports them (hash_waves, negative when the
@@ -311,6 +311,18 @@ int sfft_batch_reconstruct(sfft_batch* b, const void* const* samples, int64_t* c
  */
 int sfft_batch_autotune(sfft_batch* b, const void* const* samples, int64_t* const* supp_out, double* const* coef_out,
                         const int64_t* cap, int reps, double* hash_waves, int* fft_threads);
+
+/*
+ * Applies launch shapes that sfft_batch_autotune reported (for another batch of the same plans'
+ * shapes, e.g. a second batch object alternating with the first on another stream, so that both
+ * run the same shapes without tuning twice): hash_waves > 0 sets every packed / int32 hash grid to
+ * that many waves of resident CTAs; hash_waves < 0 selects the tensor-core hash kernel with
+ * |hash_waves| waves for the launches that qualify (as sfft_batch_select_hash); fft_threads sets
+ * the forward transforms' CTA size (0: the largest).  Errors: SFFT_EINVAL for hash_waves = 0 or
+ * |hash_waves| > 64, or for hash_waves > 0 once the tensor-core kernel is selected.  A captured
+ * graph is re-captured at the next call.  Host only.
+ */
+int sfft_batch_set_shapes(sfft_batch* b, double hash_waves, int fft_threads);
 
 /*
  * Use the tensor-core hash kernel (tcgen05: the inner products k.z_l of a 128-candidate tile and

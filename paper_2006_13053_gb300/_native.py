@@ -106,6 +106,7 @@ sfft_batch_reconstruct = _sig("sfft_batch_reconstruct", _i32, [_vp, _vp, _vp, _v
 sfft_batch_sample_sparse_poly = _sig("sfft_batch_sample_sparse_poly", _i32, [_vp, _vp, _vp, _vp, _vp, _vp])
 sfft_batch_autotune = _sig("sfft_batch_autotune", _i32, [_vp, _vp, _vp, _vp, _vp, _i32, _P(_dbl), _P(_i32)])
 sfft_batch_select_hash = _sig("sfft_batch_select_hash", _i32, [_vp, _i32])
+sfft_batch_set_shapes = _sig("sfft_batch_set_shapes", _i32, [_vp, _dbl, _i32])
 sfft_batch_launch_count = _sig("sfft_batch_launch_count", _i32, [_vp, _P(_i32), _P(_i32)])
 sfft_batch_flags = _sig("sfft_batch_flags", _i32, [_vp, _vp])
 sfft_batch_timing = _sig("sfft_batch_timing", _i32, [_vp, _i32, _vp, _vp])

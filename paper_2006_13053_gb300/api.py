@@ -331,6 +331,11 @@ class Batch:
                                       C.byref(ft)))
         return hw.value, ft.value
 
+    def set_shapes(self, hash_waves, fft_threads):
+        """Apply launch shapes that autotune() returned (e.g. for a second batch of the same plans'
+        shapes); see sfft_batch_set_shapes in the C header."""
+        N.check(N.sfft_batch_set_shapes(self.handle, float(hash_waves), int(fft_threads)))
+
     def select_hash(self, tensor=True):
         """Use the tensor-core hash kernel for the launches that qualify (see the C header)."""
         N.check(N.sfft_batch_select_hash(self.handle, 1 if tensor else 0))

@@ -454,6 +454,30 @@ int sfft_batch_autotune(sfft_batch* b, const void* const* samples, int64_t* cons
     return SFFT_OK;
 }
 
+int sfft_batch_set_shapes(sfft_batch* b, double hash_waves, int fft_threads) {
+    if (!b) { set_error("batch is NULL"); return SFFT_EINVAL; }
+    Batch* B = reinterpret_cast<Batch*>(b);
+    SFFT_CHECK(hash_waves != 0.0 && fabs(hash_waves) <= 64.0, SFFT_EINVAL, "hash_waves must be non-zero with |hash_waves| <= 64");
+    if (hash_waves > 0) {
+        for (const auto& h : B->args.hash)
+            SFFT_CHECK(h.variant != 3, SFFT_EINVAL, "the tensor-core hash kernel is selected: positive waves need a new batch");
+        for (auto& h : B->args.hash)
+            h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(std::max<int64_t>(h.tiles, 1), (int64_t)llround(h.gx0 * hash_waves)));
+    } else {
+        for (auto& h : B->args.hash)
+            if (h.tc_ok) {
+                h.variant = 3;
+                h.smem = h.tc_smem;
+                h.gx = (int)std::max<int64_t>(1, std::min<int64_t>(h.tc_tiles, (int64_t)llround(h.tc_gx0 * -hash_waves)));
+            }
+    }
+    for (auto& f : B->args.fwd) f.threads = fft_threads;
+    // a captured graph holds the old launch shapes
+    if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+    if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+    return SFFT_OK;
+}
+
 int sfft_batch_select_hash(sfft_batch* b, int tensor) {
     if (!b) { set_error("batch is NULL"); return SFFT_EINVAL; }
     Batch* B = reinterpret_cast<Batch*>(b);

@@ -614,6 +614,44 @@ def test_two_batches_interleaved_on_two_streams(G):
             p.close()
 
 
+def test_batch_set_shapes_from_autotune(G):
+    """Shapes that one batch's autotuner picked, applied to a second batch over the same plans'
+    shapes, give the same results (and the oracle's); invalid shapes are refused."""
+    import torch
+    specs = [(4, 6000, 25, 31), (6, 5000, 30, 32)]
+    plans = [[], []]
+    samples, refs = [], []
+    for d, n, s, seed in specs:
+        cand = S.uniform_distinct(n, d, -30, 30, seed)
+        L = O.L_cor26(n, 0.1)
+        M = O.lattice_size(cand, s)
+        z = S.generators(L, d, M, seed)
+        sup = S.support_indices(n, s, seed)
+        c = S.coef_cgauss(s, seed)
+        sig = S.snr_sigma(c, 40.0)
+        y = (O.sample_sparse_poly(cand[sup], c, z, M) + S.noise(L * M, sig, seed)).astype(np.complex64)
+        tau = 6 * sig / math.sqrt(M)
+        refs.append(O.reconstruct(cand, y.astype(np.complex128), z, M, tau_abs=tau, do_refine=True, refine_mode="bucket"))
+        for k in range(2):
+            plans[k].append(G.Plan(T(cand), s, L=L, M=[M] * L, z=z, precision=1, refine=1, tau_abs=tau, tau_rel=0.0,
+                                   dft=G.DFT_FP32))
+        samples.append(T(y))
+    A = G.Batch(plans[0])
+    tuned = A.autotune(samples, reps=1)
+    B = G.Batch(plans[1])
+    with pytest.raises(G.SfftError):
+        B.set_shapes(0.0, 0)
+    B.set_shapes(*tuned)
+    for Bk in (A, B):
+        for (supp, coef), ref in zip(Bk.reconstruct(samples), refs):
+            assert np.array_equal(supp.cpu().numpy(), ref.supp)
+            assert relmax(coef.cpu().numpy(), ref.coef) <= TOL_FP32_DFT
+    for Bk in (A, B):
+        Bk.close()
+    for p in plans[0] + plans[1]:
+        p.close()
+
+
 def test_batch_launch_count(G):
     """The launches one batch call enqueues: sampler 3 (clear, bucket scatter, inverse transforms);
     reconstruction clear, forward transforms, zero test, one hash launch per run of equal d,
