@@ -280,6 +280,9 @@ int sfft_sample_bspline(const sfft_plan* plan, const int32_t* dims, const int32_
                         void* samples_out);
 
 /* ---------------------------------------------------------------- batched reconstruction */
+/* The batch calls have no counterpart in the paper: they run the per-plan path of sfft_reconstruct
+ * (Algorithm 2, the optional refinement, Algorithm 4) and sfft_sample_sparse_poly (eq. 2.3) for
+ * many plans in shared launches, and control and measure those launches. */
 typedef struct sfft_batch sfft_batch;
 
 /*
@@ -454,6 +457,8 @@ int sfft_detect_noalloc(int d, const int32_t* cand, int64_t n_cand, int L, const
                         int64_t* n_detected, void* stream);
 
 /* ---------------------------------------------------------------- host utilities */
+/* (the generators' counter-based random numbers and Corollary 2.6 / eq. 4.2 lattice rules of the
+ * plan, exposed for checks on the host) */
 /* Word 0 of Philox4x64-10 (Salmon et al., SC'11) for counter (c0..c3) and key (key0, 0). */
 uint64_t sfft_philox4x64_word0(uint64_t key0, uint64_t c0, uint64_t c1, uint64_t c2, uint64_t c3);
 
