@@ -257,7 +257,7 @@ struct TwRow<R1, R2, float, TwTwo> {
 // passes (BlueIo's phases and mid_pass).
 template <int R1, int R2, int S, class T, class TW, class C>
 __device__ __forceinline__ void dif_pass(C& c, int Ns, const TW& tw) {
-    const int N = c.N, m1 = Ns / R1, m2 = m1 / R2, s1 = N / Ns, ng = N / (R1 * R2);
+    const int N = c.N, m1 = Ns / R1, m2 = m1 / R2, s1 = N / Ns * c.tws, ng = N / (R1 * R2);
     const float rm = 1.0f / (float)m2;
     // a cluster of two CTAs splits the groups at a block boundary (see BlueIo)
     const int g0 = c.rank * (ng >> 1), g1 = (c.nrank == 1 || c.rank == 1) ? ng : (ng >> 1);
@@ -300,7 +300,7 @@ __device__ __forceinline__ void dif_pass(C& c, int Ns, const TW& tw) {
 // exact adjoint of dif_pass: conjugate twiddles and inverse butterflies in reverse order
 template <int R1, int R2, class T, class TW, class C>
 __device__ __forceinline__ void dit_pass(C& c, int Ns, const TW& tw) {
-    const int N = c.N, m1 = Ns / R1, m2 = m1 / R2, s1 = N / Ns, ng = N / (R1 * R2);
+    const int N = c.N, m1 = Ns / R1, m2 = m1 / R2, s1 = N / Ns * c.tws, ng = N / (R1 * R2);
     const float rm = 1.0f / (float)m2;
     const int g0 = c.rank * (ng >> 1), g1 = (c.nrank == 1 || c.rank == 1) ? ng : (ng >> 1);
     for (int i = g0 + threadIdx.x; i < g1; i += blockDim.x) {
@@ -482,6 +482,7 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
     cplx<T>* rbuf;       // CL: the other CTA's half (distributed shared memory)
     int hN = 0, rank = 0, nrank = 1;
     int N, M, epi;
+    int tws = 1;  // twiddle stride factor: the table is for tws N (a block of a longer transform)
     bool inv;
     const cplx<TI>* in;
     const cplx<T>* chirp;
@@ -590,6 +591,57 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
     }
 };
 
+// EPI_ANALYZE: the CTA's (cluster's) sum |x|^2 and max |X|^2 to the lattice's statistics
+template <class T, class TI, class TO, bool SMB, bool CL>
+__device__ __forceinline__ void analyze_epilogue(const BlueJob& J, BlueIo<T, TI, TO, SMB, CL>& c, int epi, int rank,
+                                                 double* red, double* xchg) {
+    if (epi == EPI_ANALYZE) {
+        using R = typename BlueIo<T, TI, TO, SMB, CL>::R;
+        R ssr = c.ss, mxr = c.mx2;
+        block_reduce_sum_max(ssr, mxr, reinterpret_cast<R*>(red));
+        double ssd = (double)ssr, mx2 = (double)mxr;
+        if constexpr (CL) {  // partials of both CTAs to rank 0
+            auto cl = cooperative_groups::this_cluster();
+            double* x0 = cl.map_shared_rank(xchg, 0);
+            if (threadIdx.x == 0) { x0[2 * rank] = ssd; x0[2 * rank + 1] = mx2; }
+            cl.sync();
+            if (rank != 0) return;
+            ssd = xchg[0] + xchg[2];
+            mx2 = fmax(xchg[1], xchg[3]);
+        }
+        if (threadIdx.x == 0) {
+            const double mx = sqrt(mx2);
+            LatStats& S = *J.stat;
+            S.max32 = (float)mx;
+            S.max_abs = mx;
+            S.rms = sqrt(ssd / (double)J.M);
+        }
+    }
+}
+
+// Copy of a block of n elements between the global-scratch buffer g and the padded shared-memory
+// buffer of cb (to shared memory if IN), kIoUnroll elements per thread in flight.
+template <bool IN, class C, class T>
+__device__ __forceinline__ void stage_block(C& cb, cplx<T>* g, int n) {
+    constexpr int U = 8;
+    for (int e0 = threadIdx.x; e0 < n; e0 += U * blockDim.x) {
+        cplx<T> v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e < n) v[u] = IN ? g[e] : *cb.at(e);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * (int)blockDim.x;
+            if (e < n) {
+                if (IN) *cb.at(e) = v[u];
+                else g[e] = v[u];
+            }
+        }
+    }
+}
+
 // CL: the transform of one lattice is split over a cluster of two CTAs, each holding half of the
 // work buffer in its shared memory.  Only the first DIF pass and the last DIT pass (sub-transform
 // size N) touch the other half; every later pass works on blocks of size N / (first pass radix
@@ -601,7 +653,7 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
 template <class T, class TI, class TO, bool SMB, bool CL, int UP, class TW>
 __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, cplx<T>* rbuf, int rank, const TW& tw,
                                                int sign, int epi, const void* inp, const void* auxp, void* outp,
-                                               double* red, double* xchg) {
+                                               double* red, double* xchg, cplx<T>* smem) {
     BlueIo<T, TI, TO, SMB, CL> c;
     c.buf = buf;
     c.rbuf = rbuf;
@@ -634,9 +686,56 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
     c.load_input(h0, h1);
     // the first pass reads both halves: both CTAs' inputs must be in place
     sync(true);
+    const int np = J.npass;
+    if constexpr (!SMB && !CL) {
+        // global-scratch buffer: only the first DIF pass and the last DIT pass need the whole
+        // buffer; every pass between them works inside the blocks of N / R0 elements that the first
+        // pass leaves (R0 = its radix product), so each block is staged in shared memory for them
+        const int R0 = (J.pass_r[0] & 15) * (J.pass_r[0] >> 4), Nb = J.N / R0;
+        unsigned dyn;
+        asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+        constexpr int PS = blue_pad_shift(sizeof(cplx<T>));
+        const size_t need = (size_t)(Nb + (PS ? (Nb >> PS) + 1 : 0)) * sizeof(cplx<T>);
+        if (np >= 2 && smem && need <= dyn) {
+            run_pass_u<UP, T>(0, J.pass_r[0] & 15, J.pass_r[0] >> 4, c, J.N, tw);
+            __syncthreads();
+            BlueIo<T, TI, TO, true, false> cb;
+            cb.buf = smem;
+            cb.N = Nb;
+            cb.M = J.M;
+            cb.tws = R0;
+            for (int b = 0; b < R0; ++b) {
+                cb.filt = c.filt + (size_t)b * Nb;
+                cplx<T>* gb = c.buf + (size_t)b * Nb;
+                stage_block<true>(cb, gb, Nb);
+                __syncthreads();
+                int Ns = Nb;
+                for (int p = 1; p < np - 1; ++p) {
+                    const int r1 = J.pass_r[p] & 15, r2 = J.pass_r[p] >> 4;
+                    run_pass_u<UP, T>(0, r1, r2, cb, Ns, tw);
+                    Ns /= r1 * r2;
+                    __syncthreads();
+                }
+                run_pass_u<UP, T>(2, J.pass_r[np - 1] & 15, J.pass_r[np - 1] >> 4, cb, Ns, tw);
+                __syncthreads();
+                for (int p = np - 2; p >= 1; --p) {
+                    const int r1 = J.pass_r[p] & 15, r2 = J.pass_r[p] >> 4;
+                    Ns *= r1 * r2;
+                    run_pass_u<UP, T>(1, r1, r2, cb, Ns, tw);
+                    __syncthreads();
+                }
+                stage_block<false>(cb, gb, Nb);
+                __syncthreads();
+            }
+            run_pass_u<UP, T>(1, J.pass_r[0] & 15, J.pass_r[0] >> 4, c, J.N, tw);
+            __syncthreads();
+            c.store_output(h0, min(h1, J.M));
+            analyze_epilogue<T, TI, TO, SMB, CL>(J, c, epi, rank, red, xchg);
+            return;
+        }
+    }
     // ---- DIF passes, the fused middle pass (last DIF pass, filter, first DIT pass), DIT passes
     // in reverse order (the last writes into both halves)
-    const int np = J.npass;
     for (int p = 0, Ns = J.N; p < np - 1; ++p) {
         const int r1 = J.pass_r[p] & 15, r2 = J.pass_r[p] >> 4;
         run_pass_u<UP, T>(0, r1, r2, c, Ns, tw);
@@ -655,28 +754,7 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
     }
     // ---- output phase over this CTA's elements below M
     c.store_output(h0, min(h1, J.M));
-    if (epi == EPI_ANALYZE) {
-        using R = typename BlueIo<T, TI, TO, SMB, CL>::R;
-        R ssr = c.ss, mxr = c.mx2;
-        block_reduce_sum_max(ssr, mxr, reinterpret_cast<R*>(red));
-        double ssd = (double)ssr, mx2 = (double)mxr;
-        if constexpr (CL) {  // partials of both CTAs to rank 0
-            auto cl = cooperative_groups::this_cluster();
-            double* x0 = cl.map_shared_rank(xchg, 0);
-            if (threadIdx.x == 0) { x0[2 * rank] = ssd; x0[2 * rank + 1] = mx2; }
-            cl.sync();
-            if (rank != 0) return;
-            ssd = xchg[0] + xchg[2];
-            mx2 = fmax(xchg[1], xchg[3]);
-        }
-        if (threadIdx.x == 0) {
-            const double mx = sqrt(mx2);
-            LatStats& S = *J.stat;
-            S.max32 = (float)mx;
-            S.max_abs = mx;
-            S.rms = sqrt(ssd / (double)J.M);
-        }
-    }
+    analyze_epilogue<T, TI, TO, SMB, CL>(J, c, epi, rank, red, xchg);
 }
 
 // One CTA (MODE 0, 1) or a cluster of two CTAs (MODE 2) = one Bluestein transform.  T:
@@ -694,6 +772,8 @@ __device__ __forceinline__ void bluestein_cta(const BlueJob* __restrict__ jobs, 
     cplx<T>* buf = MODE ? reinterpret_cast<cplx<T>*>(smem_raw) : reinterpret_cast<cplx<T>*>(J.scratch);
     cplx<T>* rbuf = nullptr;
     if constexpr (MODE == 2) rbuf = cooperative_groups::this_cluster().map_shared_rank(buf, rank ^ 1);
+    // MODE 0: the dynamic shared memory stages the blocks between the first and the last pass
+    cplx<T>* stage = MODE == 0 ? reinterpret_cast<cplx<T>*>(smem_raw) : nullptr;
     const void* inp = J.in;
     const void* auxp = J.aux;
     void* outp = J.out;
@@ -720,10 +800,10 @@ __device__ __forceinline__ void bluestein_cta(const BlueJob* __restrict__ jobs, 
         for (int i = threadIdx.x; i < 256; i += blockDim.x) s_twb[i] = gb[i];
         __syncthreads();
         bluestein_body<T, TI, TO, MODE != 0, MODE == 2, UP>(J, buf, rbuf, rank, TwTwo{s_twa, s_twb}, sign, epi, inp, auxp, outp,
-                                             red, xchg);
+                                             red, xchg, stage);
     } else {
         bluestein_body<T, TI, TO, MODE != 0, MODE == 2, UP>(J, buf, rbuf, rank, TwFull<T>{reinterpret_cast<const cplx<T>*>(J.tw)},
-                                             sign, epi, inp, auxp, outp, red, xchg);
+                                             sign, epi, inp, auxp, outp, red, xchg, stage);
     }
 }
 
@@ -772,7 +852,11 @@ int launch_t(const BlueJob* djobs, int njobs, int maxN, int mode, int sign, int 
         if (mode == 1) k_bluestein<T, TI, TO, 1><<<njobs, threads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
         else k_bluestein_pair<T, TI, TO><<<2 * njobs, threads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
     } else {
-        k_bluestein<T, TI, TO, 0><<<njobs, threads, 0, st>>>(djobs, sign, epi, insts, ob, ab);
+        // the global-scratch mode stages the blocks of its middle passes in shared memory (the
+        // kernel falls back to global passes when a block does not fit)
+        const size_t bytes = blue_smem_limit();
+        SFFT_TRY(allow_smem((const void*)k_bluestein<T, TI, TO, 0>, (int)bytes));
+        k_bluestein<T, TI, TO, 0><<<njobs, threads, bytes, st>>>(djobs, sign, epi, insts, ob, ab);
     }
     return launch_check("k_bluestein");
 }
