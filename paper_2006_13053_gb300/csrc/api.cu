@@ -219,7 +219,9 @@ int Plan::build_jobs() {
         BlueJob sj = make_blue_job(t, prec, 1, 1.0);
         // FP32 plans scatter FP32 buckets into the first half of C (see k_scatter_terms)
         sj.in = prec ? (const void*)(reinterpret_cast<c32*>(C) + o) : (const void*)(C + o);
-        sj.io_flags = 16 | 32; sj.io_off = o; sj.inst = 0;
+        sj.io_flags = 16 | 32; sj.io_off = o; sj.inst = 0; sj.lat = l;
+        // a transform in one CTA's shared memory sums its buckets there (no global bucket pass)
+        if (buf_mode(prec) == 1) sj.io_flags |= 64;
         sj.scratch = buf_mode(prec) ? nullptr : (char*)scratch + (size_t)l * maxN * sizeof(c64);
         jobs_samp.push_back(sj);
     }
@@ -900,9 +902,12 @@ int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const do
     I.samp_out = samples_out;
     I.samp_noise = noise;
     SFFT_TRY(P->io_upload());
-    // buckets in the plan precision (eq. 2.3), inverse lattice DFTs, noise
-    SFFT_TRY(launch_clear(P->d_inst, 1, 0, 0, P->prec ? 2 : 1, st));
-    if (n_terms > 0) SFFT_TRY(launch_scatter_terms(P->d_inst, 1, n_terms * P->L, st));
+    // buckets in the plan precision (eq. 2.3), inverse lattice DFTs, noise; transforms in shared
+    // memory sum their own buckets
+    if (P->buf_mode(P->prec) != 1) {
+        SFFT_TRY(launch_clear(P->d_inst, 1, 0, 0, P->prec ? 2 : 1, st));
+        if (n_terms > 0) SFFT_TRY(launch_scatter_terms(P->d_inst, 1, n_terms * P->L, st));
+    }
     SFFT_TRY(launch_bluestein(P->d_jobs_samp, P->L, P->maxN, P->buf_mode(P->prec), P->prec, P->prec, P->prec, +1,
                               EPI_ADDNOISE, P->d_inst, st, nullptr, nullptr, 0,
                               uniform_pair(P->jobs_samp.data(), P->jobs_samp.size())));

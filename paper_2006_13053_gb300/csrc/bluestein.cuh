@@ -541,6 +541,33 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
             }
         }
     }
+    // Input of the sparse-polynomial sampler (eq. 2.3) built in place: the bucket sums
+    // sum_{q : k_q.z_l = h mod M} c_q of lattice l (terms of instance I, coefficients rounded to the
+    // transform precision, summed by shared-memory atomics), zero on [M, N), then the chirp product
+    // on [0, M).  Only for a buffer in this CTA's shared memory.
+    __device__ __forceinline__ void scatter_terms(const InstDesc& I, int l) {
+        for (int e = threadIdx.x; e < N; e += blockDim.x) *at(e) = cplx<T>{kc<T>(0.0), kc<T>(0.0)};
+        __syncthreads();
+        const int d = I.d;
+        const int64_t Ml = M;
+        const int32_t* __restrict__ kv = I.samp_kvec;
+        const int32_t* __restrict__ zl = I.z + (int64_t)l * d;
+        for (int64_t q = threadIdx.x; q < I.samp_nterms; q += blockDim.x) {
+            int64_t x = 0;
+            for (int t = 0; t < d; ++t) x += (int64_t)kv[q * d + t] * zl[t];
+            int64_t r = x % Ml;
+            if (r < 0) r += Ml;
+            const cplx<T> v = ccv<T>(I.samp_coef[q]);
+            cplx<T>* p = at((int)r);
+            atomicAdd(&p->x, v.x);
+            atomicAdd(&p->y, v.y);
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < M; e += blockDim.x) {
+            const cplx<T> x = *at(e), w = ldg(&chirp[e]);
+            *at(e) = inv ? mulc(x, w) : x * w;
+        }
+    }
     // outputs j in [e0, e1), e1 <= M: chirp product, scale and the epilogue (the noise of
     // EPI_ADDNOISE is complex float for float transforms, complex double otherwise)
     using NZ = typename std::conditional<std::is_same<T, float>::value, c32, c64>::type;
@@ -653,7 +680,7 @@ __device__ __forceinline__ void stage_block(C& cb, cplx<T>* g, int n) {
 template <class T, class TI, class TO, bool SMB, bool CL, int UP, class TW>
 __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, cplx<T>* rbuf, int rank, const TW& tw,
                                                int sign, int epi, const void* inp, const void* auxp, void* outp,
-                                               double* red, double* xchg, cplx<T>* smem) {
+                                               double* red, double* xchg, cplx<T>* smem, const InstDesc* insts) {
     BlueIo<T, TI, TO, SMB, CL> c;
     c.buf = buf;
     c.rbuf = rbuf;
@@ -683,7 +710,14 @@ __device__ __forceinline__ void bluestein_body(const BlueJob& J, cplx<T>* buf, c
     };
     // ---- input phase (this CTA's half of the buffer when split over a cluster)
     const int h0 = CL ? rank * (J.N >> 1) : 0, h1 = CL ? h0 + (J.N >> 1) : J.N;
-    c.load_input(h0, h1);
+    bool built = false;
+    if constexpr (SMB && !CL && (std::is_same<T, float>::value || std::is_same<T, double>::value)) {
+        if (J.io_flags & 64) {
+            c.scatter_terms(insts[J.inst], J.lat);
+            built = true;
+        }
+    }
+    if (!built) c.load_input(h0, h1);
     // the first pass reads both halves: both CTAs' inputs must be in place
     sync(true);
     const int np = J.npass;
@@ -800,10 +834,10 @@ __device__ __forceinline__ void bluestein_cta(const BlueJob* __restrict__ jobs, 
         for (int i = threadIdx.x; i < 256; i += blockDim.x) s_twb[i] = gb[i];
         __syncthreads();
         bluestein_body<T, TI, TO, MODE != 0, MODE == 2, UP>(J, buf, rbuf, rank, TwTwo{s_twa, s_twb}, sign, epi, inp, auxp, outp,
-                                             red, xchg, stage);
+                                             red, xchg, stage, insts);
     } else {
         bluestein_body<T, TI, TO, MODE != 0, MODE == 2, UP>(J, buf, rbuf, rank, TwFull<T>{reinterpret_cast<const cplx<T>*>(J.tw)},
-                                             sign, epi, inp, auxp, outp, red, xchg, stage);
+                                             sign, epi, inp, auxp, outp, red, xchg, stage, insts);
     }
 }
 

@@ -171,8 +171,11 @@ struct BlueJob {
     int M, N, nstages, tw_na;
     // io_flags: bit 0 in = samples of instance `inst` + io_off; bit 1 aux = those samples;
     //           bit 2 out = out_base (launch argument) + io_off; bit 3 aux = aux_base + io_off;
-    //           bit 4 out = samp_out of instance `inst` + io_off; bit 5 aux = its samp_noise + io_off
-    int inst, io_flags;
+    //           bit 4 out = samp_out of instance `inst` + io_off; bit 5 aux = its samp_noise + io_off;
+    //           bit 6 input = the sparse-polynomial terms of instance `inst` (samp_kvec, samp_coef),
+    //           summed into the buckets of lattice `lat` in the CTA's shared-memory buffer (buffer
+    //           mode 1 only; `in` is then unused)
+    int inst, io_flags, lat;
     int64_t io_off;
     uint8_t radix[kMaxStages];  // stage radices in DIF order
     // passes over the work buffer: one stage or two consecutive stages fused in registers;

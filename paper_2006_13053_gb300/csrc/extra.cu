@@ -44,6 +44,7 @@ struct Batch {
     std::vector<void*> allocs;
     PipeArgs args;
     std::vector<FftLaunch> samp;  // sparse-polynomial sampler transforms of every plan
+    bool samp_scatter = false;    // some sampler transform needs the global bucket pass (not in shared memory)
     int64_t max_samp_terms_L = 0;
     int64_t* d_counts = nullptr;
     int* d_order = nullptr;     // batch index -> caller's plan index (device copy of order)
@@ -170,6 +171,7 @@ static int batch_create(Batch* B, sfft_plan* const* plans, int n, int use_graph,
             lats.push_back(LatDesc{b, l, (int)P->M[l], (int)P->tabs[l]->N, P->soff[l], P->boff[l], 0,
                                    (const double*)P->tabs[l]->dft64, P->tabs[l]->dftdf});
         const int sf = P->buf_mode(P->fwd_prec()), sp = P->buf_mode(P->prec);
+        B->samp_scatter |= sp != 1;
         for (int l = 0; l < P->L; ++l) {
             BlueJob f = P->jobs_fwd[l], s = P->jobs_samp[l];
             f.inst = b; s.inst = b;
@@ -361,8 +363,10 @@ int sfft_batch_sample_sparse_poly(sfft_batch* b, const int32_t* const* kvec, con
     }
     cudaStream_t st = B->st;
     SFFT_TRY(B->stage_upload());
-    SFFT_TRY(launch_clear(B->d_inst, n, 0, 0, B->prec ? 2 : 1, st));
-    if (mx > 0) SFFT_TRY(launch_scatter_terms(B->d_inst, n, mx, st));
+    if (B->samp_scatter) {  // transforms in shared memory sum their own buckets
+        SFFT_TRY(launch_clear(B->d_inst, n, 0, 0, B->prec ? 2 : 1, st));
+        if (mx > 0) SFFT_TRY(launch_scatter_terms(B->d_inst, n, mx, st));
+    }
     for (const auto& f : B->samp)
         SFFT_TRY(launch_bluestein(f.jobs, f.njobs, f.maxN, f.mode, B->prec, B->prec, B->prec, +1, EPI_ADDNOISE, B->d_inst,
                                   st, nullptr, nullptr, f.threads, f.upair));
@@ -510,7 +514,8 @@ int sfft_batch_launch_count(sfft_batch* b, int* reconstruct, int* sampler) {
     if (A.lsq) n += 4;
     if (A.refine) n += 3;
     if (reconstruct) *reconstruct = n;
-    if (sampler) *sampler = 2 + (int)B->samp.size();  // clear, bucket scatter, inverse transforms
+    // clear and bucket scatter (only for transforms outside shared memory), inverse transforms
+    if (sampler) *sampler = (B->samp_scatter ? 2 : 0) + (int)B->samp.size();
     return SFFT_OK;
 }
 

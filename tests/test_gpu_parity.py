@@ -653,20 +653,20 @@ def test_batch_set_shapes_from_autotune(G):
 
 
 def test_batch_launch_count(G):
-    """The launches one batch call enqueues: sampler 3 (clear, bucket scatter, inverse transforms);
-    reconstruction clear, forward transforms, zero test, one hash launch per run of equal d,
-    compaction, combine, select, counts, plus 3 for the refinement (as in the benchmark's launch
-    list: 14 per step)."""
+    """The launches one batch call enqueues: sampler 1 (the inverse transforms, which sum their
+    buckets in shared memory); reconstruction clear, forward transforms, zero test, one hash launch
+    per run of equal d, compaction, combine, select, counts, plus 3 for the refinement (as in the
+    benchmark's launch list: 12 per step)."""
     import torch
     plans = []
     for i, d in enumerate((10, 10, 12)):
         cand = S.uniform_distinct(4000, d, -20, 20, i)
         plans.append(G.Plan(T(cand), 40, precision=1, refine=1, tau_rel=1e-5, seed=i))
     B = G.Batch(plans[:2])
-    assert B.launch_count() == (11, 3)
+    assert B.launch_count() == (11, 1)
     B.close()
     B = G.Batch(plans)
-    assert B.launch_count() == (12, 3)  # d = 10 and d = 12: two hash launches
+    assert B.launch_count() == (12, 1)  # d = 10 and d = 12: two hash launches
     B.close()
     for p in plans:
         p.close()
@@ -691,6 +691,47 @@ def test_batch_sampler_matches_plan_sampler(G):
         ref = p.sample_sparse_poly(k, c, z)
         torch.cuda.synchronize()
         assert torch.equal(o, ref)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_batch_sampler_buffer_modes_match_oracle(G, prec):
+    """The sparse-polynomial sampler (eq. 2.3) in every work-buffer mode against the oracle's
+    aliasing formula: s = 40 (M = 419, transform in one CTA's shared memory, which sums the buckets
+    itself), s = 2000 (M = 20663: two-CTA cluster in FP32, global scratch in FP64) and s = 6000
+    (M = 61981, global scratch).  A batch with transforms outside shared memory adds the global
+    clear and bucket pass (2 launches) before its inverse-transform launches (one per mode)."""
+    import torch
+    specs = [(40, 21), (2000, 22), (6000, 23)]
+    plans, kv, cf, refs, norms = [], [], [], [], []
+    for s, seed in specs:
+        d, n = 4, 2 * s
+        cand = S.uniform_distinct(n, d, -20, 20, seed)
+        sup = S.support_indices(n, s, seed)
+        c = S.coef_cgauss(s, seed)
+        plan = G.Plan(T(cand), s, precision=prec, seed=seed)
+        M = int(plan.M[0])
+        assert M == O.next_prime_above(10.33 * s)
+        refs.append(O.sample_sparse_poly_aliasing(cand[sup], c, np.asarray(plan.z), M))
+        norms.append(np.sqrt(np.sum(np.abs(c) ** 2)))
+        plans.append(plan)
+        kv.append(T(cand[sup]))
+        cf.append(T(c))
+    B = G.Batch(plans)
+    assert B.launch_count()[1] == 2 + (3 if prec == 1 else 2)
+    outs = B.sample_sparse_poly(kv, cf)
+    torch.cuda.synchronize()
+    tol = 1e-12 if prec == 0 else 3e-6
+    for o, ref, nc in zip(outs, refs, norms):
+        assert np.max(np.abs(o.cpu().numpy() - ref)) <= tol * nc * 10
+    B.close()
+    one = G.Batch(plans[:1])  # shared memory only: no global bucket pass
+    assert one.launch_count()[1] == 1
+    o1 = one.sample_sparse_poly(kv[:1], cf[:1])[0]
+    torch.cuda.synchronize()
+    assert np.max(np.abs(o1.cpu().numpy() - refs[0])) <= tol * norms[0] * 10
+    one.close()
+    for p in plans:
+        p.close()
 
 
 @pytest.mark.parametrize("prec,refine", [(0, 1), (1, 1)])
