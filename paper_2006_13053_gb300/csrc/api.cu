@@ -498,6 +498,12 @@ static int mark(const PipeArgs& a, int stage, cudaStream_t st) {
 
 int run_pipeline(const PipeArgs& a, cudaStream_t st) {
     const int ni = a.ninst;
+    // FP32 transforms: float buckets C for the refinement (their rounding is far below the
+    // transform's error); the second half of a sharded reconstruction gets FP64 buckets
+    const bool f32 = a.prec == 1 && a.fwd_prec == 1 && a.phase == 0;
+    // a whole reconstruction with refinement zeroes C at the buckets of Itilde in the combine (the
+    // least-squares combine uses C as scratch in between, so it keeps the full clear)
+    const int zc = a.refine && a.phase == 0 && !a.lsq ? (f32 ? 2 : 1) : 0;
     if (a.timer)
         for (int i = 0; i <= ST_COUNT; ++i) a.timer->recorded[i] = false;
     if (a.phase != 2) {
@@ -526,7 +532,7 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
         if (a.hybrid) SFFT_TRY(launch_det_hashes(a.d_inst, ni, a.maxcap, st));
         SFFT_TRY(mark(a, ST_COMBINE, st));
         if (a.hybrid) SFFT_TRY(launch_collisions(a.d_inst, ni, st));
-        SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, a.hybrid ? 0 : 3, st));
+        SFFT_TRY(launch_combine(a.d_inst, ni, a.maxcap, a.prec, a.hybrid ? 0 : 3, st, zc));
         if (a.lsq) {  // Remark 2.8 least squares on the detected set, from the medians
             SFFT_TRY(mark(a, ST_LSQ, st));
             SFFT_TRY(launch_lsq(a.d_inst, ni, a.prec, st));
@@ -539,12 +545,9 @@ int run_pipeline(const PipeArgs& a, cudaStream_t st) {
         }
     }
     if (a.refine) {
-        // FP32 transforms: float buckets C (their rounding is far below the transform's error);
-        // the second half of a sharded reconstruction gets FP64 buckets
-        const bool f32 = a.prec == 1 && a.fwd_prec == 1 && a.phase == 0;
         if (a.phase == 0) {
             SFFT_TRY(mark(a, ST_SCATTER, st));
-            SFFT_TRY(launch_clear(a.d_inst, ni, 0, 0, f32 ? 2 : 1, st));
+            if (!zc) SFFT_TRY(launch_clear(a.d_inst, ni, 0, 0, f32 ? 2 : 1, st));
             SFFT_TRY(launch_scatter_coef(a.d_inst, ni, f32, st));
         }
         // residual spectrum r_hat = ghat - C at the buckets of Itilde (eq. 2.3), median update

@@ -508,11 +508,12 @@ int sfft_batch_launch_count(sfft_batch* b, int* reconstruct, int* sampler) {
     const PipeArgs& A = B->args;
     // run_pipeline: clear, forward transforms, zero test, hash groups, compaction, combine, select;
     // the hybrid combine adds the hashes of Itilde and the collision counts, least squares four
-    // launches, the refinement a clear, the scatter and the update; the batch adds the counts
+    // launches, the refinement the scatter and the update (and a clear of its buckets after least
+    // squares, which uses them as scratch; otherwise the combine zeroes them); the batch adds the counts
     int n = 1 + (int)A.fwd.size() + 1 + (int)A.hash.size() + 1 + 1 + 1 + 1;
     if (A.hybrid) n += 2;
     if (A.lsq) n += 4;
-    if (A.refine) n += 3;
+    if (A.refine) n += A.lsq ? 3 : 2;
     if (reconstruct) *reconstruct = n;
     // clear and bucket scatter (only for transforms outside shared memory), inverse transforms
     if (sampler) *sampler = (B->samp_scatter ? 2 : 0) + (int)B->samp.size();

@@ -808,6 +808,11 @@ template <class T> __device__ __forceinline__ T pick(T a, T b, int l) {
     return l < 32 ? x : y;
 }
 
+__device__ __forceinline__ void zero_bucket(const InstDesc& I, int64_t b, int zc) {
+    if (zc == 1) I.C[b] = c64{0.0, 0.0};
+    else if (zc == 2) reinterpret_cast<c32*>(I.C)[b] = c32{0.f, 0.f};
+}
+
 // The same median for float values: a bitonic sort of 32-bit order keys (half the shuffles and
 // compares of the packed 64-bit keys), then the lattice among the keys equal to the median value
 // at rank mid - #(smaller keys) in lattice order, which is the element the packed (value,
@@ -854,8 +859,11 @@ __device__ __forceinline__ int warp_median32(int ka, int kb, int L, int lane) {
 // HASH: the hashes of Itilde are formed here (and stored for the later stages) instead of by a
 // separate k_det_hashes launch (every combine but the hybrid one, which needs the collision counts
 // of all hashes first).
+// zc: the refinement's bucket sums C are zeroed at every bucket of Itilde (1: FP64 buckets, 2: the
+// FP32 buckets of the first half), the only entries its scatter and update touch, instead of
+// clearing all sum M_l entries.
 template <class TS, bool HASH>
-__global__ void k_combine(const InstDesc* __restrict__ insts) {
+__global__ void k_combine(const InstDesc* __restrict__ insts, int zc) {
     const InstDesc& I = insts[blockIdx.y];
     const int64_t nd = min(I.cnt[0], I.cap);
     const int warps = blockDim.x >> 5;
@@ -879,6 +887,7 @@ __global__ void k_combine(const InstDesc* __restrict__ insts) {
             ha = g[b];
             if (glo) la = glo[b];
             if (hybrid) fa = I.coll[b] == 1;
+            zero_bucket(I, b, zc);
         }
         if (lane + 32 < L) {
             int32_t h;
@@ -892,6 +901,7 @@ __global__ void k_combine(const InstDesc* __restrict__ insts) {
             hb = g[b];
             if (glo) lb = glo[b];
             if (hybrid) fb = I.coll[b] == 1;
+            zero_bucket(I, b, zc);
         }
         int lre, lim;
         if (sizeof(TS) == 4 && !glo) {  // plain float buckets: 32-bit keys
@@ -1633,7 +1643,7 @@ int launch_collisions(const InstDesc* di, int ninst, cudaStream_t st) {
     return launch_check("k_collisions");
 }
 
-int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int mode, cudaStream_t st) {
+int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int mode, cudaStream_t st, int zc) {
     const int gx = det_grid(maxdet, ninst);
     if (mode == 1 || mode == 2) {  // 2: FP32 buckets
         if (mode == 2) k_refine_update<float, true><<<dim3(gx, ninst), 256, 0, st>>>(di);
@@ -1642,11 +1652,11 @@ int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int 
         return launch_check("k_refine_update");
     }
     if (mode == 3) {  // combine that forms the hashes of Itilde itself
-        if (prec) k_combine<float, true><<<dim3(gx, ninst), 256, 0, st>>>(di);
-        else k_combine<double, true><<<dim3(gx, ninst), 256, 0, st>>>(di);
+        if (prec) k_combine<float, true><<<dim3(gx, ninst), 256, 0, st>>>(di, zc);
+        else k_combine<double, true><<<dim3(gx, ninst), 256, 0, st>>>(di, zc);
     } else {
-        if (prec) k_combine<float, false><<<dim3(gx, ninst), 256, 0, st>>>(di);
-        else k_combine<double, false><<<dim3(gx, ninst), 256, 0, st>>>(di);
+        if (prec) k_combine<float, false><<<dim3(gx, ninst), 256, 0, st>>>(di, zc);
+        else k_combine<double, false><<<dim3(gx, ninst), 256, 0, st>>>(di, zc);
     }
     return launch_check("k_combine");
 }

@@ -20,7 +20,7 @@ int launch_det_hashes(const InstDesc* di, int ninst, int64_t maxdet, cudaStream_
 int launch_collisions(const InstDesc* di, int ninst, cudaStream_t st);
 // mode 0: combine (median / hybrid), 1: refinement update, 2: refinement update on FP32 buckets,
 // 3: median combine that also forms (and stores) the hashes of Itilde
-int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int mode, cudaStream_t st);
+int launch_combine(const InstDesc* di, int ninst, int64_t maxdet, int prec, int mode, cudaStream_t st, int zc = 0);
 int launch_lsq(InstDesc* di, int ninst, int prec, cudaStream_t st);
 int launch_scatter_coef(const InstDesc* di, int ninst, bool f32, cudaStream_t st);
 int launch_select(InstDesc* di, int ninst, cudaStream_t st);

@@ -655,18 +655,19 @@ def test_batch_set_shapes_from_autotune(G):
 def test_batch_launch_count(G):
     """The launches one batch call enqueues: sampler 1 (the inverse transforms, which sum their
     buckets in shared memory); reconstruction clear, forward transforms, zero test, one hash launch
-    per run of equal d, compaction, combine, select, counts, plus 3 for the refinement (as in the
-    benchmark's launch list: 12 per step)."""
+    per run of equal d, compaction, combine (which also zeroes the refinement's buckets of the
+    detected set), select, counts, plus 2 for the refinement (as in the benchmark's launch list: 11
+    per step)."""
     import torch
     plans = []
     for i, d in enumerate((10, 10, 12)):
         cand = S.uniform_distinct(4000, d, -20, 20, i)
         plans.append(G.Plan(T(cand), 40, precision=1, refine=1, tau_rel=1e-5, seed=i))
     B = G.Batch(plans[:2])
-    assert B.launch_count() == (11, 1)
+    assert B.launch_count() == (10, 1)
     B.close()
     B = G.Batch(plans)
-    assert B.launch_count() == (12, 1)  # d = 10 and d = 12: two hash launches
+    assert B.launch_count() == (11, 1)  # d = 10 and d = 12: two hash launches
     B.close()
     for p in plans:
         p.close()
