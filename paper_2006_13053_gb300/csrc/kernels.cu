@@ -33,6 +33,9 @@ __device__ __forceinline__ void df_acc(float& h, float& l, float a, df64 w) {
     h = s;
 }
 
+// A thread's terms are taken kBdUnroll at a time with their loads issued together (the root-table
+// lookups are gathers), then accumulated in the order j = t, t + B, ... as one at a time would.
+constexpr int kBdUnroll = 4;
 template <class TS>
 __device__ c64 bucket_dft(const cplx<TS>* __restrict__ x, int M, int h, const c64* __restrict__ tab,
                           const cplx<df64>* __restrict__ tabdf, double* red) {
@@ -42,26 +45,49 @@ __device__ c64 bucket_dft(const cplx<TS>* __restrict__ x, int M, int h, const c6
     double re = 0, im = 0;
     if constexpr (sizeof(TS) == 4) {
         float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
-        for (int j = threadIdx.x; j < M; j += B) {
-            const cplx<df64> w = tabdf[ph];
-            const c32 v = x[j];
-            df_acc(rh, rl, v.x, w.x);
-            df_acc(rh, rl, -v.y, w.y);
-            df_acc(ih, il, v.x, w.y);
-            df_acc(ih, il, v.y, w.x);
-            ph += inc;
-            ph = min(ph, ph - uM);  // ph + inc < 2M: one conditional subtraction
+        for (int j0 = threadIdx.x; j0 < M; j0 += kBdUnroll * (int)B) {
+            cplx<df64> w[kBdUnroll];
+            c32 v[kBdUnroll];
+#pragma unroll
+            for (int u = 0; u < kBdUnroll; ++u) {
+                const int j = j0 + u * (int)B;
+                if (j < M) {
+                    w[u] = tabdf[ph];
+                    v[u] = x[j];
+                }
+                ph += inc;
+                ph = min(ph, ph - uM);  // ph + inc < 2M: one conditional subtraction
+            }
+#pragma unroll
+            for (int u = 0; u < kBdUnroll; ++u) {
+                if (j0 + u * (int)B >= M) break;
+                df_acc(rh, rl, v[u].x, w[u].x);
+                df_acc(rh, rl, -v[u].y, w[u].y);
+                df_acc(ih, il, v[u].x, w[u].y);
+                df_acc(ih, il, v[u].y, w[u].x);
+            }
         }
         re = (double)rh + (double)rl;
         im = (double)ih + (double)il;
     } else {
-        for (int j = threadIdx.x; j < M; j += B) {
-            const c64 w = tab[ph];
-            const c64 v = cvt<double>(x[j]);
-            re += v.x * w.x - v.y * w.y;
-            im += v.x * w.y + v.y * w.x;
-            ph += inc;
-            ph = min(ph, ph - uM);
+        for (int j0 = threadIdx.x; j0 < M; j0 += kBdUnroll * (int)B) {
+            c64 w[kBdUnroll], v[kBdUnroll];
+#pragma unroll
+            for (int u = 0; u < kBdUnroll; ++u) {
+                const int j = j0 + u * (int)B;
+                if (j < M) {
+                    w[u] = tab[ph];
+                    v[u] = cvt<double>(x[j]);
+                }
+                ph += inc;
+                ph = min(ph, ph - uM);
+            }
+#pragma unroll
+            for (int u = 0; u < kBdUnroll; ++u) {
+                if (j0 + u * (int)B >= M) break;
+                re += v[u].x * w[u].x - v[u].y * w[u].y;
+                im += v[u].x * w[u].y + v[u].y * w[u].x;
+            }
         }
     }
     // block sums of re, im
@@ -107,7 +133,7 @@ constexpr int kZtThreads = 512;
 constexpr int kGuardCap = 1024;
 
 template <class TS>
-__global__ void __launch_bounds__(kZtThreads) k_zero_test(const LatDesc* __restrict__ lats, InstDesc* __restrict__ insts,
+__global__ void __launch_bounds__(kZtThreads, 2) k_zero_test(const LatDesc* __restrict__ lats, InstDesc* __restrict__ insts,
                                                           double kappa_u_log) {
     __shared__ double red[72];
     __shared__ int glist[kGuardCap];
