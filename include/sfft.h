@@ -239,9 +239,12 @@ int sfft_reconstruct_shard_end(sfft_plan* plan, const double* C_sum, int64_t* su
  *   kvec  device int32 [n_terms, d];  coef device complex double [n_terms];
  *   noise device complex [sum M] in the plan precision, or NULL;  samples_out device complex
  *   (plan precision).
- * Computed exactly through eq. (2.3): the coefficients are scattered into their buckets
- * k.z_l mod M_l and each lattice is inverse-transformed.  FP32 plans form buckets, transform
- * and noise sum in FP32 (samples within a few FP32 ulps of the exact value plus noise).
+ * Computed exactly through eq. (2.3): the coefficients are summed into their buckets
+ * k.z_l mod M_l and each lattice is inverse-transformed (a transform whose work buffer fits one
+ * CTA's shared memory sums its buckets there; the others take a global bucket pass first).  FP32
+ * plans form buckets, transform and noise sum in FP32 (samples within a few FP32 ulps of the exact
+ * value plus noise).  Bucket sums are formed by atomic additions, so a bucket of three or more
+ * terms may round differently from one call to the next.
  * Asynchronous on the plan stream.
  */
 int sfft_sample_sparse_poly(const sfft_plan* plan, const int32_t* kvec, const double* coef, int64_t n_terms,
@@ -352,8 +355,9 @@ int sfft_batch_launch_count(sfft_batch* b, int* reconstruct, int* sampler);
 int sfft_batch_flags(sfft_batch* b, int64_t* flags);
 
 /*
- * sfft_sample_sparse_poly for every plan of the batch in shared launches (one bucket scatter,
- * one inverse-transform launch).  Arrays are indexed by the caller's plan order: kvec[i]
+ * sfft_sample_sparse_poly for every plan of the batch in shared launches (one inverse-transform
+ * launch per work-buffer mode, plus a clear and a bucket scatter when some transform does not fit
+ * one CTA's shared memory).  Arrays are indexed by the caller's plan order: kvec[i]
  * device int32 [n_terms[i], d_i]; coef[i] device complex double; noise NULL or noise[i] device
  * complex [sum M] in the plan precision (may be NULL); samples_out[i] device complex (plan
  * precision).

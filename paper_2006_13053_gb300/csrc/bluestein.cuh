@@ -549,23 +549,57 @@ struct BlueIo {  // SMB: buffer in shared memory (padded layout); CL: split over
         for (int e = threadIdx.x; e < N; e += blockDim.x) *at(e) = cplx<T>{kc<T>(0.0), kc<T>(0.0)};
         __syncthreads();
         const int d = I.d;
-        const int64_t Ml = M;
         const int32_t* __restrict__ kv = I.samp_kvec;
         const int32_t* __restrict__ zl = I.z + (int64_t)l * d;
+        // h = k.z mod M term by term in 32-bit arithmetic: |k_t| mod M by a Barrett reduction
+        // (mu = floor((2^32 - 1) / M) leaves a remainder below 2M for any operand below 2^32: one
+        // conditional subtraction), its sign applied, then the product with z_t < M, below M^2 <
+        // 2^32 while M < 2^16 (always so for a buffer in one CTA's shared memory), reduced the same
+        // way; larger M take the int64 sum and remainder
+        const uint32_t uM = (uint32_t)M, mu = 0xffffffffu / uM;
+        auto red = [&](uint32_t x) -> uint32_t {
+            const uint32_t r = x - __umulhi(x, mu) * uM;
+            return min(r, r - uM);
+        };
         for (int64_t q = threadIdx.x; q < I.samp_nterms; q += blockDim.x) {
-            int64_t x = 0;
-            for (int t = 0; t < d; ++t) x += (int64_t)kv[q * d + t] * zl[t];
-            int64_t r = x % Ml;
-            if (r < 0) r += Ml;
+            uint32_t h = 0;
+            if (uM < 65536u) {
+                for (int t = 0; t < d; ++t) {
+                    const int32_t k = kv[q * d + t];
+                    uint32_t rk = red(k < 0 ? 0u - (uint32_t)k : (uint32_t)k);
+                    if (k < 0 && rk) rk = uM - rk;
+                    h += red(rk * (uint32_t)zl[t]);
+                    h = min(h, h - uM);
+                }
+            } else {
+                int64_t x = 0;
+                for (int t = 0; t < d; ++t) x += (int64_t)kv[q * d + t] * zl[t];
+                int64_t r = x % (int64_t)M;
+                if (r < 0) r += M;
+                h = (uint32_t)r;
+            }
             const cplx<T> v = ccv<T>(I.samp_coef[q]);
-            cplx<T>* p = at((int)r);
+            cplx<T>* p = at((int)h);
             atomicAdd(&p->x, v.x);
             atomicAdd(&p->y, v.y);
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < M; e += blockDim.x) {
-            const cplx<T> x = *at(e), w = ldg(&chirp[e]);
-            *at(e) = inv ? mulc(x, w) : x * w;
+        for (int b = threadIdx.x; b < M; b += kIoUnroll * (int)blockDim.x) {
+            cplx<T> xv[kIoUnroll], wv[kIoUnroll];
+#pragma unroll
+            for (int u = 0; u < kIoUnroll; ++u) {
+                const int e = b + u * (int)blockDim.x;
+                if (e < M) {
+                    xv[u] = *at(e);
+                    wv[u] = ldg(&chirp[e]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kIoUnroll; ++u) {
+                const int e = b + u * (int)blockDim.x;
+                if (e >= M) break;
+                *at(e) = inv ? mulc(xv[u], wv[u]) : xv[u] * wv[u];
+            }
         }
     }
     // outputs j in [e0, e1), e1 <= M: chirp product, scale and the epilogue (the noise of
