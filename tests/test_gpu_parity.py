@@ -314,6 +314,27 @@ def test_sampler_and_points(G, prec):
     assert np.max(np.abs(y - ref)) <= tol * np.sqrt(np.sum(np.abs(c) ** 2)) * 10
 
 
+@pytest.mark.parametrize("prec", [0, 1])
+def test_sampler_extreme_frequencies(G, prec):
+    """Bucket hashes of sampler terms with |k_t| up to 2^31 (int32 extremes, both signs) in the
+    transform that sums its own buckets (M = 211, one CTA's shared memory; 32-bit modular
+    reduction term by term) against the oracle's aliasing formula on exact int64 hashes."""
+    cand, sup, c, z, M, L = cfg1(7)
+    plan = G.Plan(T(cand), 20, L=L, M=[M] * L, z=z, precision=prec)
+    rng = np.random.default_rng(7)
+    big = np.array([2 ** 31 - 1, -2 ** 31, -2 ** 31 + 1, 2 ** 31 - 2], dtype=np.int64)
+    kv = rng.integers(-2 ** 31, 2 ** 31, size=(24, 3), dtype=np.int64)
+    kv[:4, 0] = big
+    kv[4:8, 1] = big
+    kv[8:12, 2] = big[::-1]
+    kv = kv.astype(np.int32)
+    cf = S.coef_cgauss(24, 7)
+    y = plan.sample_sparse_poly(T(kv), T(cf)).cpu().numpy()
+    ref = O.sample_sparse_poly_aliasing(kv.astype(np.int64), cf, z, M)
+    tol = 1e-12 if prec == 0 else 3e-6
+    assert np.max(np.abs(y - ref)) <= tol * np.sqrt(np.sum(np.abs(cf) ** 2)) * 10
+
+
 # ------------------------------------------------------------------ Algorithm 1, Remark 2.8, Algorithm 4
 def test_alg1_nu_quarter(G):
     cand, sup, c, z, M, L = cfg1(7)
