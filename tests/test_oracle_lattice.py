@@ -124,3 +124,11 @@ def test_aliasing_sampler_equals_direct_sum():
         a = O.sample_sparse_poly(kv, c, z, Ms)
         b = O.sample_sparse_poly_aliasing(kv, c, z, Ms)
         assert np.max(np.abs(a - b)) <= 1e-12 * np.sqrt(s) * np.max(np.abs(c))
+    # frequencies over the whole int32 range (both extremes): the hashes are exact int64 residues
+    kv = rng.integers(-2 ** 31, 2 ** 31, size=(24, 3), dtype=np.int64)
+    kv[:4, 0] = [2 ** 31 - 1, -2 ** 31, -2 ** 31 + 1, 2 ** 31 - 2]
+    c = S.coef_cgauss(24, 5)
+    z = np.stack([rng.integers(0, 211, size=3) for _ in range(4)])
+    a = O.sample_sparse_poly(kv, c, z, [211] * 4)
+    b = O.sample_sparse_poly_aliasing(kv, c, z, [211] * 4)
+    assert np.max(np.abs(a - b)) <= 1e-12 * np.sqrt(24) * np.max(np.abs(c))
